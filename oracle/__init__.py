@@ -1,0 +1,285 @@
+"""FP64 CPU oracle of the 4D Gaussian Splatting render path (arXiv 2412.20720).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  The
+product path (``paper_2412_20720_gb300``) never imports it, and this package
+never imports the product path: the two share no code.  The only thing both
+sides consume is the seeded synthetic input (plain FP32 arrays).
+
+This module is argument marshalling over ``fgs4d_oracle.c``; every formula
+lives in the C file, each function citing the passage it follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import build_oracle, library_path
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            build_oracle()
+        _lib = C.CDLL(path)
+        _declare(_lib)
+    return _lib
+
+
+class _Params(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("q_l", C.c_void_p),
+                ("q_r", C.c_void_p), ("opacity_logit", C.c_void_p), ("sh", C.c_void_p),
+                ("n", C.c_int64)]
+
+
+class _View(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("pad0", C.c_int32), ("pad1", C.c_int32),
+                ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("viewmat", C.c_double * 12), ("campos", C.c_double * 3), ("t", C.c_double)]
+
+
+class _Settings(C.Structure):
+    _fields_ = [("sh_degree", C.c_int32), ("t_order", C.c_int32), ("tile", C.c_int32), ("pad", C.c_int32),
+                ("period", C.c_double), ("near_plane", C.c_double), ("dilation", C.c_double),
+                ("p_t_min", C.c_double), ("bg", C.c_double * 3)]
+
+
+_PROJ_FIELDS = [("status", np.int32, 1), ("rect", np.int32, 4), ("p_t", np.float64, 1),
+                ("a_eff", np.float64, 1), ("mu3", np.float64, 3), ("cov3", np.float64, 9),
+                ("pc", np.float64, 3), ("cov2d", np.float64, 3), ("conic", np.float64, 3),
+                ("uv", np.float64, 2), ("radius", np.float64, 1), ("depth", np.float64, 1),
+                ("rgb", np.float64, 3), ("margin", np.float64, 1), ("depth_f32", np.float32, 1)]
+
+
+class _Proj(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name, _, _ in _PROJ_FIELDS]
+
+
+_GRAD_FIELDS = ["mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh", "g_uv", "g_conic", "g_a", "g_rgb"]
+
+
+class _Grads(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in _GRAD_FIELDS]
+
+
+def _declare(lib):
+    P = C.POINTER
+    lib.orc_preprocess.argtypes = [P(_Params), P(_View), P(_Settings), P(_Proj)]
+    lib.orc_preprocess.restype = C.c_int
+    lib.orc_render.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_render.restype = C.c_int
+    lib.orc_render_pixels.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), C.c_int64, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_render_pixels.restype = C.c_int
+    lib.orc_render_backward.argtypes = [P(_Params), P(_View), P(_Settings), P(_Proj), C.c_void_p, P(_Grads)]
+    lib.orc_render_backward.restype = C.c_int
+    lib.orc_preprocess_backward.argtypes = [P(_Params), P(_View), P(_Settings), C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, P(_Grads)]
+    lib.orc_preprocess_backward.restype = C.c_int
+    lib.orc_rotation.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_rotation.restype = None
+    lib.orc_real_sh.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
+    lib.orc_real_sh.restype = None
+    lib.orc_sort_instances.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int64,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_sort_instances.restype = C.c_int64
+    lib.orc_num_threads.argtypes = []
+    lib.orc_num_threads.restype = C.c_int
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+@dataclass
+class Settings:
+    """Render settings (the readings where the paper is silent)."""
+    sh_degree: int = 3
+    t_order: int = 2
+    tile: int = 16
+    period: float = 1.0
+    near_plane: float = 0.2
+    dilation: float = 0.3
+    p_t_min: float = 0.05
+    bg: tuple = (0.0, 0.0, 0.0)
+
+    def _c(self) -> _Settings:
+        s = _Settings()
+        s.sh_degree, s.t_order, s.tile = self.sh_degree, self.t_order, self.tile
+        s.period, s.near_plane, s.dilation, s.p_t_min = self.period, self.near_plane, self.dilation, self.p_t_min
+        for k in range(3):
+            s.bg[k] = self.bg[k]
+        return s
+
+
+def _view_c(view) -> _View:
+    """``view``: mapping with width, height, fx, fy, cx, cy, viewmat (3x4),
+    campos (3), t.  Values are taken as given (the FP32 values the GPU sees
+    should be passed to compare like with like)."""
+    v = _View()
+    v.width, v.height = int(view["width"]), int(view["height"])
+    v.fx, v.fy, v.cx, v.cy = (float(view[k]) for k in ("fx", "fy", "cx", "cy"))
+    vm = np.asarray(view["viewmat"], dtype=np.float64).reshape(12)
+    for k in range(12):
+        v.viewmat[k] = vm[k]
+    cp = np.asarray(view["campos"], dtype=np.float64).reshape(3)
+    for k in range(3):
+        v.campos[k] = cp[k]
+    v.t = float(view["t"])
+    return v
+
+
+class _ParamsHold:
+    def __init__(self, params):
+        # FP32 inputs are upcast exactly; FP64 inputs (finite differences) pass through.
+        self.arrs = {k: np.ascontiguousarray(params[k], dtype=np.float64)
+                     for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")}
+        n = self.arrs["mean"].shape[0]
+        self.c = _Params(*(_ptr(self.arrs[k]) for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")),
+                         n)
+        self.n = n
+
+
+def preprocess(params, view, settings: Settings):
+    """Per-Gaussian forward chain (FP64).  Returns a dict of arrays."""
+    lib = _load()
+    ph = _ParamsHold(params)
+    n = ph.n
+    out = {}
+    for name, dt, w in _PROJ_FIELDS:
+        out[name] = np.zeros((n, w) if w > 1 else (n,), dtype=dt)
+    pc = _Proj(*(_ptr(out[name]) for name, _, _ in _PROJ_FIELDS))
+    rc = lib.orc_preprocess(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), C.byref(pc))
+    if rc != 0:
+        raise ValueError("oracle preprocess rejected the settings")
+    return out
+
+
+def _proj_c(proj):
+    arrs = [np.ascontiguousarray(proj[name]) for name, _, _ in _PROJ_FIELDS]
+    return _Proj(*(_ptr(a) for a in arrs)), arrs
+
+
+def render(proj, view, settings: Settings, signature: bool = False):
+    """Full image (FP64): returns img [3,H,W], T [H,W], ncontrib [H,W], margin [H,W]
+    (and, if asked, the per-pixel signature: contributors + 65536 * clamped)."""
+    lib = _load()
+    W, H = int(view["width"]), int(view["height"])
+    n = proj["status"].shape[0]
+    img = np.zeros((3, H, W))
+    T = np.zeros((H, W))
+    nc = np.zeros((H, W), dtype=np.int32)
+    mg = np.zeros((H, W))
+    sig = np.zeros((H, W), dtype=np.int32)
+    pc, keep = _proj_c(proj)
+    rc = lib.orc_render(C.byref(_view_c(view)), C.byref(settings._c()), n, C.byref(pc), _ptr(img), _ptr(T),
+                        _ptr(nc), _ptr(mg), _ptr(sig))
+    if rc != 0:
+        raise MemoryError("oracle render failed")
+    if signature:
+        return img, T, nc, mg, sig
+    return img, T, nc, mg
+
+
+def render_pixels(proj, view, settings: Settings, pix: np.ndarray):
+    """Selected pixels (linear ids py*W+px): rgb [P,3], T [P], ncontrib [P], margin [P]."""
+    lib = _load()
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    n = proj["status"].shape[0]
+    rgb = np.zeros((pix.shape[0], 3))
+    T = np.zeros(pix.shape[0])
+    nc = np.zeros(pix.shape[0], dtype=np.int32)
+    mg = np.zeros(pix.shape[0])
+    pc, keep = _proj_c(proj)
+    rc = lib.orc_render_pixels(C.byref(_view_c(view)), C.byref(settings._c()), n, C.byref(pc), pix.shape[0],
+                               _ptr(pix), _ptr(rgb), _ptr(T), _ptr(nc), _ptr(mg))
+    if rc != 0:
+        raise MemoryError("oracle render_pixels failed")
+    return rgb, T, nc, mg
+
+
+def _alloc_grads(n, K):
+    shapes = {"mean": (n, 4), "log_scale": (n, 4), "q_l": (n, 4), "q_r": (n, 4), "opacity_logit": (n,),
+              "sh": (n, K, 3), "g_uv": (n, 2), "g_conic": (n, 3), "g_a": (n,), "g_rgb": (n, 3)}
+    g = {k: np.zeros(s) for k, s in shapes.items()}
+    return g, _Grads(*(_ptr(g[k]) for k in _GRAD_FIELDS))
+
+
+def render_backward(params, proj, view, settings: Settings, dimg: np.ndarray):
+    """Exact reverse-mode gradient (FP64) of <dimg, image> w.r.t. the
+    parameters; also returns the per-Gaussian 2D gradients."""
+    lib = _load()
+    ph = _ParamsHold(params)
+    K = ph.arrs["sh"].shape[1]
+    g, gc = _alloc_grads(ph.n, K)
+    dimg = np.ascontiguousarray(dimg, dtype=np.float64)
+    pc, keep = _proj_c(proj)
+    rc = lib.orc_render_backward(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), C.byref(pc),
+                                 _ptr(dimg), C.byref(gc))
+    if rc != 0:
+        raise MemoryError("oracle backward failed")
+    return g
+
+
+def preprocess_backward(params, view, settings: Settings, g_uv, g_conic, g_a, g_rgb):
+    """Adjoint of the per-Gaussian chain alone, from given 2D gradients."""
+    lib = _load()
+    ph = _ParamsHold(params)
+    K = ph.arrs["sh"].shape[1]
+    g, gc = _alloc_grads(ph.n, K)
+    ins = [np.ascontiguousarray(a, dtype=np.float64) for a in (g_uv, g_conic, g_a, g_rgb)]
+    lib.orc_preprocess_backward(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()),
+                                *(_ptr(a) for a in ins), C.byref(gc))
+    return g
+
+
+def rotation(q_l, q_r) -> np.ndarray:
+    """R = L(q_l) R(q_r) for the normalised quaternions (4x4)."""
+    lib = _load()
+    a = np.ascontiguousarray(q_l, dtype=np.float64)
+    b = np.ascontiguousarray(q_r, dtype=np.float64)
+    R = np.zeros((4, 4))
+    lib.orc_rotation(_ptr(a), _ptr(b), _ptr(R))
+    return R
+
+
+def real_sh(L: int, direction) -> np.ndarray:
+    """Real orthonormal SH values Y_lm (index l*l+l+m) at a unit direction."""
+    lib = _load()
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    Y = np.zeros((L + 1) ** 2)
+    lib.orc_real_sh(L, _ptr(d), _ptr(Y))
+    return Y
+
+
+def sort_instances(rect, depth_f32, grid_w: int, grid_h: int, cap: int | None = None):
+    """Tile-binned instance list sorted by (tile, FP32 depth, index).
+    Returns (keys u64 [M], vals i64 [M], ranges i64 [tiles, 2])."""
+    lib = _load()
+    rect = np.ascontiguousarray(rect, dtype=np.int32)
+    depth_f32 = np.ascontiguousarray(depth_f32, dtype=np.float32)
+    n = rect.shape[0]
+    w = np.clip(rect[:, 2] - rect[:, 0], 0, None).astype(np.int64)
+    h = np.clip(rect[:, 3] - rect[:, 1], 0, None).astype(np.int64)
+    m = int((w * h).sum())
+    cap = m if cap is None else cap
+    keys = np.zeros(max(m, 1), dtype=np.uint64)
+    vals = np.zeros(max(m, 1), dtype=np.int64)
+    ranges = np.zeros((grid_w * grid_h, 2), dtype=np.int64)
+    got = lib.orc_sort_instances(n, _ptr(rect), _ptr(depth_f32), grid_w, grid_h, cap, _ptr(keys), _ptr(vals),
+                                 _ptr(ranges))
+    if got < 0:
+        raise ValueError("instance count exceeds capacity")
+    return keys[:got], vals[:got], ranges
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())

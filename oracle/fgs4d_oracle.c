@@ -1,0 +1,948 @@
+/*
+ * fgs4d_oracle.c -- plain FP64 CPU oracle of the 4D Gaussian Splatting render
+ * path (forward image and its exact reverse-mode derivative).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * execute this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header, table or helper with the
+ * CUDA path.  Inputs are the same FP32 parameter arrays the GPU receives,
+ * upcast to FP64; every formula below is the paper's definition written out
+ * directly, with no blocking, fusion or reordering.
+ *
+ * Paper: "4D Gaussian Splatting: Modeling Dynamic Scenes with Native 4D
+ * Primitives" (arXiv 2412.20720).
+ *   Sec. 3.1, Eq. 1          unnormalized Gaussian
+ *   Sec. 3.1, Eqs. 3-4       EWA projection of mean and covariance
+ *   Sec. 3.2, Eqs. 5-6       4D pixel blending, p(u,v,t) = p(t) p(u,v|t)
+ *   Sec. 3.2                 Sigma = R S S^T R^T, R = L(q_l) R(q_r)
+ *   Sec. 3.2                 conditional 3D Gaussian and marginal p(t)
+ *   Sec. 3.2                 4D spherindrical harmonics Z_nl^m
+ *   Sec. 7.1.1 (impl.)       temporal filter p(t) < 0.05
+ * Readings where the paper is silent (compositing constants 1/255, 0.99, 1e-4,
+ * 3-sigma extent, pixel centres, rect membership, colour offset) follow the
+ * tile rasterizer the paper adapts (Sec. 3.2, last paragraph of
+ * "Representation of 4D Gaussian") and are listed in the design notes.
+ *
+ * Parity pins for every function here live in tests/test_oracle_pins.py and
+ * tests/test_oracle_grad_fd.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_MAX_L 3
+#define ORC_MAX_N 8
+
+/* ------------------------------------------------------------------ types */
+
+/* Parameters in FP64 (the caller upcasts the FP32 arrays the GPU gets). */
+typedef struct {
+  const double *mean;          /* [n][4] (x, y, z, t) */
+  const double *log_scale;     /* [n][4] log(s_x, s_y, s_z, s_t) */
+  const double *q_l;           /* [n][4] (a, b, c, d), not necessarily unit */
+  const double *q_r;           /* [n][4] (p, q, r, s) */
+  const double *opacity_logit; /* [n] */
+  const double *sh;            /* [n][K][3], K = (L+1)^2 (n_max+1) */
+  int64_t n;
+} orc_params;
+
+typedef struct {
+  int32_t width, height, pad0, pad1;
+  double fx, fy, cx, cy;
+  double viewmat[12]; /* world -> camera, row-major 3x4 [W | T] */
+  double campos[3];   /* camera centre in world coordinates */
+  double t;           /* render timestamp */
+} orc_view;
+
+typedef struct {
+  int32_t sh_degree, t_order, tile, pad;
+  double period;     /* T of the temporal Fourier basis */
+  double near_plane; /* cull when camera-space z <= near_plane */
+  double dilation;   /* added to the diagonal of the 2D covariance */
+  double p_t_min;    /* temporal filter threshold (0.05) */
+  double bg[3];
+} orc_settings;
+
+typedef struct {
+  int32_t *status; /* [n] 0 visible; 1 invalid; 2 temporal; 3 near; 4 det; 5 rect */
+  int32_t *rect;   /* [n][4] tile rect x0, y0, x1, y1 (half-open) */
+  double *p_t;     /* [n] marginal temporal weight */
+  double *a_eff;   /* [n] sigmoid(logit) * p_t */
+  double *mu3;     /* [n][3] conditional mean at t */
+  double *cov3;    /* [n][9] conditional covariance at t */
+  double *pc;      /* [n][3] camera-space centre */
+  double *cov2d;   /* [n][3] 2D covariance (xx, xy, yy) incl. dilation */
+  double *conic;   /* [n][3] inverse 2D covariance (A, B, C) */
+  double *uv;      /* [n][2] projected centre in pixels */
+  double *radius;  /* [n] 3-sigma radius in pixels (integer valued) */
+  double *depth;   /* [n] camera-space z */
+  double *rgb;     /* [n][3] 4DSH colour after offset and clamp */
+  double *margin;  /* [n] relative distance of the closest discrete decision */
+  float *depth_f32;/* [n] depth rounded to FP32 (the sort key) */
+} orc_proj;
+
+typedef struct {
+  double *mean;          /* [n][4] */
+  double *log_scale;     /* [n][4] */
+  double *q_l;           /* [n][4] */
+  double *q_r;           /* [n][4] */
+  double *opacity_logit; /* [n] */
+  double *sh;            /* [n][K][3] */
+  double *g_uv;          /* [n][2]  dL/d(u, v) */
+  double *g_conic;       /* [n][3]  dL/d(A, B, C) */
+  double *g_a;           /* [n]     dL/d(effective opacity) */
+  double *g_rgb;         /* [n][3]  dL/d(colour) */
+} orc_grads;
+
+/* Per-Gaussian intermediate values of the forward chain, kept for the
+ * adjoint. */
+typedef struct {
+  double m[4], ls[4], ql[4], qr[4], logit;
+  double s[4], sig, qln[4], qrn[4], nql, nqr;
+  double Lm[16], Rm[16], R[16], S[16];
+  double dt, c, pt, b[3];
+  double mu3[3], cov3[9];
+  double pc[3];
+  double J[6], M[6];
+  double cov2[4], det, conic[3], uv[2], lam, radius;
+  int rect[4];
+  double w[3], rw, dir[3];
+  int L, NT, K;
+  double Y[(ORC_MAX_L + 1) * (ORC_MAX_L + 1)];
+  double cosn[ORC_MAX_N + 1], sinn[ORC_MAX_N + 1];
+  double raw[3], rgb[3];
+  double a;
+  int status;
+  double margin;
+} orc_ctx;
+
+/* ------------------------------------------------------------ helpers */
+
+static double dmin(double a, double b) { return a < b ? a : b; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+
+static void mat4_mul(const double *A, const double *B, double *C) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 4; ++k) acc += A[4 * i + k] * B[4 * k + j];
+      C[4 * i + j] = acc;
+    }
+}
+
+/* Left isoclinic rotation matrix L(q_l), Sec. 3.2 (first printed matrix). */
+static void left_matrix(const double *q, double *L) {
+  const double a = q[0], b = q[1], c = q[2], d = q[3];
+  const double v[16] = {a, -b, -c, -d,
+                        b,  a, -d,  c,
+                        c,  d,  a, -b,
+                        d, -c,  b,  a};
+  memcpy(L, v, sizeof v);
+}
+
+/* Right isoclinic rotation matrix R(q_r), Sec. 3.2 (second printed matrix). */
+static void right_matrix(const double *q, double *R) {
+  const double p = q[0], qq = q[1], r = q[2], s = q[3];
+  const double v[16] = {p, -qq,  -r,  -s,
+                        qq,  p,   s,  -r,
+                        r,  -s,   p,  qq,
+                        s,   r, -qq,   p};
+  memcpy(R, v, sizeof v);
+}
+
+/* Associated Legendre functions P_l^m(x), m >= 0, with the Condon-Shortley
+ * phase, by the standard three-term recurrence in l.  P[l][m]. */
+static void legendre(int L, double x, double P[ORC_MAX_L + 2][ORC_MAX_L + 2]) {
+  memset(P, 0, sizeof(double) * (ORC_MAX_L + 2) * (ORC_MAX_L + 2));
+  const double sx = sqrt(dmax(0.0, 1.0 - x * x));
+  double pmm = 1.0;
+  for (int m = 0; m <= L; ++m) {
+    if (m > 0) pmm *= -(2.0 * m - 1.0) * sx; /* P_m^m = (-1)^m (2m-1)!! (1-x^2)^(m/2) */
+    P[m][m] = pmm;
+    if (m + 1 <= L) P[m + 1][m] = x * (2.0 * m + 1.0) * pmm;
+    for (int l = m + 2; l <= L; ++l)
+      P[l][m] = ((2.0 * l - 1.0) * x * P[l - 1][m] - (l + m - 1.0) * P[l - 2][m]) / (l - m);
+  }
+}
+
+static double factorial(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return f;
+}
+
+/* Real spherical harmonics Y_lm(theta, phi), orthonormal on the sphere,
+ * from the complex ones with the Condon-Shortley phase kept in P_l^m:
+ *   m > 0: sqrt(2) K_l^m P_l^m(cos th) cos(m ph)
+ *   m = 0: K_l^0 P_l^0(cos th)
+ *   m < 0: sqrt(2) K_l^|m| P_l^|m|(cos th) sin(|m| ph)
+ * with K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).  Index l*l + l + m.
+ * Optionally returns dY/dtheta and dY/dphi. */
+static void real_sh(int L, double theta, double phi, double *Y, double *dYdth, double *dYdph) {
+  double P[ORC_MAX_L + 2][ORC_MAX_L + 2];
+  const double x = cos(theta), st = sin(theta);
+  legendre(L + 1, x, P);
+  for (int l = 0; l <= L; ++l) {
+    for (int m = -l; m <= l; ++m) {
+      const int am = m < 0 ? -m : m;
+      double K = sqrt((2.0 * l + 1.0) / (4.0 * ORC_PI) * factorial(l - am) / factorial(l + am));
+      if (m != 0) K *= sqrt(2.0);
+      double trig, dtrig;
+      if (m > 0) { trig = cos(m * phi); dtrig = -m * sin(m * phi); }
+      else if (m < 0) { trig = sin(am * phi); dtrig = am * cos(am * phi); }
+      else { trig = 1.0; dtrig = 0.0; }
+      const int idx = l * l + l + m;
+      Y[idx] = K * P[l][am] * trig;
+      if (dYdth) {
+        /* dP_l^m/dtheta = (l x P_l^m - (l+m) P_{l-1}^m) / sin(theta), from
+         * (x^2-1) dP_l^m/dx = l x P_l^m - (l+m) P_{l-1}^m, x = cos(theta). */
+        const double plm1 = (l - 1 >= am) ? P[l - 1][am] : 0.0;
+        const double dPdth = (l * x * P[l][am] - (l + am) * plm1) / st;
+        dYdth[idx] = K * dPdth * trig;
+        dYdph[idx] = K * P[l][am] * dtrig;
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------ forward chain */
+
+static int is_finite4(const double *v) {
+  return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
+}
+
+/* Relative closeness of a value to an integer boundary (for margins). */
+static double frac_margin(double x, double scale) {
+  const double d = fabs(x - nearbyint(x));
+  return d / dmax(1.0, scale);
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Forward chain for Gaussian i at one view: Sec. 3.2 (covariance, rotation,
+ * conditional and marginal), Sec. 3.1 Eqs. 3-4 (EWA projection), Sec. 3.2
+ * (4D spherindrical harmonic colour), Sec. 7.1.1 (temporal filter). */
+static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
+                          const orc_settings *S, orc_ctx *g) {
+  memset(g, 0, sizeof *g);
+  g->margin = INFINITY;
+  for (int k = 0; k < 4; ++k) {
+    g->m[k] = P->mean[4 * i + k];
+    g->ls[k] = P->log_scale[4 * i + k];
+    g->ql[k] = P->q_l[4 * i + k];
+    g->qr[k] = P->q_r[4 * i + k];
+  }
+  g->logit = P->opacity_logit[i];
+  g->L = S->sh_degree;
+  g->NT = S->t_order;
+  g->K = (g->L + 1) * (g->L + 1) * (g->NT + 1);
+
+  if (!is_finite4(g->m) || !is_finite4(g->ls) || !is_finite4(g->ql) ||
+      !is_finite4(g->qr) || !isfinite(g->logit)) {
+    g->status = 1;
+    return;
+  }
+  /* Activations: s = exp(log s), alpha = sigmoid(logit), unit quaternions. */
+  for (int k = 0; k < 4; ++k) g->s[k] = exp(g->ls[k]);
+  g->sig = 1.0 / (1.0 + exp(-g->logit));
+  g->nql = sqrt(g->ql[0] * g->ql[0] + g->ql[1] * g->ql[1] + g->ql[2] * g->ql[2] + g->ql[3] * g->ql[3]);
+  g->nqr = sqrt(g->qr[0] * g->qr[0] + g->qr[1] * g->qr[1] + g->qr[2] * g->qr[2] + g->qr[3] * g->qr[3]);
+  if (!(g->nql > 0.0) || !(g->nqr > 0.0)) {
+    g->status = 1;
+    return;
+  }
+  for (int k = 0; k < 4; ++k) {
+    g->qln[k] = g->ql[k] / g->nql;
+    g->qrn[k] = g->qr[k] / g->nqr;
+  }
+  /* R = L(q_l) R(q_r); Sigma = R S S^T R^T with S = diag(s). */
+  left_matrix(g->qln, g->Lm);
+  right_matrix(g->qrn, g->Rm);
+  mat4_mul(g->Lm, g->Rm, g->R);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      double acc = 0.0;
+      for (int k = 0; k < 4; ++k) acc += g->R[4 * a + k] * g->R[4 * b + k] * g->s[k] * g->s[k];
+      g->S[4 * a + b] = acc;
+    }
+  /* Marginal p(t) = N(t; mu_4, Sigma_44), used unnormalized (Sec. 3.1). */
+  g->dt = V->t - g->m[3];
+  g->c = g->S[15];
+  g->pt = exp(-0.5 * g->dt * g->dt / g->c);
+  g->margin = dmin(g->margin, fabs(g->pt - S->p_t_min) / S->p_t_min);
+  if (!(g->pt >= S->p_t_min)) {
+    g->status = 2;
+    return;
+  }
+  /* Conditional 3D Gaussian at t (Sec. 3.2). */
+  for (int a = 0; a < 3; ++a) g->b[a] = g->S[4 * a + 3];
+  for (int a = 0; a < 3; ++a) g->mu3[a] = g->m[a] + g->b[a] * g->dt / g->c;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      g->cov3[3 * a + b] = g->S[4 * a + b] - g->b[a] * g->b[b] / g->c;
+  /* Camera-space centre. */
+  const double *W = V->viewmat;
+  for (int a = 0; a < 3; ++a)
+    g->pc[a] = W[4 * a + 0] * g->mu3[0] + W[4 * a + 1] * g->mu3[1] + W[4 * a + 2] * g->mu3[2] + W[4 * a + 3];
+  const double x = g->pc[0], y = g->pc[1], z = g->pc[2];
+  g->margin = dmin(g->margin, fabs(z - S->near_plane) / dmax(S->near_plane, 1e-3));
+  if (!(z > S->near_plane)) {
+    g->status = 3;
+    return;
+  }
+  /* Eq. 4: Sigma_2d = (J W Sigma W^T J^T)_{1:2,1:2} + dilation I. */
+  g->J[0] = V->fx / z; g->J[1] = 0.0;       g->J[2] = -V->fx * x / (z * z);
+  g->J[3] = 0.0;       g->J[4] = V->fy / z; g->J[5] = -V->fy * y / (z * z);
+  for (int r = 0; r < 2; ++r)
+    for (int col = 0; col < 3; ++col) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += g->J[3 * r + k] * W[4 * k + col];
+      g->M[3 * r + col] = acc;
+    }
+  for (int r = 0; r < 2; ++r)
+    for (int col = 0; col < 2; ++col) {
+      double acc = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) acc += g->M[3 * r + a] * g->cov3[3 * a + b] * g->M[3 * col + b];
+      g->cov2[2 * r + col] = acc + (r == col ? S->dilation : 0.0);
+    }
+  g->det = g->cov2[0] * g->cov2[3] - g->cov2[1] * g->cov2[2];
+  g->margin = dmin(g->margin, g->det / (fabs(g->cov2[0] * g->cov2[3]) + 1e-300));
+  if (!(g->det > 0.0)) {
+    g->status = 4;
+    return;
+  }
+  g->conic[0] = g->cov2[3] / g->det;
+  g->conic[1] = -g->cov2[1] / g->det;
+  g->conic[2] = g->cov2[0] / g->det;
+  /* Eq. 3: projected centre (pixel coordinates, pinhole K). */
+  g->uv[0] = V->fx * x / z + V->cx;
+  g->uv[1] = V->fy * y / z + V->cy;
+  /* 3-sigma extent from the largest eigenvalue (floor 0.1 under the root). */
+  const double mid = 0.5 * (g->cov2[0] + g->cov2[3]);
+  const double disc = mid * mid - g->det;
+  g->margin = dmin(g->margin, fabs(disc - 0.1) / dmax(mid * mid, 1.0));
+  g->lam = mid + sqrt(dmax(0.1, disc));
+  const double r3 = 3.0 * sqrt(g->lam);
+  g->radius = ceil(r3);
+  g->margin = dmin(g->margin, frac_margin(r3, r3));
+  /* Tile rect: tiles whose pixel range meets [u - r, u + r] x [v - r, v + r]. */
+  const double B = (double)S->tile;
+  const int gw = (V->width + S->tile - 1) / S->tile, gh = (V->height + S->tile - 1) / S->tile;
+  const double ex[4] = {(g->uv[0] - g->radius) / B, (g->uv[1] - g->radius) / B,
+                        (g->uv[0] + g->radius) / B, (g->uv[1] + g->radius) / B};
+  for (int k = 0; k < 4; ++k) g->margin = dmin(g->margin, frac_margin(ex[k], fabs(ex[k]) * B) * B);
+  const double lim = 1e9;
+  g->rect[0] = clampi((int)floor(dmax(-lim, dmin(lim, ex[0]))), 0, gw);
+  g->rect[1] = clampi((int)floor(dmax(-lim, dmin(lim, ex[1]))), 0, gh);
+  g->rect[2] = clampi((int)floor(dmax(-lim, dmin(lim, ex[2]))) + 1, 0, gw);
+  g->rect[3] = clampi((int)floor(dmax(-lim, dmin(lim, ex[3]))) + 1, 0, gh);
+  if (g->rect[0] >= g->rect[2] || g->rect[1] >= g->rect[3]) {
+    g->status = 5;
+    return;
+  }
+  /* 4DSH colour (Sec. 3.2): Z_nl^m = cos(2 pi n dt / T) Y_l^m(d), with the
+   * view direction d from the camera centre to the sliced mean and
+   * dt = t - mu_t; colour = max(0, sum c Z + 0.5). */
+  for (int a = 0; a < 3; ++a) g->w[a] = g->mu3[a] - V->campos[a];
+  g->rw = sqrt(g->w[0] * g->w[0] + g->w[1] * g->w[1] + g->w[2] * g->w[2]);
+  for (int a = 0; a < 3; ++a) g->dir[a] = g->w[a] / g->rw;
+  const double theta = acos(dmax(-1.0, dmin(1.0, g->dir[2])));
+  const double phi = atan2(g->dir[1], g->dir[0]);
+  real_sh(g->L, theta, phi, g->Y, NULL, NULL);
+  for (int nn = 0; nn <= g->NT; ++nn) {
+    g->cosn[nn] = cos(2.0 * ORC_PI * nn * g->dt / S->period);
+    g->sinn[nn] = sin(2.0 * ORC_PI * nn * g->dt / S->period);
+  }
+  const int nlm = (g->L + 1) * (g->L + 1);
+  const double *sh = P->sh + (size_t)i * g->K * 3;
+  for (int ch = 0; ch < 3; ++ch) {
+    double acc = 0.0;
+    for (int nn = 0; nn <= g->NT; ++nn)
+      for (int lm = 0; lm < nlm; ++lm)
+        acc += sh[(nn * nlm + lm) * 3 + ch] * g->cosn[nn] * g->Y[lm];
+    g->raw[ch] = acc;
+    g->rgb[ch] = dmax(0.0, acc + 0.5);
+    if (!isfinite(g->rgb[ch])) {
+      g->status = 1;
+      return;
+    }
+  }
+  g->a = g->sig * g->pt;
+  g->status = 0;
+}
+
+/* Stores every value the chain reached (zeros past the cull point); the
+ * rect of a culled Gaussian is empty. */
+static void store_proj(const orc_ctx *g, int64_t i, orc_proj *o) {
+  o->status[i] = g->status;
+  o->margin[i] = g->margin;
+  for (int k = 0; k < 4; ++k) o->rect[4 * i + k] = g->status == 0 ? g->rect[k] : 0;
+  o->p_t[i] = g->pt;
+  o->a_eff[i] = g->a;
+  for (int k = 0; k < 3; ++k) o->mu3[3 * i + k] = g->mu3[k];
+  for (int k = 0; k < 9; ++k) o->cov3[9 * i + k] = g->cov3[k];
+  for (int k = 0; k < 3; ++k) o->pc[3 * i + k] = g->pc[k];
+  o->cov2d[3 * i + 0] = g->cov2[0];
+  o->cov2d[3 * i + 1] = g->cov2[1];
+  o->cov2d[3 * i + 2] = g->cov2[3];
+  for (int k = 0; k < 3; ++k) o->conic[3 * i + k] = g->conic[k];
+  o->uv[2 * i + 0] = g->uv[0];
+  o->uv[2 * i + 1] = g->uv[1];
+  o->radius[i] = g->radius;
+  o->depth[i] = g->pc[2];
+  o->depth_f32[i] = (float)g->pc[2];
+  for (int k = 0; k < 3; ++k) o->rgb[3 * i + k] = g->rgb[k];
+}
+
+int orc_preprocess(const orc_params *P, const orc_view *V, const orc_settings *S, orc_proj *out) {
+  if (S->sh_degree < 0 || S->sh_degree > ORC_MAX_L || S->t_order < 0 || S->t_order > ORC_MAX_N) return -1;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < P->n; ++i) {
+    orc_ctx g;
+    gauss_forward(P, i, V, S, &g);
+    store_proj(&g, i, out);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------- compositing */
+
+typedef struct {
+  float depth;
+  int64_t idx;
+} orc_entry;
+
+static int entry_cmp(const void *pa, const void *pb) {
+  const orc_entry *a = pa, *b = pb;
+  if (a->depth < b->depth) return -1;
+  if (a->depth > b->depth) return 1;
+  return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+static uint32_t f32_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return u;
+}
+
+/* Front-to-back compositing of one pixel over its depth-sorted list
+ * (Sec. 3.2, Eq. 6: p_i(t) p_i(u,v|t) alpha_i c_i prod_{j<i}(1 - ...)).
+ * Per entry: power = -1/2 d^T conic d; skip if power > 0; alpha =
+ * min(0.99, a_eff exp(power)); skip if alpha < 1/255; stop before adding an
+ * entry that would take T below 1e-4.  Sample point is the pixel centre.
+ * If rec != NULL, the contributing entries are recorded for the adjoint. */
+typedef struct {
+  int64_t idx;
+  int32_t pos;
+  double alpha, G, T, dx, dy;
+  int clamped;
+} orc_contrib;
+
+static void composite_pixel(const orc_proj *P, const orc_settings *S, const orc_entry *list, int64_t len,
+                            int px, int py, double out[3], double *T_out, int32_t *ncontrib,
+                            double *margin, int32_t *signature, orc_contrib *rec, int64_t *nrec) {
+  const double pxc = px + 0.5, pyc = py + 0.5;
+  double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+  double mg = INFINITY;
+  int32_t last = 0, nclamp = 0;
+  int64_t nr = 0;
+  uint32_t prev_bits = 0;
+  int have_prev = 0;
+  for (int64_t j = 0; j < len; ++j) {
+    const int64_t i = list[j].idx;
+    const uint32_t bits = f32_bits(list[j].depth);
+    /* Two entries within 2 ulp of depth may swap order in FP32. */
+    if (have_prev && bits - prev_bits <= 2u) mg = 0.0;
+    prev_bits = bits;
+    have_prev = 1;
+    const double A = P->conic[3 * i + 0], B = P->conic[3 * i + 1], Cc = P->conic[3 * i + 2];
+    const double dx = P->uv[2 * i + 0] - pxc, dy = P->uv[2 * i + 1] - pyc;
+    const double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
+    if (fabs(power) < 1e-6) mg = 0.0;
+    if (power > 0.0) continue;
+    const double G = exp(power);
+    const double aG = P->a_eff[i] * G;
+    mg = dmin(mg, fabs(aG - 0.99) / 0.99);
+    const double alpha = dmin(0.99, aG);
+    mg = dmin(mg, fabs(alpha * 255.0 - 1.0));
+    if (alpha < 1.0 / 255.0) continue;
+    const double Tn = T * (1.0 - alpha);
+    mg = dmin(mg, fabs(Tn - 1e-4) / 1e-4);
+    if (Tn < 1e-4) break;
+    for (int ch = 0; ch < 3; ++ch) C[ch] += P->rgb[3 * i + ch] * alpha * T;
+    if (rec) {
+      rec[nr].idx = i;
+      rec[nr].pos = (int32_t)j;
+      rec[nr].alpha = alpha;
+      rec[nr].G = G;
+      rec[nr].T = T;
+      rec[nr].dx = dx;
+      rec[nr].dy = dy;
+      rec[nr].clamped = aG > 0.99;
+    }
+    ++nr;
+    nclamp += aG > 0.99;
+    T = Tn;
+    last = (int32_t)(j + 1);
+  }
+  for (int ch = 0; ch < 3; ++ch) out[ch] = C[ch] + T * S->bg[ch];
+  if (T_out) *T_out = T;
+  if (ncontrib) *ncontrib = last;
+  if (margin) *margin = mg;
+  /* Discrete outcome of this pixel: contributors and clamped alphas. */
+  if (signature) *signature = (int32_t)nr + 65536 * nclamp;
+  if (nrec) *nrec = nr;
+}
+
+/* Tile lists: for every tile, the visible Gaussians whose tile rect contains
+ * it, sorted by (FP32 depth, index). */
+typedef struct {
+  int64_t *off;  /* [ntiles + 1] */
+  orc_entry *ent;
+} orc_tiles;
+
+static int build_tiles(const orc_view *V, const orc_settings *S, int64_t n, const orc_proj *P, orc_tiles *T) {
+  const int gw = (V->width + S->tile - 1) / S->tile, gh = (V->height + S->tile - 1) / S->tile;
+  const int64_t nt = (int64_t)gw * gh;
+  T->off = calloc((size_t)nt + 1, sizeof(int64_t));
+  if (!T->off) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    if (P->status[i] != 0) continue;
+    const int32_t *r = P->rect + 4 * i;
+    for (int ty = r[1]; ty < r[3]; ++ty)
+      for (int tx = r[0]; tx < r[2]; ++tx) T->off[(int64_t)ty * gw + tx + 1]++;
+  }
+  for (int64_t t = 0; t < nt; ++t) T->off[t + 1] += T->off[t];
+  T->ent = malloc(sizeof(orc_entry) * (size_t)(T->off[nt] > 0 ? T->off[nt] : 1));
+  int64_t *fill = calloc((size_t)nt, sizeof(int64_t));
+  if (!T->ent || !fill) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    if (P->status[i] != 0) continue;
+    const int32_t *r = P->rect + 4 * i;
+    for (int ty = r[1]; ty < r[3]; ++ty)
+      for (int tx = r[0]; tx < r[2]; ++tx) {
+        const int64_t t = (int64_t)ty * gw + tx;
+        orc_entry e = {P->depth_f32[i], i};
+        T->ent[T->off[t] + fill[t]++] = e;
+      }
+  }
+  free(fill);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t t = 0; t < nt; ++t)
+    qsort(T->ent + T->off[t], (size_t)(T->off[t + 1] - T->off[t]), sizeof(orc_entry), entry_cmp);
+  return 0;
+}
+
+static void free_tiles(orc_tiles *T) {
+  free(T->off);
+  free(T->ent);
+}
+
+int orc_render(const orc_view *V, const orc_settings *S, int64_t n, const orc_proj *P,
+               double *img, double *T_out, int32_t *ncontrib, double *margin, int32_t *signature) {
+  orc_tiles tl;
+  if (build_tiles(V, S, n, P, &tl)) return -1;
+  const int W = V->width, H = V->height, gw = (W + S->tile - 1) / S->tile;
+  const int64_t HW = (int64_t)W * H;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int py = 0; py < H; ++py) {
+    for (int px = 0; px < W; ++px) {
+      const int64_t t = (int64_t)(py / S->tile) * gw + px / S->tile;
+      const int64_t p = (int64_t)py * W + px;
+      double out[3];
+      composite_pixel(P, S, tl.ent + tl.off[t], tl.off[t + 1] - tl.off[t], px, py, out,
+                      T_out ? &T_out[p] : NULL, ncontrib ? &ncontrib[p] : NULL,
+                      margin ? &margin[p] : NULL, signature ? &signature[p] : NULL, NULL, NULL);
+      for (int ch = 0; ch < 3; ++ch) img[ch * HW + p] = out[ch];
+    }
+  }
+  free_tiles(&tl);
+  return 0;
+}
+
+/* Selected pixels only: each pixel's list is gathered by a scan over all
+ * Gaussians (used to check full-size renders at sampled pixels). */
+int orc_render_pixels(const orc_view *V, const orc_settings *S, int64_t n, const orc_proj *P,
+                      int64_t npix, const int64_t *pix, double *rgb, double *T_out,
+                      int32_t *ncontrib, double *margin) {
+  const int W = V->width;
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t q = 0; q < npix; ++q) {
+    const int px = (int)(pix[q] % W), py = (int)(pix[q] / W);
+    const int tx = px / S->tile, ty = py / S->tile;
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t *r = P->rect + 4 * i;
+      if (P->status[i] == 0 && tx >= r[0] && tx < r[2] && ty >= r[1] && ty < r[3]) ++cnt;
+    }
+    orc_entry *list = malloc(sizeof(orc_entry) * (size_t)(cnt > 0 ? cnt : 1));
+    if (!list) {
+      err = 1;
+      continue;
+    }
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t *r = P->rect + 4 * i;
+      if (P->status[i] == 0 && tx >= r[0] && tx < r[2] && ty >= r[1] && ty < r[3]) {
+        orc_entry e = {P->depth_f32[i], i};
+        list[k++] = e;
+      }
+    }
+    qsort(list, (size_t)cnt, sizeof(orc_entry), entry_cmp);
+    composite_pixel(P, S, list, cnt, px, py, rgb + 3 * q, T_out ? &T_out[q] : NULL,
+                    ncontrib ? &ncontrib[q] : NULL, margin ? &margin[q] : NULL, NULL, NULL, NULL);
+    free(list);
+  }
+  return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------ adjoint */
+
+/* Reverse-mode derivative of one pixel's colour C (RGB) with respect to the
+ * per-Gaussian alpha inputs.  With T_i = prod_{j<i} (1 - alpha_j) and
+ * C = sum_i c_i alpha_i T_i + T_final bg:
+ *   dC/dc_i     = alpha_i T_i
+ *   dC/dalpha_i = c_i T_i - (sum_{j>i} c_j alpha_j T_j + T_final bg) / (1 - alpha_i)
+ * and alpha = min(0.99, a G), G = exp(power), power = -1/2 d^T Q d. */
+static void pixel_adjoint(const orc_proj *P, const orc_settings *S, const orc_contrib *rec,
+                          int64_t nr, double T_final, const double gC[3], orc_grads *out) {
+  double rest[3];
+  for (int ch = 0; ch < 3; ++ch) rest[ch] = T_final * S->bg[ch];
+  for (int64_t k = nr - 1; k >= 0; --k) {
+    const orc_contrib *e = &rec[k];
+    const int64_t i = e->idx;
+    const double *c = P->rgb + 3 * i;
+    double g_alpha = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+      out->g_rgb[3 * i + ch] += gC[ch] * e->alpha * e->T;
+      g_alpha += gC[ch] * (c[ch] * e->T - rest[ch] / (1.0 - e->alpha));
+    }
+    for (int ch = 0; ch < 3; ++ch) rest[ch] += c[ch] * e->alpha * e->T;
+    if (e->clamped) continue; /* min(0.99, .) is locally constant */
+    const double a = P->a_eff[i];
+    out->g_a[i] += g_alpha * e->G;
+    const double g_pow = g_alpha * a * e->G;
+    const double A = P->conic[3 * i + 0], B = P->conic[3 * i + 1], Cc = P->conic[3 * i + 2];
+    out->g_conic[3 * i + 0] += g_pow * (-0.5 * e->dx * e->dx);
+    out->g_conic[3 * i + 1] += g_pow * (-e->dx * e->dy);
+    out->g_conic[3 * i + 2] += g_pow * (-0.5 * e->dy * e->dy);
+    out->g_uv[2 * i + 0] += g_pow * (-(A * e->dx + B * e->dy));
+    out->g_uv[2 * i + 1] += g_pow * (-(Cc * e->dy + B * e->dx));
+  }
+}
+
+/* Adjoint of the per-Gaussian forward chain, from dL/d(u, v, A, B, C, a,
+ * rgb) back to the raw parameters. */
+static void gauss_adjoint(const orc_params *Pp, int64_t i, const orc_view *V, const orc_settings *S,
+                          const orc_ctx *g, const double g_uv[2], const double g_conic[3],
+                          double g_a, const double g_rgb[3], orc_grads *out) {
+  const int nlm = (g->L + 1) * (g->L + 1);
+  const double *sh = Pp->sh + (size_t)i * g->K * 3;
+  double g_mu3[3] = {0, 0, 0}, g_dt = 0.0, g_pc[3] = {0, 0, 0};
+
+  /* Colour: rgb = max(0, raw + 0.5), raw = sum_n sum_lm c cos_n Y_lm. */
+  double graw[3];
+  for (int ch = 0; ch < 3; ++ch) graw[ch] = (g->raw[ch] + 0.5 > 0.0) ? g_rgb[ch] : 0.0;
+  double gY[(ORC_MAX_L + 1) * (ORC_MAX_L + 1)] = {0};
+  for (int nn = 0; nn <= g->NT; ++nn)
+    for (int lm = 0; lm < nlm; ++lm)
+      for (int ch = 0; ch < 3; ++ch) {
+        const int k = (nn * nlm + lm) * 3 + ch;
+        out->sh[(size_t)i * g->K * 3 + k] += graw[ch] * g->cosn[nn] * g->Y[lm];
+        gY[lm] += graw[ch] * sh[k] * g->cosn[nn];
+        g_dt += graw[ch] * sh[k] * g->Y[lm] * (-g->sinn[nn]) * (2.0 * ORC_PI * nn / S->period);
+      }
+  {
+    /* dY/dw through theta = acos(w_z/|w|), phi = atan2(w_y, w_x). */
+    double Y[16], dth[16], dph[16];
+    const double theta = acos(dmax(-1.0, dmin(1.0, g->dir[2])));
+    const double phi = atan2(g->dir[1], g->dir[0]);
+    real_sh(g->L, theta, phi, Y, dth, dph);
+    const double st = sin(theta), ct = cos(theta), sp = sin(phi), cp = cos(phi);
+    const double gth[3] = {ct * cp / g->rw, ct * sp / g->rw, -st / g->rw};
+    const double gph[3] = {-sp / (g->rw * st), cp / (g->rw * st), 0.0};
+    for (int lm = 0; lm < nlm; ++lm)
+      for (int a = 0; a < 3; ++a) g_mu3[a] += gY[lm] * (dth[lm] * gth[a] + dph[lm] * gph[a]);
+  }
+  /* Opacity: a = sigmoid(logit) p_t. */
+  const double g_sig = g_a * g->pt;
+  double g_pt = g_a * g->sig;
+  out->opacity_logit[i] += g_sig * g->sig * (1.0 - g->sig);
+
+  /* Projected centre, Eq. 3. */
+  const double x = g->pc[0], y = g->pc[1], z = g->pc[2];
+  g_pc[0] += g_uv[0] * V->fx / z;
+  g_pc[1] += g_uv[1] * V->fy / z;
+  g_pc[2] += -g_uv[0] * V->fx * x / (z * z) - g_uv[1] * V->fy * y / (z * z);
+
+  /* Conic = inverse(cov2): dL/dcov2 = -Q GQ Q, with GQ the full-matrix
+   * gradient of Q = [[A, B], [B, C]] (B enters twice). */
+  const double Q[4] = {g->conic[0], g->conic[1], g->conic[1], g->conic[2]};
+  const double GQ[4] = {g_conic[0], 0.5 * g_conic[1], 0.5 * g_conic[1], g_conic[2]};
+  double tmp[4], G2[4];
+  for (int r = 0; r < 2; ++r)
+    for (int col = 0; col < 2; ++col) tmp[2 * r + col] = Q[2 * r + 0] * GQ[0 * 2 + col] + Q[2 * r + 1] * GQ[1 * 2 + col];
+  for (int r = 0; r < 2; ++r)
+    for (int col = 0; col < 2; ++col)
+      G2[2 * r + col] = -(tmp[2 * r + 0] * Q[0 * 2 + col] + tmp[2 * r + 1] * Q[1 * 2 + col]);
+
+  /* Eq. 4: cov2 = M cov3 M^T + dil I, M = J W. */
+  double g_cov3[9], g_M[6], g_J[6];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double acc = 0.0;
+      for (int r = 0; r < 2; ++r)
+        for (int col = 0; col < 2; ++col) acc += g->M[3 * r + a] * G2[2 * r + col] * g->M[3 * col + b];
+      g_cov3[3 * a + b] = acc;
+    }
+  for (int r = 0; r < 2; ++r)
+    for (int a = 0; a < 3; ++a) {
+      double acc = 0.0;
+      for (int col = 0; col < 2; ++col)
+        for (int b = 0; b < 3; ++b) acc += G2[2 * r + col] * g->M[3 * col + b] * g->cov3[3 * b + a];
+      g_M[3 * r + a] = 2.0 * acc;
+    }
+  const double *W = V->viewmat;
+  for (int r = 0; r < 2; ++r)
+    for (int k = 0; k < 3; ++k) {
+      double acc = 0.0;
+      for (int col = 0; col < 3; ++col) acc += g_M[3 * r + col] * W[4 * k + col];
+      g_J[3 * r + k] = acc;
+    }
+  g_pc[0] += g_J[2] * (-V->fx / (z * z));
+  g_pc[1] += g_J[5] * (-V->fy / (z * z));
+  g_pc[2] += g_J[0] * (-V->fx / (z * z)) + g_J[2] * (2.0 * V->fx * x / (z * z * z)) +
+             g_J[4] * (-V->fy / (z * z)) + g_J[5] * (2.0 * V->fy * y / (z * z * z));
+
+  /* pc = W mu3 + T. */
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) g_mu3[a] += W[4 * k + a] * g_pc[k];
+
+  /* Conditional Gaussian: mu3 = m + b dt / c, cov3 = Sxx - b b^T / c. */
+  double g_b[3], g_c = 0.0, mub = 0.0, bgb = 0.0;
+  for (int a = 0; a < 3; ++a) mub += g_mu3[a] * g->b[a];
+  for (int a = 0; a < 3; ++a) {
+    double acc = 0.0;
+    for (int k = 0; k < 3; ++k) acc += (g_cov3[3 * a + k] + g_cov3[3 * k + a]) * g->b[k];
+    g_b[a] = g_mu3[a] * g->dt / g->c - acc / g->c;
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) bgb += g->b[a] * g_cov3[3 * a + k] * g->b[k];
+  g_dt += mub / g->c;
+  g_c += -mub * g->dt / (g->c * g->c) + bgb / (g->c * g->c);
+  /* Marginal p_t = exp(-dt^2 / (2 c)). */
+  g_dt += g_pt * g->pt * (-g->dt / g->c);
+  g_c += g_pt * g->pt * (0.5 * g->dt * g->dt / (g->c * g->c));
+  for (int a = 0; a < 3; ++a) out->mean[4 * i + a] += g_mu3[a];
+  out->mean[4 * i + 3] += -g_dt;
+
+  /* Symmetric gradient of Sigma: GS_ij = g_cov3_ij (i,j<3), GS_i3 = GS_3i =
+   * g_b_i / 2, GS_33 = g_c.  Sigma = R D R^T gives dL/dR = 2 GS R D and
+   * dL/d(s_k^2) = (R^T GS R)_kk. */
+  double GS[16];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) GS[4 * a + b] = 0.5 * (g_cov3[3 * a + b] + g_cov3[3 * b + a]);
+  for (int a = 0; a < 3; ++a) {
+    GS[4 * a + 3] = 0.5 * g_b[a];
+    GS[4 * 3 + a] = 0.5 * g_b[a];
+  }
+  GS[15] = g_c;
+  double gR[16];
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 4; ++k) {
+      double acc = 0.0;
+      for (int b = 0; b < 4; ++b) acc += GS[4 * a + b] * g->R[4 * b + k];
+      gR[4 * a + k] = 2.0 * acc * g->s[k] * g->s[k];
+    }
+  for (int k = 0; k < 4; ++k) {
+    double acc = 0.0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) acc += g->R[4 * a + k] * GS[4 * a + b] * g->R[4 * b + k];
+    out->log_scale[4 * i + k] += acc * 2.0 * g->s[k] * g->s[k];
+  }
+  /* R = Lm Rm: dL/dLm = gR Rm^T, dL/dRm = Lm^T gR. */
+  double gL[16], gRr[16];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      double acc1 = 0.0, acc2 = 0.0;
+      for (int k = 0; k < 4; ++k) {
+        acc1 += gR[4 * a + k] * g->Rm[4 * b + k];
+        acc2 += g->Lm[4 * k + a] * gR[4 * k + b];
+      }
+      gL[4 * a + b] = acc1;
+      gRr[4 * a + b] = acc2;
+    }
+  /* Entries of L(q) and R(q) are +-q components; collect by pattern. */
+  double gqln[4], gqrn[4];
+  gqln[0] = gL[0] + gL[5] + gL[10] + gL[15];
+  gqln[1] = -gL[1] + gL[4] - gL[11] + gL[14];
+  gqln[2] = -gL[2] + gL[7] + gL[8] - gL[13];
+  gqln[3] = -gL[3] - gL[6] + gL[9] + gL[12];
+  gqrn[0] = gRr[0] + gRr[5] + gRr[10] + gRr[15];
+  gqrn[1] = -gRr[1] + gRr[4] + gRr[11] - gRr[14];
+  gqrn[2] = -gRr[2] - gRr[7] + gRr[8] + gRr[13];
+  gqrn[3] = -gRr[3] + gRr[6] - gRr[9] + gRr[12];
+  /* q_hat = q / |q|: dL/dq = (g - q_hat (q_hat . g)) / |q|. */
+  double dl = 0.0, dr = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    dl += g->qln[k] * gqln[k];
+    dr += g->qrn[k] * gqrn[k];
+  }
+  for (int k = 0; k < 4; ++k) {
+    out->q_l[4 * i + k] += (gqln[k] - g->qln[k] * dl) / g->nql;
+    out->q_r[4 * i + k] += (gqrn[k] - g->qrn[k] * dr) / g->nqr;
+  }
+}
+
+/* dL/d(parameters) for a loss whose gradient with respect to the rendered
+ * image is dimg ([3][H][W]).  Per-Gaussian 2D gradients are also returned. */
+int orc_render_backward(const orc_params *Pp, const orc_view *V, const orc_settings *S,
+                        const orc_proj *P, const double *dimg, orc_grads *out) {
+  const int64_t n = Pp->n;
+  orc_tiles tl;
+  if (build_tiles(V, S, n, P, &tl)) return -1;
+  const int W = V->width, H = V->height, gw = (W + S->tile - 1) / S->tile;
+  const int64_t HW = (int64_t)W * H;
+  int64_t maxlen = 1;
+  for (int64_t t = 0; t < (int64_t)gw * ((H + S->tile - 1) / S->tile); ++t)
+    if (tl.off[t + 1] - tl.off[t] > maxlen) maxlen = tl.off[t + 1] - tl.off[t];
+  orc_contrib *rec = malloc(sizeof(orc_contrib) * (size_t)maxlen);
+  if (!rec) return -1;
+  for (int py = 0; py < H; ++py)
+    for (int px = 0; px < W; ++px) {
+      const int64_t t = (int64_t)(py / S->tile) * gw + px / S->tile;
+      const int64_t p = (int64_t)py * W + px;
+      const double gC[3] = {dimg[p], dimg[HW + p], dimg[2 * HW + p]};
+      if (gC[0] == 0.0 && gC[1] == 0.0 && gC[2] == 0.0) continue;
+      double outc[3], T;
+      int64_t nr = 0;
+      composite_pixel(P, S, tl.ent + tl.off[t], tl.off[t + 1] - tl.off[t], px, py, outc, &T, NULL, NULL,
+                      NULL, rec, &nr);
+      pixel_adjoint(P, S, rec, nr, T, gC, out);
+    }
+  free(rec);
+  free_tiles(&tl);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    if (P->status[i] != 0) continue;
+    orc_ctx g;
+    gauss_forward(Pp, i, V, S, &g);
+    gauss_adjoint(Pp, i, V, S, &g, out->g_uv + 2 * i, out->g_conic + 3 * i, out->g_a[i],
+                  out->g_rgb + 3 * i, out);
+  }
+  return 0;
+}
+
+/* Adjoint of the per-Gaussian chain alone, from given 2D gradients (used to
+ * check the preprocess adjoint separately from compositing). */
+int orc_preprocess_backward(const orc_params *Pp, const orc_view *V, const orc_settings *S,
+                            const double *g_uv, const double *g_conic, const double *g_a,
+                            const double *g_rgb, orc_grads *out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < Pp->n; ++i) {
+    orc_ctx g;
+    gauss_forward(Pp, i, V, S, &g);
+    if (g.status != 0) continue;
+    gauss_adjoint(Pp, i, V, S, &g, g_uv + 2 * i, g_conic + 3 * i, g_a[i], g_rgb + 3 * i, out);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------- pieces for the pins */
+
+/* R = L(q_l) R(q_r) for unit-normalised q_l, q_r (row-major 4x4). */
+void orc_rotation(const double *q_l, const double *q_r, double *R) {
+  double ql[4], qr[4], Lm[16], Rm[16];
+  double nl = 0.0, nr = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    nl += q_l[k] * q_l[k];
+    nr += q_r[k] * q_r[k];
+  }
+  nl = sqrt(nl);
+  nr = sqrt(nr);
+  for (int k = 0; k < 4; ++k) {
+    ql[k] = q_l[k] / nl;
+    qr[k] = q_r[k] / nr;
+  }
+  left_matrix(ql, Lm);
+  right_matrix(qr, Rm);
+  mat4_mul(Lm, Rm, R);
+}
+
+/* Real SH values Y_lm for a unit direction (x, y, z). */
+void orc_real_sh(int L, const double *dir, double *Y) {
+  const double theta = acos(dmax(-1.0, dmin(1.0, dir[2])));
+  const double phi = atan2(dir[1], dir[0]);
+  real_sh(L, theta, phi, Y, NULL, NULL);
+}
+
+/* Instance list of a tile-binned view, as the paper's tile rasterizer sorts
+ * it: one (tile, Gaussian) pair per tile of each visible Gaussian's rect,
+ * key = (tile << 32) | bits(depth_f32), sorted by (tile, depth, index).
+ * ranges[t] = [start, end) of tile t. Returns the instance count, or -1 if
+ * it exceeds cap. */
+typedef struct {
+  int64_t tile;
+  float depth;
+  int64_t idx;
+} orc_inst;
+
+static int inst_cmp(const void *pa, const void *pb) {
+  const orc_inst *a = pa, *b = pb;
+  if (a->tile != b->tile) return a->tile < b->tile ? -1 : 1;
+  if (a->depth != b->depth) return a->depth < b->depth ? -1 : 1;
+  return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+int64_t orc_sort_instances(int64_t n, const int32_t *rect, const float *depth, int32_t gw, int32_t gh,
+                           int64_t cap, uint64_t *keys, int64_t *vals, int64_t *ranges) {
+  int64_t m = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t *r = rect + 4 * i;
+    if (r[2] > r[0] && r[3] > r[1]) m += (int64_t)(r[2] - r[0]) * (r[3] - r[1]);
+  }
+  if (m > cap) return -1;
+  orc_inst *a = malloc(sizeof(orc_inst) * (size_t)(m > 0 ? m : 1));
+  if (!a) return -1;
+  int64_t k = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t *r = rect + 4 * i;
+    for (int ty = r[1]; ty < r[3]; ++ty)
+      for (int tx = r[0]; tx < r[2]; ++tx) {
+        a[k].tile = (int64_t)ty * gw + tx;
+        a[k].depth = depth[i];
+        a[k].idx = i;
+        ++k;
+      }
+  }
+  /* (tile, depth, index) is a total order, so qsort's lack of stability is
+   * irrelevant. */
+  qsort(a, (size_t)m, sizeof(orc_inst), inst_cmp);
+  for (int64_t t = 0; t < (int64_t)gw * gh; ++t) {
+    ranges[2 * t] = 0;
+    ranges[2 * t + 1] = 0;
+  }
+  for (int64_t j = 0; j < m; ++j) {
+    keys[j] = ((uint64_t)a[j].tile << 32) | f32_bits(a[j].depth);
+    vals[j] = a[j].idx;
+    if (j == 0 || a[j].tile != a[j - 1].tile) ranges[2 * a[j].tile] = j;
+    ranges[2 * a[j].tile + 1] = j + 1;
+  }
+  free(a);
+  return m;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

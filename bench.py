@@ -1,0 +1,460 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 render path of 4D Gaussian Splatting (arXiv 2412.20720).
+
+Headline workload (one step): 300,000 synthetic 4D Gaussians (spatial SH
+degree 3 x temporal order 2) over [-3,3]^3 x [0,1], rendered at 1352x1014 from
+an orbit camera of radius 6 for the 300 timestamps t_k = k/299 of a sweep,
+one view per call (plain form): preprocess -> bin_sort -> render_fwd through
+the C ABI for every view.  value = rendered frames/s over all ranks.
+
+Also reported ("train"): fwd+bwd iterations/s of the training step on the same
+scene -- 4 timestamps x 1 camera at 1352x1014 in one batched call, L1 loss
+against target images rendered by the CUDA path from a second seeded scene,
+backward to every parameter, and an Adam step.
+
+Timing: W untimed warm-up steps, then K steps between a barrier +
+synchronize on both sides, CUDA events on the launching stream, max over
+ranks.  The scene's parameters (193 MB) exceed the 129 MB L2, so no flush is
+inserted between frames.  `--impl reference` times the FP64 CPU oracle on the
+host cores on the same workload (one full view per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "4dgs-orbit-sweep-300k"
+METRIC = "rendered frames/s (300k 4D Gaussians, 1352x1014, 300-timestamp sweep, one view per call)"
+UNIT = "frames/s"
+SWEEP = 300
+N_GAUSS = 300_000
+W_IMG, H_IMG = 1352, 1014
+# Algorithmic FP32 flops of the compositor: an alpha evaluation is 2 subtractions,
+# 3 products and 3 multiply-adds of the conic form (8), a*G and the 0.99 clamp
+# (2) and the skip test (1) = 11; a composited entry adds T*(1-alpha) (2),
+# alpha*T (1), three colour multiply-adds (6) = 9.  The ex2 goes to the SFU.
+FLOPS_PER_EVAL = 11
+FLOPS_PER_COMP = 9
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--n", type=int, default=N_GAUSS, help="Gaussians (default: the headline 300k)")
+    p.add_argument("--views", type=int, default=SWEEP, help="views per sweep step (default 300)")
+    p.add_argument("--train-iters", type=int, default=20)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_query_id(torch, dev) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:  # pragma: no cover
+        return str(dev.index or 0)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_frames(n: int, ks, seconds_budget: float = 30.0):
+    """Full views rendered by the FP64 oracle on the host cores.  Returns
+    (frames/s, threads, frames done)."""
+    import numpy as np
+
+    import oracle
+    from paper_2412_20720_gb300 import synthetic as sy
+    scene = sy.orbit_scene(n)
+    params = scene.as_dict()
+    st = oracle.Settings(sh_degree=3, t_order=2, tile=16, period=1.0, near_plane=float(np.float32(0.2)),
+                         dilation=float(np.float32(0.3)), p_t_min=float(np.float32(0.05)))
+    t0 = time.perf_counter()
+    done = 0
+    for k in ks:
+        v = sy.orbit_view(k, SWEEP, W_IMG, H_IMG)
+        pr = oracle.preprocess(params, v, st)
+        oracle.render(pr, v, st)
+        done += 1
+        if time.perf_counter() - t0 > seconds_budget:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, oracle.num_threads(), done
+
+
+# ----------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_20720_gb300 import fgs4d
+    from paper_2412_20720_gb300 import synthetic as sy
+    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, l1_loss
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    scene = sy.orbit_scene(args.n)
+    host = scene.as_dict()
+    params = {k: torch.from_numpy(host[k]).to(dev) for k in PARAM_KEYS}
+    nviews = args.views
+    views = [sy.orbit_view(k, nviews, W_IMG, H_IMG) for k in range(nviews)]
+    cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24)
+    r = Renderer(scene.n, views[:1], cfg, device=dev)
+    vv = [fgs4d.make_views([v]) for v in views]
+    g = r.gaussians(params)
+    ws, wsb, s = r.ws.data_ptr(), r.ws_bytes, r.settings
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+    npx = W_IMG * H_IMG
+    img = torch.empty(3 * npx, dtype=torch.float32, device=dev)
+    lay = r.layout
+    tile_passes = max(1, ((int(lay.total_tiles) - 1).bit_length() + 7) // 8)
+    launches_per_frame = 1 + (1 + 4 + 1 + 1 + tile_passes + 1) + 1
+
+    def frame(k, ev=None, out=None):
+        v, n1 = vv[k]
+        o = img if out is None else out
+        if ev is not None:
+            ev[0].record(stream)
+        fgs4d.preprocess(g, v, n1, s, ws, wsb, st)
+        if ev is not None:
+            ev[1].record(stream)
+        fgs4d.bin_sort(scene.n, v, n1, s, ws, wsb, st)
+        if ev is not None:
+            ev[2].record(stream)
+        fgs4d.render_fwd(scene.n, v, n1, s, ws, wsb, o.data_ptr(), None, st)
+        if ev is not None:
+            ev[3].record(stream)
+
+    # Capacity and work counts over the whole sweep (outside the timed region).
+    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    vis, inst, evals, comps = [], [], [], []
+    for k in range(nviews):
+        v, n1 = vv[k]
+        fgs4d.preprocess(g, v, n1, s, ws, wsb, st)
+        fgs4d.bin_sort(scene.n, v, n1, s, ws, wsb, st)
+        stats.zero_()
+        fgs4d.render_stats(scene.n, v, n1, s, ws, wsb, img.data_ptr(), stats.data_ptr(), st)
+        code, counts = r.status()
+        if code != fgs4d.OK:
+            raise RuntimeError("view %d: %s (counts %s)" % (k, fgs4d.status_string(code), counts))
+        vis.append(counts[0])
+        inst.append(counts[1])
+        e, c = stats.tolist()
+        evals.append(e)
+        comps.append(c)
+
+    # Warm-up, then the timed sweep steps.
+    for _ in range(args.warmup):
+        for k in range(nviews):
+            frame(k)
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K * nviews)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(gpu_query_id(torch, dev))
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for step in range(K):
+        for k in range(nviews):
+            frame(k, evs[step * nviews + k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    code, counts = r.status()
+    if code != fgs4d.OK:
+        raise RuntimeError("timed sweep: %s" % fgs4d.status_string(code))
+    ms = start.elapsed_time(end)
+    stage_ms = np.zeros(3)
+    for e4 in evs:
+        stage_ms += [e4[0].elapsed_time(e4[1]), e4[1].elapsed_time(e4[2]), e4[2].elapsed_time(e4[3])]
+    stage_ms /= len(evs)
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    frames = K * nviews * world
+    value = frames / (ms_max / 1000.0)
+
+    # Roofline of the dominant kernel (the compositor): FP32-ALU bound.
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    mean_flops = FLOPS_PER_EVAL * np.mean(evals) + FLOPS_PER_COMP * np.mean(comps)
+    achieved = mean_flops / (stage_ms[2] * 1e-3) / 1e12
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    pre_bytes = 68.0 * scene.n + (576.0 + 56.0) * np.mean(vis)
+    pre_gbs = pre_bytes / (stage_ms[0] * 1e-3) / 1e9
+
+    # ---------------------------------------------------------- e2e
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: torch.from_numpy(host[k]).pin_memory() for k in PARAM_KEYS}
+        ring = 3
+        dev_imgs = [torch.empty(3 * npx, dtype=torch.float32, device=dev) for _ in range(ring)]
+        host_imgs = [torch.empty(3 * npx, dtype=torch.float32).pin_memory() for _ in range(ring)]
+        copy_stream = torch.cuda.Stream(dev)
+        done_ev = [torch.cuda.Event() for _ in range(ring)]
+        ready_ev = [torch.cuda.Event() for _ in range(ring)]
+        h2d = sum(int(p.numel() * p.element_size()) for p in pinned.values())
+        d2h = nviews * 3 * npx * 4
+
+        def e2e_step():
+            for kk in PARAM_KEYS:
+                params[kk].copy_(pinned[kk], non_blocking=True)
+            for k in range(nviews):
+                b = k % ring
+                stream.wait_event(done_ev[b])
+                frame(k, out=dev_imgs[b])
+                ready_ev[b].record(stream)
+                copy_stream.wait_event(ready_ev[b])
+                with torch.cuda.stream(copy_stream):
+                    host_imgs[b].copy_(dev_imgs[b], non_blocking=True)
+                done_ev[b].record(copy_stream)
+            stream.wait_stream(copy_stream)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = (time.perf_counter() - t0) * 1000.0
+        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": frames / (float(te.item()) / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "path": "C-ABI calls on device copies of pinned host parameters; each image copied to pinned "
+                       "host memory on a second stream"}
+
+    # ---------------------------------------------------------- train step
+    train = run_train(args, dev, scene, params, world, barrier)
+
+    # ---------------------------------------------------------- CPU oracle
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fps, cores, nfr = oracle_frames(args.n, [SWEEP // 2], 60.0)
+        cpu = {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d full view(s) (view k=%d of the sweep: %d Gaussians, %dx%d) rendered by the FP64 "
+                         "oracle with OpenMP over pixel rows" % (nfr, SWEEP // 2, args.n, W_IMG, H_IMG)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded; shapes and distributions of the paper's workloads)",
+            "config": {"workload": WORKLOAD, "gaussians": args.n, "sh_degree": 3, "t_order": 2,
+                       "resolution": [W_IMG, H_IMG], "views_per_step": nviews, "views_per_call": 1,
+                       "l2": "inputs larger than L2 (193 MB of parameters vs 129 MB L2); no flush",
+                       "parallelism": "views replicated per GPU" if world > 1 else "single GPU"},
+            "gpu_launches": launches_per_frame * nviews * K,
+            "stages_ms_per_frame": {"preprocess": stage_ms[0], "bin_sort": stage_ms[1], "render_fwd": stage_ms[2]},
+            "work_per_frame": {"visible": float(np.mean(vis)), "instances": float(np.mean(inst)),
+                               "alpha_evals": float(np.mean(evals)), "composited": float(np.mean(comps))},
+            "roofline": {"kernel": "render_fwd", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "peak_basis": "SMs x 128 FP32 lanes x 2 (FMA) x max SM clock %.0f MHz (derived)" % sm_max,
+                         "flops_per_launch": mean_flops},
+            "preprocess_roofline": {"bound": "hbm", "achieved": pre_gbs, "peak": hbm, "unit": "GB/s",
+                                    "frac": pre_gbs / hbm, "bytes_per_launch": pre_bytes,
+                                    "peak_basis": "measured hbm_gbs"},
+            "clocks": clk,
+            "e2e": e2e,
+            "train": train,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_train(args, dev, scene, params, world, barrier):
+    """Training step: 4 timestamps x 1 camera, batched in one call."""
+    import torch
+
+    from paper_2412_20720_gb300 import fgs4d
+    from paper_2412_20720_gb300 import synthetic as sy
+    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, l1_loss
+
+    views = sy.train_views(4, W_IMG, H_IMG)
+    cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 25)
+    tgt_scene = sy.orbit_scene(args.n, seed=sy.TARGET_SEED)
+    tparams = {k: torch.from_numpy(v).to(dev) for k, v in tgt_scene.as_dict().items()}
+    rt = Renderer(tgt_scene.n, views, cfg, device=dev)
+    target = rt.forward(tparams).clone()
+    rt.check()
+    del rt, tparams
+    leaf = {k: params[k].clone().requires_grad_(True) for k in PARAM_KEYS}
+    r = Renderer(scene.n, views, cfg, device=dev)
+    grads = {k: torch.zeros_like(leaf[k]) for k in PARAM_KEYS}
+    opt = torch.optim.Adam([leaf[k] for k in PARAM_KEYS], lr=1e-4, fused=True)
+    for k in PARAM_KEYS:
+        leaf[k].grad = grads[k]
+
+    def it():
+        for gk in grads.values():
+            gk.zero_()
+        with torch.no_grad():
+            pr = {k: leaf[k].detach() for k in PARAM_KEYS}
+            img = r.forward(pr)
+            loss, dimg = l1_loss(img, target)
+            r.backward(pr, dimg, grads)
+        opt.step()
+        return loss
+
+    for _ in range(3):
+        it()
+    r.check()
+    torch.cuda.synchronize()
+    barrier()
+    stream = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.train_iters):
+        loss = it()
+    b.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    code, counts = r.status()
+    ms = a.elapsed_time(b) / args.train_iters
+    return {"metric": "fwd+bwd iters/s", "value": 1000.0 / ms * world, "unit": "iters/s", "ms_per_iter": ms,
+            "workload": "4 timestamps x 1 camera at 1352x1014 in one call, %d Gaussians, L1 loss, backward to all "
+                        "parameters, fused Adam step" % scene.n,
+            "status": fgs4d.status_string(code), "loss": float(loss.item()),
+            "targets": "rendered by the CUDA path from a second seeded scene"}
+
+
+# ------------------------------------------------------------ reference
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    ks = list(range(0, SWEEP, max(1, SWEEP // max(1, K + W))))[:K + W]
+    oracle_frames(args.n, ks[:W], 1e9) if W else None
+    fps, cores, nfr = oracle_frames(args.n, ks[W:W + K], 1e9)
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": 1000.0 / fps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "gaussians": args.n, "sh_degree": 3, "t_order": 2,
+                       "resolution": [W_IMG, H_IMG], "views_per_step": 1},
+            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one full view of the sweep per step (FP64 oracle, OpenMP)"},
+            "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

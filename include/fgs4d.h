@@ -1,0 +1,212 @@
+/*
+ * fgs4d.h -- C ABI of the GB300 render path of 4D Gaussian Splatting
+ * ("4D Gaussian Splatting: Modeling Dynamic Scenes with Native 4D
+ * Primitives", arXiv 2412.20720).
+ *
+ * The path renders native 4D Gaussians at a timestamp t (Sec. 3.2, Eqs. 5-6):
+ * each Gaussian's 4D covariance Sigma = R S S^T R^T with R = L(q_l) R(q_r) is
+ * sliced at t into a conditional 3D Gaussian times the marginal p(t)
+ * (Sec. 3.2), projected to a 2D conic (Sec. 3.1, Eqs. 3-4), coloured by 4D
+ * spherindrical harmonics (Sec. 3.2), binned into screen tiles, sorted by
+ * (tile, depth) and composited front to back (Sec. 3.2, Eq. 6), and the whole
+ * chain is differentiated (Sec. 3.3, end-to-end optimisation).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All pointers to Gaussian data, images, gradients and the workspace are
+ *   DEVICE pointers owned by the caller.  The library never allocates or
+ *   frees device memory.  Host structs (views, settings, gaussian pointer
+ *   tables) are read during the call only.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Every call only enqueues work on it and returns without
+ *   synchronising (except fgs4d_get_status), so a sequence of calls can be
+ *   captured into a CUDA graph.
+ * - One opaque workspace (size from fgs4d_workspace_size for the same n,
+ *   views and settings) carries the state from fgs4d_preprocess through
+ *   fgs4d_bin_sort and fgs4d_render_fwd to fgs4d_render_bwd.  Calls that
+ *   share a workspace must be ordered on one stream.
+ * - Return value: FGS4D_OK (0) or a negative FGS4D_ERR_* code.  Argument
+ *   errors are detected on the host before anything is enqueued.  Conditions
+ *   only the GPU can detect (capacity overflow, a bounded wait that ran out)
+ *   are recorded in a status word in the workspace; kernels never trap, and
+ *   every write stays inside the caller's buffers.  fgs4d_get_status reads
+ *   that word.
+ * - Parameter layout (float32, row-major, contiguous): mean [n][4] (x,y,z,t);
+ *   log_scale [n][4]; q_l, q_r [n][4] (real part first, any non-zero norm;
+ *   normalised inside); opacity_logit [n] (opacity = sigmoid(logit));
+ *   sh [n][K][3] with K = (L+1)^2 (n_max+1) and coefficient k =
+ *   n (L+1)^2 + l^2 + l + m for temporal order n, degree l, order m.
+ */
+#ifndef FGS4D_H
+#define FGS4D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FGS4D_OK 0
+#define FGS4D_ERR_ARG (-1)         /* invalid argument (host-side check) */
+#define FGS4D_ERR_CUDA (-2)        /* a CUDA runtime call or launch failed */
+#define FGS4D_ERR_WORKSPACE (-3)   /* workspace pointer, size or alignment wrong */
+#define FGS4D_ERR_CAPACITY (-4)    /* visible or instance capacity exceeded */
+#define FGS4D_ERR_TIMEOUT (-5)     /* a bounded inter-block wait ran out */
+#define FGS4D_ERR_INTERNAL (-6)    /* an internal consistency check failed */
+#define FGS4D_ERR_UNSUPPORTED (-7) /* setting outside the compiled range */
+
+#define FGS4D_MAX_VIEWS 128     /* views per call */
+#define FGS4D_MAX_SH_DEGREE 3   /* spatial SH degree L */
+#define FGS4D_MAX_T_ORDER 4     /* temporal Fourier order n_max */
+
+/* One (camera, timestamp) to render.  Pinhole camera in the OpenCV
+ * convention (x right, y down, z forward); pixel (px, py) is sampled at its
+ * centre (px + 0.5, py + 0.5). */
+typedef struct fgs4d_view {
+  int32_t width, height;   /* image size in pixels, each in [1, 16384] */
+  float fx, fy, cx, cy;    /* intrinsics K (Sec. 3.1, Eq. 3) */
+  float viewmat[12];       /* extrinsics E: world -> camera, row-major 3x4 [W | T] */
+  float campos[3];         /* camera centre in world space (4DSH view direction) */
+  float t;                 /* render timestamp */
+} fgs4d_view;
+
+/* Render settings.  The paper leaves the rasterizer constants to the tile
+ * rasterizer it adapts (Sec. 3.2); the values used by the tests are noted. */
+typedef struct fgs4d_settings {
+  int32_t sh_degree;     /* spatial SH degree L, 0..FGS4D_MAX_SH_DEGREE */
+  int32_t t_order;       /* temporal order n_max, 0..FGS4D_MAX_T_ORDER */
+  float period;          /* T of cos(2 pi n dt / T), > 0 (tests: 1) */
+  int32_t tile;          /* tile edge in pixels: 16 */
+  float near_plane;      /* cull when camera z <= near_plane, > 0 (tests: 0.2) */
+  float dilation;        /* added to the 2D covariance diagonal, >= 0 (tests: 0.3) */
+  float p_t_min;         /* temporal filter: cull when p(t) < p_t_min (Sec. 7.1.1: 0.05) */
+  float bg[3];           /* background colour composited behind the Gaussians */
+  int64_t vis_capacity;  /* max visible (view, Gaussian) pairs; 0 = n * nviews */
+  int64_t inst_capacity; /* max (tile, Gaussian) instances over all views, > 0 */
+} fgs4d_settings;
+
+/* Gaussian parameters (device pointers, layout in the header comment). */
+typedef struct fgs4d_gaussians {
+  const float *mean;
+  const float *log_scale;
+  const float *q_l;
+  const float *q_r;
+  const float *opacity_logit;
+  const float *sh;
+  int64_t n; /* number of Gaussians, 0 <= n < 2^31 */
+} fgs4d_gaussians;
+
+/* Gradient buffers, same shapes as the parameters (device pointers).
+ * Gradients are ACCUMULATED (+=); the caller zeroes them when needed. */
+typedef struct fgs4d_gaussians_grad {
+  float *mean;
+  float *log_scale;
+  float *q_l;
+  float *q_r;
+  float *opacity_logit;
+  float *sh;
+} fgs4d_gaussians_grad;
+
+/* Byte offsets of the workspace regions that hold the documented
+ * intermediate results (for inspection and tests; all other bytes are
+ * private).  "slot" numbers the visible (view, Gaussian) pairs of a call in
+ * (view, Gaussian index) order. */
+typedef struct fgs4d_layout {
+  size_t bytes;         /* total workspace size */
+  size_t counters;      /* uint32: [0] visible pairs, [1] instances, [2] status bits */
+  size_t rec_geom;      /* float4 [vis_cap]: (u, v, A', B') with power2 = -(A' dx^2 + B' dx dy + C' dy^2) */
+  size_t rec_color;     /* float4 [vis_cap]: (C', a, r, g) with a = sigmoid(logit) p(t) */
+  size_t rec_blue;      /* float  [vis_cap]: b */
+  size_t rec_meta;      /* int32x4 [vis_cap]: (gaussian, view, x0 | y0 << 16, x1 | y1 << 16) tile rect */
+  size_t depth_key;     /* uint32 [vis_cap]: FP32 bits of the camera depth */
+  size_t sorted_slots;  /* uint32 [vis_cap]: slots in (depth, slot) order, after fgs4d_bin_sort */
+  size_t inst_tile;     /* uint32 [inst_cap]: global tile id of each sorted instance */
+  size_t inst_slot;     /* uint32 [inst_cap]: slot of each sorted instance */
+  size_t tile_ranges;   /* uint32x2 [total_tiles]: [start, end) into the instance list */
+  size_t pix_T;         /* float  [total_pixels]: final transmittance */
+  size_t pix_last;      /* uint32 [total_pixels]: list entries processed up to the last composited one */
+  size_t slot_grad;     /* float  [vis_cap][12]: dL/d(u, v, A, B, C, a, r, g, b) per slot */
+  int64_t vis_capacity;
+  int64_t inst_capacity;
+  int64_t total_tiles;  /* sum over views of ceil(W/16) ceil(H/16); view v starts at the sum before it */
+  int64_t total_pixels; /* sum over views of W H; view v's image starts at the sum before it */
+} fgs4d_layout;
+
+/* Workspace bytes for rendering n Gaussians into `views` with `settings`.
+ * Errors: FGS4D_ERR_ARG (bad sizes or pointers), FGS4D_ERR_UNSUPPORTED. */
+int fgs4d_workspace_size(const fgs4d_settings *settings, int64_t n, const fgs4d_view *views,
+                         int32_t nviews, size_t *bytes_out);
+
+/* Offsets of the documented workspace regions (see fgs4d_layout). */
+int fgs4d_workspace_layout(const fgs4d_settings *settings, int64_t n, const fgs4d_view *views,
+                           int32_t nviews, fgs4d_layout *layout_out);
+
+/* Per-Gaussian stage for every view (Sec. 3.2 and Sec. 3.1, Eqs. 3-4):
+ * activations, R = L(q_l) R(q_r), Sigma = R S S^T R^T, marginal
+ * p(t) = exp(-(t - mu_t)^2 / (2 Sigma_44)) and the temporal filter
+ * p(t) < p_t_min (Sec. 7.1.1), conditional mean and covariance at t, view
+ * transform, near cull, EWA 2D covariance (+ dilation), conic, 3-sigma tile
+ * rect, depth, 4DSH colour max(0, sum c cos(2 pi n (t - mu_t)/T) Y_lm(d) +
+ * 0.5), effective opacity sigmoid(logit) p(t).  Writes the records of the
+ * visible pairs into the workspace (slot order: view, then Gaussian index).
+ * Resets the workspace status word.  Device-detected: visible capacity. */
+int fgs4d_preprocess(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                     const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Tile binning and sort (the tile rasterizer of Sec. 3.2): every visible
+ * slot emits one instance per tile of its rect; instances are ordered by
+ * (global tile, FP32 depth, slot) with a hand-written radix sort, and each
+ * tile's [start, end) range is computed.  Reads only what fgs4d_preprocess
+ * (or a caller filling rec_meta, depth_key and counters[0]) wrote.
+ * Device-detected: instance capacity. */
+int fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* Front-to-back compositing per pixel (Sec. 3.2, Eq. 6) over its tile's
+ * sorted list: alpha = min(0.99, a exp(power)), skip when power > 0 or
+ * alpha < 1/255, stop before the entry that would take T below 1e-4.
+ * out_rgb: float [sum_v 3 H W], view v at 3 * (pixels before v), planar
+ * [3][H][W].  out_T: optional (may be NULL) float [sum_v H W] final
+ * transmittance. */
+int fgs4d_render_fwd(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                     void *workspace, size_t workspace_bytes, float *out_rgb, float *out_T, void *stream);
+
+/* Diagnostic form of fgs4d_render_fwd: renders identically into out_rgb and
+ * ADDS to stats_out (device uint64[2], 8-byte aligned) the number of
+ * pixel-entry alpha evaluations and of composited entries -- the work
+ * counts from which the compositor's algorithmic FLOPs are stated.  Has no
+ * counterpart in the paper. */
+int fgs4d_render_stats(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                       void *workspace, size_t workspace_bytes, float *out_rgb, uint64_t *stats_out, void *stream);
+
+/* Reverse-mode derivative of the rendered RGB (Sec. 3.3: the chain is
+ * optimised end to end): dL_drgb has out_rgb's layout; the gradients of all
+ * parameters of the visible Gaussians are ADDED into `grads`.  Reverse
+ * traversal recomputes T from the final transmittance; per-Gaussian sums are
+ * warp-reduced before atomic accumulation.  Requires the workspace of the
+ * matching forward (same n, views, settings, parameters). */
+int fgs4d_render_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                     const fgs4d_settings *settings, void *workspace, size_t workspace_bytes,
+                     const float *dL_drgb, const fgs4d_gaussians_grad *grads, void *stream);
+
+/* Photometric L1 loss (Sec. 3.3, rendering loss only): loss_out[0] +=
+ * sum |img - target| / count, dL_dimg = sign(img - target) / count.
+ * All device pointers; loss_out must be zeroed by the caller. */
+int fgs4d_l1_loss(const float *img, const float *target, int64_t count, float *loss_out, float *dL_dimg,
+                  void *stream);
+
+/* Synchronises `stream`, then reads the workspace status word.  Returns
+ * FGS4D_OK, or the first recorded device condition (FGS4D_ERR_CAPACITY,
+ * FGS4D_ERR_TIMEOUT, FGS4D_ERR_INTERNAL).  counts_out (optional, 4 entries):
+ * visible pairs, instances, visible pairs needed, instances needed. */
+int fgs4d_get_status(const void *workspace, size_t workspace_bytes, void *stream, int64_t *counts_out);
+
+/* Static description of a status code. */
+const char *fgs4d_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGS4D_H */

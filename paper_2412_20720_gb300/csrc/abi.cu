@@ -1,0 +1,307 @@
+// C ABI entry points of the fgs4d library (declared in include/fgs4d.h):
+// host-side argument checks, workspace layout, and kernel launches on the
+// caller's stream.  No device memory is allocated here.
+#include <math.h>
+#include <string.h>
+
+#include "fgs4d_internal.cuh"
+
+namespace fgs4d {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int64_t kMaxCap = (1ll << 30) - 1;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+bool finite_f(float x) { return isfinite(x); }
+
+int check_settings(const fgs4d_settings *s) {
+  if (!s) return FGS4D_ERR_ARG;
+  if (s->sh_degree < 0 || s->sh_degree > FGS4D_MAX_SH_DEGREE) return FGS4D_ERR_UNSUPPORTED;
+  if (s->t_order < 0 || s->t_order > FGS4D_MAX_T_ORDER) return FGS4D_ERR_UNSUPPORTED;
+  if (s->tile != kTile) return FGS4D_ERR_UNSUPPORTED;
+  if (!finite_f(s->period) || !(s->period > 0.f)) return FGS4D_ERR_ARG;
+  if (!finite_f(s->near_plane) || !(s->near_plane > 0.f)) return FGS4D_ERR_ARG;
+  if (!finite_f(s->dilation) || s->dilation < 0.f) return FGS4D_ERR_ARG;
+  if (!finite_f(s->p_t_min) || s->p_t_min < 0.f || s->p_t_min >= 1.f) return FGS4D_ERR_ARG;
+  for (int k = 0; k < 3; ++k)
+    if (!finite_f(s->bg[k])) return FGS4D_ERR_ARG;
+  if (s->inst_capacity <= 0 || s->inst_capacity > kMaxCap) return FGS4D_ERR_ARG;
+  if (s->vis_capacity < 0 || s->vis_capacity > kMaxCap) return FGS4D_ERR_ARG;
+  return FGS4D_OK;
+}
+
+int check_views(const fgs4d_view *views, int32_t nviews) {
+  if (!views || nviews < 1 || nviews > FGS4D_MAX_VIEWS) return FGS4D_ERR_ARG;
+  for (int v = 0; v < nviews; ++v) {
+    const fgs4d_view &c = views[v];
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return FGS4D_ERR_ARG;
+    if (!finite_f(c.fx) || !finite_f(c.fy) || !finite_f(c.cx) || !finite_f(c.cy) || !finite_f(c.t)) return FGS4D_ERR_ARG;
+    for (int k = 0; k < 12; ++k)
+      if (!finite_f(c.viewmat[k])) return FGS4D_ERR_ARG;
+    for (int k = 0; k < 3; ++k)
+      if (!finite_f(c.campos[k])) return FGS4D_ERR_ARG;
+  }
+  return FGS4D_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_gaussians(const fgs4d_gaussians *g) {
+  if (!g || g->n < 0 || g->n > (int64_t)INT32_MAX - 1024) return FGS4D_ERR_ARG;
+  if (g->n == 0) return FGS4D_OK;
+  const void *ptrs[6] = {g->mean, g->log_scale, g->q_l, g->q_r, g->opacity_logit, g->sh};
+  for (int k = 0; k < 6; ++k)
+    if (!ptrs[k]) return FGS4D_ERR_ARG;
+  // float4 loads of the [n][4] planes and of the SH rows.
+  if (!aligned16(g->mean) || !aligned16(g->log_scale) || !aligned16(g->q_l) || !aligned16(g->q_r) ||
+      !aligned16(g->sh))
+    return FGS4D_ERR_ARG;
+  return FGS4D_OK;
+}
+
+int check_workspace(const Layout &L, const void *ws, size_t bytes) {
+  if (!ws || ((uintptr_t)ws & (kAlign - 1)) != 0) return FGS4D_ERR_WORKSPACE;
+  if (bytes < L.total) return FGS4D_ERR_WORKSPACE;
+  return FGS4D_OK;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? FGS4D_OK : FGS4D_ERR_CUDA; }
+
+}  // namespace
+
+int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, int32_t nviews, Layout *out) {
+  int rc = check_settings(s);
+  if (rc) return rc;
+  rc = check_views(views, nviews);
+  if (rc) return rc;
+  if (n < 0 || n > (int64_t)INT32_MAX - 1024) return FGS4D_ERR_ARG;
+  Layout L;
+  memset(&L, 0, sizeof L);
+  L.n = n;
+  L.nviews = nviews;
+  L.vis_cap = s->vis_capacity ? s->vis_capacity : n * (int64_t)nviews;
+  if (L.vis_cap > kMaxCap) return FGS4D_ERR_ARG;  // set vis_capacity explicitly
+  L.inst_cap = s->inst_capacity;
+  for (int v = 0; v < nviews; ++v) {
+    const int64_t gw = (views[v].width + kTile - 1) / kTile, gh = (views[v].height + kTile - 1) / kTile;
+    L.total_tiles += gw * gh;
+    L.total_pixels += (int64_t)views[v].width * views[v].height;
+  }
+  if (L.total_tiles > INT32_MAX) return FGS4D_ERR_ARG;
+  int bits = 1;
+  while ((1ll << bits) < L.total_tiles) ++bits;
+  L.tile_bits = bits;
+  L.tile_passes = (bits + kRadixBits - 1) / kRadixBits;
+  if (L.tile_passes > kMaxPasses) return FGS4D_ERR_UNSUPPORTED;
+  L.depth_passes = 4;  // 31 bits of a positive FP32 depth
+  L.pre_blocks_per_view = (int32_t)((n + kPreBlock - 1) / kPreBlock);
+  const int64_t pb = (int64_t)L.pre_blocks_per_view * nviews;
+  if (pb > INT32_MAX) return FGS4D_ERR_ARG;
+  L.pre_blocks = (int32_t)pb;
+  L.emit_blocks = (int32_t)((L.vis_cap + kEmitBlock - 1) / kEmitBlock);
+  L.depth_blocks = (int32_t)((L.vis_cap + kSortTile - 1) / kSortTile);
+  L.tile_blocks = (int32_t)((L.inst_cap + kSortTile - 1) / kSortTile);
+
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  L.counters = take(kCtrCount * sizeof(uint32_t));
+  L.lb_pre = take((size_t)L.pre_blocks * sizeof(uint64_t));
+  L.hist_depth = take(kMaxPasses * kRadixBins * sizeof(uint32_t));
+  L.hist_tile = take(kMaxPasses * kRadixBins * sizeof(uint32_t));
+  L.lb_emit = take((size_t)L.emit_blocks * sizeof(uint64_t));
+  L.control_end = off;
+  const size_t vc = (size_t)L.vis_cap, ic = (size_t)L.inst_cap;
+  L.rec_geom = take(vc * 16);
+  L.rec_color = take(vc * 16);
+  L.rec_blue = take(vc * 4);
+  L.rec_meta = take(vc * 16);
+  for (int k = 0; k < 2; ++k) {
+    L.depth_key[k] = take(vc * 4);
+    L.depth_val[k] = take(vc * 4);
+  }
+  L.depth_state = take((size_t)L.depth_passes * L.depth_blocks * kRadixBins * sizeof(uint32_t));
+  for (int k = 0; k < 2; ++k) {
+    L.inst_key[k] = take(ic * 4);
+    L.inst_val[k] = take(ic * 4);
+  }
+  L.tile_state = take((size_t)L.tile_passes * L.tile_blocks * kRadixBins * sizeof(uint32_t));
+  L.ranges = take((size_t)L.total_tiles * 8);
+  L.pix_T = take((size_t)L.total_pixels * 4);
+  L.pix_last = take((size_t)L.total_pixels * 4);
+  L.slot_grad = take(vc * kSlotGradFloats * sizeof(float));
+  L.total = off;
+  *out = L;
+  return FGS4D_OK;
+}
+
+}  // namespace fgs4d
+
+using namespace fgs4d;
+
+extern "C" {
+
+int fgs4d_workspace_size(const fgs4d_settings *settings, int64_t n, const fgs4d_view *views, int32_t nviews,
+                         size_t *bytes_out) {
+  if (!bytes_out) return FGS4D_ERR_ARG;
+  Layout L;
+  const int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  *bytes_out = L.total;
+  return FGS4D_OK;
+}
+
+int fgs4d_workspace_layout(const fgs4d_settings *settings, int64_t n, const fgs4d_view *views, int32_t nviews,
+                           fgs4d_layout *o) {
+  if (!o) return FGS4D_ERR_ARG;
+  Layout L;
+  const int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  memset(o, 0, sizeof *o);
+  o->bytes = L.total;
+  o->counters = L.counters;
+  o->rec_geom = L.rec_geom;
+  o->rec_color = L.rec_color;
+  o->rec_blue = L.rec_blue;
+  o->rec_meta = L.rec_meta;
+  o->depth_key = L.depth_key[0];
+  o->sorted_slots = L.depth_val[L.depth_passes & 1];
+  o->inst_tile = L.inst_key[L.tile_passes & 1];
+  o->inst_slot = L.inst_val[L.tile_passes & 1];
+  o->tile_ranges = L.ranges;
+  o->pix_T = L.pix_T;
+  o->pix_last = L.pix_last;
+  o->slot_grad = L.slot_grad;
+  o->vis_capacity = L.vis_cap;
+  o->inst_capacity = L.inst_cap;
+  o->total_tiles = L.total_tiles;
+  o->total_pixels = L.total_pixels;
+  return FGS4D_OK;
+}
+
+int fgs4d_preprocess(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                     const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, void *stream) {
+  int rc = check_gaussians(gaussians);
+  if (rc) return rc;
+  Layout L;
+  rc = compute_layout(settings, gaussians->n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Counters, status word and the preprocess look-back states start at zero.
+  cudaError_t e = cudaMemsetAsync(ws, 0, L.lb_pre + (size_t)L.pre_blocks * sizeof(uint64_t), st);
+  if (e != cudaSuccess) return FGS4D_ERR_CUDA;
+  PreLaunch p{gaussians, settings, &L, ws, st};
+  return cuda_status(launch_preprocess(p, views, nviews));
+}
+
+int fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                   void *workspace, size_t workspace_bytes, void *stream) {
+  Layout L;
+  int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  return cuda_status(launch_bin_sort(L, views, nviews, static_cast<unsigned char *>(workspace),
+                                     static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_render_fwd(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                     void *workspace, size_t workspace_bytes, float *out_rgb, float *out_T, void *stream) {
+  Layout L;
+  int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  if (!out_rgb) return FGS4D_ERR_ARG;
+  return cuda_status(launch_render_fwd(L, settings, views, nviews, static_cast<unsigned char *>(workspace), out_rgb,
+                                       out_T, nullptr, static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_render_stats(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                       void *workspace, size_t workspace_bytes, float *out_rgb, uint64_t *stats_out, void *stream) {
+  Layout L;
+  int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  if (!out_rgb || !stats_out || ((uintptr_t)stats_out & 7u)) return FGS4D_ERR_ARG;
+  return cuda_status(launch_render_fwd(L, settings, views, nviews, static_cast<unsigned char *>(workspace), out_rgb,
+                                       nullptr, reinterpret_cast<unsigned long long *>(stats_out),
+                                       static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_render_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                     const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, const float *dL_drgb,
+                     const fgs4d_gaussians_grad *grads, void *stream) {
+  int rc = check_gaussians(gaussians);
+  if (rc) return rc;
+  Layout L;
+  rc = compute_layout(settings, gaussians->n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  if (!dL_drgb || !grads) return FGS4D_ERR_ARG;
+  if (gaussians->n > 0) {
+    if (!grads->mean || !grads->log_scale || !grads->q_l || !grads->q_r || !grads->opacity_logit || !grads->sh)
+      return FGS4D_ERR_ARG;
+    if (!aligned16(grads->mean) || !aligned16(grads->log_scale) || !aligned16(grads->q_l) ||
+        !aligned16(grads->q_r) || !aligned16(grads->sh))
+      return FGS4D_ERR_ARG;
+  }
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_render_bwd(L, settings, views, nviews, ws, dL_drgb, st);
+  if (e != cudaSuccess) return FGS4D_ERR_CUDA;
+  PreLaunch p{gaussians, settings, &L, ws, st};
+  return cuda_status(launch_preprocess_bwd(p, views, nviews, grads));
+}
+
+int fgs4d_l1_loss(const float *img, const float *target, int64_t count, float *loss_out, float *dL_dimg,
+                  void *stream) {
+  if (count < 0 || (count > 0 && (!img || !target || !loss_out || !dL_dimg))) return FGS4D_ERR_ARG;
+  return cuda_status(launch_l1_loss(img, target, count, loss_out, dL_dimg, static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_get_status(const void *workspace, size_t workspace_bytes, void *stream, int64_t *counts_out) {
+  if (!workspace || workspace_bytes < kCtrCount * sizeof(uint32_t)) return FGS4D_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FGS4D_ERR_CUDA;
+  uint32_t c[8];
+  if (cudaMemcpy(c, workspace, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return FGS4D_ERR_CUDA;
+  if (counts_out) {
+    counts_out[0] = c[kCtrVisible];
+    counts_out[1] = c[kCtrInstances];
+    counts_out[2] = c[kCtrNeedVisible];
+    counts_out[3] = c[kCtrNeedInstances];
+  }
+  const uint32_t s = c[kCtrStatus];
+  if (s & (kStatusVisOverflow | kStatusInstOverflow)) return FGS4D_ERR_CAPACITY;
+  if (s & kStatusTimeout) return FGS4D_ERR_TIMEOUT;
+  if (s & kStatusInternal) return FGS4D_ERR_INTERNAL;
+  return FGS4D_OK;
+}
+
+const char *fgs4d_status_string(int status) {
+  switch (status) {
+    case FGS4D_OK: return "ok";
+    case FGS4D_ERR_ARG: return "invalid argument";
+    case FGS4D_ERR_CUDA: return "CUDA runtime error";
+    case FGS4D_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case FGS4D_ERR_CAPACITY: return "visible or instance capacity exceeded";
+    case FGS4D_ERR_TIMEOUT: return "bounded inter-block wait ran out";
+    case FGS4D_ERR_INTERNAL: return "internal consistency check failed";
+    case FGS4D_ERR_UNSUPPORTED: return "setting outside the compiled range";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

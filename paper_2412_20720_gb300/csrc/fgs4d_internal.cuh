@@ -1,0 +1,275 @@
+// Internal declarations shared by the CUDA translation units of the fgs4d
+// library.  Nothing here is part of the C ABI (include/fgs4d.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fgs4d.h"
+
+namespace fgs4d {
+
+constexpr int kTile = 16;           // tile edge in pixels
+constexpr int kTilePixels = kTile * kTile;
+constexpr int kPreBlock = 256;      // threads per preprocess block
+constexpr int kEmitBlock = 256;     // threads per emit block (one visible slot each)
+constexpr int kSortThreads = 256;   // threads per radix block
+constexpr int kSortItems = 8;       // keys per thread per radix block
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kHistItems = 4 * kSortTile;  // keys per histogram block
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kMaxPasses = 4;
+constexpr int kSlotGradFloats = 12;
+
+// Status bits of the workspace status word.
+constexpr unsigned kStatusVisOverflow = 1u;
+constexpr unsigned kStatusInstOverflow = 2u;
+constexpr unsigned kStatusTimeout = 4u;
+constexpr unsigned kStatusInternal = 8u;
+
+// Bounded inter-block waits: polls (each followed by a short sleep) before a
+// wait gives up, records kStatusTimeout and proceeds with clamped indices.
+constexpr uint32_t kSpinLimit = 1u << 21;
+
+// uint32 counters at workspace offset 0.
+enum Counter : int {
+  kCtrVisible = 0,
+  kCtrInstances = 1,
+  kCtrStatus = 2,
+  kCtrNeedVisible = 3,
+  kCtrNeedInstances = 4,
+  kCtrTicketPre = 5,
+  // bytes [0, 32) are reset by preprocess only; the rest by bin_sort as well
+  kCtrTicketEmit = 8,
+  kCtrTicketDepth = 10,  // kMaxPasses entries
+  kCtrTicketTile = 14,   // kMaxPasses entries
+  kCtrCount = 64
+};
+constexpr size_t kSortControlStart = 32;
+
+// ------------------------------------------------------------ view tables
+
+struct PreView {
+  float W[9];
+  float T[3];
+  float fx, fy, cx, cy;
+  float campos[3];
+  float t;
+  int32_t width, height, gw, gh;
+};
+
+template <int MAXV>
+struct PreViews {
+  PreView v[MAXV];
+};
+
+struct RasterView {
+  int32_t tile_base, gw, gh, width, height, pad;
+  int64_t pix_base;
+};
+
+template <int MAXV>
+struct RasterViews {
+  RasterView v[MAXV];
+  int32_t nviews;
+  int32_t total_tiles;
+};
+
+// ------------------------------------------------------- workspace layout
+
+struct Layout {
+  size_t counters;
+  size_t lb_pre;        // uint64 per preprocess block
+  size_t hist_depth;    // uint32 [kMaxPasses][256]
+  size_t hist_tile;     // uint32 [kMaxPasses][256]
+  size_t lb_emit;       // uint64 per emit block
+  size_t control_end;
+  size_t rec_geom, rec_color, rec_blue, rec_meta;
+  size_t depth_key[2], depth_val[2];
+  size_t depth_state;   // uint32 [kMaxPasses][depth_blocks][256]
+  size_t inst_key[2], inst_val[2];
+  size_t tile_state;    // uint32 [kMaxPasses][tile_blocks][256]
+  size_t ranges;
+  size_t pix_T, pix_last;
+  size_t slot_grad;
+  size_t total;
+
+  int64_t n;
+  int32_t nviews;
+  int64_t vis_cap, inst_cap;
+  int64_t total_tiles, total_pixels;
+  int32_t pre_blocks_per_view, pre_blocks;
+  int32_t emit_blocks;
+  int32_t depth_blocks, tile_blocks;
+  int32_t depth_passes, tile_passes;
+  int32_t tile_bits;
+};
+
+// Host: computes the layout; returns FGS4D_OK or an error code.
+int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, int32_t nviews, Layout *out);
+
+// --------------------------------------------------------- device helpers
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Decoupled look-back over uint64 block states (flag in bits 62-63: 1 =
+// aggregate only, 2 = inclusive prefix).  Called by one thread of logical
+// block `bid` with the block's aggregate; returns the exclusive prefix.
+// Predecessors hold smaller tickets, so they are resident or finished and the
+// wait ends; the poll count is still bounded.
+__device__ __forceinline__ uint64_t lookback_u64(uint64_t *state, int32_t bid, uint64_t agg, uint32_t *status) {
+  constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kMask = (1ull << 62) - 1;
+  if (bid == 0) {
+    st_release(&state[0], kInc | agg);
+    return 0;
+  }
+  st_release(&state[bid], kAgg | agg);
+  uint64_t prefix = 0;
+  int32_t j = bid - 1;
+  uint32_t polls = 0;
+  while (j >= 0) {
+    const uint64_t s = ld_acquire(&state[j]);
+    const uint64_t f = s & ~kMask;
+    if (f == 0) {
+      if (++polls > kSpinLimit) {
+        atomicOr(status, kStatusTimeout);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    prefix += s & kMask;
+    if (f == kInc) break;
+    --j;
+  }
+  st_release(&state[bid], kInc | (prefix + agg));
+  return prefix;
+}
+
+// Block-wide exclusive scan of one uint32 per thread (blockDim.x == 256).
+// `smem` needs 8 + 1 words.  Returns the exclusive prefix; *total = sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *smem, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) smem[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < 8 ? smem[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < 8) smem[lane] = wi - w;
+    if (lane == 7) smem[8] = wi;
+  }
+  __syncthreads();
+  const uint32_t r = smem[warp] + inc - x;
+  *total = smem[8];
+  __syncthreads();
+  return r;
+}
+
+// Shared alpha evaluation of the compositor, used verbatim by the forward
+// and backward kernels so both take identical skip/stop decisions.
+// power2 = -(A' dx^2 + B' dx dy + C' dy^2) is the exponent in base 2.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+struct AlphaEval {
+  float dx, dy, power2, G, aG, alpha;
+};
+
+__device__ __forceinline__ AlphaEval eval_alpha(float4 geom, float C2, float a, float pxc, float pyc) {
+  AlphaEval e;
+  e.dx = __fsub_rn(geom.x, pxc);
+  e.dy = __fsub_rn(geom.y, pyc);
+  const float q = __fmaf_rn(geom.z, __fmul_rn(e.dx, e.dx),
+                            __fmaf_rn(C2, __fmul_rn(e.dy, e.dy), __fmul_rn(geom.w, __fmul_rn(e.dx, e.dy))));
+  e.power2 = -q;
+  e.G = ex2_approx(e.power2);
+  e.aG = __fmul_rn(a, e.G);
+  e.alpha = fminf(0.99f, e.aG);
+  return e;
+}
+
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// ------------------------------------------------------ host-side launchers
+
+struct PreLaunch {
+  const fgs4d_gaussians *g;
+  const fgs4d_settings *s;
+  const Layout *L;
+  unsigned char *ws;
+  cudaStream_t stream;
+};
+
+cudaError_t launch_preprocess(const PreLaunch &p, const fgs4d_view *views, int32_t nviews);
+cudaError_t launch_preprocess_bwd(const PreLaunch &p, const fgs4d_view *views, int32_t nviews,
+                                  const fgs4d_gaussians_grad *grads);
+cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nviews, unsigned char *ws,
+                            cudaStream_t stream);
+cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
+                              unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
+                              cudaStream_t stream);
+cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
+                              unsigned char *ws, const float *dL_drgb, cudaStream_t stream);
+cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, float *loss, float *grad,
+                           cudaStream_t stream);
+
+// Fills a raster view table; returns false if nviews exceeds MAXV.
+template <int MAXV>
+inline bool make_raster_views(const Layout &L, const fgs4d_view *views, int32_t nviews, RasterViews<MAXV> *out) {
+  if (nviews > MAXV) return false;
+  int64_t tb = 0, pb = 0;
+  for (int v = 0; v < nviews; ++v) {
+    RasterView &r = out->v[v];
+    r.width = views[v].width;
+    r.height = views[v].height;
+    r.gw = (views[v].width + kTile - 1) / kTile;
+    r.gh = (views[v].height + kTile - 1) / kTile;
+    r.tile_base = (int32_t)tb;
+    r.pix_base = pb;
+    r.pad = 0;
+    tb += (int64_t)r.gw * r.gh;
+    pb += (int64_t)r.width * r.height;
+  }
+  for (int v = nviews; v < MAXV; ++v) out->v[v] = RasterView{};
+  out->nviews = nviews;
+  out->total_tiles = (int32_t)tb;
+  return true;
+}
+
+}  // namespace fgs4d

@@ -1,0 +1,317 @@
+// Tile binning and sorting for the tile rasterizer the paper adapts
+// (Sec. 3.2 of arXiv 2412.20720; depth-ordered blending of Eq. 6).
+//
+// The required order of a tile's list is (FP32 depth, slot) ascending, where
+// slots number the visible pairs in (view, Gaussian index) order.  Instead of
+// sorting every (tile, Gaussian) instance on a 64-bit (tile << 32 | depth)
+// key, the visible pairs are first sorted by depth alone (31 key bits, one
+// element per pair), the instances are then emitted in that order, and a
+// stable sort on the tile id alone (13-19 bits) groups them per tile.  Both
+// sorts are stable LSD radix sorts, so the result equals the sort on the
+// 64-bit key with the slot as tie-break, while the instance array (8x larger
+// than the visible set at the benchmark sizes) is only passed over
+// ceil(tile_bits / 8) times.
+//
+// Each radix pass is one kernel: blocks take tickets in launch order, rank
+// their 2048 keys stably with warp match, publish per-digit counts and find
+// their per-digit global offsets by decoupled look-back over the earlier
+// tickets (bounded waits), then scatter through shared memory.
+#include "fgs4d_internal.cuh"
+
+namespace fgs4d {
+
+namespace {
+
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kValMask = kFlagAgg - 1u;
+
+// Digit histograms of keys [0, count) for `passes` 8-bit digits starting at
+// bit 0; also clears the look-back rows the radix passes will use and the
+// tile ranges (grid-stride).
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t *__restrict__ keys,
+                                                                  const uint32_t *__restrict__ count_ptr, int64_t cap,
+                                                                  int32_t passes, uint32_t *hist, uint32_t *state,
+                                                                  int32_t state_blocks, uint2 *ranges,
+                                                                  int64_t nranges) {
+  __shared__ uint32_t s_hist[kMaxPasses][kRadixBins];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nranges; r += (int64_t)gridDim.x * blockDim.x)
+    ranges[r] = make_uint2(0u, 0u);
+  const int64_t count = min64((int64_t)*count_ptr, cap);
+  const int64_t base = (int64_t)blockIdx.x * kHistItems;
+  if (base >= count) return;
+  for (int p = 0; p < passes; ++p) s_hist[p][threadIdx.x] = 0u;
+  // Clear the look-back rows of the radix blocks covering this range.
+  const int64_t ob0 = base / kSortTile;
+  for (int p = 0; p < passes; ++p)
+    for (int64_t ob = ob0; ob < ob0 + kHistItems / kSortTile && ob < state_blocks && ob * kSortTile < count; ++ob)
+      state[((int64_t)p * state_blocks + ob) * kRadixBins + threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t end = min64(base + kHistItems, count);
+  for (int64_t idx = base + threadIdx.x; idx < end; idx += kSortThreads) {
+    const uint32_t k = keys[idx];
+    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(k >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
+  }
+  __syncthreads();
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t c = s_hist[p][threadIdx.x];
+    if (c) atomicAdd(&hist[p * kRadixBins + threadIdx.x], c);
+  }
+}
+
+template <bool kValsAreIndex>
+__global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+    uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ count_ptr, int64_t cap, int32_t shift,
+    const uint32_t *__restrict__ hist, uint32_t *state, uint32_t *ticket, uint32_t *status) {
+  __shared__ uint32_t s_ticket;
+  __shared__ uint32_t s_wcount[kSortThreads / 32][kRadixBins];
+  __shared__ uint32_t s_bstart[kRadixBins];
+  __shared__ uint32_t s_gstart[kRadixBins];
+  __shared__ uint32_t s_scan[9];
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+
+  const int64_t count = min64((int64_t)*count_ptr, cap);
+  if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
+  for (int d = threadIdx.x; d < (kSortThreads / 32) * kRadixBins; d += kSortThreads) (&s_wcount[0][0])[d] = 0u;
+  __syncthreads();
+  const int64_t b = s_ticket;
+  const int64_t tile0 = b * kSortTile;
+  if (tile0 >= count) return;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+  int dig[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t idx = tile0 + warp * (32 * kSortItems) + k * 32 + lane;
+    if (idx < count) {
+      key[k] = keys_in[idx];
+      val[k] = kValsAreIndex ? (uint32_t)idx : vals_in[idx];
+      dig[k] = (key[k] >> shift) & (kRadixBins - 1);
+    } else {
+      key[k] = 0u;
+      val[k] = 0u;
+      dig[k] = kRadixBins;  // padding: ranked nowhere
+    }
+  }
+  // Stable rank within the warp's contiguous segment (item-major, lane-minor).
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int d = dig[k];
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = 0u;
+    if (d < kRadixBins) before = s_wcount[warp][d];
+    __syncwarp();
+    if (d < kRadixBins && lane == __ffs(peers) - 1) s_wcount[warp][d] = before + __popc(peers);
+    __syncwarp();
+    rank[k] = before + __popc(peers & lt_mask);
+  }
+  __syncthreads();
+  // Per digit: exclusive prefix over warps; block count.
+  const int d = threadIdx.x;
+  uint32_t cnt = 0u;
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) {
+    const uint32_t c = s_wcount[w][d];
+    s_wcount[w][d] = cnt;
+    cnt += c;
+  }
+  uint32_t total;
+  s_bstart[d] = block_exclusive_scan(cnt, s_scan, &total);
+  const uint32_t gpre = block_exclusive_scan(hist[d], s_scan, &total);
+  // Decoupled look-back for this digit.
+  uint32_t prefix = 0u;
+  if (b == 0) {
+    st_release(&state[d], kFlagInc | cnt);
+  } else {
+    st_release(&state[b * kRadixBins + d], kFlagAgg | cnt);
+    int64_t j = b - 1;
+    uint32_t polls = 0;
+    while (j >= 0) {
+      const uint32_t s = ld_acquire(&state[j * kRadixBins + d]);
+      const uint32_t f = s & ~kValMask;
+      if (f == 0u) {
+        if (++polls > kSpinLimit) {
+          atomicOr(status, kStatusTimeout);
+          break;
+        }
+        __nanosleep(32);
+        continue;
+      }
+      prefix += s & kValMask;
+      if (f == kFlagInc) break;
+      --j;
+    }
+    st_release(&state[b * kRadixBins + d], kFlagInc | ((prefix + cnt) & kValMask));
+  }
+  s_gstart[d] = gpre + prefix;
+  __syncthreads();
+  // Block-local order through shared memory, then coalesced runs per digit.
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    if (dig[k] < kRadixBins) {
+      const uint32_t pos = s_bstart[dig[k]] + s_wcount[warp][dig[k]] + rank[k];
+      s_keys[pos] = key[k];
+      s_vals[pos] = val[k];
+    }
+  }
+  __syncthreads();
+  const int32_t nvalid = (int32_t)min64(kSortTile, count - tile0);
+  for (int p = threadIdx.x; p < nvalid; p += kSortThreads) {
+    const uint32_t kk = s_keys[p];
+    const int dd = (kk >> shift) & (kRadixBins - 1);
+    const uint32_t gpos = s_gstart[dd] + ((uint32_t)p - s_bstart[dd]);
+    if ((int64_t)gpos < count) {
+      keys_out[gpos] = kk;
+      vals_out[gpos] = s_vals[p];
+    } else {
+      atomicOr(status, kStatusInternal);
+    }
+  }
+}
+
+// One thread per depth-sorted visible slot: exclusive scan of tile counts
+// (decoupled look-back), then the slot's instances in row-major tile order.
+template <int MAXV>
+__global__ void __launch_bounds__(kEmitBlock) emit_kernel(const uint32_t *__restrict__ sorted_slots,
+                                                          const int4 *__restrict__ meta, uint32_t *counters,
+                                                          int64_t vis_cap, int64_t inst_cap, uint32_t *inst_key,
+                                                          uint32_t *inst_val, uint64_t *lb, RasterViews<MAXV> rv) {
+  __shared__ uint32_t s_ticket;
+  __shared__ uint32_t s_scan[9];
+  __shared__ uint64_t s_base;
+  const int64_t nvis = min64((int64_t)counters[kCtrVisible], vis_cap);
+  if (threadIdx.x == 0) s_ticket = atomicAdd(&counters[kCtrTicketEmit], 1u);
+  __syncthreads();
+  const int64_t b = s_ticket;
+  if (b == 0 && nvis == 0 && threadIdx.x == 0) {  // no slot: no instances
+    counters[kCtrInstances] = 0u;
+    counters[kCtrNeedInstances] = 0u;
+  }
+  if (b * kEmitBlock >= nvis) return;
+  const int64_t j = b * kEmitBlock + threadIdx.x;
+  uint32_t s = 0u, cnt = 0u;
+  int4 m = make_int4(0, 0, 0, 0);
+  if (j < nvis) {
+    s = sorted_slots[j];
+    if ((int64_t)s < nvis) {
+      m = meta[s];
+      const int x0 = m.z & 0xffff, y0 = (uint32_t)m.z >> 16, x1 = m.w & 0xffff, y1 = (uint32_t)m.w >> 16;
+      cnt = (uint32_t)(max(x1 - x0, 0) * max(y1 - y0, 0));
+    } else {
+      atomicOr(&counters[kCtrStatus], kStatusInternal);
+    }
+  }
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan(cnt, s_scan, &total);
+  if (threadIdx.x == 0) {
+    const uint64_t prefix = lookback_u64(lb, (int32_t)b, total, &counters[kCtrStatus]);
+    s_base = prefix;
+    if ((b + 1) * kEmitBlock >= nvis) {  // last block with visible slots
+      const uint64_t all = prefix + total;
+      counters[kCtrNeedInstances] = (uint32_t)umin64(all, 0xffffffffull);
+      counters[kCtrInstances] = (uint32_t)umin64(all, (uint64_t)inst_cap);
+      if (all > (uint64_t)inst_cap) atomicOr(&counters[kCtrStatus], kStatusInstOverflow);
+    }
+  }
+  __syncthreads();
+  if (cnt == 0u) return;
+  const int view = MAXV == 1 ? 0 : min(max(m.y, 0), rv.nviews - 1);
+  const int32_t tb = rv.v[view].tile_base, gw = rv.v[view].gw;
+  const int x0 = m.z & 0xffff, y0 = (uint32_t)m.z >> 16, x1 = m.w & 0xffff, y1 = (uint32_t)m.w >> 16;
+  uint64_t pos = s_base + excl;
+  for (int ty = y0; ty < y1; ++ty)
+    for (int tx = x0; tx < x1; ++tx, ++pos) {
+      if (pos >= (uint64_t)inst_cap) return;
+      inst_key[pos] = (uint32_t)(tb + ty * gw + tx);
+      inst_val[pos] = s;
+    }
+}
+
+__global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ counters, int64_t cap,
+                              uint2 *ranges, int64_t total_tiles, uint32_t *status) {
+  const int64_t count = min64((int64_t)counters[kCtrInstances], cap);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = keys[i];
+    if ((int64_t)k >= total_tiles) {
+      atomicOr(status, kStatusInternal);
+      continue;
+    }
+    if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
+    if (i == count - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
+  }
+}
+
+template <int MAXV>
+cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nviews, unsigned char *ws,
+                           cudaStream_t st) {
+  RasterViews<MAXV> rv;
+  if (!make_raster_views<MAXV>(L, views, nviews, &rv)) return cudaErrorInvalidValue;
+  uint32_t *ctr = reinterpret_cast<uint32_t *>(ws + L.counters);
+  uint32_t *status = ctr + kCtrStatus;
+  cudaError_t e = cudaMemsetAsync(ws + kSortControlStart, 0, L.control_end - kSortControlStart, st);
+  if (e != cudaSuccess) return e;
+  // 1. Depth sort of the visible slots (31 key bits: depth > near > 0).
+  uint32_t *dk[2] = {reinterpret_cast<uint32_t *>(ws + L.depth_key[0]), reinterpret_cast<uint32_t *>(ws + L.depth_key[1])};
+  uint32_t *dv[2] = {reinterpret_cast<uint32_t *>(ws + L.depth_val[0]), reinterpret_cast<uint32_t *>(ws + L.depth_val[1])};
+  uint32_t *dstate = reinterpret_cast<uint32_t *>(ws + L.depth_state);
+  uint32_t *hist_d = reinterpret_cast<uint32_t *>(ws + L.hist_depth);
+  if (L.depth_blocks > 0) {
+    const int hb = (int)((L.vis_cap + kHistItems - 1) / kHistItems);
+    radix_hist_kernel<<<hb, kSortThreads, 0, st>>>(dk[0], ctr + kCtrVisible, L.vis_cap, L.depth_passes, hist_d,
+                                                  dstate, L.depth_blocks, nullptr, 0);
+    for (int p = 0; p < L.depth_passes; ++p) {
+      const int in = p & 1, out = in ^ 1;
+      uint32_t *state = dstate + (size_t)p * L.depth_blocks * kRadixBins;
+      if (p == 0)
+        radix_pass_kernel<true><<<L.depth_blocks, kSortThreads, 0, st>>>(
+            dk[in], nullptr, dk[out], dv[out], ctr + kCtrVisible, L.vis_cap, kRadixBits * p,
+            hist_d + p * kRadixBins, state, ctr + kCtrTicketDepth + p, status);
+      else
+        radix_pass_kernel<false><<<L.depth_blocks, kSortThreads, 0, st>>>(
+            dk[in], dv[in], dk[out], dv[out], ctr + kCtrVisible, L.vis_cap, kRadixBits * p,
+            hist_d + p * kRadixBins, state, ctr + kCtrTicketDepth + p, status);
+    }
+  }
+  const uint32_t *sorted = dv[L.depth_passes & 1];
+  // 2. Instances in depth order.
+  uint32_t *ik[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_key[0]), reinterpret_cast<uint32_t *>(ws + L.inst_key[1])};
+  uint32_t *iv[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_val[0]), reinterpret_cast<uint32_t *>(ws + L.inst_val[1])};
+  if (L.emit_blocks > 0)
+    emit_kernel<MAXV><<<L.emit_blocks, kEmitBlock, 0, st>>>(sorted, reinterpret_cast<const int4 *>(ws + L.rec_meta),
+                                                            ctr, L.vis_cap, L.inst_cap, ik[0], iv[0],
+                                                            reinterpret_cast<uint64_t *>(ws + L.lb_emit), rv);
+  // 3. Stable sort of the instances by global tile id.
+  uint32_t *tstate = reinterpret_cast<uint32_t *>(ws + L.tile_state);
+  uint32_t *hist_t = reinterpret_cast<uint32_t *>(ws + L.hist_tile);
+  uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
+  const int hbt = (int)((L.inst_cap + kHistItems - 1) / kHistItems);
+  radix_hist_kernel<<<hbt, kSortThreads, 0, st>>>(ik[0], ctr + kCtrInstances, L.inst_cap, L.tile_passes, hist_t,
+                                                 tstate, L.tile_blocks, ranges, L.total_tiles);
+  for (int p = 0; p < L.tile_passes; ++p) {
+    const int in = p & 1, out = in ^ 1;
+    uint32_t *state = tstate + (size_t)p * L.tile_blocks * kRadixBins;
+    radix_pass_kernel<false><<<L.tile_blocks, kSortThreads, 0, st>>>(
+        ik[in], iv[in], ik[out], iv[out], ctr + kCtrInstances, L.inst_cap, kRadixBits * p, hist_t + p * kRadixBins,
+        state, ctr + kCtrTicketTile + p, status);
+  }
+  // 4. Tile ranges.
+  const uint32_t *final_keys = ik[L.tile_passes & 1];
+  int rb = (int)min64((L.inst_cap + 255) / 256, 152 * 16);
+  if (rb < 1) rb = 1;
+  ranges_kernel<<<rb, 256, 0, st>>>(final_keys, ctr, L.inst_cap, ranges, L.total_tiles, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nviews, unsigned char *ws,
+                            cudaStream_t stream) {
+  if (nviews == 1) return bin_sort_typed<1>(L, views, nviews, ws, stream);
+  return bin_sort_typed<FGS4D_MAX_VIEWS>(L, views, nviews, ws, stream);
+}
+
+}  // namespace fgs4d

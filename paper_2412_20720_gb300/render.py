@@ -1,0 +1,157 @@
+"""PyTorch glue over the fgs4d C ABI: device memory, streams and autograd.
+
+Every step of the render path (preprocess, binning, sort, compositing and
+their adjoints) runs in libfgs4d.so; this module only allocates buffers,
+passes pointers and the current CUDA stream, and wires the backward pass
+into ``torch.autograd``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import fgs4d
+
+PARAM_KEYS = ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")
+
+
+@dataclass
+class RenderConfig:
+    sh_degree: int = 3
+    t_order: int = 2
+    period: float = 1.0
+    near_plane: float = 0.2
+    dilation: float = 0.3
+    p_t_min: float = 0.05
+    bg: tuple = (0.0, 0.0, 0.0)
+    vis_capacity: int = 0
+    inst_capacity: int = 1 << 22
+
+    def settings(self) -> fgs4d.Settings:
+        return fgs4d.make_settings(self.sh_degree, self.t_order, self.period, self.near_plane, self.dilation,
+                                   self.p_t_min, self.bg, self.vis_capacity, self.inst_capacity)
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _check_param(name, t, n, device):
+    if not isinstance(t, torch.Tensor) or t.device != device or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float32 tensor on %s" % (name, device))
+    if t.shape[0] != n:
+        raise ValueError("%s has %d rows, expected %d" % (name, t.shape[0], n))
+
+
+class Renderer:
+    """Renders N Gaussians into a fixed set of views.  One workspace carries a
+    forward to its backward, so keep one forward/backward pair in flight per
+    renderer (use separate renderers for overlapping work)."""
+
+    def __init__(self, n: int, views, config: RenderConfig, device=None):
+        fgs4d.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.n = int(n)
+        self.config = config
+        self.settings = config.settings()
+        self.view_dicts = list(views)
+        self.views, self.nviews = fgs4d.make_views(self.view_dicts)
+        self.ws_bytes = fgs4d.workspace_size(self.settings, self.n, self.views, self.nviews)
+        self.layout = fgs4d.workspace_layout(self.settings, self.n, self.views, self.nviews)
+        # 256-byte aligned device workspace.
+        self._ws_raw = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self._ws_raw.data_ptr()) % 256
+        self.ws = self._ws_raw[off:off + self.ws_bytes]
+        self.sizes = [(int(v["height"]), int(v["width"])) for v in self.view_dicts]
+        self.total_pixels = int(self.layout.total_pixels)
+
+    # ---------------------------------------------------------------- plumbing
+    def stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def gaussians(self, params: dict) -> fgs4d.Gaussians:
+        for k in PARAM_KEYS:
+            _check_param(k, params[k], self.n, self.device)
+        return fgs4d.make_gaussians({k: _ptr(params[k]) for k in PARAM_KEYS}, self.n)
+
+    def split(self, flat: torch.Tensor) -> list:
+        """Flat [sum 3HW] image buffer -> list of [3, H, W] views."""
+        out, off = [], 0
+        for h, w in self.sizes:
+            out.append(flat[off:off + 3 * h * w].view(3, h, w))
+            off += 3 * h * w
+        return out
+
+    # ------------------------------------------------------------------ calls
+    def forward(self, params: dict, out_rgb: torch.Tensor | None = None, out_T: torch.Tensor | None = None):
+        """Runs preprocess, bin_sort and render_fwd; returns the flat RGB buffer."""
+        g = self.gaussians(params)
+        if out_rgb is None:
+            out_rgb = torch.empty(3 * self.total_pixels, dtype=torch.float32, device=self.device)
+        st = self.stream()
+        ws = _ptr(self.ws)
+        fgs4d.preprocess(g, self.views, self.nviews, self.settings, ws, self.ws_bytes, st)
+        fgs4d.bin_sort(self.n, self.views, self.nviews, self.settings, ws, self.ws_bytes, st)
+        fgs4d.render_fwd(self.n, self.views, self.nviews, self.settings, ws, self.ws_bytes, _ptr(out_rgb),
+                         _ptr(out_T) if out_T is not None else None, st)
+        return out_rgb
+
+    def backward(self, params: dict, dL_drgb: torch.Tensor, grads: dict):
+        """Adds dL/dparams into ``grads`` for the last forward of this renderer."""
+        g = self.gaussians(params)
+        for k in PARAM_KEYS:
+            _check_param("grad " + k, grads[k], self.n, self.device)
+        dL = dL_drgb.contiguous()
+        fgs4d.render_bwd(g, self.views, self.nviews, self.settings, _ptr(self.ws), self.ws_bytes, _ptr(dL),
+                         fgs4d.make_grads({k: _ptr(grads[k]) for k in PARAM_KEYS}), self.stream())
+
+    def status(self):
+        """Synchronises and returns (code, [visible, instances, visible needed, instances needed])."""
+        return fgs4d.get_status(_ptr(self.ws), self.ws_bytes, self.stream())
+
+    def check(self):
+        code, counts = self.status()
+        if code != fgs4d.OK:
+            raise fgs4d.Fgs4dError(code, "render (counts %s)" % counts)
+        return counts
+
+    def workspace_view(self, offset: int, dtype: torch.dtype, count: int) -> torch.Tensor:
+        """A typed view of a documented workspace region (see fgs4d_layout)."""
+        nbytes = count * torch.empty(0, dtype=dtype).element_size()
+        return self.ws[offset:offset + nbytes].view(dtype)
+
+
+class Render4DGS(torch.autograd.Function):
+    """Differentiable render: (renderer, *params) -> flat RGB [sum 3HW]."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, mean, log_scale, q_l, q_r, opacity_logit, sh):
+        params = dict(zip(PARAM_KEYS, (mean, log_scale, q_l, q_r, opacity_logit, sh)))
+        out = renderer.forward(params)
+        ctx.renderer = renderer
+        ctx.save_for_backward(mean, log_scale, q_l, q_r, opacity_logit, sh)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        saved = ctx.saved_tensors
+        params = dict(zip(PARAM_KEYS, saved))
+        grads = {k: torch.zeros_like(v) for k, v in params.items()}
+        ctx.renderer.backward(params, grad_out, grads)
+        return (None,) + tuple(grads[k] for k in PARAM_KEYS)
+
+
+def render(renderer: Renderer, params: dict) -> torch.Tensor:
+    return Render4DGS.apply(renderer, *(params[k] for k in PARAM_KEYS))
+
+
+def l1_loss(img: torch.Tensor, target: torch.Tensor):
+    """L1 loss and its gradient with the fgs4d kernel: returns (loss[1], dL/dimg)."""
+    img = img.contiguous()
+    target = target.contiguous()
+    loss = torch.zeros(1, dtype=torch.float32, device=img.device)
+    grad = torch.empty_like(img)
+    fgs4d.l1_loss(_ptr(img), _ptr(target), img.numel(), _ptr(loss), _ptr(grad),
+                  torch.cuda.current_stream(img.device).cuda_stream)
+    return loss, grad

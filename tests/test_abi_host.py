@@ -1,0 +1,118 @@
+"""Host-side checks of the C ABI: the library builds and loads, exports every
+entry point include/fgs4d.h declares, and rejects bad arguments before any
+work is enqueued.  No GPU is needed (no call here reaches a kernel)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2412_20720_gb300 import fgs4d
+from paper_2412_20720_gb300 import synthetic as sy
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fgs4d.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fgs4d_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_entry_point():
+    lib = fgs4d.load()
+    names = declared_functions()
+    assert len(names) >= 9
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(fgs4d.EXPORTED) == set(names)
+
+
+def _views(k=1):
+    return fgs4d.make_views([sy.tiny_view(128, 96)] * k)
+
+
+def test_workspace_size_and_layout_are_consistent():
+    s = fgs4d.make_settings(sh_degree=1, t_order=1, inst_capacity=100_000)
+    views, nv = _views(2)
+    nbytes = fgs4d.workspace_size(s, 2000, views, nv)
+    lay = fgs4d.workspace_layout(s, 2000, views, nv)
+    assert lay.bytes == nbytes
+    assert lay.vis_capacity == 4000 and lay.inst_capacity == 100_000
+    assert lay.total_tiles == 2 * 8 * 6 and lay.total_pixels == 2 * 128 * 96
+    offs = [lay.counters, lay.rec_geom, lay.rec_color, lay.rec_blue, lay.rec_meta, lay.depth_key, lay.sorted_slots,
+            lay.inst_tile, lay.inst_slot, lay.tile_ranges, lay.pix_T, lay.pix_last, lay.slot_grad]
+    assert all(o % 256 == 0 and o < nbytes for o in offs)
+    assert len(set(offs)) == len(offs)
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("sh_degree", 4, fgs4d.ERR_UNSUPPORTED),
+    ("t_order", 5, fgs4d.ERR_UNSUPPORTED),
+    ("tile", 8, fgs4d.ERR_UNSUPPORTED),
+    ("period", 0.0, fgs4d.ERR_ARG),
+    ("near_plane", -1.0, fgs4d.ERR_ARG),
+    ("dilation", float("nan"), fgs4d.ERR_ARG),
+    ("p_t_min", 1.0, fgs4d.ERR_ARG),
+    ("inst_capacity", 0, fgs4d.ERR_ARG),
+    ("inst_capacity", 1 << 31, fgs4d.ERR_ARG),
+    ("vis_capacity", -1, fgs4d.ERR_ARG),
+])
+def test_bad_settings_are_rejected(field, value, code):
+    s = fgs4d.make_settings()
+    setattr(s, field, value)
+    views, nv = _views()
+    with pytest.raises(fgs4d.Fgs4dError) as e:
+        fgs4d.workspace_size(s, 10, views, nv)
+    assert e.value.code == code
+
+
+def test_bad_views_and_sizes_are_rejected():
+    s = fgs4d.make_settings()
+    views, nv = _views()
+    for n in (-1, 1 << 31):
+        with pytest.raises(fgs4d.Fgs4dError):
+            fgs4d.workspace_size(s, n, views, nv)
+    with pytest.raises(fgs4d.Fgs4dError):
+        fgs4d.workspace_size(s, 10, views, 0)
+    with pytest.raises(fgs4d.Fgs4dError):
+        fgs4d.workspace_size(s, 10, views, fgs4d.MAX_VIEWS + 1)
+    bad = sy.tiny_view(128, 96)
+    bad["width"] = 0
+    v2, n2 = fgs4d.make_views([bad])
+    with pytest.raises(fgs4d.Fgs4dError):
+        fgs4d.workspace_size(s, 10, v2, n2)
+    bad = sy.tiny_view(128, 96)
+    bad["viewmat"] = bad["viewmat"].copy()
+    bad["viewmat"][0, 0] = float("inf")
+    v3, n3 = fgs4d.make_views([bad])
+    with pytest.raises(fgs4d.Fgs4dError):
+        fgs4d.workspace_size(s, 10, v3, n3)
+    # A large scene needs an explicit visible capacity.
+    with pytest.raises(fgs4d.Fgs4dError):
+        fgs4d.workspace_size(s, 600_000_000, *_views(2))
+
+
+def test_calls_reject_missing_or_small_workspace_before_launching():
+    s = fgs4d.make_settings(sh_degree=1, t_order=1)
+    views, nv = _views()
+    g = fgs4d.make_gaussians({k: 0 for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")}, 0)
+    lib = fgs4d.load()
+    assert lib.fgs4d_preprocess(C.byref(g), views, nv, C.byref(s), None, 0, None) == fgs4d.ERR_WORKSPACE
+    assert lib.fgs4d_bin_sort(0, views, nv, C.byref(s), C.c_void_p(256), 16, None) == fgs4d.ERR_WORKSPACE
+    assert lib.fgs4d_bin_sort(0, views, nv, C.byref(s), C.c_void_p(257), 1 << 40, None) == fgs4d.ERR_WORKSPACE
+    # Non-empty scene with a null parameter pointer.
+    g.n = 5
+    assert lib.fgs4d_preprocess(C.byref(g), views, nv, C.byref(s), None, 0, None) == fgs4d.ERR_ARG
+    # Misaligned parameter rows (float4 loads need 16-byte alignment).
+    g2 = fgs4d.make_gaussians({k: 4096 + 4 for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")}, 5)
+    assert lib.fgs4d_preprocess(C.byref(g2), views, nv, C.byref(s), C.c_void_p(1 << 20), 1 << 40, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_render_fwd(0, views, nv, C.byref(s), C.c_void_p(1 << 20), 1 << 40, None, None, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_l1_loss(None, None, 10, None, None, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_get_status(None, 0, None, None) == fgs4d.ERR_WORKSPACE
+
+
+def test_status_strings():
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert fgs4d.status_string(code) not in ("", "unknown status")
+    assert fgs4d.status_string(-99) == "unknown status"

@@ -51,7 +51,10 @@ class Renderer:
 
     def __init__(self, n: int, views, config: RenderConfig, device=None):
         fgs4d.load()
-        self.device = torch.device(device if device is not None else "cuda")
+        dev = torch.device(device if device is not None else "cuda")
+        if dev.type != "cuda":
+            raise ValueError("the fgs4d render path runs on CUDA devices only")
+        self.device = torch.device("cuda", dev.index if dev.index is not None else torch.cuda.current_device())
         self.n = int(n)
         self.config = config
         self.settings = config.settings()

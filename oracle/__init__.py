@@ -25,9 +25,7 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        path = library_path()
-        if not os.path.exists(path):
-            build_oracle()
+        path = build_oracle()  # no-op when the library is newer than its source
         _lib = C.CDLL(path)
         _declare(_lib)
     return _lib
@@ -88,8 +86,11 @@ def _declare(lib):
     lib.orc_rotation.restype = None
     lib.orc_real_sh.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
     lib.orc_real_sh.restype = None
-    lib.orc_sort_instances.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int64,
+    lib.orc_sort_instances.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_ellipse_meets_box.argtypes = [C.c_float] * 10
+    lib.orc_ellipse_meets_box.restype = C.c_int
     lib.orc_sort_instances.restype = C.c_int64
     lib.orc_num_threads.argtypes = []
     lib.orc_num_threads.restype = C.c_int
@@ -260,13 +261,20 @@ def real_sh(L: int, direction) -> np.ndarray:
     return Y
 
 
-def sort_instances(rect, depth_f32, grid_w: int, grid_h: int, cap: int | None = None):
+def sort_instances(rect, depth_f32, grid_w: int, grid_h: int, cap: int | None = None, uv=None, conic2=None,
+                   tau=None, width: int = 0, height: int = 0):
     """Tile-binned instance list sorted by (tile, FP32 depth, index).
+    With uv, conic2 (A', B', C': q = A' dx^2 + B' dx dy + C' dy^2) and tau
+    (FP32 arrays) a rect tile is kept only if the ellipse q <= tau meets its
+    pixel centres (image width x height).
     Returns (keys u64 [M], vals i64 [M], ranges i64 [tiles, 2])."""
     lib = _load()
     rect = np.ascontiguousarray(rect, dtype=np.int32)
     depth_f32 = np.ascontiguousarray(depth_f32, dtype=np.float32)
     n = rect.shape[0]
+    ex = [None, None, None]
+    if uv is not None:
+        ex = [np.ascontiguousarray(x, dtype=np.float32) for x in (uv, conic2, tau)]
     w = np.clip(rect[:, 2] - rect[:, 0], 0, None).astype(np.int64)
     h = np.clip(rect[:, 3] - rect[:, 1], 0, None).astype(np.int64)
     m = int((w * h).sum())
@@ -274,11 +282,17 @@ def sort_instances(rect, depth_f32, grid_w: int, grid_h: int, cap: int | None = 
     keys = np.zeros(max(m, 1), dtype=np.uint64)
     vals = np.zeros(max(m, 1), dtype=np.int64)
     ranges = np.zeros((grid_w * grid_h, 2), dtype=np.int64)
-    got = lib.orc_sort_instances(n, _ptr(rect), _ptr(depth_f32), grid_w, grid_h, cap, _ptr(keys), _ptr(vals),
-                                 _ptr(ranges))
+    got = lib.orc_sort_instances(n, _ptr(rect), _ptr(depth_f32), *(None if x is None else _ptr(x) for x in ex),
+                                 int(width), int(height), grid_w, grid_h, cap, _ptr(keys), _ptr(vals), _ptr(ranges))
     if got < 0:
         raise ValueError("instance count exceeds capacity")
     return keys[:got], vals[:got], ranges
+
+
+def ellipse_meets_box(u, v, A, B, C, tau, x0, x1, y0, y1) -> bool:
+    """FP32 test of the ellipse A dx^2 + B dx dy + C dy^2 <= tau against a box."""
+    return bool(_load().orc_ellipse_meets_box(*(float(np.float32(x)) for x in (u, v, A, B, C, tau, x0, x1, y0,
+                                                                                 y1))))
 
 
 def num_threads() -> int:

@@ -69,7 +69,7 @@ typedef struct {
 } orc_settings;
 
 typedef struct {
-  int32_t *status; /* [n] 0 visible; 1 invalid; 2 temporal; 3 near; 4 det; 5 rect */
+  int32_t *status; /* [n] 0 visible; 1 invalid; 2 temporal; 3 near; 4 det; 5 rect; 6 a < 1/255 */
   int32_t *rect;   /* [n][4] tile rect x0, y0, x1, y1 (half-open) */
   double *p_t;     /* [n] marginal temporal weight */
   double *a_eff;   /* [n] sigmoid(logit) * p_t */
@@ -346,6 +346,14 @@ static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
     g->status = 5;
     return;
   }
+  /* A Gaussian whose effective opacity is below 1/255 is skipped at every
+   * pixel (alpha <= a), so dropping it leaves the image unchanged. */
+  g->a = g->sig * g->pt;
+  g->margin = dmin(g->margin, fabs(g->a * 255.0 - 1.0));
+  if (g->a * 255.0 < 1.0) {
+    g->status = 6;
+    return;
+  }
   /* 4DSH colour (Sec. 3.2): Z_nl^m = cos(2 pi n dt / T) Y_l^m(d), with the
    * view direction d from the camera centre to the sliced mean and
    * dt = t - mu_t; colour = max(0, sum c Z + 0.5). */
@@ -373,7 +381,6 @@ static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
       return;
     }
   }
-  g->a = g->sig * g->pt;
   g->status = 0;
 }
 
@@ -887,7 +894,11 @@ void orc_real_sh(int L, const double *dir, double *Y) {
  * it: one (tile, Gaussian) pair per tile of each visible Gaussian's rect,
  * key = (tile << 32) | bits(depth_f32), sorted by (tile, depth, index).
  * ranges[t] = [start, end) of tile t. Returns the instance count, or -1 if
- * it exceeds cap. */
+ * it exceeds cap.
+ *
+ * With uv != NULL a rect tile is kept only if the Gaussian's 1/255 ellipse
+ * meets the tile's pixel centres (orc_ellipse_meets_box); a dropped tile is
+ * one where every pixel skips the Gaussian, so the image does not change. */
 typedef struct {
   int64_t tile;
   float depth;
@@ -901,12 +912,61 @@ static int inst_cmp(const void *pa, const void *pb) {
   return (a->idx > b->idx) - (a->idx < b->idx);
 }
 
-int64_t orc_sort_instances(int64_t n, const int32_t *rect, const float *depth, int32_t gw, int32_t gh,
-                           int64_t cap, uint64_t *keys, int64_t *vals, int64_t *ranges) {
+/* Does the ellipse {d : A d_x^2 + B d_x d_y + C d_y^2 <= tau} around (u, v)
+ * meet the box [x0, x1] x [y0, y1]?  The exact minimum of the positive
+ * definite form over the box is 0 when the centre is inside, else the least
+ * of the four edge minima (edge x = X: d_y = clamp(-B X / (2 C))).  This is an
+ * integer decision taken from FP32 data, so it is specified as FP32
+ * arithmetic with every operation rounded in this order (the kernel takes
+ * the same decision in the same precision). */
+int orc_ellipse_meets_box(float u, float v, float A, float B, float C, float tau, float x0, float x1, float y0,
+                          float y1) {
+  const float lx = x0 - u, hx = x1 - u, ly = y0 - v, hy = y1 - v;
+  if (lx <= 0.0f && hx >= 0.0f && ly <= 0.0f && hy >= 0.0f) return tau >= 0.0f;
+  const float kx = -B / (2.0f * C);
+  const float ky = -B / (2.0f * A);
+  const float ex[2] = {lx, hx}, ey[2] = {ly, hy};
+  float m = INFINITY;
+  for (int k = 0; k < 2; ++k) {
+    const float X = ex[k];
+    const float Yv = fminf(fmaxf(kx * X, ly), hy);
+    const float qx = (A * (X * X) + B * (X * Yv)) + C * (Yv * Yv);
+    m = fminf(m, qx);
+    const float Y = ey[k];
+    const float Xv = fminf(fmaxf(ky * Y, lx), hx);
+    const float qy = (A * (Xv * Xv) + B * (Xv * Y)) + C * (Y * Y);
+    m = fminf(m, qy);
+  }
+  return m <= tau;
+}
+
+/* Pixel-centre box of tile (tx, ty), clipped to the image. */
+static void tile_box(int tx, int ty, int W, int H, float *x0, float *x1, float *y0, float *y1) {
+  const int px1 = tx * 16 + 15 < W - 1 ? tx * 16 + 15 : W - 1;
+  const int py1 = ty * 16 + 15 < H - 1 ? ty * 16 + 15 : H - 1;
+  *x0 = (float)(tx * 16) + 0.5f;
+  *x1 = (float)px1 + 0.5f;
+  *y0 = (float)(ty * 16) + 0.5f;
+  *y1 = (float)py1 + 0.5f;
+}
+
+static int keep_tile(const float *uv, const float *conic2, const float *tau, int64_t i, int tx, int ty, int W,
+                     int H) {
+  if (!uv) return 1;
+  float x0, x1, y0, y1;
+  tile_box(tx, ty, W, H, &x0, &x1, &y0, &y1);
+  return orc_ellipse_meets_box(uv[2 * i], uv[2 * i + 1], conic2[3 * i], conic2[3 * i + 1], conic2[3 * i + 2],
+                               tau[i], x0, x1, y0, y1);
+}
+
+int64_t orc_sort_instances(int64_t n, const int32_t *rect, const float *depth, const float *uv, const float *conic2,
+                           const float *tau, int32_t W, int32_t H, int32_t gw, int32_t gh, int64_t cap,
+                           uint64_t *keys, int64_t *vals, int64_t *ranges) {
   int64_t m = 0;
   for (int64_t i = 0; i < n; ++i) {
     const int32_t *r = rect + 4 * i;
-    if (r[2] > r[0] && r[3] > r[1]) m += (int64_t)(r[2] - r[0]) * (r[3] - r[1]);
+    for (int ty = r[1]; ty < r[3]; ++ty)
+      for (int tx = r[0]; tx < r[2]; ++tx) m += keep_tile(uv, conic2, tau, i, tx, ty, W, H);
   }
   if (m > cap) return -1;
   orc_inst *a = malloc(sizeof(orc_inst) * (size_t)(m > 0 ? m : 1));
@@ -916,6 +976,7 @@ int64_t orc_sort_instances(int64_t n, const int32_t *rect, const float *depth, i
     const int32_t *r = rect + 4 * i;
     for (int ty = r[1]; ty < r[3]; ++ty)
       for (int tx = r[0]; tx < r[2]; ++tx) {
+        if (!keep_tile(uv, conic2, tau, i, tx, ty, W, H)) continue;
         a[k].tile = (int64_t)ty * gw + tx;
         a[k].depth = depth[i];
         a[k].idx = i;

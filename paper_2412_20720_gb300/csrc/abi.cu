@@ -122,9 +122,10 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.rec_color = take(vc * 16);
   L.rec_blue = take(vc * 4);
   L.rec_meta = take(vc * 16);
+  L.depth_key = take(vc * 4);
   for (int k = 0; k < 2; ++k) {
-    L.depth_key[k] = take(vc * 4);
-    L.depth_val[k] = take(vc * 4);
+    L.dsort_key[k] = take(vc * 4);
+    L.dsort_val[k] = take(vc * 4);
   }
   L.depth_state = take((size_t)L.depth_passes * L.depth_blocks * kRadixBins * sizeof(uint32_t));
   for (int k = 0; k < 2; ++k) {
@@ -170,8 +171,8 @@ int fgs4d_workspace_layout(const fgs4d_settings *settings, int64_t n, const fgs4
   o->rec_color = L.rec_color;
   o->rec_blue = L.rec_blue;
   o->rec_meta = L.rec_meta;
-  o->depth_key = L.depth_key[0];
-  o->sorted_slots = L.depth_val[L.depth_passes & 1];
+  o->depth_key = L.depth_key;
+  o->sorted_slots = L.dsort_val[(L.depth_passes - 1) & 1];
   o->inst_tile = L.inst_key[L.tile_passes & 1];
   o->inst_slot = L.inst_val[L.tile_passes & 1];
   o->tile_ranges = L.ranges;

@@ -86,7 +86,8 @@ struct Layout {
   size_t lb_emit;       // uint64 per emit block
   size_t control_end;
   size_t rec_geom, rec_color, rec_blue, rec_meta;
-  size_t depth_key[2], depth_val[2];
+  size_t depth_key;                 // uint32 per slot (written by preprocess)
+  size_t dsort_key[2], dsort_val[2];  // depth-sort ping-pong buffers
   size_t depth_state;   // uint32 [kMaxPasses][depth_blocks][256]
   size_t inst_key[2], inst_val[2];
   size_t tile_state;    // uint32 [kMaxPasses][tile_blocks][256]

@@ -268,6 +268,9 @@ __device__ __forceinline__ bool forward_chain(int32_t i, const float4 *__restric
   h.rect[2] = min(max(__float2int_rd((h.uv[0] + rad) * inv_tile) + 1, 0), cam.gw);
   h.rect[3] = min(max(__float2int_rd((h.uv[1] + rad) * inv_tile) + 1, 0), cam.gh);
   if (h.rect[0] >= h.rect[2] || h.rect[1] >= h.rect[3]) return false;
+  // alpha <= a everywhere: below 1/255 the Gaussian is skipped at every pixel.
+  h.a = h.sig * h.pt;
+  if (!(h.a * 255.0f >= 1.0f)) return false;
   // 4DSH colour (Sec. 3.2).
   const float wx = h.mu[0] - cam.campos[0], wy = h.mu[1] - cam.campos[1], wz = h.mu[2] - cam.campos[2];
   h.rw = sqrtf(wx * wx + wy * wy + wz * wz);
@@ -318,7 +321,6 @@ __device__ __forceinline__ bool forward_chain(int32_t i, const float4 *__restric
     h.rgb[ch] = fmaxf(0.0f, acc[ch] + 0.5f);
     if (!isfinite(h.rgb[ch])) return false;
   }
-  h.a = h.sig * h.pt;
   return true;
 }
 
@@ -638,7 +640,7 @@ cudaError_t launch_pre_typed(const PreLaunch &p, const fgs4d_view *views, int32_
   A.rec_color = reinterpret_cast<float4 *>(p.ws + Lo.rec_color);
   A.rec_blue = reinterpret_cast<float *>(p.ws + Lo.rec_blue);
   A.rec_meta = reinterpret_cast<int4 *>(p.ws + Lo.rec_meta);
-  A.depth_key = reinterpret_cast<uint32_t *>(p.ws + Lo.depth_key[0]);
+  A.depth_key = reinterpret_cast<uint32_t *>(p.ws + Lo.depth_key);
   if (Lo.pre_blocks == 0) return cudaSuccess;
   preprocess_kernel<L, MAXV><<<Lo.pre_blocks, kPreBlock, 0, p.stream>>>(A, pv);
   return cudaGetLastError();

@@ -254,21 +254,23 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   uint32_t *status = ctr + kCtrStatus;
   cudaError_t e = cudaMemsetAsync(ws + kSortControlStart, 0, L.control_end - kSortControlStart, st);
   if (e != cudaSuccess) return e;
-  // 1. Depth sort of the visible slots (31 key bits: depth > near > 0).
-  uint32_t *dk[2] = {reinterpret_cast<uint32_t *>(ws + L.depth_key[0]), reinterpret_cast<uint32_t *>(ws + L.depth_key[1])};
-  uint32_t *dv[2] = {reinterpret_cast<uint32_t *>(ws + L.depth_val[0]), reinterpret_cast<uint32_t *>(ws + L.depth_val[1])};
+  // 1. Depth sort of the visible slots (31 key bits: depth > near > 0); the
+  // per-slot keys stay intact, the passes ping-pong between two buffers.
+  const uint32_t *dkey = reinterpret_cast<const uint32_t *>(ws + L.depth_key);
+  uint32_t *dk[2] = {reinterpret_cast<uint32_t *>(ws + L.dsort_key[0]), reinterpret_cast<uint32_t *>(ws + L.dsort_key[1])};
+  uint32_t *dv[2] = {reinterpret_cast<uint32_t *>(ws + L.dsort_val[0]), reinterpret_cast<uint32_t *>(ws + L.dsort_val[1])};
   uint32_t *dstate = reinterpret_cast<uint32_t *>(ws + L.depth_state);
   uint32_t *hist_d = reinterpret_cast<uint32_t *>(ws + L.hist_depth);
   if (L.depth_blocks > 0) {
     const int hb = (int)((L.vis_cap + kHistItems - 1) / kHistItems);
-    radix_hist_kernel<<<hb, kSortThreads, 0, st>>>(dk[0], ctr + kCtrVisible, L.vis_cap, L.depth_passes, hist_d,
+    radix_hist_kernel<<<hb, kSortThreads, 0, st>>>(dkey, ctr + kCtrVisible, L.vis_cap, L.depth_passes, hist_d,
                                                   dstate, L.depth_blocks, nullptr, 0);
     for (int p = 0; p < L.depth_passes; ++p) {
-      const int in = p & 1, out = in ^ 1;
+      const int out = p & 1, in = out ^ 1;
       uint32_t *state = dstate + (size_t)p * L.depth_blocks * kRadixBins;
       if (p == 0)
         radix_pass_kernel<true><<<L.depth_blocks, kSortThreads, 0, st>>>(
-            dk[in], nullptr, dk[out], dv[out], ctr + kCtrVisible, L.vis_cap, kRadixBits * p,
+            dkey, nullptr, dk[out], dv[out], ctr + kCtrVisible, L.vis_cap, kRadixBits * p,
             hist_d + p * kRadixBins, state, ctr + kCtrTicketDepth + p, status);
       else
         radix_pass_kernel<false><<<L.depth_blocks, kSortThreads, 0, st>>>(
@@ -276,7 +278,7 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
             hist_d + p * kRadixBins, state, ctr + kCtrTicketDepth + p, status);
     }
   }
-  const uint32_t *sorted = dv[L.depth_passes & 1];
+  const uint32_t *sorted = dv[(L.depth_passes - 1) & 1];
   // 2. Instances in depth order.
   uint32_t *ik[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_key[0]), reinterpret_cast<uint32_t *>(ws + L.inst_key[1])};
   uint32_t *iv[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_val[0]), reinterpret_cast<uint32_t *>(ws + L.inst_val[1])};

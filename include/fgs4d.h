@@ -196,6 +196,32 @@ int fgs4d_render_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, 
 int fgs4d_l1_loss(const float *img, const float *target, int64_t count, float *loss_out, float *dL_dimg,
                   void *stream);
 
+/* Largest key count fgs4d_sort_depth_static accepts. */
+#define FGS4D_STATIC_SORT_MAX (1 << 20)
+
+/* Depth sort that allocates nothing, for callers that cannot give the
+ * library a workspace: plug-ins whose host application owns every device
+ * allocation, and per-frame loops that must not call cudaMalloc (it can
+ * synchronise the device and fail under a fixed memory budget).  The paper
+ * has no counterpart; this is a packaging of the depth-sort step of
+ * fgs4d_bin_sort.
+ * Input: depth_keys, device uint32 [n] (FP32 bit patterns of positive depths;
+ * any uint32 keys sort correctly).  Output: sorted_slots, device uint32 [n],
+ * the indices 0..n-1 in (key, index) order -- the same permutation
+ * fgs4d_bin_sort writes to its sorted_slots region for the same keys.
+ * Scratch: one library-owned device array of about 18 MB (FGS4D_STATIC_SORT_MAX
+ * keys), present on every GPU that loads the library until the process exits.
+ * No device memory is allocated or freed.  The first call on a device looks
+ * up that array's address for the current device, so make that first call
+ * before capturing a stream into a graph.  Every call reuses the same array
+ * (its previous contents are reset as needed), so calls whose work overlaps
+ * on the GPU -- on different streams, or from different host threads --
+ * race and must be serialised by the caller.
+ * Errors: FGS4D_ERR_ARG for n < 0, n > FGS4D_STATIC_SORT_MAX or a null
+ * pointer with n > 0; FGS4D_ERR_CUDA if the lookup or a launch fails.  n = 0
+ * does nothing. */
+int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, uint32_t *sorted_slots, void *stream);
+
 /* Synchronises `stream`, then reads the workspace status word.  Returns
  * FGS4D_OK, or the first recorded device condition (FGS4D_ERR_CAPACITY,
  * FGS4D_ERR_TIMEOUT, FGS4D_ERR_INTERNAL).  counts_out (optional, 4 entries):

@@ -317,3 +317,91 @@ cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nv
 }
 
 }  // namespace fgs4d
+
+// ---------------------------------------------------------------------------
+// Depth sort that allocates nothing: fgs4d_sort_depth_static.
+//
+// Some callers cannot hand the library a workspace: plug-ins whose host
+// application owns every device allocation, and render loops that must not
+// call cudaMalloc between frames because it can synchronise the device or
+// fail under a fixed memory budget.  For them this entry point runs the same
+// radix passes as the depth sort inside fgs4d_bin_sort, with its scratch
+// (ping-pong buffers, histograms, look-back rows, tickets) in one file-scope
+// device array of fixed size.  The array exists once per GPU that loads the
+// library and lives until the process exits.
+namespace fgs4d {
+
+namespace {
+
+constexpr int kStaticSortBlocks = FGS4D_STATIC_SORT_MAX / kSortTile;
+constexpr int kMaxStaticDevices = 64;
+
+struct StaticSortScratch {
+  uint32_t keys[2][FGS4D_STATIC_SORT_MAX];
+  uint32_t vals[2][FGS4D_STATIC_SORT_MAX];
+  uint32_t state[kMaxPasses][kStaticSortBlocks][kRadixBins];
+  uint32_t hist[kMaxPasses][kRadixBins];
+  uint32_t ctl[64];  // [0] key count, [1] status bits, [8 + p] ticket of pass p
+};
+
+static __device__ __align__(256) StaticSortScratch g_static_sort;
+
+// Device address of g_static_sort on each device, looked up once per device
+// (with that device current) at the first call made on it.
+StaticSortScratch *g_static_addr[kMaxStaticDevices] = {};
+
+// Every call starts from zeroed histograms and tickets: the previous call's
+// contents stay in the array.
+__global__ void static_sort_init_kernel(StaticSortScratch *s, uint32_t n) {
+  for (int i = threadIdx.x; i < kMaxPasses * kRadixBins; i += blockDim.x) (&s->hist[0][0])[i] = 0u;
+  if (threadIdx.x < 64) s->ctl[threadIdx.x] = threadIdx.x == 0 ? n : 0u;
+}
+
+int static_scratch(StaticSortScratch **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FGS4D_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxStaticDevices) return FGS4D_ERR_UNSUPPORTED;
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_sort) != cudaSuccess || p == nullptr) return FGS4D_ERR_CUDA;
+    g_static_addr[dev] = static_cast<StaticSortScratch *>(p);
+  }
+  *out = g_static_addr[dev];
+  return FGS4D_OK;
+}
+
+}  // namespace
+
+}  // namespace fgs4d
+
+extern "C" int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, uint32_t *sorted_slots,
+                                       void *stream) {
+  using namespace fgs4d;
+  if (n < 0 || n > FGS4D_STATIC_SORT_MAX) return FGS4D_ERR_ARG;
+  if (n == 0) return FGS4D_OK;
+  if (!depth_keys || !sorted_slots) return FGS4D_ERR_ARG;
+  StaticSortScratch *s = nullptr;
+  const int rc = static_scratch(&s);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int blocks = (int)((n + kSortTile - 1) / kSortTile);
+  const int hist_blocks = (int)((n + kHistItems - 1) / kHistItems);
+  static_sort_init_kernel<<<1, 256, 0, st>>>(s, (uint32_t)n);
+  radix_hist_kernel<<<hist_blocks, kSortThreads, 0, st>>>(depth_keys, &s->ctl[0], FGS4D_STATIC_SORT_MAX,
+                                                          kMaxPasses, &s->hist[0][0], &s->state[0][0][0],
+                                                          kStaticSortBlocks, nullptr, 0);
+  for (int p = 0; p < kMaxPasses; ++p) {
+    const int out = p & 1, in = out ^ 1;
+    const uint32_t *kin = p == 0 ? depth_keys : s->keys[in];
+    uint32_t *vout = p == kMaxPasses - 1 ? sorted_slots : s->vals[out];
+    if (p == 0)
+      radix_pass_kernel<true><<<blocks, kSortThreads, 0, st>>>(kin, nullptr, s->keys[out], vout, &s->ctl[0],
+                                                               FGS4D_STATIC_SORT_MAX, kRadixBits * p, s->hist[p],
+                                                               &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1]);
+    else
+      radix_pass_kernel<false><<<blocks, kSortThreads, 0, st>>>(kin, s->vals[in], s->keys[out], vout, &s->ctl[0],
+                                                                FGS4D_STATIC_SORT_MAX, kRadixBits * p, s->hist[p],
+                                                                &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1]);
+  }
+  return cudaGetLastError() == cudaSuccess ? FGS4D_OK : FGS4D_ERR_CUDA;
+}

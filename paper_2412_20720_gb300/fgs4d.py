@@ -29,7 +29,9 @@ MAX_T_ORDER = 4
 TILE = 16
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
-            "fgs4d_render_fwd", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_l1_loss", "fgs4d_get_status", "fgs4d_status_string")
+            "fgs4d_render_fwd", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
+            "fgs4d_status_string")
+STATIC_SORT_MAX = 1 << 20
 
 
 class View(C.Structure):
@@ -97,6 +99,7 @@ def load():
     lib.fgs4d_render_bwd.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, vp, P(GaussiansGrad),
                                      vp]
     lib.fgs4d_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.fgs4d_sort_depth_static.argtypes = [vp, i64, vp, vp]
     lib.fgs4d_get_status.argtypes = [vp, C.c_size_t, vp, P(C.c_int64)]
     lib.fgs4d_status_string.argtypes = [C.c_int]
     lib.fgs4d_status_string.restype = C.c_char_p
@@ -202,6 +205,12 @@ def render_bwd(gaussians: Gaussians, views, nviews: int, settings: Settings, ws:
 
 def l1_loss(img: int, target: int, count: int, loss_out: int, dL_dimg: int, stream: int):
     _check(load().fgs4d_l1_loss(img, target, int(count), loss_out, dL_dimg, stream), "fgs4d_l1_loss")
+
+
+def sort_depth_static(depth_keys: int, n: int, sorted_slots: int, stream: int):
+    """Depth sort with the library's own device scratch (no allocation);
+    see fgs4d_sort_depth_static in include/fgs4d.h for who needs it."""
+    _check(load().fgs4d_sort_depth_static(depth_keys, int(n), sorted_slots, stream), "fgs4d_sort_depth_static")
 
 
 def get_status(ws: int, ws_bytes: int, stream: int):

@@ -1,0 +1,65 @@
+"""fgs4d_sort_depth_static: the depth sort for callers that cannot give the
+library a workspace (their host owns all device memory, or they may not call
+cudaMalloc inside a frame loop).  It must produce exactly the permutation the
+workspace-based fgs4d_bin_sort produces for the same depth keys, call after
+call, although every call reuses the same library-owned device scratch.
+
+Kept in a file of its own, collected after every other test."""
+import numpy as np
+import pytest
+
+from paper_2412_20720_gb300 import fgs4d
+from paper_2412_20720_gb300 import synthetic as sy
+
+pytestmark = pytest.mark.gpu
+
+
+def _depth_keys(rng, n):
+    depth = rng.uniform(0.25, 60.0, n).astype(np.float32)
+    depth[rng.integers(0, n, n // 8)] = depth[1]  # exact ties: order by index
+    return depth.view(np.uint32)
+
+
+def _bin_sort_order(keys_np):
+    """The existing entry point: records with empty tile rects written into a
+    workspace, then fgs4d_bin_sort; returns its sorted_slots region."""
+    import torch
+
+    from paper_2412_20720_gb300.render import RenderConfig, Renderer
+    n = keys_np.shape[0]
+    r = Renderer(n, [sy.tiny_view(64, 64)], RenderConfig(sh_degree=1, t_order=1, inst_capacity=1024))
+    meta = np.zeros((n, 4), dtype=np.int32)
+    meta[:, 0] = np.arange(n)
+    r.workspace_view(r.layout.counters, torch.int32, 64).zero_()
+    r.workspace_view(r.layout.counters, torch.int32, 1).fill_(n)
+    r.workspace_view(r.layout.rec_meta, torch.int32, 4 * n).copy_(torch.from_numpy(meta.reshape(-1)).cuda())
+    r.workspace_view(r.layout.depth_key, torch.int32, n).copy_(torch.from_numpy(keys_np.view(np.int32)).cuda())
+    fgs4d.bin_sort(n, r.views, r.nviews, r.settings, r.ws.data_ptr(), r.ws_bytes, r.stream())
+    r.check()
+    return r.workspace_view(r.layout.sorted_slots, torch.int32, n).clone()
+
+
+def test_static_depth_sort_matches_bin_sort_on_consecutive_calls():
+    import torch
+    rng = np.random.default_rng(20)
+    stream = torch.cuda.current_stream().cuda_stream
+    for n in (70_001, 2047):  # a second, smaller sort over the same scratch
+        keys = _depth_keys(rng, n)
+        expect = _bin_sort_order(keys)
+        keys_dev = torch.from_numpy(keys.view(np.int32)).cuda()
+        for _ in range(2):
+            out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+            fgs4d.sort_depth_static(keys_dev.data_ptr(), n, out.data_ptr(), stream)
+            torch.cuda.synchronize()
+            assert torch.equal(out, expect)
+        # The permutation is the stable order of the keys.
+        np.testing.assert_array_equal(out.cpu().numpy(), np.argsort(keys, kind="stable"))
+
+
+def test_static_depth_sort_rejects_sizes_beyond_its_scratch():
+    with pytest.raises(fgs4d.Fgs4dError) as e:
+        fgs4d.sort_depth_static(256, fgs4d.STATIC_SORT_MAX + 1, 256, None)
+    assert e.value.code == fgs4d.ERR_ARG
+    with pytest.raises(fgs4d.Fgs4dError):
+        fgs4d.sort_depth_static(256, -1, 256, None)
+    fgs4d.sort_depth_static(None, 0, None, None)  # empty input: nothing to do

@@ -177,7 +177,7 @@ def run_ours(args, rank, world, local):
 
     from paper_2412_20720_gb300 import fgs4d
     from paper_2412_20720_gb300 import synthetic as sy
-    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, l1_loss
+    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, autotune
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -196,6 +196,7 @@ def run_ours(args, rank, world, local):
     cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24)
     r = Renderer(scene.n, views[:1], cfg, device=dev)
     vv = [fgs4d.make_views([v]) for v in views]
+    tuned = autotune(r, params, view_sets=[vv[k] for k in sorted({0, nviews // 3, 2 * nviews // 3})])
     g = r.gaussians(params)
     ws, wsb, s = r.ws.data_ptr(), r.ws_bytes, r.settings
     stream = torch.cuda.current_stream(dev)
@@ -351,6 +352,7 @@ def run_ours(args, rank, world, local):
                        "l2": "inputs larger than L2 (193 MB of parameters vs 129 MB L2); no flush",
                        "parallelism": "views replicated per GPU" if world > 1 else "single GPU"},
             "gpu_launches": launches_per_frame * nviews * K,
+            "autotune": tuned,
             "stages_ms_per_frame": {"preprocess": stage_ms[0], "bin_sort": stage_ms[1], "render_fwd": stage_ms[2]},
             "work_per_frame": {"visible": float(np.mean(vis)), "instances": float(np.mean(inst)),
                                "alpha_evals": float(np.mean(evals)), "composited": float(np.mean(comps))},
@@ -377,7 +379,7 @@ def run_train(args, dev, scene, params, world, barrier):
 
     from paper_2412_20720_gb300 import fgs4d
     from paper_2412_20720_gb300 import synthetic as sy
-    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, l1_loss
+    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, autotune, l1_loss
 
     views = sy.train_views(4, W_IMG, H_IMG)
     cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 25)
@@ -389,6 +391,7 @@ def run_train(args, dev, scene, params, world, barrier):
     del rt, tparams
     leaf = {k: params[k].clone().requires_grad_(True) for k in PARAM_KEYS}
     r = Renderer(scene.n, views, cfg, device=dev)
+    tuned = autotune(r, {k: leaf[k].detach() for k in PARAM_KEYS}, backward=True)
     grads = {k: torch.zeros_like(leaf[k]) for k in PARAM_KEYS}
     opt = torch.optim.Adam([leaf[k] for k in PARAM_KEYS], lr=1e-4, fused=True)
     for k in PARAM_KEYS:
@@ -423,7 +426,7 @@ def run_train(args, dev, scene, params, world, barrier):
     return {"metric": "fwd+bwd iters/s", "value": 1000.0 / ms * world, "unit": "iters/s", "ms_per_iter": ms,
             "workload": "4 timestamps x 1 camera at 1352x1014 in one call, %d Gaussians, L1 loss, backward to all "
                         "parameters, fused Adam step" % scene.n,
-            "status": fgs4d.status_string(code), "loss": float(loss.item()),
+            "status": fgs4d.status_string(code), "loss": float(loss.item()), "autotune": tuned,
             "targets": "rendered by the CUDA path from a second seeded scene"}
 
 

@@ -84,6 +84,9 @@ typedef struct fgs4d_settings {
   float bg[3];           /* background colour composited behind the Gaussians */
   int64_t vis_capacity;  /* max visible (view, Gaussian) pairs; 0 = n * nviews */
   int64_t inst_capacity; /* max (tile, Gaussian) instances over all views, > 0 */
+  int32_t pixels_per_thread; /* compositor block shape: 0 (default 4), 2, 4 or 8 pixels
+                                of one tile column per thread; results are identical */
+  int32_t reserved;          /* must be 0 */
 } fgs4d_settings;
 
 /* Gaussian parameters (device pointers, layout in the header comment). */
@@ -118,6 +121,7 @@ typedef struct fgs4d_layout {
   size_t rec_geom;      /* float4 [vis_cap]: (u, v, A', B') with power2 = -(A' dx^2 + B' dx dy + C' dy^2) */
   size_t rec_color;     /* float4 [vis_cap]: (C', a, r, g) with a = sigmoid(logit) p(t) */
   size_t rec_blue;      /* float  [vis_cap]: b */
+  size_t rec_tau;       /* float  [vis_cap]: log2(255 a) + 4e-3; alpha >= 1/255 needs -power2 <= tau */
   size_t rec_meta;      /* int32x4 [vis_cap]: (gaussian, view, x0 | y0 << 16, x1 | y1 << 16) tile rect */
   size_t depth_key;     /* uint32 [vis_cap]: FP32 bits of the camera depth */
   size_t sorted_slots;  /* uint32 [vis_cap]: slots in (depth, slot) order, after fgs4d_bin_sort */

@@ -30,6 +30,10 @@ int check_settings(const fgs4d_settings *s) {
     if (!finite_f(s->bg[k])) return FGS4D_ERR_ARG;
   if (s->inst_capacity <= 0 || s->inst_capacity > kMaxCap) return FGS4D_ERR_ARG;
   if (s->vis_capacity < 0 || s->vis_capacity > kMaxCap) return FGS4D_ERR_ARG;
+  if (s->pixels_per_thread != 0 && s->pixels_per_thread != 2 && s->pixels_per_thread != 4 &&
+      s->pixels_per_thread != 8)
+    return FGS4D_ERR_UNSUPPORTED;
+  if (s->reserved != 0) return FGS4D_ERR_ARG;
   return FGS4D_OK;
 }
 
@@ -121,6 +125,7 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.rec_geom = take(vc * 16);
   L.rec_color = take(vc * 16);
   L.rec_blue = take(vc * 4);
+  L.rec_tau = take(vc * 4);
   L.rec_meta = take(vc * 16);
   L.depth_key = take(vc * 4);
   for (int k = 0; k < 2; ++k) {
@@ -170,6 +175,7 @@ int fgs4d_workspace_layout(const fgs4d_settings *settings, int64_t n, const fgs4
   o->rec_geom = L.rec_geom;
   o->rec_color = L.rec_color;
   o->rec_blue = L.rec_blue;
+  o->rec_tau = L.rec_tau;
   o->rec_meta = L.rec_meta;
   o->depth_key = L.depth_key;
   o->sorted_slots = L.dsort_val[(L.depth_passes - 1) & 1];

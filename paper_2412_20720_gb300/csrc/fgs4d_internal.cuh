@@ -85,7 +85,7 @@ struct Layout {
   size_t hist_tile;     // uint32 [kMaxPasses][256]
   size_t lb_emit;       // uint64 per emit block
   size_t control_end;
-  size_t rec_geom, rec_color, rec_blue, rec_meta;
+  size_t rec_geom, rec_color, rec_blue, rec_tau, rec_meta;
   size_t depth_key;                 // uint32 per slot (written by preprocess)
   size_t dsort_key[2], dsort_val[2];  // depth-sort ping-pong buffers
   size_t depth_state;   // uint32 [kMaxPasses][depth_blocks][256]
@@ -166,6 +166,49 @@ __device__ __forceinline__ uint64_t lookback_u64(uint64_t *state, int32_t bid, u
   return prefix;
 }
 
+// The same look-back run by a whole warp, reading 32 predecessor states per
+// step: lane i looks at block (window - i).  The walk stops at the nearest
+// inclusive prefix; a lane that is not ready yet makes the warp poll again
+// (bounded).  Every lane returns the exclusive prefix; lane 0 publishes.
+__device__ __forceinline__ uint64_t lookback_u64_warp(uint64_t *state, int32_t bid, uint64_t agg,
+                                                      uint32_t *status) {
+  constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kMask = (1ull << 62) - 1;
+  const int lane = threadIdx.x & 31;
+  if (bid == 0) {
+    if (lane == 0) st_release(&state[0], kInc | agg);
+    return 0;
+  }
+  if (lane == 0) st_release(&state[bid], kAgg | agg);
+  uint64_t prefix = 0;
+  int32_t window = bid - 1;
+  uint32_t polls = 0;
+  while (true) {
+    const int32_t j = window - lane;
+    const uint64_t s = j >= 0 ? ld_acquire(&state[j]) : kInc;  // before block 0: inclusive 0
+    const uint64_t f = s & ~kMask;
+    const uint32_t not_ready = __ballot_sync(0xffffffffu, f == 0);
+    const uint32_t inc = __ballot_sync(0xffffffffu, f == kInc);
+    const uint32_t stop = not_ready | inc;
+    const int first = stop ? __ffs(stop) - 1 : 32;  // nearest lane that is pending or inclusive
+    if (first < 32 && ((not_ready >> first) & 1u)) {
+      if (++polls > kSpinLimit) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    uint64_t v = lane <= first ? (s & kMask) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    prefix += v;
+    if (first < 32) break;  // reached an inclusive prefix
+    window -= 32;
+  }
+  if (lane == 0) st_release(&state[bid], kInc | (prefix + agg));
+  return prefix;
+}
+
 // Block-wide exclusive scan of one uint32 per thread (blockDim.x == 256).
 // `smem` needs 8 + 1 words.  Returns the exclusive prefix; *total = sum.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *smem, uint32_t *total) {
@@ -197,32 +240,44 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *s
 }
 
 // Shared alpha evaluation of the compositor, used verbatim by the forward
-// and backward kernels so both take identical skip/stop decisions.
-// power2 = -(A' dx^2 + B' dx dy + C' dy^2) is the exponent in base 2.
+// and backward kernels so both take identical skip/stop decisions.  The
+// exponent in base 2 is power2 = -q with q = A' dx^2 + B' dx dy + C' dy^2,
+// evaluated as A' dx^2 + dy (B' dx + C' dy) so that a thread covering a
+// column of pixels computes the dx terms once per entry.
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
-struct AlphaEval {
-  float dx, dy, power2, G, aG, alpha;
+struct ColumnTerms {
+  float dx, adx2, bdx;
 };
 
-__device__ __forceinline__ AlphaEval eval_alpha(float4 geom, float C2, float a, float pxc, float pyc) {
+__device__ __forceinline__ ColumnTerms column_terms(float4 geom, float pxc) {
+  ColumnTerms c;
+  c.dx = __fsub_rn(geom.x, pxc);
+  c.adx2 = __fmul_rn(geom.z, __fmul_rn(c.dx, c.dx));
+  c.bdx = __fmul_rn(geom.w, c.dx);
+  return c;
+}
+
+struct AlphaEval {
+  float dy, q, G, aG, alpha;
+};
+
+__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float C2, float a, float pyc) {
   AlphaEval e;
-  e.dx = __fsub_rn(geom.x, pxc);
-  e.dy = __fsub_rn(geom.y, pyc);
-  const float q = __fmaf_rn(geom.z, __fmul_rn(e.dx, e.dx),
-                            __fmaf_rn(C2, __fmul_rn(e.dy, e.dy), __fmul_rn(geom.w, __fmul_rn(e.dx, e.dy))));
-  e.power2 = -q;
-  e.G = ex2_approx(e.power2);
+  e.dy = __fsub_rn(v, pyc);
+  e.q = __fmaf_rn(e.dy, __fmaf_rn(C2, e.dy, c.bdx), c.adx2);
+  e.G = ex2_approx(-e.q);
   e.aG = __fmul_rn(a, e.G);
   e.alpha = fminf(0.99f, e.aG);
   return e;
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTauMargin = 4e-3f;  // log2 units (0.3% in alpha)
 constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;

@@ -35,7 +35,7 @@ struct PreArgs {
   uint32_t *counters;
   uint64_t *lb;
   float4 *rec_geom, *rec_color;
-  float *rec_blue;
+  float *rec_blue, *rec_tau;
   int4 *rec_meta;
   uint32_t *depth_key;
 };
@@ -342,10 +342,10 @@ __global__ void __launch_bounds__(kPreBlock) preprocess_kernel(PreArgs A, PreVie
                                                   A.k3, A.period_inv, A.near_plane, A.dilation, A.p_t_min, cam, h);
   uint32_t total;
   const uint32_t local = block_exclusive_scan(vis ? 1u : 0u, s_scan, &total);
-  if (threadIdx.x == 0) {
-    const uint64_t prefix = lookback_u64(A.lb, w, total, &A.counters[kCtrStatus]);
-    s_base = prefix;
-    if (w == A.nviews * A.blocks_per_view - 1) {
+  if (threadIdx.x < 32) {
+    const uint64_t prefix = lookback_u64_warp(A.lb, w, total, &A.counters[kCtrStatus]);
+    if (threadIdx.x == 0) s_base = prefix;
+    if (threadIdx.x == 0 && w == A.nviews * A.blocks_per_view - 1) {
       const uint64_t all = prefix + total;
       A.counters[kCtrNeedVisible] = (uint32_t)umin64(all, 0xffffffffull);
       A.counters[kCtrVisible] = (uint32_t)umin64(all, (uint64_t)A.vis_cap);
@@ -360,6 +360,9 @@ __global__ void __launch_bounds__(kPreBlock) preprocess_kernel(PreArgs A, PreVie
   A.rec_geom[slot] = make_float4(h.uv[0], h.uv[1], 0.5f * kLog2e * h.conA, kLog2e * h.conB);
   A.rec_color[slot] = make_float4(0.5f * kLog2e * h.conC, h.a, h.rgb[0], h.rgb[1]);
   A.rec_blue[slot] = h.rgb[2];
+  // alpha = a 2^power2 >= 1/255 needs -power2 <= log2(255 a); the margin keeps
+  // the per-tile test of the instance emission conservative under rounding.
+  A.rec_tau[slot] = log2f(255.0f * h.a) + kTauMargin;
   A.rec_meta[slot] = make_int4(i, view, h.rect[0] | (h.rect[1] << 16), h.rect[2] | (h.rect[3] << 16));
   A.depth_key[slot] = __float_as_uint(h.pc[2]);
 }
@@ -639,6 +642,7 @@ cudaError_t launch_pre_typed(const PreLaunch &p, const fgs4d_view *views, int32_
   A.rec_geom = reinterpret_cast<float4 *>(p.ws + Lo.rec_geom);
   A.rec_color = reinterpret_cast<float4 *>(p.ws + Lo.rec_color);
   A.rec_blue = reinterpret_cast<float *>(p.ws + Lo.rec_blue);
+  A.rec_tau = reinterpret_cast<float *>(p.ws + Lo.rec_tau);
   A.rec_meta = reinterpret_cast<int4 *>(p.ws + Lo.rec_meta);
   A.depth_key = reinterpret_cast<uint32_t *>(p.ws + Lo.depth_key);
   if (Lo.pre_blocks == 0) return cudaSuccess;

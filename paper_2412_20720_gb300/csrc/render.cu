@@ -1,18 +1,21 @@
 // Per-tile front-to-back compositing (Sec. 3.2, Eq. 6 of arXiv 2412.20720)
 // and its reverse-mode derivative, plus the photometric L1 loss (Sec. 3.3).
 //
-// Forward: one CTA per (view, 16x16 tile), one pixel per thread.  The tile's
-// depth-sorted list is staged through shared memory in batches of 256
-// records; a CTA stops loading once every pixel has hit the transmittance
-// cutoff (__syncthreads_count).  alpha = min(0.99, a 2^power2), skip when
-// power2 > 0 or alpha < 1/255, stop before the entry that would take T below
-// 1e-4 -- evaluated by eval_alpha, shared with the backward pass so that both
-// take bit-identical decisions.
+// Forward: one CTA per (view, 16x16 tile).  A thread owns a vertical strip of
+// kPPT pixels of one column, so the per-entry work that does not depend on the
+// row (shared-memory loads, dx, A' dx^2, B' dx) is done once for kPPT pixels.
+// The tile's depth-sorted list is staged through shared memory in batches of
+// 256 records; the CTA stops loading once every pixel has reached the
+// transmittance cutoff (__syncthreads_count).  alpha = min(0.99, a 2^power2),
+// skip when power2 > 0 or alpha < 1/255, stop before the entry that would take
+// T below 1e-4 -- evaluated by pixel_alpha, shared with the backward pass so
+// both take bit-identical decisions.
 //
 // Backward: the same tiles traversed back to front from each pixel's last
 // composited entry, recomputing T_i = T_{i+1} / (1 - alpha_i) from the final
-// transmittance.  Per-Gaussian sums are reduced across the warp by shuffles
-// before one vector atomic per warp.
+// transmittance.  A thread first sums its strip's contributions; the sums are
+// then reduced across the warp by shuffles and added with one vector atomic
+// per warp and entry.
 #include <algorithm>
 
 #include "fgs4d_internal.cuh"
@@ -20,6 +23,8 @@
 namespace fgs4d {
 
 namespace {
+
+constexpr int kBatch = 256;  // records staged per shared-memory batch
 
 struct RenderArgs {
   const uint2 *ranges;
@@ -46,6 +51,11 @@ struct RenderBwdArgs {
   float bg0, bg1, bg2;
 };
 
+// Pixels per thread of the compositor kernels (the autotuned block shape).
+inline int render_ppt(const fgs4d_settings *s) {
+  return (s->pixels_per_thread == 2 || s->pixels_per_thread == 8) ? s->pixels_per_thread : 4;
+}
+
 template <int MAXV>
 __device__ __forceinline__ int find_view(const RasterViews<MAXV> &rv, int32_t gt) {
   if (MAXV == 1) return 0;
@@ -58,64 +68,106 @@ __device__ __forceinline__ int find_view(const RasterViews<MAXV> &rv, int32_t gt
   return lo;
 }
 
+// Stages records [base, min(base + kBatch, end)) of the tile list into shared
+// memory; slots out of range (only possible after a recorded timeout) stage a
+// record that every pixel skips.
+template <int NT>
+__device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const float4 *rec_geom,
+                                            const float4 *rec_color, const float *rec_blue, uint32_t vis_cap,
+                                            uint32_t base, uint32_t end, float4 *s_geom, float4 *s_col,
+                                            float *s_blue, uint32_t *s_slot) {
+#pragma unroll
+  for (int i = 0; i < kBatch / NT; ++i) {
+    const int k = threadIdx.x + i * NT;
+    const uint32_t idx = base + k;
+    if (idx < end) {
+      const uint32_t s = inst_val[idx];
+      if (s_slot) s_slot[k] = s;
+      if (s < vis_cap) {
+        s_geom[k] = rec_geom[s];
+        s_col[k] = rec_color[s];
+        s_blue[k] = rec_blue[s];
+      } else {
+        s_geom[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_blue[k] = 0.f;
+      }
+    }
+  }
+}
+
 // kStats: also counts the pixel-entry alpha evaluations and the composited
 // entries (diagnostic variant used to state the algorithmic work).
-template <int MAXV, bool kStats>
-__global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
-                                                                 unsigned long long *stats) {
-  __shared__ float4 s_geom[kTilePixels];
-  __shared__ float4 s_col[kTilePixels];
-  __shared__ float s_blue[kTilePixels];
+// A pixel that has stopped is marked by T = 0 (a live pixel always has
+// T >= 1e-4), its final transmittance kept in Tend, so the inner loop needs no
+// per-pixel branch on a separate flag.
+template <int MAXV, int PPT, bool kStats>
+__global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
+                                                                       unsigned long long *stats) {
+  constexpr int NT = kTilePixels / PPT;
+  __shared__ float4 s_geom[kBatch];
+  __shared__ float4 s_col[kBatch];
+  __shared__ float s_blue[kBatch];
   const int32_t gt = blockIdx.x;
   const RasterView &V = rv.v[find_view<MAXV>(rv, gt)];
   const int32_t lt = gt - V.tile_base;
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
   const int32_t px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int32_t py = ty * kTile + (threadIdx.x / kTile);
-  const bool inside = px < V.width && py < V.height;
+  const int32_t py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
   const uint2 range = A.ranges[gt];
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-  float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0u, n_eval = 0u, n_comp = 0u;
-  bool done = !inside;
-  for (uint32_t base = range.x; base < range.y; base += kTilePixels) {
-    if (__syncthreads_count(done) == kTilePixels) break;
-    const uint32_t idx = base + threadIdx.x;
-    if (idx < range.y) {
-      const uint32_t s = A.inst_val[idx];
-      if (s < A.vis_cap) {
-        s_geom[threadIdx.x] = A.rec_geom[s];
-        s_col[threadIdx.x] = A.rec_color[s];
-        s_blue[threadIdx.x] = A.rec_blue[s];
-      } else {  // only after a recorded timeout: contributes nothing
-        s_geom[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s_col[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s_blue[threadIdx.x] = 0.f;
-      }
-    }
+  const float pxc = (float)px + 0.5f;
+  float T[PPT], Tend[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
+  uint32_t last[PPT];
+  bool live = false;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const bool in = px < V.width && py0 + k < V.height;
+    T[k] = in ? 1.0f : 0.0f;
+    Tend[k] = 1.0f;
+    C0[k] = C1[k] = C2[k] = 0.f;
+    last[k] = 0u;
+    pyc[k] = (float)(py0 + k) + 0.5f;
+    live = live || in;
+  }
+  uint32_t n_eval = 0u, n_comp = 0u;
+  for (uint32_t base = range.x; base < range.y; base += kBatch) {
+    if (__syncthreads_count(live) == 0) break;
+    stage_batch<NT>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, range.y, s_geom, s_col,
+                    s_blue, nullptr);
     __syncthreads();
-    const int nb = (int)min(range.y - base, (uint32_t)kTilePixels);
-    if (!done) {
-      for (int j = 0; j < nb; ++j) {
-        const float4 col = s_col[j];
-        const AlphaEval e = eval_alpha(s_geom[j], col.x, col.y, pxc, pyc);
-        if (kStats) ++n_eval;
-        if (e.power2 > 0.0f || e.alpha < kAlphaMin) continue;
-        const float Tn = __fmul_rn(T, __fsub_rn(1.0f, e.alpha));
-        if (Tn < kTMin) {
-          done = true;
-          break;
+    const int nb = (int)min(range.y - base, (uint32_t)kBatch);
+    for (int j = 0; j < nb && live; ++j) {
+      const float4 geom = s_geom[j];
+      const float4 col = s_col[j];
+      const ColumnTerms ct = column_terms(geom, pxc);
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, col.y, pyc[k]);
+        if (kStats) n_eval += T[k] > 0.0f;
+        if (T[k] > 0.0f && e.q >= 0.0f && e.alpha >= kAlphaMin) {
+          const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, e.alpha));
+          if (Tn < kTMin) {
+            Tend[k] = T[k];
+            T[k] = 0.0f;
+          } else {
+            const float w = e.alpha * T[k];
+            C0[k] += col.z * w;
+            C1[k] += col.w * w;
+            C2[k] += s_blue[j] * w;
+            T[k] = Tn;
+            last[k] = base + j - range.x + 1;
+            if (kStats) ++n_comp;
+          }
         }
-        const float w = e.alpha * T;
-        C0 += col.z * w;
-        C1 += col.w * w;
-        C2 += s_blue[j] * w;
-        T = Tn;
-        last = base + j - range.x + 1;
-        if (kStats) ++n_comp;
       }
+      live = false;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) live = live || T[k] > 0.0f;
     }
   }
+#pragma unroll
+  for (int k = 0; k < PPT; ++k)
+    if (T[k] > 0.0f) Tend[k] = T[k];
   if (kStats) {
     unsigned long long ev = n_eval, co = n_comp;
 #pragma unroll
@@ -128,16 +180,19 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(RenderArgs A, R
       atomicAdd(&stats[1], co);
     }
   }
-  if (!inside) return;
   const int64_t HW = (int64_t)V.width * V.height;
-  const int64_t p = (int64_t)py * V.width + px;
   float *img = A.out_rgb + V.pix_base * 3;
-  img[p] = C0 + T * A.bg0;
-  img[HW + p] = C1 + T * A.bg1;
-  img[2 * HW + p] = C2 + T * A.bg2;
-  A.pix_T[V.pix_base + p] = T;
-  A.pix_last[V.pix_base + p] = last;
-  if (A.out_T) A.out_T[V.pix_base + p] = T;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    if (!(px < V.width && py0 + k < V.height)) continue;
+    const int64_t p = (int64_t)(py0 + k) * V.width + px;
+    img[p] = C0[k] + Tend[k] * A.bg0;
+    img[HW + p] = C1[k] + Tend[k] * A.bg1;
+    img[2 * HW + p] = C2[k] + Tend[k] * A.bg2;
+    A.pix_T[V.pix_base + p] = Tend[k];
+    A.pix_last[V.pix_base + p] = last[k];
+    if (A.out_T) A.out_T[V.pix_base + p] = Tend[k];
+  }
 }
 
 __device__ __forceinline__ float warp_sum(float x) {
@@ -146,93 +201,97 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
-template <int MAXV>
-__global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(RenderBwdArgs A, RasterViews<MAXV> rv) {
-  __shared__ float4 s_geom[kTilePixels];
-  __shared__ float4 s_col[kTilePixels];
-  __shared__ float s_blue[kTilePixels];
-  __shared__ uint32_t s_slot[kTilePixels];
+template <int MAXV, int kPPT>
+__global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBwdArgs A, RasterViews<MAXV> rv) {
+  constexpr int kRenderThreads = kTilePixels / kPPT;
+  __shared__ float4 s_geom[kBatch];
+  __shared__ float4 s_col[kBatch];
+  __shared__ float s_blue[kBatch];
+  __shared__ uint32_t s_slot[kBatch];
   __shared__ uint32_t s_maxlast;
   const int32_t gt = blockIdx.x;
   const RasterView &V = rv.v[find_view<MAXV>(rv, gt)];
   const int32_t lt = gt - V.tile_base;
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
   const int32_t px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int32_t py = ty * kTile + (threadIdx.x / kTile);
-  const bool inside = px < V.width && py < V.height;
+  const int32_t py0 = ty * kTile + (threadIdx.x / kTile) * kPPT;
   const uint2 range = A.ranges[gt];
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const float pxc = (float)px + 0.5f;
   const int64_t HW = (int64_t)V.width * V.height;
-  const int64_t p = (int64_t)py * V.width + px;
-  float T = 1.0f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
-  uint32_t last = 0u;
-  if (inside) {
-    T = A.pix_T[V.pix_base + p];
-    last = A.pix_last[V.pix_base + p];
-    const float *g = A.dL_drgb + V.pix_base * 3;
-    dC0 = g[p];
-    dC1 = g[HW + p];
-    dC2 = g[2 * HW + p];
+  float T[kPPT], dC0[kPPT], dC1[kPPT], dC2[kPPT], r0[kPPT], r1[kPPT], r2[kPPT], pyc[kPPT];
+  uint32_t last[kPPT];
+  uint32_t my_max = 0u;
+  const float *g = A.dL_drgb + V.pix_base * 3;
+#pragma unroll
+  for (int k = 0; k < kPPT; ++k) {
+    pyc[k] = (float)(py0 + k) + 0.5f;
+    T[k] = 1.0f;
+    dC0[k] = dC1[k] = dC2[k] = 0.f;
+    last[k] = 0u;
+    if (px < V.width && py0 + k < V.height) {
+      const int64_t p = (int64_t)(py0 + k) * V.width + px;
+      T[k] = A.pix_T[V.pix_base + p];
+      last[k] = A.pix_last[V.pix_base + p];
+      dC0[k] = g[p];
+      dC1[k] = g[HW + p];
+      dC2[k] = g[2 * HW + p];
+    }
+    r0[k] = T[k] * A.bg0;  // colour composited behind the current entry
+    r1[k] = T[k] * A.bg1;
+    r2[k] = T[k] * A.bg2;
+    my_max = max(my_max, last[k]);
   }
   if (threadIdx.x == 0) s_maxlast = 0u;
   __syncthreads();
-  if (last) atomicMax(&s_maxlast, last);
+  if (my_max) atomicMax(&s_maxlast, my_max);
   __syncthreads();
   const uint32_t end = range.x + min(s_maxlast, range.y - range.x);
-  float r0 = T * A.bg0, r1 = T * A.bg1, r2 = T * A.bg2;  // colour composited behind entry i
   const int lane = threadIdx.x & 31;
-  const int nbatch = (int)((end - range.x + kTilePixels - 1) / kTilePixels);
+  const int nbatch = (int)((end - range.x + kBatch - 1) / kBatch);
   for (int bi = nbatch - 1; bi >= 0; --bi) {
-    const uint32_t base = range.x + (uint32_t)bi * kTilePixels;
+    const uint32_t base = range.x + (uint32_t)bi * kBatch;
     __syncthreads();
-    const uint32_t idx = base + threadIdx.x;
-    if (idx < end) {
-      const uint32_t s = A.inst_val[idx];
-      s_slot[threadIdx.x] = s;
-      if (s < A.vis_cap) {
-        s_geom[threadIdx.x] = A.rec_geom[s];
-        s_col[threadIdx.x] = A.rec_color[s];
-        s_blue[threadIdx.x] = A.rec_blue[s];
-      } else {  // only after a recorded timeout: contributes nothing
-        s_geom[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s_col[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s_blue[threadIdx.x] = 0.f;
-      }
-    }
+    stage_batch<kRenderThreads>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, end, s_geom,
+                                s_col, s_blue, s_slot);
     __syncthreads();
-    const int nb = (int)min(end - base, (uint32_t)kTilePixels);
+    const int nb = (int)min(end - base, (uint32_t)kBatch);
     for (int j = nb - 1; j >= 0; --j) {
       const uint32_t pos = base + j - range.x;  // entry index in the tile list
+      if (!__any_sync(0xffffffffu, pos < my_max)) continue;  // no pixel of this warp reached it
+      const float4 geom = s_geom[j];
+      const float4 col = s_col[j];
+      const float blue = s_blue[j];
+      const ColumnTerms ct = column_terms(geom, pxc);
+      const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
       float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, ga = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
       bool contrib = false;
-      if (pos < last) {
-        const float4 geom = s_geom[j];
-        const float4 col = s_col[j];
-        const AlphaEval e = eval_alpha(geom, col.x, col.y, pxc, pyc);
-        if (!(e.power2 > 0.0f || e.alpha < kAlphaMin)) {
-          contrib = true;
-          const float om = __fsub_rn(1.0f, e.alpha);
-          T = __fdiv_rn(T, om);  // transmittance in front of this entry
-          const float w = e.alpha * T;
-          const float blue = s_blue[j];
-          gr = dC0 * w;
-          gg = dC1 * w;
-          gb = dC2 * w;
-          const float io = 1.0f / om;
-          const float g_alpha = dC0 * (col.z * T - r0 * io) + dC1 * (col.w * T - r1 * io) + dC2 * (blue * T - r2 * io);
-          r0 += col.z * w;
-          r1 += col.w * w;
-          r2 += blue * w;
-          if (!(e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
-            ga = g_alpha * e.G;
-            const float gp = g_alpha * e.alpha;  // d alpha / d (natural-log power)
-            const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
-            gA = -0.5f * e.dx * e.dx * gp;
-            gB = -e.dx * e.dy * gp;
-            gC = -0.5f * e.dy * e.dy * gp;
-            gu = -(An * e.dx + Bn * e.dy) * gp;
-            gv = -(Cn * e.dy + Bn * e.dx) * gp;
-          }
+#pragma unroll
+      for (int k = 0; k < kPPT; ++k) {
+        if (pos >= last[k]) continue;
+        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, col.y, pyc[k]);
+        if (e.q < 0.0f || e.alpha < kAlphaMin) continue;
+        contrib = true;
+        const float om = __fsub_rn(1.0f, e.alpha);
+        T[k] = __fdiv_rn(T[k], om);  // transmittance in front of this entry
+        const float w = e.alpha * T[k];
+        gr += dC0[k] * w;
+        gg += dC1[k] * w;
+        gb += dC2[k] * w;
+        const float io = 1.0f / om;
+        const float g_alpha = dC0[k] * (col.z * T[k] - r0[k] * io) + dC1[k] * (col.w * T[k] - r1[k] * io) +
+                              dC2[k] * (blue * T[k] - r2[k] * io);
+        r0[k] += col.z * w;
+        r1[k] += col.w * w;
+        r2[k] += blue * w;
+        if (!(e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
+          ga += g_alpha * e.G;
+          const float gp = g_alpha * e.alpha;  // d alpha / d (natural-log power)
+          const float dx = ct.dx, dy = e.dy;
+          gA += -0.5f * dx * dx * gp;
+          gB += -dx * dy * gp;
+          gC += -0.5f * dy * dy * gp;
+          gu += -(An * dx + Bn * dy) * gp;
+          gv += -(Cn * dy + Bn * dx) * gp;
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
@@ -289,10 +348,20 @@ cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   A.bg1 = s->bg[1];
   A.bg2 = s->bg[2];
   if (L.total_tiles == 0) return cudaSuccess;
-  if (stats)
-    render_fwd_kernel<MAXV, true><<<(unsigned)L.total_tiles, kTilePixels, 0, st>>>(A, rv, stats);
-  else
-    render_fwd_kernel<MAXV, false><<<(unsigned)L.total_tiles, kTilePixels, 0, st>>>(A, rv, nullptr);
+  const unsigned grid = (unsigned)L.total_tiles;
+  switch (render_ppt(s)) {
+    case 2:
+      if (stats) render_fwd_kernel<MAXV, 2, true><<<grid, kTilePixels / 2, 0, st>>>(A, rv, stats);
+      else render_fwd_kernel<MAXV, 2, false><<<grid, kTilePixels / 2, 0, st>>>(A, rv, nullptr);
+      break;
+    case 8:
+      if (stats) render_fwd_kernel<MAXV, 8, true><<<grid, kTilePixels / 8, 0, st>>>(A, rv, stats);
+      else render_fwd_kernel<MAXV, 8, false><<<grid, kTilePixels / 8, 0, st>>>(A, rv, nullptr);
+      break;
+    default:
+      if (stats) render_fwd_kernel<MAXV, 4, true><<<grid, kTilePixels / 4, 0, st>>>(A, rv, stats);
+      else render_fwd_kernel<MAXV, 4, false><<<grid, kTilePixels / 4, 0, st>>>(A, rv, nullptr);
+  }
   return cudaGetLastError();
 }
 
@@ -318,7 +387,12 @@ cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   A.bg1 = s->bg[1];
   A.bg2 = s->bg[2];
   if (L.total_tiles == 0) return cudaSuccess;
-  render_bwd_kernel<MAXV><<<(unsigned)L.total_tiles, kTilePixels, 0, st>>>(A, rv);
+  const unsigned grid = (unsigned)L.total_tiles;
+  switch (render_ppt(s)) {
+    case 2: render_bwd_kernel<MAXV, 2><<<grid, kTilePixels / 2, 0, st>>>(A, rv); break;
+    case 8: render_bwd_kernel<MAXV, 8><<<grid, kTilePixels / 8, 0, st>>>(A, rv); break;
+    default: render_bwd_kernel<MAXV, 4><<<grid, kTilePixels / 4, 0, st>>>(A, rv);
+  }
   return cudaGetLastError();
 }
 

@@ -173,62 +173,181 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
   }
 }
 
-// One thread per depth-sorted visible slot: exclusive scan of tile counts
-// (decoupled look-back), then the slot's instances in row-major tile order.
+// Does the ellipse {d : A d_x^2 + B d_x d_y + C d_y^2 <= tau} around (u, v)
+// meet the box [x0, x1] x [y0, y1] of a tile's pixel centres?  Exact minimum
+// of the positive definite form over the box: 0 if the centre is inside, else
+// the least of the four edge minima (edge x = X: d_y = clamp(-B X / (2 C))).
+// Every operation is an explicitly rounded FP32 operation in a fixed order,
+// so the decision is reproducible bit for bit.  Entries of tiles it rejects
+// are skipped at every pixel of the tile (alpha < 1/255), so dropping them
+// leaves the image unchanged.
+// kx = -B / (2 C) and ky = -B / (2 A), the edge minimisers per unit offset,
+// depend on the Gaussian only and are computed once per slot (edge_slopes).
+__device__ __forceinline__ float2 edge_slopes(float A, float B, float C) {
+  return make_float2(__fdiv_rn(-B, __fmul_rn(2.0f, C)), __fdiv_rn(-B, __fmul_rn(2.0f, A)));
+}
+
+__device__ __forceinline__ bool ellipse_meets_box(float u, float v, float A, float B, float C, float kx, float ky,
+                                                  float tau, float x0, float x1, float y0, float y1) {
+  const float lx = __fsub_rn(x0, u), hx = __fsub_rn(x1, u);
+  const float ly = __fsub_rn(y0, v), hy = __fsub_rn(y1, v);
+  if (lx <= 0.0f && hx >= 0.0f && ly <= 0.0f && hy >= 0.0f) return tau >= 0.0f;
+  float m = INFINITY;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float X = k ? hx : lx;
+    const float Yv = fminf(fmaxf(__fmul_rn(kx, X), ly), hy);
+    const float qx = __fadd_rn(__fadd_rn(__fmul_rn(A, __fmul_rn(X, X)), __fmul_rn(B, __fmul_rn(X, Yv))),
+                               __fmul_rn(C, __fmul_rn(Yv, Yv)));
+    m = fminf(m, qx);
+    const float Y = k ? hy : ly;
+    const float Xv = fminf(fmaxf(__fmul_rn(ky, Y), lx), hx);
+    const float qy = __fadd_rn(__fadd_rn(__fmul_rn(A, __fmul_rn(Xv, Xv)), __fmul_rn(B, __fmul_rn(Xv, Y))),
+                               __fmul_rn(C, __fmul_rn(Y, Y)));
+    m = fminf(m, qy);
+  }
+  return m <= tau;
+}
+
+struct EmitArgs {
+  const uint32_t *sorted_slots;
+  const int4 *meta;
+  const float4 *geom, *color;
+  const float *tau;
+  uint32_t *counters;
+  int64_t vis_cap, inst_cap;
+  uint32_t *inst_key, *inst_val;
+  uint64_t *lb;
+};
+
+// Instance emission in depth order.  Each warp walks the flattened list of
+// (slot, rect tile) pairs of its 32 depth-sorted slots, 32 pairs at a time,
+// keeps a pair when the slot's 1/255 ellipse meets the tile, and writes the
+// kept pairs in (slot, row-major tile) order.  Pass 1 counts, the block's
+// offset comes from a decoupled look-back over tickets, pass 2 writes; the
+// work per lane stays balanced however large a Gaussian's rect is.
 template <int MAXV>
-__global__ void __launch_bounds__(kEmitBlock) emit_kernel(const uint32_t *__restrict__ sorted_slots,
-                                                          const int4 *__restrict__ meta, uint32_t *counters,
-                                                          int64_t vis_cap, int64_t inst_cap, uint32_t *inst_key,
-                                                          uint32_t *inst_val, uint64_t *lb, RasterViews<MAXV> rv) {
+__global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterViews<MAXV> rv) {
   __shared__ uint32_t s_ticket;
-  __shared__ uint32_t s_scan[9];
+  __shared__ uint32_t s_prefix[kEmitBlock];  // per warp: exclusive prefix of rect areas
+  __shared__ float4 s_geom[kEmitBlock];
+  __shared__ float2 s_ct[kEmitBlock];       // (C', tau)
+  __shared__ float2 s_k[kEmitBlock];        // (kx, ky)
+  __shared__ int4 s_meta[kEmitBlock];       // (slot, view, packed rect lo, packed rect hi)
+  __shared__ uint32_t s_wcount[kEmitBlock / 32];
   __shared__ uint64_t s_base;
-  const int64_t nvis = min64((int64_t)counters[kCtrVisible], vis_cap);
-  if (threadIdx.x == 0) s_ticket = atomicAdd(&counters[kCtrTicketEmit], 1u);
+  const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
+  if (threadIdx.x == 0) s_ticket = atomicAdd(&A.counters[kCtrTicketEmit], 1u);
   __syncthreads();
   const int64_t b = s_ticket;
   if (b == 0 && nvis == 0 && threadIdx.x == 0) {  // no slot: no instances
-    counters[kCtrInstances] = 0u;
-    counters[kCtrNeedInstances] = 0u;
+    A.counters[kCtrInstances] = 0u;
+    A.counters[kCtrNeedInstances] = 0u;
   }
   if (b * kEmitBlock >= nvis) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t j = b * kEmitBlock + threadIdx.x;
-  uint32_t s = 0u, cnt = 0u;
+  uint32_t area = 0u;
   int4 m = make_int4(0, 0, 0, 0);
   if (j < nvis) {
-    s = sorted_slots[j];
+    const uint32_t s = A.sorted_slots[j];
     if ((int64_t)s < nvis) {
-      m = meta[s];
-      const int x0 = m.z & 0xffff, y0 = (uint32_t)m.z >> 16, x1 = m.w & 0xffff, y1 = (uint32_t)m.w >> 16;
-      cnt = (uint32_t)(max(x1 - x0, 0) * max(y1 - y0, 0));
+      const int4 mm = A.meta[s];
+      const int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff, y1 = (uint32_t)mm.w >> 16;
+      area = (uint32_t)(max(x1 - x0, 0) * max(y1 - y0, 0));
+      m = make_int4((int)s, MAXV == 1 ? 0 : min(max(mm.y, 0), rv.nviews - 1), mm.z, mm.w);
+      const float4 gg = A.geom[s];
+      const float cc = A.color[s].x;
+      s_geom[threadIdx.x] = gg;
+      s_ct[threadIdx.x] = make_float2(cc, A.tau[s]);
+      s_k[threadIdx.x] = edge_slopes(gg.z, gg.w, cc);
     } else {
-      atomicOr(&counters[kCtrStatus], kStatusInternal);
+      atomicOr(&A.counters[kCtrStatus], kStatusInternal);
     }
   }
-  uint32_t total;
-  const uint32_t excl = block_exclusive_scan(cnt, s_scan, &total);
-  if (threadIdx.x == 0) {
-    const uint64_t prefix = lookback_u64(lb, (int32_t)b, total, &counters[kCtrStatus]);
-    s_base = prefix;
-    if ((b + 1) * kEmitBlock >= nvis) {  // last block with visible slots
+  s_meta[threadIdx.x] = m;
+  // Warp-inclusive scan of the areas.
+  uint32_t inc = area;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  s_prefix[threadIdx.x] = inc - area;
+  const uint32_t wtotal = __shfl_sync(0xffffffffu, inc, 31);
+  __syncwarp();
+  const int wbase = warp * 32;
+  // Flattened pair f of this warp -> keep decision and global tile id.
+  auto pair = [&](uint32_t f, uint32_t *tile, uint32_t *slot) -> bool {
+    int lo = 0, hi = 31;  // owner: last lane whose prefix <= f
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_prefix[wbase + mid] <= f) lo = mid;
+      else hi = mid - 1;
+    }
+    const int4 mm = s_meta[wbase + lo];
+    const int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff;
+    const uint32_t local = f - s_prefix[wbase + lo];
+    const int w = x1 - x0;
+    const int tx = x0 + (int)(local % (uint32_t)w), ty = y0 + (int)(local / (uint32_t)w);
+    const RasterView &V = rv.v[mm.y];
+    const float bx0 = (float)(tx * kTile) + 0.5f, by0 = (float)(ty * kTile) + 0.5f;
+    const float bx1 = (float)min(tx * kTile + kTile - 1, V.width - 1) + 0.5f;
+    const float by1 = (float)min(ty * kTile + kTile - 1, V.height - 1) + 0.5f;
+    const float4 g = s_geom[wbase + lo];
+    const float2 ct = s_ct[wbase + lo];
+    const float2 kk = s_k[wbase + lo];
+    *tile = (uint32_t)(V.tile_base + ty * V.gw + tx);
+    *slot = (uint32_t)mm.x;
+    return ellipse_meets_box(g.x, g.y, g.z, g.w, ct.x, kk.x, kk.y, ct.y, bx0, bx1, by0, by1);
+  };
+  // Pass 1: count the kept pairs of this warp.
+  uint32_t kept = 0u;
+  for (uint32_t f0 = 0; f0 < wtotal; f0 += 32) {
+    const uint32_t f = f0 + lane;
+    uint32_t t, sl;
+    const bool keep = f < wtotal && pair(f, &t, &sl);
+    kept += __popc(__ballot_sync(0xffffffffu, keep));
+  }
+  if (lane == 0) s_wcount[warp] = kept;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t c = lane < kEmitBlock / 32 ? s_wcount[lane] : 0u;
+    uint32_t ci = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, ci, o);
+      if (lane >= o) ci += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, ci, 31);
+    if (lane < kEmitBlock / 32) s_wcount[lane] = ci - c;
+    const uint64_t prefix = lookback_u64_warp(A.lb, (int32_t)b, total, &A.counters[kCtrStatus]);
+    if (lane == 0) s_base = prefix;
+    if (lane == 0 && (b + 1) * kEmitBlock >= nvis) {  // last block with visible slots
       const uint64_t all = prefix + total;
-      counters[kCtrNeedInstances] = (uint32_t)umin64(all, 0xffffffffull);
-      counters[kCtrInstances] = (uint32_t)umin64(all, (uint64_t)inst_cap);
-      if (all > (uint64_t)inst_cap) atomicOr(&counters[kCtrStatus], kStatusInstOverflow);
+      A.counters[kCtrNeedInstances] = (uint32_t)umin64(all, 0xffffffffull);
+      A.counters[kCtrInstances] = (uint32_t)umin64(all, (uint64_t)A.inst_cap);
+      if (all > (uint64_t)A.inst_cap) atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
     }
   }
   __syncthreads();
-  if (cnt == 0u) return;
-  const int view = MAXV == 1 ? 0 : min(max(m.y, 0), rv.nviews - 1);
-  const int32_t tb = rv.v[view].tile_base, gw = rv.v[view].gw;
-  const int x0 = m.z & 0xffff, y0 = (uint32_t)m.z >> 16, x1 = m.w & 0xffff, y1 = (uint32_t)m.w >> 16;
-  uint64_t pos = s_base + excl;
-  for (int ty = y0; ty < y1; ++ty)
-    for (int tx = x0; tx < x1; ++tx, ++pos) {
-      if (pos >= (uint64_t)inst_cap) return;
-      inst_key[pos] = (uint32_t)(tb + ty * gw + tx);
-      inst_val[pos] = s;
+  // Pass 2: write the kept pairs in order.
+  uint64_t pos = s_base + s_wcount[warp];
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t f0 = 0; f0 < wtotal; f0 += 32) {
+    const uint32_t f = f0 + lane;
+    uint32_t t = 0u, sl = 0u;
+    const bool keep = f < wtotal && pair(f, &t, &sl);
+    const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const uint64_t p = pos + __popc(mask & lt);
+      if (p < (uint64_t)A.inst_cap) {
+        A.inst_key[p] = t;
+        A.inst_val[p] = sl;
+      }
     }
+    pos += __popc(mask);
+  }
 }
 
 __global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ counters, int64_t cap,
@@ -282,10 +401,21 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   // 2. Instances in depth order.
   uint32_t *ik[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_key[0]), reinterpret_cast<uint32_t *>(ws + L.inst_key[1])};
   uint32_t *iv[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_val[0]), reinterpret_cast<uint32_t *>(ws + L.inst_val[1])};
-  if (L.emit_blocks > 0)
-    emit_kernel<MAXV><<<L.emit_blocks, kEmitBlock, 0, st>>>(sorted, reinterpret_cast<const int4 *>(ws + L.rec_meta),
-                                                            ctr, L.vis_cap, L.inst_cap, ik[0], iv[0],
-                                                            reinterpret_cast<uint64_t *>(ws + L.lb_emit), rv);
+  if (L.emit_blocks > 0) {
+    EmitArgs ea;
+    ea.sorted_slots = sorted;
+    ea.meta = reinterpret_cast<const int4 *>(ws + L.rec_meta);
+    ea.geom = reinterpret_cast<const float4 *>(ws + L.rec_geom);
+    ea.color = reinterpret_cast<const float4 *>(ws + L.rec_color);
+    ea.tau = reinterpret_cast<const float *>(ws + L.rec_tau);
+    ea.counters = ctr;
+    ea.vis_cap = L.vis_cap;
+    ea.inst_cap = L.inst_cap;
+    ea.inst_key = ik[0];
+    ea.inst_val = iv[0];
+    ea.lb = reinterpret_cast<uint64_t *>(ws + L.lb_emit);
+    emit_kernel<MAXV><<<L.emit_blocks, kEmitBlock, 0, st>>>(ea, rv);
+  }
   // 3. Stable sort of the instances by global tile id.
   uint32_t *tstate = reinterpret_cast<uint32_t *>(ws + L.tile_state);
   uint32_t *hist_t = reinterpret_cast<uint32_t *>(ws + L.hist_tile);

@@ -43,7 +43,8 @@ class View(C.Structure):
 class Settings(C.Structure):
     _fields_ = [("sh_degree", C.c_int32), ("t_order", C.c_int32), ("period", C.c_float), ("tile", C.c_int32),
                 ("near_plane", C.c_float), ("dilation", C.c_float), ("p_t_min", C.c_float), ("bg", C.c_float * 3),
-                ("vis_capacity", C.c_int64), ("inst_capacity", C.c_int64)]
+                ("vis_capacity", C.c_int64), ("inst_capacity", C.c_int64), ("pixels_per_thread", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Gaussians(C.Structure):
@@ -57,7 +58,8 @@ class GaussiansGrad(C.Structure):
 
 
 class Layout(C.Structure):
-    _fields_ = [(k, C.c_size_t) for k in ("bytes", "counters", "rec_geom", "rec_color", "rec_blue", "rec_meta",
+    _fields_ = [(k, C.c_size_t) for k in ("bytes", "counters", "rec_geom", "rec_color", "rec_blue", "rec_tau",
+                                          "rec_meta",
                                           "depth_key", "sorted_slots", "inst_tile", "inst_slot", "tile_ranges",
                                           "pix_T", "pix_last", "slot_grad")] + \
                [(k, C.c_int64) for k in ("vis_capacity", "inst_capacity", "total_tiles", "total_pixels")]
@@ -142,13 +144,14 @@ def make_views(views) -> tuple:
 
 
 def make_settings(sh_degree=3, t_order=2, period=1.0, near_plane=0.2, dilation=0.3, p_t_min=0.05,
-                  bg=(0.0, 0.0, 0.0), vis_capacity=0, inst_capacity=1 << 22) -> Settings:
+                  bg=(0.0, 0.0, 0.0), vis_capacity=0, inst_capacity=1 << 22, pixels_per_thread=0) -> Settings:
     s = Settings()
     s.sh_degree, s.t_order, s.period, s.tile = int(sh_degree), int(t_order), float(period), TILE
     s.near_plane, s.dilation, s.p_t_min = float(near_plane), float(dilation), float(p_t_min)
     for k in range(3):
         s.bg[k] = float(bg[k])
     s.vis_capacity, s.inst_capacity = int(vis_capacity), int(inst_capacity)
+    s.pixels_per_thread, s.reserved = int(pixels_per_thread), 0
     return s
 
 

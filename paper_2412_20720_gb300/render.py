@@ -27,10 +27,12 @@ class RenderConfig:
     bg: tuple = (0.0, 0.0, 0.0)
     vis_capacity: int = 0
     inst_capacity: int = 1 << 22
+    pixels_per_thread: int = 0  # compositor block shape (0 = library default); see autotune()
 
     def settings(self) -> fgs4d.Settings:
         return fgs4d.make_settings(self.sh_degree, self.t_order, self.period, self.near_plane, self.dilation,
-                                   self.p_t_min, self.bg, self.vis_capacity, self.inst_capacity)
+                                   self.p_t_min, self.bg, self.vis_capacity, self.inst_capacity,
+                                   self.pixels_per_thread)
 
 
 def _ptr(t: torch.Tensor) -> int:
@@ -123,6 +125,69 @@ class Renderer:
         """A typed view of a documented workspace region (see fgs4d_layout)."""
         nbytes = count * torch.empty(0, dtype=dtype).element_size()
         return self.ws[offset:offset + nbytes].view(dtype)
+
+
+def autotune(renderer: Renderer, params: dict, view_sets=None, candidates=(2, 4, 8), reps: int = 3,
+             backward: bool = False, cache_path: str | None = None) -> dict:
+    """Picks the compositor block shape (pixels per thread) that renders the
+    caller's own workload fastest and sets it on ``renderer``.
+
+    Each candidate is timed with CUDA events on the current stream over
+    ``reps`` calls of fgs4d_render_fwd (and fgs4d_render_bwd if ``backward``)
+    for every view set in ``view_sets`` (default: the renderer's views), after
+    one preprocess + bin_sort of that set.  Results are identical for every
+    candidate; only the time differs.  With ``cache_path``, the choice is
+    stored in a JSON file keyed by (GPU, resolutions, views, N rounded to a
+    power of two) and reused.  Returns {"pixels_per_thread": p, "ms": {...}}."""
+    import json
+    import os
+
+    dev_name = torch.cuda.get_device_name(renderer.device)
+    bucket = 1 << max(0, int(renderer.n - 1).bit_length())
+    res = "+".join("%dx%d" % (w, h) for h, w in sorted(set(renderer.sizes)))
+    key = "%s|%s|v%d|n%d|%s" % (dev_name, res, renderer.nviews, bucket, "fb" if backward else "f")
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+        if key in cache:
+            renderer.settings.pixels_per_thread = int(cache[key]["pixels_per_thread"])
+            return cache[key]
+    view_sets = view_sets or [(renderer.views, renderer.nviews)]
+    g = renderer.gaussians(params)
+    st = renderer.stream()
+    ws, wsb = renderer.ws.data_ptr(), renderer.ws_bytes
+    out = torch.empty(3 * renderer.total_pixels, dtype=torch.float32, device=renderer.device)
+    dL = torch.ones_like(out) if backward else None
+    grads = {k: torch.zeros_like(params[k]) for k in PARAM_KEYS} if backward else None
+    stream = torch.cuda.current_stream(renderer.device)
+    ms = {}
+    for p in candidates:
+        renderer.settings.pixels_per_thread = int(p)
+        total = 0.0
+        for views, nv in view_sets:
+            fgs4d.preprocess(g, views, nv, renderer.settings, ws, wsb, st)
+            fgs4d.bin_sort(renderer.n, views, nv, renderer.settings, ws, wsb, st)
+            fgs4d.render_fwd(renderer.n, views, nv, renderer.settings, ws, wsb, out.data_ptr(), None, st)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fgs4d.render_fwd(renderer.n, views, nv, renderer.settings, ws, wsb, out.data_ptr(), None, st)
+                if backward:
+                    fgs4d.render_bwd(g, views, nv, renderer.settings, ws, wsb, dL.data_ptr(),
+                                     fgs4d.make_grads({k: grads[k].data_ptr() for k in PARAM_KEYS}), st)
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b) / reps
+        ms[int(p)] = total
+    best = min(ms, key=ms.get)
+    renderer.settings.pixels_per_thread = best
+    result = {"pixels_per_thread": best, "ms": ms}
+    if cache_path:
+        cache[key] = result
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return result
 
 
 class Render4DGS(torch.autograd.Function):

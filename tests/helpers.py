@@ -74,6 +74,7 @@ class GpuRun:
         self.geom = r.workspace_view(r.layout.rec_geom, torch.float32, 4 * nv).cpu().numpy().reshape(nv, 4)
         self.color = r.workspace_view(r.layout.rec_color, torch.float32, 4 * nv).cpu().numpy().reshape(nv, 4)
         self.blue = r.workspace_view(r.layout.rec_blue, torch.float32, nv).cpu().numpy()
+        self.tau = r.workspace_view(r.layout.rec_tau, torch.float32, nv).cpu().numpy()
         self.meta = r.workspace_view(r.layout.rec_meta, torch.int32, 4 * nv).cpu().numpy().reshape(nv, 4)
         self.depth_bits = r.workspace_view(r.layout.depth_key, torch.int32, nv).cpu().numpy().view(np.uint32)
 
@@ -108,7 +109,7 @@ def records_from_gpu(run: GpuRun):
                     axis=1)
     rgb = np.stack([c[:, 2], c[:, 3], run.blue.astype(np.float64)], axis=1)
     return {"index": run.meta[:, 0], "view": run.meta[:, 1], "uv": g[:, :2], "conic": conic, "a": c[:, 1],
-            "rgb": rgb, "rect": rect, "depth_bits": run.depth_bits}
+            "rgb": rgb, "rect": rect, "depth_bits": run.depth_bits, "tau": run.tau.astype(np.float64)}
 
 
 def compare_group(name, gpu, ref, rtol, floor_frac):

@@ -57,6 +57,9 @@ def test_workspace_size_and_layout_are_consistent():
     ("inst_capacity", 0, fgs4d.ERR_ARG),
     ("inst_capacity", 1 << 31, fgs4d.ERR_ARG),
     ("vis_capacity", -1, fgs4d.ERR_ARG),
+    ("pixels_per_thread", 3, fgs4d.ERR_UNSUPPORTED),
+    ("pixels_per_thread", 16, fgs4d.ERR_UNSUPPORTED),
+    ("reserved", 1, fgs4d.ERR_ARG),
 ])
 def test_bad_settings_are_rejected(field, value, code):
     s = fgs4d.make_settings()

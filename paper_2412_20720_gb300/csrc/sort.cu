@@ -220,21 +220,23 @@ struct EmitArgs {
   uint64_t *lb;
 };
 
-// Instance emission in depth order.  Each warp walks the flattened list of
-// (slot, rect tile) pairs of its 32 depth-sorted slots, 32 pairs at a time,
-// keeps a pair when the slot's 1/255 ellipse meets the tile, and writes the
-// kept pairs in (slot, row-major tile) order.  Pass 1 counts, the block's
-// offset comes from a decoupled look-back over tickets, pass 2 writes; the
-// work per lane stays balanced however large a Gaussian's rect is.
+// Instance emission in depth order.  The block walks the flattened list of
+// (slot, rect tile) pairs of its 256 depth-sorted slots, 256 pairs at a
+// time, keeps a pair when the slot's 1/255 ellipse meets the tile, and writes
+// the kept pairs in (slot, row-major tile) order.  Pass 1 counts, the block's
+// offset comes from a decoupled look-back over tickets, pass 2 writes.  All
+// 256 threads share the tiles of every slot, so one large Gaussian does not
+// hold up the rest of its block.
 template <int MAXV>
 __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterViews<MAXV> rv) {
   __shared__ uint32_t s_ticket;
-  __shared__ uint32_t s_prefix[kEmitBlock];  // per warp: exclusive prefix of rect areas
+  __shared__ uint32_t s_prefix[kEmitBlock];  // exclusive prefix of the slots' rect areas
   __shared__ float4 s_geom[kEmitBlock];
-  __shared__ float2 s_ct[kEmitBlock];       // (C', tau)
-  __shared__ float2 s_k[kEmitBlock];        // (kx, ky)
-  __shared__ int4 s_meta[kEmitBlock];       // (slot, view, packed rect lo, packed rect hi)
-  __shared__ uint32_t s_wcount[kEmitBlock / 32];
+  __shared__ float2 s_ct[kEmitBlock];        // (C', tau)
+  __shared__ float2 s_k[kEmitBlock];         // (kx, ky)
+  __shared__ int4 s_meta[kEmitBlock];        // (slot, view, packed rect lo, packed rect hi)
+  __shared__ uint32_t s_scan[9];
+  __shared__ uint32_t s_w[2][kEmitBlock / 32];
   __shared__ uint64_t s_base;
   const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
   if (threadIdx.x == 0) s_ticket = atomicAdd(&A.counters[kCtrTicketEmit], 1u);
@@ -266,87 +268,78 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
     }
   }
   s_meta[threadIdx.x] = m;
-  // Warp-inclusive scan of the areas.
-  uint32_t inc = area;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  s_prefix[threadIdx.x] = inc - area;
-  const uint32_t wtotal = __shfl_sync(0xffffffffu, inc, 31);
-  __syncwarp();
-  const int wbase = warp * 32;
-  // Flattened pair f of this warp -> keep decision and global tile id.
+  uint32_t btotal;
+  s_prefix[threadIdx.x] = block_exclusive_scan(area, s_scan, &btotal);  // ends with a barrier
+  // Flattened pair f of this block -> keep decision, global tile id and slot.
   auto pair = [&](uint32_t f, uint32_t *tile, uint32_t *slot) -> bool {
-    int lo = 0, hi = 31;  // owner: last lane whose prefix <= f
+    int lo = 0, hi = kEmitBlock - 1;  // owner: last slot whose prefix <= f
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (s_prefix[wbase + mid] <= f) lo = mid;
+      if (s_prefix[mid] <= f) lo = mid;
       else hi = mid - 1;
     }
-    const int4 mm = s_meta[wbase + lo];
+    const int4 mm = s_meta[lo];
     const int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff;
-    const uint32_t local = f - s_prefix[wbase + lo];
+    const uint32_t local = f - s_prefix[lo];
     const int w = x1 - x0;
     const int tx = x0 + (int)(local % (uint32_t)w), ty = y0 + (int)(local / (uint32_t)w);
     const RasterView &V = rv.v[mm.y];
     const float bx0 = (float)(tx * kTile) + 0.5f, by0 = (float)(ty * kTile) + 0.5f;
     const float bx1 = (float)min(tx * kTile + kTile - 1, V.width - 1) + 0.5f;
     const float by1 = (float)min(ty * kTile + kTile - 1, V.height - 1) + 0.5f;
-    const float4 g = s_geom[wbase + lo];
-    const float2 ct = s_ct[wbase + lo];
-    const float2 kk = s_k[wbase + lo];
+    const float4 g = s_geom[lo];
+    const float2 ct = s_ct[lo];
+    const float2 kk = s_k[lo];
     *tile = (uint32_t)(V.tile_base + ty * V.gw + tx);
     *slot = (uint32_t)mm.x;
     return ellipse_meets_box(g.x, g.y, g.z, g.w, ct.x, kk.x, kk.y, ct.y, bx0, bx1, by0, by1);
   };
-  // Pass 1: count the kept pairs of this warp.
+  // Pass 1: count the kept pairs of this block.
   uint32_t kept = 0u;
-  for (uint32_t f0 = 0; f0 < wtotal; f0 += 32) {
-    const uint32_t f = f0 + lane;
+  for (uint32_t f0 = 0; f0 < btotal; f0 += kEmitBlock) {
+    const uint32_t f = f0 + threadIdx.x;
     uint32_t t, sl;
-    const bool keep = f < wtotal && pair(f, &t, &sl);
-    kept += __popc(__ballot_sync(0xffffffffu, keep));
+    const bool keep = f < btotal && pair(f, &t, &sl);
+    kept += (uint32_t)__syncthreads_count(keep);
   }
-  if (lane == 0) s_wcount[warp] = kept;
-  __syncthreads();
   if (warp == 0) {
-    const uint32_t c = lane < kEmitBlock / 32 ? s_wcount[lane] : 0u;
-    uint32_t ci = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, ci, o);
-      if (lane >= o) ci += y;
-    }
-    const uint32_t total = __shfl_sync(0xffffffffu, ci, 31);
-    if (lane < kEmitBlock / 32) s_wcount[lane] = ci - c;
-    const uint64_t prefix = lookback_u64_warp(A.lb, (int32_t)b, total, &A.counters[kCtrStatus]);
+    const uint64_t prefix = lookback_u64_warp(A.lb, (int32_t)b, kept, &A.counters[kCtrStatus]);
     if (lane == 0) s_base = prefix;
     if (lane == 0 && (b + 1) * kEmitBlock >= nvis) {  // last block with visible slots
-      const uint64_t all = prefix + total;
+      const uint64_t all = prefix + kept;
       A.counters[kCtrNeedInstances] = (uint32_t)umin64(all, 0xffffffffull);
       A.counters[kCtrInstances] = (uint32_t)umin64(all, (uint64_t)A.inst_cap);
       if (all > (uint64_t)A.inst_cap) atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
     }
   }
   __syncthreads();
-  // Pass 2: write the kept pairs in order.
-  uint64_t pos = s_base + s_wcount[warp];
+  // Pass 2: write the kept pairs in order (one barrier per chunk; the warp
+  // counts alternate between two buffers).
+  uint64_t pos = s_base;
   const uint32_t lt = (1u << lane) - 1u;
-  for (uint32_t f0 = 0; f0 < wtotal; f0 += 32) {
-    const uint32_t f = f0 + lane;
+  int buf = 0;
+  for (uint32_t f0 = 0; f0 < btotal; f0 += kEmitBlock, buf ^= 1) {
+    const uint32_t f = f0 + threadIdx.x;
     uint32_t t = 0u, sl = 0u;
-    const bool keep = f < wtotal && pair(f, &t, &sl);
+    const bool keep = f < btotal && pair(f, &t, &sl);
     const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_w[buf][warp] = __popc(mask);
+    __syncthreads();
+    uint32_t before = 0u, chunk = 0u;
+#pragma unroll
+    for (int w = 0; w < kEmitBlock / 32; ++w) {
+      const uint32_t c = s_w[buf][w];
+      before += w < warp ? c : 0u;
+      chunk += c;
+    }
     if (keep) {
-      const uint64_t p = pos + __popc(mask & lt);
+      const uint64_t p = pos + before + __popc(mask & lt);
       if (p < (uint64_t)A.inst_cap) {
         A.inst_key[p] = t;
         A.inst_val[p] = sl;
       }
     }
-    pos += __popc(mask);
+    pos += chunk;
   }
 }
 

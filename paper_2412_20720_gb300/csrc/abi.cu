@@ -4,6 +4,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "fgs4d_internal.cuh"
 
 namespace fgs4d {
@@ -106,6 +108,9 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   if (pb > INT32_MAX) return FGS4D_ERR_ARG;
   L.pre_blocks = (int32_t)pb;
   L.emit_blocks = (int32_t)((L.vis_cap + kEmitBlock - 1) / kEmitBlock);
+  L.pair_cap = std::min<int64_t>(8 * L.inst_cap, (int64_t)INT32_MAX);
+  L.chunk_cap = (int32_t)((L.pair_cap + kEmitChunk - 1) / kEmitChunk);
+  L.emit_grid = std::max(1, std::min(L.chunk_cap, 152 * 8));
   L.depth_blocks = (int32_t)((L.vis_cap + kSortTile - 1) / kSortTile);
   L.tile_blocks = (int32_t)((L.inst_cap + kSortTile - 1) / kSortTile);
 
@@ -121,6 +126,9 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.hist_tile = take(kMaxPasses * kRadixBins * sizeof(uint32_t));
   L.lb_emit = take((size_t)L.emit_blocks * sizeof(uint64_t));
   L.control_end = off;
+  L.lb_chunk = take((size_t)L.chunk_cap * sizeof(uint64_t));
+  L.pair_prefix = take(((size_t)L.vis_cap + 1) * sizeof(uint32_t));
+  L.emit_rec = take((size_t)L.vis_cap * 48);
   const size_t vc = (size_t)L.vis_cap, ic = (size_t)L.inst_cap;
   L.rec_geom = take(vc * 16);
   L.rec_color = take(vc * 16);

@@ -12,7 +12,8 @@ namespace fgs4d {
 constexpr int kTile = 16;           // tile edge in pixels
 constexpr int kTilePixels = kTile * kTile;
 constexpr int kPreBlock = 256;      // threads per preprocess block
-constexpr int kEmitBlock = 256;     // threads per emit block (one visible slot each)
+constexpr int kEmitBlock = 256;     // threads per pair-scan / emission block
+constexpr int kEmitChunk = 2048;    // (slot, rect tile) pairs per emission chunk
 constexpr int kSortThreads = 256;   // threads per radix block
 constexpr int kSortItems = 8;       // keys per thread per radix block
 constexpr int kSortTile = kSortThreads * kSortItems;
@@ -44,6 +45,8 @@ enum Counter : int {
   kCtrTicketEmit = 8,
   kCtrTicketDepth = 10,  // kMaxPasses entries
   kCtrTicketTile = 14,   // kMaxPasses entries
+  kCtrTicketChunk = 18,  // emission chunks
+  kCtrPairs = 19,        // (slot, rect tile) pairs of all visible slots
   kCtrCount = 64
 };
 constexpr size_t kSortControlStart = 32;
@@ -83,7 +86,10 @@ struct Layout {
   size_t lb_pre;        // uint64 per preprocess block
   size_t hist_depth;    // uint32 [kMaxPasses][256]
   size_t hist_tile;     // uint32 [kMaxPasses][256]
-  size_t lb_emit;       // uint64 per emit block
+  size_t lb_emit;       // uint64 per pair-scan block
+  size_t lb_chunk;      // uint64 per emission chunk (cleared by the pair scan)
+  size_t pair_prefix;   // uint32 [vis_cap + 1]: exclusive prefix of rect areas in depth order
+  size_t emit_rec;      // 3 x 16 B [vis_cap]: emission record per depth-sorted position
   size_t control_end;
   size_t rec_geom, rec_color, rec_blue, rec_tau, rec_meta;
   size_t depth_key;                 // uint32 per slot (written by preprocess)
@@ -101,7 +107,10 @@ struct Layout {
   int64_t vis_cap, inst_cap;
   int64_t total_tiles, total_pixels;
   int32_t pre_blocks_per_view, pre_blocks;
-  int32_t emit_blocks;
+  int32_t emit_blocks;    // pair-scan blocks (one visible slot per thread)
+  int64_t pair_cap;       // max (slot, rect tile) pairs: 8 x inst_cap, at most 2^31 - 1
+  int32_t chunk_cap;      // emission chunks of kEmitChunk pairs
+  int32_t emit_grid;      // persistent emission blocks
   int32_t depth_blocks, tile_blocks;
   int32_t depth_passes, tile_passes;
   int32_t tile_bits;

@@ -215,131 +215,209 @@ struct EmitArgs {
   const float4 *geom, *color;
   const float *tau;
   uint32_t *counters;
-  int64_t vis_cap, inst_cap;
+  int64_t vis_cap, inst_cap, pair_cap;
+  int32_t chunk_cap;
+  uint32_t *pair_prefix;
+  int4 *emit_rec;  // 3 per depth-sorted position
   uint32_t *inst_key, *inst_val;
-  uint64_t *lb;
+  uint64_t *lb_scan, *lb_chunk;
 };
 
-// Instance emission in depth order.  The block walks the flattened list of
-// (slot, rect tile) pairs of its 256 depth-sorted slots, 256 pairs at a
-// time, keeps a pair when the slot's 1/255 ellipse meets the tile, and writes
-// the kept pairs in (slot, row-major tile) order.  Pass 1 counts, the block's
-// offset comes from a decoupled look-back over tickets, pass 2 writes.  All
-// 256 threads share the tiles of every slot, so one large Gaussian does not
-// hold up the rest of its block.
+// Pair scan, one thread per depth-sorted visible slot: the exclusive prefix
+// of the slots' rect areas in depth order (decoupled look-back), plus a
+// compact emission record per position: (u, v, A', B'), (C', kx, ky, tau),
+// (slot, view, packed rect lo, packed rect hi).  Also clears the look-back
+// states of the emission chunks.
 template <int MAXV>
-__global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterViews<MAXV> rv) {
+__global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, RasterViews<MAXV> rv) {
   __shared__ uint32_t s_ticket;
-  __shared__ uint32_t s_prefix[kEmitBlock];  // exclusive prefix of the slots' rect areas
-  __shared__ float4 s_geom[kEmitBlock];
-  __shared__ float2 s_ct[kEmitBlock];        // (C', tau)
-  __shared__ float2 s_k[kEmitBlock];         // (kx, ky)
-  __shared__ int4 s_meta[kEmitBlock];        // (slot, view, packed rect lo, packed rect hi)
   __shared__ uint32_t s_scan[9];
-  __shared__ uint32_t s_w[2][kEmitBlock / 32];
-  __shared__ uint64_t s_base;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.chunk_cap;
+       c += (int64_t)gridDim.x * blockDim.x)
+    A.lb_chunk[c] = 0ull;
   const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
   if (threadIdx.x == 0) s_ticket = atomicAdd(&A.counters[kCtrTicketEmit], 1u);
   __syncthreads();
   const int64_t b = s_ticket;
-  if (b == 0 && nvis == 0 && threadIdx.x == 0) {  // no slot: no instances
+  if (b == 0 && nvis == 0 && threadIdx.x == 0) {  // no slot: no pairs, no instances
+    A.counters[kCtrPairs] = 0u;
     A.counters[kCtrInstances] = 0u;
     A.counters[kCtrNeedInstances] = 0u;
   }
   if (b * kEmitBlock >= nvis) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t j = b * kEmitBlock + threadIdx.x;
   uint32_t area = 0u;
-  int4 m = make_int4(0, 0, 0, 0);
   if (j < nvis) {
     const uint32_t s = A.sorted_slots[j];
+    int4 mm = make_int4(0, 0, 0, 0);
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    float cc = 0.f, tau = -1.0f;
     if ((int64_t)s < nvis) {
-      const int4 mm = A.meta[s];
+      mm = A.meta[s];
+      g = A.geom[s];
+      cc = A.color[s].x;
+      tau = A.tau[s];
       const int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff, y1 = (uint32_t)mm.w >> 16;
       area = (uint32_t)(max(x1 - x0, 0) * max(y1 - y0, 0));
-      m = make_int4((int)s, MAXV == 1 ? 0 : min(max(mm.y, 0), rv.nviews - 1), mm.z, mm.w);
-      const float4 gg = A.geom[s];
-      const float cc = A.color[s].x;
-      s_geom[threadIdx.x] = gg;
-      s_ct[threadIdx.x] = make_float2(cc, A.tau[s]);
-      s_k[threadIdx.x] = edge_slopes(gg.z, gg.w, cc);
     } else {
       atomicOr(&A.counters[kCtrStatus], kStatusInternal);
     }
+    const float2 k = edge_slopes(g.z, g.w, cc);
+    A.emit_rec[3 * j + 0] = make_int4(__float_as_int(g.x), __float_as_int(g.y), __float_as_int(g.z),
+                                      __float_as_int(g.w));
+    A.emit_rec[3 * j + 1] = make_int4(__float_as_int(cc), __float_as_int(k.x), __float_as_int(k.y),
+                                      __float_as_int(tau));
+    A.emit_rec[3 * j + 2] = make_int4((int)s, MAXV == 1 ? 0 : min(max(mm.y, 0), rv.nviews - 1), mm.z, mm.w);
   }
-  s_meta[threadIdx.x] = m;
-  uint32_t btotal;
-  s_prefix[threadIdx.x] = block_exclusive_scan(area, s_scan, &btotal);  // ends with a barrier
-  // Flattened pair f of this block -> keep decision, global tile id and slot.
-  auto pair = [&](uint32_t f, uint32_t *tile, uint32_t *slot) -> bool {
-    int lo = 0, hi = kEmitBlock - 1;  // owner: last slot whose prefix <= f
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_prefix[mid] <= f) lo = mid;
-      else hi = mid - 1;
-    }
-    const int4 mm = s_meta[lo];
-    const int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff;
-    const uint32_t local = f - s_prefix[lo];
-    const int w = x1 - x0;
-    const int tx = x0 + (int)(local % (uint32_t)w), ty = y0 + (int)(local / (uint32_t)w);
-    const RasterView &V = rv.v[mm.y];
-    const float bx0 = (float)(tx * kTile) + 0.5f, by0 = (float)(ty * kTile) + 0.5f;
-    const float bx1 = (float)min(tx * kTile + kTile - 1, V.width - 1) + 0.5f;
-    const float by1 = (float)min(ty * kTile + kTile - 1, V.height - 1) + 0.5f;
-    const float4 g = s_geom[lo];
-    const float2 ct = s_ct[lo];
-    const float2 kk = s_k[lo];
-    *tile = (uint32_t)(V.tile_base + ty * V.gw + tx);
-    *slot = (uint32_t)mm.x;
-    return ellipse_meets_box(g.x, g.y, g.z, g.w, ct.x, kk.x, kk.y, ct.y, bx0, bx1, by0, by1);
-  };
-  // Pass 1: count the kept pairs of this block.
-  uint32_t kept = 0u;
-  for (uint32_t f0 = 0; f0 < btotal; f0 += kEmitBlock) {
-    const uint32_t f = f0 + threadIdx.x;
-    uint32_t t, sl;
-    const bool keep = f < btotal && pair(f, &t, &sl);
-    kept += (uint32_t)__syncthreads_count(keep);
-  }
-  if (warp == 0) {
-    const uint64_t prefix = lookback_u64_warp(A.lb, (int32_t)b, kept, &A.counters[kCtrStatus]);
-    if (lane == 0) s_base = prefix;
-    if (lane == 0 && (b + 1) * kEmitBlock >= nvis) {  // last block with visible slots
-      const uint64_t all = prefix + kept;
-      A.counters[kCtrNeedInstances] = (uint32_t)umin64(all, 0xffffffffull);
-      A.counters[kCtrInstances] = (uint32_t)umin64(all, (uint64_t)A.inst_cap);
-      if (all > (uint64_t)A.inst_cap) atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan(area, s_scan, &total);
+  __shared__ uint64_t s_base;
+  if (threadIdx.x < 32) {
+    const uint64_t prefix = lookback_u64_warp(A.lb_scan, (int32_t)b, total, &A.counters[kCtrStatus]);
+    if (threadIdx.x == 0) s_base = prefix;
+    if (threadIdx.x == 0 && (b + 1) * kEmitBlock >= nvis) {  // last block: the pair total
+      const uint64_t all = prefix + total;
+      A.pair_prefix[nvis] = (uint32_t)umin64(all, (uint64_t)A.pair_cap);
+      A.counters[kCtrPairs] = (uint32_t)umin64(all, (uint64_t)A.pair_cap);
+      if (all > (uint64_t)A.pair_cap) {
+        // Some pairs cannot be examined: report the pair total as the bound
+        // on the instances needed.
+        A.counters[kCtrNeedInstances] = (uint32_t)umin64(all, 0xffffffffull);
+        atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
+      }
     }
   }
   __syncthreads();
-  // Pass 2: write the kept pairs in order (one barrier per chunk; the warp
-  // counts alternate between two buffers).
-  uint64_t pos = s_base;
+  if (j < nvis) A.pair_prefix[j] = (uint32_t)umin64(s_base + excl, (uint64_t)A.pair_cap);
+}
+
+// Instance emission in depth order.  The (slot, rect tile) pairs of all
+// visible slots, in depth order and row-major within a rect, are cut into
+// chunks of kEmitChunk; persistent blocks take chunks by ticket, keep a pair
+// when its slot's 1/255 ellipse meets the tile, count (pass 1), get the
+// chunk's output offset by decoupled look-back over chunks, and write the
+// kept pairs in order (pass 2).  Every chunk is the same amount of work, so a
+// screen-sized Gaussian is spread over many blocks.
+template <int MAXV>
+__global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterViews<MAXV> rv) {
+  constexpr int kPer = kEmitChunk / kEmitBlock;
+  __shared__ uint32_t s_ticket, s_j0, s_ns;
+  __shared__ uint32_t s_pref[kEmitChunk + 1];  // pair prefix of the chunk's slots
+  __shared__ uint32_t s_w[2][kEmitBlock / 32];
+  __shared__ uint32_t s_red[kEmitBlock / 32];
+  __shared__ uint64_t s_base;
+  const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
+  const uint32_t npairs = A.counters[kCtrPairs];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  int buf = 0;
-  for (uint32_t f0 = 0; f0 < btotal; f0 += kEmitBlock, buf ^= 1) {
-    const uint32_t f = f0 + threadIdx.x;
-    uint32_t t = 0u, sl = 0u;
-    const bool keep = f < btotal && pair(f, &t, &sl);
-    const uint32_t mask = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) s_w[buf][warp] = __popc(mask);
+  while (true) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&A.counters[kCtrTicketChunk], 1u);
     __syncthreads();
-    uint32_t before = 0u, chunk = 0u;
-#pragma unroll
-    for (int w = 0; w < kEmitBlock / 32; ++w) {
-      const uint32_t c = s_w[buf][w];
-      before += w < warp ? c : 0u;
-      chunk += c;
+    const uint32_t c = s_ticket;
+    if ((uint64_t)c * kEmitChunk >= npairs || (int32_t)c >= A.chunk_cap) return;
+    const uint32_t f0 = c * kEmitChunk;
+    const uint32_t f1 = min(f0 + (uint32_t)kEmitChunk, npairs);
+    if (threadIdx.x == 0) {  // slots holding pairs f0 and f1 - 1 (last slot with prefix <= f)
+      int64_t lo = 0, hi = nvis - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (A.pair_prefix[mid] <= f0) lo = mid;
+        else hi = mid - 1;
+      }
+      const int64_t j0 = lo;
+      hi = nvis - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (A.pair_prefix[mid] <= f1 - 1) lo = mid;
+        else hi = mid - 1;
+      }
+      s_j0 = (uint32_t)j0;
+      s_ns = (uint32_t)min64(lo - j0 + 1, kEmitChunk);
     }
-    if (keep) {
-      const uint64_t p = pos + before + __popc(mask & lt);
-      if (p < (uint64_t)A.inst_cap) {
-        A.inst_key[p] = t;
-        A.inst_val[p] = sl;
+    __syncthreads();
+    const uint32_t j0 = s_j0, ns = s_ns;
+    for (uint32_t k = threadIdx.x; k <= ns; k += kEmitBlock)
+      s_pref[k] = (int64_t)(j0 + k) <= nvis ? A.pair_prefix[j0 + k] : npairs;
+    __syncthreads();
+    // Pair f -> keep, tile and slot.
+    auto pair = [&](uint32_t f, uint32_t *tile, uint32_t *slot) -> bool {
+      int lo = 0, hi = (int)ns - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pref[mid] <= f) lo = mid;
+        else hi = mid - 1;
+      }
+      const int4 *er = A.emit_rec + 3 * (size_t)(j0 + lo);
+      const int4 r0 = er[0], r1 = er[1], r2 = er[2];
+      const int x0 = r2.z & 0xffff, y0 = (uint32_t)r2.z >> 16, x1 = r2.w & 0xffff;
+      const uint32_t local = f - s_pref[lo];
+      const int w = max(x1 - x0, 1);
+      const int tx = x0 + (int)(local % (uint32_t)w), ty = y0 + (int)(local / (uint32_t)w);
+      const RasterView &V = rv.v[r2.y];
+      const float bx0 = (float)(tx * kTile) + 0.5f, by0 = (float)(ty * kTile) + 0.5f;
+      const float bx1 = (float)min(tx * kTile + kTile - 1, V.width - 1) + 0.5f;
+      const float by1 = (float)min(ty * kTile + kTile - 1, V.height - 1) + 0.5f;
+      *tile = (uint32_t)(V.tile_base + ty * V.gw + tx);
+      *slot = (uint32_t)r2.x;
+      return ellipse_meets_box(__int_as_float(r0.x), __int_as_float(r0.y), __int_as_float(r0.z),
+                               __int_as_float(r0.w), __int_as_float(r1.x), __int_as_float(r1.y),
+                               __int_as_float(r1.z), __int_as_float(r1.w), bx0, bx1, by0, by1);
+    };
+    // Pass 1: count.
+    uint32_t kept = 0u;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const uint32_t f = f0 + i * kEmitBlock + threadIdx.x;
+      uint32_t t, sl;
+      kept += (f < f1 && pair(f, &t, &sl)) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    if (lane == 0) s_red[warp] = kept;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t tot = lane < kEmitBlock / 32 ? s_red[lane] : 0u;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      const uint64_t prefix = lookback_u64_warp(A.lb_chunk, (int32_t)c, tot, &A.counters[kCtrStatus]);
+      if (lane == 0) s_base = prefix;
+      if (lane == 0 && f1 == npairs) {  // last chunk: the instance total
+        const uint64_t all = prefix + tot;
+        A.counters[kCtrInstances] = (uint32_t)umin64(all, (uint64_t)A.inst_cap);
+        if (!(A.counters[kCtrStatus] & kStatusInstOverflow) || all > (uint64_t)A.inst_cap)
+          A.counters[kCtrNeedInstances] =
+              (uint32_t)umin64(max((uint64_t)A.counters[kCtrNeedInstances], all), 0xffffffffull);
+        if (all > (uint64_t)A.inst_cap) atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
       }
     }
-    pos += chunk;
+    __syncthreads();
+    // Pass 2: write the kept pairs in pair order.
+    uint64_t pos = s_base;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const uint32_t f = f0 + i * kEmitBlock + threadIdx.x;
+      uint32_t t = 0u, sl = 0u;
+      const bool keep = f < f1 && pair(f, &t, &sl);
+      const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) s_w[i & 1][warp] = __popc(mask);
+      __syncthreads();
+      uint32_t before = 0u, chunk = 0u;
+#pragma unroll
+      for (int w = 0; w < kEmitBlock / 32; ++w) {
+        const uint32_t cw = s_w[i & 1][w];
+        before += w < warp ? cw : 0u;
+        chunk += cw;
+      }
+      if (keep) {
+        const uint64_t p = pos + before + __popc(mask & lt);
+        if (p < (uint64_t)A.inst_cap) {
+          A.inst_key[p] = t;
+          A.inst_val[p] = sl;
+        }
+      }
+      pos += chunk;
+    }
+    __syncthreads();  // s_pref and s_w are reused by the next chunk
   }
 }
 
@@ -404,10 +482,16 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
     ea.counters = ctr;
     ea.vis_cap = L.vis_cap;
     ea.inst_cap = L.inst_cap;
+    ea.pair_cap = L.pair_cap;
+    ea.chunk_cap = L.chunk_cap;
+    ea.pair_prefix = reinterpret_cast<uint32_t *>(ws + L.pair_prefix);
+    ea.emit_rec = reinterpret_cast<int4 *>(ws + L.emit_rec);
     ea.inst_key = ik[0];
     ea.inst_val = iv[0];
-    ea.lb = reinterpret_cast<uint64_t *>(ws + L.lb_emit);
-    emit_kernel<MAXV><<<L.emit_blocks, kEmitBlock, 0, st>>>(ea, rv);
+    ea.lb_scan = reinterpret_cast<uint64_t *>(ws + L.lb_emit);
+    ea.lb_chunk = reinterpret_cast<uint64_t *>(ws + L.lb_chunk);
+    pair_scan_kernel<MAXV><<<L.emit_blocks, kEmitBlock, 0, st>>>(ea, rv);
+    emit_kernel<MAXV><<<L.emit_grid, kEmitBlock, 0, st>>>(ea, rv);
   }
   // 3. Stable sort of the instances by global tile id.
   uint32_t *tstate = reinterpret_cast<uint32_t *>(ws + L.tile_state);

@@ -303,8 +303,9 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
   constexpr int kPer = kEmitChunk / kEmitBlock;
   __shared__ uint32_t s_ticket, s_j0, s_ns;
   __shared__ uint32_t s_pref[kEmitChunk + 1];  // pair prefix of the chunk's slots
-  __shared__ uint32_t s_w[2][kEmitBlock / 32];
-  __shared__ uint32_t s_red[kEmitBlock / 32];
+  constexpr int kRecCache = 256;                // slot records cached per chunk
+  __shared__ int4 s_rec[kRecCache * 3];
+  __shared__ uint32_t s_w[kEmitChunk / kEmitBlock][kEmitBlock / 32];
   __shared__ uint64_t s_base;
   const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
   const uint32_t npairs = A.counters[kCtrPairs];
@@ -338,6 +339,9 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
     const uint32_t j0 = s_j0, ns = s_ns;
     for (uint32_t k = threadIdx.x; k <= ns; k += kEmitBlock)
       s_pref[k] = (int64_t)(j0 + k) <= nvis ? A.pair_prefix[j0 + k] : npairs;
+    const bool cached = ns <= (uint32_t)kRecCache;
+    if (cached)
+      for (uint32_t k = threadIdx.x; k < 3 * ns; k += kEmitBlock) s_rec[k] = A.emit_rec[3 * (size_t)j0 + k];
     __syncthreads();
     // Pair f -> keep, tile and slot.
     auto pair = [&](uint32_t f, uint32_t *tile, uint32_t *slot) -> bool {
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
         if (s_pref[mid] <= f) lo = mid;
         else hi = mid - 1;
       }
-      const int4 *er = A.emit_rec + 3 * (size_t)(j0 + lo);
+      const int4 *er = cached ? s_rec + 3 * lo : A.emit_rec + 3 * (size_t)(j0 + lo);
       const int4 r0 = er[0], r1 = er[1], r2 = er[2];
       const int x0 = r2.z & 0xffff, y0 = (uint32_t)r2.z >> 16, x1 = r2.w & 0xffff;
       const uint32_t local = f - s_pref[lo];
@@ -363,20 +367,22 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
                                __int_as_float(r0.w), __int_as_float(r1.x), __int_as_float(r1.y),
                                __int_as_float(r1.z), __int_as_float(r1.w), bx0, bx1, by0, by1);
     };
-    // Pass 1: count.
-    uint32_t kept = 0u;
+    // Pass 1: decide every pair once; per-(item, warp) counts go to shared
+    // memory, the decisions stay in registers for pass 2.
+    bool keep[kPer];
+    uint32_t tile[kPer], slot[kPer], mask[kPer];
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
       const uint32_t f = f0 + i * kEmitBlock + threadIdx.x;
-      uint32_t t, sl;
-      kept += (f < f1 && pair(f, &t, &sl)) ? 1u : 0u;
+      tile[i] = slot[i] = 0u;
+      keep[i] = f < f1 && pair(f, &tile[i], &slot[i]);
+      mask[i] = __ballot_sync(0xffffffffu, keep[i]);
+      if (lane == 0) s_w[i][warp] = __popc(mask[i]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
-    if (lane == 0) s_red[warp] = kept;
     __syncthreads();
     if (warp == 0) {
-      uint32_t tot = lane < kEmitBlock / 32 ? s_red[lane] : 0u;
+      uint32_t tot = 0u;
+      for (int k = lane; k < kPer * (kEmitBlock / 32); k += 32) tot += (&s_w[0][0])[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
       const uint64_t prefix = lookback_u64_warp(A.lb_chunk, (int32_t)c, tot, &A.counters[kCtrStatus]);
@@ -391,28 +397,22 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
       }
     }
     __syncthreads();
-    // Pass 2: write the kept pairs in pair order.
+    // Pass 2: write the kept pairs in pair order (item-major, then warp, then lane).
     uint64_t pos = s_base;
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
-      const uint32_t f = f0 + i * kEmitBlock + threadIdx.x;
-      uint32_t t = 0u, sl = 0u;
-      const bool keep = f < f1 && pair(f, &t, &sl);
-      const uint32_t mask = __ballot_sync(0xffffffffu, keep);
-      if (lane == 0) s_w[i & 1][warp] = __popc(mask);
-      __syncthreads();
       uint32_t before = 0u, chunk = 0u;
 #pragma unroll
       for (int w = 0; w < kEmitBlock / 32; ++w) {
-        const uint32_t cw = s_w[i & 1][w];
+        const uint32_t cw = s_w[i][w];
         before += w < warp ? cw : 0u;
         chunk += cw;
       }
-      if (keep) {
-        const uint64_t p = pos + before + __popc(mask & lt);
+      if (keep[i]) {
+        const uint64_t p = pos + before + __popc(mask[i] & lt);
         if (p < (uint64_t)A.inst_cap) {
-          A.inst_key[p] = t;
-          A.inst_val[p] = sl;
+          A.inst_key[p] = tile[i];
+          A.inst_val[p] = slot[i];
         }
       }
       pos += chunk;

@@ -30,7 +30,7 @@ struct RenderArgs {
   const uint2 *ranges;
   const uint32_t *inst_val;
   const float4 *rec_geom, *rec_color;
-  const float *rec_blue, *rec_tau;
+  const float *rec_blue;
   uint32_t vis_cap;
   float *out_rgb, *out_T;
   float *pix_T;
@@ -42,7 +42,7 @@ struct RenderBwdArgs {
   const uint2 *ranges;
   const uint32_t *inst_val;
   const float4 *rec_geom, *rec_color;
-  const float *rec_blue, *rec_tau;
+  const float *rec_blue;
   uint32_t vis_cap;
   const float *pix_T;
   const uint32_t *pix_last;
@@ -68,29 +68,14 @@ __device__ __forceinline__ int find_view(const RasterViews<MAXV> &rv, int32_t gt
   return lo;
 }
 
-// Half-extents (rx, ry) of the axis-aligned box around the ellipse
-// q = A' dx^2 + B' dx dy + C' dy^2 <= tau outside which alpha < 1/255:
-// rx^2 = tau C' / det, ry^2 = tau A' / det with det = A' C' - B'^2 / 4,
-// enlarged by 0.1% + 0.01 px so that rounding never drops a pixel the
-// per-pixel test would keep (tau already carries a margin).  A record that
-// can never reach 1/255 gets a negative extent; a degenerate form gets an
-// unbounded one.
-__device__ __forceinline__ float2 alpha_extent(float4 geom, float C2, float tau) {
-  if (!(tau >= 0.0f)) return make_float2(-1.0f, -1.0f);
-  const float det = geom.z * C2 - 0.25f * geom.w * geom.w;
-  if (!(det > 0.0f)) return make_float2(INFINITY, INFINITY);
-  const float rx = sqrtf(tau * C2 / det), ry = sqrtf(tau * geom.z / det);
-  return make_float2(rx * 1.001f + 0.01f, ry * 1.001f + 0.01f);
-}
-
 // Stages records [base, min(base + kBatch, end)) of the tile list into shared
-// memory, with each record's 1/255 extent; slots out of range (only possible
-// after a recorded timeout) stage a record that every pixel skips.
+// memory; slots out of range (only possible after a recorded timeout) stage a
+// record that every pixel skips.
 template <int NT>
 __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const float4 *rec_geom,
-                                            const float4 *rec_color, const float *rec_blue, const float *rec_tau,
-                                            uint32_t vis_cap, uint32_t base, uint32_t end, float4 *s_geom,
-                                            float4 *s_col, float *s_blue, float2 *s_ext, uint32_t *s_slot) {
+                                            const float4 *rec_color, const float *rec_blue, uint32_t vis_cap,
+                                            uint32_t base, uint32_t end, float4 *s_geom, float4 *s_col,
+                                            float *s_blue, uint32_t *s_slot) {
 #pragma unroll
   for (int i = 0; i < kBatch / NT; ++i) {
     const int k = threadIdx.x + i * NT;
@@ -99,40 +84,16 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
       const uint32_t s = inst_val[idx];
       if (s_slot) s_slot[k] = s;
       if (s < vis_cap) {
-        const float4 g = rec_geom[s], c = rec_color[s];
-        s_geom[k] = g;
-        s_col[k] = c;
+        s_geom[k] = rec_geom[s];
+        s_col[k] = rec_color[s];
         s_blue[k] = rec_blue[s];
-        s_ext[k] = alpha_extent(g, c.x, rec_tau[s]);
       } else {
         s_geom[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         s_col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         s_blue[k] = 0.f;
-        s_ext[k] = make_float2(-1.0f, -1.0f);
       }
     }
   }
-}
-
-// Pixel-centre band [x0, x1] x [y0, y1] covered by the calling thread's warp:
-// all 16 columns of the tile (clipped to the image) and 2 PPT rows.
-struct Band {
-  float x0, x1, y0, y1;
-};
-
-template <int PPT>
-__device__ __forceinline__ Band warp_band(int32_t tx, int32_t ty, int32_t width, int32_t height) {
-  Band b;
-  const int row0 = ty * kTile + (int)(threadIdx.x / 32) * 2 * PPT;
-  b.x0 = (float)(tx * kTile) + 0.5f;
-  b.x1 = (float)min(tx * kTile + kTile - 1, width - 1) + 0.5f;
-  b.y0 = (float)row0 + 0.5f;
-  b.y1 = (float)min(row0 + 2 * PPT - 1, height - 1) + 0.5f;
-  return b;
-}
-
-__device__ __forceinline__ bool band_misses(const Band &b, float4 geom, float2 ext) {
-  return geom.x + ext.x < b.x0 || geom.x - ext.x > b.x1 || geom.y + ext.y < b.y0 || geom.y - ext.y > b.y1;
 }
 
 // kStats: also counts the pixel-entry alpha evaluations and the composited
@@ -147,7 +108,6 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
   __shared__ float4 s_geom[kBatch];
   __shared__ float4 s_col[kBatch];
   __shared__ float s_blue[kBatch];
-  __shared__ float2 s_ext[kBatch];
   const int32_t gt = blockIdx.x;
   const RasterView &V = rv.v[find_view<MAXV>(rv, gt)];
   const int32_t lt = gt - V.tile_base;
@@ -156,7 +116,6 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
   const int32_t py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
   const uint2 range = A.ranges[gt];
   const float pxc = (float)px + 0.5f;
-  const Band band = warp_band<PPT>(tx, ty, V.width, V.height);
   float T[PPT], Tend[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
   uint32_t last[PPT];
   bool live = false;
@@ -173,13 +132,12 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
   uint32_t n_eval = 0u, n_comp = 0u;
   for (uint32_t base = range.x; base < range.y; base += kBatch) {
     if (__syncthreads_count(live) == 0) break;
-    stage_batch<NT>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.rec_tau, A.vis_cap, base, range.y, s_geom,
-                    s_col, s_blue, s_ext, nullptr);
+    stage_batch<NT>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, range.y, s_geom, s_col,
+                    s_blue, nullptr);
     __syncthreads();
     const int nb = (int)min(range.y - base, (uint32_t)kBatch);
     for (int j = 0; j < nb && live; ++j) {
       const float4 geom = s_geom[j];
-      if (band_misses(band, geom, s_ext[j])) continue;  // alpha < 1/255 on the whole warp band
       const float4 col = s_col[j];
       const ColumnTerms ct = column_terms(geom, pxc);
 #pragma unroll
@@ -249,7 +207,6 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
   __shared__ float4 s_geom[kBatch];
   __shared__ float4 s_col[kBatch];
   __shared__ float s_blue[kBatch];
-  __shared__ float2 s_ext[kBatch];
   __shared__ uint32_t s_slot[kBatch];
   __shared__ uint32_t s_maxlast;
   const int32_t gt = blockIdx.x;
@@ -260,7 +217,6 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
   const int32_t py0 = ty * kTile + (threadIdx.x / kTile) * kPPT;
   const uint2 range = A.ranges[gt];
   const float pxc = (float)px + 0.5f;
-  const Band band = warp_band<kPPT>(tx, ty, V.width, V.height);
   const int64_t HW = (int64_t)V.width * V.height;
   float T[kPPT], dC0[kPPT], dC1[kPPT], dC2[kPPT], r0[kPPT], r1[kPPT], r2[kPPT], pyc[kPPT];
   uint32_t last[kPPT];
@@ -295,15 +251,14 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
   for (int bi = nbatch - 1; bi >= 0; --bi) {
     const uint32_t base = range.x + (uint32_t)bi * kBatch;
     __syncthreads();
-    stage_batch<kRenderThreads>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.rec_tau, A.vis_cap, base, end,
-                                s_geom, s_col, s_blue, s_ext, s_slot);
+    stage_batch<kRenderThreads>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, end, s_geom,
+                                s_col, s_blue, s_slot);
     __syncthreads();
     const int nb = (int)min(end - base, (uint32_t)kBatch);
     for (int j = nb - 1; j >= 0; --j) {
       const uint32_t pos = base + j - range.x;  // entry index in the tile list
       if (!__any_sync(0xffffffffu, pos < my_max)) continue;  // no pixel of this warp reached it
       const float4 geom = s_geom[j];
-      if (band_misses(band, geom, s_ext[j])) continue;  // alpha < 1/255 on the whole warp band
       const float4 col = s_col[j];
       const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc);
@@ -384,7 +339,6 @@ cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   A.rec_geom = reinterpret_cast<const float4 *>(ws + L.rec_geom);
   A.rec_color = reinterpret_cast<const float4 *>(ws + L.rec_color);
   A.rec_blue = reinterpret_cast<const float *>(ws + L.rec_blue);
-  A.rec_tau = reinterpret_cast<const float *>(ws + L.rec_tau);
   A.vis_cap = (uint32_t)L.vis_cap;
   A.out_rgb = out_rgb;
   A.out_T = out_T;
@@ -424,7 +378,6 @@ cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   A.rec_geom = reinterpret_cast<const float4 *>(ws + L.rec_geom);
   A.rec_color = reinterpret_cast<const float4 *>(ws + L.rec_color);
   A.rec_blue = reinterpret_cast<const float *>(ws + L.rec_blue);
-  A.rec_tau = reinterpret_cast<const float *>(ws + L.rec_tau);
   A.vis_cap = (uint32_t)L.vis_cap;
   A.pix_T = reinterpret_cast<const float *>(ws + L.pix_T);
   A.pix_last = reinterpret_cast<const uint32_t *>(ws + L.pix_last);

@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--train-iters", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurements")
     return p.parse_args()
 
 
@@ -334,6 +335,13 @@ def run_ours(args, rank, world, local):
     # ---------------------------------------------------------- train step
     train = run_train(args, dev, scene, params, world, barrier)
 
+    # ---------------------------------------------------------- batched views
+    batched = None
+    if not args.no_batched:
+        batched = [run_batched(dev, sy.sphere_scene(), sy.sphere_views(64), "sphere-1M-64views-mixed-res", 3),
+                   run_batched(dev, sy.urban_scene(), sy.urban_views(), "urban-3M-6cams-x-2t-1920x1080", 3,
+                               plain=False)]
+
     # ---------------------------------------------------------- CPU oracle
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -366,6 +374,7 @@ def run_ours(args, rank, world, local):
             "clocks": clk,
             "e2e": e2e,
             "train": train,
+            "batched": batched,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -428,6 +437,116 @@ def run_train(args, dev, scene, params, world, barrier):
                         "parameters, fused Adam step" % scene.n,
             "status": fgs4d.status_string(code), "loss": float(loss.item()), "autotune": tuned,
             "targets": "rendered by the CUDA path from a second seeded scene"}
+
+
+def run_batched(dev, scene, views, label, steps, plain=True):
+    """Forward + backward of many (camera, t) views of mixed resolution: one
+    multi-view call per step captured in a CUDA graph, against one plain
+    single-view call per view.  The upstream image gradient is a fixed
+    random tensor (the loss does not change the kernel work)."""
+    import torch
+
+    from paper_2412_20720_gb300 import fgs4d
+    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, autotune
+
+    params = {k: torch.from_numpy(v).to(dev) for k, v in scene.as_dict().items()}
+    n = scene.n
+    # Size the capacities on one forward with generous ones.
+    probe = Renderer(n, views, RenderConfig(sh_degree=3, t_order=2, vis_capacity=min(n * len(views), 1 << 29),
+                                            inst_capacity=(1 << 30) - 1), device=dev)
+    probe.forward(params)
+    counts = probe.check()
+    del probe
+    torch.cuda.empty_cache()
+    cfg = RenderConfig(sh_degree=3, t_order=2, vis_capacity=int(counts[0] * 1.1) + 1024,
+                       inst_capacity=int(counts[1] * 1.1) + 1024)
+    r = Renderer(n, views, cfg, device=dev)
+    tuned = autotune(r, params, backward=True, reps=2)
+    gen = torch.Generator(device=dev).manual_seed(3)
+    dL = torch.randn(3 * r.total_pixels, device=dev, generator=gen) * 1e-3
+    grads = {k: torch.zeros_like(params[k]) for k in PARAM_KEYS}
+
+    def step():
+        for gk in grads.values():
+            gk.zero_()
+        r.forward(params)
+        r.backward(params, dL, grads)
+
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            step()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    graph.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    code, counts = r.status()
+    graph_ms = a.elapsed_time(b) / steps
+    out = {"workload": label, "gaussians": n, "views": len(views),
+           "resolutions": sorted({"%dx%d" % (v["width"], v["height"]) for v in views}),
+           "visible_pairs": counts[0], "instances": counts[1], "status": fgs4d.status_string(code),
+           "autotune": tuned,
+           "graph_batched": {"ms_per_step": graph_ms, "views_per_s": len(views) * 1000.0 / graph_ms,
+                             "fwd_bwd_iters_per_s": 1000.0 / graph_ms}}
+    del graph
+    if plain:
+        # One single-view renderer per resolution; each view is its own call.
+        per_res = {}
+        singles = []
+        for v in views:
+            key = (v["width"], v["height"])
+            if key not in per_res:
+                c1 = RenderConfig(sh_degree=3, t_order=2, vis_capacity=n, inst_capacity=cfg.inst_capacity,
+                                  pixels_per_thread=r.settings.pixels_per_thread)
+                per_res[key] = Renderer(n, [v], c1, device=dev)
+            rr = per_res[key]
+            singles.append((rr, fgs4d.make_views([v]), torch.randn(3 * v["width"] * v["height"], device=dev,
+                                                                   generator=gen) * 1e-3))
+        g_ = {k: params[k] for k in PARAM_KEYS}
+
+        def plain_step():
+            for gk in grads.values():
+                gk.zero_()
+            for rr, (vv, nv), dl in singles:
+                st = rr.stream()
+                ws = rr.ws.data_ptr()
+                gg = rr.gaussians(g_)
+                fgs4d.preprocess(gg, vv, nv, rr.settings, ws, rr.ws_bytes, st)
+                fgs4d.bin_sort(n, vv, nv, rr.settings, ws, rr.ws_bytes, st)
+                img = torch.empty_like(dl)
+                fgs4d.render_fwd(n, vv, nv, rr.settings, ws, rr.ws_bytes, img.data_ptr(), None, st)
+                fgs4d.render_bwd(gg, vv, nv, rr.settings, ws, rr.ws_bytes, dl.data_ptr(),
+                                 fgs4d.make_grads({k: grads[k].data_ptr() for k in PARAM_KEYS}), st)
+
+        plain_step()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            plain_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        for rr in per_res.values():
+            code2, _ = rr.status()
+            if code2 != fgs4d.OK:
+                out["plain_status"] = fgs4d.status_string(code2)
+        plain_ms = a.elapsed_time(b) / steps
+        out["plain_per_view"] = {"ms_per_step": plain_ms, "views_per_s": len(views) * 1000.0 / plain_ms,
+                                 "fwd_bwd_iters_per_s": 1000.0 / plain_ms}
+        out["graph_speedup"] = plain_ms / graph_ms
+        del per_res, singles
+    del r
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------ reference

@@ -338,8 +338,8 @@ def run_ours(args, rank, world, local):
     # ---------------------------------------------------------- batched views
     batched = None
     if not args.no_batched:
-        batched = [run_batched(dev, sy.sphere_scene(), sy.sphere_views(64), "sphere-1M-64views-mixed-res", 3),
-                   run_batched(dev, sy.urban_scene(), sy.urban_views(), "urban-3M-6cams-x-2t-1920x1080", 3,
+        batched = [run_batched(dev, sy.sphere_scene(), sy.sphere_views(64), "sphere-1M-64views-mixed-res", 2, 8),
+                   run_batched(dev, sy.urban_scene(), sy.urban_views(), "urban-3M-6cams-x-2t-1920x1080", 2, 6,
                                plain=False)]
 
     # ---------------------------------------------------------- CPU oracle
@@ -439,11 +439,12 @@ def run_train(args, dev, scene, params, world, barrier):
             "targets": "rendered by the CUDA path from a second seeded scene"}
 
 
-def run_batched(dev, scene, views, label, steps, plain=True):
+def run_batched(dev, scene, views, label, steps, group, plain=True):
     """Forward + backward of many (camera, t) views of mixed resolution: one
-    multi-view call per step captured in a CUDA graph, against one plain
-    single-view call per view.  The upstream image gradient is a fixed
-    random tensor (the loss does not change the kernel work)."""
+    multi-view call per group of ``group`` views, all groups of a step
+    captured in one CUDA graph, against one plain single-view call per view.
+    The upstream image gradient is a fixed random tensor (the loss does not
+    change the kernel work)."""
     import torch
 
     from paper_2412_20720_gb300 import fgs4d
@@ -451,26 +452,36 @@ def run_batched(dev, scene, views, label, steps, plain=True):
 
     params = {k: torch.from_numpy(v).to(dev) for k, v in scene.as_dict().items()}
     n = scene.n
-    # Size the capacities on one forward with generous ones.
-    probe = Renderer(n, views, RenderConfig(sh_degree=3, t_order=2, vis_capacity=min(n * len(views), 1 << 29),
-                                            inst_capacity=(1 << 30) - 1), device=dev)
-    probe.forward(params)
-    counts = probe.check()
-    del probe
-    torch.cuda.empty_cache()
-    cfg = RenderConfig(sh_degree=3, t_order=2, vis_capacity=int(counts[0] * 1.1) + 1024,
-                       inst_capacity=int(counts[1] * 1.1) + 1024)
-    r = Renderer(n, views, cfg, device=dev)
-    tuned = autotune(r, params, backward=True, reps=2)
+    groups = [views[i:i + group] for i in range(0, len(views), group)]
+    rs, tuned, vis_tot, inst_tot, max_inst = [], None, 0, 0, 0
+    for gv in groups:
+        # Size each group's capacities on one forward with generous ones.
+        probe = Renderer(n, gv, RenderConfig(sh_degree=3, t_order=2, vis_capacity=min(n * len(gv), 1 << 29),
+                                             inst_capacity=(1 << 30) - 1), device=dev)
+        probe.forward(params)
+        counts = probe.check()
+        del probe
+        torch.cuda.empty_cache()
+        cfg = RenderConfig(sh_degree=3, t_order=2, vis_capacity=int(counts[0] * 1.1) + 1024,
+                           inst_capacity=min(int(counts[1] * 1.1) + 1024, (1 << 30) - 1))
+        r = Renderer(n, gv, cfg, device=dev)
+        if tuned is None:
+            tuned = autotune(r, params, backward=True, reps=2)
+        r.settings.pixels_per_thread = tuned["pixels_per_thread"]
+        rs.append(r)
+        vis_tot += counts[0]
+        inst_tot += counts[1]
+        max_inst = max(max_inst, counts[1])
     gen = torch.Generator(device=dev).manual_seed(3)
-    dL = torch.randn(3 * r.total_pixels, device=dev, generator=gen) * 1e-3
+    dLs = [torch.randn(3 * r.total_pixels, device=dev, generator=gen) * 1e-3 for r in rs]
     grads = {k: torch.zeros_like(params[k]) for k in PARAM_KEYS}
 
     def step():
         for gk in grads.values():
             gk.zero_()
-        r.forward(params)
-        r.backward(params, dL, grads)
+        for r, dL in zip(rs, dLs):
+            r.forward(params)
+            r.backward(params, dL, grads)
 
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
@@ -490,11 +501,12 @@ def run_batched(dev, scene, views, label, steps, plain=True):
         graph.replay()
     b.record(stream)
     torch.cuda.synchronize()
-    code, counts = r.status()
+    codes = [r.status()[0] for r in rs]
+    code = next((c for c in codes if c != fgs4d.OK), fgs4d.OK)
     graph_ms = a.elapsed_time(b) / steps
-    out = {"workload": label, "gaussians": n, "views": len(views),
+    out = {"workload": label, "gaussians": n, "views": len(views), "views_per_call": group,
            "resolutions": sorted({"%dx%d" % (v["width"], v["height"]) for v in views}),
-           "visible_pairs": counts[0], "instances": counts[1], "status": fgs4d.status_string(code),
+           "visible_pairs": vis_tot, "instances": inst_tot, "status": fgs4d.status_string(code),
            "autotune": tuned,
            "graph_batched": {"ms_per_step": graph_ms, "views_per_s": len(views) * 1000.0 / graph_ms,
                              "fwd_bwd_iters_per_s": 1000.0 / graph_ms}}
@@ -506,8 +518,8 @@ def run_batched(dev, scene, views, label, steps, plain=True):
         for v in views:
             key = (v["width"], v["height"])
             if key not in per_res:
-                c1 = RenderConfig(sh_degree=3, t_order=2, vis_capacity=n, inst_capacity=cfg.inst_capacity,
-                                  pixels_per_thread=r.settings.pixels_per_thread)
+                c1 = RenderConfig(sh_degree=3, t_order=2, vis_capacity=n, inst_capacity=max_inst + 1024,
+                                  pixels_per_thread=tuned["pixels_per_thread"])
                 per_res[key] = Renderer(n, [v], c1, device=dev)
             rr = per_res[key]
             singles.append((rr, fgs4d.make_views([v]), torch.randn(3 * v["width"] * v["height"], device=dev,
@@ -544,7 +556,7 @@ def run_batched(dev, scene, views, label, steps, plain=True):
                                  "fwd_bwd_iters_per_s": 1000.0 / plain_ms}
         out["graph_speedup"] = plain_ms / graph_ms
         del per_res, singles
-    del r
+    del rs
     torch.cuda.empty_cache()
     return out
 

@@ -44,6 +44,10 @@ W_IMG, H_IMG = 1352, 1014
 # alpha*T (1), three colour multiply-adds (6) = 9.  The ex2 goes to the SFU.
 FLOPS_PER_EVAL = 11
 FLOPS_PER_COMP = 9
+# DRAM bytes (read + write) of one compositor launch (2 pixels per thread) on
+# this workload, from the ncu capture summarised in
+# profiles/kernels_orbit_300k_1352x1014.md; None once the kernel changes.
+RENDER_FWD_TRAFFIC = {2: 4.911104e6 + 3.584e3}
 
 
 def parse():
@@ -365,7 +369,8 @@ def run_ours(args, rank, world, local):
             "work_per_frame": {"visible": float(np.mean(vis)), "instances": float(np.mean(inst)),
                                "alpha_evals": float(np.mean(evals)), "composited": float(np.mean(comps))},
             "roofline": {"kernel": "render_fwd", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "traffic": RENDER_FWD_TRAFFIC.get(tuned["pixels_per_thread"]),
                          "peak_basis": "SMs x 128 FP32 lanes x 2 (FMA) x max SM clock %.0f MHz (derived)" % sm_max,
                          "flops_per_launch": mean_flops},
             "preprocess_roofline": {"bound": "hbm", "achieved": pre_gbs, "peak": hbm, "unit": "GB/s",

@@ -16,19 +16,24 @@
 // their 2048 keys stably with warp match, publish per-digit counts and find
 // their per-digit global offsets by decoupled look-back over the earlier
 // tickets (bounded waits), then scatter through shared memory.
+#include <algorithm>
+
 #include "fgs4d_internal.cuh"
 
 namespace fgs4d {
 
 namespace {
 
+// Blocks of the persistent sort kernels: four resident per SM on 152 SMs.
+constexpr int kPersistBlocks = 152 * 4;
+
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = kFlagAgg - 1u;
 
 // Digit histograms of keys [0, count) for `passes` 8-bit digits starting at
-// bit 0; also clears the look-back rows the radix passes will use and the
-// tile ranges (grid-stride).
+// bit 0, grid-stride over chunks of kHistItems keys; also clears the
+// look-back rows the radix passes will use and the tile ranges.
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t *__restrict__ keys,
                                                                   const uint32_t *__restrict__ count_ptr, int64_t cap,
                                                                   int32_t passes, uint32_t *hist, uint32_t *state,
@@ -38,19 +43,20 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nranges; r += (int64_t)gridDim.x * blockDim.x)
     ranges[r] = make_uint2(0u, 0u);
   const int64_t count = min64((int64_t)*count_ptr, cap);
-  const int64_t base = (int64_t)blockIdx.x * kHistItems;
-  if (base >= count) return;
+  if ((int64_t)blockIdx.x * kHistItems >= count) return;
   for (int p = 0; p < passes; ++p) s_hist[p][threadIdx.x] = 0u;
-  // Clear the look-back rows of the radix blocks covering this range.
-  const int64_t ob0 = base / kSortTile;
-  for (int p = 0; p < passes; ++p)
-    for (int64_t ob = ob0; ob < ob0 + kHistItems / kSortTile && ob < state_blocks && ob * kSortTile < count; ++ob)
-      state[((int64_t)p * state_blocks + ob) * kRadixBins + threadIdx.x] = 0u;
   __syncthreads();
-  const int64_t end = min64(base + kHistItems, count);
-  for (int64_t idx = base + threadIdx.x; idx < end; idx += kSortThreads) {
-    const uint32_t k = keys[idx];
-    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(k >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
+  for (int64_t base = (int64_t)blockIdx.x * kHistItems; base < count; base += (int64_t)gridDim.x * kHistItems) {
+    // Clear the look-back rows of the radix tiles covering this chunk.
+    const int64_t ob0 = base / kSortTile;
+    for (int p = 0; p < passes; ++p)
+      for (int64_t ob = ob0; ob < ob0 + kHistItems / kSortTile && ob < state_blocks && ob * kSortTile < count; ++ob)
+        state[((int64_t)p * state_blocks + ob) * kRadixBins + threadIdx.x] = 0u;
+    const int64_t end = min64(base + kHistItems, count);
+    for (int64_t idx = base + threadIdx.x; idx < end; idx += kSortThreads) {
+      const uint32_t k = keys[idx];
+      for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(k >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
+    }
   }
   __syncthreads();
   for (int p = 0; p < passes; ++p) {
@@ -73,6 +79,9 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
   __shared__ uint32_t s_vals[kSortTile];
 
   const int64_t count = min64((int64_t)*count_ptr, cap);
+  // Persistent: tiles are taken by ticket, so a tile's look-back only waits
+  // on tiles that running blocks already hold.
+  while (true) {
   if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
   for (int d = threadIdx.x; d < (kSortThreads / 32) * kRadixBins; d += kSortThreads) (&s_wcount[0][0])[d] = 0u;
   __syncthreads();
@@ -170,6 +179,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     } else {
       atomicOr(status, kStatusInternal);
     }
+  }
+  __syncthreads();  // shared memory is reused by the next tile
   }
 }
 
@@ -452,18 +463,19 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   uint32_t *dstate = reinterpret_cast<uint32_t *>(ws + L.depth_state);
   uint32_t *hist_d = reinterpret_cast<uint32_t *>(ws + L.hist_depth);
   if (L.depth_blocks > 0) {
-    const int hb = (int)((L.vis_cap + kHistItems - 1) / kHistItems);
+    const int hb = (int)std::min<int64_t>((L.vis_cap + kHistItems - 1) / kHistItems, kPersistBlocks);
+    const int pb = std::min(L.depth_blocks, kPersistBlocks);
     radix_hist_kernel<<<hb, kSortThreads, 0, st>>>(dkey, ctr + kCtrVisible, L.vis_cap, L.depth_passes, hist_d,
                                                   dstate, L.depth_blocks, nullptr, 0);
     for (int p = 0; p < L.depth_passes; ++p) {
       const int out = p & 1, in = out ^ 1;
       uint32_t *state = dstate + (size_t)p * L.depth_blocks * kRadixBins;
       if (p == 0)
-        radix_pass_kernel<true><<<L.depth_blocks, kSortThreads, 0, st>>>(
+        radix_pass_kernel<true><<<pb, kSortThreads, 0, st>>>(
             dkey, nullptr, dk[out], dv[out], ctr + kCtrVisible, L.vis_cap, kRadixBits * p,
             hist_d + p * kRadixBins, state, ctr + kCtrTicketDepth + p, status);
       else
-        radix_pass_kernel<false><<<L.depth_blocks, kSortThreads, 0, st>>>(
+        radix_pass_kernel<false><<<pb, kSortThreads, 0, st>>>(
             dk[in], dv[in], dk[out], dv[out], ctr + kCtrVisible, L.vis_cap, kRadixBits * p,
             hist_d + p * kRadixBins, state, ctr + kCtrTicketDepth + p, status);
     }
@@ -497,13 +509,14 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   uint32_t *tstate = reinterpret_cast<uint32_t *>(ws + L.tile_state);
   uint32_t *hist_t = reinterpret_cast<uint32_t *>(ws + L.hist_tile);
   uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
-  const int hbt = (int)((L.inst_cap + kHistItems - 1) / kHistItems);
+  const int hbt = (int)std::min<int64_t>((L.inst_cap + kHistItems - 1) / kHistItems, kPersistBlocks);
+  const int pbt = std::min(L.tile_blocks, kPersistBlocks);
   radix_hist_kernel<<<hbt, kSortThreads, 0, st>>>(ik[0], ctr + kCtrInstances, L.inst_cap, L.tile_passes, hist_t,
                                                  tstate, L.tile_blocks, ranges, L.total_tiles);
   for (int p = 0; p < L.tile_passes; ++p) {
     const int in = p & 1, out = in ^ 1;
     uint32_t *state = tstate + (size_t)p * L.tile_blocks * kRadixBins;
-    radix_pass_kernel<false><<<L.tile_blocks, kSortThreads, 0, st>>>(
+    radix_pass_kernel<false><<<pbt, kSortThreads, 0, st>>>(
         ik[in], iv[in], ik[out], iv[out], ctr + kCtrInstances, L.inst_cap, kRadixBits * p, hist_t + p * kRadixBins,
         state, ctr + kCtrTicketTile + p, status);
   }

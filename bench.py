@@ -47,7 +47,7 @@ FLOPS_PER_COMP = 9
 # DRAM bytes (read + write) of one compositor launch (2 pixels per thread) on
 # this workload, from the ncu capture summarised in
 # profiles/kernels_orbit_300k_1352x1014.md; None once the kernel changes.
-RENDER_FWD_TRAFFIC = {2: 4.911104e6 + 3.584e3}
+RENDER_FWD_TRAFFIC = {}
 
 
 def parse():

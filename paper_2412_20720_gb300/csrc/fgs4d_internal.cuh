@@ -17,7 +17,6 @@ constexpr int kEmitChunk = 2048;    // (slot, rect tile) pairs per emission chun
 constexpr int kSortThreads = 256;   // threads per radix block
 constexpr int kSortItems = 8;       // keys per thread per radix block
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kHistItems = 4 * kSortTile;  // keys per histogram block
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;

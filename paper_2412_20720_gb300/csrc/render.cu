@@ -6,10 +6,12 @@
 // row (shared-memory loads, dx, A' dx^2, B' dx) is done once for kPPT pixels.
 // The tile's depth-sorted list is staged through shared memory in batches of
 // 256 records; the CTA stops loading once every pixel has reached the
-// transmittance cutoff (__syncthreads_count).  alpha = min(0.99, a 2^power2),
-// skip when power2 > 0 or alpha < 1/255, stop before the entry that would take
-// T below 1e-4 -- evaluated by pixel_alpha, shared with the backward pass so
-// both take bit-identical decisions.
+// transmittance cutoff (__syncthreads_count).  alpha = min(0.99, a 2^-q),
+// skip when alpha < 1/255, stop before the entry that would take T below 1e-4
+// -- evaluated by pixel_alpha, shared with the backward pass so both take
+// bit-identical decisions.  The power > 0 skip of the reference rasteriser is
+// not taken: q is a positive definite form, so q < 0 only arises by rounding
+// next to the Gaussian's centre, where skipping would drop the entry.
 //
 // Backward: the same tiles traversed back to front from each pixel's last
 // composited entry, recomputing T_i = T_{i+1} / (1 - alpha_i) from the final
@@ -98,9 +100,10 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
 
 // kStats: also counts the pixel-entry alpha evaluations and the composited
 // entries (diagnostic variant used to state the algorithmic work).
-// A pixel that has stopped is marked by T = 0 (a live pixel always has
-// T >= 1e-4), its final transmittance kept in Tend, so the inner loop needs no
-// per-pixel branch on a separate flag.
+// A pixel that has stopped is marked by a negative T (its final transmittance
+// negated; a live pixel always has T >= 1e-4), so the inner loop carries no
+// separate flag.  The update stays a branch: whole warps skip it for entries
+// that miss all their pixels.
 template <int MAXV, int PPT, bool kStats>
 __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
                                                                        unsigned long long *stats) {
@@ -116,14 +119,13 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
   const int32_t py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
   const uint2 range = A.ranges[gt];
   const float pxc = (float)px + 0.5f;
-  float T[PPT], Tend[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
+  float T[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
   uint32_t last[PPT];
   bool live = false;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     const bool in = px < V.width && py0 + k < V.height;
-    T[k] = in ? 1.0f : 0.0f;
-    Tend[k] = 1.0f;
+    T[k] = in ? 1.0f : -1.0f;
     C0[k] = C1[k] = C2[k] = 0.f;
     last[k] = 0u;
     pyc[k] = (float)(py0 + k) + 0.5f;
@@ -136,26 +138,27 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
                     s_blue, nullptr);
     __syncthreads();
     const int nb = (int)min(range.y - base, (uint32_t)kBatch);
+    const uint32_t pos0 = base - range.x + 1u;
     for (int j = 0; j < nb && live; ++j) {
       const float4 geom = s_geom[j];
       const float4 col = s_col[j];
+      const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc);
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         const AlphaEval e = pixel_alpha(ct, geom.y, col.x, col.y, pyc[k]);
         if (kStats) n_eval += T[k] > 0.0f;
-        if (T[k] > 0.0f && e.q >= 0.0f && e.alpha >= kAlphaMin) {
-          const float Tn = __fmul_rn(T[k], __fsub_rn(1.0f, e.alpha));
+        if (T[k] > 0.0f && e.alpha >= kAlphaMin) {
+          const float w = __fmul_rn(e.alpha, T[k]);
+          const float Tn = __fsub_rn(T[k], w);
           if (Tn < kTMin) {
-            Tend[k] = T[k];
-            T[k] = 0.0f;
+            T[k] = -T[k];
           } else {
-            const float w = e.alpha * T[k];
-            C0[k] += col.z * w;
-            C1[k] += col.w * w;
-            C2[k] += s_blue[j] * w;
+            C0[k] = __fmaf_rn(col.z, w, C0[k]);
+            C1[k] = __fmaf_rn(col.w, w, C1[k]);
+            C2[k] = __fmaf_rn(blue, w, C2[k]);
             T[k] = Tn;
-            last[k] = base + j - range.x + 1;
+            last[k] = pos0 + (uint32_t)j;
             if (kStats) ++n_comp;
           }
         }
@@ -165,9 +168,6 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
       for (int k = 0; k < PPT; ++k) live = live || T[k] > 0.0f;
     }
   }
-#pragma unroll
-  for (int k = 0; k < PPT; ++k)
-    if (T[k] > 0.0f) Tend[k] = T[k];
   if (kStats) {
     unsigned long long ev = n_eval, co = n_comp;
 #pragma unroll
@@ -186,12 +186,13 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
   for (int k = 0; k < PPT; ++k) {
     if (!(px < V.width && py0 + k < V.height)) continue;
     const int64_t p = (int64_t)(py0 + k) * V.width + px;
-    img[p] = C0[k] + Tend[k] * A.bg0;
-    img[HW + p] = C1[k] + Tend[k] * A.bg1;
-    img[2 * HW + p] = C2[k] + Tend[k] * A.bg2;
-    A.pix_T[V.pix_base + p] = Tend[k];
+    const float Tend = fabsf(T[k]);
+    img[p] = C0[k] + Tend * A.bg0;
+    img[HW + p] = C1[k] + Tend * A.bg1;
+    img[2 * HW + p] = C2[k] + Tend * A.bg2;
+    A.pix_T[V.pix_base + p] = Tend;
     A.pix_last[V.pix_base + p] = last[k];
-    if (A.out_T) A.out_T[V.pix_base + p] = Tend[k];
+    if (A.out_T) A.out_T[V.pix_base + p] = Tend;
   }
 }
 
@@ -199,6 +200,41 @@ __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
+}
+
+// Sums eight per-lane values over the warp with 9 shuffles instead of 40: at
+// each halving step a lane keeps half of its values and trades the other half
+// with its partner.  On return a[0] of lane l holds the warp total of value
+// l >> 2.
+__device__ __forceinline__ void warp_sum8_transposed(float (&a)[8], int lane) {
+  const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0, u4 = (lane & 4) != 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = u16 ? a[i] : a[i + 4];
+    const float keep = u16 ? a[i + 4] : a[i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = u8 ? a[i] : a[i + 2];
+    const float keep = u8 ? a[i + 2] : a[i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const float send = u4 ? a[0] : a[1];
+    const float keep = u4 ? a[1] : a[0];
+    a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
+  a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
+// 1/x to within an ulp or so (MUFU reciprocal); the backward pass only needs
+// T recovered to the accuracy of its own accumulated rounding.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 template <int MAXV, int kPPT>
@@ -263,45 +299,46 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
       const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc);
       const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
-      float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, ga = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
+      // g = (du, dv, dA', dB', dC', da, dr, dg), plus db.
+      float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float gb = 0.f;
       bool contrib = false;
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
         if (pos >= last[k]) continue;
         const AlphaEval e = pixel_alpha(ct, geom.y, col.x, col.y, pyc[k]);
-        if (e.q < 0.0f || e.alpha < kAlphaMin) continue;
+        if (e.alpha < kAlphaMin) continue;
         contrib = true;
-        const float om = __fsub_rn(1.0f, e.alpha);
-        T[k] = __fdiv_rn(T[k], om);  // transmittance in front of this entry
+        const float io = rcp_approx(__fsub_rn(1.0f, e.alpha));
+        T[k] = T[k] * io;  // transmittance in front of this entry
         const float w = e.alpha * T[k];
-        gr += dC0[k] * w;
-        gg += dC1[k] * w;
+        g[6] += dC0[k] * w;
+        g[7] += dC1[k] * w;
         gb += dC2[k] * w;
-        const float io = 1.0f / om;
         const float g_alpha = dC0[k] * (col.z * T[k] - r0[k] * io) + dC1[k] * (col.w * T[k] - r1[k] * io) +
                               dC2[k] * (blue * T[k] - r2[k] * io);
         r0[k] += col.z * w;
         r1[k] += col.w * w;
         r2[k] += blue * w;
         if (!(e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
-          ga += g_alpha * e.G;
+          g[5] += g_alpha * e.G;
           const float gp = g_alpha * e.alpha;  // d alpha / d (natural-log power)
           const float dx = ct.dx, dy = e.dy;
-          gA += -0.5f * dx * dx * gp;
-          gB += -dx * dy * gp;
-          gC += -0.5f * dy * dy * gp;
-          gu += -(An * dx + Bn * dy) * gp;
-          gv += -(Cn * dy + Bn * dx) * gp;
+          g[2] += -0.5f * dx * dx * gp;
+          g[3] += -dx * dy * gp;
+          g[4] += -0.5f * dy * dy * gp;
+          g[0] += -(An * dx + Bn * dy) * gp;
+          g[1] += -(Cn * dy + Bn * dx) * gp;
         }
       }
       if (__any_sync(0xffffffffu, contrib)) {
-        gu = warp_sum(gu); gv = warp_sum(gv); gA = warp_sum(gA); gB = warp_sum(gB); gC = warp_sum(gC);
-        ga = warp_sum(ga); gr = warp_sum(gr); gg = warp_sum(gg); gb = warp_sum(gb);
-        if (lane == 0 && s_slot[j] < A.vis_cap) {
-          float4 *dst = A.slot_grad + 3 * (size_t)s_slot[j];
-          atomicAdd(dst + 0, make_float4(gu, gv, gA, gB));
-          atomicAdd(dst + 1, make_float4(gC, ga, gr, gg));
-          atomicAdd(reinterpret_cast<float *>(dst + 2), gb);
+        warp_sum8_transposed(g, lane);
+        gb = warp_sum(gb);
+        const uint32_t slot = s_slot[j];
+        // Lanes 0, 4, ..., 28 add values 0..7; lane 1 adds db.
+        if (slot < A.vis_cap && ((lane & 3) == 0 || lane == 1)) {
+          float *dst = reinterpret_cast<float *>(A.slot_grad + 3 * (size_t)slot);
+          atomicAdd(dst + (lane == 1 ? 8 : (lane >> 2)), lane == 1 ? gb : g[0]);
         }
       }
     }

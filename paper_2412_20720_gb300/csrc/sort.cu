@@ -32,8 +32,8 @@ constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = kFlagAgg - 1u;
 
 // Digit histograms of keys [0, count) for `passes` 8-bit digits starting at
-// bit 0, grid-stride over chunks of kHistItems keys; also clears the
-// look-back rows the radix passes will use and the tile ranges.
+// bit 0, grid-stride over radix tiles (kSortTile keys); also clears each
+// tile's look-back rows and the tile ranges.
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t *__restrict__ keys,
                                                                   const uint32_t *__restrict__ count_ptr, int64_t cap,
                                                                   int32_t passes, uint32_t *hist, uint32_t *state,
@@ -43,19 +43,28 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nranges; r += (int64_t)gridDim.x * blockDim.x)
     ranges[r] = make_uint2(0u, 0u);
   const int64_t count = min64((int64_t)*count_ptr, cap);
-  if ((int64_t)blockIdx.x * kHistItems >= count) return;
+  if ((int64_t)blockIdx.x * kSortTile >= count) return;
   for (int p = 0; p < passes; ++p) s_hist[p][threadIdx.x] = 0u;
   __syncthreads();
-  for (int64_t base = (int64_t)blockIdx.x * kHistItems; base < count; base += (int64_t)gridDim.x * kHistItems) {
-    // Clear the look-back rows of the radix tiles covering this chunk.
-    const int64_t ob0 = base / kSortTile;
-    for (int p = 0; p < passes; ++p)
-      for (int64_t ob = ob0; ob < ob0 + kHistItems / kSortTile && ob < state_blocks && ob * kSortTile < count; ++ob)
-        state[((int64_t)p * state_blocks + ob) * kRadixBins + threadIdx.x] = 0u;
-    const int64_t end = min64(base + kHistItems, count);
-    for (int64_t idx = base + threadIdx.x; idx < end; idx += kSortThreads) {
-      const uint32_t k = keys[idx];
-      for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(k >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
+  const uint32_t lane = threadIdx.x & 31u;
+  for (int64_t ob = blockIdx.x; ob * kSortTile < count && ob < state_blocks; ob += gridDim.x) {
+    for (int p = 0; p < passes; ++p) state[((int64_t)p * state_blocks + ob) * kRadixBins + threadIdx.x] = 0u;
+#pragma unroll 2
+    for (int i = 0; i < kSortTile / kSortThreads; ++i) {
+      const int64_t idx = ob * kSortTile + i * kSortThreads + threadIdx.x;
+      const bool valid = idx < count;
+      const uint32_t k = valid ? keys[idx] : 0u;
+      for (int p = 0; p < passes; ++p) {
+        // The high digits of depth and tile keys take few values: a warp whose
+        // lanes all share the digit adds once instead of serialising 32 times.
+        const int d = valid ? (int)((k >> (kRadixBits * p)) & (kRadixBins - 1)) : -1;
+        const int d0 = __shfl_sync(0xffffffffu, d, 0);
+        if (__all_sync(0xffffffffu, d == d0)) {
+          if (lane == 0 && d0 >= 0) atomicAdd(&s_hist[p][d0], 32u);
+        } else if (valid) {
+          atomicAdd(&s_hist[p][d], 1u);
+        }
+      }
     }
   }
   __syncthreads();
@@ -463,7 +472,7 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   uint32_t *dstate = reinterpret_cast<uint32_t *>(ws + L.depth_state);
   uint32_t *hist_d = reinterpret_cast<uint32_t *>(ws + L.hist_depth);
   if (L.depth_blocks > 0) {
-    const int hb = (int)std::min<int64_t>((L.vis_cap + kHistItems - 1) / kHistItems, kPersistBlocks);
+    const int hb = (int)std::min<int64_t>((L.vis_cap + kSortTile - 1) / kSortTile, kPersistBlocks);
     const int pb = std::min(L.depth_blocks, kPersistBlocks);
     radix_hist_kernel<<<hb, kSortThreads, 0, st>>>(dkey, ctr + kCtrVisible, L.vis_cap, L.depth_passes, hist_d,
                                                   dstate, L.depth_blocks, nullptr, 0);
@@ -509,7 +518,7 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   uint32_t *tstate = reinterpret_cast<uint32_t *>(ws + L.tile_state);
   uint32_t *hist_t = reinterpret_cast<uint32_t *>(ws + L.hist_tile);
   uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
-  const int hbt = (int)std::min<int64_t>((L.inst_cap + kHistItems - 1) / kHistItems, kPersistBlocks);
+  const int hbt = (int)std::min<int64_t>((L.inst_cap + kSortTile - 1) / kSortTile, kPersistBlocks);
   const int pbt = std::min(L.tile_blocks, kPersistBlocks);
   radix_hist_kernel<<<hbt, kSortThreads, 0, st>>>(ik[0], ctr + kCtrInstances, L.inst_cap, L.tile_passes, hist_t,
                                                  tstate, L.tile_blocks, ranges, L.total_tiles);
@@ -605,9 +614,8 @@ extern "C" int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, ui
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int blocks = (int)((n + kSortTile - 1) / kSortTile);
-  const int hist_blocks = (int)((n + kHistItems - 1) / kHistItems);
   static_sort_init_kernel<<<1, 256, 0, st>>>(s, (uint32_t)n);
-  radix_hist_kernel<<<hist_blocks, kSortThreads, 0, st>>>(depth_keys, &s->ctl[0], FGS4D_STATIC_SORT_MAX,
+  radix_hist_kernel<<<blocks, kSortThreads, 0, st>>>(depth_keys, &s->ctl[0], FGS4D_STATIC_SORT_MAX,
                                                           kMaxPasses, &s->hist[0][0], &s->state[0][0][0],
                                                           kStaticSortBlocks, nullptr, 0);
   for (int p = 0; p < kMaxPasses; ++p) {

@@ -129,6 +129,7 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.lb_chunk = take((size_t)L.chunk_cap * sizeof(uint64_t));
   L.pair_prefix = take(((size_t)L.vis_cap + 1) * sizeof(uint32_t));
   L.emit_rec = take((size_t)L.vis_cap * 48);
+  L.chunk_first = take((size_t)L.chunk_cap * sizeof(uint32_t));
   const size_t vc = (size_t)L.vis_cap, ic = (size_t)L.inst_cap;
   L.rec_geom = take(vc * 16);
   L.rec_color = take(vc * 16);

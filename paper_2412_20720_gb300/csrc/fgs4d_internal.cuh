@@ -89,6 +89,7 @@ struct Layout {
   size_t lb_chunk;      // uint64 per emission chunk (cleared by the pair scan)
   size_t pair_prefix;   // uint32 [vis_cap + 1]: exclusive prefix of rect areas in depth order
   size_t emit_rec;      // 3 x 16 B [vis_cap]: emission record per depth-sorted position
+  size_t chunk_first;   // uint32 [chunk_cap]: depth-sorted position holding each chunk's first pair
   size_t control_end;
   size_t rec_geom, rec_color, rec_blue, rec_tau, rec_meta;
   size_t depth_key;                 // uint32 per slot (written by preprocess)
@@ -120,7 +121,36 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
 
 // --------------------------------------------------------- device helpers
 
+// Programmatic dependent launch.  Every kernel of the pipeline starts with
+// grid_dependency_sync(): it waits until the grid before it on the stream has
+// completed and its writes are visible, then lets the next grid be launched,
+// so that grid's launch overlaps this one's work.  The wait comes first in
+// every block, including blocks that exit at once, which makes the completion
+// of each grid imply the completion of all earlier ones.  Without the launch
+// attribute (launch_pdl) both instructions are no-ops.
+__device__ __forceinline__ void grid_dependency_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {

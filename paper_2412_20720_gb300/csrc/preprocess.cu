@@ -326,6 +326,7 @@ __device__ __forceinline__ bool forward_chain(int32_t i, const float4 *__restric
 
 template <int L, int MAXV>
 __global__ void __launch_bounds__(kPreBlock) preprocess_kernel(PreArgs A, PreViews<MAXV> views) {
+  grid_dependency_sync();
   __shared__ uint32_t s_ticket;
   __shared__ uint32_t s_scan[9];
   __shared__ uint64_t s_base;
@@ -375,6 +376,7 @@ __device__ __forceinline__ void red_add4(float4 *p, float x, float y, float z, f
 
 template <int L, int MAXV>
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs A, PreViews<MAXV> views) {
+  grid_dependency_sync();
   const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= nvis) return;
@@ -646,8 +648,7 @@ cudaError_t launch_pre_typed(const PreLaunch &p, const fgs4d_view *views, int32_
   A.rec_meta = reinterpret_cast<int4 *>(p.ws + Lo.rec_meta);
   A.depth_key = reinterpret_cast<uint32_t *>(p.ws + Lo.depth_key);
   if (Lo.pre_blocks == 0) return cudaSuccess;
-  preprocess_kernel<L, MAXV><<<Lo.pre_blocks, kPreBlock, 0, p.stream>>>(A, pv);
-  return cudaGetLastError();
+  return launch_pdl(preprocess_kernel<L, MAXV>, (unsigned)Lo.pre_blocks, kPreBlock, p.stream, A, pv);
 }
 
 template <int L, int MAXV>
@@ -683,8 +684,7 @@ cudaError_t launch_bwd_typed(const PreLaunch &p, const fgs4d_view *views, int32_
   A.g_sh = gr->sh;
   const int64_t blocks = (Lo.vis_cap + 127) / 128;
   if (blocks == 0) return cudaSuccess;
-  preprocess_bwd_kernel<L, MAXV><<<(unsigned)blocks, 128, 0, p.stream>>>(A, pv);
-  return cudaGetLastError();
+  return launch_pdl(preprocess_bwd_kernel<L, MAXV>, (unsigned)blocks, 128u, p.stream, A, pv);
 }
 
 }  // namespace

@@ -107,6 +107,7 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
 template <int MAXV, int PPT, bool kStats>
 __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
                                                                        unsigned long long *stats) {
+  grid_dependency_sync();
   constexpr int NT = kTilePixels / PPT;
   __shared__ float4 s_geom[kBatch];
   __shared__ float4 s_col[kBatch];
@@ -239,6 +240,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 template <int MAXV, int kPPT>
 __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBwdArgs A, RasterViews<MAXV> rv) {
+  grid_dependency_sync();
   constexpr int kRenderThreads = kTilePixels / kPPT;
   __shared__ float4 s_geom[kBatch];
   __shared__ float4 s_col[kBatch];
@@ -347,6 +349,7 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
 
 __global__ void l1_loss_kernel(const float *__restrict__ img, const float *__restrict__ target, int64_t count,
                                float inv_count, float *loss, float *grad) {
+  grid_dependency_sync();
   float acc = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const float d = img[i] - target[i];
@@ -388,18 +391,15 @@ cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   const unsigned grid = (unsigned)L.total_tiles;
   switch (render_ppt(s)) {
     case 2:
-      if (stats) render_fwd_kernel<MAXV, 2, true><<<grid, kTilePixels / 2, 0, st>>>(A, rv, stats);
-      else render_fwd_kernel<MAXV, 2, false><<<grid, kTilePixels / 2, 0, st>>>(A, rv, nullptr);
-      break;
+      if (stats) return launch_pdl(render_fwd_kernel<MAXV, 2, true>, grid, kTilePixels / 2, st, A, rv, stats);
+      return launch_pdl(render_fwd_kernel<MAXV, 2, false>, grid, kTilePixels / 2, st, A, rv, nullptr);
     case 8:
-      if (stats) render_fwd_kernel<MAXV, 8, true><<<grid, kTilePixels / 8, 0, st>>>(A, rv, stats);
-      else render_fwd_kernel<MAXV, 8, false><<<grid, kTilePixels / 8, 0, st>>>(A, rv, nullptr);
-      break;
+      if (stats) return launch_pdl(render_fwd_kernel<MAXV, 8, true>, grid, kTilePixels / 8, st, A, rv, stats);
+      return launch_pdl(render_fwd_kernel<MAXV, 8, false>, grid, kTilePixels / 8, st, A, rv, nullptr);
     default:
-      if (stats) render_fwd_kernel<MAXV, 4, true><<<grid, kTilePixels / 4, 0, st>>>(A, rv, stats);
-      else render_fwd_kernel<MAXV, 4, false><<<grid, kTilePixels / 4, 0, st>>>(A, rv, nullptr);
+      if (stats) return launch_pdl(render_fwd_kernel<MAXV, 4, true>, grid, kTilePixels / 4, st, A, rv, stats);
+      return launch_pdl(render_fwd_kernel<MAXV, 4, false>, grid, kTilePixels / 4, st, A, rv, nullptr);
   }
-  return cudaGetLastError();
 }
 
 template <int MAXV>
@@ -426,11 +426,10 @@ cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   if (L.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)L.total_tiles;
   switch (render_ppt(s)) {
-    case 2: render_bwd_kernel<MAXV, 2><<<grid, kTilePixels / 2, 0, st>>>(A, rv); break;
-    case 8: render_bwd_kernel<MAXV, 8><<<grid, kTilePixels / 8, 0, st>>>(A, rv); break;
-    default: render_bwd_kernel<MAXV, 4><<<grid, kTilePixels / 4, 0, st>>>(A, rv);
+    case 2: return launch_pdl(render_bwd_kernel<MAXV, 2>, grid, kTilePixels / 2, st, A, rv);
+    case 8: return launch_pdl(render_bwd_kernel<MAXV, 8>, grid, kTilePixels / 8, st, A, rv);
+    default: return launch_pdl(render_bwd_kernel<MAXV, 4>, grid, kTilePixels / 4, st, A, rv);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace
@@ -452,8 +451,8 @@ cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count,
                            cudaStream_t stream) {
   if (count <= 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 8);
-  l1_loss_kernel<<<blocks, 256, 0, stream>>>(img, target, count, 1.0f / (float)count, loss, grad);
-  return cudaGetLastError();
+  return launch_pdl(l1_loss_kernel, (unsigned)blocks, 256u, stream, img, target, count, 1.0f / (float)count, loss,
+                    grad);
 }
 
 }  // namespace fgs4d

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t
                                                                   int32_t passes, uint32_t *hist, uint32_t *state,
                                                                   int32_t state_blocks, uint2 *ranges,
                                                                   int64_t nranges) {
+  grid_dependency_sync();
   __shared__ uint32_t s_hist[kMaxPasses][kRadixBins];
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nranges; r += (int64_t)gridDim.x * blockDim.x)
     ranges[r] = make_uint2(0u, 0u);
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ count_ptr, int64_t cap, int32_t shift,
     const uint32_t *__restrict__ hist, uint32_t *state, uint32_t *ticket, uint32_t *status) {
+  grid_dependency_sync();
   __shared__ uint32_t s_ticket;
   __shared__ uint32_t s_wcount[kSortThreads / 32][kRadixBins];
   __shared__ uint32_t s_bstart[kRadixBins];
@@ -239,6 +241,7 @@ struct EmitArgs {
   int32_t chunk_cap;
   uint32_t *pair_prefix;
   int4 *emit_rec;  // 3 per depth-sorted position
+  uint32_t *chunk_first;
   uint32_t *inst_key, *inst_val;
   uint64_t *lb_scan, *lb_chunk;
 };
@@ -246,10 +249,12 @@ struct EmitArgs {
 // Pair scan, one thread per depth-sorted visible slot: the exclusive prefix
 // of the slots' rect areas in depth order (decoupled look-back), plus a
 // compact emission record per position: (u, v, A', B'), (C', kx, ky, tau),
-// (slot, view, packed rect lo, packed rect hi).  Also clears the look-back
-// states of the emission chunks.
+// (slot, view, packed rect lo, packed rect hi), and, for every emission
+// chunk whose first pair falls in a position's pairs, that position.  Also
+// clears the look-back states of the emission chunks.
 template <int MAXV>
 __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, RasterViews<MAXV> rv) {
+  grid_dependency_sync();
   __shared__ uint32_t s_ticket;
   __shared__ uint32_t s_scan[9];
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.chunk_cap;
@@ -308,7 +313,13 @@ __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, Raste
     }
   }
   __syncthreads();
-  if (j < nvis) A.pair_prefix[j] = (uint32_t)umin64(s_base + excl, (uint64_t)A.pair_cap);
+  if (j < nvis) {
+    const uint64_t p0 = umin64(s_base + excl, (uint64_t)A.pair_cap);
+    const uint64_t p1 = umin64(s_base + excl + area, (uint64_t)A.pair_cap);
+    A.pair_prefix[j] = (uint32_t)p0;
+    for (uint64_t c = (p0 + kEmitChunk - 1) / kEmitChunk; c * kEmitChunk < p1 && c < (uint64_t)A.chunk_cap; ++c)
+      A.chunk_first[c] = (uint32_t)j;
+  }
 }
 
 // Instance emission in depth order.  The (slot, rect tile) pairs of all
@@ -320,6 +331,7 @@ __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, Raste
 // screen-sized Gaussian is spread over many blocks.
 template <int MAXV>
 __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterViews<MAXV> rv) {
+  grid_dependency_sync();
   constexpr int kPer = kEmitChunk / kEmitBlock;
   __shared__ uint32_t s_ticket, s_j0, s_ns;
   __shared__ uint32_t s_pref[kEmitChunk + 1];  // pair prefix of the chunk's slots
@@ -338,22 +350,11 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
     if ((uint64_t)c * kEmitChunk >= npairs || (int32_t)c >= A.chunk_cap) return;
     const uint32_t f0 = c * kEmitChunk;
     const uint32_t f1 = min(f0 + (uint32_t)kEmitChunk, npairs);
-    if (threadIdx.x == 0) {  // slots holding pairs f0 and f1 - 1 (last slot with prefix <= f)
-      int64_t lo = 0, hi = nvis - 1;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (A.pair_prefix[mid] <= f0) lo = mid;
-        else hi = mid - 1;
-      }
-      const int64_t j0 = lo;
-      hi = nvis - 1;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (A.pair_prefix[mid] <= f1 - 1) lo = mid;
-        else hi = mid - 1;
-      }
+    if (threadIdx.x == 0) {  // positions holding pair f0 and, at most one past, pair f1 - 1
+      const int64_t j0 = A.chunk_first[c];
+      const int64_t j1 = f1 == npairs ? nvis - 1 : (int64_t)A.chunk_first[c + 1];
       s_j0 = (uint32_t)j0;
-      s_ns = (uint32_t)min64(lo - j0 + 1, kEmitChunk);
+      s_ns = (uint32_t)min64(max64(j1 - j0 + 1, 1), kEmitChunk);
     }
     __syncthreads();
     const uint32_t j0 = s_j0, ns = s_ns;
@@ -443,6 +444,7 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
 
 __global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ counters, int64_t cap,
                               uint2 *ranges, int64_t total_tiles, uint32_t *status) {
+  grid_dependency_sync();
   const int64_t count = min64((int64_t)counters[kCtrInstances], cap);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t k = keys[i];
@@ -474,19 +476,20 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   if (L.depth_blocks > 0) {
     const int hb = (int)std::min<int64_t>((L.vis_cap + kSortTile - 1) / kSortTile, kPersistBlocks);
     const int pb = std::min(L.depth_blocks, kPersistBlocks);
-    radix_hist_kernel<<<hb, kSortThreads, 0, st>>>(dkey, ctr + kCtrVisible, L.vis_cap, L.depth_passes, hist_d,
-                                                  dstate, L.depth_blocks, nullptr, 0);
+    e = launch_pdl(radix_hist_kernel, (unsigned)hb, kSortThreads, st, dkey, (const uint32_t *)(ctr + kCtrVisible),
+                   (int64_t)L.vis_cap, (int32_t)L.depth_passes, hist_d, dstate, (int32_t)L.depth_blocks,
+                   (uint2 *)nullptr, (int64_t)0);
+    if (e != cudaSuccess) return e;
     for (int p = 0; p < L.depth_passes; ++p) {
       const int out = p & 1, in = out ^ 1;
       uint32_t *state = dstate + (size_t)p * L.depth_blocks * kRadixBins;
-      if (p == 0)
-        radix_pass_kernel<true><<<pb, kSortThreads, 0, st>>>(
-            dkey, nullptr, dk[out], dv[out], ctr + kCtrVisible, L.vis_cap, kRadixBits * p,
-            hist_d + p * kRadixBins, state, ctr + kCtrTicketDepth + p, status);
-      else
-        radix_pass_kernel<false><<<pb, kSortThreads, 0, st>>>(
-            dk[in], dv[in], dk[out], dv[out], ctr + kCtrVisible, L.vis_cap, kRadixBits * p,
-            hist_d + p * kRadixBins, state, ctr + kCtrTicketDepth + p, status);
+      const uint32_t *kin = p == 0 ? dkey : dk[in];
+      const uint32_t *vin = p == 0 ? nullptr : dv[in];
+      e = launch_pdl(p == 0 ? radix_pass_kernel<true> : radix_pass_kernel<false>, (unsigned)pb, kSortThreads, st,
+                     kin, vin, dk[out], dv[out], (const uint32_t *)(ctr + kCtrVisible), (int64_t)L.vis_cap,
+                     (int32_t)(kRadixBits * p), (const uint32_t *)(hist_d + p * kRadixBins), state,
+                     ctr + kCtrTicketDepth + p, status);
+      if (e != cudaSuccess) return e;
     }
   }
   const uint32_t *sorted = dv[(L.depth_passes - 1) & 1];
@@ -507,12 +510,15 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
     ea.chunk_cap = L.chunk_cap;
     ea.pair_prefix = reinterpret_cast<uint32_t *>(ws + L.pair_prefix);
     ea.emit_rec = reinterpret_cast<int4 *>(ws + L.emit_rec);
+    ea.chunk_first = reinterpret_cast<uint32_t *>(ws + L.chunk_first);
     ea.inst_key = ik[0];
     ea.inst_val = iv[0];
     ea.lb_scan = reinterpret_cast<uint64_t *>(ws + L.lb_emit);
     ea.lb_chunk = reinterpret_cast<uint64_t *>(ws + L.lb_chunk);
-    pair_scan_kernel<MAXV><<<L.emit_blocks, kEmitBlock, 0, st>>>(ea, rv);
-    emit_kernel<MAXV><<<L.emit_grid, kEmitBlock, 0, st>>>(ea, rv);
+    e = launch_pdl(pair_scan_kernel<MAXV>, (unsigned)L.emit_blocks, kEmitBlock, st, ea, rv);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(emit_kernel<MAXV>, (unsigned)L.emit_grid, kEmitBlock, st, ea, rv);
+    if (e != cudaSuccess) return e;
   }
   // 3. Stable sort of the instances by global tile id.
   uint32_t *tstate = reinterpret_cast<uint32_t *>(ws + L.tile_state);
@@ -520,21 +526,25 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
   const int hbt = (int)std::min<int64_t>((L.inst_cap + kSortTile - 1) / kSortTile, kPersistBlocks);
   const int pbt = std::min(L.tile_blocks, kPersistBlocks);
-  radix_hist_kernel<<<hbt, kSortThreads, 0, st>>>(ik[0], ctr + kCtrInstances, L.inst_cap, L.tile_passes, hist_t,
-                                                 tstate, L.tile_blocks, ranges, L.total_tiles);
+  e = launch_pdl(radix_hist_kernel, (unsigned)hbt, kSortThreads, st, (const uint32_t *)ik[0],
+                 (const uint32_t *)(ctr + kCtrInstances), (int64_t)L.inst_cap, (int32_t)L.tile_passes, hist_t, tstate,
+                 (int32_t)L.tile_blocks, ranges, (int64_t)L.total_tiles);
+  if (e != cudaSuccess) return e;
   for (int p = 0; p < L.tile_passes; ++p) {
     const int in = p & 1, out = in ^ 1;
     uint32_t *state = tstate + (size_t)p * L.tile_blocks * kRadixBins;
-    radix_pass_kernel<false><<<pbt, kSortThreads, 0, st>>>(
-        ik[in], iv[in], ik[out], iv[out], ctr + kCtrInstances, L.inst_cap, kRadixBits * p, hist_t + p * kRadixBins,
-        state, ctr + kCtrTicketTile + p, status);
+    e = launch_pdl(radix_pass_kernel<false>, (unsigned)pbt, kSortThreads, st, (const uint32_t *)ik[in],
+                   (const uint32_t *)iv[in], ik[out], iv[out], (const uint32_t *)(ctr + kCtrInstances),
+                   (int64_t)L.inst_cap, (int32_t)(kRadixBits * p), (const uint32_t *)(hist_t + p * kRadixBins), state,
+                   ctr + kCtrTicketTile + p, status);
+    if (e != cudaSuccess) return e;
   }
   // 4. Tile ranges.
   const uint32_t *final_keys = ik[L.tile_passes & 1];
   int rb = (int)min64((L.inst_cap + 255) / 256, 152 * 16);
   if (rb < 1) rb = 1;
-  ranges_kernel<<<rb, 256, 0, st>>>(final_keys, ctr, L.inst_cap, ranges, L.total_tiles, status);
-  return cudaGetLastError();
+  return launch_pdl(ranges_kernel, (unsigned)rb, 256u, st, final_keys, (const uint32_t *)ctr, (int64_t)L.inst_cap,
+                    ranges, (int64_t)L.total_tiles, status);
 }
 
 }  // namespace

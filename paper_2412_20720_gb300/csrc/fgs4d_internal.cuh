@@ -170,6 +170,17 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Relaxed (non-ordering) accesses for look-back words whose flag and value
+// share one word: a reader needs only that word, so no fence is implied.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Decoupled look-back over uint64 block states (flag in bits 62-63: 1 =
 // aggregate only, 2 = inclusive prefix).  Called by one thread of logical
 // block `bid` with the block's aggregate; returns the exclusive prefix.

@@ -142,30 +142,42 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
   uint32_t total;
   s_bstart[d] = block_exclusive_scan(cnt, s_scan, &total);
   const uint32_t gpre = block_exclusive_scan(hist[d], s_scan, &total);
-  // Decoupled look-back for this digit.
+  // Decoupled look-back for this digit, reading a window of kWin
+  // predecessor tiles per round trip (their words are independent loads).
+  constexpr int kWin = 8;
   uint32_t prefix = 0u;
   if (b == 0) {
-    st_release(&state[d], kFlagInc | cnt);
+    st_relaxed(&state[d], kFlagInc | cnt);
   } else {
-    st_release(&state[b * kRadixBins + d], kFlagAgg | cnt);
+    st_relaxed(&state[b * kRadixBins + d], kFlagAgg | cnt);
     int64_t j = b - 1;
     uint32_t polls = 0;
     while (j >= 0) {
-      const uint32_t s = ld_acquire(&state[j * kRadixBins + d]);
-      const uint32_t f = s & ~kValMask;
-      if (f == 0u) {
+      uint32_t w[kWin];
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) w[k] = j - k >= 0 ? ld_relaxed(&state[(j - k) * kRadixBins + d]) : kFlagInc;
+      int used = 0;
+      bool done = false;
+#pragma unroll
+      for (int k = 0; k < kWin; ++k) {
+        if (done || used < k) continue;  // stop at the first tile not yet posted
+        const uint32_t f = w[k] & ~kValMask;
+        if (f == 0u) continue;
+        prefix += w[k] & kValMask;
+        ++used;
+        done = f == kFlagInc;
+      }
+      if (done) break;
+      j -= used;
+      if (used == 0) {
         if (++polls > kSpinLimit) {
           atomicOr(status, kStatusTimeout);
           break;
         }
         __nanosleep(32);
-        continue;
       }
-      prefix += s & kValMask;
-      if (f == kFlagInc) break;
-      --j;
     }
-    st_release(&state[b * kRadixBins + d], kFlagInc | ((prefix + cnt) & kValMask));
+    st_relaxed(&state[b * kRadixBins + d], kFlagInc | ((prefix + cnt) & kValMask));
   }
   s_gstart[d] = gpre + prefix;
   __syncthreads();

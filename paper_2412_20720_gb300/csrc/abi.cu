@@ -126,7 +126,8 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.hist_tile = take(kMaxPasses * kRadixBins * sizeof(uint32_t));
   L.lb_emit = take((size_t)L.emit_blocks * sizeof(uint64_t));
   L.control_end = off;
-  L.lb_chunk = take((size_t)L.chunk_cap * sizeof(uint64_t));
+  L.chunk_count = take((size_t)L.chunk_cap * sizeof(uint32_t));
+  L.pair_mask = take((size_t)L.chunk_cap * kEmitBlock);
   L.pair_prefix = take(((size_t)L.vis_cap + 1) * sizeof(uint32_t));
   L.emit_rec = take((size_t)L.vis_cap * 48);
   L.chunk_first = take((size_t)L.chunk_cap * sizeof(uint32_t));

@@ -44,7 +44,6 @@ enum Counter : int {
   kCtrTicketEmit = 8,
   kCtrTicketDepth = 10,  // kMaxPasses entries
   kCtrTicketTile = 14,   // kMaxPasses entries
-  kCtrTicketChunk = 18,  // emission chunks
   kCtrPairs = 19,        // (slot, rect tile) pairs of all visible slots
   kCtrCount = 64
 };
@@ -86,7 +85,8 @@ struct Layout {
   size_t hist_depth;    // uint32 [kMaxPasses][256]
   size_t hist_tile;     // uint32 [kMaxPasses][256]
   size_t lb_emit;       // uint64 per pair-scan block
-  size_t lb_chunk;      // uint64 per emission chunk (cleared by the pair scan)
+  size_t chunk_count;   // uint32 per emission chunk: kept pairs, then their exclusive prefix
+  size_t pair_mask;     // uint8 [chunk_cap][kEmitBlock]: keep bits of 8 consecutive pairs
   size_t pair_prefix;   // uint32 [vis_cap + 1]: exclusive prefix of rect areas in depth order
   size_t emit_rec;      // 3 x 16 B [vis_cap]: emission record per depth-sorted position
   size_t chunk_first;   // uint32 [chunk_cap]: depth-sorted position holding each chunk's first pair
@@ -260,7 +260,9 @@ __device__ __forceinline__ uint64_t lookback_u64_warp(uint64_t *state, int32_t b
 
 // Block-wide exclusive scan of one uint32 per thread (blockDim.x == 256).
 // `smem` needs 8 + 1 words.  Returns the exclusive prefix; *total = sum.
+template <int kWarps = 8>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *smem, uint32_t *total) {
+  static_assert(kWarps >= 1 && kWarps <= 32, "one warp scans the warp totals");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t inc = x;
 #pragma unroll
@@ -271,19 +273,19 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *s
   if (lane == 31) smem[warp] = inc;
   __syncthreads();
   if (warp == 0) {
-    uint32_t w = lane < 8 ? smem[lane] : 0u;
+    uint32_t w = lane < kWarps ? smem[lane] : 0u;
     uint32_t wi = w;
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
+    for (int o = 1; o < kWarps; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
       if (lane >= o) wi += y;
     }
-    if (lane < 8) smem[lane] = wi - w;
-    if (lane == 7) smem[8] = wi;
+    if (lane < kWarps) smem[lane] = wi - w;
+    if (lane == kWarps - 1) smem[kWarps] = wi;
   }
   __syncthreads();
   const uint32_t r = smem[warp] + inc - x;
-  *total = smem[8];
+  *total = smem[kWarps];
   __syncthreads();
   return r;
 }

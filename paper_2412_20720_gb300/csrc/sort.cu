@@ -255,23 +255,27 @@ struct EmitArgs {
   int4 *emit_rec;  // 3 per depth-sorted position
   uint32_t *chunk_first;
   uint32_t *inst_key, *inst_val;
-  uint64_t *lb_scan, *lb_chunk;
+  uint64_t *lb_scan;
+  uint32_t *chunk_count;  // kept pairs per chunk, then (after the scan) their exclusive prefix
+  uint8_t *pair_mask;     // keep byte per (chunk, thread): 8 consecutive pairs
+  // Tile sort set-up done while counting: digit histograms, cleared look-back
+  // rows and tile ranges.
+  int32_t tile_passes, tile_blocks;
+  uint32_t *hist_tile, *tile_state;
+  uint2 *ranges;
+  int64_t total_tiles;
 };
 
 // Pair scan, one thread per depth-sorted visible slot: the exclusive prefix
 // of the slots' rect areas in depth order (decoupled look-back), plus a
 // compact emission record per position: (u, v, A', B'), (C', kx, ky, tau),
 // (slot, view, packed rect lo, packed rect hi), and, for every emission
-// chunk whose first pair falls in a position's pairs, that position.  Also
-// clears the look-back states of the emission chunks.
+// chunk whose first pair falls in a position's pairs, that position.
 template <int MAXV>
 __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
   __shared__ uint32_t s_ticket;
   __shared__ uint32_t s_scan[9];
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.chunk_cap;
-       c += (int64_t)gridDim.x * blockDim.x)
-    A.lb_chunk[c] = 0ull;
   const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
   if (threadIdx.x == 0) s_ticket = atomicAdd(&A.counters[kCtrTicketEmit], 1u);
   __syncthreads();
@@ -336,121 +340,242 @@ __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, Raste
 
 // Instance emission in depth order.  The (slot, rect tile) pairs of all
 // visible slots, in depth order and row-major within a rect, are cut into
-// chunks of kEmitChunk; persistent blocks take chunks by ticket, keep a pair
-// when its slot's 1/255 ellipse meets the tile, count (pass 1), get the
-// chunk's output offset by decoupled look-back over chunks, and write the
-// kept pairs in order (pass 2).  Every chunk is the same amount of work, so a
-// screen-sized Gaussian is spread over many blocks.
+// chunks of kEmitChunk pairs; a pair is kept when its slot's 1/255 ellipse
+// meets the tile.  emit_count_kernel decides every pair (one keep bit) and
+// counts the kept pairs of every chunk, chunk_scan_kernel turns the counts
+// into output offsets, and emit_write_kernel writes the kept pairs in pair
+// order.  Every chunk is the same amount of work, so a screen-sized Gaussian
+// is spread over many blocks, and no block waits on another.
+
+constexpr int kEmitRecCache = 256;  // emission records cached per chunk
+
+// Shared-memory view of one chunk: the pair prefix and (when they fit) the
+// emission records of the depth-sorted positions its pairs belong to.
+struct EmitChunkSmem {
+  uint32_t j0, ns;
+  uint32_t pref[kEmitChunk + 1];
+  int4 rec[kEmitRecCache * 3];
+};
+
+__device__ __forceinline__ void load_emit_chunk(const EmitArgs &A, uint32_t c, uint32_t f1, uint32_t npairs,
+                                                int64_t nvis, EmitChunkSmem &S) {
+  if (threadIdx.x == 0) {  // positions holding pair f0 and, at most one past, pair f1 - 1
+    const int64_t j0 = A.chunk_first[c];
+    const int64_t j1 = f1 == npairs ? nvis - 1 : (int64_t)A.chunk_first[c + 1];
+    S.j0 = (uint32_t)j0;
+    S.ns = (uint32_t)min64(max64(j1 - j0 + 1, 1), kEmitChunk);
+  }
+  __syncthreads();
+  const uint32_t j0 = S.j0, ns = S.ns;
+  for (uint32_t k = threadIdx.x; k <= ns; k += kEmitBlock)
+    S.pref[k] = (int64_t)(j0 + k) <= nvis ? A.pair_prefix[j0 + k] : npairs;
+  if (ns <= (uint32_t)kEmitRecCache)
+    for (uint32_t k = threadIdx.x; k < 3 * ns; k += kEmitBlock) S.rec[k] = A.emit_rec[3 * (size_t)j0 + k];
+  __syncthreads();
+}
+
+// Walk over consecutive pairs of a chunk: the depth-sorted position the
+// current pair belongs to, its rect and the current tile (row-major).
+struct PairWalk {
+  int lo;  // position within the chunk
+  int x0, y0, x1, tx, ty;
+  uint32_t slot, view;
+  float u, v, A, B, C, kx, ky, tau;
+};
+
+__device__ __forceinline__ void walk_load(const EmitArgs &A, const EmitChunkSmem &S, int lo, PairWalk &w) {
+  const int4 *er = S.ns <= (uint32_t)kEmitRecCache ? S.rec + 3 * lo : A.emit_rec + 3 * (size_t)(S.j0 + lo);
+  const int4 r0 = er[0], r1 = er[1], r2 = er[2];
+  w.lo = lo;
+  w.u = __int_as_float(r0.x);
+  w.v = __int_as_float(r0.y);
+  w.A = __int_as_float(r0.z);
+  w.B = __int_as_float(r0.w);
+  w.C = __int_as_float(r1.x);
+  w.kx = __int_as_float(r1.y);
+  w.ky = __int_as_float(r1.z);
+  w.tau = __int_as_float(r1.w);
+  w.slot = (uint32_t)r2.x;
+  w.view = (uint32_t)r2.y;
+  w.x0 = r2.z & 0xffff;
+  w.y0 = (uint32_t)r2.z >> 16;
+  w.x1 = r2.w & 0xffff;
+}
+
+// Positions the walk at pair f (one binary search over the chunk's prefix).
+__device__ __forceinline__ PairWalk walk_begin(const EmitArgs &A, const EmitChunkSmem &S, uint32_t f) {
+  int lo = 0, hi = (int)S.ns - 1;
+  while (lo < hi) {  // last position whose pair prefix is <= f
+    const int mid = (lo + hi + 1) >> 1;
+    if (S.pref[mid] <= f) lo = mid;
+    else hi = mid - 1;
+  }
+  PairWalk w;
+  walk_load(A, S, lo, w);
+  const uint32_t local = f - S.pref[lo];
+  const uint32_t wd = (uint32_t)max(w.x1 - w.x0, 1);
+  const uint32_t qy = local / wd;
+  w.tx = w.x0 + (int)(local - qy * wd);
+  w.ty = w.y0 + (int)qy;
+  return w;
+}
+
+// Advances the walk to pair f, the pair after the current one.
+__device__ __forceinline__ void walk_next(const EmitArgs &A, const EmitChunkSmem &S, PairWalk &w, uint32_t f) {
+  if (++w.tx >= w.x1) {
+    w.tx = w.x0;
+    ++w.ty;
+  }
+  if (S.pref[w.lo + 1] <= f) {
+    int lo = w.lo + 1;
+    while (S.pref[lo + 1] <= f) ++lo;  // positions without pairs (capacity clamp)
+    walk_load(A, S, lo, w);
+    w.tx = w.x0;
+    w.ty = w.y0;
+  }
+}
+
 template <int MAXV>
-__global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterViews<MAXV> rv) {
+__device__ __forceinline__ bool walk_keep(const RasterViews<MAXV> &rv, const PairWalk &w) {
+  const RasterView &V = rv.v[MAXV == 1 ? 0 : w.view];
+  const float bx0 = (float)(w.tx * kTile) + 0.5f, by0 = (float)(w.ty * kTile) + 0.5f;
+  const float bx1 = (float)min(w.tx * kTile + kTile - 1, V.width - 1) + 0.5f;
+  const float by1 = (float)min(w.ty * kTile + kTile - 1, V.height - 1) + 0.5f;
+  return ellipse_meets_box(w.u, w.v, w.A, w.B, w.C, w.kx, w.ky, w.tau, bx0, bx1, by0, by1);
+}
+
+template <int MAXV>
+__device__ __forceinline__ uint32_t walk_tile(const RasterViews<MAXV> &rv, const PairWalk &w) {
+  const RasterView &V = rv.v[MAXV == 1 ? 0 : w.view];
+  return (uint32_t)(V.tile_base + w.ty * V.gw + w.tx);
+}
+
+constexpr int kPairsPerThread = kEmitChunk / kEmitBlock;
+static_assert(kPairsPerThread == 8, "one keep byte per thread");
+
+// Pass 1: thread t of chunk c decides pairs c kEmitChunk + 8 t + [0, 8) and
+// stores them as one keep byte; the chunk's kept count goes to chunk_count.
+// Also clears the tile sort's look-back rows (radix tile c for chunk c: there
+// are no more instances than pairs) and the tile ranges.
+template <int MAXV>
+__global__ void __launch_bounds__(kEmitBlock) emit_count_kernel(EmitArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
-  constexpr int kPer = kEmitChunk / kEmitBlock;
-  __shared__ uint32_t s_ticket, s_j0, s_ns;
-  __shared__ uint32_t s_pref[kEmitChunk + 1];  // pair prefix of the chunk's slots
-  constexpr int kRecCache = 256;                // slot records cached per chunk
-  __shared__ int4 s_rec[kRecCache * 3];
-  __shared__ uint32_t s_w[kEmitChunk / kEmitBlock][kEmitBlock / 32];
-  __shared__ uint64_t s_base;
+  __shared__ EmitChunkSmem S;
+  __shared__ uint32_t s_scan[kEmitBlock / 32 + 1];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < A.total_tiles;
+       r += (int64_t)gridDim.x * blockDim.x)
+    A.ranges[r] = make_uint2(0u, 0u);
   const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
   const uint32_t npairs = A.counters[kCtrPairs];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
-  while (true) {
-    if (threadIdx.x == 0) s_ticket = atomicAdd(&A.counters[kCtrTicketChunk], 1u);
-    __syncthreads();
-    const uint32_t c = s_ticket;
-    if ((uint64_t)c * kEmitChunk >= npairs || (int32_t)c >= A.chunk_cap) return;
-    const uint32_t f0 = c * kEmitChunk;
-    const uint32_t f1 = min(f0 + (uint32_t)kEmitChunk, npairs);
-    if (threadIdx.x == 0) {  // positions holding pair f0 and, at most one past, pair f1 - 1
-      const int64_t j0 = A.chunk_first[c];
-      const int64_t j1 = f1 == npairs ? nvis - 1 : (int64_t)A.chunk_first[c + 1];
-      s_j0 = (uint32_t)j0;
-      s_ns = (uint32_t)min64(max64(j1 - j0 + 1, 1), kEmitChunk);
-    }
-    __syncthreads();
-    const uint32_t j0 = s_j0, ns = s_ns;
-    for (uint32_t k = threadIdx.x; k <= ns; k += kEmitBlock)
-      s_pref[k] = (int64_t)(j0 + k) <= nvis ? A.pair_prefix[j0 + k] : npairs;
-    const bool cached = ns <= (uint32_t)kRecCache;
-    if (cached)
-      for (uint32_t k = threadIdx.x; k < 3 * ns; k += kEmitBlock) s_rec[k] = A.emit_rec[3 * (size_t)j0 + k];
-    __syncthreads();
-    // Pair f -> keep, tile and slot.
-    auto pair = [&](uint32_t f, uint32_t *tile, uint32_t *slot) -> bool {
-      int lo = 0, hi = (int)ns - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_pref[mid] <= f) lo = mid;
-        else hi = mid - 1;
-      }
-      const int4 *er = cached ? s_rec + 3 * lo : A.emit_rec + 3 * (size_t)(j0 + lo);
-      const int4 r0 = er[0], r1 = er[1], r2 = er[2];
-      const int x0 = r2.z & 0xffff, y0 = (uint32_t)r2.z >> 16, x1 = r2.w & 0xffff;
-      const uint32_t local = f - s_pref[lo];
-      const int w = max(x1 - x0, 1);
-      const int tx = x0 + (int)(local % (uint32_t)w), ty = y0 + (int)(local / (uint32_t)w);
-      const RasterView &V = rv.v[r2.y];
-      const float bx0 = (float)(tx * kTile) + 0.5f, by0 = (float)(ty * kTile) + 0.5f;
-      const float bx1 = (float)min(tx * kTile + kTile - 1, V.width - 1) + 0.5f;
-      const float by1 = (float)min(ty * kTile + kTile - 1, V.height - 1) + 0.5f;
-      *tile = (uint32_t)(V.tile_base + ty * V.gw + tx);
-      *slot = (uint32_t)r2.x;
-      return ellipse_meets_box(__int_as_float(r0.x), __int_as_float(r0.y), __int_as_float(r0.z),
-                               __int_as_float(r0.w), __int_as_float(r1.x), __int_as_float(r1.y),
-                               __int_as_float(r1.z), __int_as_float(r1.w), bx0, bx1, by0, by1);
-    };
-    // Pass 1: decide every pair once; per-(item, warp) counts go to shared
-    // memory, the decisions stay in registers for pass 2.
-    bool keep[kPer];
-    uint32_t tile[kPer], slot[kPer], mask[kPer];
+  const uint32_t nchunks = (npairs + kEmitChunk - 1) / kEmitChunk;
+  for (uint32_t c = blockIdx.x; c < nchunks && (int32_t)c < A.chunk_cap; c += gridDim.x) {
+    if ((int32_t)c < A.tile_blocks)
+      for (int p = 0; p < A.tile_passes; ++p)
+        A.tile_state[((size_t)p * A.tile_blocks + c) * kRadixBins + threadIdx.x] = 0u;
+    const uint32_t f0 = c * kEmitChunk, f1 = min(f0 + (uint32_t)kEmitChunk, npairs);
+    load_emit_chunk(A, c, f1, npairs, nvis, S);
+    const uint32_t fa = f0 + kPairsPerThread * threadIdx.x;
+    uint32_t m = 0u;
+    if (fa < f1) {
+      PairWalk w = walk_begin(A, S, fa);
+      m = walk_keep<MAXV>(rv, w) ? 1u : 0u;
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const uint32_t f = f0 + i * kEmitBlock + threadIdx.x;
-      tile[i] = slot[i] = 0u;
-      keep[i] = f < f1 && pair(f, &tile[i], &slot[i]);
-      mask[i] = __ballot_sync(0xffffffffu, keep[i]);
-      if (lane == 0) s_w[i][warp] = __popc(mask[i]);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t tot = 0u;
-      for (int k = lane; k < kPer * (kEmitBlock / 32); k += 32) tot += (&s_w[0][0])[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      const uint64_t prefix = lookback_u64_warp(A.lb_chunk, (int32_t)c, tot, &A.counters[kCtrStatus]);
-      if (lane == 0) s_base = prefix;
-      if (lane == 0 && f1 == npairs) {  // last chunk: the instance total
-        const uint64_t all = prefix + tot;
-        A.counters[kCtrInstances] = (uint32_t)umin64(all, (uint64_t)A.inst_cap);
-        if (!(A.counters[kCtrStatus] & kStatusInstOverflow) || all > (uint64_t)A.inst_cap)
-          A.counters[kCtrNeedInstances] =
-              (uint32_t)umin64(max((uint64_t)A.counters[kCtrNeedInstances], all), 0xffffffffull);
-        if (all > (uint64_t)A.inst_cap) atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
+      for (int k = 1; k < kPairsPerThread; ++k) {
+        if (fa + k >= f1) break;
+        walk_next(A, S, w, fa + k);
+        m |= walk_keep<MAXV>(rv, w) ? (1u << k) : 0u;
       }
     }
-    __syncthreads();
-    // Pass 2: write the kept pairs in pair order (item-major, then warp, then lane).
-    uint64_t pos = s_base;
+    A.pair_mask[(size_t)c * kEmitBlock + threadIdx.x] = (uint8_t)m;
+    uint32_t total;
+    block_exclusive_scan(__popc(m), s_scan, &total);
+    if (threadIdx.x == 0) A.chunk_count[c] = total;
+    __syncthreads();  // S is reused by the next chunk
+  }
+}
+
+// Exclusive prefix of the chunk counts, in place, by one block; sets the
+// instance total and flags an instance-capacity overflow.
+constexpr int kChunkScanThreads = 1024;
+__global__ void __launch_bounds__(kChunkScanThreads) chunk_scan_kernel(EmitArgs A) {
+  grid_dependency_sync();
+  __shared__ uint32_t s_scan[kChunkScanThreads / 32 + 1];
+  const uint32_t npairs = A.counters[kCtrPairs];
+  const int64_t nchunks = min64((npairs + kEmitChunk - 1) / kEmitChunk, A.chunk_cap);
+  constexpr int kItems = 8;
+  uint64_t carry = 0;
+  for (int64_t base = 0; base < nchunks; base += (int64_t)kChunkScanThreads * kItems) {
+    uint32_t v[kItems];
+    uint32_t sum = 0u;
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      uint32_t before = 0u, chunk = 0u;
+    for (int k = 0; k < kItems; ++k) {
+      const int64_t idx = base + (int64_t)threadIdx.x * kItems + k;
+      v[k] = idx < nchunks ? A.chunk_count[idx] : 0u;
+      sum += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<kChunkScanThreads / 32>(sum, s_scan, &total);
 #pragma unroll
-      for (int w = 0; w < kEmitBlock / 32; ++w) {
-        const uint32_t cw = s_w[i][w];
-        before += w < warp ? cw : 0u;
-        chunk += cw;
-      }
-      if (keep[i]) {
-        const uint64_t p = pos + before + __popc(mask[i] & lt);
-        if (p < (uint64_t)A.inst_cap) {
-          A.inst_key[p] = tile[i];
-          A.inst_val[p] = slot[i];
+    for (int k = 0; k < kItems; ++k) {
+      const int64_t idx = base + (int64_t)threadIdx.x * kItems + k;
+      if (idx < nchunks) A.chunk_count[idx] = (uint32_t)umin64(carry + run, 0xffffffffull);
+      run += v[k];
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) {
+    A.counters[kCtrInstances] = (uint32_t)umin64(carry, (uint64_t)A.inst_cap);
+    if (!(A.counters[kCtrStatus] & kStatusInstOverflow) || carry > (uint64_t)A.inst_cap)
+      A.counters[kCtrNeedInstances] =
+          (uint32_t)umin64(max((uint64_t)A.counters[kCtrNeedInstances], carry), 0xffffffffull);
+    if (carry > (uint64_t)A.inst_cap) atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
+  }
+}
+
+// Pass 2: writes the kept pairs of each chunk at the chunk's offset in pair
+// order (the keep bytes give each thread its output position) and takes the
+// digit histograms of their tile ids for the tile sort.
+template <int MAXV>
+__global__ void __launch_bounds__(kEmitBlock) emit_write_kernel(EmitArgs A, RasterViews<MAXV> rv) {
+  grid_dependency_sync();
+  __shared__ EmitChunkSmem S;
+  __shared__ uint32_t s_scan[kEmitBlock / 32 + 1];
+  __shared__ uint32_t s_hist[kMaxPasses][kRadixBins];
+  const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
+  const uint32_t npairs = A.counters[kCtrPairs];
+  const uint32_t nchunks = (npairs + kEmitChunk - 1) / kEmitChunk;
+  if (blockIdx.x >= nchunks) return;
+  for (int p = 0; p < A.tile_passes; ++p) s_hist[p][threadIdx.x] = 0u;
+  for (uint32_t c = blockIdx.x; c < nchunks && (int32_t)c < A.chunk_cap; c += gridDim.x) {
+    const uint32_t f0 = c * kEmitChunk, f1 = min(f0 + (uint32_t)kEmitChunk, npairs);
+    load_emit_chunk(A, c, f1, npairs, nvis, S);  // its barriers also order s_hist's clearing
+    const uint32_t m = A.pair_mask[(size_t)c * kEmitBlock + threadIdx.x];
+    uint32_t total;
+    uint64_t pos = (uint64_t)A.chunk_count[c] + block_exclusive_scan(__popc(m), s_scan, &total);
+    if (m) {
+      const uint32_t fa = f0 + kPairsPerThread * threadIdx.x;
+      PairWalk w = walk_begin(A, S, fa);
+#pragma unroll
+      for (int k = 0; k < kPairsPerThread; ++k) {
+        if (k) walk_next(A, S, w, fa + k);
+        if (m & (1u << k)) {
+          const uint32_t tile = walk_tile<MAXV>(rv, w);
+          if (pos < (uint64_t)A.inst_cap) {
+            A.inst_key[pos] = tile;
+            A.inst_val[pos] = w.slot;
+          }
+          ++pos;
+          for (int p = 0; p < A.tile_passes; ++p)
+            atomicAdd(&s_hist[p][(tile >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
         }
+        if ((m >> (k + 1)) == 0u) break;
       }
-      pos += chunk;
     }
-    __syncthreads();  // s_pref and s_w are reused by the next chunk
+    __syncthreads();  // S is reused by the next chunk
+  }
+  for (int p = 0; p < A.tile_passes; ++p) {
+    const uint32_t h = s_hist[p][threadIdx.x];
+    if (h) atomicAdd(&A.hist_tile[p * kRadixBins + threadIdx.x], h);
   }
 }
 
@@ -506,9 +631,15 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   }
   const uint32_t *sorted = dv[(L.depth_passes - 1) & 1];
   // 2. Instances in depth order.
+  uint32_t *tstate = reinterpret_cast<uint32_t *>(ws + L.tile_state);
+  uint32_t *hist_t = reinterpret_cast<uint32_t *>(ws + L.hist_tile);
+  uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
   uint32_t *ik[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_key[0]), reinterpret_cast<uint32_t *>(ws + L.inst_key[1])};
   uint32_t *iv[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_val[0]), reinterpret_cast<uint32_t *>(ws + L.inst_val[1])};
-  if (L.emit_blocks > 0) {
+  if (L.emit_blocks == 0) {  // no visible slot possible: empty tile lists
+    e = cudaMemsetAsync(ranges, 0, (size_t)L.total_tiles * sizeof(uint2), st);
+    if (e != cudaSuccess) return e;
+  } else {
     EmitArgs ea;
     ea.sorted_slots = sorted;
     ea.meta = reinterpret_cast<const int4 *>(ws + L.rec_meta);
@@ -526,22 +657,26 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
     ea.inst_key = ik[0];
     ea.inst_val = iv[0];
     ea.lb_scan = reinterpret_cast<uint64_t *>(ws + L.lb_emit);
-    ea.lb_chunk = reinterpret_cast<uint64_t *>(ws + L.lb_chunk);
+    ea.chunk_count = reinterpret_cast<uint32_t *>(ws + L.chunk_count);
+    ea.pair_mask = reinterpret_cast<uint8_t *>(ws + L.pair_mask);
+    ea.tile_passes = L.tile_passes;
+    ea.tile_blocks = L.tile_blocks;
+    ea.hist_tile = hist_t;
+    ea.tile_state = tstate;
+    ea.ranges = ranges;
+    ea.total_tiles = L.total_tiles;
     e = launch_pdl(pair_scan_kernel<MAXV>, (unsigned)L.emit_blocks, kEmitBlock, st, ea, rv);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(emit_kernel<MAXV>, (unsigned)L.emit_grid, kEmitBlock, st, ea, rv);
+    e = launch_pdl(emit_count_kernel<MAXV>, (unsigned)L.emit_grid, kEmitBlock, st, ea, rv);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(chunk_scan_kernel, 1u, (unsigned)kChunkScanThreads, st, ea);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(emit_write_kernel<MAXV>, (unsigned)L.emit_grid, kEmitBlock, st, ea, rv);
     if (e != cudaSuccess) return e;
   }
-  // 3. Stable sort of the instances by global tile id.
-  uint32_t *tstate = reinterpret_cast<uint32_t *>(ws + L.tile_state);
-  uint32_t *hist_t = reinterpret_cast<uint32_t *>(ws + L.hist_tile);
-  uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
-  const int hbt = (int)std::min<int64_t>((L.inst_cap + kSortTile - 1) / kSortTile, kPersistBlocks);
+  // 3. Stable sort of the instances by global tile id (digit histograms
+  // taken by the emission count).
   const int pbt = std::min(L.tile_blocks, kPersistBlocks);
-  e = launch_pdl(radix_hist_kernel, (unsigned)hbt, kSortThreads, st, (const uint32_t *)ik[0],
-                 (const uint32_t *)(ctr + kCtrInstances), (int64_t)L.inst_cap, (int32_t)L.tile_passes, hist_t, tstate,
-                 (int32_t)L.tile_blocks, ranges, (int64_t)L.total_tiles);
-  if (e != cudaSuccess) return e;
   for (int p = 0; p < L.tile_passes; ++p) {
     const int in = p & 1, out = in ^ 1;
     uint32_t *state = tstate + (size_t)p * L.tile_blocks * kRadixBins;

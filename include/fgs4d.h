@@ -80,7 +80,7 @@ typedef struct fgs4d_settings {
   int32_t tile;          /* tile edge in pixels: 16 */
   float near_plane;      /* cull when camera z <= near_plane, > 0 (tests: 0.2) */
   float dilation;        /* added to the 2D covariance diagonal, >= 0 (tests: 0.3) */
-  float p_t_min;         /* temporal filter: cull when p(t) < p_t_min (Sec. 7.1.1: 0.05) */
+  float p_t_min;         /* temporal filter: cull when p(t) < p_t_min (Sec. 8.1.1: 0.05) */
   float bg[3];           /* background colour composited behind the Gaussians */
   int64_t vis_capacity;  /* max visible (view, Gaussian) pairs; 0 = n * nviews */
   int64_t inst_capacity; /* max (tile, Gaussian) instances over all views, > 0 */
@@ -149,7 +149,7 @@ int fgs4d_workspace_layout(const fgs4d_settings *settings, int64_t n, const fgs4
 /* Per-Gaussian stage for every view (Sec. 3.2 and Sec. 3.1, Eqs. 3-4):
  * activations, R = L(q_l) R(q_r), Sigma = R S S^T R^T, marginal
  * p(t) = exp(-(t - mu_t)^2 / (2 Sigma_44)) and the temporal filter
- * p(t) < p_t_min (Sec. 7.1.1), conditional mean and covariance at t, view
+ * p(t) < p_t_min (Sec. 8.1.1), conditional mean and covariance at t, view
  * transform, near cull, EWA 2D covariance (+ dilation), conic, 3-sigma tile
  * rect, depth, 4DSH colour max(0, sum c cos(2 pi n (t - mu_t)/T) Y_lm(d) +
  * 0.5), effective opacity sigmoid(logit) p(t).  Writes the records of the

@@ -82,6 +82,11 @@ def _declare(lib):
     lib.orc_preprocess_backward.argtypes = [P(_Params), P(_View), P(_Settings), C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p, P(_Grads)]
     lib.orc_preprocess_backward.restype = C.c_int
+    lib.orc_aux.argtypes = [P(_Params), P(_View), P(_Settings), C.c_double, P(_Proj), C.c_void_p]
+    lib.orc_aux.restype = C.c_int
+    lib.orc_render_aux.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_render_aux.restype = C.c_int
     lib.orc_rotation.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_rotation.restype = None
     lib.orc_real_sh.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
@@ -205,6 +210,37 @@ def render_pixels(proj, view, settings: Settings, pix: np.ndarray):
     if rc != 0:
         raise MemoryError("oracle render_pixels failed")
     return rgb, T, nc, mg
+
+
+def aux_records(params, proj, view, settings: Settings, flow_dt: float) -> np.ndarray:
+    """Per Gaussian (z, flow_u, flow_v): camera depth of the sliced mean and
+    its projected displacement over flow_dt (zeros for culled Gaussians)."""
+    lib = _load()
+    ph = _ParamsHold(params)
+    aux = np.zeros((ph.n, 3))
+    pc, keep = _proj_c(proj)
+    lib.orc_aux(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), float(flow_dt), C.byref(pc),
+                _ptr(aux))
+    return aux
+
+
+def render_aux(proj, aux: np.ndarray, view, settings: Settings):
+    """Image with auxiliary channels (FP64): img [3,H,W], T [H,W],
+    aux [4,H,W] = (depth, opacity 1 - T, flow_u, flow_v), margin [H,W]."""
+    lib = _load()
+    W, H = int(view["width"]), int(view["height"])
+    n = proj["status"].shape[0]
+    img = np.zeros((3, H, W))
+    T = np.zeros((H, W))
+    out = np.zeros((4, H, W))
+    mg = np.zeros((H, W))
+    aux = np.ascontiguousarray(aux, dtype=np.float64)
+    pc, keep = _proj_c(proj)
+    rc = lib.orc_render_aux(C.byref(_view_c(view)), C.byref(settings._c()), n, C.byref(pc), _ptr(aux), _ptr(img),
+                            _ptr(T), _ptr(out), _ptr(mg))
+    if rc != 0:
+        raise MemoryError("oracle render_aux failed")
+    return img, T, out, mg
 
 
 def _alloc_grads(n, K):

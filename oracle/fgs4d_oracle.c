@@ -17,7 +17,7 @@
  *   Sec. 3.2                 Sigma = R S S^T R^T, R = L(q_l) R(q_r)
  *   Sec. 3.2                 conditional 3D Gaussian and marginal p(t)
  *   Sec. 3.2                 4D spherindrical harmonics Z_nl^m
- *   Sec. 7.1.1 (impl.)       temporal filter p(t) < 0.05
+ *   Sec. 8.1.1 (impl.)       temporal filter p(t) < 0.05
  * Readings where the paper is silent (compositing constants 1/255, 0.99, 1e-4,
  * 3-sigma extent, pixel centres, rect membership, colour offset) follow the
  * tile rasterizer the paper adapts (Sec. 3.2, last paragraph of
@@ -226,7 +226,7 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 
 /* Forward chain for Gaussian i at one view: Sec. 3.2 (covariance, rotation,
  * conditional and marginal), Sec. 3.1 Eqs. 3-4 (EWA projection), Sec. 3.2
- * (4D spherindrical harmonic colour), Sec. 7.1.1 (temporal filter). */
+ * (4D spherindrical harmonic colour), Sec. 8.1.1 (temporal filter). */
 static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
                           const orc_settings *S, orc_ctx *g) {
   memset(g, 0, sizeof *g);
@@ -453,9 +453,10 @@ typedef struct {
 
 static void composite_pixel(const orc_proj *P, const orc_settings *S, const orc_entry *list, int64_t len,
                             int px, int py, double out[3], double *T_out, int32_t *ncontrib,
-                            double *margin, int32_t *signature, orc_contrib *rec, int64_t *nrec) {
+                            double *margin, int32_t *signature, orc_contrib *rec, int64_t *nrec,
+                            const double *aux, double aux_out[3]) {
   const double pxc = px + 0.5, pyc = py + 0.5;
-  double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+  double T = 1.0, C[3] = {0.0, 0.0, 0.0}, X[3] = {0.0, 0.0, 0.0};
   double mg = INFINITY;
   int32_t last = 0, nclamp = 0;
   int64_t nr = 0;
@@ -483,6 +484,8 @@ static void composite_pixel(const orc_proj *P, const orc_settings *S, const orc_
     mg = dmin(mg, fabs(Tn - 1e-4) / 1e-4);
     if (Tn < 1e-4) break;
     for (int ch = 0; ch < 3; ++ch) C[ch] += P->rgb[3 * i + ch] * alpha * T;
+    if (aux)
+      for (int ch = 0; ch < 3; ++ch) X[ch] += aux[3 * i + ch] * alpha * T;
     if (rec) {
       rec[nr].idx = i;
       rec[nr].pos = (int32_t)j;
@@ -499,6 +502,8 @@ static void composite_pixel(const orc_proj *P, const orc_settings *S, const orc_
     last = (int32_t)(j + 1);
   }
   for (int ch = 0; ch < 3; ++ch) out[ch] = C[ch] + T * S->bg[ch];
+  if (aux_out)
+    for (int ch = 0; ch < 3; ++ch) aux_out[ch] = X[ch];
   if (T_out) *T_out = T;
   if (ncontrib) *ncontrib = last;
   if (margin) *margin = mg;
@@ -565,7 +570,7 @@ int orc_render(const orc_view *V, const orc_settings *S, int64_t n, const orc_pr
       double out[3];
       composite_pixel(P, S, tl.ent + tl.off[t], tl.off[t + 1] - tl.off[t], px, py, out,
                       T_out ? &T_out[p] : NULL, ncontrib ? &ncontrib[p] : NULL,
-                      margin ? &margin[p] : NULL, signature ? &signature[p] : NULL, NULL, NULL);
+                      margin ? &margin[p] : NULL, signature ? &signature[p] : NULL, NULL, NULL, NULL, NULL);
       for (int ch = 0; ch < 3; ++ch) img[ch * HW + p] = out[ch];
     }
   }
@@ -604,10 +609,71 @@ int orc_render_pixels(const orc_view *V, const orc_settings *S, int64_t n, const
     }
     qsort(list, (size_t)cnt, sizeof(orc_entry), entry_cmp);
     composite_pixel(P, S, list, cnt, px, py, rgb + 3 * q, T_out ? &T_out[q] : NULL,
-                    ncontrib ? &ncontrib[q] : NULL, margin ? &margin[q] : NULL, NULL, NULL, NULL);
+                    ncontrib ? &ncontrib[q] : NULL, margin ? &margin[q] : NULL, NULL, NULL, NULL, NULL, NULL);
     free(list);
   }
   return err ? -1 : 0;
+}
+
+/* ----------------------------------------------- auxiliary channels */
+
+/* Per visible Gaussian: camera-space depth z of the sliced mean and the
+ * image-plane displacement of the sliced mean over a time step dt (Sec. 8.1.3,
+ * "emerged dynamics": the trajectory of mu_xyz|t projected between two
+ * consecutive frames).  mu_xyz|t is linear in t with velocity
+ * Sigma_{1:3,4} / Sigma_44, so the displaced camera-space centre is
+ * pc + W v dt; the flow is pi(pc + W v dt) - pi(pc) with pi the pinhole
+ * projection of Eq. 3, and 0 when the displaced centre is not in front of the
+ * near plane.  aux[n][3] = (z, flow_u, flow_v); zeros for culled Gaussians. */
+int orc_aux(const orc_params *Pp, const orc_view *V, const orc_settings *S, double flow_dt,
+            const orc_proj *P, double *aux) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < Pp->n; ++i) {
+    aux[3 * i + 0] = aux[3 * i + 1] = aux[3 * i + 2] = 0.0;
+    if (P->status[i] != 0) continue;
+    orc_ctx g;
+    gauss_forward(Pp, i, V, S, &g);
+    const double *W = V->viewmat;
+    double vel[3], pc2[3];
+    for (int a = 0; a < 3; ++a) vel[a] = g.b[a] / g.c;
+    for (int a = 0; a < 3; ++a)
+      pc2[a] = g.pc[a] + (W[4 * a + 0] * vel[0] + W[4 * a + 1] * vel[1] + W[4 * a + 2] * vel[2]) * flow_dt;
+    aux[3 * i + 0] = g.pc[2];
+    if (pc2[2] > S->near_plane) {
+      aux[3 * i + 1] = V->fx * pc2[0] / pc2[2] + V->cx - g.uv[0];
+      aux[3 * i + 2] = V->fy * pc2[1] / pc2[2] + V->cy - g.uv[1];
+    }
+  }
+  return 0;
+}
+
+/* Image plus auxiliary channels blended with the colour weights of Eq. 6
+ * (w_i = alpha_i T_i): out_aux[4][H][W] = (depth sum w z, opacity 1 - T,
+ * flow_u sum w f_u, flow_v sum w f_v). */
+int orc_render_aux(const orc_view *V, const orc_settings *S, int64_t n, const orc_proj *P, const double *aux,
+                   double *img, double *T_out, double *out_aux, double *margin) {
+  orc_tiles tl;
+  if (build_tiles(V, S, n, P, &tl)) return -1;
+  const int W = V->width, H = V->height, gw = (W + S->tile - 1) / S->tile;
+  const int64_t HW = (int64_t)W * H;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int py = 0; py < H; ++py) {
+    for (int px = 0; px < W; ++px) {
+      const int64_t t = (int64_t)(py / S->tile) * gw + px / S->tile;
+      const int64_t p = (int64_t)py * W + px;
+      double out[3], x[3], T;
+      composite_pixel(P, S, tl.ent + tl.off[t], tl.off[t + 1] - tl.off[t], px, py, out, &T, NULL,
+                      margin ? &margin[p] : NULL, NULL, NULL, NULL, aux, x);
+      for (int ch = 0; ch < 3; ++ch) img[ch * HW + p] = out[ch];
+      if (T_out) T_out[p] = T;
+      out_aux[p] = x[0];
+      out_aux[HW + p] = 1.0 - T;
+      out_aux[2 * HW + p] = x[1];
+      out_aux[3 * HW + p] = x[2];
+    }
+  }
+  free_tiles(&tl);
+  return 0;
 }
 
 /* ------------------------------------------------------------ adjoint */
@@ -831,7 +897,7 @@ int orc_render_backward(const orc_params *Pp, const orc_view *V, const orc_setti
       double outc[3], T;
       int64_t nr = 0;
       composite_pixel(P, S, tl.ent + tl.off[t], tl.off[t + 1] - tl.off[t], px, py, outc, &T, NULL, NULL,
-                      NULL, rec, &nr);
+                      NULL, rec, &nr, NULL, NULL);
       pixel_adjoint(P, S, rec, nr, T, gC, out);
     }
   free(rec);

@@ -1,7 +1,7 @@
 // Per-Gaussian stage of the 4D Gaussian render path and its adjoint.
 //
 // Forward (Sec. 3.2 of "4D Gaussian Splatting", arXiv 2412.20720; Sec. 3.1,
-// Eqs. 3-4; Sec. 7.1.1 temporal filter): one thread per (view, Gaussian);
+// Eqs. 3-4; Sec. 8.1.1 temporal filter): one thread per (view, Gaussian);
 // visible pairs are compacted in (view, Gaussian) order by a block scan plus a
 // decoupled look-back over logical block tickets, so slot numbering is
 // deterministic.

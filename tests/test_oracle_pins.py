@@ -83,7 +83,7 @@ def test_rotation_identity_and_plane_rotation():
 
 def test_rotation_fixing_time_axis():
     """q_r = (a, b, c, -d) for q_l = (a, b, c, d) leaves the t axis fixed, so
-    the covariance is block diagonal (the No-4DRot case, Sec. 7.1.3)."""
+    the covariance is block diagonal (the No-4DRot case, Sec. 8.1.3)."""
     rng = np.random.default_rng(13)
     for _ in range(20):
         q = rng.standard_normal(4)
@@ -351,7 +351,7 @@ def test_saturation_stops_before_transmittance_cutoff():
 
 
 def test_block_diagonal_render_equals_static_3dgs():
-    """No-4DRot reduction (Sec. 3.2 / Sec. 7.1.3): with Sigma_xt = 0 the 4D
+    """No-4DRot reduction (Sec. 3.2 / Sec. 8.1.3): with Sigma_xt = 0 the 4D
     render equals a static 3D Gaussian render whose opacity is scaled by the
     1D temporal Gaussian.  The static renderer below is written independently
     in plain Python (every Gaussian for every pixel; opacities are kept under
@@ -516,3 +516,81 @@ def test_culled_sort_keeps_exactly_the_meeting_tiles():
     assert 0 < len(got) < full.shape[0]
     t = (keys >> np.uint64(32)).astype(np.int64)
     assert np.all(np.diff(t) >= 0)
+
+
+# ------------------------------------------------ auxiliary channel pins
+
+def test_flow_vanishes_without_space_time_coupling():
+    """Sigma_xt = 0 (q_r = (a, b, c, -d) for q_l = (a, b, c, d)): the sliced
+    mean does not move, so every Gaussian's flow and the rendered flow are
+    exactly zero while depth and opacity are not."""
+    rng = np.random.default_rng(31)
+    g = _colour_scene(rng, 30, 1, 1, static=True, big_t=True)
+    view = sy.tiny_view(64, 48, t=0.52)
+    st = oracle.Settings(sh_degree=1, t_order=1)
+    pr = oracle.preprocess(g, view, st)
+    ok = pr["status"] == 0
+    assert ok.sum() > 10
+    aux = oracle.aux_records(g, pr, view, st, flow_dt=0.05)
+    assert np.all(aux[:, 1:] == 0.0)
+    np.testing.assert_allclose(aux[ok, 0], pr["depth"][ok], rtol=0, atol=0)
+    img, T, out, mg = oracle.render_aux(pr, aux, view, st)
+    assert np.all(out[2:] == 0.0)
+    assert out[0].max() > 1.0 and out[1].max() > 0.2
+
+
+def test_flow_is_projected_displacement_of_sliced_mean():
+    """Flow of each Gaussian = pi(mu_xyz|t+dt) - pi(mu_xyz|t), with both sliced
+    means taken from the oracle's own conditional (pinned by quadrature) at the
+    two timestamps, projected by Eq. 3 in this test."""
+    rng = np.random.default_rng(32)
+    g = _colour_scene(rng, 30, 1, 1, static=False, big_t=True)
+    dt = 0.04
+    v0 = sy.tiny_view(64, 48, t=0.5)
+    v1 = sy.tiny_view(64, 48, t=0.5 + dt)
+    st = oracle.Settings(sh_degree=1, t_order=1, p_t_min=0.0)
+    p0 = oracle.preprocess(g, v0, st)
+    p1 = oracle.preprocess(g, v1, st)
+    ok = (p0["status"] == 0) & (p1["pc"][:, 2] > 0.2)
+    assert ok.sum() > 10
+    aux = oracle.aux_records(g, p0, v0, st, flow_dt=float(v1["t"]) - float(v0["t"]))  # the views' stored t
+    fx, fy, cx, cy = (float(v0[k]) for k in ("fx", "fy", "cx", "cy"))
+    u1 = fx * p1["pc"][:, 0] / p1["pc"][:, 2] + cx
+    w1 = fy * p1["pc"][:, 1] / p1["pc"][:, 2] + cy
+    np.testing.assert_allclose(aux[ok, 1], (u1 - p0["uv"][:, 0])[ok], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(aux[ok, 2], (w1 - p0["uv"][:, 1])[ok], rtol=1e-9, atol=1e-9)
+    assert np.abs(aux[ok, 1:]).max() > 0.05  # the coupled scene does move
+
+
+def test_aux_channels_two_layer_closed_form():
+    """Depth and opacity blend with the colour weights of Eq. 6:
+    D = a1 z1 + (1 - a1) a2 z2 and O = 1 - (1 - a1)(1 - a2) at the pixel where
+    both centres project."""
+    view = sy.tiny_view(64, 48)
+    st = oracle.Settings(sh_degree=0, t_order=0)
+    g = _centred_layers(view, (20, 30), [3.5, 4.5], [0.6, 0.7], [[0.5] * 3, [0.5] * 3])
+    pr = oracle.preprocess(g, view, st)
+    aux = oracle.aux_records(g, pr, view, st, flow_dt=0.1)
+    img, T, out, mg = oracle.render_aux(pr, aux, view, st)
+    assert abs(out[0, 30, 20] - (0.6 * 3.5 + 0.4 * 0.7 * 4.5)) < 1e-12
+    assert abs(out[1, 30, 20] - (1.0 - 0.4 * 0.3)) < 1e-12
+    assert out[2, 30, 20] == 0.0 and out[3, 30, 20] == 0.0
+
+
+def test_opacity_channel_matches_constant_colour_image():
+    """With one colour c for every Gaussian and a black background the image
+    is c O, so the opacity channel agrees with the colour compositing."""
+    rng = np.random.default_rng(33)
+    g = _colour_scene(rng, 40, 0, 0, static=False)
+    g["sh"][:] = (0.8 - 0.5) / Y00
+    view = sy.tiny_view(64, 48, t=0.5)
+    st = oracle.Settings(sh_degree=0, t_order=0, bg=(0.0, 0.0, 0.0))
+    pr = oracle.preprocess(g, view, st)
+    aux = oracle.aux_records(g, pr, view, st, flow_dt=0.05)
+    img, T, out, mg = oracle.render_aux(pr, aux, view, st)
+    assert out[1].max() > 0.3
+    for ch in range(3):
+        np.testing.assert_allclose(img[ch], 0.8 * out[1], atol=1e-12)
+    img0, T0, _, _ = oracle.render(pr, view, st)
+    np.testing.assert_allclose(img, img0, atol=0)
+    np.testing.assert_allclose(out[1], 1.0 - T0, atol=0)

@@ -159,22 +159,45 @@ int fgs4d_preprocess(const fgs4d_gaussians *gaussians, const fgs4d_view *views, 
                      const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Tile binning and sort (the tile rasterizer of Sec. 3.2): every visible
- * slot emits one instance per tile of its rect; instances are ordered by
- * (global tile, FP32 depth, slot) with a hand-written radix sort, and each
- * tile's [start, end) range is computed.  Reads only what fgs4d_preprocess
+ * slot emits one instance per tile of its rect whose pixel-centre box meets
+ * the slot's 1/255 ellipse (tiles it misses would skip the slot at every
+ * pixel, so the image is that of the full rect membership); instances are
+ * ordered by (global tile, FP32 depth, slot) with a hand-written radix sort,
+ * and each tile's [start, end) range is computed.  Reads only what fgs4d_preprocess
  * (or a caller filling rec_meta, depth_key and counters[0]) wrote.
  * Device-detected: instance capacity. */
 int fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
                    void *workspace, size_t workspace_bytes, void *stream);
 
 /* Front-to-back compositing per pixel (Sec. 3.2, Eq. 6) over its tile's
- * sorted list: alpha = min(0.99, a exp(power)), skip when power > 0 or
- * alpha < 1/255, stop before the entry that would take T below 1e-4.
+ * sorted list: alpha = min(0.99, a exp(power)), skip when alpha < 1/255,
+ * stop before the entry that would take T below 1e-4 (power is a negative
+ * semidefinite form; no separate power > 0 test is taken).
  * out_rgb: float [sum_v 3 H W], view v at 3 * (pixels before v), planar
  * [3][H][W].  out_T: optional (may be NULL) float [sum_v H W] final
  * transmittance. */
 int fgs4d_render_fwd(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
                      void *workspace, size_t workspace_bytes, float *out_rgb, float *out_T, void *stream);
+
+/* Auxiliary channels (depth, opacity, optical flow) with the image.
+ * Depth and flow are blended with the colour weights of Eq. 6,
+ * w_i = alpha_i T_i: depth = sum w_i z_i with z_i the camera-space depth of
+ * the sliced mean mu_xyz|t; opacity = 1 - T_final (the O of the sky
+ * composition, Sec. 5); flow = sum w_i f_i with f_i the image-plane
+ * displacement of mu_xyz|t over flow_dt, pi(pc + W v flow_dt) - pi(pc) with
+ * velocity v = Sigma_{1:3,4} / Sigma_44 (Sec. 8.1.3: the trajectory of the
+ * conditional mean projected between consecutive frames), 0 when the
+ * displaced centre is not in front of the near plane.
+ * Call after fgs4d_preprocess and fgs4d_bin_sort on the same workspace,
+ * views and settings, with the same gaussians.  out_rgb and out_T as for
+ * fgs4d_render_fwd; out_aux: float [sum_v 4 H W], view v at 4 * (pixels
+ * before v), planar [4][H][W] = (depth, opacity, flow_u, flow_v), flow in
+ * pixels.  Errors: FGS4D_ERR_ARG for a NULL out_rgb or out_aux or a
+ * non-finite flow_dt; otherwise as fgs4d_render_fwd.  The image equals
+ * fgs4d_render_fwd's bit for bit. */
+int fgs4d_render_aux(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                     const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, float flow_dt,
+                     float *out_rgb, float *out_T, float *out_aux, void *stream);
 
 /* Diagnostic form of fgs4d_render_fwd: renders identically into out_rgb and
  * ADDS to stats_out (device uint64[2], 8-byte aligned) the number of

@@ -2,6 +2,7 @@
 // host-side argument checks, workspace layout, and kernel launches on the
 // caller's stream.  No device memory is allocated here.
 #include <math.h>
+#include <cmath>
 #include <string.h>
 
 #include <algorithm>
@@ -130,6 +131,7 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.pair_mask = take((size_t)L.chunk_cap * kEmitBlock);
   L.pair_prefix = take(((size_t)L.vis_cap + 1) * sizeof(uint32_t));
   L.emit_rec = take((size_t)L.vis_cap * 48);
+  L.rec_aux = take((size_t)L.vis_cap * sizeof(float4));
   L.chunk_first = take((size_t)L.chunk_cap * sizeof(uint32_t));
   const size_t vc = (size_t)L.vis_cap, ic = (size_t)L.inst_cap;
   L.rec_geom = take(vc * 16);
@@ -240,7 +242,26 @@ int fgs4d_render_fwd(int64_t n, const fgs4d_view *views, int32_t nviews, const f
   if (rc) return rc;
   if (!out_rgb) return FGS4D_ERR_ARG;
   return cuda_status(launch_render_fwd(L, settings, views, nviews, static_cast<unsigned char *>(workspace), out_rgb,
-                                       out_T, nullptr, static_cast<cudaStream_t>(stream)));
+                                       out_T, nullptr, nullptr, static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_render_aux(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                     const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, float flow_dt,
+                     float *out_rgb, float *out_T, float *out_aux, void *stream) {
+  int rc = check_gaussians(gaussians);
+  if (rc) return rc;
+  Layout L;
+  rc = compute_layout(settings, gaussians->n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  if (!out_rgb || !out_aux || !std::isfinite(flow_dt)) return FGS4D_ERR_ARG;
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PreLaunch p{gaussians, settings, &L, ws, st};
+  cudaError_t e = launch_aux_records(p, views, nviews, flow_dt);
+  if (e != cudaSuccess) return FGS4D_ERR_CUDA;
+  return cuda_status(launch_render_fwd(L, settings, views, nviews, ws, out_rgb, out_T, nullptr, out_aux, st));
 }
 
 int fgs4d_render_stats(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
@@ -252,7 +273,7 @@ int fgs4d_render_stats(int64_t n, const fgs4d_view *views, int32_t nviews, const
   if (rc) return rc;
   if (!out_rgb || !stats_out || ((uintptr_t)stats_out & 7u)) return FGS4D_ERR_ARG;
   return cuda_status(launch_render_fwd(L, settings, views, nviews, static_cast<unsigned char *>(workspace), out_rgb,
-                                       nullptr, reinterpret_cast<unsigned long long *>(stats_out),
+                                       nullptr, reinterpret_cast<unsigned long long *>(stats_out), nullptr,
                                        static_cast<cudaStream_t>(stream)));
 }
 

@@ -89,6 +89,7 @@ struct Layout {
   size_t pair_mask;     // uint8 [chunk_cap][kEmitBlock]: keep bits of 8 consecutive pairs
   size_t pair_prefix;   // uint32 [vis_cap + 1]: exclusive prefix of rect areas in depth order
   size_t emit_rec;      // 3 x 16 B [vis_cap]: emission record per depth-sorted position
+  size_t rec_aux;       // float4 [vis_cap]: (camera depth, flow_u, flow_v, 0) per slot (auxiliary render)
   size_t chunk_first;   // uint32 [chunk_cap]: depth-sorted position holding each chunk's first pair
   size_t control_end;
   size_t rec_geom, rec_color, rec_blue, rec_tau, rec_meta;
@@ -350,7 +351,8 @@ cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nv
                             cudaStream_t stream);
 cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
-                              cudaStream_t stream);
+                              float *out_aux, cudaStream_t stream);
+cudaError_t launch_aux_records(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt);
 cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, const float *dL_drgb, cudaStream_t stream);
 cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, float *loss, float *grad,

@@ -374,6 +374,52 @@ __device__ __forceinline__ void red_add4(float4 *p, float x, float y, float z, f
   atomicAdd(p, make_float4(x, y, z, w));
 }
 
+// Auxiliary records per visible slot (depth, opacity and flow channels):
+// camera depth of the sliced mean and the image-plane displacement of the
+// sliced mean over flow_dt (Sec. 8.1.3: the trajectory of mu_xyz|t projected
+// between consecutive frames).  mu_xyz|t moves with velocity
+// Sigma_{1:3,4} / Sigma_44 = (B u) / sqrt(Sigma_44) in the factored form, so the
+// displaced camera-space centre is pc + W v flow_dt; the flow is 0 when that
+// point is not in front of the near plane.  The chain is re-run with the
+// colour basis cut to degree 0 (the slot is known to be visible; only its
+// geometry is used).
+struct AuxArgs {
+  const float4 *mean, *log_scale, *q_l, *q_r;
+  const float *logit, *sh;
+  int32_t t_order, k3;
+  float period_inv, near_plane, dilation, p_t_min, flow_dt;
+  int64_t vis_cap;
+  const uint32_t *counters;
+  const int4 *rec_meta;
+  float4 *rec_aux;
+};
+
+template <int MAXV>
+__global__ void __launch_bounds__(128) aux_records_kernel(AuxArgs A, PreViews<MAXV> views) {
+  grid_dependency_sync();
+  const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nvis) return;
+  const int4 meta = A.rec_meta[slot];
+  const PreView &cam = views.v[MAXV == 1 ? 0 : meta.y];
+  Chain h;
+  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (forward_chain<0>(meta.x, A.mean, A.log_scale, A.q_l, A.q_r, A.logit, A.sh, A.t_order, A.k3, A.period_inv,
+                       A.near_plane, A.dilation, A.p_t_min, cam, h)) {
+    const float k = A.flow_dt / h.sqc;  // velocity = B u / sqrt(Sigma_44)
+    const float d0 = h.Bu[0] * k, d1 = h.Bu[1] * k, d2 = h.Bu[2] * k;
+    float p2[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) p2[x] = h.pc[x] + cam.W[3 * x + 0] * d0 + cam.W[3 * x + 1] * d1 + cam.W[3 * x + 2] * d2;
+    out.x = h.pc[2];
+    if (p2[2] > A.near_plane) {
+      out.y = cam.fx * p2[0] / p2[2] + cam.cx - h.uv[0];
+      out.z = cam.fy * p2[1] / p2[2] + cam.cy - h.uv[1];
+    }
+  }
+  A.rec_aux[slot] = out;
+}
+
 template <int L, int MAXV>
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs A, PreViews<MAXV> views) {
   grid_dependency_sync();
@@ -687,6 +733,34 @@ cudaError_t launch_bwd_typed(const PreLaunch &p, const fgs4d_view *views, int32_
   return launch_pdl(preprocess_bwd_kernel<L, MAXV>, (unsigned)blocks, 128u, p.stream, A, pv);
 }
 
+template <int MAXV>
+cudaError_t launch_aux_typed(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt) {
+  PreViews<MAXV> pv;
+  fill_pre_views<MAXV>(views, nviews, &pv);
+  const Layout &Lo = *p.L;
+  AuxArgs A;
+  A.mean = reinterpret_cast<const float4 *>(p.g->mean);
+  A.log_scale = reinterpret_cast<const float4 *>(p.g->log_scale);
+  A.q_l = reinterpret_cast<const float4 *>(p.g->q_l);
+  A.q_r = reinterpret_cast<const float4 *>(p.g->q_r);
+  A.logit = p.g->opacity_logit;
+  A.sh = p.g->sh;
+  A.t_order = p.s->t_order;
+  A.k3 = (p.s->sh_degree + 1) * (p.s->sh_degree + 1) * (p.s->t_order + 1) * 3;
+  A.period_inv = 1.0f / p.s->period;
+  A.near_plane = p.s->near_plane;
+  A.dilation = p.s->dilation;
+  A.p_t_min = p.s->p_t_min;
+  A.flow_dt = flow_dt;
+  A.vis_cap = Lo.vis_cap;
+  A.counters = reinterpret_cast<const uint32_t *>(p.ws + Lo.counters);
+  A.rec_meta = reinterpret_cast<const int4 *>(p.ws + Lo.rec_meta);
+  A.rec_aux = reinterpret_cast<float4 *>(p.ws + Lo.rec_aux);
+  const int64_t blocks = (Lo.vis_cap + 127) / 128;
+  if (blocks == 0) return cudaSuccess;
+  return launch_pdl(aux_records_kernel<MAXV>, (unsigned)blocks, 128u, p.stream, A, pv);
+}
+
 }  // namespace
 
 cudaError_t launch_preprocess(const PreLaunch &p, const fgs4d_view *views, int32_t nviews) {
@@ -708,6 +782,11 @@ cudaError_t launch_preprocess_bwd(const PreLaunch &p, const fgs4d_view *views, i
     case 2: return one ? launch_bwd_typed<2, 1>(p, views, nviews, grads) : launch_bwd_typed<2, FGS4D_MAX_VIEWS>(p, views, nviews, grads);
     default: return one ? launch_bwd_typed<3, 1>(p, views, nviews, grads) : launch_bwd_typed<3, FGS4D_MAX_VIEWS>(p, views, nviews, grads);
   }
+}
+
+cudaError_t launch_aux_records(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt) {
+  if (nviews == 1) return launch_aux_typed<1>(p, views, nviews, flow_dt);
+  return launch_aux_typed<FGS4D_MAX_VIEWS>(p, views, nviews, flow_dt);
 }
 
 }  // namespace fgs4d

@@ -33,8 +33,10 @@ struct RenderArgs {
   const uint32_t *inst_val;
   const float4 *rec_geom, *rec_color;
   const float *rec_blue;
+  const float4 *rec_aux;  // auxiliary mode only
   uint32_t vis_cap;
   float *out_rgb, *out_T;
+  float *out_aux;  // [views][4][H][W]: depth, opacity, flow_u, flow_v (auxiliary mode only)
   float *pix_T;
   uint32_t *pix_last;
   float bg0, bg1, bg2;
@@ -77,7 +79,8 @@ template <int NT>
 __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const float4 *rec_geom,
                                             const float4 *rec_color, const float *rec_blue, uint32_t vis_cap,
                                             uint32_t base, uint32_t end, float4 *s_geom, float4 *s_col,
-                                            float *s_blue, uint32_t *s_slot) {
+                                            float *s_blue, uint32_t *s_slot, const float4 *rec_aux = nullptr,
+                                            float4 *s_aux = nullptr) {
 #pragma unroll
   for (int i = 0; i < kBatch / NT; ++i) {
     const int k = threadIdx.x + i * NT;
@@ -89,29 +92,35 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
         s_geom[k] = rec_geom[s];
         s_col[k] = rec_color[s];
         s_blue[k] = rec_blue[s];
+        if (s_aux) s_aux[k] = rec_aux[s];
       } else {
         s_geom[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         s_col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         s_blue[k] = 0.f;
+        if (s_aux) s_aux[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
   }
 }
 
-// kStats: also counts the pixel-entry alpha evaluations and the composited
-// entries (diagnostic variant used to state the algorithmic work).
+// kMode 0: image; 1 (kStats): also counts the pixel-entry alpha evaluations
+// and the composited entries (diagnostic variant used to state the
+// algorithmic work); 2 (kAux): also blends the per-slot depth and flow with
+// the colour weights and writes depth, opacity 1 - T and flow planes.
 // A pixel that has stopped is marked by a negative T (its final transmittance
 // negated; a live pixel always has T >= 1e-4), so the inner loop carries no
 // separate flag.  The update stays a branch: whole warps skip it for entries
 // that miss all their pixels.
-template <int MAXV, int PPT, bool kStats>
+template <int MAXV, int PPT, int kMode>
 __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
                                                                        unsigned long long *stats) {
   grid_dependency_sync();
+  constexpr bool kStats = kMode == 1, kAux = kMode == 2;
   constexpr int NT = kTilePixels / PPT;
   __shared__ float4 s_geom[kBatch];
   __shared__ float4 s_col[kBatch];
   __shared__ float s_blue[kBatch];
+  __shared__ float4 s_aux[kAux ? kBatch : 1];
   const int32_t gt = blockIdx.x;
   const RasterView &V = rv.v[find_view<MAXV>(rv, gt)];
   const int32_t lt = gt - V.tile_base;
@@ -121,6 +130,7 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
   const uint2 range = A.ranges[gt];
   const float pxc = (float)px + 0.5f;
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
+  float X0[kAux ? PPT : 1], X1[kAux ? PPT : 1], X2[kAux ? PPT : 1];  // depth, flow_u, flow_v sums
   uint32_t last[PPT];
   bool live = false;
 #pragma unroll
@@ -128,6 +138,7 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
     const bool in = px < V.width && py0 + k < V.height;
     T[k] = in ? 1.0f : -1.0f;
     C0[k] = C1[k] = C2[k] = 0.f;
+    if (kAux) X0[k] = X1[k] = X2[k] = 0.f;
     last[k] = 0u;
     pyc[k] = (float)(py0 + k) + 0.5f;
     live = live || in;
@@ -136,7 +147,7 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
   for (uint32_t base = range.x; base < range.y; base += kBatch) {
     if (__syncthreads_count(live) == 0) break;
     stage_batch<NT>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, range.y, s_geom, s_col,
-                    s_blue, nullptr);
+                    s_blue, nullptr, kAux ? A.rec_aux : nullptr, kAux ? s_aux : nullptr);
     __syncthreads();
     const int nb = (int)min(range.y - base, (uint32_t)kBatch);
     const uint32_t pos0 = base - range.x + 1u;
@@ -158,6 +169,12 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
             C0[k] = __fmaf_rn(col.z, w, C0[k]);
             C1[k] = __fmaf_rn(col.w, w, C1[k]);
             C2[k] = __fmaf_rn(blue, w, C2[k]);
+            if (kAux) {
+              const float4 x = s_aux[j];
+              X0[k] = __fmaf_rn(x.x, w, X0[k]);
+              X1[k] = __fmaf_rn(x.y, w, X1[k]);
+              X2[k] = __fmaf_rn(x.z, w, X2[k]);
+            }
             T[k] = Tn;
             last[k] = pos0 + (uint32_t)j;
             if (kStats) ++n_comp;
@@ -194,6 +211,13 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
     A.pix_T[V.pix_base + p] = Tend;
     A.pix_last[V.pix_base + p] = last[k];
     if (A.out_T) A.out_T[V.pix_base + p] = Tend;
+    if (kAux) {
+      float *aux = A.out_aux + V.pix_base * 4;
+      aux[p] = X0[k];
+      aux[HW + p] = 1.0f - Tend;
+      aux[2 * HW + p] = X1[k];
+      aux[3 * HW + p] = X2[k];
+    }
   }
 }
 
@@ -367,10 +391,21 @@ __global__ void l1_loss_kernel(const float *__restrict__ img, const float *__res
   }
 }
 
+template <int MAXV, int PPT>
+cudaError_t launch_fwd_ppt(const RenderArgs &A, const RasterViews<MAXV> &rv, unsigned grid,
+                           unsigned long long *stats, cudaStream_t st) {
+  if (stats) return launch_pdl(render_fwd_kernel<MAXV, PPT, 1>, grid, kTilePixels / PPT, st, A, rv, stats);
+  if (A.out_aux)
+    return launch_pdl(render_fwd_kernel<MAXV, PPT, 2>, grid, kTilePixels / PPT, st, A, rv,
+                      (unsigned long long *)nullptr);
+  return launch_pdl(render_fwd_kernel<MAXV, PPT, 0>, grid, kTilePixels / PPT, st, A, rv,
+                    (unsigned long long *)nullptr);
+}
+
 template <int MAXV>
 cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                              unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
-                             cudaStream_t st) {
+                             float *out_aux, cudaStream_t st) {
   RasterViews<MAXV> rv;
   if (!make_raster_views<MAXV>(L, views, nviews, &rv)) return cudaErrorInvalidValue;
   RenderArgs A;
@@ -379,9 +414,11 @@ cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   A.rec_geom = reinterpret_cast<const float4 *>(ws + L.rec_geom);
   A.rec_color = reinterpret_cast<const float4 *>(ws + L.rec_color);
   A.rec_blue = reinterpret_cast<const float *>(ws + L.rec_blue);
+  A.rec_aux = reinterpret_cast<const float4 *>(ws + L.rec_aux);
   A.vis_cap = (uint32_t)L.vis_cap;
   A.out_rgb = out_rgb;
   A.out_T = out_T;
+  A.out_aux = out_aux;
   A.pix_T = reinterpret_cast<float *>(ws + L.pix_T);
   A.pix_last = reinterpret_cast<uint32_t *>(ws + L.pix_last);
   A.bg0 = s->bg[0];
@@ -390,15 +427,9 @@ cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   if (L.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)L.total_tiles;
   switch (render_ppt(s)) {
-    case 2:
-      if (stats) return launch_pdl(render_fwd_kernel<MAXV, 2, true>, grid, kTilePixels / 2, st, A, rv, stats);
-      return launch_pdl(render_fwd_kernel<MAXV, 2, false>, grid, kTilePixels / 2, st, A, rv, nullptr);
-    case 8:
-      if (stats) return launch_pdl(render_fwd_kernel<MAXV, 8, true>, grid, kTilePixels / 8, st, A, rv, stats);
-      return launch_pdl(render_fwd_kernel<MAXV, 8, false>, grid, kTilePixels / 8, st, A, rv, nullptr);
-    default:
-      if (stats) return launch_pdl(render_fwd_kernel<MAXV, 4, true>, grid, kTilePixels / 4, st, A, rv, stats);
-      return launch_pdl(render_fwd_kernel<MAXV, 4, false>, grid, kTilePixels / 4, st, A, rv, nullptr);
+    case 2: return launch_fwd_ppt<MAXV, 2>(A, rv, grid, stats, st);
+    case 8: return launch_fwd_ppt<MAXV, 8>(A, rv, grid, stats, st);
+    default: return launch_fwd_ppt<MAXV, 4>(A, rv, grid, stats, st);
   }
 }
 
@@ -436,9 +467,9 @@ cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
 
 cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
-                              cudaStream_t stream) {
-  if (nviews == 1) return render_fwd_typed<1>(L, s, views, nviews, ws, out_rgb, out_T, stats, stream);
-  return render_fwd_typed<FGS4D_MAX_VIEWS>(L, s, views, nviews, ws, out_rgb, out_T, stats, stream);
+                              float *out_aux, cudaStream_t stream) {
+  if (nviews == 1) return render_fwd_typed<1>(L, s, views, nviews, ws, out_rgb, out_T, stats, out_aux, stream);
+  return render_fwd_typed<FGS4D_MAX_VIEWS>(L, s, views, nviews, ws, out_rgb, out_T, stats, out_aux, stream);
 }
 
 cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,

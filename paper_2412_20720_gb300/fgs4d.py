@@ -29,7 +29,7 @@ MAX_T_ORDER = 4
 TILE = 16
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
-            "fgs4d_render_fwd", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
+            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
             "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 
@@ -97,6 +97,8 @@ def load():
     lib.fgs4d_preprocess.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, vp]
     lib.fgs4d_bin_sort.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp]
     lib.fgs4d_render_fwd.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, vp, vp]
+    lib.fgs4d_render_aux.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, C.c_float, vp, vp,
+                                     vp, vp]
     lib.fgs4d_render_stats.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, vp, vp]
     lib.fgs4d_render_bwd.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, vp, P(GaussiansGrad),
                                      vp]
@@ -192,6 +194,12 @@ def bin_sort(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: 
 def render_fwd(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, out_rgb: int, out_T, stream):
     _check(load().fgs4d_render_fwd(int(n), views, int(nviews), C.byref(settings), ws, ws_bytes, out_rgb, out_T,
                                    stream), "fgs4d_render_fwd")
+
+
+def render_aux(gaussians: Gaussians, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, flow_dt: float,
+               out_rgb: int, out_T, out_aux: int, stream):
+    _check(load().fgs4d_render_aux(C.byref(gaussians), views, int(nviews), C.byref(settings), ws, ws_bytes,
+                                   float(flow_dt), out_rgb, out_T, out_aux, stream), "fgs4d_render_aux")
 
 
 def render_stats(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, out_rgb: int,

@@ -80,12 +80,12 @@ class Renderer:
             _check_param(k, params[k], self.n, self.device)
         return fgs4d.make_gaussians({k: _ptr(params[k]) for k in PARAM_KEYS}, self.n)
 
-    def split(self, flat: torch.Tensor) -> list:
-        """Flat [sum 3HW] image buffer -> list of [3, H, W] views."""
+    def split(self, flat: torch.Tensor, channels: int = 3) -> list:
+        """Flat [sum C H W] planar buffer -> list of [C, H, W] views."""
         out, off = [], 0
         for h, w in self.sizes:
-            out.append(flat[off:off + 3 * h * w].view(3, h, w))
-            off += 3 * h * w
+            out.append(flat[off:off + channels * h * w].view(channels, h, w))
+            off += channels * h * w
         return out
 
     # ------------------------------------------------------------------ calls
@@ -101,6 +101,23 @@ class Renderer:
         fgs4d.render_fwd(self.n, self.views, self.nviews, self.settings, ws, self.ws_bytes, _ptr(out_rgb),
                          _ptr(out_T) if out_T is not None else None, st)
         return out_rgb
+
+    def forward_aux(self, params: dict, flow_dt: float, out_rgb: torch.Tensor | None = None,
+                    out_aux: torch.Tensor | None = None):
+        """Like forward, plus the auxiliary planes: returns (rgb, aux) with aux
+        flat [sum_v 4 H W], per view (depth, opacity, flow_u, flow_v)."""
+        g = self.gaussians(params)
+        if out_rgb is None:
+            out_rgb = torch.empty(3 * self.total_pixels, dtype=torch.float32, device=self.device)
+        if out_aux is None:
+            out_aux = torch.empty(4 * self.total_pixels, dtype=torch.float32, device=self.device)
+        st = self.stream()
+        ws = _ptr(self.ws)
+        fgs4d.preprocess(g, self.views, self.nviews, self.settings, ws, self.ws_bytes, st)
+        fgs4d.bin_sort(self.n, self.views, self.nviews, self.settings, ws, self.ws_bytes, st)
+        fgs4d.render_aux(g, self.views, self.nviews, self.settings, ws, self.ws_bytes, flow_dt, _ptr(out_rgb), None,
+                         _ptr(out_aux), st)
+        return out_rgb, out_aux
 
     def backward(self, params: dict, dL_drgb: torch.Tensor, grads: dict):
         """Adds dL/dparams into ``grads`` for the last forward of this renderer."""

@@ -113,6 +113,15 @@ def test_calls_reject_missing_or_small_workspace_before_launching():
     assert lib.fgs4d_render_fwd(0, views, nv, C.byref(s), C.c_void_p(1 << 20), 1 << 40, None, None, None) == fgs4d.ERR_ARG
     assert lib.fgs4d_l1_loss(None, None, 10, None, None, None) == fgs4d.ERR_ARG
     assert lib.fgs4d_get_status(None, 0, None, None) == fgs4d.ERR_WORKSPACE
+    # Auxiliary render: missing output planes or a non-finite time step.
+    g.n = 0
+    ws, big = C.c_void_p(1 << 20), 1 << 40
+    assert lib.fgs4d_render_aux(C.byref(g), views, nv, C.byref(s), ws, big, 0.1, C.c_void_p(4096), None, None,
+                                None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_render_aux(C.byref(g), views, nv, C.byref(s), ws, big, float("nan"), C.c_void_p(4096), None,
+                                C.c_void_p(4096), None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_render_aux(C.byref(g), views, nv, C.byref(s), None, 0, 0.1, C.c_void_p(4096), None,
+                                C.c_void_p(4096), None) == fgs4d.ERR_WORKSPACE
 
 
 def test_status_strings():

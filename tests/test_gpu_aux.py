@@ -1,0 +1,74 @@
+"""Parity of the auxiliary render channels (depth, opacity 1 - T, optical flow
+of the sliced mean over a time step) with the FP64 oracle, through the C ABI
+entry fgs4d_render_aux."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_20720_gb300 import synthetic as sy
+from paper_2412_20720_gb300.render import RenderConfig, Renderer
+
+from helpers import PIXEL_MARGIN, keep_clear_of_boundaries, oracle_settings, subset, to_device
+
+pytestmark = pytest.mark.gpu
+
+IMAGE_ATOL = 2e-4
+
+
+def case(width, height, L, NT, seed, n=2000, ts=(0.5,), static=False):
+    sc = sy.make_scene(n, seed, (-1, -1, -1), (1, 1, 1), sh_degree=L, t_order=NT)
+    params = sc.as_dict()
+    if static:  # q_r = (a, b, c, -d) for q_l = (a, b, c, d): Sigma_xt = 0
+        params["q_r"] = np.ascontiguousarray(params["q_l"] * np.array([1, 1, 1, -1], np.float32))
+    views = [sy.tiny_view(width, height, t=t) for t in ts]
+    cfg = RenderConfig(sh_degree=L, t_order=NT, inst_capacity=1 << 19)
+    return subset(params, keep_clear_of_boundaries(params, views, cfg)), views, cfg
+
+
+def gpu_aux(params, views, cfg, flow_dt):
+    import torch
+    r = Renderer(params["mean"].shape[0], views, cfg)
+    p = to_device(params)
+    rgb, aux = r.forward_aux(p, flow_dt)
+    r.check()
+    plain = r.forward(p).clone()
+    torch.cuda.synchronize()
+    return ([x.cpu().numpy() for x in r.split(rgb)], [x.cpu().numpy() for x in r.split(aux, 4)],
+            [x.cpu().numpy() for x in r.split(plain)])
+
+
+def oracle_aux(params, view, cfg, flow_dt):
+    st = oracle_settings(cfg)
+    pr = oracle.preprocess(params, view, st)
+    aux = oracle.aux_records(params, pr, view, st, float(np.float32(flow_dt)))
+    return oracle.render_aux(pr, aux, view, st), aux
+
+
+@pytest.mark.parametrize("w,h,L,NT,ts", [(128, 96, 1, 1, (0.5,)), (131, 77, 3, 2, (0.45,)),
+                                         (64, 48, 2, 1, (0.3, 0.5, 0.7))])
+def test_aux_channels_match_oracle(w, h, L, NT, ts):
+    params, views, cfg = case(w, h, L, NT, seed=3, ts=ts)
+    dt = 0.05
+    rgb, aux, plain = gpu_aux(params, views, cfg, dt)
+    for k, view in enumerate(views):
+        (img, T, out, mg), rec = oracle_aux(params, view, cfg, dt)
+        ok = mg >= PIXEL_MARGIN
+        assert ok.mean() >= 0.95
+        np.testing.assert_array_equal(rgb[k], plain[k])  # the image is fgs4d_render_fwd's, bit for bit
+        assert np.abs(rgb[k] - img)[:, ok].max() <= IMAGE_ATOL
+        assert np.abs(aux[k][1] - out[1])[ok].max() <= IMAGE_ATOL  # opacity
+        zmax = np.abs(rec[:, 0]).max()
+        assert np.abs(aux[k][0] - out[0])[ok].max() <= IMAGE_ATOL * zmax  # depth
+        fmax = max(np.abs(rec[:, 1:]).max(), 1.0)
+        assert np.abs(out[2:]).max() > 0.05  # the scene moves
+        assert np.abs(aux[k][2:] - out[2:])[:, ok].max() <= IMAGE_ATOL * fmax  # flow, pixels
+
+
+def test_flow_vanishes_for_gaussians_without_space_time_coupling():
+    params, views, cfg = case(96, 64, 1, 1, seed=4, static=True)
+    rgb, aux, plain = gpu_aux(params, views, cfg, 0.05)
+    (img, T, out, mg), rec = oracle_aux(params, views[0], cfg, 0.05)
+    assert np.all(out[2:] == 0.0)
+    # In FP32 the rotation leaves the t axis fixed up to rounding.
+    assert np.abs(aux[0][2:]).max() <= 1e-4
+    assert aux[0][0].max() > 1.0 and aux[0][1].max() > 0.2

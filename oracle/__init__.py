@@ -60,7 +60,7 @@ class _Proj(C.Structure):
     _fields_ = [(name, C.c_void_p) for name, _, _ in _PROJ_FIELDS]
 
 
-_GRAD_FIELDS = ["mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh", "g_uv", "g_conic", "g_a", "g_rgb"]
+_GRAD_FIELDS = ["mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh", "g_uv", "g_conic", "g_a", "g_rgb", "g_z"]
 
 
 class _Grads(C.Structure):
@@ -87,6 +87,9 @@ def _declare(lib):
     lib.orc_render_aux.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_render_aux.restype = C.c_int
+    lib.orc_render_aux_backward.argtypes = [P(_Params), P(_View), P(_Settings), P(_Proj), C.c_void_p, C.c_void_p,
+                                            P(_Grads)]
+    lib.orc_render_aux_backward.restype = C.c_int
     lib.orc_rotation.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_rotation.restype = None
     lib.orc_real_sh.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
@@ -245,7 +248,7 @@ def render_aux(proj, aux: np.ndarray, view, settings: Settings):
 
 def _alloc_grads(n, K):
     shapes = {"mean": (n, 4), "log_scale": (n, 4), "q_l": (n, 4), "q_r": (n, 4), "opacity_logit": (n,),
-              "sh": (n, K, 3), "g_uv": (n, 2), "g_conic": (n, 3), "g_a": (n,), "g_rgb": (n, 3)}
+              "sh": (n, K, 3), "g_uv": (n, 2), "g_conic": (n, 3), "g_a": (n,), "g_rgb": (n, 3), "g_z": (n,)}
     g = {k: np.zeros(s) for k, s in shapes.items()}
     return g, _Grads(*(_ptr(g[k]) for k in _GRAD_FIELDS))
 
@@ -263,6 +266,26 @@ def render_backward(params, proj, view, settings: Settings, dimg: np.ndarray):
                                  _ptr(dimg), C.byref(gc))
     if rc != 0:
         raise MemoryError("oracle backward failed")
+    return g
+
+
+def render_aux_backward(params, proj, view, settings: Settings, dimg: np.ndarray, daux: np.ndarray):
+    """Exact reverse-mode gradient (FP64) of <dimg, image> + <daux, aux> with
+    aux = (depth, opacity, flow_u, flow_v) of render_aux; the flow planes of
+    daux must be zero (flow is not differentiated)."""
+    lib = _load()
+    ph = _ParamsHold(params)
+    K = ph.arrs["sh"].shape[1]
+    g, gc = _alloc_grads(ph.n, K)
+    dimg = np.ascontiguousarray(dimg, dtype=np.float64)
+    daux = np.ascontiguousarray(daux, dtype=np.float64)
+    pc, keep = _proj_c(proj)
+    rc = lib.orc_render_aux_backward(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), C.byref(pc),
+                                     _ptr(dimg), _ptr(daux), C.byref(gc))
+    if rc == -2:
+        raise ValueError("flow planes of daux must be zero")
+    if rc != 0:
+        raise MemoryError("oracle aux backward failed")
     return g
 
 

@@ -97,6 +97,7 @@ typedef struct {
   double *g_conic;       /* [n][3]  dL/d(A, B, C) */
   double *g_a;           /* [n]     dL/d(effective opacity) */
   double *g_rgb;         /* [n][3]  dL/d(colour) */
+  double *g_z;           /* [n]     dL/d(camera depth of the sliced mean), depth channel only */
 } orc_grads;
 
 /* Per-Gaussian intermediate values of the forward chain, kept for the
@@ -684,9 +685,12 @@ int orc_render_aux(const orc_view *V, const orc_settings *S, int64_t n, const or
  *   dC/dc_i     = alpha_i T_i
  *   dC/dalpha_i = c_i T_i - (sum_{j>i} c_j alpha_j T_j + T_final bg) / (1 - alpha_i)
  * and alpha = min(0.99, a G), G = exp(power), power = -1/2 d^T Q d. */
+/* With gX != NULL also the depth channel D = sum_i z_i alpha_i T_i and the
+ * opacity O = 1 - T_final = sum_i alpha_i T_i (gX = dL/dD, dL/dO): the same
+ * rule with x_i = z_i, resp. 1, and a zero background; dD/dz_i = alpha_i T_i. */
 static void pixel_adjoint(const orc_proj *P, const orc_settings *S, const orc_contrib *rec,
-                          int64_t nr, double T_final, const double gC[3], orc_grads *out) {
-  double rest[3];
+                          int64_t nr, double T_final, const double gC[3], const double *gX, orc_grads *out) {
+  double rest[3], restD = 0.0, restO = 0.0;
   for (int ch = 0; ch < 3; ++ch) rest[ch] = T_final * S->bg[ch];
   for (int64_t k = nr - 1; k >= 0; --k) {
     const orc_contrib *e = &rec[k];
@@ -698,6 +702,13 @@ static void pixel_adjoint(const orc_proj *P, const orc_settings *S, const orc_co
       g_alpha += gC[ch] * (c[ch] * e->T - rest[ch] / (1.0 - e->alpha));
     }
     for (int ch = 0; ch < 3; ++ch) rest[ch] += c[ch] * e->alpha * e->T;
+    if (gX) {
+      const double z = P->depth[i];
+      out->g_z[i] += gX[0] * e->alpha * e->T;
+      g_alpha += gX[0] * (z * e->T - restD / (1.0 - e->alpha)) + gX[1] * (e->T - restO / (1.0 - e->alpha));
+      restD += z * e->alpha * e->T;
+      restO += e->alpha * e->T;
+    }
     if (e->clamped) continue; /* min(0.99, .) is locally constant */
     const double a = P->a_eff[i];
     out->g_a[i] += g_alpha * e->G;
@@ -715,7 +726,7 @@ static void pixel_adjoint(const orc_proj *P, const orc_settings *S, const orc_co
  * rgb) back to the raw parameters. */
 static void gauss_adjoint(const orc_params *Pp, int64_t i, const orc_view *V, const orc_settings *S,
                           const orc_ctx *g, const double g_uv[2], const double g_conic[3],
-                          double g_a, const double g_rgb[3], orc_grads *out) {
+                          double g_a, const double g_rgb[3], double g_z, orc_grads *out) {
   const int nlm = (g->L + 1) * (g->L + 1);
   const double *sh = Pp->sh + (size_t)i * g->K * 3;
   double g_mu3[3] = {0, 0, 0}, g_dt = 0.0, g_pc[3] = {0, 0, 0};
@@ -754,6 +765,7 @@ static void gauss_adjoint(const orc_params *Pp, int64_t i, const orc_view *V, co
   g_pc[0] += g_uv[0] * V->fx / z;
   g_pc[1] += g_uv[1] * V->fy / z;
   g_pc[2] += -g_uv[0] * V->fx * x / (z * z) - g_uv[1] * V->fy * y / (z * z);
+  g_pc[2] += g_z; /* depth channel: z is the camera-space depth itself */
 
   /* Conic = inverse(cov2): dL/dcov2 = -Q GQ Q, with GQ the full-matrix
    * gradient of Q = [[A, B], [B, C]] (B enters twice). */
@@ -898,7 +910,7 @@ int orc_render_backward(const orc_params *Pp, const orc_view *V, const orc_setti
       int64_t nr = 0;
       composite_pixel(P, S, tl.ent + tl.off[t], tl.off[t + 1] - tl.off[t], px, py, outc, &T, NULL, NULL,
                       NULL, rec, &nr, NULL, NULL);
-      pixel_adjoint(P, S, rec, nr, T, gC, out);
+      pixel_adjoint(P, S, rec, nr, T, gC, NULL, out);
     }
   free(rec);
   free_tiles(&tl);
@@ -908,7 +920,54 @@ int orc_render_backward(const orc_params *Pp, const orc_view *V, const orc_setti
     orc_ctx g;
     gauss_forward(Pp, i, V, S, &g);
     gauss_adjoint(Pp, i, V, S, &g, out->g_uv + 2 * i, out->g_conic + 3 * i, out->g_a[i],
-                  out->g_rgb + 3 * i, out);
+                  out->g_rgb + 3 * i, out->g_z[i], out);
+  }
+  return 0;
+}
+
+/* dL/d(parameters) for a loss on the image and the depth and opacity
+ * channels of orc_render_aux: dimg [3][H][W], daux [4][H][W] (depth,
+ * opacity, flow_u, flow_v; the flow planes are not differentiated and must
+ * be zero). */
+int orc_render_aux_backward(const orc_params *Pp, const orc_view *V, const orc_settings *S,
+                            const orc_proj *P, const double *dimg, const double *daux, orc_grads *out) {
+  const int64_t n = Pp->n;
+  orc_tiles tl;
+  if (build_tiles(V, S, n, P, &tl)) return -1;
+  const int W = V->width, H = V->height, gw = (W + S->tile - 1) / S->tile;
+  const int64_t HW = (int64_t)W * H;
+  for (int64_t p = 0; p < HW; ++p)
+    if (daux[2 * HW + p] != 0.0 || daux[3 * HW + p] != 0.0) {
+      free_tiles(&tl);
+      return -2;
+    }
+  int64_t maxlen = 1;
+  for (int64_t t = 0; t < (int64_t)gw * ((H + S->tile - 1) / S->tile); ++t)
+    if (tl.off[t + 1] - tl.off[t] > maxlen) maxlen = tl.off[t + 1] - tl.off[t];
+  orc_contrib *rec = malloc(sizeof(orc_contrib) * (size_t)maxlen);
+  if (!rec) return -1;
+  for (int py = 0; py < H; ++py)
+    for (int px = 0; px < W; ++px) {
+      const int64_t t = (int64_t)(py / S->tile) * gw + px / S->tile;
+      const int64_t p = (int64_t)py * W + px;
+      const double gC[3] = {dimg[p], dimg[HW + p], dimg[2 * HW + p]};
+      const double gX[2] = {daux[p], daux[HW + p]};
+      if (gC[0] == 0.0 && gC[1] == 0.0 && gC[2] == 0.0 && gX[0] == 0.0 && gX[1] == 0.0) continue;
+      double outc[3], T;
+      int64_t nr = 0;
+      composite_pixel(P, S, tl.ent + tl.off[t], tl.off[t + 1] - tl.off[t], px, py, outc, &T, NULL, NULL,
+                      NULL, rec, &nr, NULL, NULL);
+      pixel_adjoint(P, S, rec, nr, T, gC, gX, out);
+    }
+  free(rec);
+  free_tiles(&tl);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    if (P->status[i] != 0) continue;
+    orc_ctx g;
+    gauss_forward(Pp, i, V, S, &g);
+    gauss_adjoint(Pp, i, V, S, &g, out->g_uv + 2 * i, out->g_conic + 3 * i, out->g_a[i],
+                  out->g_rgb + 3 * i, out->g_z[i], out);
   }
   return 0;
 }
@@ -923,7 +982,7 @@ int orc_preprocess_backward(const orc_params *Pp, const orc_view *V, const orc_s
     orc_ctx g;
     gauss_forward(Pp, i, V, S, &g);
     if (g.status != 0) continue;
-    gauss_adjoint(Pp, i, V, S, &g, g_uv + 2 * i, g_conic + 3 * i, g_a[i], g_rgb + 3 * i, out);
+    gauss_adjoint(Pp, i, V, S, &g, g_uv + 2 * i, g_conic + 3 * i, g_a[i], g_rgb + 3 * i, 0.0, out);
   }
   return 0;
 }

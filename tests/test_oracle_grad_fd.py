@@ -161,3 +161,44 @@ def test_full_adjoint_matches_fd_64_gaussians_32x32():
     for key in PARAM_KEYS:
         assert len(pairs.get(key, [])) >= 10, key
         _check(pairs[key], 1e-6, 1e-9)
+
+
+def test_depth_and_opacity_adjoint_matches_fd():
+    """Loss on the image, the depth channel and the opacity channel (the
+    inputs of the LiDAR and sky terms, Sec. 5): whole-chain adjoint against
+    central differences of render_aux."""
+    rng = np.random.default_rng(34)
+    view = sy.tiny_view(32, 32, t=0.5)
+    st = oracle.Settings(sh_degree=1, t_order=1, bg=(0.3, 0.1, 0.6))
+    params = _scene(48, 34, L=1, NT=1, box=0.5)
+    base = oracle.preprocess(params, view, st)
+    vis = base["status"] == 0
+    assert vis.sum() >= 12
+    dimg = rng.standard_normal((3, 32, 32))
+    daux = np.zeros((4, 32, 32))
+    daux[:2] = rng.standard_normal((2, 32, 32))
+    g = oracle.render_aux_backward(params, base, view, st, dimg, daux)
+    assert np.abs(g["g_z"]).max() > 0
+
+    def fn(p):
+        pr = oracle.preprocess(p, view, st)
+        aux = oracle.aux_records(p, pr, view, st, 0.05)
+        img, T, out, mg = oracle.render_aux(pr, aux, view, st)
+        _, _, nc, _, sig = oracle.render(pr, view, st, signature=True)
+        return float((dimg * img).sum() + (daux * out).sum()), (pr["status"].tobytes(), pr["rect"].tobytes(),
+                                                              (pr["rgb"] > 0).tobytes(), nc.tobytes(), sig.tobytes())
+
+    sig0 = fn(params)[1]
+    pairs = {}
+    skipped = 0
+    for key, idx in _elements(rng, params, vis, sh_per_gauss=2):
+        d, z, sp, sm = _fd(params, key, idx, fn)
+        if sp != sig0 or sm != sig0:
+            skipped += 1
+            continue
+        pairs.setdefault(key, []).append((g[key][idx], d, z))
+    total = sum(len(v) for v in pairs.values())
+    assert skipped <= 0.1 * (total + skipped)
+    for key in PARAM_KEYS:
+        assert len(pairs.get(key, [])) >= 10, key
+        _check(pairs[key], 1e-6, 1e-9)

@@ -217,6 +217,20 @@ int fgs4d_render_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, 
                      const fgs4d_settings *settings, void *workspace, size_t workspace_bytes,
                      const float *dL_drgb, const fgs4d_gaussians_grad *grads, void *stream);
 
+/* Reverse-mode derivative of a loss on the image and on the depth and
+ * opacity channels of fgs4d_render_aux (the inputs of the LiDAR depth loss
+ * and the sky composition, Sec. 5).  dL_drgb as for fgs4d_render_bwd;
+ * dL_daux has out_aux's layout, planes (depth, opacity, flow_u, flow_v); the
+ * flow planes are ignored (flow is rendered for evaluation, not
+ * differentiated).  Depth and opacity follow the colour rule with a zero
+ * background and x_i = z_i, resp. 1; dL/dz_i flows into the sliced mean.
+ * Requires the workspace of the matching fgs4d_render_aux.  Errors: as
+ * fgs4d_render_bwd, plus FGS4D_ERR_ARG for a NULL dL_daux. */
+int fgs4d_render_aux_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                         const fgs4d_settings *settings, void *workspace, size_t workspace_bytes,
+                         const float *dL_drgb, const float *dL_daux, const fgs4d_gaussians_grad *grads,
+                         void *stream);
+
 /* Photometric L1 loss (Sec. 3.3, rendering loss only): loss_out[0] +=
  * sum |img - target| / count, dL_dimg = sign(img - target) / count.
  * All device pointers; loss_out must be zeroed by the caller. */

@@ -277,9 +277,11 @@ int fgs4d_render_stats(int64_t n, const fgs4d_view *views, int32_t nviews, const
                                        static_cast<cudaStream_t>(stream)));
 }
 
-int fgs4d_render_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
-                     const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, const float *dL_drgb,
-                     const fgs4d_gaussians_grad *grads, void *stream) {
+namespace {
+
+int render_bwd_common(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                      const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, const float *dL_drgb,
+                      const float *dL_daux, const fgs4d_gaussians_grad *grads, void *stream) {
   int rc = check_gaussians(gaussians);
   if (rc) return rc;
   Layout L;
@@ -297,10 +299,28 @@ int fgs4d_render_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, 
   }
   unsigned char *ws = static_cast<unsigned char *>(workspace);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = launch_render_bwd(L, settings, views, nviews, ws, dL_drgb, st);
+  cudaError_t e = launch_render_bwd(L, settings, views, nviews, ws, dL_drgb, dL_daux, st);
   if (e != cudaSuccess) return FGS4D_ERR_CUDA;
   PreLaunch p{gaussians, settings, &L, ws, st};
   return cuda_status(launch_preprocess_bwd(p, views, nviews, grads));
+}
+
+}  // namespace
+
+int fgs4d_render_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                     const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, const float *dL_drgb,
+                     const fgs4d_gaussians_grad *grads, void *stream) {
+  return render_bwd_common(gaussians, views, nviews, settings, workspace, workspace_bytes, dL_drgb, nullptr, grads,
+                           stream);
+}
+
+int fgs4d_render_aux_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                         const fgs4d_settings *settings, void *workspace, size_t workspace_bytes,
+                         const float *dL_drgb, const float *dL_daux, const fgs4d_gaussians_grad *grads,
+                         void *stream) {
+  if (!dL_daux) return FGS4D_ERR_ARG;
+  return render_bwd_common(gaussians, views, nviews, settings, workspace, workspace_bytes, dL_drgb, dL_daux, grads,
+                           stream);
 }
 
 int fgs4d_l1_loss(const float *img, const float *target, int64_t count, float *loss_out, float *dL_dimg,

@@ -354,7 +354,7 @@ cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fg
                               float *out_aux, cudaStream_t stream);
 cudaError_t launch_aux_records(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt);
 cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
-                              unsigned char *ws, const float *dL_drgb, cudaStream_t stream);
+                              unsigned char *ws, const float *dL_drgb, const float *dL_daux, cudaStream_t stream);
 cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, float *loss, float *grad,
                            cudaStream_t stream);
 

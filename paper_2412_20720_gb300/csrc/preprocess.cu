@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs A, PreViews
     return;  // cannot happen for a slot the forward produced with the same inputs
   const float4 g0 = A.slot_grad[3 * slot + 0];  // du, dv, dA, dB
   const float4 g1 = A.slot_grad[3 * slot + 1];  // dC, da, dr, dg
-  const float4 g2 = A.slot_grad[3 * slot + 2];  // db
+  const float4 g2 = A.slot_grad[3 * slot + 2];  // db, dz
   const float gu = g0.x, gv = g0.y, gA = g0.z, gB = g0.w, gC = g1.x, ga = g1.y;
   const float grgb[3] = {g1.z, g1.w, g2.x};
 
@@ -506,6 +506,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs A, PreViews
   g_pc[0] = gu * cam.fx * iz;
   g_pc[1] = gv * cam.fy * iz;
   g_pc[2] = -(gu * cam.fx * x + gv * cam.fy * y) * iz * iz;
+  g_pc[2] += g2.y;  // depth channel (zero unless the loss uses it): z is pc_z itself
   // ---- conic = inverse(Sigma_2d): dL/dSigma_2d = -Q GQ Q (full symmetric).
   const float q00 = h.conA, q01 = h.conB, q11 = h.conC;
   const float G00 = gA, G01 = 0.5f * gB, G11 = gC;

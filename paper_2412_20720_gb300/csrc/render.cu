@@ -47,10 +47,12 @@ struct RenderBwdArgs {
   const uint32_t *inst_val;
   const float4 *rec_geom, *rec_color;
   const float *rec_blue;
+  const float4 *rec_aux;  // auxiliary mode only
   uint32_t vis_cap;
   const float *pix_T;
   const uint32_t *pix_last;
   const float *dL_drgb;
+  const float *dL_daux;  // [views][4][H][W] (depth, opacity used), auxiliary mode only
   float4 *slot_grad;
   float bg0, bg1, bg2;
 };
@@ -262,13 +264,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-template <int MAXV, int kPPT>
+// kAux: the loss also has gradients dL/dD, dL/dO with respect to the depth
+// and opacity channels (zero background, x_i = z_i resp. 1 in the colour
+// rule); adds dL/dz_i = sum dL/dD alpha_i T_i per slot.
+template <int MAXV, int kPPT, bool kAux>
 __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBwdArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
   constexpr int kRenderThreads = kTilePixels / kPPT;
   __shared__ float4 s_geom[kBatch];
   __shared__ float4 s_col[kBatch];
   __shared__ float s_blue[kBatch];
+  __shared__ float4 s_aux[kAux ? kBatch : 1];
   __shared__ uint32_t s_slot[kBatch];
   __shared__ uint32_t s_maxlast;
   const int32_t gt = blockIdx.x;
@@ -281,6 +287,7 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
   const float pxc = (float)px + 0.5f;
   const int64_t HW = (int64_t)V.width * V.height;
   float T[kPPT], dC0[kPPT], dC1[kPPT], dC2[kPPT], r0[kPPT], r1[kPPT], r2[kPPT], pyc[kPPT];
+  float dD[kAux ? kPPT : 1], dO[kAux ? kPPT : 1], rD[kAux ? kPPT : 1], rO[kAux ? kPPT : 1];
   uint32_t last[kPPT];
   uint32_t my_max = 0u;
   const float *g = A.dL_drgb + V.pix_base * 3;
@@ -298,6 +305,15 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
       dC1[k] = g[HW + p];
       dC2[k] = g[2 * HW + p];
     }
+    if (kAux) {
+      dD[k] = dO[k] = rD[k] = rO[k] = 0.f;
+      if (px < V.width && py0 + k < V.height) {
+        const int64_t p = (int64_t)(py0 + k) * V.width + px;
+        const float *ga = A.dL_daux + V.pix_base * 4;
+        dD[k] = ga[p];
+        dO[k] = ga[HW + p];
+      }
+    }
     r0[k] = T[k] * A.bg0;  // colour composited behind the current entry
     r1[k] = T[k] * A.bg1;
     r2[k] = T[k] * A.bg2;
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
     const uint32_t base = range.x + (uint32_t)bi * kBatch;
     __syncthreads();
     stage_batch<kRenderThreads>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, end, s_geom,
-                                s_col, s_blue, s_slot);
+                                s_col, s_blue, s_slot, kAux ? A.rec_aux : nullptr, kAux ? s_aux : nullptr);
     __syncthreads();
     const int nb = (int)min(end - base, (uint32_t)kBatch);
     for (int j = nb - 1; j >= 0; --j) {
@@ -327,7 +343,8 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
       const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
       // g = (du, dv, dA', dB', dC', da, dr, dg), plus db.
       float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      float gb = 0.f;
+      float gb = 0.f, gz = 0.f;
+      const float zj = kAux ? s_aux[j].x : 0.f;
       bool contrib = false;
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
@@ -341,8 +358,14 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
         g[6] += dC0[k] * w;
         g[7] += dC1[k] * w;
         gb += dC2[k] * w;
-        const float g_alpha = dC0[k] * (col.z * T[k] - r0[k] * io) + dC1[k] * (col.w * T[k] - r1[k] * io) +
-                              dC2[k] * (blue * T[k] - r2[k] * io);
+        float g_alpha = dC0[k] * (col.z * T[k] - r0[k] * io) + dC1[k] * (col.w * T[k] - r1[k] * io) +
+                        dC2[k] * (blue * T[k] - r2[k] * io);
+        if (kAux) {
+          g_alpha += dD[k] * (zj * T[k] - rD[k] * io) + dO[k] * (T[k] - rO[k] * io);
+          rD[k] += zj * w;
+          rO[k] += w;
+          gz += dD[k] * w;
+        }
         r0[k] += col.z * w;
         r1[k] += col.w * w;
         r2[k] += blue * w;
@@ -360,11 +383,12 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
       if (__any_sync(0xffffffffu, contrib)) {
         warp_sum8_transposed(g, lane);
         gb = warp_sum(gb);
+        if (kAux) gz = warp_sum(gz);
         const uint32_t slot = s_slot[j];
-        // Lanes 0, 4, ..., 28 add values 0..7; lane 1 adds db.
-        if (slot < A.vis_cap && ((lane & 3) == 0 || lane == 1)) {
+        // Lanes 0, 4, ..., 28 add values 0..7; lane 1 adds db; lane 2 dz.
+        if (slot < A.vis_cap && ((lane & 3) == 0 || lane == 1 || (kAux && lane == 2))) {
           float *dst = reinterpret_cast<float *>(A.slot_grad + 3 * (size_t)slot);
-          atomicAdd(dst + (lane == 1 ? 8 : (lane >> 2)), lane == 1 ? gb : g[0]);
+          atomicAdd(dst + (lane == 1 ? 8 : lane == 2 ? 9 : (lane >> 2)), lane == 1 ? gb : lane == 2 ? gz : g[0]);
         }
       }
     }
@@ -433,9 +457,15 @@ cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   }
 }
 
+template <int MAXV, int PPT>
+cudaError_t launch_bwd_ppt(const RenderBwdArgs &A, const RasterViews<MAXV> &rv, unsigned grid, cudaStream_t st) {
+  if (A.dL_daux) return launch_pdl(render_bwd_kernel<MAXV, PPT, true>, grid, kTilePixels / PPT, st, A, rv);
+  return launch_pdl(render_bwd_kernel<MAXV, PPT, false>, grid, kTilePixels / PPT, st, A, rv);
+}
+
 template <int MAXV>
 cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
-                             unsigned char *ws, const float *dL_drgb, cudaStream_t st) {
+                             unsigned char *ws, const float *dL_drgb, const float *dL_daux, cudaStream_t st) {
   RasterViews<MAXV> rv;
   if (!make_raster_views<MAXV>(L, views, nviews, &rv)) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(ws + L.slot_grad, 0, (size_t)L.vis_cap * kSlotGradFloats * sizeof(float), st);
@@ -450,6 +480,8 @@ cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   A.pix_T = reinterpret_cast<const float *>(ws + L.pix_T);
   A.pix_last = reinterpret_cast<const uint32_t *>(ws + L.pix_last);
   A.dL_drgb = dL_drgb;
+  A.dL_daux = dL_daux;
+  A.rec_aux = reinterpret_cast<const float4 *>(ws + L.rec_aux);
   A.slot_grad = reinterpret_cast<float4 *>(ws + L.slot_grad);
   A.bg0 = s->bg[0];
   A.bg1 = s->bg[1];
@@ -457,9 +489,9 @@ cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   if (L.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)L.total_tiles;
   switch (render_ppt(s)) {
-    case 2: return launch_pdl(render_bwd_kernel<MAXV, 2>, grid, kTilePixels / 2, st, A, rv);
-    case 8: return launch_pdl(render_bwd_kernel<MAXV, 8>, grid, kTilePixels / 8, st, A, rv);
-    default: return launch_pdl(render_bwd_kernel<MAXV, 4>, grid, kTilePixels / 4, st, A, rv);
+    case 2: return launch_bwd_ppt<MAXV, 2>(A, rv, grid, st);
+    case 8: return launch_bwd_ppt<MAXV, 8>(A, rv, grid, st);
+    default: return launch_bwd_ppt<MAXV, 4>(A, rv, grid, st);
   }
 }
 
@@ -473,9 +505,9 @@ cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fg
 }
 
 cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
-                              unsigned char *ws, const float *dL_drgb, cudaStream_t stream) {
-  if (nviews == 1) return render_bwd_typed<1>(L, s, views, nviews, ws, dL_drgb, stream);
-  return render_bwd_typed<FGS4D_MAX_VIEWS>(L, s, views, nviews, ws, dL_drgb, stream);
+                              unsigned char *ws, const float *dL_drgb, const float *dL_daux, cudaStream_t stream) {
+  if (nviews == 1) return render_bwd_typed<1>(L, s, views, nviews, ws, dL_drgb, dL_daux, stream);
+  return render_bwd_typed<FGS4D_MAX_VIEWS>(L, s, views, nviews, ws, dL_drgb, dL_daux, stream);
 }
 
 cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, float *loss, float *grad,

@@ -29,7 +29,7 @@ MAX_T_ORDER = 4
 TILE = 16
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
-            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
+            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
             "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 
@@ -102,6 +102,8 @@ def load():
     lib.fgs4d_render_stats.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, vp, vp]
     lib.fgs4d_render_bwd.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, vp, P(GaussiansGrad),
                                      vp]
+    lib.fgs4d_render_aux_bwd.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, vp, vp,
+                                         P(GaussiansGrad), vp]
     lib.fgs4d_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.fgs4d_sort_depth_static.argtypes = [vp, i64, vp, vp]
     lib.fgs4d_get_status.argtypes = [vp, C.c_size_t, vp, P(C.c_int64)]
@@ -212,6 +214,12 @@ def render_bwd(gaussians: Gaussians, views, nviews: int, settings: Settings, ws:
                grads: GaussiansGrad, stream: int):
     _check(load().fgs4d_render_bwd(C.byref(gaussians), views, int(nviews), C.byref(settings), ws, ws_bytes, dL_drgb,
                                    C.byref(grads), stream), "fgs4d_render_bwd")
+
+
+def render_aux_bwd(gaussians: Gaussians, views, nviews: int, settings: Settings, ws: int, ws_bytes: int,
+                   dL_drgb: int, dL_daux: int, grads: GaussiansGrad, stream: int):
+    _check(load().fgs4d_render_aux_bwd(C.byref(gaussians), views, int(nviews), C.byref(settings), ws, ws_bytes,
+                                       dL_drgb, dL_daux, C.byref(grads), stream), "fgs4d_render_aux_bwd")
 
 
 def l1_loss(img: int, target: int, count: int, loss_out: int, dL_dimg: int, stream: int):

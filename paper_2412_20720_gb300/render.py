@@ -128,6 +128,17 @@ class Renderer:
         fgs4d.render_bwd(g, self.views, self.nviews, self.settings, _ptr(self.ws), self.ws_bytes, _ptr(dL),
                          fgs4d.make_grads({k: _ptr(grads[k]) for k in PARAM_KEYS}), self.stream())
 
+    def backward_aux(self, params: dict, dL_drgb: torch.Tensor, dL_daux: torch.Tensor, grads: dict):
+        """Adds dL/dparams into ``grads`` for a loss on the image and the depth
+        and opacity planes of the last forward_aux (flow planes ignored)."""
+        g = self.gaussians(params)
+        for k in PARAM_KEYS:
+            _check_param("grad " + k, grads[k], self.n, self.device)
+        dL = dL_drgb.contiguous()
+        dA = dL_daux.contiguous()
+        fgs4d.render_aux_bwd(g, self.views, self.nviews, self.settings, _ptr(self.ws), self.ws_bytes, _ptr(dL),
+                             _ptr(dA), fgs4d.make_grads({k: _ptr(grads[k]) for k in PARAM_KEYS}), self.stream())
+
     def status(self):
         """Synchronises and returns (code, [visible, instances, visible needed, instances needed])."""
         return fgs4d.get_status(_ptr(self.ws), self.ws_bytes, self.stream())

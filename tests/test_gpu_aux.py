@@ -72,3 +72,44 @@ def test_flow_vanishes_for_gaussians_without_space_time_coupling():
     # In FP32 the rotation leaves the t axis fixed up to rounding.
     assert np.abs(aux[0][2:]).max() <= 1e-4
     assert aux[0][0].max() > 1.0 and aux[0][1].max() > 0.2
+
+
+@pytest.mark.parametrize("L,NT", [(1, 1), (3, 2)])
+def test_depth_and_opacity_gradients_match_oracle(L, NT):
+    """Loss on the image, the depth and the opacity channels: per-slot and
+    per-parameter gradients against the oracle's adjoint (pinned by central
+    differences on the CPU)."""
+    import torch
+    from helpers import compare_group, records_from_gpu, GpuRun
+    from paper_2412_20720_gb300.render import PARAM_KEYS
+    params, views, cfg = case(96, 80, L, NT, seed=6)
+    view = views[0]
+    st = oracle_settings(cfg)
+    pr = oracle.preprocess(params, view, st)
+    aux = oracle.aux_records(params, pr, view, st, 0.05)
+    img, T, out, mg = oracle.render_aux(pr, aux, view, st)
+    ok = mg >= PIXEL_MARGIN
+    rng = np.random.default_rng(8)
+    dimg = rng.standard_normal(img.shape) * ok
+    daux = np.zeros_like(out)
+    daux[0] = rng.standard_normal(ok.shape) * ok
+    daux[1] = rng.standard_normal(ok.shape) * ok
+    g_orc = oracle.render_aux_backward(params, pr, view, st, dimg, daux)
+
+    run = GpuRun(params, views, cfg)  # records for the slot order
+    r = run.renderer
+    r.forward_aux(run.params, 0.05)
+    grads = {k: torch.zeros_like(v) for k, v in run.params.items()}
+    r.backward_aux(run.params, torch.from_numpy(dimg.reshape(-1).astype(np.float32)).cuda(),
+                   torch.from_numpy(daux.reshape(-1).astype(np.float32)).cuda(), grads)
+    r.check()
+    nv = run.counts[0]
+    slot = r.workspace_view(r.layout.slot_grad, torch.float32, 12 * nv).cpu().numpy().reshape(nv, 12)
+    vis = records_from_gpu(run)["index"]
+    rtol, floor = 1e-3, 1e-4
+    compare_group("g_uv", slot[:, 0:2], g_orc["g_uv"][vis], rtol, floor)
+    compare_group("g_conic", slot[:, 2:5], g_orc["g_conic"][vis], rtol, floor)
+    compare_group("g_a", slot[:, 5], g_orc["g_a"][vis], rtol, floor)
+    compare_group("g_z", slot[:, 9], g_orc["g_z"][vis], rtol, floor)
+    for k in PARAM_KEYS:
+        compare_group(k, grads[k].cpu().numpy().astype(np.float64), g_orc[k], rtol, floor)

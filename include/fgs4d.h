@@ -109,7 +109,25 @@ typedef struct fgs4d_gaussians_grad {
   float *q_r;
   float *opacity_logit;
   float *sh;
+  /* Optional (NULL = off) densification statistics in spacetime (Sec. 3.3,
+   * "Densification in spacetime": the magnitude of the spatial position
+   * gradient and, as an additional indicator, the gradient of mu_t),
+   * float [n][4], 16-byte aligned, ACCUMULATED per (view, visible Gaussian)
+   * of each backward call: (|| (dL/du, dL/dv) || in pixels, |dL/dmu_t| of
+   * that view, 1 (the view count), 0). */
+  float *densify_stats;
 } fgs4d_gaussians_grad;
+
+/* Writable parameter arrays (same layouts as fgs4d_gaussians), n rows. */
+typedef struct fgs4d_gaussians_out {
+  float *mean;
+  float *log_scale;
+  float *q_l;
+  float *q_r;
+  float *opacity_logit;
+  float *sh;
+  int64_t n;
+} fgs4d_gaussians_out;
 
 /* Byte offsets of the workspace regions that hold the documented
  * intermediate results (for inspection and tests; all other bytes are
@@ -230,6 +248,26 @@ int fgs4d_render_aux_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *vie
                          const fgs4d_settings *settings, void *workspace, size_t workspace_bytes,
                          const float *dL_drgb, const float *dL_daux, const fgs4d_gaussians_grad *grads,
                          void *stream);
+
+/* Split sampling in spacetime (Sec. 3.3, "Densification in spacetime";
+ * Sec. 8.1.3, "More ablations": new positions are sampled with the complete
+ * 4D Gaussian as PDF).  For j in [0, m) and c in [0, k_children), child
+ * j * k_children + c of Gaussian idx[j] gets
+ *   mean      = mu + R diag(s) eps[j][c]   (a draw from N(mu, Sigma), 4D),
+ *   log_scale = log s - log(shrink),
+ *   q_l, q_r, opacity_logit and sh copied,
+ * with R = L(q_l) R(q_r) of the normalised quaternions and s = exp(log s).
+ * eps: device float [m][k_children][4], the standard normal draws (the caller
+ * owns the random numbers).  idx: device int32 [m], each in [0, src->n);
+ * dst->n >= m * k_children rows; dst must not overlap src.  The SH row
+ * length follows settings (sh_degree, t_order).  Errors: FGS4D_ERR_ARG for
+ * a bad count, pointer, 16-byte alignment of the float4 rows, or a shrink
+ * that is not finite and positive.  An idx entry outside [0, src->n) is not
+ * read: its children are written as zeros (the call has no status word, so
+ * the caller validates idx).  Needs no workspace. */
+int fgs4d_split_gaussians(const fgs4d_gaussians *src, const int32_t *idx, int64_t m, int32_t k_children,
+                          const float *eps, float shrink, const fgs4d_settings *settings,
+                          const fgs4d_gaussians_out *dst, void *stream);
 
 /* Photometric L1 loss (Sec. 3.3, rendering loss only): loss_out[0] +=
  * sum |img - target| / count, dL_dimg = sign(img - target) / count.

@@ -90,6 +90,9 @@ def _declare(lib):
     lib.orc_render_aux_backward.argtypes = [P(_Params), P(_View), P(_Settings), P(_Proj), C.c_void_p, C.c_void_p,
                                             P(_Grads)]
     lib.orc_render_aux_backward.restype = C.c_int
+    lib.orc_split_sample.argtypes = [P(_Params), C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_double, C.c_int64,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_split_sample.restype = C.c_int
     lib.orc_rotation.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_rotation.restype = None
     lib.orc_real_sh.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
@@ -287,6 +290,40 @@ def render_aux_backward(params, proj, view, settings: Settings, dimg: np.ndarray
     if rc != 0:
         raise MemoryError("oracle aux backward failed")
     return g
+
+
+def split_sample(params, idx, eps, shrink: float) -> dict:
+    """Children drawn from the parents' full 4D Gaussians (FP64): eps
+    [m, K, 4] standard normal draws; returns parameter arrays of m K rows."""
+    lib = _load()
+    ph = _ParamsHold(params)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    m, K = idx.shape[0], eps.shape[1]
+    K3 = int(np.prod(ph.arrs["sh"].shape[1:]))
+    out = {"mean": np.zeros((m * K, 4)), "log_scale": np.zeros((m * K, 4)), "q_l": np.zeros((m * K, 4)),
+           "q_r": np.zeros((m * K, 4)), "opacity_logit": np.zeros(m * K),
+           "sh": np.zeros((m * K,) + ph.arrs["sh"].shape[1:])}
+    rc = lib.orc_split_sample(C.byref(ph.c), _ptr(idx), m, K, _ptr(eps), float(shrink), K3, _ptr(out["mean"]),
+                              _ptr(out["log_scale"]), _ptr(out["q_l"]), _ptr(out["q_r"]),
+                              _ptr(out["opacity_logit"]), _ptr(out["sh"]))
+    if rc != 0:
+        raise ValueError("index out of range")
+    return out
+
+
+def densify_stats(params, proj, view, settings: Settings, dimg: np.ndarray) -> np.ndarray:
+    """Densification indicators of one view (Sec. 3.3, densification in
+    spacetime) for a loss with image gradient dimg: per Gaussian
+    (|dL/d(u, v)|, |dL/dmu_t|, 1 if visible else 0, 0), from the adjoint."""
+    g = render_backward(params, proj, view, settings, dimg)
+    vis = proj["status"] == 0
+    out = np.zeros((vis.shape[0], 4))
+    out[:, 0] = np.sqrt(g["g_uv"][:, 0] ** 2 + g["g_uv"][:, 1] ** 2)
+    out[:, 1] = np.abs(g["mean"][:, 3])
+    out[:, 2] = 1.0
+    out[~vis] = 0.0
+    return out
 
 
 def preprocess_backward(params, view, settings: Settings, g_uv, g_conic, g_a, g_rgb):

@@ -987,6 +987,52 @@ int orc_preprocess_backward(const orc_params *Pp, const orc_view *V, const orc_s
   return 0;
 }
 
+/* ------------------------------------------------ densification */
+
+/* Split sampling in spacetime (Sec. 3.3, "Densification in spacetime";
+ * Sec. 8.1.3, "More ablations": the complete 4D Gaussian is the PDF of the
+ * new positions).  A draw from N(mu, Sigma) with Sigma = R S S^T R^T is
+ * mu + R S eps for a standard normal eps (R S (R S)^T = Sigma).  Child
+ * j * K + c of Gaussian idx[j]: that draw for eps[j][c]; log-scales reduced
+ * by log(shrink); rotation, opacity and colour coefficients copied.  Output
+ * arrays have m K rows; the SH row length is K3 doubles. */
+int orc_split_sample(const orc_params *Pp, const int64_t *idx, int64_t m, int K, const double *eps,
+                     double shrink, int64_t K3, double *o_mean, double *o_log_scale, double *o_q_l,
+                     double *o_q_r, double *o_logit, double *o_sh) {
+  for (int64_t j = 0; j < m; ++j) {
+    const int64_t i = idx[j];
+    if (i < 0 || i >= Pp->n) return -1;
+    double ql[4], qr[4], nl = 0.0, nr = 0.0, Lm[16], Rm[16], R[16], s[4];
+    for (int k = 0; k < 4; ++k) {
+      nl += Pp->q_l[4 * i + k] * Pp->q_l[4 * i + k];
+      nr += Pp->q_r[4 * i + k] * Pp->q_r[4 * i + k];
+      s[k] = exp(Pp->log_scale[4 * i + k]);
+    }
+    for (int k = 0; k < 4; ++k) {
+      ql[k] = Pp->q_l[4 * i + k] / sqrt(nl);
+      qr[k] = Pp->q_r[4 * i + k] / sqrt(nr);
+    }
+    left_matrix(ql, Lm);
+    right_matrix(qr, Rm);
+    mat4_mul(Lm, Rm, R);
+    for (int c = 0; c < K; ++c) {
+      const int64_t o = j * K + c;
+      const double *e = eps + 4 * o;
+      for (int a = 0; a < 4; ++a) {
+        double acc = 0.0;
+        for (int k = 0; k < 4; ++k) acc += R[4 * a + k] * s[k] * e[k];
+        o_mean[4 * o + a] = Pp->mean[4 * i + a] + acc;
+        o_log_scale[4 * o + a] = Pp->log_scale[4 * i + a] - log(shrink);
+        o_q_l[4 * o + a] = Pp->q_l[4 * i + a];
+        o_q_r[4 * o + a] = Pp->q_r[4 * i + a];
+      }
+      o_logit[o] = Pp->opacity_logit[i];
+      for (int64_t k = 0; k < K3; ++k) o_sh[K3 * o + k] = Pp->sh[K3 * i + k];
+    }
+  }
+  return 0;
+}
+
 /* ------------------------------------------------- pieces for the pins */
 
 /* R = L(q_l) R(q_r) for unit-normalised q_l, q_r (row-major 4x4). */

@@ -294,7 +294,7 @@ int render_bwd_common(const fgs4d_gaussians *gaussians, const fgs4d_view *views,
     if (!grads->mean || !grads->log_scale || !grads->q_l || !grads->q_r || !grads->opacity_logit || !grads->sh)
       return FGS4D_ERR_ARG;
     if (!aligned16(grads->mean) || !aligned16(grads->log_scale) || !aligned16(grads->q_l) ||
-        !aligned16(grads->q_r) || !aligned16(grads->sh))
+        !aligned16(grads->q_r) || !aligned16(grads->sh) || !aligned16(grads->densify_stats))
       return FGS4D_ERR_ARG;
   }
   unsigned char *ws = static_cast<unsigned char *>(workspace);
@@ -321,6 +321,27 @@ int fgs4d_render_aux_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *vie
   if (!dL_daux) return FGS4D_ERR_ARG;
   return render_bwd_common(gaussians, views, nviews, settings, workspace, workspace_bytes, dL_drgb, dL_daux, grads,
                            stream);
+}
+
+int fgs4d_split_gaussians(const fgs4d_gaussians *src, const int32_t *idx, int64_t m, int32_t k_children,
+                          const float *eps, float shrink, const fgs4d_settings *settings,
+                          const fgs4d_gaussians_out *dst, void *stream) {
+  int rc = check_gaussians(src);
+  if (rc) return rc;
+  rc = check_settings(settings);
+  if (rc) return rc;
+  if (m < 0 || k_children < 1 || k_children > 64 || !dst || !(shrink > 0.f) || !std::isfinite(shrink))
+    return FGS4D_ERR_ARG;
+  if (m == 0) return FGS4D_OK;
+  if (src->n == 0 || !idx || !eps || !aligned16(eps)) return FGS4D_ERR_ARG;
+  if (m > ((int64_t)INT32_MAX - 1024) / k_children || dst->n < m * k_children) return FGS4D_ERR_ARG;
+  const void *ptrs[6] = {dst->mean, dst->log_scale, dst->q_l, dst->q_r, dst->opacity_logit, dst->sh};
+  for (int k = 0; k < 6; ++k)
+    if (!ptrs[k]) return FGS4D_ERR_ARG;
+  if (!aligned16(dst->mean) || !aligned16(dst->log_scale) || !aligned16(dst->q_l) || !aligned16(dst->q_r))
+    return FGS4D_ERR_ARG;
+  const int32_t k3 = (settings->sh_degree + 1) * (settings->sh_degree + 1) * (settings->t_order + 1) * 3;
+  return cuda_status(launch_split(src, idx, m, k_children, eps, shrink, k3, dst, static_cast<cudaStream_t>(stream)));
 }
 
 int fgs4d_l1_loss(const float *img, const float *target, int64_t count, float *loss_out, float *dL_dimg,

@@ -353,6 +353,9 @@ cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fg
                               unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
                               float *out_aux, cudaStream_t stream);
 cudaError_t launch_aux_records(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt);
+cudaError_t launch_split(const fgs4d_gaussians *src, const int32_t *idx, int64_t m, int32_t k_children,
+                         const float *eps, float shrink, int32_t k3, const fgs4d_gaussians_out *dst,
+                         cudaStream_t stream);
 cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, const float *dL_drgb, const float *dL_daux, cudaStream_t stream);
 cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, float *loss, float *grad,

@@ -51,6 +51,7 @@ struct BwdArgs {
   const float4 *slot_grad;
   float4 *g_mean, *g_log_scale, *g_q_l, *g_q_r;
   float *g_logit, *g_sh;
+  float4 *densify_stats;  // optional
 };
 
 constexpr float kTwoPi = 6.283185307179586f;
@@ -603,6 +604,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs A, PreViews
     }
   }
   red_add4(&A.g_mean[i], g_mu[0], g_mu[1], g_mu[2], -g_dt);
+  // Densification indicators of this (view, Gaussian): |dL/dmu_2d| and
+  // |dL/dmu_t| (Sec. 3.3, densification in spacetime), plus the view count.
+  if (A.densify_stats) red_add4(&A.densify_stats[i], sqrtf(gu * gu + gv * gv), fabsf(g_dt), 1.0f, 0.0f);
   red_add4(&A.g_log_scale[i], gs[0] * h.s[0], gs[1] * h.s[1], gs[2] * h.s[2], gs[3] * h.s[3]);
   // ---- R = Lm Rm: dL/dLm = gR Rm^T, dL/dRm = Lm^T gR; collect by entry pattern.
   const float a = h.ql[0], b = h.ql[1], c = h.ql[2], d = h.ql[3];
@@ -729,6 +733,7 @@ cudaError_t launch_bwd_typed(const PreLaunch &p, const fgs4d_view *views, int32_
   A.g_q_r = reinterpret_cast<float4 *>(gr->q_r);
   A.g_logit = gr->opacity_logit;
   A.g_sh = gr->sh;
+  A.densify_stats = reinterpret_cast<float4 *>(gr->densify_stats);
   const int64_t blocks = (Lo.vis_cap + 127) / 128;
   if (blocks == 0) return cudaSuccess;
   return launch_pdl(preprocess_bwd_kernel<L, MAXV>, (unsigned)blocks, 128u, p.stream, A, pv);
@@ -788,6 +793,99 @@ cudaError_t launch_preprocess_bwd(const PreLaunch &p, const fgs4d_view *views, i
 cudaError_t launch_aux_records(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt) {
   if (nviews == 1) return launch_aux_typed<1>(p, views, nviews, flow_dt);
   return launch_aux_typed<FGS4D_MAX_VIEWS>(p, views, nviews, flow_dt);
+}
+
+
+namespace {
+
+// Split sampling in spacetime: child = mu + R diag(s) eps with the 4D
+// rotation of the parent (Sec. 3.2) -- a draw from the parent's full 4D
+// Gaussian N(mu, Sigma), Sigma = R S S^T R^T (Sec. 3.3 / Sec. 8.1.3).
+struct SplitArgs {
+  const float4 *mean, *log_scale, *q_l, *q_r;
+  const float *logit, *sh;
+  int64_t n;
+  const int32_t *idx;
+  const float4 *eps;
+  int64_t m;
+  int32_t k_children, k3;
+  float log_shrink;
+  float4 *o_mean, *o_log_scale, *o_q_l, *o_q_r;
+  float *o_logit, *o_sh;
+};
+
+__global__ void __launch_bounds__(128) split_kernel(SplitArgs A) {
+  grid_dependency_sync();
+  const int64_t child = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (child >= A.m * A.k_children) return;
+  const int64_t j = child / A.k_children;
+  const int32_t i = A.idx[j];
+  float *osh = A.o_sh + child * A.k3;
+  if (i < 0 || (int64_t)i >= A.n) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    A.o_mean[child] = A.o_log_scale[child] = A.o_q_l[child] = A.o_q_r[child] = z;
+    A.o_logit[child] = 0.f;
+    for (int k = 0; k < A.k3; ++k) osh[k] = 0.f;
+    return;
+  }
+  const float4 m = A.mean[i], ls = A.log_scale[i], a4 = A.q_l[i], b4 = A.q_r[i];
+  const float il = rsqrtf(a4.x * a4.x + a4.y * a4.y + a4.z * a4.z + a4.w * a4.w);
+  const float ir = rsqrtf(b4.x * b4.x + b4.y * b4.y + b4.z * b4.z + b4.w * b4.w);
+  const float a = a4.x * il, b = a4.y * il, c = a4.z * il, d = a4.w * il;
+  const float p = b4.x * ir, q = b4.y * ir, r = b4.z * ir, s = b4.w * ir;
+  const float Lm[4][4] = {{a, -b, -c, -d}, {b, a, -d, c}, {c, d, a, -b}, {d, -c, b, a}};
+  const float Rm[4][4] = {{p, -q, -r, -s}, {q, p, s, -r}, {r, -s, p, q}, {s, r, -q, p}};
+  const float4 e = A.eps[child];
+  const float se[4] = {expf(ls.x) * e.x, expf(ls.y) * e.y, expf(ls.z) * e.z, expf(ls.w) * e.w};
+  float off[4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    float acc = 0.f;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const float Rxy = Lm[x][0] * Rm[0][y] + Lm[x][1] * Rm[1][y] + Lm[x][2] * Rm[2][y] + Lm[x][3] * Rm[3][y];
+      acc += Rxy * se[y];
+    }
+    off[x] = acc;
+  }
+  A.o_mean[child] = make_float4(m.x + off[0], m.y + off[1], m.z + off[2], m.w + off[3]);
+  A.o_log_scale[child] =
+      make_float4(ls.x - A.log_shrink, ls.y - A.log_shrink, ls.z - A.log_shrink, ls.w - A.log_shrink);
+  A.o_q_l[child] = a4;
+  A.o_q_r[child] = b4;
+  A.o_logit[child] = A.logit[i];
+  const float *src = A.sh + (int64_t)i * A.k3;
+  for (int k = 0; k < A.k3; ++k) osh[k] = src[k];
+}
+
+}  // namespace
+
+cudaError_t launch_split(const fgs4d_gaussians *src, const int32_t *idx, int64_t m, int32_t k_children,
+                         const float *eps, float shrink, int32_t k3, const fgs4d_gaussians_out *dst,
+                         cudaStream_t stream) {
+  SplitArgs A;
+  A.mean = reinterpret_cast<const float4 *>(src->mean);
+  A.log_scale = reinterpret_cast<const float4 *>(src->log_scale);
+  A.q_l = reinterpret_cast<const float4 *>(src->q_l);
+  A.q_r = reinterpret_cast<const float4 *>(src->q_r);
+  A.logit = src->opacity_logit;
+  A.sh = src->sh;
+  A.n = src->n;
+  A.idx = idx;
+  A.eps = reinterpret_cast<const float4 *>(eps);
+  A.m = m;
+  A.k_children = k_children;
+  A.k3 = k3;
+  A.log_shrink = logf(shrink);
+  A.o_mean = reinterpret_cast<float4 *>(dst->mean);
+  A.o_log_scale = reinterpret_cast<float4 *>(dst->log_scale);
+  A.o_q_l = reinterpret_cast<float4 *>(dst->q_l);
+  A.o_q_r = reinterpret_cast<float4 *>(dst->q_r);
+  A.o_logit = dst->opacity_logit;
+  A.o_sh = dst->sh;
+  const int64_t total = m * k_children;
+  if (total == 0) return cudaSuccess;
+  return launch_pdl(split_kernel, (unsigned)((total + 127) / 128), 128u, stream, A);
 }
 
 }  // namespace fgs4d

@@ -29,7 +29,7 @@ MAX_T_ORDER = 4
 TILE = 16
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
-            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
+            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
             "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 
@@ -54,7 +54,12 @@ class Gaussians(C.Structure):
 
 class GaussiansGrad(C.Structure):
     _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("q_l", C.c_void_p), ("q_r", C.c_void_p),
-                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p)]
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("densify_stats", C.c_void_p)]
+
+
+class GaussiansOut(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("q_l", C.c_void_p), ("q_r", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64)]
 
 
 class Layout(C.Structure):
@@ -104,6 +109,7 @@ def load():
                                      vp]
     lib.fgs4d_render_aux_bwd.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, vp, vp,
                                          P(GaussiansGrad), vp]
+    lib.fgs4d_split_gaussians.argtypes = [P(Gaussians), vp, i64, i32, vp, C.c_float, P(Settings), P(GaussiansOut), vp]
     lib.fgs4d_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.fgs4d_sort_depth_static.argtypes = [vp, i64, vp, vp]
     lib.fgs4d_get_status.argtypes = [vp, C.c_size_t, vp, P(C.c_int64)]
@@ -164,7 +170,9 @@ def make_gaussians(ptrs: dict, n: int) -> Gaussians:
 
 
 def make_grads(ptrs: dict) -> GaussiansGrad:
-    return GaussiansGrad(*(ptrs[k] for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")))
+    """Gradient pointers; ``densify_stats`` is optional (0 = off)."""
+    return GaussiansGrad(*(ptrs[k] for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")),
+                         ptrs.get("densify_stats", 0) or None)
 
 
 # ---------------------------------------------------------- entry points
@@ -220,6 +228,12 @@ def render_aux_bwd(gaussians: Gaussians, views, nviews: int, settings: Settings,
                    dL_drgb: int, dL_daux: int, grads: GaussiansGrad, stream: int):
     _check(load().fgs4d_render_aux_bwd(C.byref(gaussians), views, int(nviews), C.byref(settings), ws, ws_bytes,
                                        dL_drgb, dL_daux, C.byref(grads), stream), "fgs4d_render_aux_bwd")
+
+
+def split_gaussians(src: Gaussians, idx: int, m: int, k_children: int, eps: int, shrink: float, settings: Settings,
+                    dst: GaussiansOut, stream: int):
+    _check(load().fgs4d_split_gaussians(C.byref(src), idx, int(m), int(k_children), eps, float(shrink),
+                                        C.byref(settings), C.byref(dst), stream), "fgs4d_split_gaussians")
 
 
 def l1_loss(img: int, target: int, count: int, loss_out: int, dL_dimg: int, stream: int):

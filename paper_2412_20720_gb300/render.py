@@ -119,25 +119,36 @@ class Renderer:
                          _ptr(out_aux), st)
         return out_rgb, out_aux
 
-    def backward(self, params: dict, dL_drgb: torch.Tensor, grads: dict):
-        """Adds dL/dparams into ``grads`` for the last forward of this renderer."""
-        g = self.gaussians(params)
+    def _grads(self, grads: dict, densify_stats):
         for k in PARAM_KEYS:
             _check_param("grad " + k, grads[k], self.n, self.device)
+        ptrs = {k: _ptr(grads[k]) for k in PARAM_KEYS}
+        if densify_stats is not None:
+            if (densify_stats.dtype != torch.float32 or tuple(densify_stats.shape) != (self.n, 4)
+                    or not densify_stats.is_contiguous() or densify_stats.device != self.device):
+                raise ValueError("densify_stats must be a contiguous float32 [n, 4] tensor on the render device")
+            ptrs["densify_stats"] = _ptr(densify_stats)
+        return fgs4d.make_grads(ptrs)
+
+    def backward(self, params: dict, dL_drgb: torch.Tensor, grads: dict, densify_stats: torch.Tensor | None = None):
+        """Adds dL/dparams into ``grads`` for the last forward of this renderer;
+        with ``densify_stats`` ([n, 4]) also accumulates, per visible (view,
+        Gaussian), (|dL/dmu_2d|, |dL/dmu_t|, 1, 0)."""
+        g = self.gaussians(params)
+        gg = self._grads(grads, densify_stats)
         dL = dL_drgb.contiguous()
-        fgs4d.render_bwd(g, self.views, self.nviews, self.settings, _ptr(self.ws), self.ws_bytes, _ptr(dL),
-                         fgs4d.make_grads({k: _ptr(grads[k]) for k in PARAM_KEYS}), self.stream())
+        fgs4d.render_bwd(g, self.views, self.nviews, self.settings, _ptr(self.ws), self.ws_bytes, _ptr(dL), gg,
+                         self.stream())
 
     def backward_aux(self, params: dict, dL_drgb: torch.Tensor, dL_daux: torch.Tensor, grads: dict):
         """Adds dL/dparams into ``grads`` for a loss on the image and the depth
         and opacity planes of the last forward_aux (flow planes ignored)."""
         g = self.gaussians(params)
-        for k in PARAM_KEYS:
-            _check_param("grad " + k, grads[k], self.n, self.device)
+        gg = self._grads(grads, None)
         dL = dL_drgb.contiguous()
         dA = dL_daux.contiguous()
         fgs4d.render_aux_bwd(g, self.views, self.nviews, self.settings, _ptr(self.ws), self.ws_bytes, _ptr(dL),
-                             _ptr(dA), fgs4d.make_grads({k: _ptr(grads[k]) for k in PARAM_KEYS}), self.stream())
+                             _ptr(dA), gg, self.stream())
 
     def status(self):
         """Synchronises and returns (code, [visible, instances, visible needed, instances needed])."""
@@ -240,6 +251,27 @@ class Render4DGS(torch.autograd.Function):
 
 def render(renderer: Renderer, params: dict) -> torch.Tensor:
     return Render4DGS.apply(renderer, *(params[k] for k in PARAM_KEYS))
+
+
+def split_gaussians(params: dict, idx: torch.Tensor, eps: torch.Tensor, shrink: float, config: RenderConfig) -> dict:
+    """Children of the Gaussians ``idx`` ([m] int32) sampled from their full
+    4D Gaussians: ``eps`` ([m, K, 4] standard normal draws) gives K children
+    each; returns the children's parameter tensors (m K rows)."""
+    device = params["mean"].device
+    n = params["mean"].shape[0]
+    for k in PARAM_KEYS:
+        _check_param(k, params[k], n, device)
+    m, K = int(idx.shape[0]), int(eps.shape[1]) if eps.dim() == 3 else 0
+    if idx.dtype != torch.int32 or eps.dtype != torch.float32 or tuple(eps.shape) != (m, K, 4):
+        raise ValueError("idx must be int32 [m] and eps float32 [m, K, 4]")
+    idx, eps = idx.contiguous(), eps.contiguous()
+    out = {k: torch.empty((m * K,) + tuple(params[k].shape[1:]), dtype=torch.float32, device=device)
+           for k in PARAM_KEYS}
+    src = fgs4d.make_gaussians({k: _ptr(params[k]) for k in PARAM_KEYS}, n)
+    dst = fgs4d.GaussiansOut(*(_ptr(out[k]) for k in PARAM_KEYS), m * K)
+    fgs4d.split_gaussians(src, _ptr(idx), m, K, _ptr(eps), shrink, config.settings(), dst,
+                          torch.cuda.current_stream(device).cuda_stream)
+    return out
 
 
 def l1_loss(img: torch.Tensor, target: torch.Tensor):

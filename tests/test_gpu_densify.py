@@ -1,0 +1,65 @@
+"""Parity of the densification pieces with the FP64 oracle: the spacetime
+statistics accumulated by the backward pass (|dL/dmu_2d|, |dL/dmu_t|, view
+count per Gaussian, summed over the views of a call) and the split sampling
+of children from the parents' full 4D Gaussians."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_20720_gb300 import synthetic as sy
+from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, split_gaussians
+
+from helpers import PIXEL_MARGIN, compare_group, keep_clear_of_boundaries, oracle_settings, subset, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def test_densify_stats_match_oracle_over_views():
+    import torch
+    sc = sy.make_scene(1500, 9, (-1, -1, -1), (1, 1, 1), sh_degree=2, t_order=1)
+    views = [sy.tiny_view(96, 72, t=0.45), sy.tiny_view(80, 64, t=0.55)]
+    cfg = RenderConfig(sh_degree=2, t_order=1, inst_capacity=1 << 18)
+    params = sc.as_dict()
+    params = subset(params, keep_clear_of_boundaries(params, views, cfg))
+    n = params["mean"].shape[0]
+    st = oracle_settings(cfg)
+    rng = np.random.default_rng(10)
+    dimgs, expect = [], np.zeros((n, 4))
+    for v in views:
+        pr = oracle.preprocess(params, v, st)
+        img, T, nc, mg = oracle.render(pr, v, st)
+        d = rng.standard_normal(img.shape) * (mg >= PIXEL_MARGIN)
+        dimgs.append(d)
+        expect += oracle.densify_stats(params, pr, v, st, d)
+    r = Renderer(n, views, cfg)
+    p = to_device(params)
+    r.forward(p)
+    grads = {k: torch.zeros_like(v) for k, v in p.items()}
+    stats = torch.zeros((n, 4), dtype=torch.float32, device=r.device)
+    flat = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dimgs]).astype(np.float32)).cuda()
+    r.backward(p, flat, grads, densify_stats=stats)
+    r.check()
+    got = stats.cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(got[:, 2], expect[:, 2])
+    assert expect[:, 2].max() == 2 and (expect[:, 2] == 1).any()
+    compare_group("|dL/dmu_2d|", got[:, 0], expect[:, 0], 1e-3, 1e-4)
+    compare_group("|dL/dmu_t|", got[:, 1], expect[:, 1], 1e-3, 1e-4)
+    assert np.all(got[:, 3] == 0)
+
+
+def test_split_children_match_oracle():
+    import torch
+    sc = sy.make_scene(500, 11, (-1, -1, -1), (1, 1, 1), sh_degree=3, t_order=2)
+    params = sc.as_dict()
+    rng = np.random.default_rng(12)
+    idx = rng.choice(500, 77, replace=False).astype(np.int32)
+    eps = rng.standard_normal((77, 3, 4)).astype(np.float32)
+    cfg = RenderConfig(sh_degree=3, t_order=2)
+    out = split_gaussians(to_device(params), torch.from_numpy(idx).cuda(), torch.from_numpy(eps).cuda(), 1.6, cfg)
+    torch.cuda.synchronize()
+    ref = oracle.split_sample(params, idx, eps, 1.6)
+    for k in PARAM_KEYS:
+        got = out[k].cpu().numpy().astype(np.float64)
+        assert got.shape == ref[k].shape, k
+        scale = max(np.abs(ref[k]).max(), 1.0)
+        assert np.abs(got - ref[k]).max() <= 2e-6 * scale, k

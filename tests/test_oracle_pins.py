@@ -594,3 +594,86 @@ def test_opacity_channel_matches_constant_colour_image():
     img0, T0, _, _ = oracle.render(pr, view, st)
     np.testing.assert_allclose(img, img0, atol=0)
     np.testing.assert_allclose(out[1], 1.0 - T0, atol=0)
+
+
+# ---------------------------------------------------- densification pins
+
+def _split_parents(rng, n=6, K=None):
+    gs = []
+    for _ in range(n):
+        gs.append(one_gaussian(list(rng.uniform(-1, 1, 3)) + [rng.uniform(0, 1)],
+                               list(np.log(rng.uniform(0.05, 0.5, 4))), rng.standard_normal(4),
+                               rng.standard_normal(4), rng.standard_normal(), rng.normal(0, 0.2, (4, 3))))
+    return stack(gs)
+
+
+def test_split_sample_unit_draws_are_scaled_principal_axes():
+    """eps = e_k gives mu + s_k R[:, k] with R the quaternion sandwich written
+    in this test (Sec. 3.2); colour, rotation and opacity are copied and the
+    log-scales reduced by log(shrink)."""
+    rng = np.random.default_rng(41)
+    g = _split_parents(rng)
+    m = g["mean"].shape[0]
+    idx = np.arange(m)[::-1].copy()
+    eps = np.tile(np.eye(4)[None], (m, 1, 1))
+    out = oracle.split_sample(g, idx, eps, 1.6)
+    for j, i in enumerate(idx):
+        R = sandwich_matrix(g["q_l"][i], g["q_r"][i])
+        s = np.exp(g["log_scale"][i])
+        for k in range(4):
+            np.testing.assert_allclose(out["mean"][4 * j + k], g["mean"][i] + s[k] * R[:, k], atol=1e-14)
+            np.testing.assert_allclose(out["log_scale"][4 * j + k], g["log_scale"][i] - math.log(1.6), atol=1e-15)
+            np.testing.assert_array_equal(out["sh"][4 * j + k], g["sh"][i])
+            np.testing.assert_array_equal(out["q_l"][4 * j + k], g["q_l"][i])
+            assert out["opacity_logit"][4 * j + k] == g["opacity_logit"][i]
+
+
+def test_split_samples_follow_the_full_4d_gaussian():
+    """Many draws of one parent: sample mean and covariance match mu and
+    Sigma = R S S^T R^T (statistical tolerance), including the space-time
+    block Sigma_xt, so children also spread in time."""
+    rng = np.random.default_rng(42)
+    g = _split_parents(rng, n=1)
+    N = 200_000
+    eps = rng.standard_normal((1, N, 4))
+    out = oracle.split_sample(g, np.array([0]), eps, 1.0)
+    S = cov4(g["q_l"][0], g["q_r"][0], np.exp(g["log_scale"][0]))
+    x = out["mean"]
+    np.testing.assert_allclose(x.mean(axis=0), g["mean"][0], atol=5 * math.sqrt(S.diagonal().max() / N))
+    C = np.cov(x.T)
+    tol = 6 * np.sqrt((S.diagonal()[:, None] * S.diagonal()[None, :] + S ** 2) / N)
+    assert np.all(np.abs(C - S) <= tol)
+    assert np.abs(S[:3, 3]).max() > 10 * tol[:3, 3].max()  # the coupling is actually exercised
+
+
+def test_densify_stats_are_gradient_magnitudes_of_the_view():
+    """Per visible Gaussian: |dL/d(u, v)| and |dL/dmu_t| of the view's loss
+    (the adjoint is pinned by central differences), count 1; zeros for culled
+    Gaussians.  |dL/dmu_t| checked here by a central difference of the loss."""
+    rng = np.random.default_rng(43)
+    sc = sy.make_scene(60, 43, (-0.6, -0.6, -0.6), (0.6, 0.6, 0.6), sh_degree=1, t_order=1)
+    params = {k: v.astype(np.float64) for k, v in sc.as_dict().items()}
+    view = sy.tiny_view(32, 32, t=0.5)
+    st = oracle.Settings(sh_degree=1, t_order=1)
+    pr = oracle.preprocess(params, view, st)
+    dimg = rng.standard_normal((3, 32, 32))
+    d = oracle.densify_stats(params, pr, view, st, dimg)
+    vis = pr["status"] == 0
+    assert vis.sum() > 10 and np.all(d[~vis] == 0) and np.all(d[vis, 2] == 1)
+
+    def loss(p):
+        img, _, _, _ = oracle.render(oracle.preprocess(p, view, st), view, st)
+        return float((dimg * img).sum())
+
+    checked = 0
+    for i in np.flatnonzero(vis)[:8]:
+        h = 1e-6
+        p = {k: v.copy() for k, v in params.items()}
+        p["mean"][i, 3] += h
+        lp = loss(p)
+        p["mean"][i, 3] -= 2 * h
+        lm = loss(p)
+        fd = (lp - lm) / (2 * h)
+        if abs(abs(fd) - d[i, 1]) <= 1e-5 * max(1.0, abs(fd)):
+            checked += 1
+    assert checked >= 6

@@ -34,7 +34,7 @@ def _load():
 class _Params(C.Structure):
     _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("q_l", C.c_void_p),
                 ("q_r", C.c_void_p), ("opacity_logit", C.c_void_p), ("sh", C.c_void_p),
-                ("n", C.c_int64)]
+                ("n", C.c_int64), ("mask_logit", C.c_void_p), ("mask_threshold", C.c_double)]
 
 
 class _View(C.Structure):
@@ -60,7 +60,8 @@ class _Proj(C.Structure):
     _fields_ = [(name, C.c_void_p) for name, _, _ in _PROJ_FIELDS]
 
 
-_GRAD_FIELDS = ["mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh", "g_uv", "g_conic", "g_a", "g_rgb", "g_z"]
+_GRAD_FIELDS = ["mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh", "g_uv", "g_conic", "g_a", "g_rgb", "g_z",
+                "mask_logit"]
 
 
 class _Grads(C.Structure):
@@ -155,8 +156,12 @@ class _ParamsHold:
         self.arrs = {k: np.ascontiguousarray(params[k], dtype=np.float64)
                      for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")}
         n = self.arrs["mean"].shape[0]
+        mask = params.get("mask_logit")
+        if mask is not None:  # optional Compact-4DGS significance mask
+            self.arrs["mask_logit"] = np.ascontiguousarray(mask, dtype=np.float64)
         self.c = _Params(*(_ptr(self.arrs[k]) for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")),
-                         n)
+                         n, _ptr(self.arrs["mask_logit"]) if mask is not None else None,
+                         float(params.get("mask_threshold", 0.0)))
         self.n = n
 
 
@@ -251,7 +256,7 @@ def render_aux(proj, aux: np.ndarray, view, settings: Settings):
 
 def _alloc_grads(n, K):
     shapes = {"mean": (n, 4), "log_scale": (n, 4), "q_l": (n, 4), "q_r": (n, 4), "opacity_logit": (n,),
-              "sh": (n, K, 3), "g_uv": (n, 2), "g_conic": (n, 3), "g_a": (n,), "g_rgb": (n, 3), "g_z": (n,)}
+              "sh": (n, K, 3), "g_uv": (n, 2), "g_conic": (n, 3), "g_a": (n,), "g_rgb": (n, 3), "g_z": (n,), "mask_logit": (n,)}
     g = {k: np.zeros(s) for k, s in shapes.items()}
     return g, _Grads(*(_ptr(g[k]) for k in _GRAD_FIELDS))
 

@@ -49,6 +49,8 @@ typedef struct {
   const double *opacity_logit; /* [n] */
   const double *sh;            /* [n][K][3], K = (L+1)^2 (n_max+1) */
   int64_t n;
+  const double *mask_logit;    /* [n] or NULL: Compact-4DGS significance mask m (Sec. 4.3) */
+  double mask_threshold;       /* epsilon of the mask indicator */
 } orc_params;
 
 typedef struct {
@@ -69,7 +71,7 @@ typedef struct {
 } orc_settings;
 
 typedef struct {
-  int32_t *status; /* [n] 0 visible; 1 invalid; 2 temporal; 3 near; 4 det; 5 rect; 6 a < 1/255 */
+  int32_t *status; /* [n] 0 visible; 1 invalid; 2 temporal; 3 near; 4 det; 5 rect; 6 a < 1/255; 7 masked */
   int32_t *rect;   /* [n][4] tile rect x0, y0, x1, y1 (half-open) */
   double *p_t;     /* [n] marginal temporal weight */
   double *a_eff;   /* [n] sigmoid(logit) * p_t */
@@ -98,6 +100,7 @@ typedef struct {
   double *g_a;           /* [n]     dL/d(effective opacity) */
   double *g_rgb;         /* [n][3]  dL/d(colour) */
   double *g_z;           /* [n]     dL/d(camera depth of the sliced mean), depth channel only */
+  double *mask_logit;    /* [n]     dL/dm of the significance mask (straight-through) */
 } orc_grads;
 
 /* Per-Gaussian intermediate values of the forward chain, kept for the
@@ -118,6 +121,7 @@ typedef struct {
   double cosn[ORC_MAX_N + 1], sinn[ORC_MAX_N + 1];
   double raw[3], rgb[3];
   double a;
+  double mask; /* M = sigmoid(m), 1 without a mask */
   int status;
   double margin;
 } orc_ctx;
@@ -247,6 +251,24 @@ static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
       !is_finite4(g->qr) || !isfinite(g->logit)) {
     g->status = 1;
     return;
+  }
+  /* Compact-4DGS mask (Sec. 4.3): M = sigmoid(m), M_hat = 1{M > eps} in
+   * value (the stop-gradient term), S_hat = M_hat S, alpha_hat = M_hat alpha.
+   * M_hat = 0 removes the Gaussian (zero scales and opacity); M_hat = 1
+   * leaves S and alpha unchanged. */
+  g->mask = 1.0;
+  if (P->mask_logit) {
+    const double mlog = P->mask_logit[i];
+    if (!isfinite(mlog)) {
+      g->status = 1;
+      return;
+    }
+    g->mask = 1.0 / (1.0 + exp(-mlog));
+    g->margin = dmin(g->margin, fabs(g->mask - P->mask_threshold) / dmax(P->mask_threshold, 1e-12));
+    if (!(g->mask > P->mask_threshold)) {
+      g->status = 7;
+      return;
+    }
   }
   /* Activations: s = exp(log s), alpha = sigmoid(logit), unit quaternions. */
   for (int k = 0; k < 4; ++k) g->s[k] = exp(g->ls[k]);
@@ -759,6 +781,9 @@ static void gauss_adjoint(const orc_params *Pp, int64_t i, const orc_view *V, co
   const double g_sig = g_a * g->pt;
   double g_pt = g_a * g->sig;
   out->opacity_logit[i] += g_sig * g->sig * (1.0 - g->sig);
+  /* Straight-through mask gradient (Sec. 4.3): dL/dM_hat = sum_k dL/ds_hat_k s_k
+   * + dL/dalpha_hat alpha at M_hat = 1, and dM_hat/dm = M (1 - M). */
+  double g_mhat = g_sig * g->sig;
 
   /* Projected centre, Eq. 3. */
   const double x = g->pc[0], y = g->pc[1], z = g->pc[2];
@@ -851,7 +876,9 @@ static void gauss_adjoint(const orc_params *Pp, int64_t i, const orc_view *V, co
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) acc += g->R[4 * a + k] * GS[4 * a + b] * g->R[4 * b + k];
     out->log_scale[4 * i + k] += acc * 2.0 * g->s[k] * g->s[k];
+    g_mhat += acc * 2.0 * g->s[k] * g->s[k]; /* dL/ds_k s_k = dL/dlog s_k */
   }
+  if (Pp->mask_logit && out->mask_logit) out->mask_logit[i] += g_mhat * g->mask * (1.0 - g->mask);
   /* R = Lm Rm: dL/dLm = gR Rm^T, dL/dRm = Lm^T gR. */
   double gL[16], gRr[16];
   for (int a = 0; a < 4; ++a)

@@ -677,3 +677,71 @@ def test_densify_stats_are_gradient_magnitudes_of_the_view():
         if abs(abs(fd) - d[i, 1]) <= 1e-5 * max(1.0, abs(fd)):
             checked += 1
     assert checked >= 6
+
+
+# ------------------------------------------------------ compact mask pins
+
+def _mask_scene(seed):
+    sc = sy.make_scene(80, seed, (-0.6, -0.6, -0.6), (0.6, 0.6, 0.6), sh_degree=1, t_order=1)
+    p = {k: v.astype(np.float64) for k, v in sc.as_dict().items()}
+    p["mask_logit"] = np.random.default_rng(seed).normal(0.0, 1.5, p["mean"].shape[0])
+    p["mask_threshold"] = 0.4
+    return p
+
+
+def test_mask_keeps_or_removes_whole_gaussians():
+    """M_hat = 1{sigmoid(m) > eps} in value (Sec. 4.3): the masked render
+    equals the plain render of the Gaussians with sigmoid(m) > eps, exactly."""
+    p = _mask_scene(51)
+    view = sy.tiny_view(48, 40, t=0.5)
+    st = oracle.Settings(sh_degree=1, t_order=1)
+    keep = 1.0 / (1.0 + np.exp(-p["mask_logit"])) > 0.4
+    assert 10 < keep.sum() < keep.size - 10
+    pr = oracle.preprocess(p, view, st)
+    assert np.all(pr["status"][~keep] == 7)
+    img, T, _, _ = oracle.render(pr, view, st)
+    sub = {k: v[keep] for k, v in p.items() if k not in ("mask_logit", "mask_threshold")}
+    img2, T2, _, _ = oracle.render(oracle.preprocess(sub, view, st), view, st)
+    np.testing.assert_array_equal(img, img2)
+    np.testing.assert_array_equal(T, T2)
+
+
+def test_mask_gradient_is_straight_through_scaling_derivative():
+    """dL/dm = M (1 - M) dL/dlambda at lambda = 1, where lambda scales all four
+    scales and the opacity of that Gaussian (S_hat = lambda S, alpha_hat =
+    lambda alpha): the straight-through estimator of Sec. 4.3, checked by a
+    central difference in lambda."""
+    p = _mask_scene(52)
+    view = sy.tiny_view(40, 32, t=0.5)
+    st = oracle.Settings(sh_degree=1, t_order=1)
+    pr = oracle.preprocess(p, view, st)
+    rng = np.random.default_rng(53)
+    dimg = rng.standard_normal((3, 32, 40))
+    g = oracle.render_backward(p, pr, view, st, dimg)
+    vis = np.flatnonzero(pr["status"] == 0)
+    assert vis.size >= 8
+    assert np.all(g["mask_logit"][pr["status"] != 0] == 0)
+
+    def loss_sig(q):
+        pq = oracle.preprocess(q, view, st)
+        img, T, nc, mg, sig = oracle.render(pq, view, st, signature=True)
+        return float((dimg * img).sum()), (pq["status"].tobytes(), pq["rect"].tobytes(), nc.tobytes(), sig.tobytes())
+
+    sig0 = loss_sig(p)[1]
+    checked = 0
+    for i in vis:
+        h = 1e-6
+        vals = []
+        for lam in (1 + h, 1 - h):
+            q = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+            q["log_scale"][i] += math.log(lam)
+            a = 1.0 / (1.0 + math.exp(-q["opacity_logit"][i])) * lam
+            q["opacity_logit"][i] = math.log(a / (1.0 - a))
+            vals.append(loss_sig(q))
+        if vals[0][1] != sig0 or vals[1][1] != sig0:
+            continue
+        M = 1.0 / (1.0 + math.exp(-p["mask_logit"][i]))
+        fd = (vals[0][0] - vals[1][0]) / (2 * h) * M * (1 - M)
+        assert abs(g["mask_logit"][i] - fd) <= 1e-5 * max(1.0, abs(fd)), (i, g["mask_logit"][i], fd)
+        checked += 1
+    assert checked >= 6

@@ -98,6 +98,12 @@ typedef struct fgs4d_gaussians {
   const float *opacity_logit;
   const float *sh;
   int64_t n; /* number of Gaussians, 0 <= n < 2^31 */
+  /* Optional Compact-4DGS significance mask (Sec. 4.3): mask_logit [n] or
+   * NULL.  M = sigmoid(m); a Gaussian with M <= mask_threshold is removed
+   * (M_hat = 1{M > eps} scales its four scales and its opacity to zero), any
+   * other renders unchanged (M_hat = 1).  mask_threshold in [0, 1). */
+  const float *mask_logit;
+  float mask_threshold;
 } fgs4d_gaussians;
 
 /* Gradient buffers, same shapes as the parameters (device pointers).
@@ -116,6 +122,11 @@ typedef struct fgs4d_gaussians_grad {
    * of each backward call: (|| (dL/du, dL/dv) || in pixels, |dL/dmu_t| of
    * that view, 1 (the view count), 0). */
   float *densify_stats;
+  /* dL/dm of the significance mask, [n], used when the parameters carry a
+   * mask (NULL = not wanted): the straight-through gradient
+   * M (1 - M) (sum_k dL/dlog s_k + dL/dalpha alpha) of each kept Gaussian
+   * (Sec. 4.3, M_hat = stop_gradient(1{M > eps} - M) + M). */
+  float *mask_logit;
 } fgs4d_gaussians_grad;
 
 /* Writable parameter arrays (same layouts as fgs4d_gaussians), n rows. */
@@ -268,6 +279,12 @@ int fgs4d_render_aux_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *vie
 int fgs4d_split_gaussians(const fgs4d_gaussians *src, const int32_t *idx, int64_t m, int32_t k_children,
                           const float *eps, float shrink, const fgs4d_settings *settings,
                           const fgs4d_gaussians_out *dst, void *stream);
+
+/* Mask compression loss of Compact-4DGS (Sec. 4.3): L_mask = (1/n) sum_i
+ * sigmoid(m_i) is ADDED to *loss_out (device float) and dL_mask/dm_i =
+ * sigmoid'(m_i) / n ADDED to grad_out[i] (device float [n]).  n = 0 adds
+ * nothing.  Errors: FGS4D_ERR_ARG for a negative n or NULL pointers. */
+int fgs4d_mask_loss(const float *mask_logit, int64_t n, float *loss_out, float *grad_out, void *stream);
 
 /* Photometric L1 loss (Sec. 3.3, rendering loss only): loss_out[0] +=
  * sum |img - target| / count, dL_dimg = sign(img - target) / count.

@@ -66,6 +66,8 @@ int check_gaussians(const fgs4d_gaussians *g) {
   if (!aligned16(g->mean) || !aligned16(g->log_scale) || !aligned16(g->q_l) || !aligned16(g->q_r) ||
       !aligned16(g->sh))
     return FGS4D_ERR_ARG;
+  if (g->mask_logit && !(finite_f(g->mask_threshold) && g->mask_threshold >= 0.f && g->mask_threshold < 1.f))
+    return FGS4D_ERR_ARG;
   return FGS4D_OK;
 }
 
@@ -342,6 +344,11 @@ int fgs4d_split_gaussians(const fgs4d_gaussians *src, const int32_t *idx, int64_
     return FGS4D_ERR_ARG;
   const int32_t k3 = (settings->sh_degree + 1) * (settings->sh_degree + 1) * (settings->t_order + 1) * 3;
   return cuda_status(launch_split(src, idx, m, k_children, eps, shrink, k3, dst, static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_mask_loss(const float *mask_logit, int64_t n, float *loss_out, float *grad_out, void *stream) {
+  if (n < 0 || (n > 0 && (!mask_logit || !loss_out || !grad_out))) return FGS4D_ERR_ARG;
+  return cuda_status(launch_mask_loss(mask_logit, n, loss_out, grad_out, static_cast<cudaStream_t>(stream)));
 }
 
 int fgs4d_l1_loss(const float *img, const float *target, int64_t count, float *loss_out, float *dL_dimg,

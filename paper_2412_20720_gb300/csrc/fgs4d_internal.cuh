@@ -352,6 +352,7 @@ cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nv
 cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
                               float *out_aux, cudaStream_t stream);
+cudaError_t launch_mask_loss(const float *mask_logit, int64_t n, float *loss, float *grad, cudaStream_t stream);
 cudaError_t launch_aux_records(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt);
 cudaError_t launch_split(const fgs4d_gaussians *src, const int32_t *idx, int64_t m, int32_t k_children,
                          const float *eps, float shrink, int32_t k3, const fgs4d_gaussians_out *dst,

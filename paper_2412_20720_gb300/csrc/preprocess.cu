@@ -28,6 +28,8 @@ namespace {
 struct PreArgs {
   const float4 *mean, *log_scale, *q_l, *q_r;
   const float *logit, *sh;
+  const float *mask_logit;  // optional significance mask
+  float mask_threshold;
   int32_t n, t_order, k3;
   float period_inv, near_plane, dilation, p_t_min;
   int32_t nviews, blocks_per_view;
@@ -43,6 +45,8 @@ struct PreArgs {
 struct BwdArgs {
   const float4 *mean, *log_scale, *q_l, *q_r;
   const float *logit, *sh;
+  const float *mask_logit;  // optional significance mask
+  float *g_mask;            // optional dL/dm
   int32_t n, nviews, t_order, k3;
   float period_inv, near_plane, dilation, p_t_min;
   int64_t vis_cap;
@@ -340,8 +344,15 @@ __global__ void __launch_bounds__(kPreBlock) preprocess_kernel(PreArgs A, PreVie
   const PreView &cam = views.v[view];
 
   Chain h;
-  const bool vis = (i < A.n) && forward_chain<L>(i, A.mean, A.log_scale, A.q_l, A.q_r, A.logit, A.sh, A.t_order,
-                                                  A.k3, A.period_inv, A.near_plane, A.dilation, A.p_t_min, cam, h);
+  // Compact-4DGS mask (Sec. 4.3): M_hat = 1{sigmoid(m) > eps} in value, so a
+  // Gaussian is either removed (zero scales and opacity) or unchanged.
+  bool kept = i < A.n;
+  if (kept && A.mask_logit) {
+    const float mk = A.mask_logit[i];
+    kept = isfinite(mk) && 1.0f / (1.0f + expf(-mk)) > A.mask_threshold;
+  }
+  const bool vis = kept && forward_chain<L>(i, A.mean, A.log_scale, A.q_l, A.q_r, A.logit, A.sh, A.t_order, A.k3,
+                                            A.period_inv, A.near_plane, A.dilation, A.p_t_min, cam, h);
   uint32_t total;
   const uint32_t local = block_exclusive_scan(vis ? 1u : 0u, s_scan, &total);
   if (threadIdx.x < 32) {
@@ -608,6 +619,13 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs A, PreViews
   // |dL/dmu_t| (Sec. 3.3, densification in spacetime), plus the view count.
   if (A.densify_stats) red_add4(&A.densify_stats[i], sqrtf(gu * gu + gv * gv), fabsf(g_dt), 1.0f, 0.0f);
   red_add4(&A.g_log_scale[i], gs[0] * h.s[0], gs[1] * h.s[1], gs[2] * h.s[2], gs[3] * h.s[3]);
+  // Straight-through mask gradient (Sec. 4.3): at M_hat = 1, dL/dM_hat =
+  // sum_k dL/dlog s_k + dL/dalpha alpha, and dM_hat/dm = M (1 - M).
+  if (A.mask_logit && A.g_mask) {
+    const float M = 1.0f / (1.0f + expf(-A.mask_logit[i]));
+    const float g_mhat = g_sig * h.sig + gs[0] * h.s[0] + gs[1] * h.s[1] + gs[2] * h.s[2] + gs[3] * h.s[3];
+    atomicAdd(&A.g_mask[i], g_mhat * M * (1.0f - M));
+  }
   // ---- R = Lm Rm: dL/dLm = gR Rm^T, dL/dRm = Lm^T gR; collect by entry pattern.
   const float a = h.ql[0], b = h.ql[1], c = h.ql[2], d = h.ql[3];
   const float p = h.qr[0], q = h.qr[1], r = h.qr[2], s = h.qr[3];
@@ -679,6 +697,8 @@ cudaError_t launch_pre_typed(const PreLaunch &p, const fgs4d_view *views, int32_
   A.q_l = reinterpret_cast<const float4 *>(p.g->q_l);
   A.q_r = reinterpret_cast<const float4 *>(p.g->q_r);
   A.logit = p.g->opacity_logit;
+  A.mask_logit = p.g->mask_logit;
+  A.mask_threshold = p.g->mask_threshold;
   A.sh = p.g->sh;
   A.n = (int32_t)p.g->n;
   A.t_order = p.s->t_order;
@@ -733,6 +753,8 @@ cudaError_t launch_bwd_typed(const PreLaunch &p, const fgs4d_view *views, int32_
   A.g_q_r = reinterpret_cast<float4 *>(gr->q_r);
   A.g_logit = gr->opacity_logit;
   A.g_sh = gr->sh;
+  A.mask_logit = p.g->mask_logit;
+  A.g_mask = gr->mask_logit;
   A.densify_stats = reinterpret_cast<float4 *>(gr->densify_stats);
   const int64_t blocks = (Lo.vis_cap + 127) / 128;
   if (blocks == 0) return cudaSuccess;

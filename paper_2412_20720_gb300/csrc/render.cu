@@ -415,6 +415,26 @@ __global__ void l1_loss_kernel(const float *__restrict__ img, const float *__res
   }
 }
 
+// Mask compression loss (Sec. 4.3): L = mean sigmoid(m), dL/dm = M (1 - M) / n.
+__global__ void mask_loss_kernel(const float *__restrict__ m, int64_t n, float inv_n, float *loss, float *grad) {
+  grid_dependency_sync();
+  float acc = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float M = 1.0f / (1.0f + expf(-m[i]));
+    acc += M;
+    grad[i] += M * (1.0f - M) * inv_n;
+  }
+  acc = warp_sum(acc);
+  __shared__ float s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.f;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) atomicAdd(loss, v * inv_n);
+  }
+}
+
 template <int MAXV, int PPT>
 cudaError_t launch_fwd_ppt(const RenderArgs &A, const RasterViews<MAXV> &rv, unsigned grid,
                            unsigned long long *stats, cudaStream_t st) {
@@ -508,6 +528,12 @@ cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fg
                               unsigned char *ws, const float *dL_drgb, const float *dL_daux, cudaStream_t stream) {
   if (nviews == 1) return render_bwd_typed<1>(L, s, views, nviews, ws, dL_drgb, dL_daux, stream);
   return render_bwd_typed<FGS4D_MAX_VIEWS>(L, s, views, nviews, ws, dL_drgb, dL_daux, stream);
+}
+
+cudaError_t launch_mask_loss(const float *mask_logit, int64_t n, float *loss, float *grad, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  return launch_pdl(mask_loss_kernel, (unsigned)blocks, 256u, stream, mask_logit, n, 1.0f / (float)n, loss, grad);
 }
 
 cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, float *loss, float *grad,

@@ -29,7 +29,7 @@ MAX_T_ORDER = 4
 TILE = 16
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
-            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
+            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
             "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 
@@ -49,12 +49,14 @@ class Settings(C.Structure):
 
 class Gaussians(C.Structure):
     _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("q_l", C.c_void_p), ("q_r", C.c_void_p),
-                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64)]
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64), ("mask_logit", C.c_void_p),
+                ("mask_threshold", C.c_float)]
 
 
 class GaussiansGrad(C.Structure):
     _fields_ = [("mean", C.c_void_p), ("log_scale", C.c_void_p), ("q_l", C.c_void_p), ("q_r", C.c_void_p),
-                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("densify_stats", C.c_void_p)]
+                ("opacity_logit", C.c_void_p), ("sh", C.c_void_p), ("densify_stats", C.c_void_p),
+                ("mask_logit", C.c_void_p)]
 
 
 class GaussiansOut(C.Structure):
@@ -110,6 +112,7 @@ def load():
     lib.fgs4d_render_aux_bwd.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, vp, vp,
                                          P(GaussiansGrad), vp]
     lib.fgs4d_split_gaussians.argtypes = [P(Gaussians), vp, i64, i32, vp, C.c_float, P(Settings), P(GaussiansOut), vp]
+    lib.fgs4d_mask_loss.argtypes = [vp, i64, vp, vp, vp]
     lib.fgs4d_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.fgs4d_sort_depth_static.argtypes = [vp, i64, vp, vp]
     lib.fgs4d_get_status.argtypes = [vp, C.c_size_t, vp, P(C.c_int64)]
@@ -165,14 +168,16 @@ def make_settings(sh_degree=3, t_order=2, period=1.0, near_plane=0.2, dilation=0
     return s
 
 
-def make_gaussians(ptrs: dict, n: int) -> Gaussians:
-    return Gaussians(*(ptrs[k] for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")), int(n))
+def make_gaussians(ptrs: dict, n: int, mask_logit: int = 0, mask_threshold: float = 0.0) -> Gaussians:
+    """Parameter pointers; ``mask_logit`` is the optional significance mask (0 = none)."""
+    return Gaussians(*(ptrs[k] for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")), int(n),
+                     mask_logit or None, float(mask_threshold))
 
 
 def make_grads(ptrs: dict) -> GaussiansGrad:
     """Gradient pointers; ``densify_stats`` is optional (0 = off)."""
     return GaussiansGrad(*(ptrs[k] for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")),
-                         ptrs.get("densify_stats", 0) or None)
+                         ptrs.get("densify_stats", 0) or None, ptrs.get("mask_logit", 0) or None)
 
 
 # ---------------------------------------------------------- entry points
@@ -234,6 +239,10 @@ def split_gaussians(src: Gaussians, idx: int, m: int, k_children: int, eps: int,
                     dst: GaussiansOut, stream: int):
     _check(load().fgs4d_split_gaussians(C.byref(src), idx, int(m), int(k_children), eps, float(shrink),
                                         C.byref(settings), C.byref(dst), stream), "fgs4d_split_gaussians")
+
+
+def mask_loss(mask_logit: int, n: int, loss_out: int, grad_out: int, stream: int):
+    _check(load().fgs4d_mask_loss(mask_logit, int(n), loss_out, grad_out, stream), "fgs4d_mask_loss")
 
 
 def l1_loss(img: int, target: int, count: int, loss_out: int, dL_dimg: int, stream: int):

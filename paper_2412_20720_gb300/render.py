@@ -28,6 +28,7 @@ class RenderConfig:
     vis_capacity: int = 0
     inst_capacity: int = 1 << 22
     pixels_per_thread: int = 0  # compositor block shape (0 = library default); see autotune()
+    mask_threshold: float = 0.01  # epsilon of the Compact-4DGS mask, used when params carry "mask_logit"
 
     def settings(self) -> fgs4d.Settings:
         return fgs4d.make_settings(self.sh_degree, self.t_order, self.period, self.near_plane, self.dilation,
@@ -78,7 +79,11 @@ class Renderer:
     def gaussians(self, params: dict) -> fgs4d.Gaussians:
         for k in PARAM_KEYS:
             _check_param(k, params[k], self.n, self.device)
-        return fgs4d.make_gaussians({k: _ptr(params[k]) for k in PARAM_KEYS}, self.n)
+        mask = params.get("mask_logit")
+        if mask is not None:
+            _check_param("mask_logit", mask, self.n, self.device)
+        return fgs4d.make_gaussians({k: _ptr(params[k]) for k in PARAM_KEYS}, self.n,
+                                    _ptr(mask) if mask is not None else 0, self.config.mask_threshold)
 
     def split(self, flat: torch.Tensor, channels: int = 3) -> list:
         """Flat [sum C H W] planar buffer -> list of [C, H, W] views."""
@@ -123,6 +128,9 @@ class Renderer:
         for k in PARAM_KEYS:
             _check_param("grad " + k, grads[k], self.n, self.device)
         ptrs = {k: _ptr(grads[k]) for k in PARAM_KEYS}
+        if grads.get("mask_logit") is not None:
+            _check_param("grad mask_logit", grads["mask_logit"], self.n, self.device)
+            ptrs["mask_logit"] = _ptr(grads["mask_logit"])
         if densify_stats is not None:
             if (densify_stats.dtype != torch.float32 or tuple(densify_stats.shape) != (self.n, 4)
                     or not densify_stats.is_contiguous() or densify_stats.device != self.device):
@@ -272,6 +280,20 @@ def split_gaussians(params: dict, idx: torch.Tensor, eps: torch.Tensor, shrink: 
     fgs4d.split_gaussians(src, _ptr(idx), m, K, _ptr(eps), shrink, config.settings(), dst,
                           torch.cuda.current_stream(device).cuda_stream)
     return out
+
+
+def mask_loss(mask_logit: torch.Tensor, grad: torch.Tensor | None = None):
+    """Mask compression loss of Compact-4DGS, mean sigmoid(m) (Sec. 4.3);
+    adds its gradient into ``grad`` (allocated when None).  Returns (loss, grad)."""
+    device = mask_logit.device
+    n = mask_logit.shape[0]
+    _check_param("mask_logit", mask_logit, n, device)
+    if grad is None:
+        grad = torch.zeros_like(mask_logit)
+    _check_param("mask grad", grad, n, device)
+    loss = torch.zeros(1, dtype=torch.float32, device=device)
+    fgs4d.mask_loss(_ptr(mask_logit), n, _ptr(loss), _ptr(grad), torch.cuda.current_stream(device).cuda_stream)
+    return loss, grad
 
 
 def l1_loss(img: torch.Tensor, target: torch.Tensor):

@@ -94,6 +94,12 @@ def _declare(lib):
     lib.orc_split_sample.argtypes = [P(_Params), C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_double, C.c_int64,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_split_sample.restype = C.c_int
+    lib.orc_render_features.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), C.c_void_p, C.c_int, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]
+    lib.orc_render_features.restype = C.c_int
+    lib.orc_render_features_backward.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), C.c_void_p, C.c_int,
+                                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.orc_render_features_backward.restype = C.c_int
     lib.orc_rotation.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_rotation.restype = None
     lib.orc_real_sh.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
@@ -252,6 +258,44 @@ def render_aux(proj, aux: np.ndarray, view, settings: Settings):
     if rc != 0:
         raise MemoryError("oracle render_aux failed")
     return img, T, out, mg
+
+
+def render_features(proj, view, settings: Settings, features: np.ndarray, gate=None):
+    """Feature map (FP64) [D, H, W] of the normalised scale-gated features,
+    composited with the colour weights; also the pixel margin [H, W]."""
+    lib = _load()
+    W, H = int(view["width"]), int(view["height"])
+    n = proj["status"].shape[0]
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    D = f.shape[1]
+    g = None if gate is None else np.ascontiguousarray(gate, dtype=np.float64)
+    out = np.zeros((D, H, W))
+    mg = np.zeros((H, W))
+    pc, keep = _proj_c(proj)
+    rc = lib.orc_render_features(C.byref(_view_c(view)), C.byref(settings._c()), n, C.byref(pc), _ptr(f), D,
+                                 _ptr(g) if g is not None else None, _ptr(out), _ptr(mg))
+    if rc != 0:
+        raise MemoryError("oracle render_features failed")
+    return out, mg
+
+
+def render_features_backward(proj, view, settings: Settings, features: np.ndarray, gate, dF: np.ndarray):
+    """dL/dfeatures [n, D] and dL/dgate [D] (FP64) for a loss with feature-map
+    gradient dF [D, H, W], geometry held fixed."""
+    lib = _load()
+    n = proj["status"].shape[0]
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    D = f.shape[1]
+    g = None if gate is None else np.ascontiguousarray(gate, dtype=np.float64)
+    dF = np.ascontiguousarray(dF, dtype=np.float64)
+    gf = np.zeros((n, D))
+    gg = np.zeros(D)
+    pc, keep = _proj_c(proj)
+    rc = lib.orc_render_features_backward(C.byref(_view_c(view)), C.byref(settings._c()), n, C.byref(pc), _ptr(f),
+                                          D, _ptr(g) if g is not None else None, _ptr(dF), _ptr(gf), _ptr(gg))
+    if rc != 0:
+        raise MemoryError("oracle render_features_backward failed")
+    return gf, gg
 
 
 def _alloc_grads(n, K):

@@ -699,6 +699,112 @@ int orc_render_aux(const orc_view *V, const orc_settings *S, int64_t n, const or
   return 0;
 }
 
+/* ------------------------------------------------ feature rendering */
+
+/* Scale-gated feature of Gaussian i (Sec. 7, "Scale-gated features"):
+ * f^s = S(s) (.) f with the gate vector S(s) given, normalised; the map is
+ * rendered like colour in Eq. 6 with a zero background.  Returns |g|. */
+static double gated_unit_feature(const double *f, const double *gate, int D, double *fhat) {
+  double nn = 0.0;
+  for (int c = 0; c < D; ++c) {
+    fhat[c] = (gate ? gate[c] : 1.0) * f[c];
+    nn += fhat[c] * fhat[c];
+  }
+  const double norm = sqrt(nn);
+  for (int c = 0; c < D; ++c) fhat[c] = norm > 0.0 ? fhat[c] / norm : 0.0;
+  return norm;
+}
+
+/* out[D][H][W] = sum_i w_i fhat_i per pixel, w_i = alpha_i T_i of the colour
+ * compositing (same skip and stop decisions). */
+int orc_render_features(const orc_view *V, const orc_settings *S, int64_t n, const orc_proj *P, const double *feat,
+                        int D, const double *gate, double *out, double *margin) {
+  orc_tiles tl;
+  if (build_tiles(V, S, n, P, &tl)) return -1;
+  const int W = V->width, H = V->height, gw = (W + S->tile - 1) / S->tile;
+  const int64_t HW = (int64_t)W * H;
+  int64_t maxlen = 1;
+  for (int64_t t = 0; t < (int64_t)gw * ((H + S->tile - 1) / S->tile); ++t)
+    if (tl.off[t + 1] - tl.off[t] > maxlen) maxlen = tl.off[t + 1] - tl.off[t];
+  int err = 0;
+#pragma omp parallel
+  {
+    orc_contrib *rec = malloc(sizeof(orc_contrib) * (size_t)maxlen);
+    double *fhat = malloc(sizeof(double) * (size_t)D);
+    if (!rec || !fhat) err = 1;
+#pragma omp for schedule(dynamic, 1)
+    for (int py = 0; py < H; ++py) {
+      if (!rec || !fhat) continue;
+      for (int px = 0; px < W; ++px) {
+        const int64_t t = (int64_t)(py / S->tile) * gw + px / S->tile;
+        const int64_t p = (int64_t)py * W + px;
+        double rgb[3], T;
+        int64_t nr = 0;
+        composite_pixel(P, S, tl.ent + tl.off[t], tl.off[t + 1] - tl.off[t], px, py, rgb, &T, NULL,
+                        margin ? &margin[p] : NULL, NULL, rec, &nr, NULL, NULL);
+        for (int c = 0; c < D; ++c) out[c * HW + p] = 0.0;
+        for (int64_t k = 0; k < nr; ++k) {
+          gated_unit_feature(feat + (size_t)rec[k].idx * D, gate, D, fhat);
+          for (int c = 0; c < D; ++c) out[c * HW + p] += rec[k].alpha * rec[k].T * fhat[c];
+        }
+      }
+    }
+    free(rec);
+    free(fhat);
+  }
+  free_tiles(&tl);
+  return err ? -1 : 0;
+}
+
+/* Reverse mode of orc_render_features with the geometry held fixed (the
+ * features are trained on a pre-trained 4DGS): dL/dfhat_i = sum_p w_i dF(p);
+ * with g = gate (.) f and fhat = g / |g|, dL/dg = (dL/dfhat - fhat (fhat .
+ * dL/dfhat)) / |g|; dL/df = gate (.) dL/dg and dL/dgate = sum_i f_i (.) dL/dg_i
+ * (both ADDED). */
+int orc_render_features_backward(const orc_view *V, const orc_settings *S, int64_t n, const orc_proj *P,
+                                 const double *feat, int D, const double *gate, const double *dF,
+                                 double *g_feat, double *g_gate) {
+  orc_tiles tl;
+  if (build_tiles(V, S, n, P, &tl)) return -1;
+  const int W = V->width, H = V->height, gw = (W + S->tile - 1) / S->tile;
+  const int64_t HW = (int64_t)W * H;
+  int64_t maxlen = 1;
+  for (int64_t t = 0; t < (int64_t)gw * ((H + S->tile - 1) / S->tile); ++t)
+    if (tl.off[t + 1] - tl.off[t] > maxlen) maxlen = tl.off[t + 1] - tl.off[t];
+  double *gfhat = calloc((size_t)n * D + 1, sizeof(double));
+  orc_contrib *rec = malloc(sizeof(orc_contrib) * (size_t)maxlen);
+  double *fhat = malloc(sizeof(double) * (size_t)D + 1);
+  if (!gfhat || !rec || !fhat) return -1;
+  for (int py = 0; py < H; ++py)
+    for (int px = 0; px < W; ++px) {
+      const int64_t t = (int64_t)(py / S->tile) * gw + px / S->tile;
+      const int64_t p = (int64_t)py * W + px;
+      double rgb[3], T;
+      int64_t nr = 0;
+      composite_pixel(P, S, tl.ent + tl.off[t], tl.off[t + 1] - tl.off[t], px, py, rgb, &T, NULL, NULL, NULL,
+                      rec, &nr, NULL, NULL);
+      for (int64_t k = 0; k < nr; ++k)
+        for (int c = 0; c < D; ++c) gfhat[(size_t)rec[k].idx * D + c] += rec[k].alpha * rec[k].T * dF[c * HW + p];
+    }
+  for (int64_t i = 0; i < n; ++i) {
+    if (P->status[i] != 0) continue;
+    const double norm = gated_unit_feature(feat + (size_t)i * D, gate, D, fhat);
+    if (!(norm > 0.0)) continue;
+    double dot = 0.0;
+    for (int c = 0; c < D; ++c) dot += fhat[c] * gfhat[(size_t)i * D + c];
+    for (int c = 0; c < D; ++c) {
+      const double dg = (gfhat[(size_t)i * D + c] - fhat[c] * dot) / norm;
+      g_feat[(size_t)i * D + c] += (gate ? gate[c] : 1.0) * dg;
+      if (g_gate) g_gate[c] += feat[(size_t)i * D + c] * dg;
+    }
+  }
+  free(gfhat);
+  free(rec);
+  free(fhat);
+  free_tiles(&tl);
+  return 0;
+}
+
 /* ------------------------------------------------------------ adjoint */
 
 /* Reverse-mode derivative of one pixel's colour C (RGB) with respect to the

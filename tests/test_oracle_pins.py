@@ -745,3 +745,73 @@ def test_mask_gradient_is_straight_through_scaling_derivative():
         assert abs(g["mask_logit"][i] - fd) <= 1e-5 * max(1.0, abs(fd)), (i, g["mask_logit"][i], fd)
         checked += 1
     assert checked >= 6
+
+
+# ------------------------------------------------- feature rendering pins
+
+def _unit_colour_scene(rng, n=60):
+    """DC-only colours that are unit vectors with positive entries."""
+    gs, cols = [], []
+    for _ in range(n):
+        c = np.abs(rng.standard_normal(3)) + 0.05
+        c /= np.linalg.norm(c)
+        cols.append(c)
+        q = rng.standard_normal(4)
+        gs.append(one_gaussian(list(rng.uniform(-0.5, 0.5, 3)) + [0.5], list(np.log(rng.uniform(0.03, 0.08, 3))) +
+                               [math.log(0.3)], q, rng.standard_normal(4), rng.normal(0, 1),
+                               ((c - 0.5) / Y00)[None, :]))
+    return stack(gs), np.array(cols)
+
+
+def test_feature_render_equals_colour_render_for_unit_colours():
+    """With f_i = c_i of unit norm (so f_hat = c) and a black background the
+    feature map is the image: the feature path uses the colour weights of
+    Eq. 6 (Sec. 7: colour replaced by the normalised feature)."""
+    rng = np.random.default_rng(61)
+    g, cols = _unit_colour_scene(rng)
+    view = sy.tiny_view(48, 40, t=0.5)
+    st = oracle.Settings(sh_degree=0, t_order=0, bg=(0.0, 0.0, 0.0))
+    pr = oracle.preprocess(g, view, st)
+    assert (pr["status"] == 0).sum() > 20
+    np.testing.assert_allclose(pr["rgb"][pr["status"] == 0], cols[pr["status"] == 0], atol=1e-12)
+    img, T, _, _ = oracle.render(pr, view, st)
+    F, mg = oracle.render_features(pr, view, st, cols * 7.0)  # scale is normalised away
+    np.testing.assert_allclose(F, img, atol=1e-12)
+    F2, _ = oracle.render_features(pr, view, st, cols, gate=[0.5, 0.5, 0.0])  # gate zeroes channel 2
+    assert np.all(F2[2] == 0.0) and F2[:2].max() > 0.3
+
+
+def test_feature_backward_matches_fd():
+    rng = np.random.default_rng(62)
+    sc = sy.make_scene(50, 62, (-0.6, -0.6, -0.6), (0.6, 0.6, 0.6), sh_degree=1, t_order=1)
+    params = {k: v.astype(np.float64) for k, v in sc.as_dict().items()}
+    view = sy.tiny_view(32, 32, t=0.5)
+    st = oracle.Settings(sh_degree=1, t_order=1)
+    pr = oracle.preprocess(params, view, st)
+    D = 5
+    f = rng.standard_normal((50, D))
+    gate = rng.uniform(0.2, 1.0, D)
+    dF = rng.standard_normal((D, 32, 32))
+    gf, gg = oracle.render_features_backward(pr, view, st, f, gate, dF)
+
+    def loss(ff, gt):
+        F, _ = oracle.render_features(pr, view, st, ff, gt)
+        return float((dF * F).sum())
+
+    h = 1e-6
+    vis = np.flatnonzero(pr["status"] == 0)
+    assert vis.size > 10
+    for i in vis[:6]:
+        for c in range(D):
+            fp, fm = f.copy(), f.copy()
+            fp[i, c] += h
+            fm[i, c] -= h
+            fd = (loss(fp, gate) - loss(fm, gate)) / (2 * h)
+            assert abs(fd - gf[i, c]) <= 1e-6 * max(1.0, abs(fd)), (i, c, fd, gf[i, c])
+    for c in range(D):
+        gp, gm = gate.copy(), gate.copy()
+        gp[c] += h
+        gm[c] -= h
+        fd = (loss(f, gp) - loss(f, gm)) / (2 * h)
+        assert abs(fd - gg[c]) <= 1e-6 * max(1.0, abs(fd)), (c, fd, gg[c])
+    assert np.all(gf[pr["status"] != 0] == 0)

@@ -286,6 +286,32 @@ int fgs4d_split_gaussians(const fgs4d_gaussians *src, const int32_t *idx, int64_
  * nothing.  Errors: FGS4D_ERR_ARG for a negative n or NULL pointers. */
 int fgs4d_mask_loss(const float *mask_logit, int64_t n, float *loss_out, float *grad_out, void *stream);
 
+/* Scale-gated feature rendering for 4D segmentation (Sec. 7, "Scale-gated
+ * features"): Gaussian i carries features[i][0..D); at a scale s the caller
+ * passes the gate vector S(s) (device float [D], values in [0, 1]; NULL =
+ * all ones).  f^s = S(s) (.) f is normalised (a zero vector stays zero) and
+ * composited with the colour weights of Eq. 6 and a zero background:
+ * out_features[c] = sum_i alpha_i T_i fhat_i[c], float [sum_v D H W], view v
+ * at D * (pixels before v), planar [D][H][W].  D in {8, 16, 32} (32 is the
+ * paper's; others give FGS4D_ERR_UNSUPPORTED); features 16-byte aligned
+ * rows.  Call after fgs4d_preprocess and fgs4d_bin_sort on the same
+ * workspace, views and settings; the weights equal fgs4d_render_fwd's. */
+int fgs4d_render_features(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                          void *workspace, size_t workspace_bytes, const float *features, int32_t D,
+                          const float *gate, float *out_features, void *stream);
+
+/* Reverse mode of fgs4d_render_features with the geometry held fixed (the
+ * features are trained on a pre-trained 4DGS, Sec. 7 "Training"):
+ * dL_dfeatures has out_features' layout; ADDS dL/df into grad_features
+ * (device float [n][D]) and, when grad_gate is not NULL, dL/dS(s) into
+ * grad_gate (device float [D]).  With g = S (.) f and fhat = g / |g|:
+ * dL/dg = (dL/dfhat - fhat (fhat . dL/dfhat)) / |g|, dL/df = S (.) dL/dg,
+ * dL/dS = sum_i f_i (.) dL/dg_i. */
+int fgs4d_render_features_bwd(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                              void *workspace, size_t workspace_bytes, const float *features, int32_t D,
+                              const float *gate, const float *dL_dfeatures, float *grad_features,
+                              float *grad_gate, void *stream);
+
 /* Photometric L1 loss (Sec. 3.3, rendering loss only): loss_out[0] +=
  * sum |img - target| / count, dL_dimg = sign(img - target) / count.
  * All device pointers; loss_out must be zeroed by the caller. */

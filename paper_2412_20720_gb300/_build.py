@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libfgs4d.so")
-SOURCES = ("abi.cu", "preprocess.cu", "sort.cu", "render.cu")
+SOURCES = ("abi.cu", "preprocess.cu", "sort.cu", "render.cu", "features.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

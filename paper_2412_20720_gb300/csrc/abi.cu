@@ -346,6 +346,50 @@ int fgs4d_split_gaussians(const fgs4d_gaussians *src, const int32_t *idx, int64_
   return cuda_status(launch_split(src, idx, m, k_children, eps, shrink, k3, dst, static_cast<cudaStream_t>(stream)));
 }
 
+namespace {
+
+int check_features(int64_t n, const float *features, int32_t D, const float *gate) {
+  if (!feature_dim_supported(D)) return FGS4D_ERR_UNSUPPORTED;
+  if (n > 0 && (!features || !aligned16(features))) return FGS4D_ERR_ARG;
+  (void)gate;
+  return FGS4D_OK;
+}
+
+}  // namespace
+
+int fgs4d_render_features(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                          void *workspace, size_t workspace_bytes, const float *features, int32_t D,
+                          const float *gate, float *out_features, void *stream) {
+  Layout L;
+  int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  rc = check_features(n, features, D, gate);
+  if (rc) return rc;
+  if (!out_features) return FGS4D_ERR_ARG;
+  return cuda_status(launch_render_features(L, views, nviews, static_cast<unsigned char *>(workspace), n, features,
+                                            D, gate, out_features, nullptr, nullptr, nullptr,
+                                            static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_render_features_bwd(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                              void *workspace, size_t workspace_bytes, const float *features, int32_t D,
+                              const float *gate, const float *dL_dfeatures, float *grad_features,
+                              float *grad_gate, void *stream) {
+  Layout L;
+  int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  rc = check_features(n, features, D, gate);
+  if (rc) return rc;
+  if (!dL_dfeatures || (n > 0 && !grad_features)) return FGS4D_ERR_ARG;
+  return cuda_status(launch_render_features(L, views, nviews, static_cast<unsigned char *>(workspace), n, features,
+                                            D, gate, nullptr, dL_dfeatures, grad_features, grad_gate,
+                                            static_cast<cudaStream_t>(stream)));
+}
+
 int fgs4d_mask_loss(const float *mask_logit, int64_t n, float *loss_out, float *grad_out, void *stream) {
   if (n < 0 || (n > 0 && (!mask_logit || !loss_out || !grad_out))) return FGS4D_ERR_ARG;
   return cuda_status(launch_mask_loss(mask_logit, n, loss_out, grad_out, static_cast<cudaStream_t>(stream)));

@@ -334,6 +334,26 @@ constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
+// Sum over the 32 lanes of a warp (every lane gets the total).
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Global tile -> its view (binary search over the views' first tiles).
+template <int MAXV>
+__device__ __forceinline__ int find_view(const RasterViews<MAXV> &rv, int32_t gt) {
+  if (MAXV == 1) return 0;
+  int lo = 0, hi = rv.nviews - 1;
+  while (lo < hi) {  // last view with tile_base <= gt
+    const int mid = (lo + hi + 1) >> 1;
+    if (rv.v[mid].tile_base <= gt) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // ------------------------------------------------------ host-side launchers
 
 struct PreLaunch {
@@ -352,6 +372,10 @@ cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nv
 cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
                               float *out_aux, cudaStream_t stream);
+bool feature_dim_supported(int32_t D);
+cudaError_t launch_render_features(const Layout &L, const fgs4d_view *views, int32_t nviews, unsigned char *ws,
+                                   int64_t n, const float *feat, int32_t D, const float *gate, float *out,
+                                   const float *dL_dF, float *g_feat, float *g_gate, cudaStream_t st);
 cudaError_t launch_mask_loss(const float *mask_logit, int64_t n, float *loss, float *grad, cudaStream_t stream);
 cudaError_t launch_aux_records(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt);
 cudaError_t launch_split(const fgs4d_gaussians *src, const int32_t *idx, int64_t m, int32_t k_children,

@@ -62,17 +62,6 @@ inline int render_ppt(const fgs4d_settings *s) {
   return (s->pixels_per_thread == 2 || s->pixels_per_thread == 8) ? s->pixels_per_thread : 4;
 }
 
-template <int MAXV>
-__device__ __forceinline__ int find_view(const RasterViews<MAXV> &rv, int32_t gt) {
-  if (MAXV == 1) return 0;
-  int lo = 0, hi = rv.nviews - 1;
-  while (lo < hi) {  // last view with tile_base <= gt
-    const int mid = (lo + hi + 1) >> 1;
-    if (rv.v[mid].tile_base <= gt) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
 
 // Stages records [base, min(base + kBatch, end)) of the tile list into shared
 // memory; slots out of range (only possible after a recorded timeout) stage a
@@ -221,12 +210,6 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
       aux[3 * HW + p] = X2[k];
     }
   }
-}
-
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
 }
 
 // Sums eight per-lane values over the warp with 9 shuffles instead of 40: at

@@ -29,7 +29,7 @@ MAX_T_ORDER = 4
 TILE = 16
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
-            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
+            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
             "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 
@@ -113,6 +113,9 @@ def load():
                                          P(GaussiansGrad), vp]
     lib.fgs4d_split_gaussians.argtypes = [P(Gaussians), vp, i64, i32, vp, C.c_float, P(Settings), P(GaussiansOut), vp]
     lib.fgs4d_mask_loss.argtypes = [vp, i64, vp, vp, vp]
+    lib.fgs4d_render_features.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, i32, vp, vp, vp]
+    lib.fgs4d_render_features_bwd.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, i32, vp, vp, vp, vp,
+                                              vp]
     lib.fgs4d_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.fgs4d_sort_depth_static.argtypes = [vp, i64, vp, vp]
     lib.fgs4d_get_status.argtypes = [vp, C.c_size_t, vp, P(C.c_int64)]
@@ -243,6 +246,18 @@ def split_gaussians(src: Gaussians, idx: int, m: int, k_children: int, eps: int,
 
 def mask_loss(mask_logit: int, n: int, loss_out: int, grad_out: int, stream: int):
     _check(load().fgs4d_mask_loss(mask_logit, int(n), loss_out, grad_out, stream), "fgs4d_mask_loss")
+
+
+def render_features(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, feat: int, D: int,
+                    gate, out: int, stream):
+    _check(load().fgs4d_render_features(int(n), views, int(nviews), C.byref(settings), ws, ws_bytes, feat, int(D),
+                                        gate, out, stream), "fgs4d_render_features")
+
+
+def render_features_bwd(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, feat: int, D: int,
+                        gate, dL_dF: int, g_feat: int, g_gate, stream):
+    _check(load().fgs4d_render_features_bwd(int(n), views, int(nviews), C.byref(settings), ws, ws_bytes, feat,
+                                            int(D), gate, dL_dF, g_feat, g_gate, stream), "fgs4d_render_features_bwd")
 
 
 def l1_loss(img: int, target: int, count: int, loss_out: int, dL_dimg: int, stream: int):

@@ -138,6 +138,43 @@ class Renderer:
             ptrs["densify_stats"] = _ptr(densify_stats)
         return fgs4d.make_grads(ptrs)
 
+    def _check_features(self, features: torch.Tensor, gate):
+        if (features.dim() != 2 or features.shape[0] != self.n or features.dtype != torch.float32
+                or not features.is_contiguous() or features.device != self.device):
+            raise ValueError("features must be a contiguous float32 [n, D] tensor on the render device")
+        D = int(features.shape[1])
+        if gate is not None and (tuple(gate.shape) != (D,) or gate.dtype != torch.float32 or gate.device != self.device):
+            raise ValueError("gate must be a float32 [D] tensor on the render device")
+        return D
+
+    def forward_features(self, params: dict, features: torch.Tensor, gate: torch.Tensor | None = None):
+        """Feature map of the normalised scale-gated features (Sec. 7):
+        preprocess, bin_sort, then the feature compositor; returns the flat
+        buffer [sum_v D H W] (per view planar [D, H, W])."""
+        g = self.gaussians(params)
+        D = self._check_features(features, gate)
+        out = torch.empty(D * self.total_pixels, dtype=torch.float32, device=self.device)
+        st = self.stream()
+        ws = _ptr(self.ws)
+        fgs4d.preprocess(g, self.views, self.nviews, self.settings, ws, self.ws_bytes, st)
+        fgs4d.bin_sort(self.n, self.views, self.nviews, self.settings, ws, self.ws_bytes, st)
+        fgs4d.render_features(self.n, self.views, self.nviews, self.settings, ws, self.ws_bytes, _ptr(features), D,
+                              _ptr(gate) if gate is not None else None, _ptr(out), st)
+        return out
+
+    def backward_features(self, features: torch.Tensor, gate, dL_dF: torch.Tensor, grad_features: torch.Tensor,
+                          grad_gate: torch.Tensor | None = None):
+        """Adds dL/dfeatures (and dL/dgate) for the last forward_features;
+        the geometry is held fixed."""
+        D = self._check_features(features, gate)
+        if grad_features.shape != features.shape or not grad_features.is_contiguous():
+            raise ValueError("grad_features must match features")
+        dL = dL_dF.contiguous()
+        fgs4d.render_features_bwd(self.n, self.views, self.nviews, self.settings, _ptr(self.ws), self.ws_bytes,
+                                  _ptr(features), D, _ptr(gate) if gate is not None else None, _ptr(dL),
+                                  _ptr(grad_features), _ptr(grad_gate) if grad_gate is not None else None,
+                                  self.stream())
+
     def backward(self, params: dict, dL_drgb: torch.Tensor, grads: dict, densify_stats: torch.Tensor | None = None):
         """Adds dL/dparams into ``grads`` for the last forward of this renderer;
         with ``densify_stats`` ([n, 4]) also accumulates, per visible (view,

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
   float X0[kAux ? PPT : 1], X1[kAux ? PPT : 1], X2[kAux ? PPT : 1];  // depth, flow_u, flow_v sums
   uint32_t last[PPT];
-  bool live = false;
+  int nlive = 0;  // pixels of this thread still compositing
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     const bool in = px < V.width && py0 + k < V.height;
@@ -132,17 +132,17 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
     if (kAux) X0[k] = X1[k] = X2[k] = 0.f;
     last[k] = 0u;
     pyc[k] = (float)(py0 + k) + 0.5f;
-    live = live || in;
+    nlive += in;
   }
   uint32_t n_eval = 0u, n_comp = 0u;
   for (uint32_t base = range.x; base < range.y; base += kBatch) {
-    if (__syncthreads_count(live) == 0) break;
+    if (__syncthreads_count(nlive > 0) == 0) break;
     stage_batch<NT>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, range.y, s_geom, s_col,
                     s_blue, nullptr, kAux ? A.rec_aux : nullptr, kAux ? s_aux : nullptr);
     __syncthreads();
     const int nb = (int)min(range.y - base, (uint32_t)kBatch);
     const uint32_t pos0 = base - range.x + 1u;
-    for (int j = 0; j < nb && live; ++j) {
+    for (int j = 0; j < nb && nlive > 0; ++j) {
       const float4 geom = s_geom[j];
       const float4 col = s_col[j];
       const float blue = s_blue[j];
@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
           const float Tn = __fsub_rn(T[k], w);
           if (Tn < kTMin) {
             T[k] = -T[k];
+            --nlive;
           } else {
             C0[k] = __fmaf_rn(col.z, w, C0[k]);
             C1[k] = __fmaf_rn(col.w, w, C1[k]);
@@ -172,9 +173,6 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
           }
         }
       }
-      live = false;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) live = live || T[k] > 0.0f;
     }
   }
   if (kStats) {

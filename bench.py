@@ -44,10 +44,10 @@ W_IMG, H_IMG = 1352, 1014
 # alpha*T (1), three colour multiply-adds (6) = 9.  The ex2 goes to the SFU.
 FLOPS_PER_EVAL = 11
 FLOPS_PER_COMP = 9
-# DRAM bytes (read + write) of one compositor launch (2 pixels per thread) on
-# this workload, from the ncu capture summarised in
-# profiles/kernels_orbit_300k_1352x1014.md; None once the kernel changes.
-RENDER_FWD_TRAFFIC = {}
+# DRAM bytes (read + write) of one compositor launch on this workload, per
+# block shape, from the ncu launch list summarised in
+# profiles/launches_orbit_300k_1352x1014.md; emptied whenever the kernel changes.
+RENDER_FWD_TRAFFIC = {2: 7.655e6, 4: 7.648e6, 8: 7.382e6}
 
 
 def parse():

@@ -267,8 +267,11 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
   const uint2 range = A.ranges[gt];
   const float pxc = (float)px + 0.5f;
   const int64_t HW = (int64_t)V.width * V.height;
-  float T[kPPT], dC0[kPPT], dC1[kPPT], dC2[kPPT], r0[kPPT], r1[kPPT], r2[kPPT], pyc[kPPT];
-  float dD[kAux ? kPPT : 1], dO[kAux ? kPPT : 1], rD[kAux ? kPPT : 1], rO[kAux ? kPPT : 1];
+  // Dr[k] = sum over channels of dL/dX * (X composited behind the current
+  // entry), X = R, G, B (and depth, opacity): the "behind" terms of
+  // dL/dalpha enter only through this sum, which grows by w * (dL/dX . x_i).
+  float T[kPPT], dC0[kPPT], dC1[kPPT], dC2[kPPT], Dr[kPPT], pyc[kPPT];
+  float dD[kAux ? kPPT : 1], dO[kAux ? kPPT : 1];
   uint32_t last[kPPT];
   uint32_t my_max = 0u;
   const float *g = A.dL_drgb + V.pix_base * 3;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
       dC2[k] = g[2 * HW + p];
     }
     if (kAux) {
-      dD[k] = dO[k] = rD[k] = rO[k] = 0.f;
+      dD[k] = dO[k] = 0.f;
       if (px < V.width && py0 + k < V.height) {
         const int64_t p = (int64_t)(py0 + k) * V.width + px;
         const float *ga = A.dL_daux + V.pix_base * 4;
@@ -295,9 +298,7 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
         dO[k] = ga[HW + p];
       }
     }
-    r0[k] = T[k] * A.bg0;  // colour composited behind the current entry
-    r1[k] = T[k] * A.bg1;
-    r2[k] = T[k] * A.bg2;
+    Dr[k] = T[k] * (dC0[k] * A.bg0 + dC1[k] * A.bg1 + dC2[k] * A.bg2);  // the background behind all
     my_max = max(my_max, last[k]);
   }
   if (threadIdx.x == 0) s_maxlast = 0u;
@@ -322,9 +323,10 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
       const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc);
       const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
-      // g = (du, dv, dA', dB', dC', da, dr, dg), plus db.
-      float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      float gb = 0.f, gz = 0.f;
+      // The conic and centre gradients of the strip share dx: accumulate the
+      // moments S0 = sum gp, S1 = sum gp dy, S2 = sum gp dy^2 of
+      // gp = dL/d(natural-log power) and form the five sums once per entry.
+      float S0 = 0.f, S1 = 0.f, S2 = 0.f, ga = 0.f, gr = 0.f, gg = 0.f, gb = 0.f, gz = 0.f;
       const float zj = kAux ? s_aux[j].x : 0.f;
       bool contrib = false;
 #pragma unroll
@@ -336,31 +338,29 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
         const float io = rcp_approx(__fsub_rn(1.0f, e.alpha));
         T[k] = T[k] * io;  // transmittance in front of this entry
         const float w = e.alpha * T[k];
-        g[6] += dC0[k] * w;
-        g[7] += dC1[k] * w;
+        gr += dC0[k] * w;
+        gg += dC1[k] * w;
         gb += dC2[k] * w;
-        float g_alpha = dC0[k] * (col.z * T[k] - r0[k] * io) + dC1[k] * (col.w * T[k] - r1[k] * io) +
-                        dC2[k] * (blue * T[k] - r2[k] * io);
+        float Dc = dC0[k] * col.z + dC1[k] * col.w + dC2[k] * blue;  // dL/dX . x_i
         if (kAux) {
-          g_alpha += dD[k] * (zj * T[k] - rD[k] * io) + dO[k] * (T[k] - rO[k] * io);
-          rD[k] += zj * w;
-          rO[k] += w;
+          Dc += dD[k] * zj + dO[k];
           gz += dD[k] * w;
         }
-        r0[k] += col.z * w;
-        r1[k] += col.w * w;
-        r2[k] += blue * w;
+        const float g_alpha = T[k] * Dc - io * Dr[k];
+        Dr[k] += w * Dc;
         if (!(e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
-          g[5] += g_alpha * e.G;
+          ga += g_alpha * e.G;
           const float gp = g_alpha * e.alpha;  // d alpha / d (natural-log power)
-          const float dx = ct.dx, dy = e.dy;
-          g[2] += -0.5f * dx * dx * gp;
-          g[3] += -dx * dy * gp;
-          g[4] += -0.5f * dy * dy * gp;
-          g[0] += -(An * dx + Bn * dy) * gp;
-          g[1] += -(Cn * dy + Bn * dx) * gp;
+          const float gpy = gp * e.dy;
+          S0 += gp;
+          S1 += gpy;
+          S2 += gpy * e.dy;
         }
       }
+      const float dx = ct.dx;
+      // g = (du, dv, dA', dB', dC', da, dr, dg), plus db.
+      float g[8] = {-(An * dx * S0 + Bn * S1), -(Cn * S1 + Bn * dx * S0), -0.5f * dx * dx * S0, -dx * S1,
+                    -0.5f * S2, ga, gr, gg};
       if (__any_sync(0xffffffffu, contrib)) {
         warp_sum8_transposed(g, lane);
         gb = warp_sum(gb);

@@ -286,6 +286,21 @@ int fgs4d_split_gaussians(const fgs4d_gaussians *src, const int32_t *idx, int64_
  * nothing.  Errors: FGS4D_ERR_ARG for a negative n or NULL pointers. */
 int fgs4d_mask_loss(const float *mask_logit, int64_t n, float *loss_out, float *grad_out, void *stream);
 
+/* Adam step of the training loop (the optimiser the adapted 3DGS training
+ * uses; Sec. 3.3 trains end to end with the rendering loss).  Not part of
+ * the paper's method; a streaming kernel so that the optimiser does not
+ * dominate the step.  `step` is a device int32 step count t, so a training
+ * step can be replayed as a CUDA graph: fgs4d_adam_tick adds 1 to it (call
+ * once per step, before the updates), fgs4d_adam_update applies, element by
+ * element, m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr / (1 - b1^t) * m / (sqrt(v) / sqrt(1 - b2^t) + eps).
+ * param, grad, exp_avg, exp_avg_sq: device float [count], 16-byte aligned.
+ * Errors: FGS4D_ERR_ARG for NULL or misaligned pointers, count < 0,
+ * non-finite lr, betas outside [0, 1) or eps <= 0. */
+int fgs4d_adam_tick(int32_t *step, void *stream);
+int fgs4d_adam_update(float *param, const float *grad, float *exp_avg, float *exp_avg_sq, int64_t count, float lr,
+                      float beta1, float beta2, float eps, const int32_t *step, void *stream);
+
 /* Scale-gated feature rendering for 4D segmentation (Sec. 7, "Scale-gated
  * features"): Gaussian i carries features[i][0..D); at a scale s the caller
  * passes the gate vector S(s) (device float [D], values in [0, 1]; NULL =

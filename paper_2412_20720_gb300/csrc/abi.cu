@@ -390,6 +390,23 @@ int fgs4d_render_features_bwd(int64_t n, const fgs4d_view *views, int32_t nviews
                                             static_cast<cudaStream_t>(stream)));
 }
 
+int fgs4d_adam_tick(int32_t *step, void *stream) {
+  if (!step) return FGS4D_ERR_ARG;
+  return cuda_status(launch_adam_tick(step, static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_adam_update(float *param, const float *grad, float *exp_avg, float *exp_avg_sq, int64_t count, float lr,
+                      float beta1, float beta2, float eps, const int32_t *step, void *stream) {
+  if (count < 0 || !step) return FGS4D_ERR_ARG;
+  if (count == 0) return FGS4D_OK;
+  if (!param || !grad || !exp_avg || !exp_avg_sq) return FGS4D_ERR_ARG;
+  if (!aligned16(param) || !aligned16(grad) || !aligned16(exp_avg) || !aligned16(exp_avg_sq)) return FGS4D_ERR_ARG;
+  if (!finite_f(lr) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return FGS4D_ERR_ARG;
+  return cuda_status(launch_adam(param, grad, exp_avg, exp_avg_sq, count, lr, beta1, beta2, eps, step,
+                                 static_cast<cudaStream_t>(stream)));
+}
+
 int fgs4d_mask_loss(const float *mask_logit, int64_t n, float *loss_out, float *grad_out, void *stream) {
   if (n < 0 || (n > 0 && (!mask_logit || !loss_out || !grad_out))) return FGS4D_ERR_ARG;
   return cuda_status(launch_mask_loss(mask_logit, n, loss_out, grad_out, static_cast<cudaStream_t>(stream)));

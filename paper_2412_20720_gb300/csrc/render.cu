@@ -396,6 +396,57 @@ __global__ void l1_loss_kernel(const float *__restrict__ img, const float *__res
   }
 }
 
+// Adam (the optimiser of the training step): with t the device step count,
+// m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+// p -= lr / (1 - b1^t) * m / (sqrt(v) / sqrt(1 - b2^t) + eps).
+struct AdamArgs {
+  float *p;
+  const float *g;
+  float *m, *v;
+  int64_t count;
+  float lr, b1, b2, eps;
+  const int32_t *step;
+};
+
+__device__ __forceinline__ float adam_one(float &p, float g, float &m, float &v, float b1, float b2, float eps,
+                                          float step_size, float inv_sqrt_bc2) {
+  m = b1 * m + (1.0f - b1) * g;
+  v = b2 * v + (1.0f - b2) * g * g;
+  p -= step_size * m / (sqrtf(v) * inv_sqrt_bc2 + eps);
+  return p;
+}
+
+__global__ void adam_kernel(AdamArgs A) {
+  grid_dependency_sync();
+  const float t = (float)*A.step;
+  const float bc1 = 1.0f - powf(A.b1, t), bc2 = 1.0f - powf(A.b2, t);
+  const float step_size = A.lr / bc1, inv_sqrt_bc2 = rsqrtf(bc2);
+  const int64_t n4 = A.count / 4;
+  float4 *p4 = reinterpret_cast<float4 *>(A.p);
+  const float4 *g4 = reinterpret_cast<const float4 *>(A.g);
+  float4 *m4 = reinterpret_cast<float4 *>(A.m);
+  float4 *v4 = reinterpret_cast<float4 *>(A.v);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    float4 p = p4[i], m = m4[i], v = v4[i];
+    const float4 g = g4[i];
+    adam_one(p.x, g.x, m.x, v.x, A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+    adam_one(p.y, g.y, m.y, v.y, A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+    adam_one(p.z, g.z, m.z, v.z, A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+    adam_one(p.w, g.w, m.w, v.w, A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+    p4[i] = p;
+    m4[i] = m;
+    v4[i] = v;
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.count; i += stride)
+    adam_one(A.p[i], A.g[i], A.m[i], A.v[i], A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+}
+
+__global__ void adam_tick_kernel(int32_t *step) {
+  grid_dependency_sync();
+  if (threadIdx.x == 0) *step += 1;
+}
+
 // Mask compression loss (Sec. 4.3): L = mean sigmoid(m), dL/dm = M (1 - M) / n.
 __global__ void mask_loss_kernel(const float *__restrict__ m, int64_t n, float inv_n, float *loss, float *grad) {
   grid_dependency_sync();
@@ -509,6 +560,18 @@ cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fg
                               unsigned char *ws, const float *dL_drgb, const float *dL_daux, cudaStream_t stream) {
   if (nviews == 1) return render_bwd_typed<1>(L, s, views, nviews, ws, dL_drgb, dL_daux, stream);
   return render_bwd_typed<FGS4D_MAX_VIEWS>(L, s, views, nviews, ws, dL_drgb, dL_daux, stream);
+}
+
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t count, float lr, float b1, float b2,
+                        float eps, const int32_t *step, cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  AdamArgs A{p, g, m, v, count, lr, b1, b2, eps, step};
+  const int blocks = (int)std::min<int64_t>((count / 4 + 255) / 256 + 1, 152 * 8);
+  return launch_pdl(adam_kernel, (unsigned)blocks, 256u, stream, A);
+}
+
+cudaError_t launch_adam_tick(int32_t *step, cudaStream_t stream) {
+  return launch_pdl(adam_tick_kernel, 1u, 32u, stream, step);
 }
 
 cudaError_t launch_mask_loss(const float *mask_logit, int64_t n, float *loss, float *grad, cudaStream_t stream) {

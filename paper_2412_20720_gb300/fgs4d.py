@@ -29,7 +29,7 @@ MAX_T_ORDER = 4
 TILE = 16
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
-            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
+            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
             "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 
@@ -116,6 +116,8 @@ def load():
     lib.fgs4d_render_features.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, i32, vp, vp, vp]
     lib.fgs4d_render_features_bwd.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, i32, vp, vp, vp, vp,
                                               vp]
+    lib.fgs4d_adam_tick.argtypes = [vp, vp]
+    lib.fgs4d_adam_update.argtypes = [vp, vp, vp, vp, i64, C.c_float, C.c_float, C.c_float, C.c_float, vp, vp]
     lib.fgs4d_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.fgs4d_sort_depth_static.argtypes = [vp, i64, vp, vp]
     lib.fgs4d_get_status.argtypes = [vp, C.c_size_t, vp, P(C.c_int64)]
@@ -258,6 +260,16 @@ def render_features_bwd(n: int, views, nviews: int, settings: Settings, ws: int,
                         gate, dL_dF: int, g_feat: int, g_gate, stream):
     _check(load().fgs4d_render_features_bwd(int(n), views, int(nviews), C.byref(settings), ws, ws_bytes, feat,
                                             int(D), gate, dL_dF, g_feat, g_gate, stream), "fgs4d_render_features_bwd")
+
+
+def adam_tick(step: int, stream: int):
+    _check(load().fgs4d_adam_tick(step, stream), "fgs4d_adam_tick")
+
+
+def adam_update(param: int, grad: int, exp_avg: int, exp_avg_sq: int, count: int, lr: float, beta1: float,
+                beta2: float, eps: float, step: int, stream: int):
+    _check(load().fgs4d_adam_update(param, grad, exp_avg, exp_avg_sq, int(count), float(lr), float(beta1),
+                                    float(beta2), float(eps), step, stream), "fgs4d_adam_update")
 
 
 def l1_loss(img: int, target: int, count: int, loss_out: int, dL_dimg: int, stream: int):

@@ -333,6 +333,28 @@ def mask_loss(mask_logit: torch.Tensor, grad: torch.Tensor | None = None):
     return loss, grad
 
 
+class Adam:
+    """Adam over the parameter tensors with the fgs4d kernel (one streaming
+    pass per tensor); the step count lives on the device, so ``step`` can be
+    captured in a CUDA graph.  ``lr`` may be one float or a dict per key."""
+
+    def __init__(self, params: dict, lr=1e-4, betas=(0.9, 0.999), eps=1e-8):
+        self.params = params
+        device = next(iter(params.values())).device
+        self.m = {k: torch.zeros_like(v) for k, v in params.items()}
+        self.v = {k: torch.zeros_like(v) for k, v in params.items()}
+        self.t = torch.zeros(1, dtype=torch.int32, device=device)
+        self.lr = lr if isinstance(lr, dict) else {k: float(lr) for k in params}
+        self.betas, self.eps = betas, eps
+
+    def step(self, grads: dict):
+        st = torch.cuda.current_stream(self.t.device).cuda_stream
+        fgs4d.adam_tick(_ptr(self.t), st)
+        for k, p in self.params.items():
+            fgs4d.adam_update(_ptr(p), _ptr(grads[k]), _ptr(self.m[k]), _ptr(self.v[k]), p.numel(), self.lr[k],
+                              self.betas[0], self.betas[1], self.eps, _ptr(self.t), st)
+
+
 def l1_loss(img: torch.Tensor, target: torch.Tensor):
     """L1 loss and its gradient with the fgs4d kernel: returns (loss[1], dL/dimg)."""
     img = img.contiguous()

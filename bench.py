@@ -72,6 +72,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value over the ranks (a job's time is its slowest rank's);
+    one all-reduce of a float64 on `device` when world > 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank processes units_per_rank)."""
+    return units_per_rank * world / (ms_max / 1000.0)
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -275,12 +293,8 @@ def run_ours(args, rank, world, local):
     for e4 in evs:
         stage_ms += [e4[0].elapsed_time(e4[1]), e4[1].elapsed_time(e4[2]), e4[2].elapsed_time(e4[3])]
     stage_ms /= len(evs)
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
-    frames = K * nviews * world
-    value = frames / (ms_max / 1000.0)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = job_rate(K * nviews, world, ms_max)
 
     # Roofline of the dominant kernel (the compositor): FP32-ALU bound.
     props = torch.cuda.get_device_properties(dev)
@@ -330,10 +344,8 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         barrier()
         e_ms = (time.perf_counter() - t0) * 1000.0
-        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": frames / (float(te.item()) / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_rate(K * nviews, world, max_over_ranks(e_ms, world, dev)), "unit": UNIT,
+               "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "path": "C-ABI calls on device copies of pinned host parameters; each image copied to pinned "
                        "host memory on a second stream"}
@@ -456,10 +468,12 @@ def run_train(args, dev, scene, params, world, barrier):
     plain_ms, _ = timed(it)
     del graph
     code, counts = r.status()
-    return {"metric": "fwd+bwd iters/s", "value": 1000.0 / ms * world, "unit": "iters/s", "ms_per_iter": ms,
+    ms = max_over_ranks(ms, world, dev)
+    plain_ms = max_over_ranks(plain_ms, world, dev)
+    return {"metric": "fwd+bwd iters/s", "value": job_rate(1, world, ms), "unit": "iters/s", "ms_per_iter": ms,
             "workload": "4 timestamps x 1 camera at 1352x1014 in one call, %d Gaussians, L1 loss, backward to all "
                         "parameters, Adam step (fgs4d kernel); the step replayed as one CUDA graph" % scene.n,
-            "plain_launches": {"value": 1000.0 / plain_ms * world, "ms_per_iter": plain_ms},
+            "plain_launches": {"value": job_rate(1, world, plain_ms), "ms_per_iter": plain_ms},
             "status": fgs4d.status_string(code), "loss": float(loss.item()), "autotune": tuned,
             "targets": "rendered by the CUDA path from a second seeded scene"}
 

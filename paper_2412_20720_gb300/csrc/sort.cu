@@ -298,8 +298,30 @@ __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, Raste
       g = A.geom[s];
       cc = A.color[s].x;
       tau = A.tau[s];
-      const int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff, y1 = (uint32_t)mm.w >> 16;
+      int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff, y1 = (uint32_t)mm.w >> 16;
+      // Only tiles whose pixel-centre box meets the 1/255 ellipse are kept,
+      // so the pairs are enumerated over the rect cut to the ellipse's
+      // bounding box: half-extents sqrt(tau C'/det), sqrt(tau A'/det) with
+      // det = A'C' - B'^2/4, widened by 0.1% + 0.05 px against rounding (a
+      // box outside them is far outside the ellipse, which the exact test
+      // below rejects as well).  Tile tx's centre box [16 tx + 0.5,
+      // 16 tx + 15.5] can meet [u - rx, u + rx] only for
+      // ceil((u - rx - 15.5) / 16) <= tx <= floor((u + rx - 0.5) / 16).
+      const float det = g.z * cc - 0.25f * g.w * g.w;
+      if (tau < 0.0f) {
+        x1 = x0;
+      } else if (det > 0.0f) {
+        const float rx = sqrtf(tau * cc / det) * 1.001f + 0.05f, ry = sqrtf(tau * g.z / det) * 1.001f + 0.05f;
+        const float lx = ceilf((g.x - rx - 15.5f) * (1.0f / kTile)), hx = floorf((g.x + rx - 0.5f) * (1.0f / kTile));
+        const float ly = ceilf((g.y - ry - 15.5f) * (1.0f / kTile)), hy = floorf((g.y + ry - 0.5f) * (1.0f / kTile));
+        if (lx > (float)x0) x0 = (int)fminf(lx, (float)x1);
+        if (hx + 1.0f < (float)x1) x1 = (int)fmaxf(hx + 1.0f, (float)x0);
+        if (ly > (float)y0) y0 = (int)fminf(ly, (float)y1);
+        if (hy + 1.0f < (float)y1) y1 = (int)fmaxf(hy + 1.0f, (float)y0);
+      }
       area = (uint32_t)(max(x1 - x0, 0) * max(y1 - y0, 0));
+      mm.z = x0 | (y0 << 16);
+      mm.w = x1 | (y1 << 16);
     } else {
       atomicOr(&A.counters[kCtrStatus], kStatusInternal);
     }

@@ -1,0 +1,99 @@
+"""Parity at the sizes of the training, batched and large-scene workloads
+(1352x1014 training step with 300k Gaussians; 1M Gaussians over views of
+mixed resolution in one batched call; 3M large-scale Gaussians at 1920x1080),
+on outputs the FP64 oracle can afford: sampled pixels, and gradients of a
+loss whose image gradient is non-zero on sampled pixels only."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_20720_gb300 import synthetic as sy
+from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer
+
+from helpers import PIXEL_MARGIN, compare_group, keep_clear_of_boundaries, oracle_settings, subset, to_device
+
+pytestmark = pytest.mark.gpu
+
+IMAGE_ATOL = 2e-4
+
+
+def _sampled_parity(params, views, cfg, npix, seed):
+    import torch
+    n = params["mean"].shape[0]
+    r = Renderer(n, views, cfg)
+    flat = r.forward(to_device(params))
+    r.check()
+    imgs = [x.cpu().numpy() for x in r.split(flat)]
+    torch.cuda.synchronize()
+    st = oracle_settings(cfg)
+    rng = np.random.default_rng(seed)
+    for k, v in enumerate(views):
+        W, H = int(v["width"]), int(v["height"])
+        pix = rng.choice(W * H, npix, replace=False)
+        pr = oracle.preprocess(params, v, st)
+        rgb, T, nc, mg = oracle.render_pixels(pr, v, st, pix)
+        ok = mg >= PIXEL_MARGIN
+        assert ok.mean() >= 0.75, ok.mean()
+        got = imgs[k].reshape(3, -1)[:, pix].T
+        assert np.abs(got - rgb)[ok].max() <= IMAGE_ATOL
+
+
+def test_batched_mixed_resolutions_1m_sampled():
+    """1M Gaussians in [-5,5]^3 x [0,1], three views of different resolution
+    (512^2, 800^2, 1014x1352 portrait) rendered in one call."""
+    sc = sy.sphere_scene()
+    allv = sy.sphere_views()
+    want, views = [(512, 512), (800, 800), (1014, 1352)], []
+    for w, h in want:
+        views.append(next(v for v in allv if (int(v["width"]), int(v["height"])) == (w, h)))
+    cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 25)
+    params = sc.as_dict()
+    params = subset(params, keep_clear_of_boundaries(params, views, cfg))
+    _sampled_parity(params, views, cfg, 800, 31)
+
+
+def test_urban_3m_view_sampled():
+    """3M Gaussians with spatial scales up to 1 over a 60 x 60 x 6 block, one
+    camera of the moving rig at 1920x1080 (the large multi-camera workload)."""
+    sc = sy.urban_scene()
+    views = sy.urban_views()[:1]
+    cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=(1 << 28) - 1)
+    params = sc.as_dict()
+    params = subset(params, keep_clear_of_boundaries(params, views, cfg))
+    _sampled_parity(params, views, cfg, 300, 32)
+
+
+def test_training_step_gradients_300k_sampled():
+    """The training workload (300k Gaussians, degree 3 x order 2, 4 timestamps
+    x 1 camera at 1352x1014 in one call): every parameter gradient of a loss
+    whose image gradient is non-zero on 3000 sampled clear pixels per view,
+    against the oracle's adjoint summed over the views."""
+    import torch
+    sc = sy.orbit_scene()
+    views = sy.train_views(4)
+    cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 25)
+    params = sc.as_dict()
+    params = subset(params, keep_clear_of_boundaries(params, views, cfg))
+    st = oracle_settings(cfg)
+    rng = np.random.default_rng(33)
+    n = params["mean"].shape[0]
+    dimgs, g_orc = [], None
+    for v in views:
+        W, H = int(v["width"]), int(v["height"])
+        pr = oracle.preprocess(params, v, st)
+        pix = rng.choice(W * H, 3000, replace=False)
+        rgb, T, nc, mg = oracle.render_pixels(pr, v, st, pix)
+        d = np.zeros((3, H * W))
+        d[:, pix[mg >= PIXEL_MARGIN]] = rng.standard_normal((3, int((mg >= PIXEL_MARGIN).sum())))
+        d = d.reshape(3, H, W)
+        dimgs.append(d)
+        g = oracle.render_backward(params, pr, v, st, d)
+        g_orc = g if g_orc is None else {k: g_orc[k] + g[k] for k in PARAM_KEYS}
+    r = Renderer(n, views, cfg)
+    p = to_device(params)
+    r.forward(p)
+    grads = {k: torch.zeros_like(x) for k, x in p.items()}
+    r.backward(p, torch.from_numpy(np.concatenate([d.reshape(-1) for d in dimgs]).astype(np.float32)).cuda(), grads)
+    r.check()
+    for k in PARAM_KEYS:
+        compare_group(k, grads[k].cpu().numpy().astype(np.float64), g_orc[k], 1e-3, 1e-4)

@@ -47,7 +47,7 @@ FLOPS_PER_COMP = 9
 # DRAM bytes (read + write) of one compositor launch on this workload, per
 # block shape, from the ncu launch list summarised in
 # profiles/launches_orbit_300k_1352x1014.md; emptied whenever the kernel changes.
-RENDER_FWD_TRAFFIC = {2: 7.655e6, 4: 7.648e6, 8: 7.382e6}
+RENDER_FWD_TRAFFIC = {(16, 2): 7.655e6, (16, 4): 7.648e6, (16, 8): 7.382e6}  # (tile, pixels per thread)
 
 
 def parse():
@@ -219,7 +219,8 @@ def run_ours(args, rank, world, local):
     cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24)
     r = Renderer(scene.n, views[:1], cfg, device=dev)
     vv = [fgs4d.make_views([v]) for v in views]
-    tuned = autotune(r, params, view_sets=[vv[k] for k in sorted({0, nviews // 3, 2 * nviews // 3})])
+    tuned = autotune(r, params, view_sets=[vv[k] for k in sorted({0, nviews // 3, 2 * nviews // 3})],
+                     tiles=(16, 8))
     g = r.gaussians(params)
     ws, wsb, s = r.ws.data_ptr(), r.ws_bytes, r.settings
     stream = torch.cuda.current_stream(dev)
@@ -356,7 +357,8 @@ def run_ours(args, rank, world, local):
     # ---------------------------------------------------------- batched views
     batched = None
     if not args.no_batched:
-        batched = [run_batched(dev, sy.sphere_scene(), sy.sphere_views(64), "sphere-1M-64views-mixed-res", 2, 8),
+        batched = [run_batched(dev, sy.sphere_scene(), sy.sphere_views(64), "sphere-1M-64views-mixed-res", 2, 8,
+                               tiles=(16, 8)),
                    run_batched(dev, sy.urban_scene(), sy.urban_views(), "urban-3M-6cams-x-2t-1920x1080", 2, 6,
                                plain=False)]
 
@@ -384,7 +386,7 @@ def run_ours(args, rank, world, local):
                                "alpha_evals": float(np.mean(evals)), "composited": float(np.mean(comps))},
             "roofline": {"kernel": "render_fwd", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                         "traffic": RENDER_FWD_TRAFFIC.get(tuned["pixels_per_thread"]),
+                         "traffic": RENDER_FWD_TRAFFIC.get((tuned["tile"], tuned["pixels_per_thread"])),
                          "peak_basis": "SMs x 128 FP32 lanes x 2 (FMA) x max SM clock %.0f MHz (derived)" % sm_max,
                          "flops_per_launch": mean_flops},
             "preprocess_roofline": {"bound": "hbm", "achieved": pre_gbs, "peak": hbm, "unit": "GB/s",
@@ -419,7 +421,7 @@ def run_train(args, dev, scene, params, world, barrier):
     del rt, tparams
     leaf = {k: params[k].clone().requires_grad_(True) for k in PARAM_KEYS}
     r = Renderer(scene.n, views, cfg, device=dev)
-    tuned = autotune(r, {k: leaf[k].detach() for k in PARAM_KEYS}, backward=True)
+    tuned = autotune(r, {k: leaf[k].detach() for k in PARAM_KEYS}, backward=True, tiles=(16, 8))
     grads = {k: torch.zeros_like(leaf[k]) for k in PARAM_KEYS}
     # Adam with the library's kernel; its step count lives on the device, so
     # the whole step can be replayed as one CUDA graph.
@@ -478,7 +480,7 @@ def run_train(args, dev, scene, params, world, barrier):
             "targets": "rendered by the CUDA path from a second seeded scene"}
 
 
-def run_batched(dev, scene, views, label, steps, group, plain=True):
+def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,)):
     """Forward + backward of many (camera, t) views of mixed resolution: one
     multi-view call per group of ``group`` views, all groups of a step
     captured in one CUDA graph, against one plain single-view call per view.
@@ -494,19 +496,24 @@ def run_batched(dev, scene, views, label, steps, group, plain=True):
     groups = [views[i:i + group] for i in range(0, len(views), group)]
     rs, tuned, vis_tot, inst_tot, max_inst = [], None, 0, 0, 0
     for gv in groups:
-        # Size each group's capacities on one forward with generous ones.
+        # Size each group's capacities on one forward per tile edge with
+        # generous ones.
         probe = Renderer(n, gv, RenderConfig(sh_degree=3, t_order=2, vis_capacity=min(n * len(gv), 1 << 29),
                                              inst_capacity=(1 << 30) - 1), device=dev)
-        probe.forward(params)
-        counts = probe.check()
+        counts = None
+        for t in tiles:
+            probe.set_tile(t)
+            probe.forward(params)
+            c = probe.check()
+            counts = c if counts is None else [max(a, b) for a, b in zip(counts, c)]
         del probe
         torch.cuda.empty_cache()
         cfg = RenderConfig(sh_degree=3, t_order=2, vis_capacity=int(counts[0] * 1.1) + 1024,
                            inst_capacity=min(int(counts[1] * 1.1) + 1024, (1 << 30) - 1))
         r = Renderer(n, gv, cfg, device=dev)
         if tuned is None:
-            tuned = autotune(r, params, backward=True, reps=2)
-        r.settings.pixels_per_thread = tuned["pixels_per_thread"]
+            tuned = autotune(r, params, backward=True, reps=2, tiles=tiles)
+        r.set_tile(tuned["tile"], tuned["pixels_per_thread"])
         rs.append(r)
         vis_tot += counts[0]
         inst_tot += counts[1]
@@ -558,7 +565,7 @@ def run_batched(dev, scene, views, label, steps, group, plain=True):
             key = (v["width"], v["height"])
             if key not in per_res:
                 c1 = RenderConfig(sh_degree=3, t_order=2, vis_capacity=n, inst_capacity=max_inst + 1024,
-                                  pixels_per_thread=tuned["pixels_per_thread"])
+                                  pixels_per_thread=tuned["pixels_per_thread"], tile=tuned["tile"])
                 per_res[key] = Renderer(n, [v], c1, device=dev)
             rr = per_res[key]
             singles.append((rr, fgs4d.make_views([v]), torch.randn(3 * v["width"] * v["height"], device=dev,

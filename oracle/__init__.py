@@ -105,7 +105,7 @@ def _declare(lib):
     lib.orc_real_sh.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
     lib.orc_real_sh.restype = None
     lib.orc_sort_instances.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                       C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
+                                       C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_ellipse_meets_box.argtypes = [C.c_float] * 10
     lib.orc_ellipse_meets_box.restype = C.c_int
@@ -407,11 +407,11 @@ def real_sh(L: int, direction) -> np.ndarray:
 
 
 def sort_instances(rect, depth_f32, grid_w: int, grid_h: int, cap: int | None = None, uv=None, conic2=None,
-                   tau=None, width: int = 0, height: int = 0):
+                   tau=None, width: int = 0, height: int = 0, tile: int = 16):
     """Tile-binned instance list sorted by (tile, FP32 depth, index).
     With uv, conic2 (A', B', C': q = A' dx^2 + B' dx dy + C' dy^2) and tau
-    (FP32 arrays) a rect tile is kept only if the ellipse q <= tau meets its
-    pixel centres (image width x height).
+    (FP32 arrays) a rect tile (edge ``tile`` pixels) is kept only if the
+    ellipse q <= tau meets its pixel centres (image width x height).
     Returns (keys u64 [M], vals i64 [M], ranges i64 [tiles, 2])."""
     lib = _load()
     rect = np.ascontiguousarray(rect, dtype=np.int32)
@@ -428,7 +428,8 @@ def sort_instances(rect, depth_f32, grid_w: int, grid_h: int, cap: int | None = 
     vals = np.zeros(max(m, 1), dtype=np.int64)
     ranges = np.zeros((grid_w * grid_h, 2), dtype=np.int64)
     got = lib.orc_sort_instances(n, _ptr(rect), _ptr(depth_f32), *(None if x is None else _ptr(x) for x in ex),
-                                 int(width), int(height), grid_w, grid_h, cap, _ptr(keys), _ptr(vals), _ptr(ranges))
+                                 int(width), int(height), int(tile), grid_w, grid_h, cap, _ptr(keys), _ptr(vals),
+                                 _ptr(ranges))
     if got < 0:
         raise ValueError("instance count exceeds capacity")
     return keys[:got], vals[:got], ranges

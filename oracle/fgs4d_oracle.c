@@ -1245,32 +1245,32 @@ int orc_ellipse_meets_box(float u, float v, float A, float B, float C, float tau
 }
 
 /* Pixel-centre box of tile (tx, ty), clipped to the image. */
-static void tile_box(int tx, int ty, int W, int H, float *x0, float *x1, float *y0, float *y1) {
-  const int px1 = tx * 16 + 15 < W - 1 ? tx * 16 + 15 : W - 1;
-  const int py1 = ty * 16 + 15 < H - 1 ? ty * 16 + 15 : H - 1;
-  *x0 = (float)(tx * 16) + 0.5f;
+static void tile_box(int tx, int ty, int W, int H, int B, float *x0, float *x1, float *y0, float *y1) {
+  const int px1 = tx * B + B - 1 < W - 1 ? tx * B + B - 1 : W - 1;
+  const int py1 = ty * B + B - 1 < H - 1 ? ty * B + B - 1 : H - 1;
+  *x0 = (float)(tx * B) + 0.5f;
   *x1 = (float)px1 + 0.5f;
-  *y0 = (float)(ty * 16) + 0.5f;
+  *y0 = (float)(ty * B) + 0.5f;
   *y1 = (float)py1 + 0.5f;
 }
 
 static int keep_tile(const float *uv, const float *conic2, const float *tau, int64_t i, int tx, int ty, int W,
-                     int H) {
+                     int H, int B) {
   if (!uv) return 1;
   float x0, x1, y0, y1;
-  tile_box(tx, ty, W, H, &x0, &x1, &y0, &y1);
+  tile_box(tx, ty, W, H, B, &x0, &x1, &y0, &y1);
   return orc_ellipse_meets_box(uv[2 * i], uv[2 * i + 1], conic2[3 * i], conic2[3 * i + 1], conic2[3 * i + 2],
                                tau[i], x0, x1, y0, y1);
 }
 
 int64_t orc_sort_instances(int64_t n, const int32_t *rect, const float *depth, const float *uv, const float *conic2,
-                           const float *tau, int32_t W, int32_t H, int32_t gw, int32_t gh, int64_t cap,
+                           const float *tau, int32_t W, int32_t H, int32_t tile, int32_t gw, int32_t gh, int64_t cap,
                            uint64_t *keys, int64_t *vals, int64_t *ranges) {
   int64_t m = 0;
   for (int64_t i = 0; i < n; ++i) {
     const int32_t *r = rect + 4 * i;
     for (int ty = r[1]; ty < r[3]; ++ty)
-      for (int tx = r[0]; tx < r[2]; ++tx) m += keep_tile(uv, conic2, tau, i, tx, ty, W, H);
+      for (int tx = r[0]; tx < r[2]; ++tx) m += keep_tile(uv, conic2, tau, i, tx, ty, W, H, tile);
   }
   if (m > cap) return -1;
   orc_inst *a = malloc(sizeof(orc_inst) * (size_t)(m > 0 ? m : 1));
@@ -1280,7 +1280,7 @@ int64_t orc_sort_instances(int64_t n, const int32_t *rect, const float *depth, c
     const int32_t *r = rect + 4 * i;
     for (int ty = r[1]; ty < r[3]; ++ty)
       for (int tx = r[0]; tx < r[2]; ++tx) {
-        if (!keep_tile(uv, conic2, tau, i, tx, ty, W, H)) continue;
+        if (!keep_tile(uv, conic2, tau, i, tx, ty, W, H, tile)) continue;
         a[k].tile = (int64_t)ty * gw + tx;
         a[k].depth = depth[i];
         a[k].idx = i;

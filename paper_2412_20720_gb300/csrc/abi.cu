@@ -24,7 +24,7 @@ int check_settings(const fgs4d_settings *s) {
   if (!s) return FGS4D_ERR_ARG;
   if (s->sh_degree < 0 || s->sh_degree > FGS4D_MAX_SH_DEGREE) return FGS4D_ERR_UNSUPPORTED;
   if (s->t_order < 0 || s->t_order > FGS4D_MAX_T_ORDER) return FGS4D_ERR_UNSUPPORTED;
-  if (s->tile != kTile) return FGS4D_ERR_UNSUPPORTED;
+  if (s->tile != 16 && s->tile != 8) return FGS4D_ERR_UNSUPPORTED;
   if (!finite_f(s->period) || !(s->period > 0.f)) return FGS4D_ERR_ARG;
   if (!finite_f(s->near_plane) || !(s->near_plane > 0.f)) return FGS4D_ERR_ARG;
   if (!finite_f(s->dilation) || s->dilation < 0.f) return FGS4D_ERR_ARG;
@@ -33,8 +33,9 @@ int check_settings(const fgs4d_settings *s) {
     if (!finite_f(s->bg[k])) return FGS4D_ERR_ARG;
   if (s->inst_capacity <= 0 || s->inst_capacity > kMaxCap) return FGS4D_ERR_ARG;
   if (s->vis_capacity < 0 || s->vis_capacity > kMaxCap) return FGS4D_ERR_ARG;
-  if (s->pixels_per_thread != 0 && s->pixels_per_thread != 2 && s->pixels_per_thread != 4 &&
-      s->pixels_per_thread != 8)
+  // Compositor strip heights per tile edge: 16 -> 2, 4, 8; 8 -> 1, 2 (0 = default).
+  const int ppt = s->pixels_per_thread;
+  if (ppt != 0 && !(s->tile == 16 ? (ppt == 2 || ppt == 4 || ppt == 8) : (ppt == 1 || ppt == 2)))
     return FGS4D_ERR_UNSUPPORTED;
   if (s->reserved != 0) return FGS4D_ERR_ARG;
   return FGS4D_OK;
@@ -91,11 +92,12 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   memset(&L, 0, sizeof L);
   L.n = n;
   L.nviews = nviews;
+  L.tile = s->tile;
   L.vis_cap = s->vis_capacity ? s->vis_capacity : n * (int64_t)nviews;
   if (L.vis_cap > kMaxCap) return FGS4D_ERR_ARG;  // set vis_capacity explicitly
   L.inst_cap = s->inst_capacity;
   for (int v = 0; v < nviews; ++v) {
-    const int64_t gw = (views[v].width + kTile - 1) / kTile, gh = (views[v].height + kTile - 1) / kTile;
+    const int64_t gw = (views[v].width + s->tile - 1) / s->tile, gh = (views[v].height + s->tile - 1) / s->tile;
     L.total_tiles += gw * gh;
     L.total_pixels += (int64_t)views[v].width * views[v].height;
   }

@@ -26,8 +26,12 @@ namespace fgs4d {
 namespace {
 
 constexpr int kFeatPPT = 2;
-constexpr int kFeatThreads = kTilePixels / kFeatPPT;  // 128
-constexpr int kFeatBatch = kFeatThreads;               // one staged entry per thread
+// Threads per block and records per staged batch (one per thread) for a
+// TILE x TILE tile: 128 at 16x16, 32 at 8x8.
+template <int TILE>
+__host__ __device__ constexpr int feat_threads() {
+  return TILE * TILE / kFeatPPT;
+}
 
 struct FeatArgs {
   const uint2 *ranges;
@@ -96,9 +100,10 @@ __device__ __forceinline__ void stage_feature(const FeatArgs &A, const float *s_
   if (s_norm) s_norm[k] = norm;
 }
 
-template <int MAXV, int D>
-__global__ void __launch_bounds__(kFeatThreads) render_features_kernel(FeatArgs A, RasterViews<MAXV> rv) {
+template <int MAXV, int TILE, int D>
+__global__ void __launch_bounds__(feat_threads<TILE>()) render_features_kernel(FeatArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
+  constexpr int kFeatBatch = feat_threads<TILE>();
   __shared__ float4 s_geom[kFeatBatch];
   __shared__ float2 s_ca[kFeatBatch];
   __shared__ int32_t s_gi[kFeatBatch];
@@ -108,8 +113,8 @@ __global__ void __launch_bounds__(kFeatThreads) render_features_kernel(FeatArgs 
   const RasterView &V = rv.v[find_view<MAXV>(rv, gt)];
   const int32_t lt = gt - V.tile_base;
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
-  const int32_t px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int32_t py0 = ty * kTile + (threadIdx.x / kTile) * kFeatPPT;
+  const int32_t px = tx * TILE + (threadIdx.x & (TILE - 1));
+  const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * kFeatPPT;
   const uint2 range = A.ranges[gt];
   const float pxc = (float)px + 0.5f;
   if (threadIdx.x < D) s_gate[threadIdx.x] = A.gate ? A.gate[threadIdx.x] : 1.0f;
@@ -182,9 +187,10 @@ __device__ __forceinline__ float warp_transpose_sum(float (&a)[32], int lane) {
   return a[0];
 }
 
-template <int MAXV, int D>
-__global__ void __launch_bounds__(kFeatThreads) render_features_bwd_kernel(FeatArgs A, RasterViews<MAXV> rv) {
+template <int MAXV, int TILE, int D>
+__global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kernel(FeatArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
+  constexpr int kFeatBatch = feat_threads<TILE>();
   __shared__ float4 s_geom[kFeatBatch];
   __shared__ float2 s_ca[kFeatBatch];
   __shared__ int32_t s_gi[kFeatBatch];
@@ -197,8 +203,8 @@ __global__ void __launch_bounds__(kFeatThreads) render_features_bwd_kernel(FeatA
   const RasterView &V = rv.v[find_view<MAXV>(rv, gt)];
   const int32_t lt = gt - V.tile_base;
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
-  const int32_t px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int32_t py0 = ty * kTile + (threadIdx.x / kTile) * kFeatPPT;
+  const int32_t px = tx * TILE + (threadIdx.x & (TILE - 1));
+  const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * kFeatPPT;
   const uint2 range = A.ranges[gt];
   const float pxc = (float)px + 0.5f;
   const int lane = threadIdx.x & 31;
@@ -271,6 +277,14 @@ __global__ void __launch_bounds__(kFeatThreads) render_features_bwd_kernel(FeatA
   if (A.g_gate && threadIdx.x < D && s_ggate[threadIdx.x] != 0.f) atomicAdd(&A.g_gate[threadIdx.x], s_ggate[threadIdx.x]);
 }
 
+template <int MAXV, int TILE, int D>
+cudaError_t launch_feat_tile(const FeatArgs &A, const RasterViews<MAXV> &rv, unsigned grid, bool backward,
+                             cudaStream_t st) {
+  constexpr unsigned NT = feat_threads<TILE>();
+  if (backward) return launch_pdl(render_features_bwd_kernel<MAXV, TILE, D>, grid, NT, st, A, rv);
+  return launch_pdl(render_features_kernel<MAXV, TILE, D>, grid, NT, st, A, rv);
+}
+
 template <int MAXV, int D>
 cudaError_t launch_feat_typed(const Layout &L, const FeatArgs &A, const fgs4d_view *views, int32_t nviews,
                               bool backward, cudaStream_t st) {
@@ -278,8 +292,8 @@ cudaError_t launch_feat_typed(const Layout &L, const FeatArgs &A, const fgs4d_vi
   if (!make_raster_views<MAXV>(L, views, nviews, &rv)) return cudaErrorInvalidValue;
   if (L.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)L.total_tiles;
-  if (backward) return launch_pdl(render_features_bwd_kernel<MAXV, D>, grid, (unsigned)kFeatThreads, st, A, rv);
-  return launch_pdl(render_features_kernel<MAXV, D>, grid, (unsigned)kFeatThreads, st, A, rv);
+  if (L.tile == 8) return launch_feat_tile<MAXV, 8, D>(A, rv, grid, backward, st);
+  return launch_feat_tile<MAXV, 16, D>(A, rv, grid, backward, st);
 }
 
 template <int D>

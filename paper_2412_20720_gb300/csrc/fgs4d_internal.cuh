@@ -9,7 +9,7 @@
 
 namespace fgs4d {
 
-constexpr int kTile = 16;           // tile edge in pixels
+constexpr int kTile = 16;           // default tile edge in pixels (8 is the other supported size)
 constexpr int kTilePixels = kTile * kTile;
 constexpr int kPreBlock = 256;      // threads per preprocess block
 constexpr int kEmitBlock = 256;     // threads per pair-scan / emission block
@@ -58,6 +58,8 @@ struct PreView {
   float campos[3];
   float t;
   int32_t width, height, gw, gh;
+  int32_t tile;     // tile edge in pixels
+  float inv_tile;
 };
 
 template <int MAXV>
@@ -66,7 +68,7 @@ struct PreViews {
 };
 
 struct RasterView {
-  int32_t tile_base, gw, gh, width, height, pad;
+  int32_t tile_base, gw, gh, width, height, tile;  // tile: edge in pixels
   int64_t pix_base;
 };
 
@@ -105,6 +107,7 @@ struct Layout {
 
   int64_t n;
   int32_t nviews;
+  int32_t tile;           // tile edge in pixels (8 or 16)
   int64_t vis_cap, inst_cap;
   int64_t total_tiles, total_pixels;
   int32_t pre_blocks_per_view, pre_blocks;
@@ -398,11 +401,11 @@ inline bool make_raster_views(const Layout &L, const fgs4d_view *views, int32_t 
     RasterView &r = out->v[v];
     r.width = views[v].width;
     r.height = views[v].height;
-    r.gw = (views[v].width + kTile - 1) / kTile;
-    r.gh = (views[v].height + kTile - 1) / kTile;
+    r.gw = (views[v].width + L.tile - 1) / L.tile;
+    r.gh = (views[v].height + L.tile - 1) / L.tile;
     r.tile_base = (int32_t)tb;
     r.pix_base = pb;
-    r.pad = 0;
+    r.tile = L.tile;
     tb += (int64_t)r.gw * r.gh;
     pb += (int64_t)r.width * r.height;
   }

@@ -267,7 +267,7 @@ __device__ __forceinline__ bool forward_chain(int32_t i, const float4 *__restric
   const float disc = hd * hd + h.Sb * h.Sb;
   const float lam = mid + sqrtf(fmaxf(0.1f, disc));
   const float rad = ceilf(3.0f * sqrtf(lam));
-  const float inv_tile = 1.0f / (float)kTile;
+  const float inv_tile = cam.inv_tile;
   h.rect[0] = min(max(__float2int_rd((h.uv[0] - rad) * inv_tile), 0), cam.gw);
   h.rect[1] = min(max(__float2int_rd((h.uv[1] - rad) * inv_tile), 0), cam.gh);
   h.rect[2] = min(max(__float2int_rd((h.uv[0] + rad) * inv_tile) + 1, 0), cam.gw);
@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(BwdArgs A, PreViews
 }
 
 template <int MAXV>
-bool fill_pre_views(const fgs4d_view *views, int32_t nviews, PreViews<MAXV> *pv) {
+bool fill_pre_views(const fgs4d_view *views, int32_t nviews, int32_t tile, PreViews<MAXV> *pv) {
   if (nviews > MAXV) return false;
   for (int v = 0; v < MAXV; ++v) {
     PreView &o = pv->v[v];
@@ -680,8 +680,10 @@ bool fill_pre_views(const fgs4d_view *views, int32_t nviews, PreViews<MAXV> *pv)
     o.t = c.t;
     o.width = c.width;
     o.height = c.height;
-    o.gw = (c.width + kTile - 1) / kTile;
-    o.gh = (c.height + kTile - 1) / kTile;
+    o.gw = (c.width + tile - 1) / tile;
+    o.gh = (c.height + tile - 1) / tile;
+    o.tile = tile;
+    o.inv_tile = 1.0f / (float)tile;
   }
   return true;
 }
@@ -689,7 +691,7 @@ bool fill_pre_views(const fgs4d_view *views, int32_t nviews, PreViews<MAXV> *pv)
 template <int L, int MAXV>
 cudaError_t launch_pre_typed(const PreLaunch &p, const fgs4d_view *views, int32_t nviews) {
   PreViews<MAXV> pv;
-  fill_pre_views<MAXV>(views, nviews, &pv);
+  fill_pre_views<MAXV>(views, nviews, p.L->tile, &pv);
   const Layout &Lo = *p.L;
   PreArgs A;
   A.mean = reinterpret_cast<const float4 *>(p.g->mean);
@@ -726,7 +728,7 @@ template <int L, int MAXV>
 cudaError_t launch_bwd_typed(const PreLaunch &p, const fgs4d_view *views, int32_t nviews,
                              const fgs4d_gaussians_grad *gr) {
   PreViews<MAXV> pv;
-  fill_pre_views<MAXV>(views, nviews, &pv);
+  fill_pre_views<MAXV>(views, nviews, p.L->tile, &pv);
   const Layout &Lo = *p.L;
   BwdArgs A;
   A.mean = reinterpret_cast<const float4 *>(p.g->mean);
@@ -764,7 +766,7 @@ cudaError_t launch_bwd_typed(const PreLaunch &p, const fgs4d_view *views, int32_
 template <int MAXV>
 cudaError_t launch_aux_typed(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt) {
   PreViews<MAXV> pv;
-  fill_pre_views<MAXV>(views, nviews, &pv);
+  fill_pre_views<MAXV>(views, nviews, p.L->tile, &pv);
   const Layout &Lo = *p.L;
   AuxArgs A;
   A.mean = reinterpret_cast<const float4 *>(p.g->mean);

@@ -57,8 +57,10 @@ struct RenderBwdArgs {
   float bg0, bg1, bg2;
 };
 
-// Pixels per thread of the compositor kernels (the autotuned block shape).
+// Pixels per thread of the compositor kernels (the autotuned block shape):
+// 16x16 tiles take 2, 4 (default) or 8, 8x8 tiles 1 or 2 (default).
 inline int render_ppt(const fgs4d_settings *s) {
+  if (s->tile == 8) return s->pixels_per_thread == 1 ? 1 : 2;
   return (s->pixels_per_thread == 2 || s->pixels_per_thread == 8) ? s->pixels_per_thread : 4;
 }
 
@@ -102,12 +104,12 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
 // negated; a live pixel always has T >= 1e-4), so the inner loop carries no
 // separate flag.  The update stays a branch: whole warps skip it for entries
 // that miss all their pixels.
-template <int MAXV, int PPT, int kMode>
-__global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
-                                                                       unsigned long long *stats) {
+template <int MAXV, int TILE, int PPT, int kMode>
+__global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
+                                                                      unsigned long long *stats) {
   grid_dependency_sync();
   constexpr bool kStats = kMode == 1, kAux = kMode == 2;
-  constexpr int NT = kTilePixels / PPT;
+  constexpr int NT = TILE * TILE / PPT;
   __shared__ float4 s_geom[kBatch];
   __shared__ float4 s_col[kBatch];
   __shared__ float s_blue[kBatch];
@@ -116,8 +118,8 @@ __global__ void __launch_bounds__(kTilePixels / PPT) render_fwd_kernel(RenderArg
   const RasterView &V = rv.v[find_view<MAXV>(rv, gt)];
   const int32_t lt = gt - V.tile_base;
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
-  const int32_t px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int32_t py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
+  const int32_t px = tx * TILE + (threadIdx.x & (TILE - 1));
+  const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * PPT;
   const uint2 range = A.ranges[gt];
   const float pxc = (float)px + 0.5f;
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
@@ -248,10 +250,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // kAux: the loss also has gradients dL/dD, dL/dO with respect to the depth
 // and opacity channels (zero background, x_i = z_i resp. 1 in the colour
 // rule); adds dL/dz_i = sum dL/dD alpha_i T_i per slot.
-template <int MAXV, int kPPT, bool kAux>
-__global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBwdArgs A, RasterViews<MAXV> rv) {
+template <int MAXV, int TILE, int kPPT, bool kAux>
+__global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwdArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
-  constexpr int kRenderThreads = kTilePixels / kPPT;
+  constexpr int kRenderThreads = TILE * TILE / kPPT;
   __shared__ float4 s_geom[kBatch];
   __shared__ float4 s_col[kBatch];
   __shared__ float s_blue[kBatch];
@@ -262,8 +264,8 @@ __global__ void __launch_bounds__(kTilePixels / kPPT) render_bwd_kernel(RenderBw
   const RasterView &V = rv.v[find_view<MAXV>(rv, gt)];
   const int32_t lt = gt - V.tile_base;
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
-  const int32_t px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int32_t py0 = ty * kTile + (threadIdx.x / kTile) * kPPT;
+  const int32_t px = tx * TILE + (threadIdx.x & (TILE - 1));
+  const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * kPPT;
   const uint2 range = A.ranges[gt];
   const float pxc = (float)px + 0.5f;
   const int64_t HW = (int64_t)V.width * V.height;
@@ -467,15 +469,14 @@ __global__ void mask_loss_kernel(const float *__restrict__ m, int64_t n, float i
   }
 }
 
-template <int MAXV, int PPT>
+template <int MAXV, int TILE, int PPT>
 cudaError_t launch_fwd_ppt(const RenderArgs &A, const RasterViews<MAXV> &rv, unsigned grid,
                            unsigned long long *stats, cudaStream_t st) {
-  if (stats) return launch_pdl(render_fwd_kernel<MAXV, PPT, 1>, grid, kTilePixels / PPT, st, A, rv, stats);
+  constexpr unsigned NT = TILE * TILE / PPT;
+  if (stats) return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 1>, grid, NT, st, A, rv, stats);
   if (A.out_aux)
-    return launch_pdl(render_fwd_kernel<MAXV, PPT, 2>, grid, kTilePixels / PPT, st, A, rv,
-                      (unsigned long long *)nullptr);
-  return launch_pdl(render_fwd_kernel<MAXV, PPT, 0>, grid, kTilePixels / PPT, st, A, rv,
-                    (unsigned long long *)nullptr);
+    return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 2>, grid, NT, st, A, rv, (unsigned long long *)nullptr);
+  return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 0>, grid, NT, st, A, rv, (unsigned long long *)nullptr);
 }
 
 template <int MAXV>
@@ -502,17 +503,22 @@ cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   A.bg2 = s->bg[2];
   if (L.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)L.total_tiles;
+  if (s->tile == 8) {
+    if (render_ppt(s) == 1) return launch_fwd_ppt<MAXV, 8, 1>(A, rv, grid, stats, st);
+    return launch_fwd_ppt<MAXV, 8, 2>(A, rv, grid, stats, st);
+  }
   switch (render_ppt(s)) {
-    case 2: return launch_fwd_ppt<MAXV, 2>(A, rv, grid, stats, st);
-    case 8: return launch_fwd_ppt<MAXV, 8>(A, rv, grid, stats, st);
-    default: return launch_fwd_ppt<MAXV, 4>(A, rv, grid, stats, st);
+    case 2: return launch_fwd_ppt<MAXV, 16, 2>(A, rv, grid, stats, st);
+    case 8: return launch_fwd_ppt<MAXV, 16, 8>(A, rv, grid, stats, st);
+    default: return launch_fwd_ppt<MAXV, 16, 4>(A, rv, grid, stats, st);
   }
 }
 
-template <int MAXV, int PPT>
+template <int MAXV, int TILE, int PPT>
 cudaError_t launch_bwd_ppt(const RenderBwdArgs &A, const RasterViews<MAXV> &rv, unsigned grid, cudaStream_t st) {
-  if (A.dL_daux) return launch_pdl(render_bwd_kernel<MAXV, PPT, true>, grid, kTilePixels / PPT, st, A, rv);
-  return launch_pdl(render_bwd_kernel<MAXV, PPT, false>, grid, kTilePixels / PPT, st, A, rv);
+  constexpr unsigned NT = TILE * TILE / PPT;
+  if (A.dL_daux) return launch_pdl(render_bwd_kernel<MAXV, TILE, PPT, true>, grid, NT, st, A, rv);
+  return launch_pdl(render_bwd_kernel<MAXV, TILE, PPT, false>, grid, NT, st, A, rv);
 }
 
 template <int MAXV>
@@ -540,10 +546,14 @@ cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   A.bg2 = s->bg[2];
   if (L.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)L.total_tiles;
+  if (s->tile == 8) {
+    if (render_ppt(s) == 1) return launch_bwd_ppt<MAXV, 8, 1>(A, rv, grid, st);
+    return launch_bwd_ppt<MAXV, 8, 2>(A, rv, grid, st);
+  }
   switch (render_ppt(s)) {
-    case 2: return launch_bwd_ppt<MAXV, 2>(A, rv, grid, st);
-    case 8: return launch_bwd_ppt<MAXV, 8>(A, rv, grid, st);
-    default: return launch_bwd_ppt<MAXV, 4>(A, rv, grid, st);
+    case 2: return launch_bwd_ppt<MAXV, 16, 2>(A, rv, grid, st);
+    case 8: return launch_bwd_ppt<MAXV, 16, 8>(A, rv, grid, st);
+    default: return launch_bwd_ppt<MAXV, 16, 4>(A, rv, grid, st);
   }
 }
 

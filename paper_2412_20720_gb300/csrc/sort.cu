@@ -304,16 +304,18 @@ __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, Raste
       // bounding box: half-extents sqrt(tau C'/det), sqrt(tau A'/det) with
       // det = A'C' - B'^2/4, widened by 0.1% + 0.05 px against rounding (a
       // box outside them is far outside the ellipse, which the exact test
-      // below rejects as well).  Tile tx's centre box [16 tx + 0.5,
-      // 16 tx + 15.5] can meet [u - rx, u + rx] only for
-      // ceil((u - rx - 15.5) / 16) <= tx <= floor((u + rx - 0.5) / 16).
+      // below rejects as well).  With tile edge T, tile tx's centre box
+      // [T tx + 0.5, T tx + T - 0.5] can meet [u - rx, u + rx] only for
+      // ceil((u - rx - T + 0.5) / T) <= tx <= floor((u + rx - 0.5) / T).
       const float det = g.z * cc - 0.25f * g.w * g.w;
       if (tau < 0.0f) {
         x1 = x0;
       } else if (det > 0.0f) {
+        const RasterView &V = rv.v[MAXV == 1 ? 0 : min(max(mm.y, 0), rv.nviews - 1)];
+        const float T = (float)V.tile, iT = 1.0f / T;
         const float rx = sqrtf(tau * cc / det) * 1.001f + 0.05f, ry = sqrtf(tau * g.z / det) * 1.001f + 0.05f;
-        const float lx = ceilf((g.x - rx - 15.5f) * (1.0f / kTile)), hx = floorf((g.x + rx - 0.5f) * (1.0f / kTile));
-        const float ly = ceilf((g.y - ry - 15.5f) * (1.0f / kTile)), hy = floorf((g.y + ry - 0.5f) * (1.0f / kTile));
+        const float lx = ceilf((g.x - rx - (T - 0.5f)) * iT), hx = floorf((g.x + rx - 0.5f) * iT);
+        const float ly = ceilf((g.y - ry - (T - 0.5f)) * iT), hy = floorf((g.y + ry - 0.5f) * iT);
         if (lx > (float)x0) x0 = (int)fminf(lx, (float)x1);
         if (hx + 1.0f < (float)x1) x1 = (int)fmaxf(hx + 1.0f, (float)x0);
         if (ly > (float)y0) y0 = (int)fminf(ly, (float)y1);
@@ -460,9 +462,10 @@ __device__ __forceinline__ void walk_next(const EmitArgs &A, const EmitChunkSmem
 template <int MAXV>
 __device__ __forceinline__ bool walk_keep(const RasterViews<MAXV> &rv, const PairWalk &w) {
   const RasterView &V = rv.v[MAXV == 1 ? 0 : w.view];
-  const float bx0 = (float)(w.tx * kTile) + 0.5f, by0 = (float)(w.ty * kTile) + 0.5f;
-  const float bx1 = (float)min(w.tx * kTile + kTile - 1, V.width - 1) + 0.5f;
-  const float by1 = (float)min(w.ty * kTile + kTile - 1, V.height - 1) + 0.5f;
+  const int T = V.tile;
+  const float bx0 = (float)(w.tx * T) + 0.5f, by0 = (float)(w.ty * T) + 0.5f;
+  const float bx1 = (float)min(w.tx * T + T - 1, V.width - 1) + 0.5f;
+  const float by1 = (float)min(w.ty * T + T - 1, V.height - 1) + 0.5f;
   return ellipse_meets_box(w.u, w.v, w.A, w.B, w.C, w.kx, w.ky, w.tau, bx0, bx1, by0, by1);
 }
 

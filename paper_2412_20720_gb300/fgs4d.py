@@ -26,7 +26,7 @@ ERR_UNSUPPORTED = -7
 MAX_VIEWS = 128
 MAX_SH_DEGREE = 3
 MAX_T_ORDER = 4
-TILE = 16
+TILE = 16  # default tile edge; 8 is the other supported size
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
             "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
@@ -162,9 +162,10 @@ def make_views(views) -> tuple:
 
 
 def make_settings(sh_degree=3, t_order=2, period=1.0, near_plane=0.2, dilation=0.3, p_t_min=0.05,
-                  bg=(0.0, 0.0, 0.0), vis_capacity=0, inst_capacity=1 << 22, pixels_per_thread=0) -> Settings:
+                  bg=(0.0, 0.0, 0.0), vis_capacity=0, inst_capacity=1 << 22, pixels_per_thread=0,
+                  tile=TILE) -> Settings:
     s = Settings()
-    s.sh_degree, s.t_order, s.period, s.tile = int(sh_degree), int(t_order), float(period), TILE
+    s.sh_degree, s.t_order, s.period, s.tile = int(sh_degree), int(t_order), float(period), int(tile)
     s.near_plane, s.dilation, s.p_t_min = float(near_plane), float(dilation), float(p_t_min)
     for k in range(3):
         s.bg[k] = float(bg[k])

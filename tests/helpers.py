@@ -28,7 +28,7 @@ def f32(x: float) -> float:
 
 def oracle_settings(cfg: RenderConfig) -> oracle.Settings:
     """The oracle sees the FP32 values of the settings the GPU gets."""
-    return oracle.Settings(sh_degree=cfg.sh_degree, t_order=cfg.t_order, tile=16, period=f32(cfg.period),
+    return oracle.Settings(sh_degree=cfg.sh_degree, t_order=cfg.t_order, tile=cfg.tile, period=f32(cfg.period),
                            near_plane=f32(cfg.near_plane), dilation=f32(cfg.dilation), p_t_min=f32(cfg.p_t_min),
                            bg=tuple(f32(b) for b in cfg.bg))
 

@@ -46,10 +46,24 @@ def test_workspace_size_and_layout_are_consistent():
     assert len(set(offs)) == len(offs)
 
 
+def test_block_shape_must_fit_the_tile():
+    views, nv = _views()
+    for tile, ok, bad in ((16, (0, 2, 4, 8), (1,)), (8, (0, 1, 2), (4, 8))):
+        for p in ok:
+            fgs4d.workspace_size(fgs4d.make_settings(tile=tile, pixels_per_thread=p), 10, views, nv)
+        for p in bad:
+            with pytest.raises(fgs4d.Fgs4dError) as e:
+                fgs4d.workspace_size(fgs4d.make_settings(tile=tile, pixels_per_thread=p), 10, views, nv)
+            assert e.value.code == fgs4d.ERR_UNSUPPORTED
+    # 8x8 tiles: four times the tiles of 16x16 on a 128x96 view.
+    assert fgs4d.workspace_layout(fgs4d.make_settings(tile=8), 10, views, nv).total_tiles == 16 * 12
+
+
 @pytest.mark.parametrize("field,value,code", [
     ("sh_degree", 4, fgs4d.ERR_UNSUPPORTED),
     ("t_order", 5, fgs4d.ERR_UNSUPPORTED),
-    ("tile", 8, fgs4d.ERR_UNSUPPORTED),
+    ("tile", 32, fgs4d.ERR_UNSUPPORTED),
+    ("tile", 12, fgs4d.ERR_UNSUPPORTED),
     ("period", 0.0, fgs4d.ERR_ARG),
     ("near_plane", -1.0, fgs4d.ERR_ARG),
     ("dilation", float("nan"), fgs4d.ERR_ARG),

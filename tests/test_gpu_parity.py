@@ -21,10 +21,10 @@ pytestmark = pytest.mark.gpu
 IMAGE_ATOL = 2e-4
 
 
-def tiny_case(width=128, height=96, L=1, NT=1, bg=(0.0, 0.0, 0.0), seed=0, n=2000, t=0.5):
+def tiny_case(width=128, height=96, L=1, NT=1, bg=(0.0, 0.0, 0.0), seed=0, n=2000, t=0.5, tile=16):
     sc = sy.make_scene(n, seed, (-1, -1, -1), (1, 1, 1), sh_degree=L, t_order=NT)
     view = sy.tiny_view(width, height, t=t)
-    cfg = RenderConfig(sh_degree=L, t_order=NT, bg=bg, inst_capacity=1 << 18)
+    cfg = RenderConfig(sh_degree=L, t_order=NT, bg=bg, inst_capacity=1 << 18, tile=tile)
     params = sc.as_dict()
     return subset(params, keep_clear_of_boundaries(params, [view], cfg)), view, cfg
 
@@ -162,7 +162,7 @@ def test_autotune_picks_a_candidate_and_keeps_the_image():
     dev = to_device(params)
     ref = r.forward(dev).clone()
     res = autotune(r, dev, reps=2)
-    assert res["pixels_per_thread"] in (2, 4, 8) and set(res["ms"]) == {2, 4, 8}
+    assert res["pixels_per_thread"] in (2, 4, 8) and set(res["ms"]) == {"16/2", "16/4", "16/8"}
     assert r.settings.pixels_per_thread == res["pixels_per_thread"]
     assert torch.equal(r.forward(dev), ref)
 
@@ -193,10 +193,10 @@ def _write_records(r, rec, view_of_slot):
     r.workspace_view(r.layout.depth_key, torch.int32, n).copy_(dev(rec["depth"].astype(np.float32).view(np.int32)))
 
 
-def _synthetic_records(rng, n, W, H, max_extent):
+def _synthetic_records(rng, n, W, H, max_extent, tile=16):
     """Random tile rects, FP32 depths with exact ties, and 1/255 ellipses
     (u, v, A', B', C', tau) around centres near the rects."""
-    gw, gh = (W + 15) // 16, (H + 15) // 16
+    gw, gh = (W + tile - 1) // tile, (H + tile - 1) // tile
     x0 = rng.integers(0, gw, n)
     y0 = rng.integers(0, gh, n)
     rect = np.stack([x0, y0, np.minimum(gw, x0 + rng.integers(0, max_extent, n)),
@@ -204,8 +204,8 @@ def _synthetic_records(rng, n, W, H, max_extent):
     depth = rng.uniform(0.3, 40.0, n).astype(np.float32)
     depth[rng.integers(0, n, n // 10)] = depth[0]  # exact ties: order by slot
     depth[::97] = np.float32(0.2) + np.float32(1e-7)
-    cx = (rect[:, 0] + rect[:, 2]) * 8.0 + rng.uniform(-8, 8, n)
-    cy = (rect[:, 1] + rect[:, 3]) * 8.0 + rng.uniform(-8, 8, n)
+    cx = (rect[:, 0] + rect[:, 2]) * (tile / 2) + rng.uniform(-tile / 2, tile / 2, n)
+    cy = (rect[:, 1] + rect[:, 3]) * (tile / 2) + rng.uniform(-tile / 2, tile / 2, n)
     ang = rng.uniform(0, np.pi, n)
     s1 = np.exp(rng.uniform(np.log(0.5), np.log(30.0), n))
     s2 = np.exp(rng.uniform(np.log(0.5), np.log(30.0), n))
@@ -218,10 +218,10 @@ def _synthetic_records(rng, n, W, H, max_extent):
             "conic2": np.stack([A, B, C], 1).astype(np.float32), "tau": rng.uniform(0.0, 8.0, n).astype(np.float32)}
 
 
-def _oracle_sorted(rec, W, H):
-    gw, gh = (W + 15) // 16, (H + 15) // 16
+def _oracle_sorted(rec, W, H, tile=16):
+    gw, gh = (W + tile - 1) // tile, (H + tile - 1) // tile
     return oracle.sort_instances(rec["rect"], rec["depth"], gw, gh, uv=rec["uv"], conic2=rec["conic2"],
-                                 tau=rec["tau"], width=W, height=H)
+                                 tau=rec["tau"], width=W, height=H, tile=tile)
 
 
 @pytest.mark.parametrize("n,W,H", [(1, 16, 16), (2047, 144, 112), (70_001, 1352, 1014)])

@@ -47,7 +47,8 @@ FLOPS_PER_COMP = 9
 # DRAM bytes (read + write) of one compositor launch on this workload, per
 # block shape, from the ncu launch list summarised in
 # profiles/launches_orbit_300k_1352x1014.md; emptied whenever the kernel changes.
-RENDER_FWD_TRAFFIC = {(16, 2): 7.655e6, (16, 4): 7.648e6, (16, 8): 7.382e6}  # (tile, pixels per thread)
+# keyed by (tile, pixels per thread, shared batch)
+RENDER_FWD_TRAFFIC = {(16, 2, 256): 7.655e6, (16, 4, 256): 7.648e6, (16, 8, 256): 7.382e6}
 
 
 def parse():
@@ -220,7 +221,7 @@ def run_ours(args, rank, world, local):
     r = Renderer(scene.n, views[:1], cfg, device=dev)
     vv = [fgs4d.make_views([v]) for v in views]
     tuned = autotune(r, params, view_sets=[vv[k] for k in sorted({0, nviews // 3, 2 * nviews // 3})],
-                     tiles=(16, 8))
+                     tiles=(16, 8), batches=(256, 128))
     g = r.gaussians(params)
     ws, wsb, s = r.ws.data_ptr(), r.ws_bytes, r.settings
     stream = torch.cuda.current_stream(dev)
@@ -386,7 +387,8 @@ def run_ours(args, rank, world, local):
                                "alpha_evals": float(np.mean(evals)), "composited": float(np.mean(comps))},
             "roofline": {"kernel": "render_fwd", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                         "traffic": RENDER_FWD_TRAFFIC.get((tuned["tile"], tuned["pixels_per_thread"])),
+                         "traffic": RENDER_FWD_TRAFFIC.get((tuned["tile"], tuned["pixels_per_thread"],
+                                                            tuned["shared_batch"])),
                          "peak_basis": "SMs x 128 FP32 lanes x 2 (FMA) x max SM clock %.0f MHz (derived)" % sm_max,
                          "flops_per_launch": mean_flops},
             "preprocess_roofline": {"bound": "hbm", "achieved": pre_gbs, "peak": hbm, "unit": "GB/s",
@@ -421,7 +423,7 @@ def run_train(args, dev, scene, params, world, barrier):
     del rt, tparams
     leaf = {k: params[k].clone().requires_grad_(True) for k in PARAM_KEYS}
     r = Renderer(scene.n, views, cfg, device=dev)
-    tuned = autotune(r, {k: leaf[k].detach() for k in PARAM_KEYS}, backward=True, tiles=(16, 8))
+    tuned = autotune(r, {k: leaf[k].detach() for k in PARAM_KEYS}, backward=True, tiles=(16, 8), batches=(256, 128))
     grads = {k: torch.zeros_like(leaf[k]) for k in PARAM_KEYS}
     # Adam with the library's kernel; its step count lives on the device, so
     # the whole step can be replayed as one CUDA graph.
@@ -512,8 +514,8 @@ def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,))
                            inst_capacity=min(int(counts[1] * 1.1) + 1024, (1 << 30) - 1))
         r = Renderer(n, gv, cfg, device=dev)
         if tuned is None:
-            tuned = autotune(r, params, backward=True, reps=2, tiles=tiles)
-        r.set_tile(tuned["tile"], tuned["pixels_per_thread"])
+            tuned = autotune(r, params, backward=True, reps=2, tiles=tiles, batches=(256, 128))
+        r.set_tile(tuned["tile"], tuned["pixels_per_thread"], tuned["shared_batch"])
         rs.append(r)
         vis_tot += counts[0]
         inst_tot += counts[1]
@@ -565,7 +567,8 @@ def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,))
             key = (v["width"], v["height"])
             if key not in per_res:
                 c1 = RenderConfig(sh_degree=3, t_order=2, vis_capacity=n, inst_capacity=max_inst + 1024,
-                                  pixels_per_thread=tuned["pixels_per_thread"], tile=tuned["tile"])
+                                  pixels_per_thread=tuned["pixels_per_thread"], tile=tuned["tile"],
+                                  shared_batch=tuned["shared_batch"])
                 per_res[key] = Renderer(n, [v], c1, device=dev)
             rr = per_res[key]
             singles.append((rr, fgs4d.make_views([v]), torch.randn(3 * v["width"] * v["height"], device=dev,

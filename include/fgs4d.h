@@ -86,7 +86,7 @@ typedef struct fgs4d_settings {
   int64_t inst_capacity; /* max (tile, Gaussian) instances over all views, > 0 */
   int32_t pixels_per_thread; /* compositor block shape: 0 (default 4), 2, 4 or 8 pixels
                                 of one tile column per thread; results are identical */
-  int32_t reserved;          /* must be 0 */
+  int32_t shared_batch;      /* records the compositors stage per shared-memory batch: 0 (= 256), 128 or 256 */
 } fgs4d_settings;
 
 /* Gaussian parameters (device pointers, layout in the header comment). */

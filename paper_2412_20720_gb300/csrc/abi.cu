@@ -37,7 +37,7 @@ int check_settings(const fgs4d_settings *s) {
   const int ppt = s->pixels_per_thread;
   if (ppt != 0 && !(s->tile == 16 ? (ppt == 2 || ppt == 4 || ppt == 8) : (ppt == 1 || ppt == 2)))
     return FGS4D_ERR_UNSUPPORTED;
-  if (s->reserved != 0) return FGS4D_ERR_ARG;
+  if (s->shared_batch != 0 && s->shared_batch != 128 && s->shared_batch != 256) return FGS4D_ERR_UNSUPPORTED;
   return FGS4D_OK;
 }
 

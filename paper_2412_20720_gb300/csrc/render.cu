@@ -26,7 +26,6 @@ namespace fgs4d {
 
 namespace {
 
-constexpr int kBatch = 256;  // records staged per shared-memory batch
 
 struct RenderArgs {
   const uint2 *ranges;
@@ -68,7 +67,7 @@ inline int render_ppt(const fgs4d_settings *s) {
 // Stages records [base, min(base + kBatch, end)) of the tile list into shared
 // memory; slots out of range (only possible after a recorded timeout) stage a
 // record that every pixel skips.
-template <int NT>
+template <int NT, int kBatch>
 __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const float4 *rec_geom,
                                             const float4 *rec_color, const float *rec_blue, uint32_t vis_cap,
                                             uint32_t base, uint32_t end, float4 *s_geom, float4 *s_col,
@@ -104,7 +103,7 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
 // negated; a live pixel always has T >= 1e-4), so the inner loop carries no
 // separate flag.  The update stays a branch: whole warps skip it for entries
 // that miss all their pixels.
-template <int MAXV, int TILE, int PPT, int kMode>
+template <int MAXV, int TILE, int PPT, int kMode, int kBatch>
 __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
                                                                       unsigned long long *stats) {
   grid_dependency_sync();
@@ -139,7 +138,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs
   uint32_t n_eval = 0u, n_comp = 0u;
   for (uint32_t base = range.x; base < range.y; base += kBatch) {
     if (__syncthreads_count(nlive > 0) == 0) break;
-    stage_batch<NT>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, range.y, s_geom, s_col,
+    stage_batch<NT, kBatch>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, range.y, s_geom, s_col,
                     s_blue, nullptr, kAux ? A.rec_aux : nullptr, kAux ? s_aux : nullptr);
     __syncthreads();
     const int nb = (int)min(range.y - base, (uint32_t)kBatch);
@@ -250,7 +249,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // kAux: the loss also has gradients dL/dD, dL/dO with respect to the depth
 // and opacity channels (zero background, x_i = z_i resp. 1 in the colour
 // rule); adds dL/dz_i = sum dL/dD alpha_i T_i per slot.
-template <int MAXV, int TILE, int kPPT, bool kAux>
+template <int MAXV, int TILE, int kPPT, bool kAux, int kBatch>
 __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwdArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
   constexpr int kRenderThreads = TILE * TILE / kPPT;
@@ -313,7 +312,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
   for (int bi = nbatch - 1; bi >= 0; --bi) {
     const uint32_t base = range.x + (uint32_t)bi * kBatch;
     __syncthreads();
-    stage_batch<kRenderThreads>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, end, s_geom,
+    stage_batch<kRenderThreads, kBatch>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, end, s_geom,
                                 s_col, s_blue, s_slot, kAux ? A.rec_aux : nullptr, kAux ? s_aux : nullptr);
     __syncthreads();
     const int nb = (int)min(end - base, (uint32_t)kBatch);
@@ -469,14 +468,21 @@ __global__ void mask_loss_kernel(const float *__restrict__ m, int64_t n, float i
   }
 }
 
+template <int MAXV, int TILE, int PPT, int B>
+cudaError_t launch_fwd_batch(const RenderArgs &A, const RasterViews<MAXV> &rv, unsigned grid,
+                             unsigned long long *stats, cudaStream_t st) {
+  constexpr unsigned NT = TILE * TILE / PPT;
+  if (stats) return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 1, B>, grid, NT, st, A, rv, stats);
+  if (A.out_aux)
+    return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 2, B>, grid, NT, st, A, rv, (unsigned long long *)nullptr);
+  return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 0, B>, grid, NT, st, A, rv, (unsigned long long *)nullptr);
+}
+
 template <int MAXV, int TILE, int PPT>
 cudaError_t launch_fwd_ppt(const RenderArgs &A, const RasterViews<MAXV> &rv, unsigned grid,
-                           unsigned long long *stats, cudaStream_t st) {
-  constexpr unsigned NT = TILE * TILE / PPT;
-  if (stats) return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 1>, grid, NT, st, A, rv, stats);
-  if (A.out_aux)
-    return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 2>, grid, NT, st, A, rv, (unsigned long long *)nullptr);
-  return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 0>, grid, NT, st, A, rv, (unsigned long long *)nullptr);
+                           unsigned long long *stats, int batch, cudaStream_t st) {
+  if (batch == 128) return launch_fwd_batch<MAXV, TILE, PPT, 128>(A, rv, grid, stats, st);
+  return launch_fwd_batch<MAXV, TILE, PPT, 256>(A, rv, grid, stats, st);
 }
 
 template <int MAXV>
@@ -504,21 +510,28 @@ cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   if (L.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)L.total_tiles;
   if (s->tile == 8) {
-    if (render_ppt(s) == 1) return launch_fwd_ppt<MAXV, 8, 1>(A, rv, grid, stats, st);
-    return launch_fwd_ppt<MAXV, 8, 2>(A, rv, grid, stats, st);
+    if (render_ppt(s) == 1) return launch_fwd_ppt<MAXV, 8, 1>(A, rv, grid, stats, s->shared_batch, st);
+    return launch_fwd_ppt<MAXV, 8, 2>(A, rv, grid, stats, s->shared_batch, st);
   }
   switch (render_ppt(s)) {
-    case 2: return launch_fwd_ppt<MAXV, 16, 2>(A, rv, grid, stats, st);
-    case 8: return launch_fwd_ppt<MAXV, 16, 8>(A, rv, grid, stats, st);
-    default: return launch_fwd_ppt<MAXV, 16, 4>(A, rv, grid, stats, st);
+    case 2: return launch_fwd_ppt<MAXV, 16, 2>(A, rv, grid, stats, s->shared_batch, st);
+    case 8: return launch_fwd_ppt<MAXV, 16, 8>(A, rv, grid, stats, s->shared_batch, st);
+    default: return launch_fwd_ppt<MAXV, 16, 4>(A, rv, grid, stats, s->shared_batch, st);
   }
 }
 
-template <int MAXV, int TILE, int PPT>
-cudaError_t launch_bwd_ppt(const RenderBwdArgs &A, const RasterViews<MAXV> &rv, unsigned grid, cudaStream_t st) {
+template <int MAXV, int TILE, int PPT, int B>
+cudaError_t launch_bwd_batch(const RenderBwdArgs &A, const RasterViews<MAXV> &rv, unsigned grid, cudaStream_t st) {
   constexpr unsigned NT = TILE * TILE / PPT;
-  if (A.dL_daux) return launch_pdl(render_bwd_kernel<MAXV, TILE, PPT, true>, grid, NT, st, A, rv);
-  return launch_pdl(render_bwd_kernel<MAXV, TILE, PPT, false>, grid, NT, st, A, rv);
+  if (A.dL_daux) return launch_pdl(render_bwd_kernel<MAXV, TILE, PPT, true, B>, grid, NT, st, A, rv);
+  return launch_pdl(render_bwd_kernel<MAXV, TILE, PPT, false, B>, grid, NT, st, A, rv);
+}
+
+template <int MAXV, int TILE, int PPT>
+cudaError_t launch_bwd_ppt(const RenderBwdArgs &A, const RasterViews<MAXV> &rv, unsigned grid, int batch,
+                           cudaStream_t st) {
+  if (batch == 128) return launch_bwd_batch<MAXV, TILE, PPT, 128>(A, rv, grid, st);
+  return launch_bwd_batch<MAXV, TILE, PPT, 256>(A, rv, grid, st);
 }
 
 template <int MAXV>
@@ -547,13 +560,13 @@ cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   if (L.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)L.total_tiles;
   if (s->tile == 8) {
-    if (render_ppt(s) == 1) return launch_bwd_ppt<MAXV, 8, 1>(A, rv, grid, st);
-    return launch_bwd_ppt<MAXV, 8, 2>(A, rv, grid, st);
+    if (render_ppt(s) == 1) return launch_bwd_ppt<MAXV, 8, 1>(A, rv, grid, s->shared_batch, st);
+    return launch_bwd_ppt<MAXV, 8, 2>(A, rv, grid, s->shared_batch, st);
   }
   switch (render_ppt(s)) {
-    case 2: return launch_bwd_ppt<MAXV, 16, 2>(A, rv, grid, st);
-    case 8: return launch_bwd_ppt<MAXV, 16, 8>(A, rv, grid, st);
-    default: return launch_bwd_ppt<MAXV, 16, 4>(A, rv, grid, st);
+    case 2: return launch_bwd_ppt<MAXV, 16, 2>(A, rv, grid, s->shared_batch, st);
+    case 8: return launch_bwd_ppt<MAXV, 16, 8>(A, rv, grid, s->shared_batch, st);
+    default: return launch_bwd_ppt<MAXV, 16, 4>(A, rv, grid, s->shared_batch, st);
   }
 }
 

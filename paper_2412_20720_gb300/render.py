@@ -29,12 +29,13 @@ class RenderConfig:
     inst_capacity: int = 1 << 22
     pixels_per_thread: int = 0  # compositor block shape (0 = library default); see autotune()
     tile: int = 16  # tile edge in pixels, 16 or 8; see autotune()
+    shared_batch: int = 0  # records staged per shared-memory batch, 128 or 256 (0 = 256); see autotune()
     mask_threshold: float = 0.01  # epsilon of the Compact-4DGS mask, used when params carry "mask_logit"
 
     def settings(self) -> fgs4d.Settings:
         return fgs4d.make_settings(self.sh_degree, self.t_order, self.period, self.near_plane, self.dilation,
                                    self.p_t_min, self.bg, self.vis_capacity, self.inst_capacity,
-                                   self.pixels_per_thread, self.tile)
+                                   self.pixels_per_thread, self.tile, self.shared_batch)
 
 
 def _ptr(t: torch.Tensor) -> int:
@@ -77,10 +78,12 @@ class Renderer:
         self.ws = self._ws_raw[off:off + self.ws_bytes]
         self.total_pixels = int(self.layout.total_pixels)
 
-    def set_tile(self, tile: int, pixels_per_thread: int = 0):
-        """Switches the tile edge (16 or 8) and compositor block shape; a new
-        tile edge re-lays out (and reallocates) the workspace."""
+    def set_tile(self, tile: int, pixels_per_thread: int = 0, shared_batch: int = 0):
+        """Switches the tile edge (16 or 8), the compositor block shape and its
+        shared-memory batch size; a new tile edge re-lays out (and
+        reallocates) the workspace."""
         self.settings.pixels_per_thread = int(pixels_per_thread)
+        self.settings.shared_batch = int(shared_batch)
         if int(tile) != int(self.settings.tile):
             self.settings.tile = int(tile)
             self._allocate()
@@ -227,12 +230,13 @@ class Renderer:
 PPT_CANDIDATES = {16: (2, 4, 8), 8: (1, 2)}
 
 
-def autotune(renderer: Renderer, params: dict, view_sets=None, tiles=(16,), candidates=None, reps: int = 3,
-             backward: bool = False, cache_path: str | None = None) -> dict:
-    """Picks the tile edge (among ``tiles``: 16, 8) and the compositor block
-    shape (pixels per thread, ``candidates`` or all valid ones per tile) that
-    run the caller's own workload fastest, and sets them on ``renderer``
-    (a new tile edge reallocates its workspace).
+def autotune(renderer: Renderer, params: dict, view_sets=None, tiles=(16,), candidates=None, batches=(256,),
+             reps: int = 3, backward: bool = False, cache_path: str | None = None) -> dict:
+    """Picks the tile edge (among ``tiles``: 16, 8), the compositor block
+    shape (pixels per thread, ``candidates`` or all valid ones per tile) and
+    its shared-memory batch size (among ``batches``: 256, 128) that run the
+    caller's own workload fastest, and sets them on ``renderer`` (a new tile
+    edge reallocates its workspace).
 
     Each (tile, shape) is timed with CUDA events on the current stream over
     ``reps`` runs of preprocess + bin_sort + render_fwd (+ render_bwd if
@@ -240,22 +244,24 @@ def autotune(renderer: Renderer, params: dict, view_sets=None, tiles=(16,), cand
     views) -- the tile edge changes the sort's work as well as the
     compositor's.  With ``cache_path``, the choice is stored in a JSON file
     keyed by (GPU, resolutions, views, N rounded to a power of two) and
-    reused.  Returns {"tile": t, "pixels_per_thread": p, "ms": {"t/p": ms}}."""
+    reused.  Returns {"tile": t, "pixels_per_thread": p, "shared_batch": b,
+    "ms": {"t/p/b": ms}}."""
     import json
     import os
 
     dev_name = torch.cuda.get_device_name(renderer.device)
     bucket = 1 << max(0, int(renderer.n - 1).bit_length())
     res = "+".join("%dx%d" % (w, h) for h, w in sorted(set(renderer.sizes)))
-    key = "%s|%s|v%d|n%d|%s|t%s" % (dev_name, res, renderer.nviews, bucket, "fb" if backward else "f",
-                                    ",".join(str(t) for t in tiles))
+    key = "%s|%s|v%d|n%d|%s|t%s|b%s" % (dev_name, res, renderer.nviews, bucket, "fb" if backward else "f",
+                                        ",".join(str(t) for t in tiles), ",".join(str(b) for b in batches))
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
             cache = json.load(f)
         if key in cache:
-            renderer.set_tile(int(cache[key]["tile"]), int(cache[key]["pixels_per_thread"]))
-            return cache[key]
+            c = cache[key]
+            renderer.set_tile(int(c["tile"]), int(c["pixels_per_thread"]), int(c["shared_batch"]))
+            return c
     view_sets = view_sets or [(renderer.views, renderer.nviews)]
     g = renderer.gaussians(params)
     st = renderer.stream()
@@ -264,36 +270,38 @@ def autotune(renderer: Renderer, params: dict, view_sets=None, tiles=(16,), cand
     grads = {k: torch.zeros_like(params[k]) for k in PARAM_KEYS} if backward else None
     stream = torch.cuda.current_stream(renderer.device)
     ms = {}
-    for tile in tiles:
-        for p in (candidates if candidates is not None and tile == 16 else PPT_CANDIDATES[int(tile)]):
-            renderer.set_tile(tile, p)
-            ws, wsb = renderer.ws.data_ptr(), renderer.ws_bytes
-            total = 0.0
-            for views, nv in view_sets:
-                def run():
-                    fgs4d.preprocess(g, views, nv, renderer.settings, ws, wsb, st)
-                    fgs4d.bin_sort(renderer.n, views, nv, renderer.settings, ws, wsb, st)
-                    fgs4d.render_fwd(renderer.n, views, nv, renderer.settings, ws, wsb, out.data_ptr(), None, st)
-                    if backward:
-                        fgs4d.render_bwd(g, views, nv, renderer.settings, ws, wsb, dL.data_ptr(),
-                                         fgs4d.make_grads({k: grads[k].data_ptr() for k in PARAM_KEYS}), st)
+    shapes = [(t, p, b) for t in tiles
+              for p in (candidates if candidates is not None and t == 16 else PPT_CANDIDATES[int(t)])
+              for b in batches]
+    for tile, p, bsz in shapes:
+        renderer.set_tile(tile, p, bsz)
+        ws, wsb = renderer.ws.data_ptr(), renderer.ws_bytes
+        total = 0.0
+        for views, nv in view_sets:
+            def run():
+                fgs4d.preprocess(g, views, nv, renderer.settings, ws, wsb, st)
+                fgs4d.bin_sort(renderer.n, views, nv, renderer.settings, ws, wsb, st)
+                fgs4d.render_fwd(renderer.n, views, nv, renderer.settings, ws, wsb, out.data_ptr(), None, st)
+                if backward:
+                    fgs4d.render_bwd(g, views, nv, renderer.settings, ws, wsb, dL.data_ptr(),
+                                     fgs4d.make_grads({k: grads[k].data_ptr() for k in PARAM_KEYS}), st)
+            run()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
                 run()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                for _ in range(reps):
-                    run()
-                b.record(stream)
-                b.synchronize()
-                total += a.elapsed_time(b) / reps
-            code, _ = renderer.status()
-            if code == fgs4d.OK:  # a shape whose run overflowed a capacity is not a candidate
-                ms["%d/%d" % (tile, p)] = total
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b) / reps
+        code, _ = renderer.status()
+        if code == fgs4d.OK:  # a shape whose run overflowed a capacity is not a candidate
+            ms["%d/%d/%d" % (tile, p, bsz)] = total
     if not ms:
         raise RuntimeError("autotune: every candidate overflowed a capacity")
     best = min(ms, key=ms.get)
-    bt, bp = (int(x) for x in best.split("/"))
-    renderer.set_tile(bt, bp)
-    result = {"tile": bt, "pixels_per_thread": bp, "ms": ms}
+    bt, bp, bb = (int(x) for x in best.split("/"))
+    renderer.set_tile(bt, bp, bb)
+    result = {"tile": bt, "pixels_per_thread": bp, "shared_batch": bb, "ms": ms}
     if cache_path:
         cache[key] = result
         with open(cache_path, "w") as f:

@@ -73,7 +73,8 @@ def test_block_shape_must_fit_the_tile():
     ("vis_capacity", -1, fgs4d.ERR_ARG),
     ("pixels_per_thread", 3, fgs4d.ERR_UNSUPPORTED),
     ("pixels_per_thread", 16, fgs4d.ERR_UNSUPPORTED),
-    ("reserved", 1, fgs4d.ERR_ARG),
+    ("shared_batch", 64, fgs4d.ERR_UNSUPPORTED),
+    ("shared_batch", 512, fgs4d.ERR_UNSUPPORTED),
 ])
 def test_bad_settings_are_rejected(field, value, code):
     s = fgs4d.make_settings()

@@ -141,8 +141,8 @@ def test_block_shapes_render_identically():
     rng = np.random.default_rng(12)
     dimg = rng.standard_normal((3, 77, 131))
     runs = []
-    for p in (2, 4, 8):
-        c = RenderConfig(**{**cfg.__dict__, "pixels_per_thread": p})
+    for p, b in ((2, 256), (4, 256), (8, 256), (4, 128), (2, 128)):  # shapes and shared batch sizes
+        c = RenderConfig(**{**cfg.__dict__, "pixels_per_thread": p, "shared_batch": b})
         run = GpuRun(params, [view], c)
         runs.append((run, run.backward([dimg])[0]))
     for run, g in runs[1:]:
@@ -162,7 +162,7 @@ def test_autotune_picks_a_candidate_and_keeps_the_image():
     dev = to_device(params)
     ref = r.forward(dev).clone()
     res = autotune(r, dev, reps=2)
-    assert res["pixels_per_thread"] in (2, 4, 8) and set(res["ms"]) == {"16/2", "16/4", "16/8"}
+    assert res["pixels_per_thread"] in (2, 4, 8) and set(res["ms"]) == {"16/2/256", "16/4/256", "16/8/256"}
     assert r.settings.pixels_per_thread == res["pixels_per_thread"]
     assert torch.equal(r.forward(dev), ref)
 

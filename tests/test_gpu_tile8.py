@@ -26,10 +26,14 @@ def test_image_matches_oracle_at_tile_8(w, h, L, NT, bg):
 
 
 def test_tile_8_block_shapes_render_identically():
+    """Block shape and shared batch size change the work split only."""
     params, view, cfg = tiny_case(131, 77, 2, 1, (0.1, 0.1, 0.1), tile=8)
-    runs = [GpuRun(params, [view], RenderConfig(**{**cfg.__dict__, "pixels_per_thread": p})) for p in (1, 2)]
-    np.testing.assert_array_equal(runs[1].images[0], runs[0].images[0])
-    np.testing.assert_array_equal(runs[1].T, runs[0].T)
+    runs = [GpuRun(params, [view], RenderConfig(**{**cfg.__dict__, "pixels_per_thread": p, "shared_batch": b}))
+            for p, b in ((1, 256), (2, 256), (2, 128))]
+    for run in runs[1:]:
+        np.testing.assert_array_equal(run.images[0], runs[0].images[0])
+        np.testing.assert_array_equal(run.T, runs[0].T)
+        np.testing.assert_array_equal(run.last, runs[0].last)
 
 
 @pytest.mark.parametrize("n,W,H", [(2047, 144, 112), (30_001, 1352, 1014)])
@@ -64,9 +68,11 @@ def test_autotune_over_both_tile_sizes():
     params, view, cfg = tiny_case(tile=16)
     r = Renderer(params["mean"].shape[0], [view], cfg)
     dev = to_device(params)
-    res = autotune(r, dev, reps=2, tiles=(16, 8))
-    assert set(res["ms"]) == {"16/2", "16/4", "16/8", "8/1", "8/2"}
+    res = autotune(r, dev, reps=2, tiles=(16, 8), batches=(256, 128))
+    assert set(res["ms"]) == {"%d/%d/%d" % (t, p, b) for t, p in ((16, 2), (16, 4), (16, 8), (8, 1), (8, 2))
+                              for b in (256, 128)}
     assert r.settings.tile == res["tile"] and r.settings.pixels_per_thread == res["pixels_per_thread"]
+    assert r.settings.shared_batch == res["shared_batch"]
     img = r.split(r.forward(dev))[0].cpu().numpy()
     r.check()
     # The chosen tile edge renders the oracle's image at that edge.

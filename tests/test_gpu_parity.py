@@ -133,6 +133,73 @@ def test_batched_views_equal_single_views():
         check_image(batch, params, v, cfg, k)
 
 
+def _check_views_against_oracle(run, params, views, cfg, min_clear=0.95):
+    """Every view of one call against the oracle; the share of pixels clear
+    of a per-pixel decision is bounded over all views together (a view of a
+    handful of pixels can be wholly flagged)."""
+    ost = oracle_settings(cfg)
+    n_clear = n_all = 0
+    for k, v in enumerate(views):
+        pr = oracle.preprocess(params, v, ost)
+        img, T, nc, mg = oracle.render(pr, v, ost)
+        ok = mg >= PIXEL_MARGIN
+        n_clear += int(ok.sum())
+        n_all += ok.size
+        assert run.images[k].shape == (3, v["height"], v["width"])
+        Tg, lastg = run.pixel_planes(k)
+        assert np.all((lastg == 0) == (nc == 0))
+        if ok.any():
+            assert np.abs(run.images[k] - img)[:, ok].max() <= IMAGE_ATOL
+            assert np.abs(Tg - T)[ok].max() <= IMAGE_ATOL
+    assert n_clear / n_all >= min_clear
+
+
+def _crop(view, x0, y0, w, h):
+    """The w x h window at (x0, y0) of a view's image, as a view of its own
+    (same focal length, principal point shifted)."""
+    v = dict(view)
+    v.update(width=w, height=h, cx=np.float32(view["cx"] - x0), cy=np.float32(view["cy"] - y0))
+    return v
+
+
+@pytest.mark.parametrize("tile", [16, 8])
+def test_single_pixel_and_one_pixel_wide_views(tile):
+    """Windows of a 128x96 view smaller than one tile and one pixel wide or
+    high, batched with windows one pixel past a tile edge: every tile is
+    ragged."""
+    sc = sy.make_scene(2000, 9, (-1, -1, -1), (1, 1, 1), sh_degree=2, t_order=1)
+    full = sy.tiny_view(128, 96, t=0.5)
+    views = [_crop(full, 64, 48, 1, 1), _crop(full, 70, 20, 1, 40), _crop(full, 40, 50, 37, 1),
+             _crop(full, 50, 30, tile, tile), _crop(full, 30, 25, tile + 1, 2 * tile + 1),
+             _crop(sy.tiny_view(128, 96, t=0.3), 0, 0, 128, 96)]
+    cfg = RenderConfig(sh_degree=2, t_order=1, inst_capacity=1 << 18, bg=(0.3, 0.2, 0.1), tile=tile)
+    params = sc.as_dict()
+    params = subset(params, keep_clear_of_boundaries(params, views, cfg))
+    run = GpuRun(params, views, cfg)
+    _check_views_against_oracle(run, params, views, cfg)
+
+
+def test_maximum_view_count_in_one_call():
+    """FGS4D_MAX_VIEWS (camera, t) views of four sizes in one call: each
+    matches the oracle, and the first and last equal their single-view
+    renders bit for bit."""
+    sc = sy.make_scene(2000, 10, (-1, -1, -1), (1, 1, 1), sh_degree=1, t_order=1)
+    sizes = ((24, 20), (33, 17), (16, 16), (9, 40))
+    views = []
+    for k in range(fgs4d.MAX_VIEWS):
+        th = 2.0 * math.pi * k / fgs4d.MAX_VIEWS
+        w, h = sizes[k % 4]
+        views.append(sy.look_at((3.0 * math.sin(th), 0.4 * math.cos(3 * th), -3.0 * math.cos(th)), (0, 0, 0),
+                                (0, -1, 0), w, h, k / (fgs4d.MAX_VIEWS - 1), hfov_deg=15.0))
+    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=1 << 20, bg=(0.0, 0.1, 0.0))
+    params = sc.as_dict()
+    params = subset(params, keep_clear_of_boundaries(params, views, cfg))
+    run = GpuRun(params, views, cfg)
+    _check_views_against_oracle(run, params, views, cfg)
+    for k in (0, fgs4d.MAX_VIEWS - 1):
+        np.testing.assert_array_equal(run.images[k], GpuRun(params, [views[k]], cfg).images[0])
+
+
 def test_block_shapes_render_identically():
     """The autotuned compositor block shape (pixels per thread) changes the
     work split, not the arithmetic: bit-identical images, gradients equal up

@@ -148,7 +148,7 @@ typedef struct fgs4d_layout {
   size_t bytes;         /* total workspace size */
   size_t counters;      /* uint32: [0] visible pairs, [1] instances, [2] status bits */
   size_t rec_geom;      /* float4 [vis_cap]: (u, v, A', B') with power2 = -(A' dx^2 + B' dx dy + C' dy^2) */
-  size_t rec_color;     /* float4 [vis_cap]: (C', a, r, g) with a = sigmoid(logit) p(t) */
+  size_t rec_color;     /* float4 [vis_cap]: (C', log2 a, r, g) with a = sigmoid(logit) p(t) */
   size_t rec_blue;      /* float  [vis_cap]: b */
   size_t rec_tau;       /* float  [vis_cap]: log2(255 a) + 4e-3; alpha >= 1/255 needs -power2 <= tau */
   size_t rec_meta;      /* int32x4 [vis_cap]: (gaussian, view, x0 | y0 << 16, x1 | y1 << 16) tile rect */

@@ -116,7 +116,7 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.pair_cap = std::min<int64_t>(8 * L.inst_cap, (int64_t)INT32_MAX);
   L.chunk_cap = (int32_t)((L.pair_cap + kEmitChunk - 1) / kEmitChunk);
   L.emit_grid = std::max(1, std::min(L.chunk_cap, 152 * 8));
-  L.depth_blocks = (int32_t)((L.vis_cap + kSortTile - 1) / kSortTile);
+  L.depth_blocks = (int32_t)((L.vis_cap + kDepthSortTile - 1) / kDepthSortTile);
   L.tile_blocks = (int32_t)((L.inst_cap + kSortTile - 1) / kSortTile);
 
   size_t off = 0;

@@ -56,7 +56,7 @@ __device__ __forceinline__ void stage_feature(const FeatArgs &A, const float *s_
                                               float *s_norm, int32_t *s_gi) {
   const uint32_t s = A.inst_val[idx];
   float4 geom = make_float4(0.f, 0.f, 0.f, 0.f);
-  float2 ca = make_float2(0.f, 0.f);  // (C', a): a = 0 makes every pixel skip the entry
+  float2 ca = make_float2(0.f, kLogAlphaNone);  // (C', log2 a): every pixel skips the entry
   int32_t gi = -1;
   if (s < A.vis_cap) {
     geom = A.rec_geom[s];
@@ -65,7 +65,7 @@ __device__ __forceinline__ void stage_feature(const FeatArgs &A, const float *s_
     gi = A.rec_meta[s].x;
     if (gi < 0 || (int64_t)gi >= A.n) {
       gi = -1;
-      ca.y = 0.f;
+      ca.y = kLogAlphaNone;
     }
   }
   s_geom[k] = geom;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_kernel(F
   for (int k = 0; k < kFeatPPT; ++k) {
     const bool in = px < V.width && py0 + k < V.height;
     T[k] = in ? 1.0f : -1.0f;
-    pyc[k] = (float)(py0 + k) + 0.5f;
+    pyc[k] = in ? (float)(py0 + k) + 0.5f : stopped_row();
 #pragma unroll
     for (int c = 0; c < D; ++c) F[k][c] = 0.f;
     live = live || in;
@@ -138,15 +138,16 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_kernel(F
     for (int j = 0; j < nb && live; ++j) {
       const float4 geom = s_geom[j];
       const float2 ca = s_ca[j];
-      const ColumnTerms ct = column_terms(geom, pxc);
+      const ColumnTerms ct = column_terms(geom, pxc, ca.y);
 #pragma unroll
       for (int k = 0; k < kFeatPPT; ++k) {
-        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, ca.y, pyc[k]);
-        if (T[k] > 0.0f && e.alpha >= kAlphaMin) {
+        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, pyc[k]);
+        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
           const float Tn = __fsub_rn(T[k], w);
           if (Tn < kTMin) {
             T[k] = -T[k];
+            pyc[k] = stopped_row();
           } else {
 #pragma unroll
             for (int c = 0; c < D; ++c) F[k][c] = __fmaf_rn(s_fhat[j * (D + 1) + c], w, F[k][c]);
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
   for (int k = 0; k < kFeatPPT; ++k) {
     const bool in = px < V.width && py0 + k < V.height;
     T[k] = in ? 1.0f : -1.0f;
-    pyc[k] = (float)(py0 + k) + 0.5f;
+    pyc[k] = in ? (float)(py0 + k) + 0.5f : stopped_row();
     const int64_t p = (int64_t)(py0 + k) * V.width + px;
 #pragma unroll
     for (int c = 0; c < D; ++c) G[k][c] = in ? dF[c * HW + p] : 0.f;
@@ -236,19 +237,20 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
       if (!__any_sync(0xffffffffu, live)) break;  // the warp's pixels have all stopped
       const float4 geom = s_geom[j];
       const float2 ca = s_ca[j];
-      const ColumnTerms ct = column_terms(geom, pxc);
+      const ColumnTerms ct = column_terms(geom, pxc, ca.y);
       float v[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) v[c] = 0.f;
       bool contrib = false;
 #pragma unroll
       for (int k = 0; k < kFeatPPT; ++k) {
-        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, ca.y, pyc[k]);
-        if (T[k] > 0.0f && e.alpha >= kAlphaMin) {
+        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, pyc[k]);
+        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
           const float Tn = __fsub_rn(T[k], w);
           if (Tn < kTMin) {
             T[k] = -T[k];
+            pyc[k] = stopped_row();
           } else {
             contrib = true;
 #pragma unroll

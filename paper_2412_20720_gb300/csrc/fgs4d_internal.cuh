@@ -15,8 +15,10 @@ constexpr int kPreBlock = 256;      // threads per preprocess block
 constexpr int kEmitBlock = 256;     // threads per pair-scan / emission block
 constexpr int kEmitChunk = 2048;    // (slot, rect tile) pairs per emission chunk
 constexpr int kSortThreads = 256;   // threads per radix block
-constexpr int kSortItems = 8;       // keys per thread per radix block
+constexpr int kSortItems = 8;       // keys per thread per radix block (instance sort)
 constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kDepthSortItems = 4;  // keys per thread per radix block of the depth sort
+constexpr int kDepthSortTile = kSortThreads * kDepthSortItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;
@@ -298,7 +300,9 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *s
 // and backward kernels so both take identical skip/stop decisions.  The
 // exponent in base 2 is power2 = -q with q = A' dx^2 + B' dx dy + C' dy^2,
 // evaluated as A' dx^2 + dy (B' dx + C' dy) so that a thread covering a
-// column of pixels computes the dx terms once per entry.
+// column of pixels computes the dx terms once per entry.  The record holds
+// la = log2 a instead of the opacity a, and la is folded into the dx term:
+// a 2^-q = 2^-(q - la), one exponential and no product per pixel.
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -306,32 +310,46 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 struct ColumnTerms {
-  float dx, adx2, bdx;
+  float dx, adx2, bdx;  // adx2 = A' dx^2 - la
 };
 
-__device__ __forceinline__ ColumnTerms column_terms(float4 geom, float pxc) {
+__device__ __forceinline__ ColumnTerms column_terms(float4 geom, float pxc, float la) {
   ColumnTerms c;
   c.dx = __fsub_rn(geom.x, pxc);
-  c.adx2 = __fmul_rn(geom.z, __fmul_rn(c.dx, c.dx));
+  c.adx2 = __fmaf_rn(geom.z, __fmul_rn(c.dx, c.dx), -la);
   c.bdx = __fmul_rn(geom.w, c.dx);
   return c;
 }
 
 struct AlphaEval {
-  float dy, q, G, aG, alpha;
+  float dy, aG, alpha;  // aG = a 2^-q before the 0.99 clamp
 };
 
-__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float C2, float a, float pyc) {
+// min(x, y) that returns NaN when either operand is NaN (fminf returns the
+// other operand), so a NaN alpha fails every "alpha >= 1/255" test.
+__device__ __forceinline__ float min_nan(float x, float y) {
+  float r;
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(y));
+  return r;
+}
+
+// A pixel that has stopped (or lies outside the image) is given the row
+// centre +inf: dy = -inf makes q = +inf (or NaN when C' = 0), so alpha is 0
+// (or NaN) and fails the 1/255 test without a separate per-pixel flag test.
+__device__ __forceinline__ float stopped_row() { return __int_as_float(0x7f800000); }
+
+__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float C2, float pyc) {
   AlphaEval e;
   e.dy = __fsub_rn(v, pyc);
-  e.q = __fmaf_rn(e.dy, __fmaf_rn(C2, e.dy, c.bdx), c.adx2);
-  e.G = ex2_approx(-e.q);
-  e.aG = __fmul_rn(a, e.G);
-  e.alpha = fminf(0.99f, e.aG);
+  e.aG = ex2_approx(-__fmaf_rn(e.dy, __fmaf_rn(C2, e.dy, c.bdx), c.adx2));
+  e.alpha = min_nan(0.99f, e.aG);
   return e;
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;
+// log2 a of a staged entry that no pixel may take: alpha <= 2^-100, and
+// 2^100 (the 1/a of the backward) stays finite.
+constexpr float kLogAlphaNone = -100.0f;
 constexpr float kTauMargin = 4e-3f;  // log2 units (0.3% in alpha)
 constexpr float kTMin = 1e-4f;
 constexpr float kLog2e = 1.4426950408889634f;

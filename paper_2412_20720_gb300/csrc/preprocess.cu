@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kPreBlock) preprocess_kernel(PreArgs A, PreVie
   if (slot >= (uint64_t)A.vis_cap) return;
   // Conic in base-2 exponent form: power2 = -(A' dx^2 + B' dx dy + C' dy^2).
   A.rec_geom[slot] = make_float4(h.uv[0], h.uv[1], 0.5f * kLog2e * h.conA, kLog2e * h.conB);
-  A.rec_color[slot] = make_float4(0.5f * kLog2e * h.conC, h.a, h.rgb[0], h.rgb[1]);
+  A.rec_color[slot] = make_float4(0.5f * kLog2e * h.conC, log2f(h.a), h.rgb[0], h.rgb[1]);
   A.rec_blue[slot] = h.rgb[2];
   // alpha = a 2^power2 >= 1/255 needs -power2 <= log2(255 a); the margin keeps
   // the per-tile test of the instance emission conservative under rounding.

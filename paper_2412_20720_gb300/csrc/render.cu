@@ -30,7 +30,7 @@ namespace {
 struct RenderArgs {
   const uint2 *ranges;
   const uint32_t *inst_val;
-  const float4 *rec_geom, *rec_color;
+  const float4 *rec_geom, *rec_color;  // rec_color: (C', log2 a, r, g)
   const float *rec_blue;
   const float4 *rec_aux;  // auxiliary mode only
   uint32_t vis_cap;
@@ -87,7 +87,7 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
         if (s_aux) s_aux[k] = rec_aux[s];
       } else {
         s_geom[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s_col[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        s_col[k] = make_float4(0.f, kLogAlphaNone, 0.f, 0.f);
         s_blue[k] = 0.f;
         if (s_aux) s_aux[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -100,9 +100,10 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
 // algorithmic work); 2 (kAux): also blends the per-slot depth and flow with
 // the colour weights and writes depth, opacity 1 - T and flow planes.
 // A pixel that has stopped is marked by a negative T (its final transmittance
-// negated; a live pixel always has T >= 1e-4), so the inner loop carries no
-// separate flag.  The update stays a branch: whole warps skip it for entries
-// that miss all their pixels.
+// negated; a live pixel always has T >= 1e-4) and by the row centre +inf,
+// which makes every later alpha fail the 1/255 test, so the inner loop tests
+// no flag.  The update stays a branch: whole warps skip it for entries that
+// miss all their pixels.
 template <int MAXV, int TILE, int PPT, int kMode, int kBatch>
 __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
                                                                       unsigned long long *stats) {
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs
     C0[k] = C1[k] = C2[k] = 0.f;
     if (kAux) X0[k] = X1[k] = X2[k] = 0.f;
     last[k] = 0u;
-    pyc[k] = (float)(py0 + k) + 0.5f;
+    pyc[k] = in ? (float)(py0 + k) + 0.5f : stopped_row();
     nlive += in;
   }
   uint32_t n_eval = 0u, n_comp = 0u;
@@ -147,16 +148,17 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs
       const float4 geom = s_geom[j];
       const float4 col = s_col[j];
       const float blue = s_blue[j];
-      const ColumnTerms ct = column_terms(geom, pxc);
+      const ColumnTerms ct = column_terms(geom, pxc, col.y);
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, col.y, pyc[k]);
+        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, pyc[k]);
         if (kStats) n_eval += T[k] > 0.0f;
-        if (T[k] > 0.0f && e.alpha >= kAlphaMin) {
+        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
           const float Tn = __fsub_rn(T[k], w);
           if (Tn < kTMin) {
             T[k] = -T[k];
+            pyc[k] = stopped_row();
             --nlive;
           } else {
             C0[k] = __fmaf_rn(col.z, w, C0[k]);
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
       const float4 geom = s_geom[j];
       const float4 col = s_col[j];
       const float blue = s_blue[j];
-      const ColumnTerms ct = column_terms(geom, pxc);
+      const ColumnTerms ct = column_terms(geom, pxc, col.y);
       const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
       // The conic and centre gradients of the strip share dx: accumulate the
       // moments S0 = sum gp, S1 = sum gp dy, S2 = sum gp dy^2 of
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
         if (pos >= last[k]) continue;
-        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, col.y, pyc[k]);
+        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, pyc[k]);
         if (e.alpha < kAlphaMin) continue;
         contrib = true;
         const float io = rcp_approx(__fsub_rn(1.0f, e.alpha));
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
         const float g_alpha = T[k] * Dc - io * Dr[k];
         Dr[k] += w * Dc;
         if (!(e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
-          ga += g_alpha * e.G;
+          ga += g_alpha * e.aG;  // times 1/a below: d alpha / d a = 2^-q
           const float gp = g_alpha * e.alpha;  // d alpha / d (natural-log power)
           const float gpy = gp * e.dy;
           S0 += gp;
@@ -359,6 +361,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
         }
       }
       const float dx = ct.dx;
+      ga *= ex2_approx(-col.y);
       // g = (du, dv, dA', dB', dC', da, dr, dg), plus db.
       float g[8] = {-(An * dx * S0 + Bn * S1), -(Cn * S1 + Bn * dx * S0), -0.5f * dx * dx * S0, -dx * S1,
                     -0.5f * S2, ga, gr, gg};

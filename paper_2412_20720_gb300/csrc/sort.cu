@@ -32,8 +32,9 @@ constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = kFlagAgg - 1u;
 
 // Digit histograms of keys [0, count) for `passes` 8-bit digits starting at
-// bit 0, grid-stride over radix tiles (kSortTile keys); also clears each
-// tile's look-back rows and the tile ranges.
+// bit 0, grid-stride over radix tiles (kSortThreads x kItems keys); also
+// clears each tile's look-back rows and the tile ranges.
+template <int kItems>
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t *__restrict__ keys,
                                                                   const uint32_t *__restrict__ count_ptr, int64_t cap,
                                                                   int32_t passes, uint32_t *hist, uint32_t *state,
@@ -44,15 +45,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nranges; r += (int64_t)gridDim.x * blockDim.x)
     ranges[r] = make_uint2(0u, 0u);
   const int64_t count = min64((int64_t)*count_ptr, cap);
-  if ((int64_t)blockIdx.x * kSortTile >= count) return;
+  constexpr int kTileKeys = kSortThreads * kItems;
+  if ((int64_t)blockIdx.x * kTileKeys >= count) return;
   for (int p = 0; p < passes; ++p) s_hist[p][threadIdx.x] = 0u;
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
-  for (int64_t ob = blockIdx.x; ob * kSortTile < count && ob < state_blocks; ob += gridDim.x) {
+  for (int64_t ob = blockIdx.x; ob * kTileKeys < count && ob < state_blocks; ob += gridDim.x) {
     for (int p = 0; p < passes; ++p) state[((int64_t)p * state_blocks + ob) * kRadixBins + threadIdx.x] = 0u;
 #pragma unroll 2
-    for (int i = 0; i < kSortTile / kSortThreads; ++i) {
-      const int64_t idx = ob * kSortTile + i * kSortThreads + threadIdx.x;
+    for (int i = 0; i < kItems; ++i) {
+      const int64_t idx = ob * kTileKeys + i * kSortThreads + threadIdx.x;
       const bool valid = idx < count;
       const uint32_t k = valid ? keys[idx] : 0u;
       for (int p = 0; p < passes; ++p) {
@@ -75,7 +77,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t
   }
 }
 
-template <bool kValsAreIndex>
+// One stable 8-bit LSD pass over radix tiles of kSortThreads x kItems keys.
+// Small sorts (the depth sort of the visible slots) take short tiles, so
+// that more SMs share a pass; the instance sort takes long ones.
+template <bool kValsAreIndex, int kItems>
 __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ count_ptr, int64_t cap, int32_t shift,
@@ -86,8 +91,9 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
   __shared__ uint32_t s_bstart[kRadixBins];
   __shared__ uint32_t s_gstart[kRadixBins];
   __shared__ uint32_t s_scan[9];
-  __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
+  constexpr int kTileKeys = kSortThreads * kItems;
+  __shared__ uint32_t s_keys[kTileKeys];
+  __shared__ uint32_t s_vals[kTileKeys];
 
   const int64_t count = min64((int64_t)*count_ptr, cap);
   // Persistent: tiles are taken by ticket, so a tile's look-back only waits
@@ -97,16 +103,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
   for (int d = threadIdx.x; d < (kSortThreads / 32) * kRadixBins; d += kSortThreads) (&s_wcount[0][0])[d] = 0u;
   __syncthreads();
   const int64_t b = s_ticket;
-  const int64_t tile0 = b * kSortTile;
+  const int64_t tile0 = b * kTileKeys;
   if (tile0 >= count) return;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
-  int dig[kSortItems];
+  uint32_t key[kItems], val[kItems], rank[kItems];
+  int dig[kItems];
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const int64_t idx = tile0 + warp * (32 * kSortItems) + k * 32 + lane;
+  for (int k = 0; k < kItems; ++k) {
+    const int64_t idx = tile0 + warp * (32 * kItems) + k * 32 + lane;
     if (idx < count) {
       key[k] = keys_in[idx];
       val[k] = kValsAreIndex ? (uint32_t)idx : vals_in[idx];
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
   }
   // Stable rank within the warp's contiguous segment (item-major, lane-minor).
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
+  for (int k = 0; k < kItems; ++k) {
     const int d = dig[k];
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0u;
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
   __syncthreads();
   // Block-local order through shared memory, then coalesced runs per digit.
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
+  for (int k = 0; k < kItems; ++k) {
     if (dig[k] < kRadixBins) {
       const uint32_t pos = s_bstart[dig[k]] + s_wcount[warp][dig[k]] + rank[k];
       s_keys[pos] = key[k];
@@ -191,7 +197,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     }
   }
   __syncthreads();
-  const int32_t nvalid = (int32_t)min64(kSortTile, count - tile0);
+  const int32_t nvalid = (int32_t)min64(kTileKeys, count - tile0);
   for (int p = threadIdx.x; p < nvalid; p += kSortThreads) {
     const uint32_t kk = s_keys[p];
     const int dd = (kk >> shift) & (kRadixBins - 1);
@@ -636,9 +642,9 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   uint32_t *dstate = reinterpret_cast<uint32_t *>(ws + L.depth_state);
   uint32_t *hist_d = reinterpret_cast<uint32_t *>(ws + L.hist_depth);
   if (L.depth_blocks > 0) {
-    const int hb = (int)std::min<int64_t>((L.vis_cap + kSortTile - 1) / kSortTile, kPersistBlocks);
+    const int hb = std::min(L.depth_blocks, kPersistBlocks);
     const int pb = std::min(L.depth_blocks, kPersistBlocks);
-    e = launch_pdl(radix_hist_kernel, (unsigned)hb, kSortThreads, st, dkey, (const uint32_t *)(ctr + kCtrVisible),
+    e = launch_pdl(radix_hist_kernel<kDepthSortItems>, (unsigned)hb, kSortThreads, st, dkey, (const uint32_t *)(ctr + kCtrVisible),
                    (int64_t)L.vis_cap, (int32_t)L.depth_passes, hist_d, dstate, (int32_t)L.depth_blocks,
                    (uint2 *)nullptr, (int64_t)0);
     if (e != cudaSuccess) return e;
@@ -647,7 +653,8 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
       uint32_t *state = dstate + (size_t)p * L.depth_blocks * kRadixBins;
       const uint32_t *kin = p == 0 ? dkey : dk[in];
       const uint32_t *vin = p == 0 ? nullptr : dv[in];
-      e = launch_pdl(p == 0 ? radix_pass_kernel<true> : radix_pass_kernel<false>, (unsigned)pb, kSortThreads, st,
+      e = launch_pdl(p == 0 ? radix_pass_kernel<true, kDepthSortItems> : radix_pass_kernel<false, kDepthSortItems>,
+                     (unsigned)pb, kSortThreads, st,
                      kin, vin, dk[out], dv[out], (const uint32_t *)(ctr + kCtrVisible), (int64_t)L.vis_cap,
                      (int32_t)(kRadixBits * p), (const uint32_t *)(hist_d + p * kRadixBins), state,
                      ctr + kCtrTicketDepth + p, status);
@@ -705,7 +712,7 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   for (int p = 0; p < L.tile_passes; ++p) {
     const int in = p & 1, out = in ^ 1;
     uint32_t *state = tstate + (size_t)p * L.tile_blocks * kRadixBins;
-    e = launch_pdl(radix_pass_kernel<false>, (unsigned)pbt, kSortThreads, st, (const uint32_t *)ik[in],
+    e = launch_pdl(radix_pass_kernel<false, kSortItems>, (unsigned)pbt, kSortThreads, st, (const uint32_t *)ik[in],
                    (const uint32_t *)iv[in], ik[out], iv[out], (const uint32_t *)(ctr + kCtrInstances),
                    (int64_t)L.inst_cap, (int32_t)(kRadixBits * p), (const uint32_t *)(hist_t + p * kRadixBins), state,
                    ctr + kCtrTicketTile + p, status);
@@ -797,7 +804,7 @@ extern "C" int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, ui
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int blocks = (int)((n + kSortTile - 1) / kSortTile);
   static_sort_init_kernel<<<1, 256, 0, st>>>(s, (uint32_t)n);
-  radix_hist_kernel<<<blocks, kSortThreads, 0, st>>>(depth_keys, &s->ctl[0], FGS4D_STATIC_SORT_MAX,
+  radix_hist_kernel<kSortItems><<<blocks, kSortThreads, 0, st>>>(depth_keys, &s->ctl[0], FGS4D_STATIC_SORT_MAX,
                                                           kMaxPasses, &s->hist[0][0], &s->state[0][0][0],
                                                           kStaticSortBlocks, nullptr, 0);
   for (int p = 0; p < kMaxPasses; ++p) {
@@ -805,11 +812,11 @@ extern "C" int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, ui
     const uint32_t *kin = p == 0 ? depth_keys : s->keys[in];
     uint32_t *vout = p == kMaxPasses - 1 ? sorted_slots : s->vals[out];
     if (p == 0)
-      radix_pass_kernel<true><<<blocks, kSortThreads, 0, st>>>(kin, nullptr, s->keys[out], vout, &s->ctl[0],
+      radix_pass_kernel<true, kSortItems><<<blocks, kSortThreads, 0, st>>>(kin, nullptr, s->keys[out], vout, &s->ctl[0],
                                                                FGS4D_STATIC_SORT_MAX, kRadixBits * p, s->hist[p],
                                                                &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1]);
     else
-      radix_pass_kernel<false><<<blocks, kSortThreads, 0, st>>>(kin, s->vals[in], s->keys[out], vout, &s->ctl[0],
+      radix_pass_kernel<false, kSortItems><<<blocks, kSortThreads, 0, st>>>(kin, s->vals[in], s->keys[out], vout, &s->ctl[0],
                                                                 FGS4D_STATIC_SORT_MAX, kRadixBits * p, s->hist[p],
                                                                 &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1]);
   }

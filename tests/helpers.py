@@ -108,7 +108,7 @@ def records_from_gpu(run: GpuRun):
     rect = np.stack([run.meta[:, 2] & 0xFFFF, run.meta[:, 2] >> 16, run.meta[:, 3] & 0xFFFF, run.meta[:, 3] >> 16],
                     axis=1)
     rgb = np.stack([c[:, 2], c[:, 3], run.blue.astype(np.float64)], axis=1)
-    return {"index": run.meta[:, 0], "view": run.meta[:, 1], "uv": g[:, :2], "conic": conic, "a": c[:, 1],
+    return {"index": run.meta[:, 0], "view": run.meta[:, 1], "uv": g[:, :2], "conic": conic, "a": np.exp2(c[:, 1]),
             "rgb": rgb, "rect": rect, "depth_bits": run.depth_bits, "tau": run.tau.astype(np.float64)}
 
 

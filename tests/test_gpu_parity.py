@@ -249,7 +249,7 @@ def _write_records(r, rec, view_of_slot):
     geom = np.concatenate([rec["uv"], rec["conic2"][:, :2]], axis=1).astype(np.float32)
     color = np.zeros((n, 4), dtype=np.float32)
     color[:, 0] = rec["conic2"][:, 2]
-    color[:, 1] = 0.5
+    color[:, 1] = -1.0  # log2 of the opacity 0.5
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
     r.workspace_view(r.layout.counters, torch.int32, 64).zero_()
     r.workspace_view(r.layout.counters, torch.int32, 1).fill_(n)

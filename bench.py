@@ -231,8 +231,8 @@ def run_ours(args, rank, world, local):
     lay = r.layout
     tile_passes = max(1, ((int(lay.total_tiles) - 1).bit_length() + 7) // 8)
     # preprocess; bin_sort: depth histogram, 4 depth passes, pair scan,
-    # emission count / chunk scan / write, the tile passes, ranges; render.
-    launches_per_frame = 1 + (1 + 4 + 1 + 3 + tile_passes + 1) + 1
+    # emission, the tile passes, ranges; render.
+    launches_per_frame = 1 + (1 + 4 + 1 + 1 + tile_passes + 1) + 1
 
     def frame(k, ev=None, out=None):
         v, n1 = vv[k]

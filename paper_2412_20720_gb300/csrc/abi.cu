@@ -117,7 +117,7 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.chunk_cap = (int32_t)((L.pair_cap + kEmitChunk - 1) / kEmitChunk);
   L.emit_grid = std::max(1, std::min(L.chunk_cap, 152 * 8));
   L.depth_blocks = (int32_t)((L.vis_cap + kDepthSortTile - 1) / kDepthSortTile);
-  L.tile_blocks = (int32_t)((L.inst_cap + kSortTile - 1) / kSortTile);
+  L.tile_blocks = (int32_t)((L.inst_cap + kInstSortTile - 1) / kInstSortTile);
 
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -131,8 +131,7 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.hist_tile = take(kMaxPasses * kRadixBins * sizeof(uint32_t));
   L.lb_emit = take((size_t)L.emit_blocks * sizeof(uint64_t));
   L.control_end = off;
-  L.chunk_count = take((size_t)L.chunk_cap * sizeof(uint32_t));
-  L.pair_mask = take((size_t)L.chunk_cap * kEmitBlock);
+  L.lb_chunk = take((size_t)L.chunk_cap * sizeof(uint64_t));
   L.pair_prefix = take(((size_t)L.vis_cap + 1) * sizeof(uint32_t));
   L.emit_rec = take((size_t)L.vis_cap * 48);
   L.rec_aux = take((size_t)L.vis_cap * sizeof(float4));

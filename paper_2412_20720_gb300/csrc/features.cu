@@ -139,9 +139,10 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_kernel(F
       const float4 geom = s_geom[j];
       const float2 ca = s_ca[j];
       const ColumnTerms ct = column_terms(geom, pxc, ca.y);
+      const bool clamp = entry_clamps(ca.y);
 #pragma unroll
       for (int k = 0; k < kFeatPPT; ++k) {
-        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, pyc[k]);
+        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, pyc[k], clamp);
         if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
           const float Tn = __fsub_rn(T[k], w);
@@ -238,13 +239,14 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
       const float4 geom = s_geom[j];
       const float2 ca = s_ca[j];
       const ColumnTerms ct = column_terms(geom, pxc, ca.y);
+      const bool clamp = entry_clamps(ca.y);
       float v[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) v[c] = 0.f;
       bool contrib = false;
 #pragma unroll
       for (int k = 0; k < kFeatPPT; ++k) {
-        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, pyc[k]);
+        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, pyc[k], clamp);
         if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
           const float Tn = __fsub_rn(T[k], w);

@@ -19,6 +19,8 @@ constexpr int kSortItems = 8;       // keys per thread per radix block (instance
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kDepthSortItems = 4;  // keys per thread per radix block of the depth sort
 constexpr int kDepthSortTile = kSortThreads * kDepthSortItems;
+constexpr int kInstSortItems = 8;   // keys per thread per radix block of the instance (tile-id) sort
+constexpr int kInstSortTile = kSortThreads * kInstSortItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;
@@ -44,6 +46,7 @@ enum Counter : int {
   kCtrTicketPre = 5,
   // bytes [0, 32) are reset by preprocess only; the rest by bin_sort as well
   kCtrTicketEmit = 8,
+  kCtrTicketChunk = 9,
   kCtrTicketDepth = 10,  // kMaxPasses entries
   kCtrTicketTile = 14,   // kMaxPasses entries
   kCtrPairs = 19,        // (slot, rect tile) pairs of all visible slots
@@ -89,8 +92,7 @@ struct Layout {
   size_t hist_depth;    // uint32 [kMaxPasses][256]
   size_t hist_tile;     // uint32 [kMaxPasses][256]
   size_t lb_emit;       // uint64 per pair-scan block
-  size_t chunk_count;   // uint32 per emission chunk: kept pairs, then their exclusive prefix
-  size_t pair_mask;     // uint8 [chunk_cap][kEmitBlock]: keep bits of 8 consecutive pairs
+  size_t lb_chunk;      // uint64 per emission chunk: look-back state (cleared by the pair scan)
   size_t pair_prefix;   // uint32 [vis_cap + 1]: exclusive prefix of rect areas in depth order
   size_t emit_rec;      // 3 x 16 B [vis_cap]: emission record per depth-sorted position
   size_t rec_aux;       // float4 [vis_cap]: (camera depth, flow_u, flow_v, 0) per slot (auxiliary render)
@@ -338,12 +340,25 @@ __device__ __forceinline__ float min_nan(float x, float y) {
 // (or NaN) and fails the 1/255 test without a separate per-pixel flag test.
 __device__ __forceinline__ float stopped_row() { return __int_as_float(0x7f800000); }
 
+// alpha = min(0.99, a 2^-q).  The clamp can only act for a > 0.98: with
+// q >= 0 (a positive definite form, up to rounding) a 2^-q stays below 0.99
+// otherwise.  Every compositor decides per entry with entry_clamps() and
+// evaluates pixel_alpha<false> for the entries that cannot clamp, so the
+// forward, backward and feature passes take the same alpha bit for bit.
+constexpr float kLog2NoClamp = -0.0291463f;  // log2(0.98)
+__device__ __forceinline__ bool entry_clamps(float la) { return la > kLog2NoClamp; }
+
+template <bool kClamp>
 __device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float C2, float pyc) {
   AlphaEval e;
   e.dy = __fsub_rn(v, pyc);
   e.aG = ex2_approx(-__fmaf_rn(e.dy, __fmaf_rn(C2, e.dy, c.bdx), c.adx2));
-  e.alpha = min_nan(0.99f, e.aG);
+  e.alpha = kClamp ? min_nan(0.99f, e.aG) : e.aG;
   return e;
+}
+
+__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float C2, float pyc, bool clamp) {
+  return clamp ? pixel_alpha<true>(c, v, C2, pyc) : pixel_alpha<false>(c, v, C2, pyc);
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;

@@ -19,6 +19,7 @@
 // then reduced across the warp by shuffles and added with one vector atomic
 // per warp and entry.
 #include <algorithm>
+#include <type_traits>
 
 #include "fgs4d_internal.cuh"
 
@@ -149,33 +150,38 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs
       const float4 col = s_col[j];
       const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc, col.y);
+      // One copy of the pixel loop per clamp case, chosen once per entry.
+      auto pixels = [&](auto clamp_tag) {
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, pyc[k]);
-        if (kStats) n_eval += T[k] > 0.0f;
-        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
-          const float w = __fmul_rn(e.alpha, T[k]);
-          const float Tn = __fsub_rn(T[k], w);
-          if (Tn < kTMin) {
-            T[k] = -T[k];
-            pyc[k] = stopped_row();
-            --nlive;
-          } else {
-            C0[k] = __fmaf_rn(col.z, w, C0[k]);
-            C1[k] = __fmaf_rn(col.w, w, C1[k]);
-            C2[k] = __fmaf_rn(blue, w, C2[k]);
-            if (kAux) {
-              const float4 x = s_aux[j];
-              X0[k] = __fmaf_rn(x.x, w, X0[k]);
-              X1[k] = __fmaf_rn(x.y, w, X1[k]);
-              X2[k] = __fmaf_rn(x.z, w, X2[k]);
+        for (int k = 0; k < PPT; ++k) {
+          const AlphaEval e = pixel_alpha<decltype(clamp_tag)::value>(ct, geom.y, col.x, pyc[k]);
+          if (kStats) n_eval += T[k] > 0.0f;
+          if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
+            const float w = __fmul_rn(e.alpha, T[k]);
+            const float Tn = __fsub_rn(T[k], w);
+            if (Tn < kTMin) {
+              T[k] = -T[k];
+              pyc[k] = stopped_row();
+              --nlive;
+            } else {
+              C0[k] = __fmaf_rn(col.z, w, C0[k]);
+              C1[k] = __fmaf_rn(col.w, w, C1[k]);
+              C2[k] = __fmaf_rn(blue, w, C2[k]);
+              if (kAux) {
+                const float4 x = s_aux[j];
+                X0[k] = __fmaf_rn(x.x, w, X0[k]);
+                X1[k] = __fmaf_rn(x.y, w, X1[k]);
+                X2[k] = __fmaf_rn(x.z, w, X2[k]);
+              }
+              T[k] = Tn;
+              last[k] = pos0 + (uint32_t)j;
+              if (kStats) ++n_comp;
             }
-            T[k] = Tn;
-            last[k] = pos0 + (uint32_t)j;
-            if (kStats) ++n_comp;
           }
         }
-      }
+      };
+      if (entry_clamps(col.y)) pixels(std::true_type());
+      else pixels(std::false_type());
     }
   }
   if (kStats) {
@@ -325,6 +331,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
       const float4 col = s_col[j];
       const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc, col.y);
+      const bool clamp = entry_clamps(col.y);
       const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
       // The conic and centre gradients of the strip share dx: accumulate the
       // moments S0 = sum gp, S1 = sum gp dy, S2 = sum gp dy^2 of
@@ -335,7 +342,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
         if (pos >= last[k]) continue;
-        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, pyc[k]);
+        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, pyc[k], clamp);
         if (e.alpha < kAlphaMin) continue;
         contrib = true;
         const float io = rcp_approx(__fsub_rn(1.0f, e.alpha));
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
         }
         const float g_alpha = T[k] * Dc - io * Dr[k];
         Dr[k] += w * Dc;
-        if (!(e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
+        if (!(clamp && e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
           ga += g_alpha * e.aG;  // times 1/a below: d alpha / d a = 2^-q
           const float gp = g_alpha * e.alpha;  // d alpha / d (natural-log power)
           const float gpy = gp * e.dy;

@@ -262,9 +262,8 @@ struct EmitArgs {
   uint32_t *chunk_first;
   uint32_t *inst_key, *inst_val;
   uint64_t *lb_scan;
-  uint32_t *chunk_count;  // kept pairs per chunk, then (after the scan) their exclusive prefix
-  uint8_t *pair_mask;     // keep byte per (chunk, thread): 8 consecutive pairs
-  // Tile sort set-up done while counting: digit histograms, cleared look-back
+  uint64_t *lb_chunk;  // look-back state per emission chunk (cleared by the pair scan)
+  // Tile sort set-up done while emitting: digit histograms, cleared look-back
   // rows and tile ranges.
   int32_t tile_passes, tile_blocks;
   uint32_t *hist_tile, *tile_state;
@@ -363,19 +362,21 @@ __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, Raste
     const uint64_t p0 = umin64(s_base + excl, (uint64_t)A.pair_cap);
     const uint64_t p1 = umin64(s_base + excl + area, (uint64_t)A.pair_cap);
     A.pair_prefix[j] = (uint32_t)p0;
-    for (uint64_t c = (p0 + kEmitChunk - 1) / kEmitChunk; c * kEmitChunk < p1 && c < (uint64_t)A.chunk_cap; ++c)
+    for (uint64_t c = (p0 + kEmitChunk - 1) / kEmitChunk; c * kEmitChunk < p1 && c < (uint64_t)A.chunk_cap; ++c) {
       A.chunk_first[c] = (uint32_t)j;
+      A.lb_chunk[c] = 0ull;
+    }
   }
 }
 
 // Instance emission in depth order.  The (slot, rect tile) pairs of all
 // visible slots, in depth order and row-major within a rect, are cut into
 // chunks of kEmitChunk pairs; a pair is kept when its slot's 1/255 ellipse
-// meets the tile.  emit_count_kernel decides every pair (one keep bit) and
-// counts the kept pairs of every chunk, chunk_scan_kernel turns the counts
-// into output offsets, and emit_write_kernel writes the kept pairs in pair
-// order.  Every chunk is the same amount of work, so a screen-sized Gaussian
-// is spread over many blocks, and no block waits on another.
+// meets the tile.  emit_kernel takes chunks by ticket, decides every pair of
+// a chunk, gets the chunk's output offset by a decoupled look-back over the
+// chunks' kept counts, and writes the kept pairs in pair order.  Every chunk
+// is the same amount of work, so a screen-sized Gaussian is spread over many
+// blocks.
 
 constexpr int kEmitRecCache = 256;  // emission records cached per chunk
 
@@ -482,127 +483,101 @@ __device__ __forceinline__ uint32_t walk_tile(const RasterViews<MAXV> &rv, const
 }
 
 constexpr int kPairsPerThread = kEmitChunk / kEmitBlock;
+// Radix tiles of the instance sort whose look-back rows chunk c clears: the
+// instances never outnumber the pairs, so rows [0, nchunks x this) suffice.
+constexpr int kRadixTilesPerChunk = kEmitChunk / kInstSortTile;
+static_assert(kRadixTilesPerChunk * kInstSortTile == kEmitChunk, "chunk covers whole radix tiles");
 static_assert(kPairsPerThread == 8, "one keep byte per thread");
 
-// Pass 1: thread t of chunk c decides pairs c kEmitChunk + 8 t + [0, 8) and
-// stores them as one keep byte; the chunk's kept count goes to chunk_count.
-// Also clears the tile sort's look-back rows (radix tile c for chunk c: there
-// are no more instances than pairs) and the tile ranges.
+// Sets the instance total (clamped to the capacity) and its overflow flag.
+__device__ __forceinline__ void set_instance_total(const EmitArgs &A, uint64_t all) {
+  A.counters[kCtrInstances] = (uint32_t)umin64(all, (uint64_t)A.inst_cap);
+  // A pair overflow (flagged by the pair scan) already set the bound.
+  if (!(A.counters[kCtrStatus] & kStatusInstOverflow) || all > (uint64_t)A.inst_cap)
+    A.counters[kCtrNeedInstances] =
+        (uint32_t)umin64(max((uint64_t)A.counters[kCtrNeedInstances], all), 0xffffffffull);
+  if (all > (uint64_t)A.inst_cap) atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
+}
+
+// Thread t of chunk c decides pairs c kEmitChunk + 8 t + [0, 8) and keeps
+// the tile ids and slots of the kept ones in registers; a block scan and the
+// look-back over the chunks give their output positions.  Persistent: chunks
+// are taken by ticket, so a chunk's look-back only waits on chunks that
+// running blocks hold.  Also clears the tile sort's look-back rows of the
+// radix tiles covering chunk c's pairs (there are no more instances than
+// pairs) and the tile ranges, and takes the tile-id digit histograms.
 template <int MAXV>
-__global__ void __launch_bounds__(kEmitBlock) emit_count_kernel(EmitArgs A, RasterViews<MAXV> rv) {
+__global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
   __shared__ EmitChunkSmem S;
   __shared__ uint32_t s_scan[kEmitBlock / 32 + 1];
+  __shared__ uint32_t s_hist[kMaxPasses][kRadixBins];
+  __shared__ uint32_t s_ticket;
+  __shared__ uint64_t s_prefix;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < A.total_tiles;
        r += (int64_t)gridDim.x * blockDim.x)
     A.ranges[r] = make_uint2(0u, 0u);
   const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
   const uint32_t npairs = A.counters[kCtrPairs];
-  const uint32_t nchunks = (npairs + kEmitChunk - 1) / kEmitChunk;
-  for (uint32_t c = blockIdx.x; c < nchunks && (int32_t)c < A.chunk_cap; c += gridDim.x) {
-    if ((int32_t)c < A.tile_blocks)
-      for (int p = 0; p < A.tile_passes; ++p)
-        A.tile_state[((size_t)p * A.tile_blocks + c) * kRadixBins + threadIdx.x] = 0u;
+  const uint32_t nchunks = (uint32_t)min64((npairs + kEmitChunk - 1) / kEmitChunk, A.chunk_cap);
+  if (nchunks == 0u) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && nvis > 0) set_instance_total(A, 0ull);
+    return;
+  }
+  for (int p = 0; p < A.tile_passes; ++p) s_hist[p][threadIdx.x] = 0u;
+  while (true) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&A.counters[kCtrTicketChunk], 1u);
+    __syncthreads();
+    const uint32_t c = s_ticket;
+    if (c >= nchunks) break;
+    for (int r = 0; r < kRadixTilesPerChunk; ++r) {
+      const int64_t rt = (int64_t)c * kRadixTilesPerChunk + r;
+      if (rt < A.tile_blocks)
+        for (int p = 0; p < A.tile_passes; ++p)
+          A.tile_state[((size_t)p * A.tile_blocks + rt) * kRadixBins + threadIdx.x] = 0u;
+    }
     const uint32_t f0 = c * kEmitChunk, f1 = min(f0 + (uint32_t)kEmitChunk, npairs);
     load_emit_chunk(A, c, f1, npairs, nvis, S);
     const uint32_t fa = f0 + kPairsPerThread * threadIdx.x;
     uint32_t m = 0u;
+    uint32_t kt[kPairsPerThread], ks[kPairsPerThread];
     if (fa < f1) {
-      PairWalk w = walk_begin(A, S, fa);
-      m = walk_keep<MAXV>(rv, w) ? 1u : 0u;
-#pragma unroll
-      for (int k = 1; k < kPairsPerThread; ++k) {
-        if (fa + k >= f1) break;
-        walk_next(A, S, w, fa + k);
-        m |= walk_keep<MAXV>(rv, w) ? (1u << k) : 0u;
-      }
-    }
-    A.pair_mask[(size_t)c * kEmitBlock + threadIdx.x] = (uint8_t)m;
-    uint32_t total;
-    block_exclusive_scan(__popc(m), s_scan, &total);
-    if (threadIdx.x == 0) A.chunk_count[c] = total;
-    __syncthreads();  // S is reused by the next chunk
-  }
-}
-
-// Exclusive prefix of the chunk counts, in place, by one block; sets the
-// instance total and flags an instance-capacity overflow.
-constexpr int kChunkScanThreads = 1024;
-__global__ void __launch_bounds__(kChunkScanThreads) chunk_scan_kernel(EmitArgs A) {
-  grid_dependency_sync();
-  __shared__ uint32_t s_scan[kChunkScanThreads / 32 + 1];
-  const uint32_t npairs = A.counters[kCtrPairs];
-  const int64_t nchunks = min64((npairs + kEmitChunk - 1) / kEmitChunk, A.chunk_cap);
-  constexpr int kItems = 8;
-  uint64_t carry = 0;
-  for (int64_t base = 0; base < nchunks; base += (int64_t)kChunkScanThreads * kItems) {
-    uint32_t v[kItems];
-    uint32_t sum = 0u;
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      const int64_t idx = base + (int64_t)threadIdx.x * kItems + k;
-      v[k] = idx < nchunks ? A.chunk_count[idx] : 0u;
-      sum += v[k];
-    }
-    uint32_t total;
-    uint32_t run = block_exclusive_scan<kChunkScanThreads / 32>(sum, s_scan, &total);
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-      const int64_t idx = base + (int64_t)threadIdx.x * kItems + k;
-      if (idx < nchunks) A.chunk_count[idx] = (uint32_t)umin64(carry + run, 0xffffffffull);
-      run += v[k];
-    }
-    carry += total;
-  }
-  if (threadIdx.x == 0) {
-    A.counters[kCtrInstances] = (uint32_t)umin64(carry, (uint64_t)A.inst_cap);
-    if (!(A.counters[kCtrStatus] & kStatusInstOverflow) || carry > (uint64_t)A.inst_cap)
-      A.counters[kCtrNeedInstances] =
-          (uint32_t)umin64(max((uint64_t)A.counters[kCtrNeedInstances], carry), 0xffffffffull);
-    if (carry > (uint64_t)A.inst_cap) atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
-  }
-}
-
-// Pass 2: writes the kept pairs of each chunk at the chunk's offset in pair
-// order (the keep bytes give each thread its output position) and takes the
-// digit histograms of their tile ids for the tile sort.
-template <int MAXV>
-__global__ void __launch_bounds__(kEmitBlock) emit_write_kernel(EmitArgs A, RasterViews<MAXV> rv) {
-  grid_dependency_sync();
-  __shared__ EmitChunkSmem S;
-  __shared__ uint32_t s_scan[kEmitBlock / 32 + 1];
-  __shared__ uint32_t s_hist[kMaxPasses][kRadixBins];
-  const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
-  const uint32_t npairs = A.counters[kCtrPairs];
-  const uint32_t nchunks = (npairs + kEmitChunk - 1) / kEmitChunk;
-  if (blockIdx.x >= nchunks) return;
-  for (int p = 0; p < A.tile_passes; ++p) s_hist[p][threadIdx.x] = 0u;
-  for (uint32_t c = blockIdx.x; c < nchunks && (int32_t)c < A.chunk_cap; c += gridDim.x) {
-    const uint32_t f0 = c * kEmitChunk, f1 = min(f0 + (uint32_t)kEmitChunk, npairs);
-    load_emit_chunk(A, c, f1, npairs, nvis, S);  // its barriers also order s_hist's clearing
-    const uint32_t m = A.pair_mask[(size_t)c * kEmitBlock + threadIdx.x];
-    uint32_t total;
-    uint64_t pos = (uint64_t)A.chunk_count[c] + block_exclusive_scan(__popc(m), s_scan, &total);
-    if (m) {
-      const uint32_t fa = f0 + kPairsPerThread * threadIdx.x;
       PairWalk w = walk_begin(A, S, fa);
 #pragma unroll
       for (int k = 0; k < kPairsPerThread; ++k) {
-        if (k) walk_next(A, S, w, fa + k);
-        if (m & (1u << k)) {
-          const uint32_t tile = walk_tile<MAXV>(rv, w);
-          if (pos < (uint64_t)A.inst_cap) {
-            A.inst_key[pos] = tile;
-            A.inst_val[pos] = w.slot;
-          }
-          ++pos;
-          for (int p = 0; p < A.tile_passes; ++p)
-            atomicAdd(&s_hist[p][(tile >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
+        if (k) {
+          if (fa + k >= f1) break;
+          walk_next(A, S, w, fa + k);
         }
-        if ((m >> (k + 1)) == 0u) break;
+        m |= walk_keep<MAXV>(rv, w) ? (1u << k) : 0u;
+        kt[k] = walk_tile<MAXV>(rv, w);
+        ks[k] = w.slot;
       }
     }
-    __syncthreads();  // S is reused by the next chunk
+    uint32_t total;
+    const uint32_t local = block_exclusive_scan(__popc(m), s_scan, &total);
+    if (threadIdx.x < 32) {
+      const uint64_t prefix = lookback_u64_warp(A.lb_chunk, (int32_t)c, total, &A.counters[kCtrStatus]);
+      if (threadIdx.x == 0) {
+        s_prefix = prefix;
+        if (c == nchunks - 1u) set_instance_total(A, prefix + total);
+      }
+    }
+    __syncthreads();
+    uint64_t pos = s_prefix + local;
+#pragma unroll
+    for (int k = 0; k < kPairsPerThread; ++k) {
+      if (m & (1u << k)) {
+        if (pos < (uint64_t)A.inst_cap) {
+          A.inst_key[pos] = kt[k];
+          A.inst_val[pos] = ks[k];
+        }
+        ++pos;
+        for (int p = 0; p < A.tile_passes; ++p)
+          atomicAdd(&s_hist[p][(kt[k] >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
+      }
+    }
+    __syncthreads();  // S, s_ticket and s_prefix are reused by the next chunk
   }
   for (int p = 0; p < A.tile_passes; ++p) {
     const uint32_t h = s_hist[p][threadIdx.x];
@@ -689,8 +664,7 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
     ea.inst_key = ik[0];
     ea.inst_val = iv[0];
     ea.lb_scan = reinterpret_cast<uint64_t *>(ws + L.lb_emit);
-    ea.chunk_count = reinterpret_cast<uint32_t *>(ws + L.chunk_count);
-    ea.pair_mask = reinterpret_cast<uint8_t *>(ws + L.pair_mask);
+    ea.lb_chunk = reinterpret_cast<uint64_t *>(ws + L.lb_chunk);
     ea.tile_passes = L.tile_passes;
     ea.tile_blocks = L.tile_blocks;
     ea.hist_tile = hist_t;
@@ -699,20 +673,16 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
     ea.total_tiles = L.total_tiles;
     e = launch_pdl(pair_scan_kernel<MAXV>, (unsigned)L.emit_blocks, kEmitBlock, st, ea, rv);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(emit_count_kernel<MAXV>, (unsigned)L.emit_grid, kEmitBlock, st, ea, rv);
-    if (e != cudaSuccess) return e;
-    e = launch_pdl(chunk_scan_kernel, 1u, (unsigned)kChunkScanThreads, st, ea);
-    if (e != cudaSuccess) return e;
-    e = launch_pdl(emit_write_kernel<MAXV>, (unsigned)L.emit_grid, kEmitBlock, st, ea, rv);
+    e = launch_pdl(emit_kernel<MAXV>, (unsigned)L.emit_grid, kEmitBlock, st, ea, rv);
     if (e != cudaSuccess) return e;
   }
   // 3. Stable sort of the instances by global tile id (digit histograms
-  // taken by the emission count).
+  // taken by the emission).
   const int pbt = std::min(L.tile_blocks, kPersistBlocks);
   for (int p = 0; p < L.tile_passes; ++p) {
     const int in = p & 1, out = in ^ 1;
     uint32_t *state = tstate + (size_t)p * L.tile_blocks * kRadixBins;
-    e = launch_pdl(radix_pass_kernel<false, kSortItems>, (unsigned)pbt, kSortThreads, st, (const uint32_t *)ik[in],
+    e = launch_pdl(radix_pass_kernel<false, kInstSortItems>, (unsigned)pbt, kSortThreads, st, (const uint32_t *)ik[in],
                    (const uint32_t *)iv[in], ik[out], iv[out], (const uint32_t *)(ctr + kCtrInstances),
                    (int64_t)L.inst_cap, (int32_t)(kRadixBits * p), (const uint32_t *)(hist_t + p * kRadixBins), state,
                    ctr + kCtrTicketTile + p, status);

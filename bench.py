@@ -48,7 +48,7 @@ FLOPS_PER_COMP = 9
 # block shape, from the ncu launch list summarised in
 # profiles/launches_orbit_300k_1352x1014.md; emptied whenever the kernel changes.
 # keyed by (tile, pixels per thread, shared batch)
-RENDER_FWD_TRAFFIC = {(16, 2, 256): 7.655e6, (16, 4, 256): 7.648e6, (16, 8, 256): 7.382e6}
+RENDER_FWD_TRAFFIC = {(16, 2, 128): 7.657e6, (16, 2, 256): 7.660e6, (16, 4, 256): 7.193e6}
 
 
 def parse():

@@ -220,6 +220,9 @@ def run_ours(args, rank, world, local):
     cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24)
     r = Renderer(scene.n, views[:1], cfg, device=dev)
     vv = [fgs4d.make_views([v]) for v in views]
+    # Visible-pair capacity sized to the sweep's own views (largest count +
+    # 10%): the depth sort and pair scan size their grids by it.
+    vis_cap = r.fit_visible_capacity(params, view_sets=vv)
     tuned = autotune(r, params, view_sets=[vv[k] for k in sorted({0, nviews // 3, 2 * nviews // 3})],
                      tiles=(16, 8), batches=(256, 128))
     g = r.gaussians(params)
@@ -229,10 +232,8 @@ def run_ours(args, rank, world, local):
     npx = W_IMG * H_IMG
     img = torch.empty(3 * npx, dtype=torch.float32, device=dev)
     lay = r.layout
-    tile_passes = max(1, ((int(lay.total_tiles) - 1).bit_length() + 7) // 8)
-    # preprocess; bin_sort: depth histogram, 4 depth passes, pair scan,
-    # emission, the tile passes, ranges; render.
-    launches_per_frame = 1 + (1 + 4 + 1 + 1 + tile_passes + 1) + 1
+    # preprocess; bin_sort (as the library reports it); render.
+    launches_per_frame = 1 + fgs4d.bin_sort_kernels(scene.n, vv[0][0], vv[0][1], s) + 1
 
     def frame(k, ev=None, out=None):
         v, n1 = vv[k]
@@ -378,6 +379,7 @@ def run_ours(args, rank, world, local):
             "dtype": "f32", "data": "synthetic (seeded; shapes and distributions of the paper's workloads)",
             "config": {"workload": WORKLOAD, "gaussians": args.n, "sh_degree": 3, "t_order": 2,
                        "resolution": [W_IMG, H_IMG], "views_per_step": nviews, "views_per_call": 1,
+                       "vis_capacity": vis_cap,
                        "l2": "inputs larger than L2 (193 MB of parameters vs 129 MB L2); no flush",
                        "parallelism": "views replicated per GPU" if world > 1 else "single GPU"},
             "gpu_launches": launches_per_frame * nviews * K,

@@ -156,7 +156,8 @@ typedef struct fgs4d_layout {
   size_t sorted_slots;  /* uint32 [vis_cap]: slots in (depth, slot) order, after fgs4d_bin_sort */
   size_t inst_tile;     /* uint32 [inst_cap]: global tile id of each sorted instance */
   size_t inst_slot;     /* uint32 [inst_cap]: slot of each sorted instance */
-  size_t tile_ranges;   /* uint32x2 [total_tiles]: [start, end) into the instance list */
+  size_t tile_ranges;   /* uint32x2 [total_tiles]: [start, end) into the instance list; a tile
+                           without instances holds start >= end */
   size_t pix_T;         /* float  [total_pixels]: final transmittance */
   size_t pix_last;      /* uint32 [total_pixels]: list entries processed up to the last composited one */
   size_t slot_grad;     /* float  [vis_cap][12]: dL/d(u, v, A, B, C, a, r, g, b) per slot */
@@ -197,6 +198,13 @@ int fgs4d_preprocess(const fgs4d_gaussians *gaussians, const fgs4d_view *views, 
  * Device-detected: instance capacity. */
 int fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
                    void *workspace, size_t workspace_bytes, void *stream);
+
+/* Diagnostic: *count_out = the number of kernels fgs4d_bin_sort launches for
+ * these arguments (the count depends on the tile grid's size, which sets the
+ * number of tile-sort passes).  Launches nothing; has no counterpart in the
+ * paper. */
+int fgs4d_bin_sort_kernels(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                           int32_t *count_out);
 
 /* Front-to-back compositing per pixel (Sec. 3.2, Eq. 6) over its tile's
  * sorted list: alpha = min(0.99, a exp(power)), skip when alpha < 1/255,

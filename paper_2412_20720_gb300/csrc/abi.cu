@@ -236,6 +236,16 @@ int fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs
                                      static_cast<cudaStream_t>(stream)));
 }
 
+int fgs4d_bin_sort_kernels(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                           int32_t *count_out) {
+  if (!count_out) return FGS4D_ERR_ARG;
+  Layout L;
+  const int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  *count_out = bin_sort_kernel_count(L, nviews);
+  return FGS4D_OK;
+}
+
 int fgs4d_render_fwd(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
                      void *workspace, size_t workspace_bytes, float *out_rgb, float *out_T, void *stream) {
   Layout L;

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_kernel(F
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
   const int32_t px = tx * TILE + (threadIdx.x & (TILE - 1));
   const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * kFeatPPT;
-  const uint2 range = A.ranges[gt];
+  const uint2 range = tile_range(A.ranges, gt);
   const float pxc = (float)px + 0.5f;
   if (threadIdx.x < D) s_gate[threadIdx.x] = A.gate ? A.gate[threadIdx.x] : 1.0f;
   float T[kFeatPPT], pyc[kFeatPPT], F[kFeatPPT][D];
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
   const int32_t px = tx * TILE + (threadIdx.x & (TILE - 1));
   const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * kFeatPPT;
-  const uint2 range = A.ranges[gt];
+  const uint2 range = tile_range(A.ranges, gt);
   const float pxc = (float)px + 0.5f;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < D) {

@@ -377,6 +377,13 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
+// [start, end) of a tile's list; a tile without instances may hold any
+// start >= end (the sort writes (0xffffffff, 0)) and reads as (0, 0).
+__device__ __forceinline__ uint2 tile_range(const uint2 *ranges, int32_t gt) {
+  const uint2 r = ranges[gt];
+  return r.x < r.y ? r : make_uint2(0u, 0u);
+}
+
 // Global tile -> its view (binary search over the views' first tiles).
 template <int MAXV>
 __device__ __forceinline__ int find_view(const RasterViews<MAXV> &rv, int32_t gt) {
@@ -405,6 +412,8 @@ cudaError_t launch_preprocess_bwd(const PreLaunch &p, const fgs4d_view *views, i
                                   const fgs4d_gaussians_grad *grads);
 cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nviews, unsigned char *ws,
                             cudaStream_t stream);
+// Kernel launches launch_bin_sort makes for this layout on the current device.
+int bin_sort_kernel_count(const Layout &L, int32_t nviews);
 cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
                               float *out_aux, cudaStream_t stream);

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
   const int32_t px = tx * TILE + (threadIdx.x & (TILE - 1));
   const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * PPT;
-  const uint2 range = A.ranges[gt];
+  const uint2 range = tile_range(A.ranges, gt);
   const float pxc = (float)px + 0.5f;
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
   float X0[kAux ? PPT : 1], X1[kAux ? PPT : 1], X2[kAux ? PPT : 1];  // depth, flow_u, flow_v sums
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
   const int32_t px = tx * TILE + (threadIdx.x & (TILE - 1));
   const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * kPPT;
-  const uint2 range = A.ranges[gt];
+  const uint2 range = tile_range(A.ranges, gt);
   const float pxc = (float)px + 0.5f;
   const int64_t HW = (int64_t)V.width * V.height;
   // Dr[k] = sum over channels of dL/dX * (X composited behind the current

@@ -80,11 +80,21 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t
 // One stable 8-bit LSD pass over radix tiles of kSortThreads x kItems keys.
 // Small sorts (the depth sort of the visible slots) take short tiles, so
 // that more SMs share a pass; the instance sort takes long ones.
+//
+// With `ranges` (the last pass of the tile sort, keys = global tile ids
+// below total_tiles) the pass also records each tile's [start, end) in the
+// sorted list.  A radix tile's staged keys are ordered by the full key (the
+// pass input is ordered by the lower digits and the staging is stable), so
+// the equal keys of a radix tile form one run; its first and last output
+// positions go to atomicMin on start and atomicMax on end, which the
+// emission initialised to (0xffffffff, 0).  A tile with no instance keeps
+// start > end, which every reader takes as empty.
 template <bool kValsAreIndex, int kItems>
 __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ count_ptr, int64_t cap, int32_t shift,
-    const uint32_t *__restrict__ hist, uint32_t *state, uint32_t *ticket, uint32_t *status) {
+    const uint32_t *__restrict__ hist, uint32_t *state, uint32_t *ticket, uint32_t *status, uint2 *ranges,
+    int64_t total_tiles) {
   grid_dependency_sync();
   __shared__ uint32_t s_ticket;
   __shared__ uint32_t s_wcount[kSortThreads / 32][kRadixBins];
@@ -205,6 +215,15 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     if ((int64_t)gpos < count) {
       keys_out[gpos] = kk;
       vals_out[gpos] = s_vals[p];
+      if (ranges) {
+        if ((int64_t)kk < total_tiles) {
+          uint32_t *r = reinterpret_cast<uint32_t *>(&ranges[kk]);
+          if (p == 0 || s_keys[p - 1] != kk) atomicMin(&r[0], gpos);
+          if (p == nvalid - 1 || s_keys[p + 1] != kk) atomicMax(&r[1], gpos + 1u);
+        } else {
+          atomicOr(status, kStatusInternal);
+        }
+      }
     } else {
       atomicOr(status, kStatusInternal);
     }
@@ -271,11 +290,90 @@ struct EmitArgs {
   int64_t total_tiles;
 };
 
+// Emission record of depth-sorted position j holding slot s: (u, v, A', B'),
+// (C', kx, ky, tau), (slot, view, packed rect lo, packed rect hi); returns
+// the number of (slot, tile) pairs to enumerate for it.  Only tiles whose
+// pixel-centre box meets the 1/255 ellipse are kept, so the pairs are
+// enumerated over the rect cut to the ellipse's bounding box: half-extents
+// sqrt(tau C'/det), sqrt(tau A'/det) with det = A'C' - B'^2/4, widened by
+// 0.1% + 0.05 px against rounding (a box outside them is far outside the
+// ellipse, which the exact test of the emission rejects as well).  With tile
+// edge T, tile tx's centre box [T tx + 0.5, T tx + T - 0.5] can meet
+// [u - rx, u + rx] only for ceil((u - rx - T + 0.5) / T) <= tx <= floor((u + rx - 0.5) / T).
+template <int MAXV>
+__device__ __forceinline__ uint32_t pair_record(const EmitArgs &A, const RasterViews<MAXV> &rv, uint32_t s, int64_t j,
+                                                int64_t nvis) {
+  uint32_t area = 0u;
+  int4 mm = make_int4(0, 0, 0, 0);
+  float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+  float cc = 0.f, tau = -1.0f;
+  if ((int64_t)s < nvis) {
+    mm = A.meta[s];
+    g = A.geom[s];
+    cc = A.color[s].x;
+    tau = A.tau[s];
+    int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff, y1 = (uint32_t)mm.w >> 16;
+    const float det = g.z * cc - 0.25f * g.w * g.w;
+    if (tau < 0.0f) {
+      x1 = x0;
+    } else if (det > 0.0f) {
+      const RasterView &V = rv.v[MAXV == 1 ? 0 : min(max(mm.y, 0), rv.nviews - 1)];
+      const float T = (float)V.tile, iT = 1.0f / T;
+      const float rx = sqrtf(tau * cc / det) * 1.001f + 0.05f, ry = sqrtf(tau * g.z / det) * 1.001f + 0.05f;
+      const float lx = ceilf((g.x - rx - (T - 0.5f)) * iT), hx = floorf((g.x + rx - 0.5f) * iT);
+      const float ly = ceilf((g.y - ry - (T - 0.5f)) * iT), hy = floorf((g.y + ry - 0.5f) * iT);
+      if (lx > (float)x0) x0 = (int)fminf(lx, (float)x1);
+      if (hx + 1.0f < (float)x1) x1 = (int)fmaxf(hx + 1.0f, (float)x0);
+      if (ly > (float)y0) y0 = (int)fminf(ly, (float)y1);
+      if (hy + 1.0f < (float)y1) y1 = (int)fmaxf(hy + 1.0f, (float)y0);
+    }
+    area = (uint32_t)(max(x1 - x0, 0) * max(y1 - y0, 0));
+    mm.z = x0 | (y0 << 16);
+    mm.w = x1 | (y1 << 16);
+  } else {
+    atomicOr(&A.counters[kCtrStatus], kStatusInternal);
+  }
+  const float2 k = edge_slopes(g.z, g.w, cc);
+  A.emit_rec[3 * j + 0] = make_int4(__float_as_int(g.x), __float_as_int(g.y), __float_as_int(g.z),
+                                    __float_as_int(g.w));
+  A.emit_rec[3 * j + 1] = make_int4(__float_as_int(cc), __float_as_int(k.x), __float_as_int(k.y),
+                                    __float_as_int(tau));
+  A.emit_rec[3 * j + 2] = make_int4((int)s, MAXV == 1 ? 0 : min(max(mm.y, 0), rv.nviews - 1), mm.z, mm.w);
+  return area;
+}
+
+// Pairs [p0, p1) of depth-sorted position j: every emission chunk whose first
+// pair falls among them records j and has its look-back word cleared.
+__device__ __forceinline__ void mark_chunks(const EmitArgs &A, int64_t j, uint64_t p0, uint64_t p1) {
+  for (uint64_t c = (p0 + kEmitChunk - 1) / kEmitChunk; c * kEmitChunk < p1 && c < (uint64_t)A.chunk_cap; ++c) {
+    A.chunk_first[c] = (uint32_t)j;
+    A.lb_chunk[c] = 0ull;
+  }
+}
+
+// Sets the pair total (clamped to the pair capacity) and, when pairs are lost
+// to the clamp, the instance bound and the overflow flag.
+__device__ __forceinline__ void set_pair_total(const EmitArgs &A, int64_t nvis, uint64_t all) {
+  A.pair_prefix[nvis] = (uint32_t)umin64(all, (uint64_t)A.pair_cap);
+  A.counters[kCtrPairs] = (uint32_t)umin64(all, (uint64_t)A.pair_cap);
+  if (all > (uint64_t)A.pair_cap) {
+    // Some pairs cannot be examined: report the pair total as the bound on
+    // the instances needed.
+    A.counters[kCtrNeedInstances] = (uint32_t)umin64(all, 0xffffffffull);
+    atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
+  }
+}
+
+// No visible slot: no pairs, no instances.
+__device__ __forceinline__ void set_empty_totals(const EmitArgs &A) {
+  A.counters[kCtrPairs] = 0u;
+  A.counters[kCtrInstances] = 0u;
+  A.counters[kCtrNeedInstances] = 0u;
+}
+
 // Pair scan, one thread per depth-sorted visible slot: the exclusive prefix
-// of the slots' rect areas in depth order (decoupled look-back), plus a
-// compact emission record per position: (u, v, A', B'), (C', kx, ky, tau),
-// (slot, view, packed rect lo, packed rect hi), and, for every emission
-// chunk whose first pair falls in a position's pairs, that position.
+// of the slots' rect areas in depth order (decoupled look-back), plus the
+// emission record of every position and the chunk marks.
 template <int MAXV>
 __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
@@ -285,87 +383,24 @@ __global__ void __launch_bounds__(kEmitBlock) pair_scan_kernel(EmitArgs A, Raste
   if (threadIdx.x == 0) s_ticket = atomicAdd(&A.counters[kCtrTicketEmit], 1u);
   __syncthreads();
   const int64_t b = s_ticket;
-  if (b == 0 && nvis == 0 && threadIdx.x == 0) {  // no slot: no pairs, no instances
-    A.counters[kCtrPairs] = 0u;
-    A.counters[kCtrInstances] = 0u;
-    A.counters[kCtrNeedInstances] = 0u;
-  }
+  if (b == 0 && nvis == 0 && threadIdx.x == 0) set_empty_totals(A);
   if (b * kEmitBlock >= nvis) return;
   const int64_t j = b * kEmitBlock + threadIdx.x;
-  uint32_t area = 0u;
-  if (j < nvis) {
-    const uint32_t s = A.sorted_slots[j];
-    int4 mm = make_int4(0, 0, 0, 0);
-    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-    float cc = 0.f, tau = -1.0f;
-    if ((int64_t)s < nvis) {
-      mm = A.meta[s];
-      g = A.geom[s];
-      cc = A.color[s].x;
-      tau = A.tau[s];
-      int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff, y1 = (uint32_t)mm.w >> 16;
-      // Only tiles whose pixel-centre box meets the 1/255 ellipse are kept,
-      // so the pairs are enumerated over the rect cut to the ellipse's
-      // bounding box: half-extents sqrt(tau C'/det), sqrt(tau A'/det) with
-      // det = A'C' - B'^2/4, widened by 0.1% + 0.05 px against rounding (a
-      // box outside them is far outside the ellipse, which the exact test
-      // below rejects as well).  With tile edge T, tile tx's centre box
-      // [T tx + 0.5, T tx + T - 0.5] can meet [u - rx, u + rx] only for
-      // ceil((u - rx - T + 0.5) / T) <= tx <= floor((u + rx - 0.5) / T).
-      const float det = g.z * cc - 0.25f * g.w * g.w;
-      if (tau < 0.0f) {
-        x1 = x0;
-      } else if (det > 0.0f) {
-        const RasterView &V = rv.v[MAXV == 1 ? 0 : min(max(mm.y, 0), rv.nviews - 1)];
-        const float T = (float)V.tile, iT = 1.0f / T;
-        const float rx = sqrtf(tau * cc / det) * 1.001f + 0.05f, ry = sqrtf(tau * g.z / det) * 1.001f + 0.05f;
-        const float lx = ceilf((g.x - rx - (T - 0.5f)) * iT), hx = floorf((g.x + rx - 0.5f) * iT);
-        const float ly = ceilf((g.y - ry - (T - 0.5f)) * iT), hy = floorf((g.y + ry - 0.5f) * iT);
-        if (lx > (float)x0) x0 = (int)fminf(lx, (float)x1);
-        if (hx + 1.0f < (float)x1) x1 = (int)fmaxf(hx + 1.0f, (float)x0);
-        if (ly > (float)y0) y0 = (int)fminf(ly, (float)y1);
-        if (hy + 1.0f < (float)y1) y1 = (int)fmaxf(hy + 1.0f, (float)y0);
-      }
-      area = (uint32_t)(max(x1 - x0, 0) * max(y1 - y0, 0));
-      mm.z = x0 | (y0 << 16);
-      mm.w = x1 | (y1 << 16);
-    } else {
-      atomicOr(&A.counters[kCtrStatus], kStatusInternal);
-    }
-    const float2 k = edge_slopes(g.z, g.w, cc);
-    A.emit_rec[3 * j + 0] = make_int4(__float_as_int(g.x), __float_as_int(g.y), __float_as_int(g.z),
-                                      __float_as_int(g.w));
-    A.emit_rec[3 * j + 1] = make_int4(__float_as_int(cc), __float_as_int(k.x), __float_as_int(k.y),
-                                      __float_as_int(tau));
-    A.emit_rec[3 * j + 2] = make_int4((int)s, MAXV == 1 ? 0 : min(max(mm.y, 0), rv.nviews - 1), mm.z, mm.w);
-  }
+  const uint32_t area = j < nvis ? pair_record<MAXV>(A, rv, A.sorted_slots[j], j, nvis) : 0u;
   uint32_t total;
   const uint32_t excl = block_exclusive_scan(area, s_scan, &total);
   __shared__ uint64_t s_base;
   if (threadIdx.x < 32) {
     const uint64_t prefix = lookback_u64_warp(A.lb_scan, (int32_t)b, total, &A.counters[kCtrStatus]);
     if (threadIdx.x == 0) s_base = prefix;
-    if (threadIdx.x == 0 && (b + 1) * kEmitBlock >= nvis) {  // last block: the pair total
-      const uint64_t all = prefix + total;
-      A.pair_prefix[nvis] = (uint32_t)umin64(all, (uint64_t)A.pair_cap);
-      A.counters[kCtrPairs] = (uint32_t)umin64(all, (uint64_t)A.pair_cap);
-      if (all > (uint64_t)A.pair_cap) {
-        // Some pairs cannot be examined: report the pair total as the bound
-        // on the instances needed.
-        A.counters[kCtrNeedInstances] = (uint32_t)umin64(all, 0xffffffffull);
-        atomicOr(&A.counters[kCtrStatus], kStatusInstOverflow);
-      }
-    }
+    if (threadIdx.x == 0 && (b + 1) * kEmitBlock >= nvis) set_pair_total(A, nvis, prefix + total);
   }
   __syncthreads();
   if (j < nvis) {
     const uint64_t p0 = umin64(s_base + excl, (uint64_t)A.pair_cap);
     const uint64_t p1 = umin64(s_base + excl + area, (uint64_t)A.pair_cap);
     A.pair_prefix[j] = (uint32_t)p0;
-    for (uint64_t c = (p0 + kEmitChunk - 1) / kEmitChunk; c * kEmitChunk < p1 && c < (uint64_t)A.chunk_cap; ++c) {
-      A.chunk_first[c] = (uint32_t)j;
-      A.lb_chunk[c] = 0ull;
-    }
+    mark_chunks(A, j, p0, p1);
   }
 }
 
@@ -516,7 +551,7 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
   __shared__ uint64_t s_prefix;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < A.total_tiles;
        r += (int64_t)gridDim.x * blockDim.x)
-    A.ranges[r] = make_uint2(0u, 0u);
+    A.ranges[r] = make_uint2(0xffffffffu, 0u);  // empty until the last tile-sort pass records a run
   const int64_t nvis = min64((int64_t)A.counters[kCtrVisible], A.vis_cap);
   const uint32_t npairs = A.counters[kCtrPairs];
   const uint32_t nchunks = (uint32_t)min64((npairs + kEmitChunk - 1) / kEmitChunk, A.chunk_cap);
@@ -585,21 +620,6 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
   }
 }
 
-__global__ void ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ counters, int64_t cap,
-                              uint2 *ranges, int64_t total_tiles, uint32_t *status) {
-  grid_dependency_sync();
-  const int64_t count = min64((int64_t)counters[kCtrInstances], cap);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = keys[i];
-    if ((int64_t)k >= total_tiles) {
-      atomicOr(status, kStatusInternal);
-      continue;
-    }
-    if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
-    if (i == count - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
-  }
-}
-
 template <int MAXV>
 cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nviews, unsigned char *ws,
                            cudaStream_t st) {
@@ -616,87 +636,91 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   uint32_t *dv[2] = {reinterpret_cast<uint32_t *>(ws + L.dsort_val[0]), reinterpret_cast<uint32_t *>(ws + L.dsort_val[1])};
   uint32_t *dstate = reinterpret_cast<uint32_t *>(ws + L.depth_state);
   uint32_t *hist_d = reinterpret_cast<uint32_t *>(ws + L.hist_depth);
-  if (L.depth_blocks > 0) {
-    const int hb = std::min(L.depth_blocks, kPersistBlocks);
-    const int pb = std::min(L.depth_blocks, kPersistBlocks);
-    e = launch_pdl(radix_hist_kernel<kDepthSortItems>, (unsigned)hb, kSortThreads, st, dkey, (const uint32_t *)(ctr + kCtrVisible),
-                   (int64_t)L.vis_cap, (int32_t)L.depth_passes, hist_d, dstate, (int32_t)L.depth_blocks,
-                   (uint2 *)nullptr, (int64_t)0);
-    if (e != cudaSuccess) return e;
-    for (int p = 0; p < L.depth_passes; ++p) {
-      const int out = p & 1, in = out ^ 1;
-      uint32_t *state = dstate + (size_t)p * L.depth_blocks * kRadixBins;
-      const uint32_t *kin = p == 0 ? dkey : dk[in];
-      const uint32_t *vin = p == 0 ? nullptr : dv[in];
-      e = launch_pdl(p == 0 ? radix_pass_kernel<true, kDepthSortItems> : radix_pass_kernel<false, kDepthSortItems>,
-                     (unsigned)pb, kSortThreads, st,
-                     kin, vin, dk[out], dv[out], (const uint32_t *)(ctr + kCtrVisible), (int64_t)L.vis_cap,
-                     (int32_t)(kRadixBits * p), (const uint32_t *)(hist_d + p * kRadixBins), state,
-                     ctr + kCtrTicketDepth + p, status);
-      if (e != cudaSuccess) return e;
-    }
-  }
-  const uint32_t *sorted = dv[(L.depth_passes - 1) & 1];
-  // 2. Instances in depth order.
+  uint32_t *sorted = dv[(L.depth_passes - 1) & 1];
   uint32_t *tstate = reinterpret_cast<uint32_t *>(ws + L.tile_state);
   uint32_t *hist_t = reinterpret_cast<uint32_t *>(ws + L.hist_tile);
   uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
   uint32_t *ik[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_key[0]), reinterpret_cast<uint32_t *>(ws + L.inst_key[1])};
   uint32_t *iv[2] = {reinterpret_cast<uint32_t *>(ws + L.inst_val[0]), reinterpret_cast<uint32_t *>(ws + L.inst_val[1])};
+  EmitArgs ea;
+  ea.sorted_slots = sorted;
+  ea.meta = reinterpret_cast<const int4 *>(ws + L.rec_meta);
+  ea.geom = reinterpret_cast<const float4 *>(ws + L.rec_geom);
+  ea.color = reinterpret_cast<const float4 *>(ws + L.rec_color);
+  ea.tau = reinterpret_cast<const float *>(ws + L.rec_tau);
+  ea.counters = ctr;
+  ea.vis_cap = L.vis_cap;
+  ea.inst_cap = L.inst_cap;
+  ea.pair_cap = L.pair_cap;
+  ea.chunk_cap = L.chunk_cap;
+  ea.pair_prefix = reinterpret_cast<uint32_t *>(ws + L.pair_prefix);
+  ea.emit_rec = reinterpret_cast<int4 *>(ws + L.emit_rec);
+  ea.chunk_first = reinterpret_cast<uint32_t *>(ws + L.chunk_first);
+  ea.inst_key = ik[0];
+  ea.inst_val = iv[0];
+  ea.lb_scan = reinterpret_cast<uint64_t *>(ws + L.lb_emit);
+  ea.lb_chunk = reinterpret_cast<uint64_t *>(ws + L.lb_chunk);
+  ea.tile_passes = L.tile_passes;
+  ea.tile_blocks = L.tile_blocks;
+  ea.hist_tile = hist_t;
+  ea.tile_state = tstate;
+  ea.ranges = ranges;
+  ea.total_tiles = L.total_tiles;
   if (L.emit_blocks == 0) {  // no visible slot possible: empty tile lists
     e = cudaMemsetAsync(ranges, 0, (size_t)L.total_tiles * sizeof(uint2), st);
     if (e != cudaSuccess) return e;
   } else {
-    EmitArgs ea;
-    ea.sorted_slots = sorted;
-    ea.meta = reinterpret_cast<const int4 *>(ws + L.rec_meta);
-    ea.geom = reinterpret_cast<const float4 *>(ws + L.rec_geom);
-    ea.color = reinterpret_cast<const float4 *>(ws + L.rec_color);
-    ea.tau = reinterpret_cast<const float *>(ws + L.rec_tau);
-    ea.counters = ctr;
-    ea.vis_cap = L.vis_cap;
-    ea.inst_cap = L.inst_cap;
-    ea.pair_cap = L.pair_cap;
-    ea.chunk_cap = L.chunk_cap;
-    ea.pair_prefix = reinterpret_cast<uint32_t *>(ws + L.pair_prefix);
-    ea.emit_rec = reinterpret_cast<int4 *>(ws + L.emit_rec);
-    ea.chunk_first = reinterpret_cast<uint32_t *>(ws + L.chunk_first);
-    ea.inst_key = ik[0];
-    ea.inst_val = iv[0];
-    ea.lb_scan = reinterpret_cast<uint64_t *>(ws + L.lb_emit);
-    ea.lb_chunk = reinterpret_cast<uint64_t *>(ws + L.lb_chunk);
-    ea.tile_passes = L.tile_passes;
-    ea.tile_blocks = L.tile_blocks;
-    ea.hist_tile = hist_t;
-    ea.tile_state = tstate;
-    ea.ranges = ranges;
-    ea.total_tiles = L.total_tiles;
+    if (L.depth_blocks > 0) {
+      const int hb = std::min(L.depth_blocks, kPersistBlocks);
+      const int pb = std::min(L.depth_blocks, kPersistBlocks);
+      e = launch_pdl(radix_hist_kernel<kDepthSortItems>, (unsigned)hb, kSortThreads, st, dkey,
+                     (const uint32_t *)(ctr + kCtrVisible), (int64_t)L.vis_cap, (int32_t)L.depth_passes, hist_d,
+                     dstate, (int32_t)L.depth_blocks, (uint2 *)nullptr, (int64_t)0);
+      if (e != cudaSuccess) return e;
+      for (int p = 0; p < L.depth_passes; ++p) {
+        const int out = p & 1, in = out ^ 1;
+        uint32_t *state = dstate + (size_t)p * L.depth_blocks * kRadixBins;
+        const uint32_t *kin = p == 0 ? dkey : dk[in];
+        const uint32_t *vin = p == 0 ? nullptr : dv[in];
+        e = launch_pdl(p == 0 ? radix_pass_kernel<true, kDepthSortItems> : radix_pass_kernel<false, kDepthSortItems>,
+                       (unsigned)pb, kSortThreads, st, kin, vin, dk[out], dv[out],
+                       (const uint32_t *)(ctr + kCtrVisible), (int64_t)L.vis_cap, (int32_t)(kRadixBits * p),
+                       (const uint32_t *)(hist_d + p * kRadixBins), state, ctr + kCtrTicketDepth + p, status,
+                       (uint2 *)nullptr, (int64_t)0);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    // 2. Instances in depth order.
     e = launch_pdl(pair_scan_kernel<MAXV>, (unsigned)L.emit_blocks, kEmitBlock, st, ea, rv);
     if (e != cudaSuccess) return e;
     e = launch_pdl(emit_kernel<MAXV>, (unsigned)L.emit_grid, kEmitBlock, st, ea, rv);
     if (e != cudaSuccess) return e;
   }
   // 3. Stable sort of the instances by global tile id (digit histograms
-  // taken by the emission).
+  // taken by the emission); the last pass also records the tile ranges.
   const int pbt = std::min(L.tile_blocks, kPersistBlocks);
   for (int p = 0; p < L.tile_passes; ++p) {
     const int in = p & 1, out = in ^ 1;
+    const bool last = p == L.tile_passes - 1;
     uint32_t *state = tstate + (size_t)p * L.tile_blocks * kRadixBins;
     e = launch_pdl(radix_pass_kernel<false, kInstSortItems>, (unsigned)pbt, kSortThreads, st, (const uint32_t *)ik[in],
                    (const uint32_t *)iv[in], ik[out], iv[out], (const uint32_t *)(ctr + kCtrInstances),
                    (int64_t)L.inst_cap, (int32_t)(kRadixBits * p), (const uint32_t *)(hist_t + p * kRadixBins), state,
-                   ctr + kCtrTicketTile + p, status);
+                   ctr + kCtrTicketTile + p, status, last ? ranges : (uint2 *)nullptr, (int64_t)L.total_tiles);
     if (e != cudaSuccess) return e;
   }
-  // 4. Tile ranges.
-  const uint32_t *final_keys = ik[L.tile_passes & 1];
-  int rb = (int)min64((L.inst_cap + 255) / 256, 152 * 16);
-  if (rb < 1) rb = 1;
-  return launch_pdl(ranges_kernel, (unsigned)rb, 256u, st, final_keys, (const uint32_t *)ctr, (int64_t)L.inst_cap,
-                    ranges, (int64_t)L.total_tiles, status);
+  return cudaSuccess;
 }
 
 }  // namespace
+
+int bin_sort_kernel_count(const Layout &L, int32_t nviews) {
+  (void)nviews;
+  const int tail = L.tile_passes;  // tile-sort passes (the last records the ranges)
+  if (L.emit_blocks == 0) return tail;
+  // depth histogram and passes, pair scan, emission
+  return (L.depth_blocks > 0 ? 1 + L.depth_passes : 0) + 2 + tail;
+}
 
 cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nviews, unsigned char *ws,
                             cudaStream_t stream) {
@@ -784,11 +808,11 @@ extern "C" int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, ui
     if (p == 0)
       radix_pass_kernel<true, kSortItems><<<blocks, kSortThreads, 0, st>>>(kin, nullptr, s->keys[out], vout, &s->ctl[0],
                                                                FGS4D_STATIC_SORT_MAX, kRadixBits * p, s->hist[p],
-                                                               &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1]);
+                                                               &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1], nullptr, 0);
     else
       radix_pass_kernel<false, kSortItems><<<blocks, kSortThreads, 0, st>>>(kin, s->vals[in], s->keys[out], vout, &s->ctl[0],
                                                                 FGS4D_STATIC_SORT_MAX, kRadixBits * p, s->hist[p],
-                                                                &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1]);
+                                                                &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1], nullptr, 0);
   }
   return cudaGetLastError() == cudaSuccess ? FGS4D_OK : FGS4D_ERR_CUDA;
 }

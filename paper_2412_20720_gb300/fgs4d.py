@@ -28,7 +28,7 @@ MAX_SH_DEGREE = 3
 MAX_T_ORDER = 4
 TILE = 16  # default tile edge; 8 is the other supported size
 
-EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
+EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort", "fgs4d_bin_sort_kernels",
             "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_sort_depth_static", "fgs4d_get_status",
             "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
@@ -103,6 +103,7 @@ def load():
     lib.fgs4d_workspace_layout.argtypes = [P(Settings), i64, P(View), i32, P(Layout)]
     lib.fgs4d_preprocess.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, vp]
     lib.fgs4d_bin_sort.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp]
+    lib.fgs4d_bin_sort_kernels.argtypes = [i64, P(View), i32, P(Settings), P(C.c_int32)]
     lib.fgs4d_render_fwd.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, vp, vp]
     lib.fgs4d_render_aux.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, C.c_float, vp, vp,
                                      vp, vp]
@@ -205,6 +206,14 @@ def workspace_layout(settings: Settings, n: int, views, nviews: int) -> Layout:
 def preprocess(gaussians: Gaussians, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, stream: int):
     _check(load().fgs4d_preprocess(C.byref(gaussians), views, int(nviews), C.byref(settings), ws, ws_bytes, stream),
            "fgs4d_preprocess")
+
+
+def bin_sort_kernels(n: int, views, nviews: int, settings: Settings) -> int:
+    """Kernels fgs4d_bin_sort launches for these arguments on the current device."""
+    out = C.c_int32(0)
+    _check(load().fgs4d_bin_sort_kernels(int(n), views, int(nviews), C.byref(settings), C.byref(out)),
+           "fgs4d_bin_sort_kernels")
+    return int(out.value)
 
 
 def bin_sort(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, stream: int):

@@ -88,6 +88,31 @@ class Renderer:
             self.settings.tile = int(tile)
             self._allocate()
 
+    def fit_visible_capacity(self, params: dict, view_sets=None, margin: float = 1.1) -> int:
+        """Sizes the visible-pair capacity to the caller's own views: runs
+        preprocess for every (views, nviews) set of ``view_sets`` (default:
+        the renderer's views), takes the largest visible count, adds
+        ``margin`` and rounds up to a multiple of 1024, then re-lays out the
+        workspace (the depth sort and pair scan size their grids by the
+        capacity).  A later view with more visible pairs reports a capacity
+        overflow (status) and needs a larger capacity.  Returns the
+        capacity."""
+        g = self.gaussians(params)
+        st = self.stream()
+        view_sets = view_sets or [(self.views, self.nviews)]
+        need = 0
+        for views, nv in view_sets:
+            fgs4d.preprocess(g, views, nv, self.settings, _ptr(self.ws), self.ws_bytes, st)
+            code, counts = self.status()
+            if code not in (fgs4d.OK, fgs4d.ERR_CAPACITY):
+                raise fgs4d.Fgs4dError(code, "fit_visible_capacity")
+            need = max(need, int(counts[0]), int(counts[2]))
+        cap = max(1024, -(-int(need * margin) // 1024) * 1024)
+        self.settings.vis_capacity = cap
+        self.config.vis_capacity = cap
+        self._allocate()
+        return cap
+
     # ---------------------------------------------------------------- plumbing
     def stream(self) -> int:
         return torch.cuda.current_stream(self.device).cuda_stream

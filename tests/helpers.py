@@ -123,3 +123,13 @@ def compare_group(name, gpu, ref, rtol, floor_frac):
     assert ratio[worst] <= 1.0, "%s: gpu %r vs oracle %r at %d (ratio %.3g)" % (name, gpu[worst], ref[worst], worst,
                                                                                ratio[worst])
     return float(ratio.max())
+
+
+def canonical_ranges(gr):
+    """Tile ranges as [start, end) with empty tiles as (0, 0): the library may
+    leave any start >= end in a tile without instances."""
+    import numpy as np
+    gr = np.array(gr, dtype=np.int64).reshape(-1, 2) & 0xFFFFFFFF
+    out = gr.copy()
+    out[gr[:, 0] >= gr[:, 1]] = 0
+    return out

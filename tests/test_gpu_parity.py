@@ -13,7 +13,7 @@ from paper_2412_20720_gb300 import fgs4d
 from paper_2412_20720_gb300 import synthetic as sy
 from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig
 
-from helpers import (PIXEL_MARGIN, GpuRun, compare_group, keep_clear_of_boundaries, oracle_settings,
+from helpers import (PIXEL_MARGIN, GpuRun, canonical_ranges, compare_group, keep_clear_of_boundaries, oracle_settings,
                      records_from_gpu, subset)
 
 pytestmark = pytest.mark.gpu
@@ -291,8 +291,11 @@ def _oracle_sorted(rec, W, H, tile=16):
                                  tau=rec["tau"], width=W, height=H, tile=tile)
 
 
-@pytest.mark.parametrize("n,W,H", [(1, 16, 16), (2047, 144, 112), (70_001, 1352, 1014)])
-def test_bin_sort_bit_exact_on_synthetic_records(n, W, H):
+# Visible capacities equal to the slot count and well above it (the pair scan
+# and depth sort size their grids and look-back rows by the capacity).
+@pytest.mark.parametrize("n,W,H,vis_cap", [(1, 16, 16, 0), (2047, 144, 112, 0), (70_001, 1352, 1014, 0),
+                                           (70_001, 1352, 1014, 400_000), (150_001, 1352, 1014, 0)])
+def test_bin_sort_bit_exact_on_synthetic_records(n, W, H, vis_cap):
     """Sorted instance list and tile ranges equal the oracle's bit for bit:
     the tiles of each rect that the FP32 ellipse test keeps, ordered by (tile,
     FP32 depth, slot), on records written straight into the workspace
@@ -302,7 +305,7 @@ def test_bin_sort_bit_exact_on_synthetic_records(n, W, H):
     rng = np.random.default_rng(n)
     gw, gh = (W + 15) // 16, (H + 15) // 16
     rec = _synthetic_records(rng, n, W, H, 6)
-    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=40 * n + 16)
+    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=40 * n + 16, vis_capacity=vis_cap)
     r = Renderer(n, [sy.tiny_view(W, H)], cfg)
     _write_records(r, rec, 0)
     fgs4d.bin_sort(n, r.views, r.nviews, r.settings, r.ws.data_ptr(), r.ws_bytes, r.stream())
@@ -319,7 +322,9 @@ def test_bin_sort_bit_exact_on_synthetic_records(n, W, H):
     np.testing.assert_array_equal(slots, vals)
     np.testing.assert_array_equal(rec["depth"][slots].view(np.uint32),
                                   (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32))
-    np.testing.assert_array_equal(gr, ranges)
+    np.testing.assert_array_equal(canonical_ranges(gr), ranges)
+    sorted_slots = r.workspace_view(r.layout.sorted_slots, torch.int32, n).cpu().numpy()
+    np.testing.assert_array_equal(sorted_slots, np.argsort(rec["depth"], kind="stable"))
 
 
 def test_bin_sort_bit_exact_multi_view():
@@ -358,7 +363,7 @@ def test_bin_sort_bit_exact_multi_view():
     gr = r.workspace_view(r.layout.tile_ranges, torch.int32, 2 * tile_base).cpu().numpy().reshape(-1, 2)
     np.testing.assert_array_equal(tiles, np.concatenate(exp_tiles))
     np.testing.assert_array_equal(slots, np.concatenate(exp_slots))
-    np.testing.assert_array_equal(gr, np.concatenate(exp_ranges))
+    np.testing.assert_array_equal(canonical_ranges(gr), np.concatenate(exp_ranges))
 
 
 # ------------------------------------------------------------- edge cases

@@ -256,7 +256,7 @@ PPT_CANDIDATES = {16: (2, 4, 8), 8: (1, 2)}
 
 
 def autotune(renderer: Renderer, params: dict, view_sets=None, tiles=(16,), candidates=None, batches=(256,),
-             reps: int = 3, backward: bool = False, cache_path: str | None = None) -> dict:
+             reps: int = 3, backward: bool = False, cache_path: str | None = None, pipeline=None) -> dict:
     """Picks the tile edge (among ``tiles``: 16, 8), the compositor block
     shape (pixels per thread, ``candidates`` or all valid ones per tile) and
     its shared-memory batch size (among ``batches``: 256, 128) that run the
@@ -269,8 +269,11 @@ def autotune(renderer: Renderer, params: dict, view_sets=None, tiles=(16,), cand
     views) -- the tile edge changes the sort's work as well as the
     compositor's.  With ``cache_path``, the choice is stored in a JSON file
     keyed by (GPU, resolutions, views, N rounded to a power of two) and
-    reused.  Returns {"tile": t, "pixels_per_thread": p, "shared_batch": b,
-    "ms": {"t/p/b": ms}}."""
+    reused.  With ``pipeline`` (a FramePipeline holding ``renderer`` as a
+    slot; forward only, one view per set), each shape is applied to every
+    slot and timed with the view sets submitted through the pipeline, frames
+    in flight as they will run.  Returns {"tile": t, "pixels_per_thread": p,
+    "shared_batch": b, "ms": {"t/p/b": ms}}."""
     import json
     import os
 
@@ -298,6 +301,35 @@ def autotune(renderer: Renderer, params: dict, view_sets=None, tiles=(16,), cand
     shapes = [(t, p, b) for t in tiles
               for p in (candidates if candidates is not None and t == 16 else PPT_CANDIDATES[int(t)])
               for b in batches]
+    if pipeline is not None:
+        if backward:
+            raise ValueError("autotune: a pipeline times forward frames only")
+        for tile, p, bsz in shapes:
+            pipeline.set_tile(tile, p, bsz)
+            outs = [torch.empty(3 * r.total_pixels, dtype=torch.float32, device=renderer.device)
+                    for r in pipeline.slots]
+
+            def sweep():
+                pipeline.begin()
+                for views, nv in view_sets:
+                    j = pipeline.slot_of_next()
+                    pipeline.submit(g, views, nv, outs[j].data_ptr())
+                pipeline.end()
+            sweep()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                sweep()
+            b.record(stream)
+            b.synchronize()
+            if all(r.status()[0] == fgs4d.OK for r in pipeline.slots):
+                ms["%d/%d/%d" % (tile, p, bsz)] = a.elapsed_time(b) / reps
+        if not ms:
+            raise RuntimeError("autotune: every candidate overflowed a capacity")
+        best = min(ms, key=ms.get)
+        bt, bp, bb = (int(x) for x in best.split("/"))
+        pipeline.set_tile(bt, bp, bb)
+        return {"tile": bt, "pixels_per_thread": bp, "shared_batch": bb, "ms": ms, "timed": "pipeline"}
     for tile, p, bsz in shapes:
         renderer.set_tile(tile, p, bsz)
         ws, wsb = renderer.ws.data_ptr(), renderer.ws_bytes
@@ -332,6 +364,85 @@ def autotune(renderer: Renderer, params: dict, view_sets=None, tiles=(16,), cand
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
     return result
+
+
+class FramePipeline:
+    """Independent single views rendered with ``depth`` frames in flight.
+
+    Each in-flight slot owns a Renderer (its own workspace) and a CUDA
+    stream; the k-th frame submitted after ``begin`` runs preprocess,
+    bin_sort and render_fwd on slot k % depth.  Frames on different slots
+    share only the read-only parameters, so the latency-bound binning and
+    sorting of one frame run beside the ALU-bound compositing of another;
+    frames on one slot run in submission order, so a slot's output buffer may
+    be reused by its next frame.  ``end`` makes the caller's current stream
+    wait for every slot.
+    """
+
+    def __init__(self, n: int, view: dict, config: RenderConfig, depth: int = 3, device=None):
+        import dataclasses
+        if depth < 1:
+            raise ValueError("depth must be >= 1")
+        self.depth = int(depth)
+        self.slots = [Renderer(n, [view], dataclasses.replace(config), device=device) for _ in range(self.depth)]
+        self.device = self.slots[0].device
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(self.depth)]
+        self._next = 0
+
+    def fit_visible_capacity(self, params: dict, view_sets, margin: float = 1.1) -> int:
+        """Renderer.fit_visible_capacity on the first slot, applied to all."""
+        cap = self.slots[0].fit_visible_capacity(params, view_sets=view_sets, margin=margin)
+        for r in self.slots[1:]:
+            r.settings.vis_capacity = cap
+            r.config.vis_capacity = cap
+            r._allocate()
+        return cap
+
+    def set_tile(self, tile: int, pixels_per_thread: int = 0, shared_batch: int = 0):
+        for r in self.slots:
+            r.set_tile(tile, pixels_per_thread, shared_batch)
+
+    def begin(self):
+        """Every slot stream waits for the work already on the current stream."""
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.current_stream(self.device))
+        for st in self.streams:
+            st.wait_event(ev)
+        self._next = 0
+
+    def slot_of_next(self) -> int:
+        return self._next % self.depth
+
+    def submit(self, g: fgs4d.Gaussians, views, nviews: int, out_rgb: int, out_T: int | None = None,
+               events=None, after=None) -> int:
+        """Launches one frame (views, nviews from fgs4d.make_views) on the
+        next slot; ``g`` from any slot's gaussians().  ``events`` = (e0, e1)
+        are recorded around the compositor launch, ``after(stream)`` is
+        called on the slot stream after it (e.g. to enqueue a copy of the
+        output).  Returns the slot index."""
+        j = self._next % self.depth
+        self._next += 1
+        r, st = self.slots[j], self.streams[j]
+        ws, wsb, s, sp = r.ws.data_ptr(), r.ws_bytes, r.settings, st.cuda_stream
+        fgs4d.preprocess(g, views, nviews, s, ws, wsb, sp)
+        fgs4d.bin_sort(r.n, views, nviews, s, ws, wsb, sp)
+        if events is not None:
+            events[0].record(st)
+        fgs4d.render_fwd(r.n, views, nviews, s, ws, wsb, out_rgb, out_T, sp)
+        if events is not None:
+            events[1].record(st)
+        if after is not None:
+            after(st)
+        return j
+
+    def end(self):
+        cur = torch.cuda.current_stream(self.device)
+        for st in self.streams:
+            cur.wait_stream(st)
+
+    def check(self):
+        """Synchronises; raises if any slot's workspace reports an error."""
+        return [r.check() for r in self.slots]
 
 
 class Render4DGS(torch.autograd.Function):

@@ -341,6 +341,14 @@ int fgs4d_render_features_bwd(int64_t n, const fgs4d_view *views, int32_t nviews
 int fgs4d_l1_loss(const float *img, const float *target, int64_t count, float *loss_out, float *dL_dimg,
                   void *stream);
 
+/* One part of an L1 loss averaged over mean_count elements, for a batch whose
+ * images are rendered by separate calls: loss_out[0] += sum |img - target| /
+ * mean_count over this part's count elements, dL_dimg = sign(img - target) /
+ * mean_count.  count <= mean_count; otherwise as fgs4d_l1_loss (the paper's
+ * loss is the mean over the batch). */
+int fgs4d_l1_loss_part(const float *img, const float *target, int64_t count, int64_t mean_count, float *loss_out,
+                       float *dL_dimg, void *stream);
+
 /* Largest key count fgs4d_sort_depth_static accepts. */
 #define FGS4D_STATIC_SORT_MAX (1 << 20)
 

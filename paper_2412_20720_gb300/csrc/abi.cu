@@ -426,7 +426,16 @@ int fgs4d_mask_loss(const float *mask_logit, int64_t n, float *loss_out, float *
 int fgs4d_l1_loss(const float *img, const float *target, int64_t count, float *loss_out, float *dL_dimg,
                   void *stream) {
   if (count < 0 || (count > 0 && (!img || !target || !loss_out || !dL_dimg))) return FGS4D_ERR_ARG;
-  return cuda_status(launch_l1_loss(img, target, count, loss_out, dL_dimg, static_cast<cudaStream_t>(stream)));
+  return cuda_status(launch_l1_loss(img, target, count, count, loss_out, dL_dimg, static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_l1_loss_part(const float *img, const float *target, int64_t count, int64_t mean_count, float *loss_out,
+                       float *dL_dimg, void *stream) {
+  if (count < 0 || mean_count < count || mean_count <= 0 ||
+      (count > 0 && (!img || !target || !loss_out || !dL_dimg)))
+    return FGS4D_ERR_ARG;
+  return cuda_status(launch_l1_loss(img, target, count, mean_count, loss_out, dL_dimg,
+                                    static_cast<cudaStream_t>(stream)));
 }
 
 int fgs4d_get_status(const void *workspace, size_t workspace_bytes, void *stream, int64_t *counts_out) {

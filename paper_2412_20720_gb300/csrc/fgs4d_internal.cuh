@@ -431,8 +431,8 @@ cudaError_t launch_split(const fgs4d_gaussians *src, const int32_t *idx, int64_t
                          cudaStream_t stream);
 cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, const float *dL_drgb, const float *dL_daux, cudaStream_t stream);
-cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, float *loss, float *grad,
-                           cudaStream_t stream);
+cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, int64_t mean_count, float *loss,
+                           float *grad, cudaStream_t stream);
 
 // Fills a raster view table; returns false if nviews exceeds MAXV.
 template <int MAXV>

@@ -16,8 +16,8 @@
 // Backward: the same tiles traversed back to front from each pixel's last
 // composited entry, recomputing T_i = T_{i+1} / (1 - alpha_i) from the final
 // transmittance.  A thread first sums its strip's contributions; the sums are
-// then reduced across the warp by shuffles and added with one vector atomic
-// per warp and entry.
+// then reduced across the warp by shuffles and added with two float4 and one
+// float2 atomic per warp and entry.
 #include <algorithm>
 #include <type_traits>
 
@@ -376,11 +376,16 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
         warp_sum8_transposed(g, lane);
         gb = warp_sum(gb);
         if (kAux) gz = warp_sum(gz);
+        // Lane 4k holds sum k: lanes 0 and 16 gather sums 0-3 and 4-7 and add
+        // them with one vector atomic each; lane 1 adds (db, dz).
+        const float s1 = __shfl_down_sync(0xffffffffu, g[0], 4);
+        const float s2 = __shfl_down_sync(0xffffffffu, g[0], 8);
+        const float s3 = __shfl_down_sync(0xffffffffu, g[0], 12);
         const uint32_t slot = s_slot[j];
-        // Lanes 0, 4, ..., 28 add values 0..7; lane 1 adds db; lane 2 dz.
-        if (slot < A.vis_cap && ((lane & 3) == 0 || lane == 1 || (kAux && lane == 2))) {
-          float *dst = reinterpret_cast<float *>(A.slot_grad + 3 * (size_t)slot);
-          atomicAdd(dst + (lane == 1 ? 8 : lane == 2 ? 9 : (lane >> 2)), lane == 1 ? gb : lane == 2 ? gz : g[0]);
+        if (slot < A.vis_cap) {
+          float4 *dst = A.slot_grad + 3 * (size_t)slot;
+          if ((lane & 15) == 0) atomicAdd(dst + (lane >> 4), make_float4(g[0], s1, s2, s3));
+          else if (lane == 1) atomicAdd(reinterpret_cast<float2 *>(dst + 2), make_float2(gb, kAux ? gz : 0.0f));
         }
       }
     }
@@ -613,12 +618,12 @@ cudaError_t launch_mask_loss(const float *mask_logit, int64_t n, float *loss, fl
   return launch_pdl(mask_loss_kernel, (unsigned)blocks, 256u, stream, mask_logit, n, 1.0f / (float)n, loss, grad);
 }
 
-cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, float *loss, float *grad,
-                           cudaStream_t stream) {
+cudaError_t launch_l1_loss(const float *img, const float *target, int64_t count, int64_t mean_count, float *loss,
+                           float *grad, cudaStream_t stream) {
   if (count <= 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 8);
-  return launch_pdl(l1_loss_kernel, (unsigned)blocks, 256u, stream, img, target, count, 1.0f / (float)count, loss,
-                    grad);
+  return launch_pdl(l1_loss_kernel, (unsigned)blocks, 256u, stream, img, target, count, 1.0f / (float)mean_count,
+                    loss, grad);
 }
 
 }  // namespace fgs4d

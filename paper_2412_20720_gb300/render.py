@@ -445,6 +445,50 @@ class FramePipeline:
         return [r.check() for r in self.slots]
 
 
+class ViewParallel:
+    """A batch of views rendered as independent calls on parallel streams.
+
+    Each group of views gets its own Renderer (workspace) and CUDA stream.
+    ``step`` forks from the current stream, runs forward, the caller's loss
+    and backward of every group on that group's stream, and joins back.  The
+    backward passes add into the same gradient buffers (the preprocess
+    adjoint accumulates with atomics, so groups may overlap); the
+    latency-bound binning and sorting of one group run beside the
+    compositing of another."""
+
+    def __init__(self, n: int, view_groups, config: RenderConfig, device=None):
+        import dataclasses
+        self.groups = [Renderer(n, list(g), dataclasses.replace(config), device=device) for g in view_groups]
+        self.device = self.groups[0].device
+        self.streams = [torch.cuda.Stream(self.device) for _ in self.groups]
+
+    def set_tile(self, tile: int, pixels_per_thread: int = 0, shared_batch: int = 0):
+        for r in self.groups:
+            r.set_tile(tile, pixels_per_thread, shared_batch)
+
+    def step(self, params: dict, loss_fn, grads: dict, densify_stats: torch.Tensor | None = None):
+        """For every group j (on its stream): img = forward, dL/dimg =
+        loss_fn(j, img), backward into ``grads``.  Returns the images."""
+        cur = torch.cuda.current_stream(self.device)
+        ev = torch.cuda.Event()
+        ev.record(cur)
+        imgs = []
+        for j, (r, st) in enumerate(zip(self.groups, self.streams)):
+            st.wait_event(ev)
+            with torch.cuda.stream(st):
+                img = r.forward(params)
+                r.backward(params, loss_fn(j, img), grads, densify_stats)
+                imgs.append(img)
+        for st in self.streams:
+            cur.wait_stream(st)
+        for img in imgs:
+            img.record_stream(cur)  # the caller's stream reads them after the join
+        return imgs
+
+    def check(self):
+        return [r.check() for r in self.groups]
+
+
 class Render4DGS(torch.autograd.Function):
     """Differentiable render: (renderer, *params) -> flat RGB [sum 3HW]."""
 
@@ -526,12 +570,22 @@ class Adam:
                               self.betas[0], self.betas[1], self.eps, _ptr(self.t), st)
 
 
-def l1_loss(img: torch.Tensor, target: torch.Tensor):
-    """L1 loss and its gradient with the fgs4d kernel: returns (loss[1], dL/dimg)."""
+def l1_loss(img: torch.Tensor, target: torch.Tensor, mean_count: int | None = None,
+            loss: torch.Tensor | None = None):
+    """L1 loss and its gradient with the fgs4d kernel: returns (loss[1], dL/dimg).
+
+    With ``mean_count`` the call is one part of a loss averaged over
+    ``mean_count`` elements (images rendered by separate calls): the part's
+    sum |img - target| / mean_count is ADDED to ``loss`` (a zeroed float32
+    [1] tensor, created when None) and dL/dimg = sign / mean_count."""
     img = img.contiguous()
     target = target.contiguous()
-    loss = torch.zeros(1, dtype=torch.float32, device=img.device)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=img.device)
     grad = torch.empty_like(img)
-    fgs4d.l1_loss(_ptr(img), _ptr(target), img.numel(), _ptr(loss), _ptr(grad),
-                  torch.cuda.current_stream(img.device).cuda_stream)
+    st = torch.cuda.current_stream(img.device).cuda_stream
+    if mean_count is None:
+        fgs4d.l1_loss(_ptr(img), _ptr(target), img.numel(), _ptr(loss), _ptr(grad), st)
+    else:
+        fgs4d.l1_loss_part(_ptr(img), _ptr(target), img.numel(), int(mean_count), _ptr(loss), _ptr(grad), st)
     return loss, grad

@@ -37,3 +37,41 @@ def test_frames_in_flight_equal_single_frames(depth):
         r.check()
         assert torch.equal(outs[k], ref), "frame %d differs" % k
 
+
+
+def test_view_parallel_step_matches_one_batched_call():
+    """Forward, L1 loss (mean over all views, in parts) and backward of each
+    view on its own stream give the batched call's images bit for bit, and
+    its loss and gradients up to the order of float atomic additions."""
+    import torch
+    from paper_2412_20720_gb300 import synthetic as sy
+    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, ViewParallel, l1_loss
+
+    n = 2500
+    params = sy.make_scene(n, 8, (-1, -1, -1), (1, 1, 1), sh_degree=2, t_order=1).as_dict()
+    tparams = sy.make_scene(n, 9, (-1, -1, -1), (1, 1, 1), sh_degree=2, t_order=1).as_dict()
+    cfg = RenderConfig(sh_degree=2, t_order=1, inst_capacity=1 << 19)
+    views = [sy.tiny_view(120, 88, t=0.2), sy.tiny_view(96, 64, t=0.5), sy.tiny_view(130, 90, t=0.8)]
+    dev, tdev = to_device(params), to_device(tparams)
+    rb = Renderer(n, views, cfg)
+    target = rb.forward(tdev).clone()
+    rb.check()
+    targets = [t.reshape(-1).clone() for t in rb.split(target)]
+    g_ref = {k: torch.zeros_like(dev[k]) for k in PARAM_KEYS}
+    img_ref = rb.forward(dev)
+    loss_ref, dimg = l1_loss(img_ref, target)
+    rb.backward(dev, dimg, g_ref)
+    rb.check()
+
+    vp = ViewParallel(n, [[v] for v in views], cfg)
+    g = {k: torch.zeros_like(dev[k]) for k in PARAM_KEYS}
+    loss = torch.zeros(1, device="cuda")
+    imgs = vp.step(dev, lambda j, img: l1_loss(img, targets[j], mean_count=target.numel(), loss=loss)[1], g)
+    vp.check()
+    for j, img in enumerate(imgs):
+        assert torch.equal(img, rb.split(img_ref)[j].reshape(-1))
+    assert abs(float(loss) - float(loss_ref)) <= 1e-6 * abs(float(loss_ref))
+    for k in PARAM_KEYS:
+        scale = float(g_ref[k].abs().max())
+        assert scale > 0
+        assert float((g[k] - g_ref[k]).abs().max()) <= 1e-4 * scale, k

@@ -70,7 +70,8 @@ def test_view_parallel_step_matches_one_batched_call():
     vp.check()
     for j, img in enumerate(imgs):
         assert torch.equal(img, rb.split(img_ref)[j].reshape(-1))
-    assert abs(float(loss) - float(loss_ref)) <= 1e-6 * abs(float(loss_ref))
+    # float32 sums of ~33k terms in different orders (block partial sums, atomics)
+    assert abs(float(loss) - float(loss_ref)) <= 2e-5 * abs(float(loss_ref))
     for k in PARAM_KEYS:
         scale = float(g_ref[k].abs().max())
         assert scale > 0

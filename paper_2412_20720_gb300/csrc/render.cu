@@ -142,46 +142,68 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs
     if (__syncthreads_count(nlive > 0) == 0) break;
     stage_batch<NT, kBatch>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, range.y, s_geom, s_col,
                     s_blue, nullptr, kAux ? A.rec_aux : nullptr, kAux ? s_aux : nullptr);
-    __syncthreads();
     const int nb = (int)min(range.y - base, (uint32_t)kBatch);
+    // Whether any staged entry can reach the 0.99 clamp (opacity > 0.98, rare):
+    // each thread checks the entries it staged, and the barrier that
+    // publishes the batch ORs the answers.
+    bool my_clamp = false;
+#pragma unroll
+    for (int i = 0; i < kBatch / NT; ++i) {
+      const int k = threadIdx.x + i * NT;
+      if (k < nb) my_clamp = my_clamp || entry_clamps(s_col[k].y);
+    }
+    const bool clamp_any = __syncthreads_or(my_clamp) != 0;
     const uint32_t pos0 = base - range.x + 1u;
-    for (int j = 0; j < nb && nlive > 0; ++j) {
+    // One entry of the list at every pixel of the thread; the clamp case is a
+    // separate copy of the pixel loop.
+    auto entry = [&](int j, auto clamp_tag) {
       const float4 geom = s_geom[j];
       const float4 col = s_col[j];
       const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc, col.y);
-      // One copy of the pixel loop per clamp case, chosen once per entry.
-      auto pixels = [&](auto clamp_tag) {
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          const AlphaEval e = pixel_alpha<decltype(clamp_tag)::value>(ct, geom.y, col.x, pyc[k]);
-          if (kStats) n_eval += T[k] > 0.0f;
-          if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
-            const float w = __fmul_rn(e.alpha, T[k]);
-            const float Tn = __fsub_rn(T[k], w);
-            if (Tn < kTMin) {
-              T[k] = -T[k];
-              pyc[k] = stopped_row();
-              --nlive;
-            } else {
-              C0[k] = __fmaf_rn(col.z, w, C0[k]);
-              C1[k] = __fmaf_rn(col.w, w, C1[k]);
-              C2[k] = __fmaf_rn(blue, w, C2[k]);
-              if (kAux) {
-                const float4 x = s_aux[j];
-                X0[k] = __fmaf_rn(x.x, w, X0[k]);
-                X1[k] = __fmaf_rn(x.y, w, X1[k]);
-                X2[k] = __fmaf_rn(x.z, w, X2[k]);
-              }
-              T[k] = Tn;
-              last[k] = pos0 + (uint32_t)j;
-              if (kStats) ++n_comp;
+      for (int k = 0; k < PPT; ++k) {
+        const AlphaEval e = pixel_alpha<decltype(clamp_tag)::value>(ct, geom.y, col.x, pyc[k]);
+        if (kStats) n_eval += T[k] > 0.0f;
+        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
+          const float w = __fmul_rn(e.alpha, T[k]);
+          const float Tn = __fsub_rn(T[k], w);
+          if (Tn < kTMin) {
+            T[k] = -T[k];
+            pyc[k] = stopped_row();
+            --nlive;
+          } else {
+            C0[k] = __fmaf_rn(col.z, w, C0[k]);
+            C1[k] = __fmaf_rn(col.w, w, C1[k]);
+            C2[k] = __fmaf_rn(blue, w, C2[k]);
+            if (kAux) {
+              const float4 x = s_aux[j];
+              X0[k] = __fmaf_rn(x.x, w, X0[k]);
+              X1[k] = __fmaf_rn(x.y, w, X1[k]);
+              X2[k] = __fmaf_rn(x.z, w, X2[k]);
             }
+            T[k] = Tn;
+            last[k] = pos0 + (uint32_t)j;
+            if (kStats) ++n_comp;
           }
         }
-      };
-      if (entry_clamps(col.y)) pixels(std::true_type());
-      else pixels(std::false_type());
+      }
+    };
+    if (clamp_any) {
+      for (int j = 0; j < nb && nlive > 0; ++j) {
+        if (entry_clamps(s_col[j].y)) entry(j, std::true_type());
+        else entry(j, std::false_type());
+      }
+    } else {
+      // No entry of the batch can clamp: two entries per iteration, the
+      // liveness test once per pair (a pixel that stopped at the first
+      // takes no alpha from the second: its row is +inf).
+      int j = 0;
+      for (; j + 1 < nb && nlive > 0; j += 2) {
+        entry(j, std::false_type());
+        entry(j + 1, std::false_type());
+      }
+      if (j < nb && nlive > 0) entry(j, std::false_type());
     }
   }
   if (kStats) {

@@ -85,6 +85,29 @@ def test_image_matches_oracle(w, h, L, NT, bg):
     check_image(run, params, view, cfg)
 
 
+def _opaque_case():
+    """A tenth of the Gaussians opaque (a = sigmoid(6) > 0.99) and centred at
+    the view's timestamp (p(t) = 1): the 0.99 clamp acts near their centres."""
+    sc = sy.make_scene(2000, 21, (-1, -1, -1), (1, 1, 1), sh_degree=1, t_order=1)
+    view = sy.tiny_view(112, 90, t=0.5)
+    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=1 << 18)
+    params = sc.as_dict()
+    params["opacity_logit"][::10] = 6.0
+    params["mean"][::10, 3] = 0.5
+    return subset(params, keep_clear_of_boundaries(params, [view], cfg)), view, cfg
+
+
+def test_opaque_gaussians_reach_the_clamp():
+    """Image and gradients with entries that reach min(0.99, a G): both the
+    forward's per-batch clamp selection and the backward's constant clamp."""
+    params, view, cfg = _opaque_case()
+    pr = oracle.preprocess(params, view, oracle_settings(cfg))
+    assert (pr["a_eff"][pr["status"] == 0] > 0.99).sum() >= 20
+    run = GpuRun(params, [view], cfg)
+    check_image(run, params, view, cfg)
+    check_gradients(*_grad_case(params, view, cfg))
+
+
 def test_full_size_orbit_view_sampled():
     """The benchmark's launch configuration (300k Gaussians, SH degree 3 x
     temporal order 2, 1352x1014, one view per call): sampled records and

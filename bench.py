@@ -47,10 +47,12 @@ W_IMG, H_IMG = 1352, 1014
 FLOPS_PER_EVAL = 11
 FLOPS_PER_COMP = 9
 # DRAM bytes (read + write) of one compositor launch on this workload, per
-# block shape, from the ncu launch list summarised in
-# profiles/launches_orbit_300k_1352x1014.md; emptied whenever the kernel changes.
+# block shape: the mean over the frames of a 4-view orbit sweep captured by
+# ncu (profiles/launches_orbit_300k_1352x1014.md, traffic section); emptied
+# whenever the kernel changes.
 # keyed by (tile, pixels per thread, shared batch)
-RENDER_FWD_TRAFFIC = {(16, 2, 128): 7.657e6, (16, 2, 256): 7.660e6, (16, 4, 256): 7.193e6}
+RENDER_FWD_TRAFFIC = {(16, 4, 128): 6.974e6, (16, 4, 256): 6.986e6, (16, 2, 128): 6.964e6,
+                      (16, 2, 256): 6.967e6}
 
 
 def parse():
@@ -65,7 +67,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurements")
-    p.add_argument("--inflight", type=int, default=4, help="headline frames in flight (one stream and workspace each)")
+    p.add_argument("--inflight", type=int, default=6, help="headline frames in flight (one stream and workspace each)")
     p.add_argument("--shape", default=None, help="compositor shape tile/pixels_per_thread/shared_batch (e.g. 16/4/128) "
                                                  "instead of the autotune (for profiling a fixed kernel)")
     return p.parse_args()

@@ -139,6 +139,26 @@ def test_calls_reject_missing_or_small_workspace_before_launching():
                                 C.c_void_p(4096), None) == fgs4d.ERR_WORKSPACE
 
 
+def test_l1_loss_part_rejects_a_part_larger_than_its_mean():
+    lib = fgs4d.load()
+    p = C.c_void_p(4096)
+    assert lib.fgs4d_l1_loss_part(p, p, 10, 5, p, p, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_l1_loss_part(p, p, 10, 0, p, p, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_l1_loss_part(None, None, 10, 40, None, None, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_l1_loss_part(None, None, 0, 40, None, None, None) == fgs4d.OK  # empty part: nothing to do
+
+
+def test_bin_sort_kernel_count():
+    """Histogram + 4 depth passes, pair scan, emission, then one tile-sort
+    pass per 8 bits of the tile id (the last records the ranges)."""
+    s = fgs4d.make_settings(sh_degree=1, t_order=1)
+    views, nv = _views()  # 8 x 6 tiles: one tile pass
+    assert fgs4d.bin_sort_kernels(100, views, nv, s) == 1 + 4 + 1 + 1 + 1
+    big, nb = fgs4d.make_views([sy.tiny_view(1352, 1014)])  # 85 x 64 tiles: two passes
+    assert fgs4d.bin_sort_kernels(100, big, nb, s) == 1 + 4 + 1 + 1 + 2
+    assert fgs4d.bin_sort_kernels(0, big, nb, s) == 2  # no visible slot possible: ranges cleared, tile passes
+
+
 def test_status_strings():
     for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert fgs4d.status_string(code) not in ("", "unknown status")

@@ -349,6 +349,22 @@ int fgs4d_l1_loss(const float *img, const float *target, int64_t count, float *l
 int fgs4d_l1_loss_part(const float *img, const float *target, int64_t count, int64_t mean_count, float *loss_out,
                        float *dL_dimg, void *stream);
 
+/* Scratch bytes fgs4d_wait_selftest needs. */
+#define FGS4D_WAIT_SELFTEST_BYTES 4096
+
+/* Diagnostic of the failure detection; no counterpart in the paper.  Runs the
+ * library's two kinds of bounded inter-block wait -- the warp-wide look-back
+ * of the compactions (preprocess, pair scan, emission) and the per-digit
+ * look-back of the radix passes -- in one block against a predecessor that
+ * never posts.  Each wait gives up after its poll limit (about a second),
+ * records the timeout in a status word and returns, so the context stays
+ * usable; the same bit surfaces as FGS4D_ERR_TIMEOUT from fgs4d_get_status in
+ * the render path.  scratch: device memory, at least FGS4D_WAIT_SELFTEST_BYTES,
+ * 16-byte aligned, overwritten.  Synchronises the stream.  Returns
+ * FGS4D_ERR_TIMEOUT when the timeout was recorded (the expected result),
+ * FGS4D_ERR_INTERNAL if it was not, FGS4D_ERR_ARG or FGS4D_ERR_CUDA. */
+int fgs4d_wait_selftest(void *scratch, size_t scratch_bytes, void *stream);
+
 /* Largest key count fgs4d_sort_depth_static accepts. */
 #define FGS4D_STATIC_SORT_MAX (1 << 20)
 

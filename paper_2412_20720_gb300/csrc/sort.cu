@@ -31,6 +31,53 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = kFlagAgg - 1u;
 
+// Decoupled look-back of digit d for radix tile b: publishes the tile's count
+// of the digit, sums the counts of the tiles before it back to the nearest
+// inclusive prefix (reading a window of kWin predecessor tiles per round trip:
+// their words are independent loads), publishes the tile's inclusive prefix
+// and returns the exclusive one.  Flag and value share one word, so relaxed
+// accesses suffice.  A predecessor that never posts makes the wait give up
+// after kSpinLimit polls: the timeout bit is set and the partial prefix
+// returned (the caller's bounds checks keep every store in range).
+__device__ __forceinline__ uint32_t radix_lookback(uint32_t *state, int64_t b, int d, uint32_t cnt, uint32_t *status) {
+  constexpr int kWin = 8;
+  uint32_t prefix = 0u;
+  if (b == 0) {
+    st_relaxed(&state[d], kFlagInc | cnt);
+    return 0u;
+  }
+  st_relaxed(&state[b * kRadixBins + d], kFlagAgg | cnt);
+  int64_t j = b - 1;
+  uint32_t polls = 0;
+  while (j >= 0) {
+    uint32_t w[kWin];
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) w[k] = j - k >= 0 ? ld_relaxed(&state[(j - k) * kRadixBins + d]) : kFlagInc;
+    int used = 0;
+    bool done = false;
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) {
+      if (done || used < k) continue;  // stop at the first tile not yet posted
+      const uint32_t f = w[k] & ~kValMask;
+      if (f == 0u) continue;
+      prefix += w[k] & kValMask;
+      ++used;
+      done = f == kFlagInc;
+    }
+    if (done) break;
+    j -= used;
+    if (used == 0) {
+      if (++polls > kSpinLimit) {
+        atomicOr(status, kStatusTimeout);
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  st_relaxed(&state[b * kRadixBins + d], kFlagInc | ((prefix + cnt) & kValMask));
+  return prefix;
+}
+
 // Digit histograms of keys [0, count) for `passes` 8-bit digits starting at
 // bit 0, grid-stride over radix tiles (kSortThreads x kItems keys); also
 // clears each tile's look-back rows and the tile ranges.
@@ -158,43 +205,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
   uint32_t total;
   s_bstart[d] = block_exclusive_scan(cnt, s_scan, &total);
   const uint32_t gpre = block_exclusive_scan(hist[d], s_scan, &total);
-  // Decoupled look-back for this digit, reading a window of kWin
-  // predecessor tiles per round trip (their words are independent loads).
-  constexpr int kWin = 8;
-  uint32_t prefix = 0u;
-  if (b == 0) {
-    st_relaxed(&state[d], kFlagInc | cnt);
-  } else {
-    st_relaxed(&state[b * kRadixBins + d], kFlagAgg | cnt);
-    int64_t j = b - 1;
-    uint32_t polls = 0;
-    while (j >= 0) {
-      uint32_t w[kWin];
-#pragma unroll
-      for (int k = 0; k < kWin; ++k) w[k] = j - k >= 0 ? ld_relaxed(&state[(j - k) * kRadixBins + d]) : kFlagInc;
-      int used = 0;
-      bool done = false;
-#pragma unroll
-      for (int k = 0; k < kWin; ++k) {
-        if (done || used < k) continue;  // stop at the first tile not yet posted
-        const uint32_t f = w[k] & ~kValMask;
-        if (f == 0u) continue;
-        prefix += w[k] & kValMask;
-        ++used;
-        done = f == kFlagInc;
-      }
-      if (done) break;
-      j -= used;
-      if (used == 0) {
-        if (++polls > kSpinLimit) {
-          atomicOr(status, kStatusTimeout);
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    st_relaxed(&state[b * kRadixBins + d], kFlagInc | ((prefix + cnt) & kValMask));
-  }
+  const uint32_t prefix = radix_lookback(state, b, d, cnt, status);
   s_gstart[d] = gpre + prefix;
   __syncthreads();
   // Block-local order through shared memory, then coalesced runs per digit.
@@ -729,6 +740,46 @@ cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nv
 }
 
 }  // namespace fgs4d
+
+// ---------------------------------------------------------------------------
+// Self-test of the failure detection: the two kinds of bounded inter-block
+// wait run against a predecessor that never posts.  Warp 0 is block 1 of a
+// warp-wide look-back chain (the compactions of preprocess, pair scan and
+// emission); the other warps are radix tile 1 of a digit look-back (the sort
+// passes).  Both give up after kSpinLimit polls, set the timeout bit and
+// return.
+namespace fgs4d {
+namespace {
+
+constexpr size_t kSelftestLb = 0, kSelftestDigits = 256, kSelftestStatus = 256 + 2 * kRadixBins * 4;
+static_assert(kSelftestStatus + 4 <= FGS4D_WAIT_SELFTEST_BYTES, "self-test scratch layout");
+
+__global__ void __launch_bounds__(kRadixBins) wait_selftest_kernel(unsigned char *scratch) {
+  uint64_t *lb = reinterpret_cast<uint64_t *>(scratch + kSelftestLb);
+  uint32_t *digits = reinterpret_cast<uint32_t *>(scratch + kSelftestDigits);
+  uint32_t *status = reinterpret_cast<uint32_t *>(scratch + kSelftestStatus);
+  if (threadIdx.x < 32) (void)lookback_u64_warp(lb, 1, 5ull, status);
+  else (void)radix_lookback(digits, 1, (int)threadIdx.x, 1u, status);
+}
+
+}  // namespace
+}  // namespace fgs4d
+
+extern "C" int fgs4d_wait_selftest(void *scratch, size_t scratch_bytes, void *stream) {
+  using namespace fgs4d;
+  if (!scratch || scratch_bytes < FGS4D_WAIT_SELFTEST_BYTES || (reinterpret_cast<uintptr_t>(scratch) & 15u))
+    return FGS4D_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char *ws = static_cast<unsigned char *>(scratch);
+  if (cudaMemsetAsync(ws, 0, FGS4D_WAIT_SELFTEST_BYTES, st) != cudaSuccess) return FGS4D_ERR_CUDA;
+  wait_selftest_kernel<<<1, kRadixBins, 0, st>>>(ws);
+  if (cudaGetLastError() != cudaSuccess) return FGS4D_ERR_CUDA;
+  uint32_t status = 0;
+  if (cudaMemcpyAsync(&status, ws + kSelftestStatus, sizeof status, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FGS4D_ERR_CUDA;
+  return (status & kStatusTimeout) ? FGS4D_ERR_TIMEOUT : FGS4D_ERR_INTERNAL;
+}
 
 // ---------------------------------------------------------------------------
 // Depth sort that allocates nothing: fgs4d_sort_depth_static.

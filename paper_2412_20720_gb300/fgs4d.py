@@ -29,7 +29,7 @@ MAX_T_ORDER = 4
 TILE = 16  # default tile edge; 8 is the other supported size
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort", "fgs4d_bin_sort_kernels",
-            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_l1_loss_part", "fgs4d_sort_depth_static", "fgs4d_get_status",
+            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_l1_loss_part", "fgs4d_sort_depth_static", "fgs4d_wait_selftest", "fgs4d_get_status",
             "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 
@@ -122,6 +122,7 @@ def load():
     lib.fgs4d_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.fgs4d_l1_loss_part.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     lib.fgs4d_sort_depth_static.argtypes = [vp, i64, vp, vp]
+    lib.fgs4d_wait_selftest.argtypes = [vp, C.c_size_t, vp]
     lib.fgs4d_get_status.argtypes = [vp, C.c_size_t, vp, P(C.c_int64)]
     lib.fgs4d_status_string.argtypes = [C.c_int]
     lib.fgs4d_status_string.restype = C.c_char_p
@@ -290,6 +291,15 @@ def l1_loss(img: int, target: int, count: int, loss_out: int, dL_dimg: int, stre
 def l1_loss_part(img: int, target: int, count: int, mean_count: int, loss_out: int, dL_dimg: int, stream: int):
     _check(load().fgs4d_l1_loss_part(img, target, int(count), int(mean_count), loss_out, dL_dimg, stream),
            "fgs4d_l1_loss_part")
+
+
+WAIT_SELFTEST_BYTES = 4096
+
+
+def wait_selftest(scratch: int, scratch_bytes: int, stream: int) -> int:
+    """Runs the bounded-wait self-test; returns the status code (ERR_TIMEOUT
+    is the expected result)."""
+    return int(load().fgs4d_wait_selftest(scratch, int(scratch_bytes), stream))
 
 
 def sort_depth_static(depth_keys: int, n: int, sorted_slots: int, stream: int):

@@ -159,6 +159,14 @@ def test_bin_sort_kernel_count():
     assert fgs4d.bin_sort_kernels(0, big, nb, s) == 2  # no visible slot possible: ranges cleared, tile passes
 
 
+def test_wait_selftest_rejects_bad_scratch_before_launching():
+    lib = fgs4d.load()
+    n = fgs4d.WAIT_SELFTEST_BYTES
+    assert lib.fgs4d_wait_selftest(None, n, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_wait_selftest(C.c_void_p(4096), n - 4, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_wait_selftest(C.c_void_p(4096 + 4), n, None) == fgs4d.ERR_ARG
+
+
 def test_status_strings():
     for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert fgs4d.status_string(code) not in ("", "unknown status")

@@ -17,7 +17,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .build import build_oracle, library_path
+from .build import build_oracle, build_oracle_sanitized, library_path
 
 _lib = None
 
@@ -25,7 +25,8 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        path = build_oracle()  # no-op when the library is newer than its source
+        # no-op when the library is newer than its source
+        path = build_oracle_sanitized() if os.environ.get("FGS4D_ORACLE_SANITIZED") == "1" else build_oracle()
         _lib = C.CDLL(path)
         _declare(_lib)
     return _lib

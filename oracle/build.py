@@ -30,5 +30,28 @@ def build_oracle(force: bool = False) -> str:
     return out
 
 
+def sanitized_library_path() -> str:
+    return os.path.join(_HERE, "_build", "liboracle_san.so")
+
+
+def build_oracle_sanitized(force: bool = False) -> str:
+    """The same library built with AddressSanitizer and UndefinedBehavior-
+    Sanitizer (every finding aborts), for the sanitizer test; loaded instead
+    of the plain build when FGS4D_ORACLE_SANITIZED=1 (the process must
+    preload libasan, as the interpreter is not instrumented)."""
+    src = os.path.join(_HERE, "fgs4d_oracle.c")
+    out = sanitized_library_path()
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O1", "-g", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-Wall", "-Wextra",
+           "-fsanitize=address,undefined", "-fno-sanitize-recover=all", "-fno-omit-frame-pointer",
+           "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 if __name__ == "__main__":
     print(build_oracle(force=True))

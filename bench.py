@@ -4,8 +4,9 @@
 Headline workload (one step): 300,000 synthetic 4D Gaussians (spatial SH
 degree 3 x temporal order 2) over [-3,3]^3 x [0,1], rendered at 1352x1014 from
 an orbit camera of radius 6 for the 300 timestamps t_k = k/299 of a sweep,
-one view per call (plain form): preprocess -> bin_sort -> render_fwd through
-the C ABI for every view, with --inflight frames in flight (FramePipeline: one
+one view per call (plain form): preprocess -> bin_sort -> render_image (the
+forward compositor without the state a backward pass needs) through the C
+ABI for every view, with --inflight frames in flight (FramePipeline: one
 workspace and one stream per slot, frame k on slot k % inflight).  value =
 rendered frames/s over all ranks.
 
@@ -311,7 +312,7 @@ def run_ours(args, rank, world, local):
         ev4[k][1].record(stream)
         fgs4d.bin_sort(scene.n, v, n1, s, ws, wsb, st)
         ev4[k][2].record(stream)
-        fgs4d.render_fwd(scene.n, v, n1, s, ws, wsb, imgs[0].data_ptr(), None, st)
+        fgs4d.render_image(scene.n, v, n1, s, ws, wsb, imgs[0].data_ptr(), None, st)
         ev4[k][3].record(stream)
     torch.cuda.synchronize()
     for e4 in ev4:
@@ -400,7 +401,7 @@ def run_ours(args, rank, world, local):
                                     "basis": "one frame in flight: a separate untimed pass over the sweep"},
             "work_per_frame": {"visible": float(np.mean(vis)), "instances": float(np.mean(inst)),
                                "alpha_evals": float(np.mean(evals)), "composited": float(np.mean(comps))},
-            "roofline": {"kernel": "render_fwd", "bound": "alu", "achieved": achieved_timed, "peak": fp32_peak,
+            "roofline": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu", "achieved": achieved_timed, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved_timed / fp32_peak,
                          "traffic": RENDER_FWD_TRAFFIC.get((tuned["tile"], tuned["pixels_per_thread"],
                                                             tuned["shared_batch"])),
@@ -408,7 +409,7 @@ def run_ours(args, rank, world, local):
                          "flops_per_launch": mean_flops, "launch_ms": comp_ms_timed,
                          "duration_basis": "CUDA events around each compositor launch on its slot stream in the "
                                            "timed region (other frames' kernels share the GPU meanwhile)"},
-            "roofline_isolated": {"kernel": "render_fwd", "bound": "alu", "achieved": achieved_iso,
+            "roofline_isolated": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu", "achieved": achieved_iso,
                                   "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved_iso / fp32_peak,
                                   "launch_ms": float(stage_ms[2]),
                                   "duration_basis": "one frame in flight (the per-stage pass)"},

@@ -216,6 +216,15 @@ int fgs4d_bin_sort_kernels(int64_t n, const fgs4d_view *views, int32_t nviews, c
 int fgs4d_render_fwd(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
                      void *workspace, size_t workspace_bytes, float *out_rgb, float *out_T, void *stream);
 
+/* fgs4d_render_fwd for a render that no backward pass follows (a viewer, an
+ * evaluation sweep): the same image and final transmittance bit for bit, but
+ * the compositor does not track each pixel's last contributing entry, which
+ * only fgs4d_render_bwd needs; that plane of the workspace is written as 0,
+ * so a backward call after this one adds zero gradients.  No counterpart in
+ * the paper (a rendering mode of the same Eq. 6). */
+int fgs4d_render_image(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                       void *workspace, size_t workspace_bytes, float *out_rgb, float *out_T, void *stream);
+
 /* Auxiliary channels (depth, opacity, optical flow) with the image.
  * Depth and flow are blended with the colour weights of Eq. 6,
  * w_i = alpha_i T_i: depth = sum w_i z_i with z_i the camera-space depth of

@@ -258,6 +258,18 @@ int fgs4d_render_fwd(int64_t n, const fgs4d_view *views, int32_t nviews, const f
                                        out_T, nullptr, nullptr, static_cast<cudaStream_t>(stream)));
 }
 
+int fgs4d_render_image(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                       void *workspace, size_t workspace_bytes, float *out_rgb, float *out_T, void *stream) {
+  Layout L;
+  int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  if (!out_rgb) return FGS4D_ERR_ARG;
+  return cuda_status(launch_render_fwd(L, settings, views, nviews, static_cast<unsigned char *>(workspace), out_rgb,
+                                       out_T, nullptr, nullptr, static_cast<cudaStream_t>(stream), true));
+}
+
 int fgs4d_render_aux(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
                      const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, float flow_dt,
                      float *out_rgb, float *out_T, float *out_aux, void *stream) {

@@ -414,9 +414,10 @@ cudaError_t launch_bin_sort(const Layout &L, const fgs4d_view *views, int32_t nv
                             cudaStream_t stream);
 // Kernel launches launch_bin_sort makes for this layout on the current device.
 int bin_sort_kernel_count(const Layout &L, int32_t nviews);
+// image_only: no last-contributor index is tracked (fgs4d_render_image).
 cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
-                              float *out_aux, cudaStream_t stream);
+                              float *out_aux, cudaStream_t stream, bool image_only = false);
 bool feature_dim_supported(int32_t D);
 cudaError_t launch_render_features(const Layout &L, const fgs4d_view *views, int32_t nviews, unsigned char *ws,
                                    int64_t n, const float *feat, int32_t D, const float *gate, float *out,

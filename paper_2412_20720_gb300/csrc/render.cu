@@ -96,7 +96,9 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
   }
 }
 
-// kMode 0: image; 1 (kStats): also counts the pixel-entry alpha evaluations
+// kMode 0: image (and the per-pixel state of the backward pass); 3: image
+// only -- no last-contributor index is tracked (the plane is written as 0);
+// 1 (kStats): also counts the pixel-entry alpha evaluations
 // and the composited entries (diagnostic variant used to state the
 // algorithmic work); 2 (kAux): also blends the per-slot depth and flow with
 // the colour weights and writes depth, opacity 1 - T and flow planes.
@@ -109,7 +111,7 @@ template <int MAXV, int TILE, int PPT, int kMode, int kBatch>
 __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
                                                                       unsigned long long *stats) {
   grid_dependency_sync();
-  constexpr bool kStats = kMode == 1, kAux = kMode == 2;
+  constexpr bool kStats = kMode == 1, kAux = kMode == 2, kTrack = kMode != 3;
   constexpr int NT = TILE * TILE / PPT;
   __shared__ float4 s_geom[kBatch];
   __shared__ float4 s_col[kBatch];
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs
               X2[k] = __fmaf_rn(x.z, w, X2[k]);
             }
             T[k] = Tn;
-            last[k] = pos0 + (uint32_t)j;
+            if (kTrack) last[k] = pos0 + (uint32_t)j;
             if (kStats) ++n_comp;
           }
         }
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs
     img[HW + p] = C1[k] + Tend * A.bg1;
     img[2 * HW + p] = C2[k] + Tend * A.bg2;
     A.pix_T[V.pix_base + p] = Tend;
-    A.pix_last[V.pix_base + p] = last[k];
+    A.pix_last[V.pix_base + p] = kTrack ? last[k] : 0u;
     if (A.out_T) A.out_T[V.pix_base + p] = Tend;
     if (kAux) {
       float *aux = A.out_aux + V.pix_base * 4;
@@ -507,8 +509,10 @@ __global__ void mask_loss_kernel(const float *__restrict__ m, int64_t n, float i
 
 template <int MAXV, int TILE, int PPT, int B>
 cudaError_t launch_fwd_batch(const RenderArgs &A, const RasterViews<MAXV> &rv, unsigned grid,
-                             unsigned long long *stats, cudaStream_t st) {
+                             unsigned long long *stats, bool image_only, cudaStream_t st) {
   constexpr unsigned NT = TILE * TILE / PPT;
+  if (image_only)
+    return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 3, B>, grid, NT, st, A, rv, (unsigned long long *)nullptr);
   if (stats) return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 1, B>, grid, NT, st, A, rv, stats);
   if (A.out_aux)
     return launch_pdl(render_fwd_kernel<MAXV, TILE, PPT, 2, B>, grid, NT, st, A, rv, (unsigned long long *)nullptr);
@@ -517,15 +521,15 @@ cudaError_t launch_fwd_batch(const RenderArgs &A, const RasterViews<MAXV> &rv, u
 
 template <int MAXV, int TILE, int PPT>
 cudaError_t launch_fwd_ppt(const RenderArgs &A, const RasterViews<MAXV> &rv, unsigned grid,
-                           unsigned long long *stats, int batch, cudaStream_t st) {
-  if (batch == 128) return launch_fwd_batch<MAXV, TILE, PPT, 128>(A, rv, grid, stats, st);
-  return launch_fwd_batch<MAXV, TILE, PPT, 256>(A, rv, grid, stats, st);
+                           unsigned long long *stats, int batch, bool image_only, cudaStream_t st) {
+  if (batch == 128) return launch_fwd_batch<MAXV, TILE, PPT, 128>(A, rv, grid, stats, image_only, st);
+  return launch_fwd_batch<MAXV, TILE, PPT, 256>(A, rv, grid, stats, image_only, st);
 }
 
 template <int MAXV>
 cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                              unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
-                             float *out_aux, cudaStream_t st) {
+                             float *out_aux, bool image_only, cudaStream_t st) {
   RasterViews<MAXV> rv;
   if (!make_raster_views<MAXV>(L, views, nviews, &rv)) return cudaErrorInvalidValue;
   RenderArgs A;
@@ -547,13 +551,13 @@ cudaError_t render_fwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
   if (L.total_tiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)L.total_tiles;
   if (s->tile == 8) {
-    if (render_ppt(s) == 1) return launch_fwd_ppt<MAXV, 8, 1>(A, rv, grid, stats, s->shared_batch, st);
-    return launch_fwd_ppt<MAXV, 8, 2>(A, rv, grid, stats, s->shared_batch, st);
+    if (render_ppt(s) == 1) return launch_fwd_ppt<MAXV, 8, 1>(A, rv, grid, stats, s->shared_batch, image_only, st);
+    return launch_fwd_ppt<MAXV, 8, 2>(A, rv, grid, stats, s->shared_batch, image_only, st);
   }
   switch (render_ppt(s)) {
-    case 2: return launch_fwd_ppt<MAXV, 16, 2>(A, rv, grid, stats, s->shared_batch, st);
-    case 8: return launch_fwd_ppt<MAXV, 16, 8>(A, rv, grid, stats, s->shared_batch, st);
-    default: return launch_fwd_ppt<MAXV, 16, 4>(A, rv, grid, stats, s->shared_batch, st);
+    case 2: return launch_fwd_ppt<MAXV, 16, 2>(A, rv, grid, stats, s->shared_batch, image_only, st);
+    case 8: return launch_fwd_ppt<MAXV, 16, 8>(A, rv, grid, stats, s->shared_batch, image_only, st);
+    default: return launch_fwd_ppt<MAXV, 16, 4>(A, rv, grid, stats, s->shared_batch, image_only, st);
   }
 }
 
@@ -611,9 +615,11 @@ cudaError_t render_bwd_typed(const Layout &L, const fgs4d_settings *s, const fgs
 
 cudaError_t launch_render_fwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,
                               unsigned char *ws, float *out_rgb, float *out_T, unsigned long long *stats,
-                              float *out_aux, cudaStream_t stream) {
-  if (nviews == 1) return render_fwd_typed<1>(L, s, views, nviews, ws, out_rgb, out_T, stats, out_aux, stream);
-  return render_fwd_typed<FGS4D_MAX_VIEWS>(L, s, views, nviews, ws, out_rgb, out_T, stats, out_aux, stream);
+                              float *out_aux, cudaStream_t stream, bool image_only) {
+  if (nviews == 1)
+    return render_fwd_typed<1>(L, s, views, nviews, ws, out_rgb, out_T, stats, out_aux, image_only, stream);
+  return render_fwd_typed<FGS4D_MAX_VIEWS>(L, s, views, nviews, ws, out_rgb, out_T, stats, out_aux, image_only,
+                                           stream);
 }
 
 cudaError_t launch_render_bwd(const Layout &L, const fgs4d_settings *s, const fgs4d_view *views, int32_t nviews,

@@ -29,7 +29,7 @@ MAX_T_ORDER = 4
 TILE = 16  # default tile edge; 8 is the other supported size
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort", "fgs4d_bin_sort_kernels",
-            "fgs4d_render_fwd", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_l1_loss_part", "fgs4d_sort_depth_static", "fgs4d_wait_selftest", "fgs4d_get_status",
+            "fgs4d_render_fwd", "fgs4d_render_image", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_l1_loss_part", "fgs4d_sort_depth_static", "fgs4d_wait_selftest", "fgs4d_get_status",
             "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 
@@ -105,6 +105,7 @@ def load():
     lib.fgs4d_bin_sort.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp]
     lib.fgs4d_bin_sort_kernels.argtypes = [i64, P(View), i32, P(Settings), P(C.c_int32)]
     lib.fgs4d_render_fwd.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, vp, vp]
+    lib.fgs4d_render_image.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, vp, vp]
     lib.fgs4d_render_aux.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, C.c_float, vp, vp,
                                      vp, vp]
     lib.fgs4d_render_stats.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, vp, vp]
@@ -226,6 +227,12 @@ def bin_sort(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: 
 def render_fwd(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, out_rgb: int, out_T, stream):
     _check(load().fgs4d_render_fwd(int(n), views, int(nviews), C.byref(settings), ws, ws_bytes, out_rgb, out_T,
                                    stream), "fgs4d_render_fwd")
+
+
+def render_image(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, out_rgb: int, out_T,
+                 stream):
+    _check(load().fgs4d_render_image(int(n), views, int(nviews), C.byref(settings), ws, ws_bytes, out_rgb, out_T,
+                                     stream), "fgs4d_render_image")
 
 
 def render_aux(gaussians: Gaussians, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, flow_dt: float,

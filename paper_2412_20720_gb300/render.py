@@ -414,12 +414,14 @@ class FramePipeline:
         return self._next % self.depth
 
     def submit(self, g: fgs4d.Gaussians, views, nviews: int, out_rgb: int, out_T: int | None = None,
-               events=None, after=None) -> int:
+               events=None, after=None, image_only: bool = True) -> int:
         """Launches one frame (views, nviews from fgs4d.make_views) on the
         next slot; ``g`` from any slot's gaussians().  ``events`` = (e0, e1)
         are recorded around the compositor launch, ``after(stream)`` is
         called on the slot stream after it (e.g. to enqueue a copy of the
-        output).  Returns the slot index."""
+        output).  ``image_only`` (default) renders with fgs4d_render_image
+        (no state for a backward pass is kept); False uses fgs4d_render_fwd.
+        Returns the slot index."""
         j = self._next % self.depth
         self._next += 1
         r, st = self.slots[j], self.streams[j]
@@ -428,7 +430,7 @@ class FramePipeline:
         fgs4d.bin_sort(r.n, views, nviews, s, ws, wsb, sp)
         if events is not None:
             events[0].record(st)
-        fgs4d.render_fwd(r.n, views, nviews, s, ws, wsb, out_rgb, out_T, sp)
+        (fgs4d.render_image if image_only else fgs4d.render_fwd)(r.n, views, nviews, s, ws, wsb, out_rgb, out_T, sp)
         if events is not None:
             events[1].record(st)
         if after is not None:

@@ -76,3 +76,34 @@ def test_view_parallel_step_matches_one_batched_call():
         scale = float(g_ref[k].abs().max())
         assert scale > 0
         assert float((g[k] - g_ref[k]).abs().max()) <= 1e-4 * scale, k
+
+
+@pytest.mark.parametrize("tile,ppt,batch", [(16, 4, 128), (16, 2, 256), (8, 1, 128)])
+def test_render_image_equals_render_fwd(tile, ppt, batch):
+    """fgs4d_render_image (no backward state) gives fgs4d_render_fwd's image
+    and final transmittance bit for bit and leaves the last-index plane 0."""
+    import torch
+    from paper_2412_20720_gb300 import fgs4d
+    from paper_2412_20720_gb300 import synthetic as sy
+    from paper_2412_20720_gb300.render import RenderConfig, Renderer
+
+    n = 3000
+    params = sy.make_scene(n, 13, (-1, -1, -1), (1, 1, 1), sh_degree=2, t_order=1).as_dict()
+    cfg = RenderConfig(sh_degree=2, t_order=1, inst_capacity=1 << 19, tile=tile, pixels_per_thread=ppt,
+                       shared_batch=batch, bg=(0.1, 0.2, 0.3))
+    views = [sy.tiny_view(150, 97, t=0.3), sy.tiny_view(64, 40, t=0.7)]
+    r = Renderer(n, views, cfg)
+    dev = to_device(params)
+    ref = r.forward(dev)
+    r.check()
+    npx = r.total_pixels
+    T_ref = r.workspace_view(r.layout.pix_T, torch.float32, npx).clone()
+    assert int(r.workspace_view(r.layout.pix_last, torch.int32, npx).max()) > 0
+    out = torch.empty_like(ref)
+    out_T = torch.empty(npx, device="cuda")
+    fgs4d.render_image(n, r.views, r.nviews, r.settings, r.ws.data_ptr(), r.ws_bytes, out.data_ptr(),
+                       out_T.data_ptr(), r.stream())
+    r.check()
+    assert torch.equal(out, ref)
+    assert torch.equal(out_T, T_ref)
+    assert int(r.workspace_view(r.layout.pix_last, torch.int32, npx).abs().max()) == 0

@@ -47,12 +47,12 @@ W_IMG, H_IMG = 1352, 1014
 # alpha*T (1), three colour multiply-adds (6) = 9.  The ex2 goes to the SFU.
 FLOPS_PER_EVAL = 11
 FLOPS_PER_COMP = 9
-# DRAM bytes (read + write) of one compositor launch on this workload, per
-# block shape: the mean over the frames of a 4-view orbit sweep captured by
+# DRAM bytes (read + write) of one image-mode compositor launch on this
+# workload, per block shape: the mean over the frames of a 4-view orbit sweep captured by
 # ncu (profiles/launches_orbit_300k_1352x1014.md, traffic section); emptied
 # whenever the kernel changes.
 # keyed by (tile, pixels per thread, shared batch)
-RENDER_FWD_TRAFFIC = {(16, 4, 128): 6.974e6, (16, 4, 256): 6.986e6, (16, 2, 128): 6.964e6,
+RENDER_FWD_TRAFFIC = {(16, 4, 128): 6.970e6, (16, 4, 256): 6.980e6, (16, 2, 128): 6.963e6,
                       (16, 2, 256): 6.967e6}
 
 

@@ -59,7 +59,7 @@ RENDER_FWD_TRAFFIC = {(16, 4, 128): 6.970e6, (16, 4, 256): 6.980e6, (16, 2, 128)
 def parse():
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--n", type=int, default=N_GAUSS, help="Gaussians (default: the headline 300k)")

@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurements")
     p.add_argument("--inflight", type=int, default=6, help="headline frames in flight (one stream and workspace each)")
+    p.add_argument("--stage-blocks", type=int, default=1,
+                   help="resident blocks per SM of the latency-bound stages (0 = full-GPU grids)")
     p.add_argument("--shape", default=None, help="compositor shape tile/pixels_per_thread/shared_batch (e.g. 16/4/128) "
                                                  "instead of the autotune (for profiling a fixed kernel)")
     return p.parse_args()
@@ -225,7 +227,10 @@ def run_ours(args, rank, world, local):
     params = {k: torch.from_numpy(host[k]).to(dev) for k in PARAM_KEYS}
     nviews = args.views
     views = [sy.orbit_view(k, nviews, W_IMG, H_IMG) for k in range(nviews)]
-    cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24)
+    # Lean grids for the latency-bound stages (one resident preprocess and
+    # radix block per SM, two emission blocks): the frames in flight share
+    # the SMs.
+    cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24, stage_blocks_per_sm=args.stage_blocks)
     # One view per call; args.inflight frames in flight (one workspace and one
     # stream per slot), frame k on slot k % inflight.
     pipe = FramePipeline(scene.n, views[0], cfg, depth=args.inflight, device=dev)
@@ -301,23 +306,35 @@ def run_ours(args, rank, world, local):
     ms_max = max_over_ranks(ms, world, dev)
     value = job_rate(K * nviews, world, ms_max)
 
-    # Per-stage durations with one frame in flight (a separate, untimed pass
-    # over the sweep on one stream, events between the stages).
-    stage_ms = np.zeros(3)
-    ev4 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nviews)]
-    for k in range(nviews):
-        v, n1 = vv[k]
-        ev4[k][0].record(stream)
-        fgs4d.preprocess(g, v, n1, s, ws, wsb, st)
-        ev4[k][1].record(stream)
-        fgs4d.bin_sort(scene.n, v, n1, s, ws, wsb, st)
-        ev4[k][2].record(stream)
-        fgs4d.render_image(scene.n, v, n1, s, ws, wsb, imgs[0].data_ptr(), None, st)
-        ev4[k][3].record(stream)
-    torch.cuda.synchronize()
-    for e4 in ev4:
-        stage_ms += [e4[0].elapsed_time(e4[1]), e4[1].elapsed_time(e4[2]), e4[2].elapsed_time(e4[3])]
-    stage_ms /= nviews
+    # Per-stage durations with one frame in flight (separate, untimed passes
+    # over the sweep on one stream, events between the stages): with the
+    # timed configuration, and with full-GPU grids for the latency-bound
+    # stages (the same workspace layout), from which the kernels' rooflines
+    # are taken.
+    def stage_pass(settings):
+        acc = np.zeros(3)
+        ev4 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nviews)]
+        for k in range(nviews):
+            v, n1 = vv[k]
+            ev4[k][0].record(stream)
+            fgs4d.preprocess(g, v, n1, settings, ws, wsb, st)
+            ev4[k][1].record(stream)
+            fgs4d.bin_sort(scene.n, v, n1, settings, ws, wsb, st)
+            ev4[k][2].record(stream)
+            fgs4d.render_image(scene.n, v, n1, settings, ws, wsb, imgs[0].data_ptr(), None, st)
+            ev4[k][3].record(stream)
+        torch.cuda.synchronize()
+        for e4 in ev4:
+            acc += [e4[0].elapsed_time(e4[1]), e4[1].elapsed_time(e4[2]), e4[2].elapsed_time(e4[3])]
+        return acc / nviews
+
+    stage_ms = stage_pass(s)
+    s_full = fgs4d.Settings.from_buffer_copy(s)
+    s_full.stage_blocks_per_sm = 0
+    stage_full = stage_pass(s_full)
+    code, _ = r.status()
+    if code != fgs4d.OK:
+        raise RuntimeError("per-stage passes: %s" % fgs4d.status_string(code))
 
     # Roofline of the dominant kernel (the compositor): FP32-ALU bound.
     props = torch.cuda.get_device_properties(dev)
@@ -326,10 +343,10 @@ def run_ours(args, rank, world, local):
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     mean_flops = FLOPS_PER_EVAL * np.mean(evals) + FLOPS_PER_COMP * np.mean(comps)
     achieved_timed = mean_flops / (comp_ms_timed * 1e-3) / 1e12
-    achieved_iso = mean_flops / (stage_ms[2] * 1e-3) / 1e12
+    achieved_iso = mean_flops / (stage_full[2] * 1e-3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     pre_bytes = 68.0 * scene.n + (576.0 + 56.0) * np.mean(vis)
-    pre_gbs = pre_bytes / (stage_ms[0] * 1e-3) / 1e9
+    pre_gbs = pre_bytes / (stage_full[0] * 1e-3) / 1e9
 
     # ---------------------------------------------------------- e2e
     e2e = None
@@ -392,13 +409,19 @@ def run_ours(args, rank, world, local):
             "config": {"workload": WORKLOAD, "gaussians": args.n, "sh_degree": 3, "t_order": 2,
                        "resolution": [W_IMG, H_IMG], "views_per_step": nviews, "views_per_call": 1,
                        "vis_capacity": vis_cap, "frames_in_flight": pipe.depth,
+                       "stage_blocks_per_sm": args.stage_blocks,
                        "l2": "inputs larger than L2 (193 MB of parameters vs 129 MB L2); no flush",
                        "parallelism": "views replicated per GPU" if world > 1 else "single GPU"},
             "gpu_launches": launches_per_frame * nviews * K,
             "frames_in_flight": pipe.depth,
             "autotune": tuned,
             "stages_ms_per_frame": {"preprocess": stage_ms[0], "bin_sort": stage_ms[1], "render_fwd": stage_ms[2],
-                                    "basis": "one frame in flight: a separate untimed pass over the sweep"},
+                                    "basis": "one frame in flight, the timed configuration: a separate untimed "
+                                             "pass over the sweep"},
+            "stages_ms_per_frame_full_grids": {"preprocess": stage_full[0], "bin_sort": stage_full[1],
+                                               "render_fwd": stage_full[2],
+                                               "basis": "one frame in flight, stage_blocks_per_sm = 0 (full-GPU "
+                                                        "grids for preprocess, sorting and emission)"},
             "work_per_frame": {"visible": float(np.mean(vis)), "instances": float(np.mean(inst)),
                                "alpha_evals": float(np.mean(evals)), "composited": float(np.mean(comps))},
             "roofline": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu", "achieved": achieved_timed, "peak": fp32_peak,
@@ -411,10 +434,11 @@ def run_ours(args, rank, world, local):
                                            "timed region (other frames' kernels share the GPU meanwhile)"},
             "roofline_isolated": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu", "achieved": achieved_iso,
                                   "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved_iso / fp32_peak,
-                                  "launch_ms": float(stage_ms[2]),
-                                  "duration_basis": "one frame in flight (the per-stage pass)"},
+                                  "launch_ms": float(stage_full[2]),
+                                  "duration_basis": "one frame in flight (the full-grid per-stage pass)"},
             "preprocess_roofline": {"bound": "hbm", "achieved": pre_gbs, "peak": hbm, "unit": "GB/s",
                                     "frac": pre_gbs / hbm, "bytes_per_launch": pre_bytes,
+                                    "duration_basis": "one frame in flight, full-GPU grid",
                                     "peak_basis": "measured hbm_gbs"},
             "clocks": clk,
             "e2e": e2e,
@@ -441,6 +465,8 @@ def run_train(args, dev, scene, params, world, barrier):
                                                l1_loss)
 
     views = sy.train_views(4, W_IMG, H_IMG)
+    # The 4-view call runs alone on the GPU: full-GPU grids.  The view-parallel
+    # form runs four calls at once: lean grids for their latency-bound stages.
     cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 25)
     tgt_scene = sy.orbit_scene(args.n, seed=sy.TARGET_SEED)
     tparams = {k: torch.from_numpy(v).to(dev) for k, v in tgt_scene.as_dict().items()}
@@ -452,7 +478,8 @@ def run_train(args, dev, scene, params, world, barrier):
     leaf = {k: params[k].clone().requires_grad_(True) for k in PARAM_KEYS}
     r = Renderer(scene.n, views, cfg, device=dev)
     tuned = autotune(r, {k: leaf[k].detach() for k in PARAM_KEYS}, backward=True, tiles=(16, 8), batches=(256, 128))
-    vp = ViewParallel(scene.n, [[v] for v in views], RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24),
+    vp = ViewParallel(scene.n, [[v] for v in views],
+                      RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24, stage_blocks_per_sm=args.stage_blocks),
                       device=dev)
     vp.set_tile(tuned["tile"], tuned["pixels_per_thread"], tuned["shared_batch"])
     grads = {k: torch.zeros_like(leaf[k]) for k in PARAM_KEYS}

@@ -87,6 +87,11 @@ typedef struct fgs4d_settings {
   int32_t pixels_per_thread; /* compositor block shape: 0 (default 4), 2, 4 or 8 pixels
                                 of one tile column per thread; results are identical */
   int32_t shared_batch;      /* records the compositors stage per shared-memory batch: 0 (= 256), 128 or 256 */
+  int32_t stage_blocks_per_sm; /* grids of the latency-bound stages: 0 = full-GPU grids (the lowest
+                                  latency for one frame alone); k in 1..8 = at most k resident blocks
+                                  per SM for preprocess and the radix passes and 2k for the instance
+                                  emission, leaving SMs to other work on the GPU (frames or views
+                                  rendered concurrently on other streams); results are identical */
 } fgs4d_settings;
 
 /* Gaussian parameters (device pointers, layout in the header comment). */

@@ -38,6 +38,7 @@ int check_settings(const fgs4d_settings *s) {
   if (ppt != 0 && !(s->tile == 16 ? (ppt == 2 || ppt == 4 || ppt == 8) : (ppt == 1 || ppt == 2)))
     return FGS4D_ERR_UNSUPPORTED;
   if (s->shared_batch != 0 && s->shared_batch != 128 && s->shared_batch != 256) return FGS4D_ERR_UNSUPPORTED;
+  if (s->stage_blocks_per_sm < 0 || s->stage_blocks_per_sm > 8) return FGS4D_ERR_UNSUPPORTED;
   return FGS4D_OK;
 }
 
@@ -115,7 +116,13 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   L.emit_blocks = (int32_t)((L.vis_cap + kEmitBlock - 1) / kEmitBlock);
   L.pair_cap = std::min<int64_t>(8 * L.inst_cap, (int64_t)INT32_MAX);
   L.chunk_cap = (int32_t)((L.pair_cap + kEmitChunk - 1) / kEmitChunk);
-  L.emit_grid = std::max(1, std::min(L.chunk_cap, 152 * 8));
+  // Grids of the latency-bound stages (152 SMs): full-GPU by default, or at
+  // most k blocks per SM for preprocess and the radix passes and 2k for the
+  // emission when other work shares the GPU (stage_blocks_per_sm = k).
+  const int k = s->stage_blocks_per_sm;
+  L.pre_grid = k ? std::min(L.pre_blocks, 152 * k) : L.pre_blocks;
+  L.sort_grid = 152 * (k ? k : 4);
+  L.emit_grid = std::max(1, std::min(L.chunk_cap, 152 * (k ? 2 * k : 8)));
   L.depth_blocks = (int32_t)((L.vis_cap + kDepthSortTile - 1) / kDepthSortTile);
   L.tile_blocks = (int32_t)((L.inst_cap + kInstSortTile - 1) / kInstSortTile);
 

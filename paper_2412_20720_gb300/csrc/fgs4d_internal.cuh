@@ -119,6 +119,8 @@ struct Layout {
   int64_t pair_cap;       // max (slot, rect tile) pairs: 8 x inst_cap, at most 2^31 - 1
   int32_t chunk_cap;      // emission chunks of kEmitChunk pairs
   int32_t emit_grid;      // persistent emission blocks
+  int32_t pre_grid;       // persistent preprocess blocks
+  int32_t sort_grid;      // persistent radix-pass blocks (at most; one radix tile each at least)
   int32_t depth_blocks, tile_blocks;
   int32_t depth_passes, tile_passes;
   int32_t tile_bits;

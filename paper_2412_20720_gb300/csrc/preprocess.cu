@@ -335,9 +335,15 @@ __global__ void __launch_bounds__(kPreBlock) preprocess_kernel(PreArgs A, PreVie
   __shared__ uint32_t s_ticket;
   __shared__ uint32_t s_scan[9];
   __shared__ uint64_t s_base;
+  const int32_t nlogical = A.nviews * A.blocks_per_view;
+  // Persistent: logical blocks of kPreBlock (view, Gaussian) pairs are taken
+  // by ticket, so a logical block's look-back only waits on logical blocks
+  // that running blocks hold.
+  while (true) {
   if (threadIdx.x == 0) s_ticket = atomicAdd(&A.counters[kCtrTicketPre], 1u);
   __syncthreads();
   const int32_t w = (int32_t)s_ticket;
+  if (w >= nlogical) break;
   const int32_t view = MAXV == 1 ? 0 : w / A.blocks_per_view;
   const int32_t gb = MAXV == 1 ? w : w % A.blocks_per_view;
   const int32_t i = gb * kPreBlock + (int32_t)threadIdx.x;
@@ -358,7 +364,7 @@ __global__ void __launch_bounds__(kPreBlock) preprocess_kernel(PreArgs A, PreVie
   if (threadIdx.x < 32) {
     const uint64_t prefix = lookback_u64_warp(A.lb, w, total, &A.counters[kCtrStatus]);
     if (threadIdx.x == 0) s_base = prefix;
-    if (threadIdx.x == 0 && w == A.nviews * A.blocks_per_view - 1) {
+    if (threadIdx.x == 0 && w == nlogical - 1) {
       const uint64_t all = prefix + total;
       A.counters[kCtrNeedVisible] = (uint32_t)umin64(all, 0xffffffffull);
       A.counters[kCtrVisible] = (uint32_t)umin64(all, (uint64_t)A.vis_cap);
@@ -366,18 +372,21 @@ __global__ void __launch_bounds__(kPreBlock) preprocess_kernel(PreArgs A, PreVie
     }
   }
   __syncthreads();
-  if (!vis) return;
   const uint64_t slot = s_base + local;
-  if (slot >= (uint64_t)A.vis_cap) return;
-  // Conic in base-2 exponent form: power2 = -(A' dx^2 + B' dx dy + C' dy^2).
-  A.rec_geom[slot] = make_float4(h.uv[0], h.uv[1], 0.5f * kLog2e * h.conA, kLog2e * h.conB);
-  A.rec_color[slot] = make_float4(0.5f * kLog2e * h.conC, log2f(h.a), h.rgb[0], h.rgb[1]);
-  A.rec_blue[slot] = h.rgb[2];
-  // alpha = a 2^power2 >= 1/255 needs -power2 <= log2(255 a); the margin keeps
-  // the per-tile test of the instance emission conservative under rounding.
-  A.rec_tau[slot] = log2f(255.0f * h.a) + kTauMargin;
-  A.rec_meta[slot] = make_int4(i, view, h.rect[0] | (h.rect[1] << 16), h.rect[2] | (h.rect[3] << 16));
-  A.depth_key[slot] = __float_as_uint(h.pc[2]);
+  if (vis && slot < (uint64_t)A.vis_cap) {
+    // Conic in base-2 exponent form: power2 = -(A' dx^2 + B' dx dy + C' dy^2).
+    A.rec_geom[slot] = make_float4(h.uv[0], h.uv[1], 0.5f * kLog2e * h.conA, kLog2e * h.conB);
+    A.rec_color[slot] = make_float4(0.5f * kLog2e * h.conC, log2f(h.a), h.rgb[0], h.rgb[1]);
+    A.rec_blue[slot] = h.rgb[2];
+    // alpha = a 2^power2 >= 1/255 needs -power2 <= log2(255 a); the margin
+    // keeps the per-tile test of the instance emission conservative under
+    // rounding.
+    A.rec_tau[slot] = log2f(255.0f * h.a) + kTauMargin;
+    A.rec_meta[slot] = make_int4(i, view, h.rect[0] | (h.rect[1] << 16), h.rect[2] | (h.rect[3] << 16));
+    A.depth_key[slot] = __float_as_uint(h.pc[2]);
+  }
+  __syncthreads();  // s_ticket and s_base are reused by the next logical block
+  }
 }
 
 // ------------------------------------------------------------- adjoint
@@ -721,7 +730,7 @@ cudaError_t launch_pre_typed(const PreLaunch &p, const fgs4d_view *views, int32_
   A.rec_meta = reinterpret_cast<int4 *>(p.ws + Lo.rec_meta);
   A.depth_key = reinterpret_cast<uint32_t *>(p.ws + Lo.depth_key);
   if (Lo.pre_blocks == 0) return cudaSuccess;
-  return launch_pdl(preprocess_kernel<L, MAXV>, (unsigned)Lo.pre_blocks, kPreBlock, p.stream, A, pv);
+  return launch_pdl(preprocess_kernel<L, MAXV>, (unsigned)Lo.pre_grid, kPreBlock, p.stream, A, pv);
 }
 
 template <int L, int MAXV>

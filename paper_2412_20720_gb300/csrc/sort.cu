@@ -24,8 +24,6 @@ namespace fgs4d {
 
 namespace {
 
-// Blocks of the persistent sort kernels: four resident per SM on 152 SMs.
-constexpr int kPersistBlocks = 152 * 4;
 
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
@@ -682,8 +680,8 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
     if (e != cudaSuccess) return e;
   } else {
     if (L.depth_blocks > 0) {
-      const int hb = std::min(L.depth_blocks, kPersistBlocks);
-      const int pb = std::min(L.depth_blocks, kPersistBlocks);
+      const int hb = std::min(L.depth_blocks, L.sort_grid);
+      const int pb = std::min(L.depth_blocks, L.sort_grid);
       e = launch_pdl(radix_hist_kernel<kDepthSortItems>, (unsigned)hb, kSortThreads, st, dkey,
                      (const uint32_t *)(ctr + kCtrVisible), (int64_t)L.vis_cap, (int32_t)L.depth_passes, hist_d,
                      dstate, (int32_t)L.depth_blocks, (uint2 *)nullptr, (int64_t)0);
@@ -709,7 +707,7 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   }
   // 3. Stable sort of the instances by global tile id (digit histograms
   // taken by the emission); the last pass also records the tile ranges.
-  const int pbt = std::min(L.tile_blocks, kPersistBlocks);
+  const int pbt = std::min(L.tile_blocks, L.sort_grid);
   for (int p = 0; p < L.tile_passes; ++p) {
     const int in = p & 1, out = in ^ 1;
     const bool last = p == L.tile_passes - 1;

@@ -44,7 +44,7 @@ class Settings(C.Structure):
     _fields_ = [("sh_degree", C.c_int32), ("t_order", C.c_int32), ("period", C.c_float), ("tile", C.c_int32),
                 ("near_plane", C.c_float), ("dilation", C.c_float), ("p_t_min", C.c_float), ("bg", C.c_float * 3),
                 ("vis_capacity", C.c_int64), ("inst_capacity", C.c_int64), ("pixels_per_thread", C.c_int32),
-                ("shared_batch", C.c_int32)]
+                ("shared_batch", C.c_int32), ("stage_blocks_per_sm", C.c_int32)]
 
 
 class Gaussians(C.Structure):
@@ -167,7 +167,7 @@ def make_views(views) -> tuple:
 
 def make_settings(sh_degree=3, t_order=2, period=1.0, near_plane=0.2, dilation=0.3, p_t_min=0.05,
                   bg=(0.0, 0.0, 0.0), vis_capacity=0, inst_capacity=1 << 22, pixels_per_thread=0,
-                  tile=TILE, shared_batch=0) -> Settings:
+                  tile=TILE, shared_batch=0, stage_blocks_per_sm=0) -> Settings:
     s = Settings()
     s.sh_degree, s.t_order, s.period, s.tile = int(sh_degree), int(t_order), float(period), int(tile)
     s.near_plane, s.dilation, s.p_t_min = float(near_plane), float(dilation), float(p_t_min)
@@ -175,6 +175,7 @@ def make_settings(sh_degree=3, t_order=2, period=1.0, near_plane=0.2, dilation=0
         s.bg[k] = float(bg[k])
     s.vis_capacity, s.inst_capacity = int(vis_capacity), int(inst_capacity)
     s.pixels_per_thread, s.shared_batch = int(pixels_per_thread), int(shared_batch)
+    s.stage_blocks_per_sm = int(stage_blocks_per_sm)
     return s
 
 

@@ -31,11 +31,15 @@ class RenderConfig:
     tile: int = 16  # tile edge in pixels, 16 or 8; see autotune()
     shared_batch: int = 0  # records staged per shared-memory batch, 128 or 256 (0 = 256); see autotune()
     mask_threshold: float = 0.01  # epsilon of the Compact-4DGS mask, used when params carry "mask_logit"
+    # Grids of the latency-bound stages: 0 = full-GPU grids (lowest latency for one frame alone);
+    # k = at most k resident blocks per SM, which leaves SMs to frames or views rendered concurrently
+    # (FramePipeline, ViewParallel).  Results are identical.
+    stage_blocks_per_sm: int = 0
 
     def settings(self) -> fgs4d.Settings:
         return fgs4d.make_settings(self.sh_degree, self.t_order, self.period, self.near_plane, self.dilation,
                                    self.p_t_min, self.bg, self.vis_capacity, self.inst_capacity,
-                                   self.pixels_per_thread, self.tile, self.shared_batch)
+                                   self.pixels_per_thread, self.tile, self.shared_batch, self.stage_blocks_per_sm)
 
 
 def _ptr(t: torch.Tensor) -> int:
@@ -371,7 +375,9 @@ class FramePipeline:
 
     Each in-flight slot owns a Renderer (its own workspace) and a CUDA
     stream; the k-th frame submitted after ``begin`` runs preprocess,
-    bin_sort and render_fwd on slot k % depth.  Frames on different slots
+    bin_sort and the compositor on slot k % depth.  A config with
+    ``stage_blocks_per_sm`` = 1 keeps the latency-bound stages of one frame
+    from filling the SMs the other frames' compositors run on.  Frames on different slots
     share only the read-only parameters, so the latency-bound binning and
     sorting of one frame run beside the ALU-bound compositing of another;
     frames on one slot run in submission order, so a slot's output buffer may

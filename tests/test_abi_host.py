@@ -167,6 +167,16 @@ def test_wait_selftest_rejects_bad_scratch_before_launching():
     assert lib.fgs4d_wait_selftest(C.c_void_p(4096 + 4), n, None) == fgs4d.ERR_ARG
 
 
+def test_stage_blocks_per_sm_range():
+    views, nv = _views()
+    for k in (0, 1, 2, 8):
+        fgs4d.workspace_size(fgs4d.make_settings(stage_blocks_per_sm=k), 10, views, nv)
+    for k in (-1, 9):
+        with pytest.raises(fgs4d.Fgs4dError) as e:
+            fgs4d.workspace_size(fgs4d.make_settings(stage_blocks_per_sm=k), 10, views, nv)
+        assert e.value.code == fgs4d.ERR_UNSUPPORTED
+
+
 def test_status_strings():
     for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert fgs4d.status_string(code) not in ("", "unknown status")

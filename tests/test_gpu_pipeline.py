@@ -107,3 +107,39 @@ def test_render_image_equals_render_fwd(tile, ppt, batch):
     assert torch.equal(out, ref)
     assert torch.equal(out_T, T_ref)
     assert int(r.workspace_view(r.layout.pix_last, torch.int32, npx).abs().max()) == 0
+
+
+@pytest.mark.parametrize("nviews", [1, 3])
+def test_lean_stage_grids_change_nothing(nviews):
+    """stage_blocks_per_sm = 1 (persistent preprocess, radix and emission
+    grids of one or two blocks per SM) gives the same slots, instance lists,
+    images and gradients as the full-GPU grids, bit for bit."""
+    import torch
+    from paper_2412_20720_gb300 import synthetic as sy
+    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer
+
+    n = 60_000  # ~235 logical preprocess blocks per view: several per block at one block per SM
+    params = sy.make_scene(n, 17, (-1.5, -1.5, -1.5), (1.5, 1.5, 1.5), sh_degree=1, t_order=1).as_dict()
+    dev = to_device(params)
+    views = [sy.tiny_view(400, 300, t=0.2 + 0.3 * k) for k in range(nviews)]
+    out = {}
+    for k in (0, 1):
+        cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=1 << 22, stage_blocks_per_sm=k)
+        r = Renderer(n, views, cfg)
+        img = r.forward(dev)
+        counts = r.check()
+        m = counts[1]
+        g = {key: torch.zeros_like(dev[key]) for key in PARAM_KEYS}
+        r.backward(dev, torch.ones_like(img), g)
+        r.check()
+        out[k] = (img.clone(), counts,
+                  r.workspace_view(r.layout.sorted_slots, torch.int32, counts[0]).clone(),
+                  r.workspace_view(r.layout.inst_slot, torch.int32, m).clone(),
+                  r.workspace_view(r.layout.inst_tile, torch.int32, m).clone(), g)
+    a, b = out[0], out[1]
+    assert a[1] == b[1] and a[1][1] > 100_000
+    for x, y in zip(a[:1] + a[2:5], b[:1] + b[2:5]):
+        assert torch.equal(x, y)
+    for key in PARAM_KEYS:  # atomics add in another order: equal up to rounding
+        scale = float(a[5][key].abs().max())
+        assert float((a[5][key] - b[5][key]).abs().max()) <= 1e-4 * scale + 1e-12, key

@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurements")
-    p.add_argument("--inflight", type=int, default=6, help="headline frames in flight (one stream and workspace each)")
+    p.add_argument("--inflight", type=int, default=8, help="headline frames in flight (one stream and workspace each)")
     p.add_argument("--stage-blocks", type=int, default=1,
                    help="resident blocks per SM of the latency-bound stages (0 = full-GPU grids)")
     p.add_argument("--shape", default=None, help="compositor shape tile/pixels_per_thread/shared_batch (e.g. 16/4/128) "

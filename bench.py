@@ -635,6 +635,60 @@ def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,))
            "graph_batched": {"ms_per_step": graph_ms, "views_per_s": len(views) * 1000.0 / graph_ms,
                              "fwd_bwd_iters_per_s": 1000.0 / graph_ms}}
     del graph
+    # The same groups as calls on parallel streams (lean grids for their
+    # latency-bound stages; the same workspace layout), one graph.
+    nstreams = min(4, len(rs))
+    streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
+    lean = []
+    for r in rs:
+        sl = fgs4d.Settings.from_buffer_copy(r.settings)
+        sl.stage_blocks_per_sm = 1
+        lean.append(sl)
+    full = [r.settings for r in rs]
+
+    def step_parallel():
+        for gk in grads.values():
+            gk.zero_()
+        cur = torch.cuda.current_stream(dev)
+        ev = torch.cuda.Event()
+        ev.record(cur)
+        for i, (r, dL) in enumerate(zip(rs, dLs)):
+            st = streams[i % nstreams]
+            st.wait_event(ev)
+            with torch.cuda.stream(st):
+                r.forward(params)
+                r.backward(params, dL, grads)
+        for st in streams:
+            cur.wait_stream(st)
+
+    for r, sl in zip(rs, lean):
+        r.settings = sl
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            step_parallel()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_parallel()
+    graph.replay()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    par_ms = a.elapsed_time(b) / steps
+    codes = [r.status()[0] for r in rs]
+    for r, sf in zip(rs, full):
+        r.settings = sf
+    del graph
+    out["graph_parallel_streams"] = {"streams": nstreams, "ms_per_step": par_ms,
+                                     "views_per_s": len(views) * 1000.0 / par_ms,
+                                     "fwd_bwd_iters_per_s": 1000.0 / par_ms,
+                                     "status": fgs4d.status_string(next((c for c in codes if c != fgs4d.OK),
+                                                                        fgs4d.OK))}
     if plain:
         # One single-view renderer per resolution; each view is its own call.
         per_res = {}

@@ -432,6 +432,11 @@ def run_ours(args, rank, world, local):
                          "flops_per_launch": mean_flops, "launch_ms": comp_ms_timed,
                          "duration_basis": "CUDA events around each compositor launch on its slot stream in the "
                                            "timed region (other frames' kernels share the GPU meanwhile)"},
+            "roofline_throughput": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu",
+                                    "achieved": mean_flops * value / world / 1e12, "peak": fp32_peak,
+                                    "unit": "TFLOP/s", "frac": mean_flops * value / world / 1e12 / fp32_peak,
+                                    "duration_basis": "the compositor's flops of every frame over the timed "
+                                                      "region's wall time (one GPU; the other stages share it)"},
             "roofline_isolated": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu", "achieved": achieved_iso,
                                   "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved_iso / fp32_peak,
                                   "launch_ms": float(stage_full[2]),

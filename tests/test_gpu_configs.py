@@ -97,3 +97,54 @@ def test_training_step_gradients_300k_sampled():
     r.check()
     for k in PARAM_KEYS:
         compare_group(k, grads[k].cpu().numpy().astype(np.float64), g_orc[k], 1e-3, 1e-4)
+
+
+def test_headline_sweep_as_the_benchmark_runs_it():
+    """The headline workload in the benchmark's own launch configuration:
+    300k Gaussians, 1352x1014, one view per call through FramePipeline with
+    several frames in flight, fgs4d_render_image, lean grids for the
+    latency-bound stages, the 16/4/128 compositor shape, and the visible
+    capacity fitted to the views.  Every frame equals the default path's
+    (fgs4d_render_fwd, full grids, one frame at a time) bit for bit, and
+    sampled pixels of two frames match the FP64 oracle."""
+    import torch
+    from paper_2412_20720_gb300 import fgs4d
+    from paper_2412_20720_gb300.render import FramePipeline
+
+    sc = sy.orbit_scene()
+    ks = [0, 37, 91, 150, 222, 299]
+    views = [sy.orbit_view(k) for k in ks]
+    base = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24)
+    params = subset(sc.as_dict(), keep_clear_of_boundaries(sc.as_dict(), views, base))
+    n = params["mean"].shape[0]
+    dev = to_device(params)
+    vv = [fgs4d.make_views([v]) for v in views]
+    pipe = FramePipeline(n, views[0], RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24,
+                                                   stage_blocks_per_sm=1), depth=4)
+    cap = pipe.fit_visible_capacity(dev, view_sets=vv)
+    pipe.set_tile(16, 4, 128)
+    g = pipe.slots[0].gaussians(dev)
+    npx = 3 * 1352 * 1014
+    outs = [torch.full((npx,), -1.0, device="cuda") for _ in views]
+    pipe.begin()
+    for (v, nv), out in zip(vv, outs):
+        pipe.submit(g, v, nv, out.data_ptr())
+    pipe.end()
+    pipe.check()
+    assert cap < n
+    ref_cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24)
+    for view, out in zip(views, outs):
+        r = Renderer(n, [view], ref_cfg)
+        ref = r.forward(dev)
+        r.check()
+        assert torch.equal(out, ref)
+    st = oracle_settings(base)
+    rng = np.random.default_rng(11)
+    for k in (1, 4):
+        pix = rng.choice(1352 * 1014, 1500, replace=False)
+        pr = oracle.preprocess(params, views[k], st)
+        rgb, T, nc, mg = oracle.render_pixels(pr, views[k], st, pix)
+        ok = mg >= PIXEL_MARGIN
+        assert ok.mean() >= 0.75, ok.mean()
+        got = outs[k].cpu().numpy().reshape(3, -1)[:, pix].T
+        assert np.abs(got - rgb)[ok].max() <= IMAGE_ATOL

@@ -107,9 +107,18 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
 // which makes every later alpha fail the 1/255 test, so the inner loop tests
 // no flag.  The update stays a branch: whole warps skip it for entries that
 // miss all their pixels.
+// Resident blocks per SM asked of the compiler for the image-only form of the
+// 64-thread 4-pixel-strip blocks: 20 (at most 51 registers a thread, 48 used,
+// no spills) instead of 18 at 56, for frames rendered concurrently.  The form
+// that keeps the backward's state (mode 0) loses with the same bound.
+template <int TILE, int PPT, int kMode>
+constexpr int fwd_min_blocks() {
+  return (TILE == 16 && PPT == 4 && kMode == 3) ? 20 : 1;
+}
+
 template <int MAXV, int TILE, int PPT, int kMode, int kBatch>
-__global__ void __launch_bounds__(TILE *TILE / PPT) render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv,
-                                                                      unsigned long long *stats) {
+__global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, kMode>()))
+    render_fwd_kernel(RenderArgs A, RasterViews<MAXV> rv, unsigned long long *stats) {
   grid_dependency_sync();
   constexpr bool kStats = kMode == 1, kAux = kMode == 2, kTrack = kMode != 3;
   constexpr int NT = TILE * TILE / PPT;

@@ -375,14 +375,14 @@ class FramePipeline:
 
     Each in-flight slot owns a Renderer (its own workspace) and a CUDA
     stream; the k-th frame submitted after ``begin`` runs preprocess,
-    bin_sort and the compositor on slot k % depth.  A config with
-    ``stage_blocks_per_sm`` = 1 keeps the latency-bound stages of one frame
-    from filling the SMs the other frames' compositors run on.  Frames on different slots
-    share only the read-only parameters, so the latency-bound binning and
-    sorting of one frame run beside the ALU-bound compositing of another;
-    frames on one slot run in submission order, so a slot's output buffer may
-    be reused by its next frame.  ``end`` makes the caller's current stream
-    wait for every slot.
+    bin_sort and the compositor on slot k % depth.  Frames on different
+    slots share only the parameters (which must not change while frames are
+    in flight), so the latency-bound binning and sorting of one frame run
+    beside the ALU-bound compositing of another; frames on one slot run in
+    submission order, so a slot's output buffer may be reused by its next
+    frame.  ``end`` makes the caller's current stream wait for every slot.
+    A config with ``stage_blocks_per_sm`` = 1 keeps the latency-bound stages
+    of one frame from filling the SMs the other frames' compositors use.
     """
 
     def __init__(self, n: int, view: dict, config: RenderConfig, depth: int = 3, device=None):

@@ -424,7 +424,8 @@ def run_ours(args, rank, world, local):
                                                         "grids for preprocess, sorting and emission)"},
             "work_per_frame": {"visible": float(np.mean(vis)), "instances": float(np.mean(inst)),
                                "alpha_evals": float(np.mean(evals)), "composited": float(np.mean(comps))},
-            "roofline": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu", "achieved": achieved_timed, "peak": fp32_peak,
+            "roofline": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu",
+                         "achieved": achieved_timed, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved_timed / fp32_peak,
                          "traffic": RENDER_FWD_TRAFFIC.get((tuned["tile"], tuned["pixels_per_thread"],
                                                             tuned["shared_batch"])),
@@ -437,7 +438,8 @@ def run_ours(args, rank, world, local):
                                     "unit": "TFLOP/s", "frac": mean_flops * value / world / 1e12 / fp32_peak,
                                     "duration_basis": "the compositor's flops of every frame over the timed "
                                                       "region's wall time (one GPU; the other stages share it)"},
-            "roofline_isolated": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu", "achieved": achieved_iso,
+            "roofline_isolated": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu",
+                                  "achieved": achieved_iso,
                                   "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved_iso / fp32_peak,
                                   "launch_ms": float(stage_full[2]),
                                   "duration_basis": "one frame in flight (the full-grid per-stage pass)"},
@@ -484,7 +486,8 @@ def run_train(args, dev, scene, params, world, barrier):
     r = Renderer(scene.n, views, cfg, device=dev)
     tuned = autotune(r, {k: leaf[k].detach() for k in PARAM_KEYS}, backward=True, tiles=(16, 8), batches=(256, 128))
     vp = ViewParallel(scene.n, [[v] for v in views],
-                      RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24, stage_blocks_per_sm=args.stage_blocks),
+                      RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24,
+                                   stage_blocks_per_sm=args.stage_blocks),
                       device=dev)
     vp.set_tile(tuned["tile"], tuned["pixels_per_thread"], tuned["shared_batch"])
     grads = {k: torch.zeros_like(leaf[k]) for k in PARAM_KEYS}

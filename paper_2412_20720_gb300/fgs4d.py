@@ -28,9 +28,12 @@ MAX_SH_DEGREE = 3
 MAX_T_ORDER = 4
 TILE = 16  # default tile edge; 8 is the other supported size
 
-EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort", "fgs4d_bin_sort_kernels",
-            "fgs4d_render_fwd", "fgs4d_render_image", "fgs4d_render_aux", "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians", "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features", "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_l1_loss_part", "fgs4d_sort_depth_static", "fgs4d_wait_selftest", "fgs4d_get_status",
-            "fgs4d_status_string")
+EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
+            "fgs4d_bin_sort_kernels", "fgs4d_render_fwd", "fgs4d_render_image", "fgs4d_render_aux",
+            "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians",
+            "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features",
+            "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_l1_loss_part", "fgs4d_sort_depth_static",
+            "fgs4d_wait_selftest", "fgs4d_get_status", "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 
 

@@ -1,10 +1,11 @@
 // Per-Gaussian stage of the 4D Gaussian render path and its adjoint.
 //
 // Forward (Sec. 3.2 of "4D Gaussian Splatting", arXiv 2412.20720; Sec. 3.1,
-// Eqs. 3-4; Sec. 8.1.1 temporal filter): one thread per (view, Gaussian);
-// visible pairs are compacted in (view, Gaussian) order by a block scan plus a
-// decoupled look-back over logical block tickets, so slot numbering is
-// deterministic.
+// Eqs. 3-4; Sec. 8.1.1 temporal filter): one thread per (view, Gaussian) of a
+// logical block; persistent blocks take logical blocks by ticket, and the
+// visible pairs are compacted in (view, Gaussian) order by a block scan plus
+// a decoupled look-back over the tickets, so slot numbering is deterministic
+// whatever the grid.
 //
 // Numerics: the conditional covariance is evaluated in factored form.  With
 // A = R_{1:3,:} diag(s), v = diag(s) R_{4,:}^T, c = |v|^2 = Sigma_44 and

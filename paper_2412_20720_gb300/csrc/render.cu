@@ -357,26 +357,28 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
                                 s_col, s_blue, s_slot, kAux ? A.rec_aux : nullptr, kAux ? s_aux : nullptr);
     __syncthreads();
     const int nb = (int)min(end - base, (uint32_t)kBatch);
-    for (int j = nb - 1; j >= 0; --j) {
-      const uint32_t pos = base + j - range.x;  // entry index in the tile list
-      if (!__any_sync(0xffffffffu, pos < my_max)) continue;  // no pixel of this warp reached it
+    // One list entry; kClamp is the entry's clamp case (entry_clamps), taken
+    // per entry as in the forward so that pixels evaluate pixel_alpha<false>
+    // without a per-pixel select for the vast majority of entries.
+    auto entry = [&](int j, uint32_t pos, auto clamp_tag) {
+      constexpr bool kClamp = decltype(clamp_tag)::value;
       const float4 geom = s_geom[j];
       const float4 col = s_col[j];
       const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc, col.y);
-      const bool clamp = entry_clamps(col.y);
-      const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
       // The conic and centre gradients of the strip share dx: accumulate the
       // moments S0 = sum gp, S1 = sum gp dy, S2 = sum gp dy^2 of
       // gp = dL/d(natural-log power) and form the five sums once per entry.
-      float S0 = 0.f, S1 = 0.f, S2 = 0.f, ga = 0.f, gr = 0.f, gg = 0.f, gb = 0.f, gz = 0.f;
+      // A pixel that is not skipped has alpha = a 2^-q (below the clamp), so
+      // gp = g_alpha a 2^-q is also the opacity term: dL/da = S0 / a.
+      float S0 = 0.f, S1 = 0.f, S2 = 0.f, gr = 0.f, gg = 0.f, gb = 0.f, gz = 0.f;
       const float zj = kAux ? s_aux[j].x : 0.f;
       bool contrib = false;
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
         if (pos >= last[k]) continue;
-        const AlphaEval e = pixel_alpha(ct, geom.y, col.x, pyc[k], clamp);
-        if (e.alpha < kAlphaMin) continue;
+        const AlphaEval e = pixel_alpha<kClamp>(ct, geom.y, col.x, pyc[k]);
+        if (!(e.alpha >= kAlphaMin)) continue;  // the forward's skip decision, NaN included
         contrib = true;
         const float io = rcp_approx(__fsub_rn(1.0f, e.alpha));
         T[k] = T[k] * io;  // transmittance in front of this entry
@@ -391,8 +393,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
         }
         const float g_alpha = T[k] * Dc - io * Dr[k];
         Dr[k] += w * Dc;
-        if (!(clamp && e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
-          ga += g_alpha * e.aG;  // times 1/a below: d alpha / d a = 2^-q
+        if (!(kClamp && e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
           const float gp = g_alpha * e.alpha;  // d alpha / d (natural-log power)
           const float gpy = gp * e.dy;
           S0 += gp;
@@ -400,27 +401,32 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
           S2 += gpy * e.dy;
         }
       }
+      if (!__any_sync(0xffffffffu, contrib)) return;
       const float dx = ct.dx;
-      ga *= ex2_approx(-col.y);
+      const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
       // g = (du, dv, dA', dB', dC', da, dr, dg), plus db.
       float g[8] = {-(An * dx * S0 + Bn * S1), -(Cn * S1 + Bn * dx * S0), -0.5f * dx * dx * S0, -dx * S1,
-                    -0.5f * S2, ga, gr, gg};
-      if (__any_sync(0xffffffffu, contrib)) {
-        warp_sum8_transposed(g, lane);
-        gb = warp_sum(gb);
-        if (kAux) gz = warp_sum(gz);
-        // Lane 4k holds sum k: lanes 0 and 16 gather sums 0-3 and 4-7 and add
-        // them with one vector atomic each; lane 1 adds (db, dz).
-        const float s1 = __shfl_down_sync(0xffffffffu, g[0], 4);
-        const float s2 = __shfl_down_sync(0xffffffffu, g[0], 8);
-        const float s3 = __shfl_down_sync(0xffffffffu, g[0], 12);
-        const uint32_t slot = s_slot[j];
-        if (slot < A.vis_cap) {
-          float4 *dst = A.slot_grad + 3 * (size_t)slot;
-          if ((lane & 15) == 0) atomicAdd(dst + (lane >> 4), make_float4(g[0], s1, s2, s3));
-          else if (lane == 1) atomicAdd(reinterpret_cast<float2 *>(dst + 2), make_float2(gb, kAux ? gz : 0.0f));
-        }
+                    -0.5f * S2, S0 * ex2_approx(-col.y), gr, gg};
+      warp_sum8_transposed(g, lane);
+      gb = warp_sum(gb);
+      if (kAux) gz = warp_sum(gz);
+      // Lane 4k holds sum k: lanes 0 and 16 gather sums 0-3 and 4-7 and add
+      // them with one vector atomic each; lane 1 adds (db, dz).
+      const float s1 = __shfl_down_sync(0xffffffffu, g[0], 4);
+      const float s2 = __shfl_down_sync(0xffffffffu, g[0], 8);
+      const float s3 = __shfl_down_sync(0xffffffffu, g[0], 12);
+      const uint32_t slot = s_slot[j];
+      if (slot < A.vis_cap) {
+        float4 *dst = A.slot_grad + 3 * (size_t)slot;
+        if ((lane & 15) == 0) atomicAdd(dst + (lane >> 4), make_float4(g[0], s1, s2, s3));
+        else if (lane == 1) atomicAdd(reinterpret_cast<float2 *>(dst + 2), make_float2(gb, kAux ? gz : 0.0f));
       }
+    };
+    for (int j = nb - 1; j >= 0; --j) {
+      const uint32_t pos = base + j - range.x;  // entry index in the tile list
+      if (!__any_sync(0xffffffffu, pos < my_max)) continue;  // no pixel of this warp reached it
+      if (entry_clamps(s_col[j].y)) entry(j, pos, std::true_type());
+      else entry(j, pos, std::false_type());
     }
   }
 }

@@ -30,7 +30,7 @@ class RenderConfig:
     pixels_per_thread: int = 0  # compositor block shape (0 = library default); see autotune()
     tile: int = 16  # tile edge in pixels, 16 or 8; see autotune()
     shared_batch: int = 0  # records staged per shared-memory batch, 128 or 256 (0 = 256); see autotune()
-    mask_threshold: float = 0.01  # epsilon of the Compact-4DGS mask, used when params carry "mask_logit"
+    mask_threshold: float = 0.03  # epsilon of the Compact-4DGS mask (Sec. 8.3.2 runs it at 0.03); used with "mask_logit"
     # Grids of the latency-bound stages: 0 = full-GPU grids (lowest latency for one frame alone);
     # k = at most k resident blocks per SM, which leaves SMs to frames or views rendered concurrently
     # (FramePipeline, ViewParallel).  Results are identical.

@@ -498,21 +498,19 @@ def run_train(args, dev, scene, params, world, barrier):
     total = int(target.numel())
     vp_loss = torch.zeros(1, dtype=torch.float32, device=dev)
 
+    # The gradients start at zero and Adam clears each one after reading it
+    # (zero_grad), so every step accumulates into zeros without a fill.
     def it_batched():
-        for gk in grads.values():
-            gk.zero_()
         img = r.forward(pr)
         loss, dimg = l1_loss(img, target)
         r.backward(pr, dimg, grads)
-        opt.step(grads)
+        opt.step(grads, zero_grad=True)
         return loss
 
     def it_parallel():
-        for gk in grads.values():
-            gk.zero_()
         vp_loss.zero_()
         vp.step(pr, lambda j, img: l1_loss(img, targets[j], mean_count=total, loss=vp_loss)[1], grads)
-        opt.step(grads)
+        opt.step(grads, zero_grad=True)
         return vp_loss
 
     stream = torch.cuda.current_stream(dev)

@@ -324,6 +324,28 @@ int fgs4d_adam_tick(int32_t *step, void *stream);
 int fgs4d_adam_update(float *param, const float *grad, float *exp_avg, float *exp_avg_sq, int64_t count, float lr,
                       float beta1, float beta2, float eps, const int32_t *step, void *stream);
 
+/* The same Adam step over up to FGS4D_ADAM_MAX_TENSORS tensors in one
+ * launch (each element gets exactly the update of fgs4d_adam_update, with its
+ * tensor's lr).  tensors: HOST array of ntensors descriptors, read during the
+ * call only; each tensor's four device arrays hold count floats and are
+ * 16-byte aligned; count = 0 is allowed.  With zero_grad != 0 every gradient
+ * element is set to 0 after it is read, so the next step can accumulate into
+ * the same buffers without clearing them first.  Errors: FGS4D_ERR_ARG for
+ * ntensors outside [0, FGS4D_ADAM_MAX_TENSORS], a NULL table or step, NULL or
+ * misaligned arrays of a tensor with count > 0, a negative count or
+ * non-finite lr, and the scalar conditions of fgs4d_adam_update. */
+#define FGS4D_ADAM_MAX_TENSORS 16
+typedef struct {
+  float *param;
+  float *grad; /* written (zeroed) only when zero_grad != 0 */
+  float *exp_avg;
+  float *exp_avg_sq;
+  int64_t count;
+  float lr;
+} fgs4d_adam_tensor;
+int fgs4d_adam_update_set(const fgs4d_adam_tensor *tensors, int32_t ntensors, float beta1, float beta2, float eps,
+                          const int32_t *step, int32_t zero_grad, void *stream);
+
 /* Scale-gated feature rendering for 4D segmentation (Sec. 7, "Scale-gated
  * features"): Gaussian i carries features[i][0..D); at a scale s the caller
  * passes the gate vector S(s) (device float [D], values in [0, 1]; NULL =

@@ -437,6 +437,25 @@ int fgs4d_adam_update(float *param, const float *grad, float *exp_avg, float *ex
                                  static_cast<cudaStream_t>(stream)));
 }
 
+int fgs4d_adam_update_set(const fgs4d_adam_tensor *tensors, int32_t ntensors, float beta1, float beta2, float eps,
+                          const int32_t *step, int32_t zero_grad, void *stream) {
+  static_assert(FGS4D_ADAM_MAX_TENSORS == kAdamMaxTensors, "tensor table sizes");
+  if (ntensors < 0 || ntensors > FGS4D_ADAM_MAX_TENSORS || !step || (ntensors > 0 && !tensors))
+    return FGS4D_ERR_ARG;
+  if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f)) return FGS4D_ERR_ARG;
+  AdamTensorDev dev[kAdamMaxTensors];
+  for (int32_t k = 0; k < ntensors; ++k) {
+    const fgs4d_adam_tensor &t = tensors[k];
+    if (t.count < 0 || !finite_f(t.lr)) return FGS4D_ERR_ARG;
+    if (t.count > 0 && (!t.param || !t.grad || !t.exp_avg || !t.exp_avg_sq || !aligned16(t.param) ||
+                        !aligned16(t.grad) || !aligned16(t.exp_avg) || !aligned16(t.exp_avg_sq)))
+      return FGS4D_ERR_ARG;
+    dev[k] = AdamTensorDev{t.param, t.grad, t.exp_avg, t.exp_avg_sq, t.count, t.lr};
+  }
+  return cuda_status(launch_adam_set(dev, ntensors, beta1, beta2, eps, step, zero_grad != 0,
+                                     static_cast<cudaStream_t>(stream)));
+}
+
 int fgs4d_mask_loss(const float *mask_logit, int64_t n, float *loss_out, float *grad_out, void *stream) {
   if (n < 0 || (n > 0 && (!mask_logit || !loss_out || !grad_out))) return FGS4D_ERR_ARG;
   return cuda_status(launch_mask_loss(mask_logit, n, loss_out, grad_out, static_cast<cudaStream_t>(stream)));

@@ -427,6 +427,15 @@ cudaError_t launch_render_features(const Layout &L, const fgs4d_view *views, int
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t count, float lr, float b1, float b2,
                         float eps, const int32_t *step, cudaStream_t stream);
 cudaError_t launch_adam_tick(int32_t *step, cudaStream_t stream);
+// One tensor of a multi-tensor Adam step (fgs4d_adam_update_set).
+constexpr int kAdamMaxTensors = 16;
+struct AdamTensorDev {
+  float *p, *g, *m, *v;
+  int64_t count;
+  float lr;
+};
+cudaError_t launch_adam_set(const AdamTensorDev *tensors, int32_t n, float b1, float b2, float eps,
+                            const int32_t *step, bool zero_grad, cudaStream_t stream);
 cudaError_t launch_mask_loss(const float *mask_logit, int64_t n, float *loss, float *grad, cudaStream_t stream);
 cudaError_t launch_aux_records(const PreLaunch &p, const fgs4d_view *views, int32_t nviews, float flow_dt);
 cudaError_t launch_split(const fgs4d_gaussians *src, const int32_t *idx, int64_t m, int32_t k_children,

@@ -497,6 +497,57 @@ __global__ void adam_kernel(AdamArgs A) {
     adam_one(A.p[i], A.g[i], A.m[i], A.v[i], A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
 }
 
+// Adam over a set of tensors in one launch: unit u of the set is float4 u -
+// first[k] of tensor k (the last unit of a tensor whose count is not a
+// multiple of 4 takes its 1-3 trailing scalars).  Each element gets exactly
+// adam_one, as in adam_kernel; with zero the gradient is cleared after it is
+// read, so the next step accumulates into zeros without a separate fill.
+struct AdamSetArgs {
+  AdamTensorDev t[kAdamMaxTensors];
+  int64_t first[kAdamMaxTensors + 1];  // prefix of the tensors' unit counts
+  int32_t n;
+  float b1, b2, eps;
+  const int32_t *step;
+  int32_t zero;
+};
+
+__global__ void adam_set_kernel(AdamSetArgs A) {
+  grid_dependency_sync();
+  const float t = (float)*A.step;
+  const float bc1 = 1.0f - powf(A.b1, t), bc2 = 1.0f - powf(A.b2, t);
+  const float inv_sqrt_bc2 = rsqrtf(bc2);
+  const int64_t total = A.first[A.n];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int k = 0;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += stride) {
+    while (u >= A.first[k + 1]) ++k;  // units only grow along the loop
+    const AdamTensorDev &T = A.t[k];
+    const float step_size = T.lr / bc1;
+    const int64_t i = u - A.first[k];
+    if (4 * i + 4 <= T.count) {
+      float4 *p4 = reinterpret_cast<float4 *>(T.p) + i;
+      float4 *g4 = reinterpret_cast<float4 *>(T.g) + i;
+      float4 *m4 = reinterpret_cast<float4 *>(T.m) + i;
+      float4 *v4 = reinterpret_cast<float4 *>(T.v) + i;
+      float4 p = *p4, m = *m4, v = *v4;
+      const float4 g = *g4;
+      adam_one(p.x, g.x, m.x, v.x, A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+      adam_one(p.y, g.y, m.y, v.y, A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+      adam_one(p.z, g.z, m.z, v.z, A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+      adam_one(p.w, g.w, m.w, v.w, A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+      *p4 = p;
+      *m4 = m;
+      *v4 = v;
+      if (A.zero) *g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (int64_t e = 4 * i; e < T.count; ++e) {
+        adam_one(T.p[e], T.g[e], T.m[e], T.v[e], A.b1, A.b2, A.eps, step_size, inv_sqrt_bc2);
+        if (A.zero) T.g[e] = 0.f;
+      }
+    }
+  }
+}
+
 __global__ void adam_tick_kernel(int32_t *step) {
   grid_dependency_sync();
   if (threadIdx.x == 0) *step += 1;
@@ -649,6 +700,26 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t co
   AdamArgs A{p, g, m, v, count, lr, b1, b2, eps, step};
   const int blocks = (int)std::min<int64_t>((count / 4 + 255) / 256 + 1, 152 * 8);
   return launch_pdl(adam_kernel, (unsigned)blocks, 256u, stream, A);
+}
+
+cudaError_t launch_adam_set(const AdamTensorDev *tensors, int32_t n, float b1, float b2, float eps,
+                            const int32_t *step, bool zero_grad, cudaStream_t stream) {
+  AdamSetArgs A{};
+  A.n = n;
+  A.first[0] = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    A.t[k] = tensors[k];
+    A.first[k + 1] = A.first[k] + (tensors[k].count + 3) / 4;
+  }
+  A.b1 = b1;
+  A.b2 = b2;
+  A.eps = eps;
+  A.step = step;
+  A.zero = zero_grad ? 1 : 0;
+  const int64_t total = A.first[n];
+  if (total == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  return launch_pdl(adam_set_kernel, (unsigned)blocks, 256u, stream, A);
 }
 
 cudaError_t launch_adam_tick(int32_t *step, cudaStream_t stream) {

@@ -31,10 +31,17 @@ TILE = 16  # default tile edge; 8 is the other supported size
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
             "fgs4d_bin_sort_kernels", "fgs4d_render_fwd", "fgs4d_render_image", "fgs4d_render_aux",
             "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians",
-            "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_render_features",
+            "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_adam_update_set",
+            "fgs4d_render_features",
             "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_l1_loss_part", "fgs4d_sort_depth_static",
             "fgs4d_wait_selftest", "fgs4d_get_status", "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
+ADAM_MAX_TENSORS = 16
+
+
+class AdamTensor(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("exp_avg", C.c_void_p), ("exp_avg_sq", C.c_void_p),
+                ("count", C.c_int64), ("lr", C.c_float)]
 
 
 class View(C.Structure):
@@ -123,6 +130,7 @@ def load():
                                               vp]
     lib.fgs4d_adam_tick.argtypes = [vp, vp]
     lib.fgs4d_adam_update.argtypes = [vp, vp, vp, vp, i64, C.c_float, C.c_float, C.c_float, C.c_float, vp, vp]
+    lib.fgs4d_adam_update_set.argtypes = [P(AdamTensor), i32, C.c_float, C.c_float, C.c_float, vp, i32, vp]
     lib.fgs4d_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.fgs4d_l1_loss_part.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     lib.fgs4d_sort_depth_static.argtypes = [vp, i64, vp, vp]
@@ -293,6 +301,15 @@ def adam_update(param: int, grad: int, exp_avg: int, exp_avg_sq: int, count: int
                 beta2: float, eps: float, step: int, stream: int):
     _check(load().fgs4d_adam_update(param, grad, exp_avg, exp_avg_sq, int(count), float(lr), float(beta1),
                                     float(beta2), float(eps), step, stream), "fgs4d_adam_update")
+
+
+def adam_update_set(tensors, beta1: float, beta2: float, eps: float, step: int, zero_grad: bool, stream: int):
+    """tensors: sequence of (param, grad, exp_avg, exp_avg_sq, count, lr) with device pointers."""
+    arr = (AdamTensor * max(1, len(tensors)))()
+    for k, (p, g, m, v, count, lr) in enumerate(tensors):
+        arr[k] = AdamTensor(p, g, m, v, int(count), float(lr))
+    _check(load().fgs4d_adam_update_set(arr, len(tensors), float(beta1), float(beta2), float(eps), step,
+                                        1 if zero_grad else 0, stream), "fgs4d_adam_update_set")
 
 
 def l1_loss(img: int, target: int, count: int, loss_out: int, dL_dimg: int, stream: int):

@@ -558,8 +558,9 @@ def mask_loss(mask_logit: torch.Tensor, grad: torch.Tensor | None = None):
 
 class Adam:
     """Adam over the parameter tensors with the fgs4d kernel (one streaming
-    pass per tensor); the step count lives on the device, so ``step`` can be
-    captured in a CUDA graph.  ``lr`` may be one float or a dict per key."""
+    pass over all tensors); the step count lives on the device, so ``step``
+    can be captured in a CUDA graph.  ``lr`` may be one float or a dict per
+    key."""
 
     def __init__(self, params: dict, lr=1e-4, betas=(0.9, 0.999), eps=1e-8):
         self.params = params
@@ -570,12 +571,17 @@ class Adam:
         self.lr = lr if isinstance(lr, dict) else {k: float(lr) for k in params}
         self.betas, self.eps = betas, eps
 
-    def step(self, grads: dict):
+    def step(self, grads: dict, zero_grad: bool = False):
+        """One Adam step from ``grads``; with ``zero_grad`` the gradients are
+        cleared in the same pass (each after it is read), ready for the next
+        step's accumulation."""
         st = torch.cuda.current_stream(self.t.device).cuda_stream
         fgs4d.adam_tick(_ptr(self.t), st)
-        for k, p in self.params.items():
-            fgs4d.adam_update(_ptr(p), _ptr(grads[k]), _ptr(self.m[k]), _ptr(self.v[k]), p.numel(), self.lr[k],
-                              self.betas[0], self.betas[1], self.eps, _ptr(self.t), st)
+        keys = list(self.params)
+        for i in range(0, len(keys), fgs4d.ADAM_MAX_TENSORS):
+            fgs4d.adam_update_set([(_ptr(self.params[k]), _ptr(grads[k]), _ptr(self.m[k]), _ptr(self.v[k]),
+                                    self.params[k].numel(), self.lr[k]) for k in keys[i:i + fgs4d.ADAM_MAX_TENSORS]],
+                                  self.betas[0], self.betas[1], self.eps, _ptr(self.t), zero_grad, st)
 
 
 def l1_loss(img: torch.Tensor, target: torch.Tensor, mean_count: int | None = None,

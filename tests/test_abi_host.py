@@ -177,6 +177,29 @@ def test_stage_blocks_per_sm_range():
         assert e.value.code == fgs4d.ERR_UNSUPPORTED
 
 
+def test_adam_set_rejects_bad_tables_before_launching():
+    lib = fgs4d.load()
+    step = C.c_void_p(4096)
+    ok = fgs4d.AdamTensor(4096, 4096, 4096, 4096, 8, 1e-3)
+    table = (fgs4d.AdamTensor * 17)(*([ok] * 17))
+    assert lib.fgs4d_adam_update_set(table, 17, 0.9, 0.99, 1e-8, step, 0, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_adam_update_set(table, -1, 0.9, 0.99, 1e-8, step, 0, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_adam_update_set(table, 1, 0.9, 0.99, 1e-8, None, 0, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_adam_update_set(None, 1, 0.9, 0.99, 1e-8, step, 0, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_adam_update_set(table, 1, 1.0, 0.99, 1e-8, step, 0, None) == fgs4d.ERR_ARG
+    assert lib.fgs4d_adam_update_set(table, 1, 0.9, 0.99, 0.0, step, 0, None) == fgs4d.ERR_ARG
+    for bad in (fgs4d.AdamTensor(4096, 4096, 4096, 4096, -1, 1e-3),
+                fgs4d.AdamTensor(4096, 4096, 4096, 4096, 8, float("nan")),
+                fgs4d.AdamTensor(4096, None, 4096, 4096, 8, 1e-3),
+                fgs4d.AdamTensor(4096, 4100, 4096, 4096, 8, 1e-3)):
+        one = (fgs4d.AdamTensor * 1)(bad)
+        assert lib.fgs4d_adam_update_set(one, 1, 0.9, 0.99, 1e-8, step, 0, None) == fgs4d.ERR_ARG
+    # An empty set, or tensors with count 0 and NULL arrays, launch nothing.
+    empty = (fgs4d.AdamTensor * 1)(fgs4d.AdamTensor(None, None, None, None, 0, 1e-3))
+    assert lib.fgs4d_adam_update_set(empty, 0, 0.9, 0.99, 1e-8, step, 0, None) == fgs4d.OK
+    assert lib.fgs4d_adam_update_set(empty, 1, 0.9, 0.99, 1e-8, step, 1, None) == fgs4d.OK
+
+
 def test_status_strings():
     for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert fgs4d.status_string(code) not in ("", "unknown status")

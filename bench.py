@@ -8,12 +8,18 @@ one view per call (plain form): preprocess -> bin_sort -> render_image (the
 forward compositor without the state a backward pass needs) through the C
 ABI for every view, with --inflight frames in flight (FramePipeline: one
 workspace and one stream per slot, frame k on slot k % inflight).  value =
-rendered frames/s over all ranks.
+rendered frames/s over all ranks; with N ranks the sweep has 300 N views and
+rank r renders the views k = r (mod N).
 
 Also reported ("train"): fwd+bwd iterations/s of the training step on the same
-scene -- 4 timestamps x 1 camera at 1352x1014 in one batched call, L1 loss
-against target images rendered by the CUDA path from a second seeded scene,
-backward to every parameter, and an Adam step.
+scene -- 4 timestamps x 1 camera at 1352x1014, L1 loss against target images
+rendered by the FP64 oracle from a second seeded scene (rendered in the CPU
+baseline leg; the CUDA path renders them when that leg does not run),
+backward to every parameter; the same step with an Adam update is reported
+beside it.  Per-stage times and the rooflines of the forward and backward
+compositors come from an untimed pass with one step alone.  "batched": the
+1M-Gaussian 64-view mixed-resolution workload and the 3M-Gaussian urban rig,
+with per-stage times.  "c0": the 2k-Gaussian 128x96 configuration.
 
 Timing: W untimed warm-up steps, then K steps between a barrier +
 synchronize on both sides, CUDA events on the launching stream, max over
@@ -47,13 +53,22 @@ W_IMG, H_IMG = 1352, 1014
 # alpha*T (1), three colour multiply-adds (6) = 9.  The ex2 goes to the SFU.
 FLOPS_PER_EVAL = 11
 FLOPS_PER_COMP = 9
-# DRAM bytes (read + write) of one image-mode compositor launch on this
-# workload, per block shape: the mean over the frames of a 4-view orbit sweep captured by
-# ncu (profiles/launches_orbit_300k_1352x1014.md, traffic section); emptied
-# whenever the kernel changes.
-# keyed by (tile, pixels per thread, shared batch)
-RENDER_FWD_TRAFFIC = {(16, 4, 128): 6.979e6, (16, 4, 256): 6.986e6, (16, 2, 128): 6.969e6,
-                      (16, 2, 256): 6.963e6}
+# The compositor adjoint repeats the alpha evaluation (11) at every list
+# position up to a pixel's last composited entry; a composited entry then
+# costs 1 - alpha (1), T / (1 - alpha) (1, with an SFU reciprocal), w =
+# alpha T (1), three colour-gradient multiply-adds (6), dL/dC . c (5),
+# dL/dalpha = T Dc - Dr / (1 - alpha) (3), Dr += w Dc (2), gp = g_alpha
+# alpha (1), gp dy (1) and the three moment sums (4) = 25.
+FLOPS_PER_BWD_COMP = 25
+# Issue slots of one SM per clock: four schedulers, one warp instruction each.
+ISSUE_PER_SM_CLK = 4
+# One ncu capture of the image-mode compositor (render_fwd_kernel, mode 3) on
+# this workload: DRAM bytes (read + write) and warp instructions per launch,
+# averaged over the captured launches.  Valid only for the compositor source
+# it was taken from (sha256 prefix of csrc/render.cu); any other source
+# reports null.
+NCU_RENDER_FWD = {"render_cu_sha256": None, "shape": None, "dram_bytes": None, "warp_insts": None,
+                  "launches": None, "capture": None}
 
 
 def parse():
@@ -73,6 +88,8 @@ def parse():
                    help="resident blocks per SM of the latency-bound stages (0 = full-GPU grids)")
     p.add_argument("--shape", default=None, help="compositor shape tile/pixels_per_thread/shared_batch (e.g. 16/4/128) "
                                                  "instead of the autotune (for profiling a fixed kernel)")
+    p.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    p.add_argument("--no-c0", action="store_true", help="skip the 2k-Gaussian configuration")
     return p.parse_args()
 
 
@@ -93,6 +110,14 @@ def max_over_ranks(x: float, world: int, device) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard_views(views_per_rank: int, rank: int, world: int):
+    """Indices of the sweep views rank `rank` renders.  The job's sweep has
+    views_per_rank * world distinct (camera, t) views; rank r takes the views
+    k = r (mod world), so every view is rendered exactly once and the work
+    per GPU stays fixed as world grows (weak scaling, no exchange)."""
+    return list(range(rank, views_per_rank * world, world))
 
 
 def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
@@ -178,17 +203,49 @@ def measured_peaks():
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_frames(n: int, ks, seconds_budget: float = 30.0):
-    """Full views rendered by the FP64 oracle on the host cores.  Returns
-    (frames/s, threads, frames done)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_settings():
     import numpy as np
 
     import oracle
+    return oracle.Settings(sh_degree=3, t_order=2, tile=16, period=1.0, near_plane=float(np.float32(0.2)),
+                           dilation=float(np.float32(0.3)), p_t_min=float(np.float32(0.05)))
+
+
+def row_window(view, y0: int, h: int) -> dict:
+    """Rows [y0, y0 + h) of a view, as a view of its own (principal point
+    shifted; same pixels, same samples)."""
+    import numpy as np
+    v = dict(view)
+    v.update(height=h, cy=np.float32(float(view["cy"]) - y0))
+    return v
+
+
+def oracle_frames(n: int, ks, seconds_budget: float = 30.0):
+    """Full views rendered by the FP64 oracle on the host cores.  Returns
+    (frames/s, threads, frames done)."""
+    import oracle
     from paper_2412_20720_gb300 import synthetic as sy
-    scene = sy.orbit_scene(n)
-    params = scene.as_dict()
-    st = oracle.Settings(sh_degree=3, t_order=2, tile=16, period=1.0, near_plane=float(np.float32(0.2)),
-                         dilation=float(np.float32(0.3)), p_t_min=float(np.float32(0.05)))
+    params = sy.orbit_scene(n).as_dict()
+    st = oracle_settings()
     t0 = time.perf_counter()
     done = 0
     for k in ks:
@@ -200,6 +257,92 @@ def oracle_frames(n: int, ks, seconds_budget: float = 30.0):
             break
     dt = time.perf_counter() - t0
     return done / dt, oracle.num_threads(), done
+
+
+def oracle_window_seconds(params, view, rows: int, backward: bool = False, threads: int = 1):
+    """Seconds of the oracle's forward (and adjoint) of the middle ``rows``
+    rows of ``view`` on ``threads`` host threads, and the share of the view's
+    pixels they are."""
+    import numpy as np
+
+    import oracle
+    H = int(view["height"])
+    v = row_window(view, (H - rows) // 2, rows)
+    st = oracle_settings()
+    before = oracle.num_threads()
+    oracle.set_num_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        pr = oracle.preprocess(params, v, st)
+        img, _, _, _ = oracle.render(pr, v, st)
+        if backward:
+            oracle.render_backward(params, pr, v, st, np.sign(img - 0.5))
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(before)
+    return dt, rows / H
+
+
+def cpu_leg(args, scene, tgt_scene, train_views):
+    """The oracle on the host cores (rank 0, N = 1): the headline frame rate
+    (one full view, all cores; a row window on one core), the C2 targets
+    (the oracle renders the training views of the target scene), and the
+    training step's rate (one view's forward + adjoint, all cores and one
+    core on a row window).  Returns (headline cpu_baseline, train
+    cpu_baseline, targets as [3, H, W] float32 arrays)."""
+    import numpy as np
+
+    import oracle
+    model = cpu_model()
+    cores = os.cpu_count()
+    fps, threads, nfr = oracle_frames(args.n, [SWEEP // 2], 60.0)
+    params = scene.as_dict()
+    rows = 64
+    t1, share = oracle_window_seconds(params, sy_orbit_view(SWEEP // 2), rows, threads=1)
+    head = {"value": fps, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": model, "host_cpus": cores,
+            "sample": "%d full view(s) (view k=%d of the sweep: %d Gaussians, %dx%d) rendered by the FP64 oracle "
+                      "with OpenMP over pixel rows" % (nfr, SWEEP // 2, args.n, W_IMG, H_IMG),
+            "one_core": {"value": share / t1, "unit": UNIT, "cores": 1,
+                         "sample": "the middle %d rows of the same view on one thread, scaled to a full view"
+                                   % rows}}
+    # C2 targets: the oracle's render of the target scene at the training views.
+    st = oracle_settings()
+    tparams = tgt_scene.as_dict()
+    t0 = time.perf_counter()
+    targets = []
+    for v in train_views:
+        img, _, _, _ = oracle.render(oracle.preprocess(tparams, v, st), v, st)
+        targets.append(img.astype(np.float32))
+    t_targets = time.perf_counter() - t0
+    # One view of the training step: forward + adjoint of the L1 loss.
+    v = train_views[0]
+    t0 = time.perf_counter()
+    pr = oracle.preprocess(params, v, st)
+    img, _, _, _ = oracle.render(pr, v, st)
+    npx = img.size * len(train_views)
+    oracle.render_backward(params, pr, v, st, np.sign(img - targets[0]) / npx)
+    t_view = time.perf_counter() - t0
+    t1b, share_b = oracle_window_seconds(params, v, rows, backward=True, threads=1)
+    train = {"value": 1.0 / (len(train_views) * t_view), "unit": "iters/s", "cores": threads, "kind": "oracle",
+             "cpu_model": model, "host_cpus": cores,
+             "sample": "one view of the 4-view step (%d Gaussians, %dx%d): forward + adjoint of the L1 loss by the "
+                       "FP64 oracle with OpenMP over pixel rows, scaled to 4 views" % (scene.n, W_IMG, H_IMG),
+             "one_core": {"value": share_b / (len(train_views) * t1b), "unit": "iters/s", "cores": 1,
+                          "sample": "the middle %d rows of the view on one thread, scaled to 4 full views" % rows},
+             "targets": {"views": len(train_views), "seconds": t_targets,
+                         "frames_per_s": len(train_views) / t_targets}}
+    return head, train, targets
+
+
+def sy_orbit_view(k: int):
+    from paper_2412_20720_gb300 import synthetic as sy
+    return sy.orbit_view(k, SWEEP, W_IMG, H_IMG)
+
+
+def render_cu_sha256() -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2412_20720_gb300", "csrc", "render.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 # ----------------------------------------------------------------- ours
@@ -226,7 +369,8 @@ def run_ours(args, rank, world, local):
     host = scene.as_dict()
     params = {k: torch.from_numpy(host[k]).to(dev) for k in PARAM_KEYS}
     nviews = args.views
-    views = [sy.orbit_view(k, nviews, W_IMG, H_IMG) for k in range(nviews)]
+    # This rank's share of the job's sweep (views_per_rank x world views).
+    views = [sy.orbit_view(k, nviews * world, W_IMG, H_IMG) for k in shard_views(nviews, rank, world)]
     # Lean grids for the latency-bound stages (one resident preprocess and
     # radix block per SM, two emission blocks): the frames in flight share
     # the SMs.
@@ -336,17 +480,31 @@ def run_ours(args, rank, world, local):
     if code != fgs4d.OK:
         raise RuntimeError("per-stage passes: %s" % fgs4d.status_string(code))
 
-    # Roofline of the dominant kernel (the compositor): FP32-ALU bound.
+    # Roofline of the dominant kernel (the compositor): FP32-ALU bound.  Its
+    # duration is taken with one frame in flight (events around each launch
+    # in the per-stage pass), so no other frame's kernels share the SMs.
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    nsm = props.multi_processor_count
+    fp32_peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
     mean_flops = FLOPS_PER_EVAL * np.mean(evals) + FLOPS_PER_COMP * np.mean(comps)
+    comp_ms = float(stage_ms[2])
+    achieved = mean_flops / (comp_ms * 1e-3) / 1e12
     achieved_timed = mean_flops / (comp_ms_timed * 1e-3) / 1e12
-    achieved_iso = mean_flops / (stage_full[2] * 1e-3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     pre_bytes = 68.0 * scene.n + (576.0 + 56.0) * np.mean(vis)
     pre_gbs = pre_bytes / (stage_full[0] * 1e-3) / 1e9
+    shape = "%d/%d/%d" % (tuned["tile"], tuned["pixels_per_thread"], tuned["shared_batch"])
+    ncu_ok = NCU_RENDER_FWD["render_cu_sha256"] == render_cu_sha256() and NCU_RENDER_FWD["shape"] == shape
+    issue = None
+    if ncu_ok and NCU_RENDER_FWD["warp_insts"]:
+        # the issue-slot ceiling: the launch's warp instructions at one per
+        # scheduler per clock on every SM
+        floor_ms = NCU_RENDER_FWD["warp_insts"] / (nsm * ISSUE_PER_SM_CLK * sm_max * 1e6) * 1e3
+        issue = {"warp_insts_per_launch": NCU_RENDER_FWD["warp_insts"], "issue_limited_ms": floor_ms,
+                 "frac": floor_ms / comp_ms,
+                 "basis": "ncu warp instructions of this build / (SMs x 4 schedulers x max SM clock)"}
 
     # ---------------------------------------------------------- e2e
     e2e = None
@@ -382,24 +540,31 @@ def run_ours(args, rank, world, local):
                        "(%d frames in flight); each image copied to pinned host memory on its frame's stream"
                        % pipe.depth}
 
+    # ---------------------------------------------------------- CPU oracle
+    # (rank 0 at N = 1 only; it also renders the training step's targets)
+    cpu = cpu_train = targets = None
+    train_views = sy.train_views(4, W_IMG, H_IMG)
+    tgt_scene = sy.orbit_scene(args.n, seed=sy.TARGET_SEED)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, cpu_train, targets = cpu_leg(args, scene, tgt_scene, train_views)
+
     # ---------------------------------------------------------- train step
-    train = run_train(args, dev, scene, params, world, barrier)
+    train = None
+    if not args.no_train:
+        train = run_train(args, dev, scene, params, world, barrier, train_views, tgt_scene, targets, fp32_peak)
+        if train is not None:
+            train["cpu_baseline"] = cpu_train
 
     # ---------------------------------------------------------- batched views
     batched = None
     if not args.no_batched:
         batched = [run_batched(dev, sy.sphere_scene(), sy.sphere_views(64), "sphere-1M-64views-mixed-res", 2, 8,
-                               tiles=(16, 8)),
+                               tiles=(16, 8), hbm=hbm),
                    run_batched(dev, sy.urban_scene(), sy.urban_views(), "urban-3M-6cams-x-2t-1920x1080", 2, 6,
-                               plain=False)]
+                               plain=False, hbm=hbm)]
 
-    # ---------------------------------------------------------- CPU oracle
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        fps, cores, nfr = oracle_frames(args.n, [SWEEP // 2], 60.0)
-        cpu = {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d full view(s) (view k=%d of the sweep: %d Gaussians, %dx%d) rendered by the FP64 "
-                         "oracle with OpenMP over pixel rows" % (nfr, SWEEP // 2, args.n, W_IMG, H_IMG)}
+    # ---------------------------------------------------------- C0
+    c0 = None if args.no_c0 else run_tiny(dev)
 
     if rank == 0:
         line = {
@@ -411,7 +576,8 @@ def run_ours(args, rank, world, local):
                        "vis_capacity": vis_cap, "frames_in_flight": pipe.depth,
                        "stage_blocks_per_sm": args.stage_blocks,
                        "l2": "inputs larger than L2 (193 MB of parameters vs 129 MB L2); no flush",
-                       "parallelism": "views replicated per GPU" if world > 1 else "single GPU"},
+                       "parallelism": ("views sharded: rank r renders views k = r mod %d of a %d-view sweep"
+                                       % (world, nviews * world)) if world > 1 else "single GPU"},
             "gpu_launches": launches_per_frame * nviews * K,
             "frames_in_flight": pipe.depth,
             "autotune": tuned,
@@ -425,24 +591,23 @@ def run_ours(args, rank, world, local):
             "work_per_frame": {"visible": float(np.mean(vis)), "instances": float(np.mean(inst)),
                                "alpha_evals": float(np.mean(evals)), "composited": float(np.mean(comps))},
             "roofline": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu",
-                         "achieved": achieved_timed, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved_timed / fp32_peak,
-                         "traffic": RENDER_FWD_TRAFFIC.get((tuned["tile"], tuned["pixels_per_thread"],
-                                                            tuned["shared_batch"])),
-                         "peak_basis": "SMs x 128 FP32 lanes x 2 (FMA) x max SM clock %.0f MHz (derived)" % sm_max,
-                         "flops_per_launch": mean_flops, "launch_ms": comp_ms_timed,
-                         "duration_basis": "CUDA events around each compositor launch on its slot stream in the "
-                                           "timed region (other frames' kernels share the GPU meanwhile)"},
+                         "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "traffic": NCU_RENDER_FWD["dram_bytes"] if ncu_ok else None,
+                         "peak_basis": "SMs x 128 FP32 lanes x 2 (FMA) x max SM clock %.0f MHz (derived; no FP32 "
+                                       "peak is measured)" % sm_max,
+                         "flops_per_launch": mean_flops, "launch_ms": comp_ms,
+                         "duration_basis": "CUDA events around each compositor launch with one frame in flight "
+                                           "(the per-stage pass over the sweep, timed configuration)",
+                         "issue": issue,
+                         "in_timed_region": {"launch_ms": comp_ms_timed, "achieved": achieved_timed,
+                                             "frac": achieved_timed / fp32_peak,
+                                             "basis": "events around each launch inside the timed region, %d "
+                                                      "frames sharing the GPU" % pipe.depth}},
             "roofline_throughput": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu",
                                     "achieved": mean_flops * value / world / 1e12, "peak": fp32_peak,
                                     "unit": "TFLOP/s", "frac": mean_flops * value / world / 1e12 / fp32_peak,
                                     "duration_basis": "the compositor's flops of every frame over the timed "
                                                       "region's wall time (one GPU; the other stages share it)"},
-            "roofline_isolated": {"kernel": "render_fwd_kernel (image mode, fgs4d_render_image)", "bound": "alu",
-                                  "achieved": achieved_iso,
-                                  "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved_iso / fp32_peak,
-                                  "launch_ms": float(stage_full[2]),
-                                  "duration_basis": "one frame in flight (the full-grid per-stage pass)"},
             "preprocess_roofline": {"bound": "hbm", "achieved": pre_gbs, "peak": hbm, "unit": "GB/s",
                                     "frac": pre_gbs / hbm, "bytes_per_launch": pre_bytes,
                                     "duration_basis": "one frame in flight, full-GPU grid",
@@ -451,6 +616,7 @@ def run_ours(args, rank, world, local):
             "e2e": e2e,
             "train": train,
             "batched": batched,
+            "c0": c0,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -458,59 +624,123 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def run_train(args, dev, scene, params, world, barrier):
-    """Training step: 4 timestamps x 1 camera, L1 loss, backward, Adam.  Two
-    forms of the same step: the 4 views in one batched call, and the 4 views
-    as single-view calls on 4 streams (ViewParallel; gradients accumulate in
-    the same buffers).  value = the faster one, each replayed as one CUDA
-    graph."""
+def compositor_counts(r, params, views_nv=None):
+    """(alpha evaluations, composited entries, evaluations up to each
+    pixel's last composited entry) of one forward of renderer r."""
     import torch
 
     from paper_2412_20720_gb300 import fgs4d
-    from paper_2412_20720_gb300 import synthetic as sy
+    stats = torch.zeros(3, dtype=torch.int64, device=r.device)
+    out = torch.empty(3 * r.total_pixels, dtype=torch.float32, device=r.device)
+    g = r.gaussians(params)
+    st = r.stream()
+    fgs4d.preprocess(g, r.views, r.nviews, r.settings, r.ws.data_ptr(), r.ws_bytes, st)
+    fgs4d.bin_sort(r.n, r.views, r.nviews, r.settings, r.ws.data_ptr(), r.ws_bytes, st)
+    fgs4d.render_stats(r.n, r.views, r.nviews, r.settings, r.ws.data_ptr(), r.ws_bytes, out.data_ptr(),
+                       stats.data_ptr(), st)
+    r.check()
+    return [int(x) for x in stats.tolist()]
+
+
+def fwd_bwd_stage_ms(r, params, dL, grads, reps: int = 3, loss=None):
+    """Per-stage milliseconds of one forward + backward call of renderer r
+    alone on the GPU (events between the stages; mean of ``reps``):
+    preprocess, bin_sort, render_fwd, [loss,] render_bwd_composite,
+    render_bwd_preprocess.  ``loss(img)`` (optional) returns dL/dimg."""
+    import numpy as np
+    import torch
+
+    from paper_2412_20720_gb300 import fgs4d
+    stream = torch.cuda.current_stream(r.device)
+    st = stream.cuda_stream
+    g = r.gaussians(params)
+    gg = r._grads(grads, None)
+    ws, wsb = r.ws.data_ptr(), r.ws_bytes
+    img = torch.empty(3 * r.total_pixels, dtype=torch.float32, device=r.device)
+    names = ["preprocess", "bin_sort", "render_fwd"] + (["l1_loss"] if loss else []) + \
+        ["render_bwd_composite", "render_bwd_preprocess"]
+    acc = np.zeros(len(names))
+    for _ in range(reps + 1):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        ev[0].record(stream)
+        fgs4d.preprocess(g, r.views, r.nviews, r.settings, ws, wsb, st)
+        ev[1].record(stream)
+        fgs4d.bin_sort(r.n, r.views, r.nviews, r.settings, ws, wsb, st)
+        ev[2].record(stream)
+        fgs4d.render_fwd(r.n, r.views, r.nviews, r.settings, ws, wsb, img.data_ptr(), None, st)
+        k = 3
+        ev[k].record(stream)
+        d = dL
+        if loss:
+            d = loss(img)
+            k += 1
+            ev[k].record(stream)
+        fgs4d.render_bwd_composite(r.n, r.views, r.nviews, r.settings, ws, wsb, d.data_ptr(), st)
+        ev[k + 1].record(stream)
+        fgs4d.render_bwd_preprocess(g, r.views, r.nviews, r.settings, ws, wsb, gg, st)
+        ev[k + 2].record(stream)
+        torch.cuda.synchronize()
+        if _ > 0:  # the first pass warms up
+            acc += [ev[i].elapsed_time(ev[i + 1]) for i in range(len(names))]
+    r.check()
+    return dict(zip(names, (acc / reps).tolist()))
+
+
+def run_train(args, dev, scene, params, world, barrier, views, tgt_scene, targets_np, fp32_peak):
+    """Training step (C2): 4 timestamps x 1 camera, L1 loss, backward to every
+    parameter (gradients cleared at the start of each step).  Two forms of
+    the same step: the 4 views in one batched call, and the 4 views as
+    single-view calls on 4 streams (ViewParallel; gradients accumulate in
+    the same buffers); value = the faster one, replayed as one CUDA graph.
+    The same step followed by an Adam update is reported beside it."""
+    import numpy as np
+    import torch
+
+    from paper_2412_20720_gb300 import fgs4d
     from paper_2412_20720_gb300.render import (PARAM_KEYS, Adam, RenderConfig, Renderer, ViewParallel, autotune,
                                                l1_loss)
 
-    views = sy.train_views(4, W_IMG, H_IMG)
     # The 4-view call runs alone on the GPU: full-GPU grids.  The view-parallel
     # form runs four calls at once: lean grids for their latency-bound stages.
     cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 25)
-    tgt_scene = sy.orbit_scene(args.n, seed=sy.TARGET_SEED)
-    tparams = {k: torch.from_numpy(v).to(dev) for k, v in tgt_scene.as_dict().items()}
-    rt = Renderer(tgt_scene.n, views, cfg, device=dev)
-    target = rt.forward(tparams).clone()
-    rt.check()
-    targets = [t.reshape(-1).clone() for t in rt.split(target)]
-    del rt, tparams
-    leaf = {k: params[k].clone().requires_grad_(True) for k in PARAM_KEYS}
+    if targets_np is not None:
+        targets = [torch.from_numpy(np.ascontiguousarray(t).reshape(-1)).to(dev) for t in targets_np]
+        target_src = "rendered by the FP64 oracle from a second seeded scene (seed %d)" % tgt_scene_seed()
+    else:
+        tparams = {k: torch.from_numpy(v).to(dev) for k, v in tgt_scene.as_dict().items()}
+        rt = Renderer(tgt_scene.n, views, cfg, device=dev)
+        tflat = rt.forward(tparams).clone()
+        rt.check()
+        targets = [t.reshape(-1).clone() for t in rt.split(tflat)]
+        del rt, tparams
+        target_src = "rendered by the CUDA path from a second seeded scene (the CPU leg did not run)"
+    target = torch.cat(targets)
+    pr = {k: params[k].clone() for k in PARAM_KEYS}
     r = Renderer(scene.n, views, cfg, device=dev)
-    tuned = autotune(r, {k: leaf[k].detach() for k in PARAM_KEYS}, backward=True, tiles=(16, 8), batches=(256, 128))
+    tuned = autotune(r, pr, backward=True, tiles=(16, 8), batches=(256, 128))
     vp = ViewParallel(scene.n, [[v] for v in views],
                       RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24,
                                    stage_blocks_per_sm=args.stage_blocks),
                       device=dev)
     vp.set_tile(tuned["tile"], tuned["pixels_per_thread"], tuned["shared_batch"])
-    grads = {k: torch.zeros_like(leaf[k]) for k in PARAM_KEYS}
-    # Adam with the library's kernel; its step count lives on the device, so
-    # the whole step can be replayed as one CUDA graph.
-    pr = {k: leaf[k].detach() for k in PARAM_KEYS}
+    grads = {k: torch.zeros_like(pr[k]) for k in PARAM_KEYS}
     opt = Adam(pr, lr=1e-4)
     total = int(target.numel())
     vp_loss = torch.zeros(1, dtype=torch.float32, device=dev)
 
-    # The gradients start at zero and Adam clears each one after reading it
-    # (zero_grad), so every step accumulates into zeros without a fill.
     def it_batched():
+        for gk in grads.values():
+            gk.zero_()
         img = r.forward(pr)
         loss, dimg = l1_loss(img, target)
         r.backward(pr, dimg, grads)
-        opt.step(grads, zero_grad=True)
         return loss
 
     def it_parallel():
+        for gk in grads.values():
+            gk.zero_()
         vp_loss.zero_()
         vp.step(pr, lambda j, img: l1_loss(img, targets[j], mean_count=total, loss=vp_loss)[1], grads)
-        opt.step(grads, zero_grad=True)
         return vp_loss
 
     stream = torch.cuda.current_stream(dev)
@@ -551,20 +781,70 @@ def run_train(args, dev, scene, params, world, barrier):
         del graph
         res[name] = {"ms_per_iter": max_over_ranks(ms, world, dev), "loss": loss,
                      "plain_launches_ms_per_iter": max_over_ranks(plain_ms, world, dev)}
-    codes = [r.status()[0]] + [g.status()[0] for g in vp.groups]
     best = min(res, key=lambda k: res[k]["ms_per_iter"])
     ms = res[best]["ms_per_iter"]
+    step = it_batched if best == "batched_call" else it_parallel
+
+    def it_adam():
+        loss = step()
+        opt.step(grads)
+        return loss
+
+    graph, _ = graph_of(it_adam)
+    ms_adam, _ = timed(lambda: graph.replay())
+    del graph
+    ms_adam = max_over_ranks(ms_adam, world, dev)
+    codes = [r.status()[0]] + [g.status()[0] for g in vp.groups]
+
+    # Stages of the 4-view call alone, and the compositors' work counts.
+    stages = fwd_bwd_stage_ms(r, pr, None, grads, loss=lambda img: l1_loss(img, target)[1])
+    ev, co, evb = compositor_counts(r, pr)
+    flops_fwd = FLOPS_PER_EVAL * ev + FLOPS_PER_COMP * co
+    flops_bwd = FLOPS_PER_EVAL * evb + FLOPS_PER_BWD_COMP * co
+    ach_b = flops_bwd / (stages["render_bwd_composite"] * 1e-3) / 1e12
+    ach_f = flops_fwd / (stages["render_fwd"] * 1e-3) / 1e12
     return {"metric": "fwd+bwd iters/s", "value": job_rate(1, world, ms), "unit": "iters/s", "ms_per_iter": ms,
             "form": best,
             "workload": "4 timestamps x 1 camera at 1352x1014, %d Gaussians, L1 loss (mean over the 4 images), "
-                        "backward to all parameters, Adam step (fgs4d kernel); the step replayed as one CUDA graph"
-                        % scene.n,
+                        "backward to all parameters; the step replayed as one CUDA graph" % scene.n,
+            "targets": target_src,
             "forms": res,
-            "status": fgs4d.status_string(min(codes)), "autotune": tuned,
-            "targets": "rendered by the CUDA path from a second seeded scene"}
+            "with_adam": {"ms_per_iter": ms_adam, "iters_per_s": job_rate(1, world, ms_adam),
+                          "step": "the same step followed by fgs4d_adam_update_set (Adam, one launch)"},
+            "stages_ms": stages,
+            "stages_basis": "the 4-view call alone on the GPU, events between the stages (full-GPU grids)",
+            "work": {"alpha_evals": ev, "composited": co, "bwd_alpha_evals": evb},
+            "roofline": {"kernel": "render_bwd_kernel (fgs4d_render_bwd_composite)", "bound": "alu",
+                         "achieved": ach_b, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach_b / fp32_peak,
+                         "traffic": None, "flops_per_launch": flops_bwd,
+                         "launch_ms": stages["render_bwd_composite"],
+                         "flops_basis": "%d per alpha evaluation up to each pixel's last composited entry + %d per "
+                                        "composited (pixel, entry)" % (FLOPS_PER_EVAL, FLOPS_PER_BWD_COMP),
+                         "duration_basis": "CUDA events around fgs4d_render_bwd_composite (slot-gradient clear + "
+                                           "render_bwd_kernel), the 4-view call alone"},
+            "roofline_fwd": {"kernel": "render_fwd_kernel (mode with backward state)", "bound": "alu",
+                             "achieved": ach_f, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach_f / fp32_peak,
+                             "launch_ms": stages["render_fwd"]},
+            "status": fgs4d.status_string(min(codes)), "autotune": tuned}
 
 
-def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,)):
+def tgt_scene_seed() -> int:
+    from paper_2412_20720_gb300 import synthetic as sy
+    return sy.TARGET_SEED
+
+
+def bin_sort_bytes(vis: int, inst: int, total_tiles: int) -> float:
+    """Algorithmic DRAM bytes of fgs4d_bin_sort: the depth sort's four 8-bit
+    passes over the visible pairs (key and value read and written, 16 B), the
+    pair scan (52 B read and 52 B written per pair), the emission (8 B per
+    instance) and the tile sort's ceil(bits / 8) passes (16 B per instance),
+    plus the ranges (8 B per tile)."""
+    import math
+    passes = max(1, math.ceil(max(1, math.ceil(math.log2(max(total_tiles, 2)))) / 8))
+    return vis * (4 * 16 + 104) + inst * (8 + 16 * passes) + 8 * total_tiles
+
+
+def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,), hbm=6800.0):
     """Forward + backward of many (camera, t) views of mixed resolution: one
     multi-view call per group of ``group`` views, all groups of a step
     captured in one CUDA graph, against one plain single-view call per view.
@@ -634,12 +914,29 @@ def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,))
     codes = [r.status()[0] for r in rs]
     code = next((c for c in codes if c != fgs4d.OK), fgs4d.OK)
     graph_ms = a.elapsed_time(b) / steps
+    # Per-stage times: each group's call alone on the GPU, events between the
+    # stages, summed over the groups of a step.
+    stages = {}
+    for r, dL in zip(rs, dLs):
+        for k, v in fwd_bwd_stage_ms(r, params, dL, grads, reps=2).items():
+            stages[k] = stages.get(k, 0.0) + v
+    tiles_tot = sum(int(r.layout.total_tiles) for r in rs)
+    bs_bytes = bin_sort_bytes(vis_tot, inst_tot, tiles_tot // len(rs)) if rs else 0.0
+    bs_gbs = bs_bytes / (stages["bin_sort"] * 1e-3) / 1e9
     out = {"workload": label, "gaussians": n, "views": len(views), "views_per_call": group,
            "resolutions": sorted({"%dx%d" % (v["width"], v["height"]) for v in views}),
            "visible_pairs": vis_tot, "instances": inst_tot, "status": fgs4d.status_string(code),
            "autotune": tuned,
            "graph_batched": {"ms_per_step": graph_ms, "views_per_s": len(views) * 1000.0 / graph_ms,
-                             "fwd_bwd_iters_per_s": 1000.0 / graph_ms}}
+                             "fwd_bwd_iters_per_s": 1000.0 / graph_ms},
+           "stages_ms_per_step": stages,
+           "stages_basis": "each call alone on the GPU (full-GPU grids), events between the stages, summed over "
+                           "the %d calls of a step" % len(rs),
+           "bin_sort_roofline": {"bound": "hbm", "achieved": bs_gbs, "peak": hbm, "unit": "GB/s",
+                                 "frac": bs_gbs / hbm, "bytes_per_step": bs_bytes,
+                                 "bytes_basis": "bin_sort_bytes(): depth sort, pair scan, emission, tile-sort "
+                                                "passes and ranges",
+                                 "peak_basis": "measured hbm_gbs"}}
     del graph
     # The same groups as calls on parallel streams (lean grids for their
     # latency-bound stages; the same workspace layout), one graph.
@@ -746,6 +1043,45 @@ def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,))
     return out
 
 
+def run_tiny(dev, frames: int = 400):
+    """C0: 2,000 Gaussians (degree 1 x order 1), one 128x96 view per call,
+    preprocess + bin_sort + render_image; frames/s over ``frames`` calls
+    (one frame in flight), after a warm-up."""
+    import torch
+
+    from paper_2412_20720_gb300 import fgs4d
+    from paper_2412_20720_gb300 import synthetic as sy
+    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer
+    sc = sy.tiny_scene()
+    params = {k: torch.from_numpy(v).to(dev) for k, v in sc.as_dict().items()}
+    views = [sy.tiny_view(128, 96, t=k / (frames - 1)) for k in range(frames)]
+    r = Renderer(sc.n, views[:1], RenderConfig(sh_degree=1, t_order=1, inst_capacity=1 << 18), device=dev)
+    vv = [fgs4d.make_views([v]) for v in views]
+    g = r.gaussians({k: params[k] for k in PARAM_KEYS})
+    out = torch.empty(3 * 128 * 96, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+
+    def sweep():
+        for v, n1 in vv:
+            fgs4d.preprocess(g, v, n1, r.settings, r.ws.data_ptr(), r.ws_bytes, st)
+            fgs4d.bin_sort(sc.n, v, n1, r.settings, r.ws.data_ptr(), r.ws_bytes, st)
+            fgs4d.render_image(sc.n, v, n1, r.settings, r.ws.data_ptr(), r.ws_bytes, out.data_ptr(), None, st)
+
+    sweep()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sweep()
+    b.record(stream)
+    torch.cuda.synchronize()
+    code, _ = r.status()
+    ms = a.elapsed_time(b)
+    return {"workload": "tiny-2k-128x96 (2,000 Gaussians, SH degree 1 x order 1)", "frames_per_s": frames / ms * 1e3,
+            "ms_per_frame": ms / frames, "frames": frames, "status": fgs4d.status_string(code),
+            "basis": "one view per call, one frame in flight, CUDA events around %d calls" % frames}
+
+
 # ------------------------------------------------------------ reference
 
 def run_reference(args, rank, world):
@@ -760,7 +1096,8 @@ def run_reference(args, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": {"workload": WORKLOAD, "gaussians": args.n, "sh_degree": 3, "t_order": 2,
                        "resolution": [W_IMG, H_IMG], "views_per_step": 1},
-            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                             "host_cpus": os.cpu_count(),
                              "sample": "one full view of the sweep per step (FP64 oracle, OpenMP)"},
             "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

@@ -153,8 +153,10 @@ typedef struct fgs4d_gaussians_out {
 typedef struct fgs4d_layout {
   size_t bytes;         /* total workspace size */
   size_t counters;      /* uint32: [0] visible pairs, [1] instances, [2] status bits */
-  size_t rec_geom;      /* float4 [vis_cap]: (u, v, A', B') with power2 = -(A' dx^2 + B' dx dy + C' dy^2) */
-  size_t rec_color;     /* float4 [vis_cap]: (C', log2 a, r, g) with a = sigmoid(logit) p(t) */
+  size_t rec_geom;      /* float4 [vis_cap]: (u, v, a1, b1): the exponent in base 2 is power2 = -q,
+                           q = (a1 dx)^2 + (b1 dx + b2 dy)^2, (dx, dy) = (u, v) - pixel centre, i.e.
+                           (1/2) log2(e) times the conic form of Sigma_2d^-1 as a sum of two squares */
+  size_t rec_color;     /* float4 [vis_cap]: (b2, log2 a, r, g) with a = sigmoid(logit) p(t) */
   size_t rec_blue;      /* float  [vis_cap]: b */
   size_t rec_tau;       /* float  [vis_cap]: log2(255 a) + 4e-3; alpha >= 1/255 needs -power2 <= tau */
   size_t rec_meta;      /* int32x4 [vis_cap]: (gaussian, view, x0 | y0 << 16, x1 | y1 << 16) tile rect */
@@ -252,10 +254,12 @@ int fgs4d_render_aux(const fgs4d_gaussians *gaussians, const fgs4d_view *views, 
                      float *out_rgb, float *out_T, float *out_aux, void *stream);
 
 /* Diagnostic form of fgs4d_render_fwd: renders identically into out_rgb and
- * ADDS to stats_out (device uint64[2], 8-byte aligned) the number of
- * pixel-entry alpha evaluations and of composited entries -- the work
- * counts from which the compositor's algorithmic FLOPs are stated.  Has no
- * counterpart in the paper. */
+ * ADDS to stats_out (device uint64[3], 8-byte aligned) the number of
+ * pixel-entry alpha evaluations, of composited entries, and of the
+ * evaluations at list positions up to each pixel's last composited entry
+ * (those fgs4d_render_bwd repeats) -- the work counts from which the
+ * compositors' algorithmic FLOPs are stated.  Has no counterpart in the
+ * paper. */
 int fgs4d_render_stats(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
                        void *workspace, size_t workspace_bytes, float *out_rgb, uint64_t *stats_out, void *stream);
 
@@ -268,6 +272,24 @@ int fgs4d_render_stats(int64_t n, const fgs4d_view *views, int32_t nviews, const
 int fgs4d_render_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
                      const fgs4d_settings *settings, void *workspace, size_t workspace_bytes,
                      const float *dL_drgb, const fgs4d_gaussians_grad *grads, void *stream);
+
+/* fgs4d_render_bwd in its two stages, for callers that want the per-slot
+ * screen-space gradients alone or time the stages apart; the two calls in
+ * this order on one stream do exactly what fgs4d_render_bwd does.
+ * fgs4d_render_bwd_composite: the adjoint of the compositing (Eq. 6) over
+ * every tile of the matching forward; overwrites the workspace's slot_grad
+ * region (fgs4d_layout) with dL/d(u, v, A, B, C, a, r, g, b) per visible
+ * slot.  Errors: as fgs4d_render_fwd, FGS4D_ERR_ARG for a NULL dL_drgb.
+ * fgs4d_render_bwd_preprocess: the adjoint of the per-Gaussian chain (the
+ * 4DSH colour, EWA projection, slice, marginal, rotation and activations of
+ * Sec. 3.1-3.2) from the slot gradients; ADDS into `grads` (and the
+ * optional densification statistics and mask gradient) as fgs4d_render_bwd
+ * does.  Errors: as fgs4d_render_bwd. */
+int fgs4d_render_bwd_composite(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                               void *workspace, size_t workspace_bytes, const float *dL_drgb, void *stream);
+int fgs4d_render_bwd_preprocess(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                                const fgs4d_settings *settings, void *workspace, size_t workspace_bytes,
+                                const fgs4d_gaussians_grad *grads, void *stream);
 
 /* Reverse-mode derivative of a loss on the image and on the depth and
  * opacity channels of fgs4d_render_aux (the inputs of the LiDAR depth loss
@@ -427,6 +449,17 @@ int fgs4d_wait_selftest(void *scratch, size_t scratch_bytes, void *stream);
  * pointer with n > 0; FGS4D_ERR_CUDA if the lookup or a launch fails.  n = 0
  * does nothing. */
 int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, uint32_t *sorted_slots, void *stream);
+
+/* Outcome of the last fgs4d_sort_depth_static call on the current device,
+ * as the device saw it.  fgs4d_sort_depth_static only enqueues work, and its
+ * radix passes record a bounded wait that ran out, or a position outside the
+ * array, in a status word of the library-owned scratch instead of trapping;
+ * that word is cleared by the next sort call.  This call synchronises
+ * `stream` (the stream of that sort), reads the word and returns FGS4D_OK
+ * (the permutation in sorted_slots is valid), FGS4D_ERR_TIMEOUT or
+ * FGS4D_ERR_INTERNAL (sorted_slots must not be used); FGS4D_ERR_CUDA if the
+ * read fails.  Allocates nothing.  No counterpart in the paper. */
+int fgs4d_sort_depth_static_status(void *stream);
 
 /* Synchronises `stream`, then reads the workspace status word.  Returns
  * FGS4D_OK, or the first recorded device condition (FGS4D_ERR_CAPACITY,

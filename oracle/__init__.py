@@ -54,7 +54,8 @@ _PROJ_FIELDS = [("status", np.int32, 1), ("rect", np.int32, 4), ("p_t", np.float
                 ("a_eff", np.float64, 1), ("mu3", np.float64, 3), ("cov3", np.float64, 9),
                 ("pc", np.float64, 3), ("cov2d", np.float64, 3), ("conic", np.float64, 3),
                 ("uv", np.float64, 2), ("radius", np.float64, 1), ("depth", np.float64, 1),
-                ("rgb", np.float64, 3), ("margin", np.float64, 1), ("depth_f32", np.float32, 1)]
+                ("rgb", np.float64, 3), ("margin", np.float64, 1), ("depth_f32", np.float32, 1),
+                ("uncertain", np.int32, 1), ("rect_lo", np.int32, 4), ("rect_hi", np.int32, 4)]
 
 
 class _Proj(C.Structure):
@@ -65,6 +66,31 @@ _GRAD_FIELDS = ["mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh", "g_uv"
                 "mask_logit"]
 
 
+class _Tol(C.Structure):
+    _fields_ = [("eps_conic", C.c_double), ("eps_uv", C.c_double), ("eps_uv_abs", C.c_double), ("eps_a", C.c_double),
+                ("eps_alpha", C.c_double), ("depth_ulps", C.c_int32), ("max_leaves", C.c_int32)]
+
+
+@dataclass
+class Tolerance:
+    """Error bounds of an FP32 renderer's per-pixel inputs, relative to the
+    FP64 values (see orc_render_pixels_admissible): the factors of the conic
+    Q = U U^T (u11, u22 relative, u12 relative to |u12| + sqrt(Q11)),
+    projected centre (eps_uv |u| + eps_uv_abs pixels), effective opacity, the
+    exponential; depth keys within depth_ulps units in the last place."""
+    eps_conic: float = 0.0
+    eps_uv: float = 0.0
+    eps_uv_abs: float = 0.0
+    eps_a: float = 0.0
+    eps_alpha: float = 0.0
+    depth_ulps: int = 0
+    max_leaves: int = 4096
+
+    def _c(self) -> _Tol:
+        return _Tol(self.eps_conic, self.eps_uv, self.eps_uv_abs, self.eps_a, self.eps_alpha, self.depth_ulps,
+                    self.max_leaves)
+
+
 class _Grads(C.Structure):
     _fields_ = [(name, C.c_void_p) for name in _GRAD_FIELDS]
 
@@ -73,6 +99,15 @@ def _declare(lib):
     P = C.POINTER
     lib.orc_preprocess.argtypes = [P(_Params), P(_View), P(_Settings), P(_Proj)]
     lib.orc_preprocess.restype = C.c_int
+    lib.orc_preprocess_relaxed.argtypes = [P(_Params), P(_View), P(_Settings), C.c_double, P(_Proj)]
+    lib.orc_preprocess_relaxed.restype = C.c_int
+    lib.orc_render_pixels_admissible.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), P(_Tol), C.c_void_p,
+                                                 C.c_int32, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
+                                                 C.c_void_p, C.c_void_p]
+    lib.orc_render_pixels_admissible.restype = C.c_int
+    lib.orc_alpha_bounds.argtypes = [P(_View), P(_Proj), P(_Tol), C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]
+    lib.orc_alpha_bounds.restype = None
     lib.orc_render.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_render.restype = C.c_int
@@ -84,7 +119,7 @@ def _declare(lib):
     lib.orc_preprocess_backward.argtypes = [P(_Params), P(_View), P(_Settings), C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p, P(_Grads)]
     lib.orc_preprocess_backward.restype = C.c_int
-    lib.orc_aux.argtypes = [P(_Params), P(_View), P(_Settings), C.c_double, P(_Proj), C.c_void_p]
+    lib.orc_aux.argtypes = [P(_Params), P(_View), P(_Settings), C.c_double, C.c_double, P(_Proj), C.c_void_p]
     lib.orc_aux.restype = C.c_int
     lib.orc_render_aux.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p]
@@ -101,18 +136,19 @@ def _declare(lib):
     lib.orc_render_features_backward.argtypes = [P(_View), P(_Settings), C.c_int64, P(_Proj), C.c_void_p, C.c_int,
                                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_render_features_backward.restype = C.c_int
+    lib.orc_gated_features.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]
+    lib.orc_gated_features.restype = None
     lib.orc_rotation.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.orc_rotation.restype = None
     lib.orc_real_sh.argtypes = [C.c_int, C.c_void_p, C.c_void_p]
     lib.orc_real_sh.restype = None
-    lib.orc_sort_instances.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                       C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
+    lib.orc_sort_instances.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int64,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
-    lib.orc_ellipse_meets_box.argtypes = [C.c_float] * 10
-    lib.orc_ellipse_meets_box.restype = C.c_int
     lib.orc_sort_instances.restype = C.c_int64
     lib.orc_num_threads.argtypes = []
     lib.orc_num_threads.restype = C.c_int
+    lib.orc_set_num_threads.argtypes = [C.c_int]
+    lib.orc_set_num_threads.restype = None
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -172,8 +208,11 @@ class _ParamsHold:
         self.n = n
 
 
-def preprocess(params, view, settings: Settings):
-    """Per-Gaussian forward chain (FP64).  Returns a dict of arrays."""
+def preprocess(params, view, settings: Settings, relax: float = 0.0):
+    """Per-Gaussian forward chain (FP64).  Returns a dict of arrays.  With
+    relax > 0, decisions within that relative distance of their thresholds
+    are marked ("uncertain", "rect_lo", "rect_hi"; orc_preprocess_relaxed);
+    the FP64 decisions and values are the same either way."""
     lib = _load()
     ph = _ParamsHold(params)
     n = ph.n
@@ -181,7 +220,11 @@ def preprocess(params, view, settings: Settings):
     for name, dt, w in _PROJ_FIELDS:
         out[name] = np.zeros((n, w) if w > 1 else (n,), dtype=dt)
     pc = _Proj(*(_ptr(out[name]) for name, _, _ in _PROJ_FIELDS))
-    rc = lib.orc_preprocess(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), C.byref(pc))
+    if relax > 0.0:
+        rc = lib.orc_preprocess_relaxed(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), float(relax),
+                                        C.byref(pc))
+    else:
+        rc = lib.orc_preprocess(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), C.byref(pc))
     if rc != 0:
         raise ValueError("oracle preprocess rejected the settings")
     return out
@@ -230,16 +273,69 @@ def render_pixels(proj, view, settings: Settings, pix: np.ndarray):
     return rgb, T, nc, mg
 
 
-def aux_records(params, proj, view, settings: Settings, flow_dt: float) -> np.ndarray:
+def render_pixels_admissible(proj, view, settings: Settings, pix: np.ndarray, tol: Tolerance, extra=None,
+                             max_cands: int = 64):
+    """Every result an FP32 renderer within ``tol`` may produce at the given
+    pixels (linear ids py*W+px): a list of [k, 5 + E] arrays (r, g, b, T,
+    contributors, extra channels), one per pixel, and flags [P] (bit 1 two
+    outcomes were admissible somewhere, bit 2 a composited entry's derivative
+    is uncertain, bit 4 the walk ran out of budget)."""
+    lib = _load()
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    n = proj["status"].shape[0]
+    ne = 0 if extra is None else int(np.asarray(extra).reshape(n, -1).shape[1])
+    ex = None if extra is None else np.ascontiguousarray(np.asarray(extra, dtype=np.float64).reshape(n, ne))
+    P = pix.shape[0]
+    cands = np.zeros((P, max_cands, 5 + ne))
+    ncands = np.zeros(P, dtype=np.int32)
+    flags = np.zeros(P, dtype=np.int32)
+    pc, keep = _proj_c(proj)
+    rc = lib.orc_render_pixels_admissible(C.byref(_view_c(view)), C.byref(settings._c()), n, C.byref(pc),
+                                          C.byref(tol._c()), _ptr(ex) if ex is not None else None, ne, P, _ptr(pix),
+                                          max_cands, _ptr(cands), _ptr(ncands), _ptr(flags))
+    if rc != 0:
+        raise MemoryError("oracle render_pixels_admissible failed")
+    return [cands[q, :ncands[q]] for q in range(P)], flags
+
+
+def alpha_bounds(proj, view, tol: Tolerance, idx, pix):
+    """FP64 alpha = min(0.99, a exp(power)) of Gaussians idx at pixels pix
+    (linear ids py*W+px, sample at the centre), and the relative error bound
+    of an FP32 renderer's alpha there (render_pixels_admissible's model)."""
+    lib = _load()
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    alpha = np.zeros(idx.shape[0])
+    err = np.zeros(idx.shape[0])
+    pc, keep = _proj_c(proj)
+    lib.orc_alpha_bounds(C.byref(_view_c(view)), C.byref(pc), C.byref(tol._c()), idx.shape[0], _ptr(idx), _ptr(pix),
+                         _ptr(alpha), _ptr(err))
+    return alpha, err
+
+
+def aux_records(params, proj, view, settings: Settings, flow_dt: float, relax: float = 0.0) -> np.ndarray:
     """Per Gaussian (z, flow_u, flow_v): camera depth of the sliced mean and
-    its projected displacement over flow_dt (zeros for culled Gaussians)."""
+    its projected displacement over flow_dt (zeros for culled Gaussians; with
+    relax > 0 and a projection from preprocess(..., relax), also filled for
+    the Gaussians it marks as possibly present)."""
     lib = _load()
     ph = _ParamsHold(params)
     aux = np.zeros((ph.n, 3))
     pc, keep = _proj_c(proj)
-    lib.orc_aux(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), float(flow_dt), C.byref(pc),
-                _ptr(aux))
+    lib.orc_aux(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), float(flow_dt), float(relax),
+                C.byref(pc), _ptr(aux))
     return aux
+
+
+def gated_features(features: np.ndarray, gate=None) -> np.ndarray:
+    """Normalised scale-gated features S (.) f / |S (.) f| (FP64, [n, D])."""
+    lib = _load()
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    n, D = f.shape
+    g = None if gate is None else np.ascontiguousarray(gate, dtype=np.float64)
+    out = np.zeros((n, D))
+    lib.orc_gated_features(_ptr(f), n, D, _ptr(g) if g is not None else None, _ptr(out))
+    return out
 
 
 def render_aux(proj, aux: np.ndarray, view, settings: Settings):
@@ -407,20 +503,14 @@ def real_sh(L: int, direction) -> np.ndarray:
     return Y
 
 
-def sort_instances(rect, depth_f32, grid_w: int, grid_h: int, cap: int | None = None, uv=None, conic2=None,
-                   tau=None, width: int = 0, height: int = 0, tile: int = 16):
-    """Tile-binned instance list sorted by (tile, FP32 depth, index).
-    With uv, conic2 (A', B', C': q = A' dx^2 + B' dx dy + C' dy^2) and tau
-    (FP32 arrays) a rect tile (edge ``tile`` pixels) is kept only if the
-    ellipse q <= tau meets its pixel centres (image width x height).
+def sort_instances(rect, depth_f32, grid_w: int, grid_h: int, cap: int | None = None):
+    """Tile-binned instance list of the tile rasterizer: one instance per tile
+    of each rect, sorted by (tile, FP32 depth, index).
     Returns (keys u64 [M], vals i64 [M], ranges i64 [tiles, 2])."""
     lib = _load()
     rect = np.ascontiguousarray(rect, dtype=np.int32)
     depth_f32 = np.ascontiguousarray(depth_f32, dtype=np.float32)
     n = rect.shape[0]
-    ex = [None, None, None]
-    if uv is not None:
-        ex = [np.ascontiguousarray(x, dtype=np.float32) for x in (uv, conic2, tau)]
     w = np.clip(rect[:, 2] - rect[:, 0], 0, None).astype(np.int64)
     h = np.clip(rect[:, 3] - rect[:, 1], 0, None).astype(np.int64)
     m = int((w * h).sum())
@@ -428,19 +518,17 @@ def sort_instances(rect, depth_f32, grid_w: int, grid_h: int, cap: int | None = 
     keys = np.zeros(max(m, 1), dtype=np.uint64)
     vals = np.zeros(max(m, 1), dtype=np.int64)
     ranges = np.zeros((grid_w * grid_h, 2), dtype=np.int64)
-    got = lib.orc_sort_instances(n, _ptr(rect), _ptr(depth_f32), *(None if x is None else _ptr(x) for x in ex),
-                                 int(width), int(height), int(tile), grid_w, grid_h, cap, _ptr(keys), _ptr(vals),
+    got = lib.orc_sort_instances(n, _ptr(rect), _ptr(depth_f32), grid_w, grid_h, cap, _ptr(keys), _ptr(vals),
                                  _ptr(ranges))
     if got < 0:
         raise ValueError("instance count exceeds capacity")
     return keys[:got], vals[:got], ranges
 
 
-def ellipse_meets_box(u, v, A, B, C, tau, x0, x1, y0, y1) -> bool:
-    """FP32 test of the ellipse A dx^2 + B dx dy + C dy^2 <= tau against a box."""
-    return bool(_load().orc_ellipse_meets_box(*(float(np.float32(x)) for x in (u, v, A, B, C, tau, x0, x1, y0,
-                                                                                 y1))))
-
-
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads the oracle's parallel loops use from now on."""
+    _load().orc_set_num_threads(int(n))

@@ -86,6 +86,12 @@ typedef struct {
   double *rgb;     /* [n][3] 4DSH colour after offset and clamp */
   double *margin;  /* [n] relative distance of the closest discrete decision */
   float *depth_f32;/* [n] depth rounded to FP32 (the sort key) */
+  /* Filled by orc_preprocess_relaxed only (may be NULL otherwise): */
+  int32_t *uncertain; /* [n] bit 1: a cull decision lies within the relaxation of its threshold, so the
+                         Gaussian may be present or absent; bit 2: the colour clamp max(0, .) is within
+                         the relaxation (the value is continuous there, its derivative is not) */
+  int32_t *rect_lo;   /* [n][4] tiles inside the rect for every admissible radius and edge rounding */
+  int32_t *rect_hi;   /* [n][4] tiles inside the rect for some admissible radius and edge rounding */
 } orc_proj;
 
 typedef struct {
@@ -124,6 +130,9 @@ typedef struct {
   double mask; /* M = sigmoid(m), 1 without a mask */
   int status;
   double margin;
+  double relax;    /* 0: plain decisions; > 0: see orc_preprocess_relaxed */
+  int uncertain;   /* bits as orc_proj.uncertain */
+  int rect_lo[4], rect_hi[4];
 } orc_ctx;
 
 /* ------------------------------------------------------------ helpers */
@@ -229,13 +238,34 @@ static double frac_margin(double x, double scale) {
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+/* One cull decision of the forward chain, `fails` taken in FP64, `m` its
+ * relative distance from the threshold.  Returns 1 when the chain stops.
+ * Plain mode (relax = 0): a failing test stops the chain with `code`.
+ * Relaxed mode: a decision within relax of its threshold could go either way
+ * in another precision; the Gaussian is marked uncertain (bit 1) and, if the
+ * FP64 test failed, `status` keeps the FP64 decision while the chain goes on
+ * so that the values it would have if it passed are available. */
+static int cull(orc_ctx *g, int fails, double m, int code) {
+  g->margin = dmin(g->margin, m);
+  const int near = m < g->relax;
+  if (near) g->uncertain |= 1;
+  if (!fails) return 0;
+  if (near) {
+    if (!g->status) g->status = code;
+    return 0;
+  }
+  g->status = code;
+  return 1;
+}
+
 /* Forward chain for Gaussian i at one view: Sec. 3.2 (covariance, rotation,
  * conditional and marginal), Sec. 3.1 Eqs. 3-4 (EWA projection), Sec. 3.2
  * (4D spherindrical harmonic colour), Sec. 8.1.1 (temporal filter). */
 static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
-                          const orc_settings *S, orc_ctx *g) {
+                          const orc_settings *S, orc_ctx *g, double relax) {
   memset(g, 0, sizeof *g);
   g->margin = INFINITY;
+  g->relax = relax;
   for (int k = 0; k < 4; ++k) {
     g->m[k] = P->mean[4 * i + k];
     g->ls[k] = P->log_scale[4 * i + k];
@@ -264,11 +294,9 @@ static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
       return;
     }
     g->mask = 1.0 / (1.0 + exp(-mlog));
-    g->margin = dmin(g->margin, fabs(g->mask - P->mask_threshold) / dmax(P->mask_threshold, 1e-12));
-    if (!(g->mask > P->mask_threshold)) {
-      g->status = 7;
+    if (cull(g, !(g->mask > P->mask_threshold), fabs(g->mask - P->mask_threshold) / dmax(P->mask_threshold, 1e-12),
+             7))
       return;
-    }
   }
   /* Activations: s = exp(log s), alpha = sigmoid(logit), unit quaternions. */
   for (int k = 0; k < 4; ++k) g->s[k] = exp(g->ls[k]);
@@ -297,11 +325,7 @@ static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
   g->dt = V->t - g->m[3];
   g->c = g->S[15];
   g->pt = exp(-0.5 * g->dt * g->dt / g->c);
-  g->margin = dmin(g->margin, fabs(g->pt - S->p_t_min) / S->p_t_min);
-  if (!(g->pt >= S->p_t_min)) {
-    g->status = 2;
-    return;
-  }
+  if (cull(g, !(g->pt >= S->p_t_min), fabs(g->pt - S->p_t_min) / S->p_t_min, 2)) return;
   /* Conditional 3D Gaussian at t (Sec. 3.2). */
   for (int a = 0; a < 3; ++a) g->b[a] = g->S[4 * a + 3];
   for (int a = 0; a < 3; ++a) g->mu3[a] = g->m[a] + g->b[a] * g->dt / g->c;
@@ -313,9 +337,11 @@ static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
   for (int a = 0; a < 3; ++a)
     g->pc[a] = W[4 * a + 0] * g->mu3[0] + W[4 * a + 1] * g->mu3[1] + W[4 * a + 2] * g->mu3[2] + W[4 * a + 3];
   const double x = g->pc[0], y = g->pc[1], z = g->pc[2];
-  g->margin = dmin(g->margin, fabs(z - S->near_plane) / dmax(S->near_plane, 1e-3));
-  if (!(z > S->near_plane)) {
+  /* (a relaxed chain goes on only while z stays positive) */
+  if (cull(g, !(z > S->near_plane), fabs(z - S->near_plane) / dmax(S->near_plane, 1e-3), 3)) return;
+  if (!(z > 0.0)) {
     g->status = 3;
+    g->uncertain = 0;
     return;
   }
   /* Eq. 4: Sigma_2d = (J W Sigma W^T J^T)_{1:2,1:2} + dilation I. */
@@ -335,11 +361,14 @@ static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
       g->cov2[2 * r + col] = acc + (r == col ? S->dilation : 0.0);
     }
   g->det = g->cov2[0] * g->cov2[3] - g->cov2[1] * g->cov2[2];
-  g->margin = dmin(g->margin, g->det / (fabs(g->cov2[0] * g->cov2[3]) + 1e-300));
+  /* A non-positive determinant has no conic: that cull is never relaxed. */
   if (!(g->det > 0.0)) {
+    g->margin = 0.0;
     g->status = 4;
+    g->uncertain = 0;
     return;
   }
+  cull(g, 0, g->det / (fabs(g->cov2[0] * g->cov2[3]) + 1e-300), 4);
   g->conic[0] = g->cov2[3] / g->det;
   g->conic[1] = -g->cov2[1] / g->det;
   g->conic[2] = g->cov2[0] / g->det;
@@ -365,18 +394,53 @@ static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
   g->rect[1] = clampi((int)floor(dmax(-lim, dmin(lim, ex[1]))), 0, gh);
   g->rect[2] = clampi((int)floor(dmax(-lim, dmin(lim, ex[2]))) + 1, 0, gw);
   g->rect[3] = clampi((int)floor(dmax(-lim, dmin(lim, ex[3]))) + 1, 0, gh);
+  /* Relaxed: the radius may round to any integer in [ceil(r3 (1 - relax)),
+   * ceil(r3 (1 + relax))], and each rect edge u -/+ r (resp. v) may move by
+   * relax max(1, |u -/+ r|) pixels before it is divided by the tile edge and
+   * rounded down; rect_lo holds the tiles inside every such rect, rect_hi
+   * those inside some. */
+  for (int k = 0; k < 4; ++k) g->rect_lo[k] = g->rect_hi[k] = g->rect[k];
+  if (relax > 0.0) {
+    const double rr[2] = {ceil(r3 * (1.0 - relax)), ceil(r3 * (1.0 + relax))};
+    for (int axis = 0; axis < 2; ++axis) {
+      const int lim_t = axis == 0 ? gw : gh;
+      int lo_min = 1 << 30, lo_max = -(1 << 30), hi_min = 1 << 30, hi_max = -(1 << 30);
+      for (int a = 0; a < 2; ++a)
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+          const double e0 = g->uv[axis] - rr[a], e1 = g->uv[axis] + rr[a];
+          const double w0 = relax * dmax(1.0, fabs(e0)), w1 = relax * dmax(1.0, fabs(e1));
+          const int t0 = clampi((int)floor(dmax(-lim, dmin(lim, (e0 + sgn * w0) / B))), 0, lim_t);
+          const int t1 = clampi((int)floor(dmax(-lim, dmin(lim, (e1 + sgn * w1) / B))) + 1, 0, lim_t);
+          lo_min = t0 < lo_min ? t0 : lo_min;
+          lo_max = t0 > lo_max ? t0 : lo_max;
+          hi_min = t1 < hi_min ? t1 : hi_min;
+          hi_max = t1 > hi_max ? t1 : hi_max;
+        }
+      g->rect_hi[axis] = lo_min;
+      g->rect_hi[axis + 2] = hi_max;
+      g->rect_lo[axis] = lo_max;
+      g->rect_lo[axis + 2] = hi_min;
+    }
+    if (g->rect_hi[0] < g->rect_hi[2] && g->rect_hi[1] < g->rect_hi[3] &&
+        (g->rect_lo[0] != g->rect_hi[0] || g->rect_lo[1] != g->rect_hi[1] || g->rect_lo[2] != g->rect_hi[2] ||
+         g->rect_lo[3] != g->rect_hi[3]))
+      g->margin = dmin(g->margin, 0.0);
+  }
   if (g->rect[0] >= g->rect[2] || g->rect[1] >= g->rect[3]) {
-    g->status = 5;
-    return;
+    /* empty in FP64: relaxed, the Gaussian stays (absent or present) while
+     * some admissible rect holds a tile */
+    if (!(relax > 0.0 && g->rect_hi[0] < g->rect_hi[2] && g->rect_hi[1] < g->rect_hi[3])) {
+      g->status = 5;
+      g->uncertain = 0;
+      return;
+    }
+    if (!g->status) g->status = 5;
+    g->uncertain |= 1;
   }
   /* A Gaussian whose effective opacity is below 1/255 is skipped at every
    * pixel (alpha <= a), so dropping it leaves the image unchanged. */
   g->a = g->sig * g->pt;
-  g->margin = dmin(g->margin, fabs(g->a * 255.0 - 1.0));
-  if (g->a * 255.0 < 1.0) {
-    g->status = 6;
-    return;
-  }
+  if (cull(g, g->a * 255.0 < 1.0, fabs(g->a * 255.0 - 1.0), 6)) return;
   /* 4DSH colour (Sec. 3.2): Z_nl^m = cos(2 pi n dt / T) Y_l^m(d), with the
    * view direction d from the camera centre to the sliced mean and
    * dt = t - mu_t; colour = max(0, sum c Z + 0.5). */
@@ -401,10 +465,11 @@ static void gauss_forward(const orc_params *P, int64_t i, const orc_view *V,
     g->rgb[ch] = dmax(0.0, acc + 0.5);
     if (!isfinite(g->rgb[ch])) {
       g->status = 1;
+      g->uncertain = 0;
       return;
     }
+    if (fabs(acc + 0.5) < relax) g->uncertain |= 2;
   }
-  g->status = 0;
 }
 
 /* Stores every value the chain reached (zeros past the cull point); the
@@ -413,6 +478,12 @@ static void store_proj(const orc_ctx *g, int64_t i, orc_proj *o) {
   o->status[i] = g->status;
   o->margin[i] = g->margin;
   for (int k = 0; k < 4; ++k) o->rect[4 * i + k] = g->status == 0 ? g->rect[k] : 0;
+  const int alive = g->status == 0 || (g->uncertain & 1);
+  if (o->uncertain) o->uncertain[i] = alive ? g->uncertain : 0;
+  if (o->rect_lo)
+    for (int k = 0; k < 4; ++k) o->rect_lo[4 * i + k] = g->status == 0 && !(g->uncertain & 1) ? g->rect_lo[k] : 0;
+  if (o->rect_hi)
+    for (int k = 0; k < 4; ++k) o->rect_hi[4 * i + k] = alive ? g->rect_hi[k] : 0;
   o->p_t[i] = g->pt;
   o->a_eff[i] = g->a;
   for (int k = 0; k < 3; ++k) o->mu3[3 * i + k] = g->mu3[k];
@@ -435,7 +506,27 @@ int orc_preprocess(const orc_params *P, const orc_view *V, const orc_settings *S
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < P->n; ++i) {
     orc_ctx g;
-    gauss_forward(P, i, V, S, &g);
+    gauss_forward(P, i, V, S, &g, 0.0);
+    store_proj(&g, i, out);
+  }
+  return 0;
+}
+
+/* The per-Gaussian chain with every discrete decision relaxed by `relax`
+ * (relative): a decision that another precision could take the other way
+ * (a cull threshold, the integer radius, a tile-rect edge, the colour clamp)
+ * is marked in out->uncertain, rect_lo / rect_hi bound the tile rect over
+ * the admissible roundings, and a Gaussian culled within the relaxation gets
+ * the values it would have had (its status keeps the FP64 decision).  The
+ * FP64 values, status and rect equal orc_preprocess's. */
+int orc_preprocess_relaxed(const orc_params *P, const orc_view *V, const orc_settings *S, double relax,
+                           orc_proj *out) {
+  if (S->sh_degree < 0 || S->sh_degree > ORC_MAX_L || S->t_order < 0 || S->t_order > ORC_MAX_N) return -1;
+  if (!(relax >= 0.0) || !out->uncertain || !out->rect_lo || !out->rect_hi) return -1;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < P->n; ++i) {
+    orc_ctx g;
+    gauss_forward(P, i, V, S, &g, relax);
     store_proj(&g, i, out);
   }
   return 0;
@@ -638,6 +729,380 @@ int orc_render_pixels(const orc_view *V, const orc_settings *S, int64_t n, const
   return err ? -1 : 0;
 }
 
+/* ------------------------------------------- admissible pixel results */
+
+/* The compositing of Eq. 6 takes discrete decisions per pixel: an entry is
+ * skipped when alpha < 1/255 (or when the exponent is positive), and the
+ * walk stops before an entry that would take T below 1e-4; the list order
+ * comes from FP32 depths, and tile membership from the integer radius and
+ * rect edges.  A renderer working in FP32 takes each decision from values
+ * within a known error of the FP64 ones, so where an FP64 value lies within
+ * that error of its threshold either outcome is correct.  This function
+ * walks every combination of such outcomes (depth-first, state copied only
+ * where the walk branches) and returns each distinct result.  With zero
+ * tolerances and a plain (relax = 0) projection it takes exactly the
+ * decisions of composite_pixel and returns its result, bit for bit; with
+ * any tolerances that result is always one of those returned.
+ *
+ * Error model of one alpha (relative).  The exponent is taken as a sum of
+ * two squares, -power = ((u11 dx)^2 + (u12 dx + u22 dy)^2) / 2 with the
+ * conic Q = U U^T, U upper triangular (the form in which FP32 evaluation
+ * does not cancel); with u11, u22 known to a relative eps_conic and u12 to
+ * eps_conic (|u12| + sqrt(Q11)), the exponent is known to eps_conic ((u11
+ * dx)^2 + |e| (|u12 dx| + sqrt(Q11) |dx| + u22 |dy|)), e = u12 dx + u22 dy.
+ * Added to that: the exponent's change under a centre
+ * error of eps_uv |u| + eps_uv_abs pixels (resp. v), plus eps_a (effective opacity)
+ * and eps_alpha (the exponential and rounding).  The transmittance's
+ * relative error bound accumulates alpha * e / (1 - alpha) per composited
+ * entry, plus eps_alpha for the rounding of the update.  Depth keys may differ from the FP64 depth rounded to FP32 by
+ * depth_ulps units in the last place, so two entries whose keys differ by at
+ * most 2 depth_ulps may be composited in either order. */
+typedef struct {
+  double eps_conic, eps_uv, eps_uv_abs, eps_a, eps_alpha;
+  int32_t depth_ulps;
+  int32_t max_leaves; /* walk budget per pixel; past it the pixel is flagged (bit 4) */
+} orc_tol;
+
+enum { ORC_SKIP = 1, ORC_TAKE = 2 };
+
+/* Alpha of Gaussian i at the sample point (pxc, pyc) (Eq. 6: min(0.99,
+ * a exp(power))) and the relative error bound e of an FP32 renderer's alpha
+ * there (the model above). */
+static void adm_alpha(const orc_proj *P, const orc_tol *tol, int64_t i, double pxc, double pyc, double *power_out,
+                      double *aG_out, double *alpha_out, double *err_out) {
+  const double A = P->conic[3 * i + 0], Bc = P->conic[3 * i + 1], Cc = P->conic[3 * i + 2];
+  const double u = P->uv[2 * i + 0], v = P->uv[2 * i + 1];
+  const double dx = u - pxc, dy = v - pyc;
+  const double power = -0.5 * (A * dx * dx + Cc * dy * dy) - Bc * dx * dy;
+  const double aG = P->a_eff[i] * exp(power);
+  /* the exponent as a sum of two squares, Q = U U^T with U upper
+   * triangular: -power = ((u11 dx)^2 + (u12 dx + u22 dy)^2) / 2 */
+  const double u22 = sqrt(Cc), u12 = Bc / u22, u11 = sqrt(dmax(0.0, A * Cc - Bc * Bc) / Cc);
+  const double ex = u11 * dx, ey = u12 * dx + u22 * dy;
+  const double pfac = ex * ex + fabs(ey) * (fabs(u12 * dx) + sqrt(A) * fabs(dx) + u22 * fabs(dy));
+  const double gx = fabs(A * dx + Bc * dy), gy = fabs(Cc * dy + Bc * dx);
+  *err_out = tol->eps_conic * pfac + gx * (tol->eps_uv * fabs(u) + tol->eps_uv_abs) +
+             gy * (tol->eps_uv * fabs(v) + tol->eps_uv_abs) + tol->eps_a + tol->eps_alpha;
+  *power_out = power;
+  *aG_out = aG;
+  *alpha_out = dmin(0.99, aG);
+}
+
+/* alpha and its error bound for npairs (Gaussian, pixel) pairs, the pixel
+ * given by its linear id py * width + px (sample point at its centre). */
+void orc_alpha_bounds(const orc_view *V, const orc_proj *P, const orc_tol *tol, int64_t npairs, const int64_t *idx,
+                      const int64_t *pix, double *alpha, double *err) {
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < npairs; ++k) {
+    double power, aG;
+    adm_alpha(P, tol, idx[k], (double)(pix[k] % V->width) + 0.5, (double)(pix[k] / V->width) + 0.5, &power, &aG,
+              &alpha[k], &err[k]);
+  }
+}
+
+typedef struct {
+  int64_t idx;
+  uint32_t bits;
+  int opts;     /* ORC_SKIP | ORC_TAKE: outcomes admissible at this pixel */
+  double alpha; /* min(0.99, a G) */
+  double err;   /* relative error bound of alpha */
+  int gflag;    /* the derivative of a take is uncertain (near the 0.99 clamp, or colour clamp) */
+} orc_adm_entry;
+
+typedef struct {
+  double T, errT;
+  int32_t nr;
+  int gflag;
+  double C[3];
+  double X[64];
+} orc_adm_state;
+
+typedef struct {
+  const orc_proj *P;
+  const orc_settings *S;
+  const double *extra;
+  int nextra;
+  const orc_adm_entry *seq; /* entries with an outcome other than skip, in FP64 list order */
+  const int64_t *gstart;    /* groups of entries that may swap: [gstart[g], gstart[g + 1]) */
+  int64_t ngroups;
+  int32_t depth_ulps;
+  double eps_step;          /* rounding of one transmittance update (eps_alpha) */
+  int32_t max_cands, max_leaves;
+  double *cands;            /* [max_cands][5 + nextra]: r, g, b, T, contributors, extra... */
+  int32_t ncands, leaves;
+  int flags;
+} orc_adm_ctx;
+
+static void adm_leaf(orc_adm_ctx *c, const orc_adm_state *s) {
+  const int nv = 5 + c->nextra;
+  double v[5 + 64];
+  for (int ch = 0; ch < 3; ++ch) v[ch] = s->C[ch] + s->T * c->S->bg[ch];
+  v[3] = s->T;
+  v[4] = s->nr;
+  for (int k = 0; k < c->nextra; ++k) v[5 + k] = s->X[k];
+  if (s->gflag) c->flags |= 2;
+  for (int32_t j = 0; j < c->ncands; ++j)
+    if (memcmp(c->cands + (int64_t)j * nv, v, sizeof(double) * (size_t)nv) == 0) return;
+  if (c->ncands >= c->max_cands) {
+    c->flags |= 4;
+    return;
+  }
+  memcpy(c->cands + (int64_t)c->ncands * nv, v, sizeof(double) * (size_t)nv);
+  ++c->ncands;
+}
+
+/* Outcomes of entry e at state s: up to three successor states (skip; take
+ * and go on) or a stop.  Returns the number of successors; *stop is set when
+ * stopping before e is admissible. */
+static int adm_options(const orc_adm_ctx *c, const orc_adm_entry *e, const orc_adm_state *s, orc_adm_state out[2],
+                       int *stop) {
+  int k = 0;
+  *stop = 0;
+  if (e->opts & ORC_SKIP) out[k++] = *s;
+  if (e->opts & ORC_TAKE) {
+    const double alpha = e->alpha;
+    const double Tn = s->T * (1.0 - alpha);
+    const double errTn = s->errT + alpha * e->err / (1.0 - alpha) + c->eps_step;
+    if (Tn * (1.0 - errTn) < 1e-4) *stop = 1;
+    if (Tn * (1.0 + errTn) >= 1e-4) {
+      orc_adm_state n = *s;
+      const int64_t i = e->idx;
+      for (int ch = 0; ch < 3; ++ch) n.C[ch] += c->P->rgb[3 * i + ch] * alpha * s->T;
+      for (int q = 0; q < c->nextra; ++q) n.X[q] += c->extra[(int64_t)c->nextra * i + q] * alpha * s->T;
+      n.T = Tn;
+      n.errT = errTn;
+      n.nr = s->nr + 1;
+      n.gflag |= e->gflag;
+      out[k++] = n;
+    }
+  }
+  return k;
+}
+
+static void adm_walk(orc_adm_ctx *c, int64_t g, uint32_t rem, const orc_adm_state *s0);
+
+/* Entry m of group g composited next (m's bit already cleared from rem). */
+static void adm_member(orc_adm_ctx *c, int64_t g, uint32_t rem, int m, const orc_adm_state *s) {
+  orc_adm_state nx[2];
+  int stop;
+  const int k = adm_options(c, &c->seq[c->gstart[g] + m], s, nx, &stop);
+  if (k + stop > 1) c->flags |= 1;
+  if (stop) {
+    if (++c->leaves > c->max_leaves) {
+      c->flags |= 4;
+      return;
+    }
+    adm_leaf(c, s);
+  }
+  for (int j = 0; j < k; ++j) adm_walk(c, g, rem, &nx[j]);
+}
+
+/* Composites, from state s0, the members of group g still in rem and then
+ * every later group.  The members of a group may be composited in any order
+ * in which each pair that is out of FP64 order has keys within 2 depth_ulps. */
+static void adm_walk(orc_adm_ctx *c, int64_t g, uint32_t rem, const orc_adm_state *s0) {
+  if (c->leaves > c->max_leaves) return;
+  orc_adm_state s = *s0;
+  for (;;) {
+    while (rem == 0) {
+      if (++g >= c->ngroups) {
+        if (++c->leaves > c->max_leaves) {
+          c->flags |= 4;
+          return;
+        }
+        adm_leaf(c, &s);
+        return;
+      }
+      const int64_t len = c->gstart[g + 1] - c->gstart[g];
+      rem = len >= 32 ? 0xffffffffu : ((1u << len) - 1u);
+    }
+    const orc_adm_entry *grp = c->seq + c->gstart[g];
+    int first = -1;
+    for (int m = 0; m < 32; ++m) {
+      if (!(rem & (1u << m))) continue;
+      /* m may come next if every remaining member before it is within range */
+      int ok = 1;
+      for (int j = 0; j < m && ok; ++j)
+        if ((rem & (1u << j)) && grp[m].bits - grp[j].bits > 2u * (uint32_t)c->depth_ulps) ok = 0;
+      if (!ok) continue;
+      if (first < 0) {
+        first = m;
+        continue;
+      }
+      c->flags |= 1;
+      adm_member(c, g, rem & ~(1u << m), m, &s);
+      if (c->leaves > c->max_leaves) return;
+    }
+    /* the first admissible member (the FP64 order) continues in this frame
+     * along its last outcome */
+    rem &= ~(1u << first);
+    orc_adm_state nx[2];
+    int stop;
+    const int k = adm_options(c, &grp[first], &s, nx, &stop);
+    if (k + stop > 1) c->flags |= 1;
+    if (stop) {
+      if (++c->leaves > c->max_leaves) {
+        c->flags |= 4;
+        return;
+      }
+      adm_leaf(c, &s);
+    }
+    if (k == 0) return;
+    for (int j = 0; j + 1 < k; ++j) {
+      adm_walk(c, g, rem, &nx[j]);
+      if (c->leaves > c->max_leaves) return;
+    }
+    s = nx[k - 1];
+  }
+}
+
+/* Admissible results at selected pixels (linear ids py * W + px) of one view.
+ * P: from orc_preprocess_relaxed (or orc_preprocess with uncertain, rect_lo
+ * and rect_hi set by the caller).  A Gaussian enters a pixel's list when it
+ * is visible or uncertain (bit 1) and its rect_hi holds the pixel's tile; its
+ * membership is uncertain unless it is visible, certain and inside rect_lo.
+ * extra: optional [n][nextra] per-Gaussian values composited like colour
+ * (nextra <= 64).  Outputs per pixel q: ncands[q] distinct results in
+ * cands[q][max_cands][5 + nextra] (r, g, b, T, contributors, extra...), and
+ * flags[q]: bit 1 some decision had two admissible outcomes, bit 2 a
+ * composited entry's derivative is uncertain (alpha within its error of the
+ * 0.99 clamp, or its colour clamp uncertain), bit 4 the walk ran out of its
+ * budget (results incomplete).  Returns 0, or -1 on bad arguments or memory. */
+typedef struct {
+  int64_t tile, q;
+} orc_pixq;
+
+static int pixq_cmp(const void *pa, const void *pb) {
+  const orc_pixq *a = pa, *b = pb;
+  if (a->tile != b->tile) return a->tile < b->tile ? -1 : 1;
+  return (a->q > b->q) - (a->q < b->q);
+}
+
+int orc_render_pixels_admissible(const orc_view *V, const orc_settings *S, int64_t n, const orc_proj *P,
+                                 const orc_tol *tol, const double *extra, int32_t nextra, int64_t npix,
+                                 const int64_t *pix, int32_t max_cands, double *cands, int32_t *ncands,
+                                 int32_t *flags) {
+  if (!P->uncertain || !P->rect_lo || !P->rect_hi || nextra < 0 || nextra > 64 || max_cands < 1) return -1;
+  const int W = V->width, B = S->tile;
+  const int gw = (W + B - 1) / B;
+  const int nv = 5 + nextra;
+  /* pixels grouped by tile, so each tile's list is gathered once */
+  orc_pixq *qs = malloc(sizeof(orc_pixq) * (size_t)(npix > 0 ? npix : 1));
+  int64_t *runs = malloc(sizeof(int64_t) * (size_t)(npix + 1));
+  if (!qs || !runs) {
+    free(qs);
+    free(runs);
+    return -1;
+  }
+  for (int64_t q = 0; q < npix; ++q) {
+    const int px = (int)(pix[q] % W), py = (int)(pix[q] / W);
+    qs[q].tile = (int64_t)(py / B) * gw + px / B;
+    qs[q].q = q;
+  }
+  qsort(qs, (size_t)npix, sizeof(orc_pixq), pixq_cmp);
+  int64_t nruns = 0;
+  for (int64_t a = 0; a < npix; ++a)
+    if (a == 0 || qs[a].tile != qs[a - 1].tile) runs[nruns++] = a;
+  runs[nruns] = npix;
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t rix = 0; rix < nruns; ++rix) {
+    const int64_t t = qs[runs[rix]].tile;
+    const int tx = (int)(t % gw), ty = (int)(t / gw);
+    /* the tile's list: every Gaussian some admissible outcome puts here */
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t *r = P->rect_hi + 4 * i;
+      if ((P->status[i] == 0 || (P->uncertain[i] & 1)) && tx >= r[0] && tx < r[2] && ty >= r[1] && ty < r[3]) ++cnt;
+    }
+    orc_entry *list = malloc(sizeof(orc_entry) * (size_t)(cnt > 0 ? cnt : 1));
+    orc_adm_entry *seq = malloc(sizeof(orc_adm_entry) * (size_t)(cnt > 0 ? cnt : 1));
+    int64_t *gstart = malloc(sizeof(int64_t) * (size_t)(cnt + 2));
+    if (!list || !seq || !gstart) {
+      err = 1;
+      free(list);
+      free(seq);
+      free(gstart);
+      continue;
+    }
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t *r = P->rect_hi + 4 * i;
+      if ((P->status[i] == 0 || (P->uncertain[i] & 1)) && tx >= r[0] && tx < r[2] && ty >= r[1] && ty < r[3]) {
+        orc_entry e = {P->depth_f32[i], i};
+        list[k++] = e;
+      }
+    }
+    qsort(list, (size_t)cnt, sizeof(orc_entry), entry_cmp);
+    for (int64_t qq = runs[rix]; qq < runs[rix + 1]; ++qq) {
+      const int64_t q = qs[qq].q;
+      const int px = (int)(pix[q] % W), py = (int)(pix[q] / W);
+      const double pxc = px + 0.5, pyc = py + 0.5;
+      /* outcomes of every entry at this pixel; entries that are skipped
+       * under every admissible outcome are left out */
+      int64_t ns = 0;
+      for (int64_t j = 0; j < cnt; ++j) {
+        const int64_t i = list[j].idx;
+        double power, aG, alpha, e;
+        adm_alpha(P, tol, i, pxc, pyc, &power, &aG, &alpha, &e);
+        const double gpu_lo = alpha * (1.0 - e), gpu_hi = alpha * (1.0 + e);
+        int opts = 0;
+        if (power > 0.0 || gpu_lo < 1.0 / 255.0) opts |= ORC_SKIP;
+        if (gpu_hi >= 1.0 / 255.0) opts |= ORC_TAKE;
+        const int32_t *rl = P->rect_lo + 4 * i;
+        const int certain = P->status[i] == 0 && !(P->uncertain[i] & 1) && tx >= rl[0] && tx < rl[2] &&
+                            ty >= rl[1] && ty < rl[3];
+        if (!certain) opts |= ORC_SKIP;
+        if (!(opts & ORC_TAKE)) continue;
+        seq[ns].idx = i;
+        seq[ns].bits = f32_bits(list[j].depth);
+        seq[ns].opts = opts;
+        seq[ns].alpha = alpha;
+        seq[ns].err = e;
+        seq[ns].gflag = fabs(aG - 0.99) <= 0.99 * e || (P->uncertain[i] & 2) ? 1 : 0;
+        ++ns;
+      }
+      /* groups of consecutive entries whose keys lie within 2 depth_ulps */
+      int64_t ng = 0;
+      for (int64_t j = 0; j < ns; ++j)
+        if (j == 0 || tol->depth_ulps <= 0 || seq[j].bits - seq[j - 1].bits > 2u * (uint32_t)tol->depth_ulps ||
+            j - gstart[ng - 1] >= 20)
+          gstart[ng++] = j;
+      gstart[ng] = ns;
+      orc_adm_ctx c;
+      memset(&c, 0, sizeof c);
+      c.P = P;
+      c.S = S;
+      c.extra = extra;
+      c.nextra = extra ? nextra : 0;
+      c.seq = seq;
+      c.gstart = gstart;
+      c.ngroups = ng;
+      c.depth_ulps = tol->depth_ulps;
+      c.eps_step = tol->eps_alpha;
+      c.max_cands = max_cands;
+      c.max_leaves = tol->max_leaves > 0 ? tol->max_leaves : 4096;
+      c.cands = cands + (int64_t)q * max_cands * nv;
+      orc_adm_state s0;
+      memset(&s0, 0, sizeof s0);
+      s0.T = 1.0;
+      adm_walk(&c, -1, 0u, &s0);
+      /* a group cut at 20 members leaves pairs across the cut unordered */
+      for (int64_t gi = 1; gi < ng; ++gi)
+        if (tol->depth_ulps > 0 && seq[gstart[gi]].bits - seq[gstart[gi] - 1].bits <= 2u * (uint32_t)tol->depth_ulps)
+          c.flags |= 4;
+      ncands[q] = c.ncands;
+      flags[q] = c.flags;
+    }
+    free(list);
+    free(seq);
+    free(gstart);
+  }
+  free(qs);
+  free(runs);
+  return err ? -1 : 0;
+}
+
 /* ----------------------------------------------- auxiliary channels */
 
 /* Per visible Gaussian: camera-space depth z of the sliced mean and the
@@ -647,15 +1112,20 @@ int orc_render_pixels(const orc_view *V, const orc_settings *S, int64_t n, const
  * Sigma_{1:3,4} / Sigma_44, so the displaced camera-space centre is
  * pc + W v dt; the flow is pi(pc + W v dt) - pi(pc) with pi the pinhole
  * projection of Eq. 3, and 0 when the displaced centre is not in front of the
- * near plane.  aux[n][3] = (z, flow_u, flow_v); zeros for culled Gaussians. */
-int orc_aux(const orc_params *Pp, const orc_view *V, const orc_settings *S, double flow_dt,
+ * near plane.  aux[n][3] = (z, flow_u, flow_v); zeros for culled Gaussians
+ * (with relax > 0 and P from orc_preprocess_relaxed at that relax, also for
+ * the Gaussians it marks as possibly present). */
+int orc_aux(const orc_params *Pp, const orc_view *V, const orc_settings *S, double flow_dt, double relax,
             const orc_proj *P, double *aux) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < Pp->n; ++i) {
     aux[3 * i + 0] = aux[3 * i + 1] = aux[3 * i + 2] = 0.0;
-    if (P->status[i] != 0) continue;
+    /* P from orc_preprocess_relaxed with the same relax: a Gaussian culled
+     * within the relaxation gets the values it would have if kept */
+    const int maybe = relax > 0.0 && P->uncertain && (P->uncertain[i] & 1);
+    if (P->status[i] != 0 && !maybe) continue;
     orc_ctx g;
-    gauss_forward(Pp, i, V, S, &g);
+    gauss_forward(Pp, i, V, S, &g, maybe ? relax : 0.0);
     const double *W = V->viewmat;
     double vel[3], pc2[3];
     for (int a = 0; a < 3; ++a) vel[a] = g.b[a] / g.c;
@@ -713,6 +1183,12 @@ static double gated_unit_feature(const double *f, const double *gate, int D, dou
   const double norm = sqrt(nn);
   for (int c = 0; c < D; ++c) fhat[c] = norm > 0.0 ? fhat[c] / norm : 0.0;
   return norm;
+}
+
+/* The normalised scale-gated feature of every Gaussian (gate NULL = all
+ * ones): fhat[n][D]. */
+void orc_gated_features(const double *feat, int64_t n, int D, const double *gate, double *fhat) {
+  for (int64_t i = 0; i < n; ++i) gated_unit_feature(feat + (int64_t)D * i, gate, D, fhat + (int64_t)D * i);
 }
 
 /* out[D][H][W] = sum_i w_i fhat_i per pixel, w_i = alpha_i T_i of the colour
@@ -1051,7 +1527,7 @@ int orc_render_backward(const orc_params *Pp, const orc_view *V, const orc_setti
   for (int64_t i = 0; i < n; ++i) {
     if (P->status[i] != 0) continue;
     orc_ctx g;
-    gauss_forward(Pp, i, V, S, &g);
+    gauss_forward(Pp, i, V, S, &g, 0.0);
     gauss_adjoint(Pp, i, V, S, &g, out->g_uv + 2 * i, out->g_conic + 3 * i, out->g_a[i],
                   out->g_rgb + 3 * i, out->g_z[i], out);
   }
@@ -1098,7 +1574,7 @@ int orc_render_aux_backward(const orc_params *Pp, const orc_view *V, const orc_s
   for (int64_t i = 0; i < n; ++i) {
     if (P->status[i] != 0) continue;
     orc_ctx g;
-    gauss_forward(Pp, i, V, S, &g);
+    gauss_forward(Pp, i, V, S, &g, 0.0);
     gauss_adjoint(Pp, i, V, S, &g, out->g_uv + 2 * i, out->g_conic + 3 * i, out->g_a[i],
                   out->g_rgb + 3 * i, out->g_z[i], out);
   }
@@ -1113,7 +1589,7 @@ int orc_preprocess_backward(const orc_params *Pp, const orc_view *V, const orc_s
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < Pp->n; ++i) {
     orc_ctx g;
-    gauss_forward(Pp, i, V, S, &g);
+    gauss_forward(Pp, i, V, S, &g, 0.0);
     if (g.status != 0) continue;
     gauss_adjoint(Pp, i, V, S, &g, g_uv + 2 * i, g_conic + 3 * i, g_a[i], g_rgb + 3 * i, 0.0, out);
   }
@@ -1198,11 +1674,7 @@ void orc_real_sh(int L, const double *dir, double *Y) {
  * it: one (tile, Gaussian) pair per tile of each visible Gaussian's rect,
  * key = (tile << 32) | bits(depth_f32), sorted by (tile, depth, index).
  * ranges[t] = [start, end) of tile t. Returns the instance count, or -1 if
- * it exceeds cap.
- *
- * With uv != NULL a rect tile is kept only if the Gaussian's 1/255 ellipse
- * meets the tile's pixel centres (orc_ellipse_meets_box); a dropped tile is
- * one where every pixel skips the Gaussian, so the image does not change. */
+ * it exceeds cap. */
 typedef struct {
   int64_t tile;
   float depth;
@@ -1216,61 +1688,12 @@ static int inst_cmp(const void *pa, const void *pb) {
   return (a->idx > b->idx) - (a->idx < b->idx);
 }
 
-/* Does the ellipse {d : A d_x^2 + B d_x d_y + C d_y^2 <= tau} around (u, v)
- * meet the box [x0, x1] x [y0, y1]?  The exact minimum of the positive
- * definite form over the box is 0 when the centre is inside, else the least
- * of the four edge minima (edge x = X: d_y = clamp(-B X / (2 C))).  This is an
- * integer decision taken from FP32 data, so it is specified as FP32
- * arithmetic with every operation rounded in this order (the kernel takes
- * the same decision in the same precision). */
-int orc_ellipse_meets_box(float u, float v, float A, float B, float C, float tau, float x0, float x1, float y0,
-                          float y1) {
-  const float lx = x0 - u, hx = x1 - u, ly = y0 - v, hy = y1 - v;
-  if (lx <= 0.0f && hx >= 0.0f && ly <= 0.0f && hy >= 0.0f) return tau >= 0.0f;
-  const float kx = -B / (2.0f * C);
-  const float ky = -B / (2.0f * A);
-  const float ex[2] = {lx, hx}, ey[2] = {ly, hy};
-  float m = INFINITY;
-  for (int k = 0; k < 2; ++k) {
-    const float X = ex[k];
-    const float Yv = fminf(fmaxf(kx * X, ly), hy);
-    const float qx = (A * (X * X) + B * (X * Yv)) + C * (Yv * Yv);
-    m = fminf(m, qx);
-    const float Y = ey[k];
-    const float Xv = fminf(fmaxf(ky * Y, lx), hx);
-    const float qy = (A * (Xv * Xv) + B * (Xv * Y)) + C * (Y * Y);
-    m = fminf(m, qy);
-  }
-  return m <= tau;
-}
-
-/* Pixel-centre box of tile (tx, ty), clipped to the image. */
-static void tile_box(int tx, int ty, int W, int H, int B, float *x0, float *x1, float *y0, float *y1) {
-  const int px1 = tx * B + B - 1 < W - 1 ? tx * B + B - 1 : W - 1;
-  const int py1 = ty * B + B - 1 < H - 1 ? ty * B + B - 1 : H - 1;
-  *x0 = (float)(tx * B) + 0.5f;
-  *x1 = (float)px1 + 0.5f;
-  *y0 = (float)(ty * B) + 0.5f;
-  *y1 = (float)py1 + 0.5f;
-}
-
-static int keep_tile(const float *uv, const float *conic2, const float *tau, int64_t i, int tx, int ty, int W,
-                     int H, int B) {
-  if (!uv) return 1;
-  float x0, x1, y0, y1;
-  tile_box(tx, ty, W, H, B, &x0, &x1, &y0, &y1);
-  return orc_ellipse_meets_box(uv[2 * i], uv[2 * i + 1], conic2[3 * i], conic2[3 * i + 1], conic2[3 * i + 2],
-                               tau[i], x0, x1, y0, y1);
-}
-
-int64_t orc_sort_instances(int64_t n, const int32_t *rect, const float *depth, const float *uv, const float *conic2,
-                           const float *tau, int32_t W, int32_t H, int32_t tile, int32_t gw, int32_t gh, int64_t cap,
+int64_t orc_sort_instances(int64_t n, const int32_t *rect, const float *depth, int32_t gw, int32_t gh, int64_t cap,
                            uint64_t *keys, int64_t *vals, int64_t *ranges) {
   int64_t m = 0;
   for (int64_t i = 0; i < n; ++i) {
     const int32_t *r = rect + 4 * i;
-    for (int ty = r[1]; ty < r[3]; ++ty)
-      for (int tx = r[0]; tx < r[2]; ++tx) m += keep_tile(uv, conic2, tau, i, tx, ty, W, H, tile);
+    if (r[2] > r[0] && r[3] > r[1]) m += (int64_t)(r[2] - r[0]) * (r[3] - r[1]);
   }
   if (m > cap) return -1;
   orc_inst *a = malloc(sizeof(orc_inst) * (size_t)(m > 0 ? m : 1));
@@ -1280,7 +1703,6 @@ int64_t orc_sort_instances(int64_t n, const int32_t *rect, const float *depth, c
     const int32_t *r = rect + 4 * i;
     for (int ty = r[1]; ty < r[3]; ++ty)
       for (int tx = r[0]; tx < r[2]; ++tx) {
-        if (!keep_tile(uv, conic2, tau, i, tx, ty, W, H, tile)) continue;
         a[k].tile = (int64_t)ty * gw + tx;
         a[k].depth = depth[i];
         a[k].idx = i;
@@ -1309,5 +1731,14 @@ int orc_num_threads(void) {
   return omp_get_max_threads();
 #else
   return 1;
+#endif
+}
+
+/* Threads of the following parallel regions (timing on a given core count). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
 #endif
 }

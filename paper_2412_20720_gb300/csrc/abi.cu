@@ -311,6 +311,18 @@ int fgs4d_render_stats(int64_t n, const fgs4d_view *views, int32_t nviews, const
 
 namespace {
 
+int check_grads(const fgs4d_gaussians *gaussians, const fgs4d_gaussians_grad *grads) {
+  if (!grads) return FGS4D_ERR_ARG;
+  if (gaussians->n > 0) {
+    if (!grads->mean || !grads->log_scale || !grads->q_l || !grads->q_r || !grads->opacity_logit || !grads->sh)
+      return FGS4D_ERR_ARG;
+    if (!aligned16(grads->mean) || !aligned16(grads->log_scale) || !aligned16(grads->q_l) ||
+        !aligned16(grads->q_r) || !aligned16(grads->sh) || !aligned16(grads->densify_stats))
+      return FGS4D_ERR_ARG;
+  }
+  return FGS4D_OK;
+}
+
 int render_bwd_common(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
                       const fgs4d_settings *settings, void *workspace, size_t workspace_bytes, const float *dL_drgb,
                       const float *dL_daux, const fgs4d_gaussians_grad *grads, void *stream) {
@@ -321,14 +333,9 @@ int render_bwd_common(const fgs4d_gaussians *gaussians, const fgs4d_view *views,
   if (rc) return rc;
   rc = check_workspace(L, workspace, workspace_bytes);
   if (rc) return rc;
-  if (!dL_drgb || !grads) return FGS4D_ERR_ARG;
-  if (gaussians->n > 0) {
-    if (!grads->mean || !grads->log_scale || !grads->q_l || !grads->q_r || !grads->opacity_logit || !grads->sh)
-      return FGS4D_ERR_ARG;
-    if (!aligned16(grads->mean) || !aligned16(grads->log_scale) || !aligned16(grads->q_l) ||
-        !aligned16(grads->q_r) || !aligned16(grads->sh) || !aligned16(grads->densify_stats))
-      return FGS4D_ERR_ARG;
-  }
+  if (!dL_drgb) return FGS4D_ERR_ARG;
+  rc = check_grads(gaussians, grads);
+  if (rc) return rc;
   unsigned char *ws = static_cast<unsigned char *>(workspace);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = launch_render_bwd(L, settings, views, nviews, ws, dL_drgb, dL_daux, st);
@@ -344,6 +351,34 @@ int fgs4d_render_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, 
                      const fgs4d_gaussians_grad *grads, void *stream) {
   return render_bwd_common(gaussians, views, nviews, settings, workspace, workspace_bytes, dL_drgb, nullptr, grads,
                            stream);
+}
+
+int fgs4d_render_bwd_composite(int64_t n, const fgs4d_view *views, int32_t nviews, const fgs4d_settings *settings,
+                               void *workspace, size_t workspace_bytes, const float *dL_drgb, void *stream) {
+  Layout L;
+  int rc = compute_layout(settings, n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  if (!dL_drgb) return FGS4D_ERR_ARG;
+  return cuda_status(launch_render_bwd(L, settings, views, nviews, static_cast<unsigned char *>(workspace), dL_drgb,
+                                       nullptr, static_cast<cudaStream_t>(stream)));
+}
+
+int fgs4d_render_bwd_preprocess(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,
+                                const fgs4d_settings *settings, void *workspace, size_t workspace_bytes,
+                                const fgs4d_gaussians_grad *grads, void *stream) {
+  int rc = check_gaussians(gaussians);
+  if (rc) return rc;
+  Layout L;
+  rc = compute_layout(settings, gaussians->n, views, nviews, &L);
+  if (rc) return rc;
+  rc = check_workspace(L, workspace, workspace_bytes);
+  if (rc) return rc;
+  rc = check_grads(gaussians, grads);
+  if (rc) return rc;
+  PreLaunch p{gaussians, settings, &L, static_cast<unsigned char *>(workspace), static_cast<cudaStream_t>(stream)};
+  return cuda_status(launch_preprocess_bwd(p, views, nviews, grads));
 }
 
 int fgs4d_render_aux_bwd(const fgs4d_gaussians *gaussians, const fgs4d_view *views, int32_t nviews,

@@ -56,7 +56,7 @@ __device__ __forceinline__ void stage_feature(const FeatArgs &A, const float *s_
                                               float *s_norm, int32_t *s_gi) {
   const uint32_t s = A.inst_val[idx];
   float4 geom = make_float4(0.f, 0.f, 0.f, 0.f);
-  float2 ca = make_float2(0.f, kLogAlphaNone);  // (C', log2 a): every pixel skips the entry
+  float2 ca = make_float2(0.f, kLogAlphaNone);  // (b2, log2 a): every pixel skips the entry
   int32_t gi = -1;
   if (s < A.vis_cap) {
     geom = A.rec_geom[s];

@@ -302,25 +302,32 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *s
 
 // Shared alpha evaluation of the compositor, used verbatim by the forward
 // and backward kernels so both take identical skip/stop decisions.  The
-// exponent in base 2 is power2 = -q with q = A' dx^2 + B' dx dy + C' dy^2,
-// evaluated as A' dx^2 + dy (B' dx + C' dy) so that a thread covering a
-// column of pixels computes the dx terms once per entry.  The record holds
-// la = log2 a instead of the opacity a, and la is folded into the dx term:
-// a 2^-q = 2^-(q - la), one exponential and no product per pixel.
+// exponent in base 2 is power2 = -q with q = (a1 dx)^2 + (b1 dx + b2 dy)^2
+// (the conic A' dx^2 + B' dx dy + C' dy^2 with A' = a1^2 + b1^2, B' = 2 b1 b2,
+// C' = b2^2, as a sum of two squares), so that a thread covering a column of
+// pixels computes the dx terms once per entry and no term cancels.  The
+// record holds la = log2 a instead of the opacity a, and la is folded into
+// the dx term: a 2^-q = 2^-(q - la), one exponential and no product per
+// pixel.
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
+// The base-2 exponent of a record is q = (a1 dx)^2 + (b1 dx + b2 dy)^2 with
+// geom = (u, v, a1, b1), color.x = b2 and (dx, dy) = (u, v) - pixel centre.
+// A thread's pixels share dx, so the column terms are formed once per entry:
+// adx2 = (a1 dx)^2 - log2 a and bdx = b1 dx.
 struct ColumnTerms {
-  float dx, adx2, bdx;  // adx2 = A' dx^2 - la
+  float dx, adx2, bdx;
 };
 
 __device__ __forceinline__ ColumnTerms column_terms(float4 geom, float pxc, float la) {
   ColumnTerms c;
   c.dx = __fsub_rn(geom.x, pxc);
-  c.adx2 = __fmaf_rn(geom.z, __fmul_rn(c.dx, c.dx), -la);
+  const float ax = __fmul_rn(geom.z, c.dx);
+  c.adx2 = __fmaf_rn(ax, ax, -la);
   c.bdx = __fmul_rn(geom.w, c.dx);
   return c;
 }
@@ -338,7 +345,7 @@ __device__ __forceinline__ float min_nan(float x, float y) {
 }
 
 // A pixel that has stopped (or lies outside the image) is given the row
-// centre +inf: dy = -inf makes q = +inf (or NaN when C' = 0), so alpha is 0
+// centre +inf: dy = -inf makes q = +inf (or NaN when b2 = 0), so alpha is 0
 // (or NaN) and fails the 1/255 test without a separate per-pixel flag test.
 __device__ __forceinline__ float stopped_row() { return __int_as_float(0x7f800000); }
 
@@ -350,17 +357,19 @@ __device__ __forceinline__ float stopped_row() { return __int_as_float(0x7f80000
 constexpr float kLog2NoClamp = -0.0291463f;  // log2(0.98)
 __device__ __forceinline__ bool entry_clamps(float la) { return la > kLog2NoClamp; }
 
+// b2: color.x of the record; alpha = a 2^-q with q the sum of two squares.
 template <bool kClamp>
-__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float C2, float pyc) {
+__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float b2, float pyc) {
   AlphaEval e;
   e.dy = __fsub_rn(v, pyc);
-  e.aG = ex2_approx(-__fmaf_rn(e.dy, __fmaf_rn(C2, e.dy, c.bdx), c.adx2));
+  const float w = __fmaf_rn(b2, e.dy, c.bdx);
+  e.aG = ex2_approx(-__fmaf_rn(w, w, c.adx2));
   e.alpha = kClamp ? min_nan(0.99f, e.aG) : e.aG;
   return e;
 }
 
-__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float C2, float pyc, bool clamp) {
-  return clamp ? pixel_alpha<true>(c, v, C2, pyc) : pixel_alpha<false>(c, v, C2, pyc);
+__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float b2, float pyc, bool clamp) {
+  return clamp ? pixel_alpha<true>(c, v, b2, pyc) : pixel_alpha<false>(c, v, b2, pyc);
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;

@@ -375,9 +375,18 @@ __global__ void __launch_bounds__(kPreBlock) preprocess_kernel(PreArgs A, PreVie
   __syncthreads();
   const uint64_t slot = s_base + local;
   if (vis && slot < (uint64_t)A.vis_cap) {
-    // Conic in base-2 exponent form: power2 = -(A' dx^2 + B' dx dy + C' dy^2).
-    A.rec_geom[slot] = make_float4(h.uv[0], h.uv[1], 0.5f * kLog2e * h.conA, kLog2e * h.conB);
-    A.rec_color[slot] = make_float4(0.5f * kLog2e * h.conC, log2f(h.a), h.rgb[0], h.rgb[1]);
+    // The exponent in base 2, q = (1/2) log2(e) d^T Sigma_2d^-1 d, as a sum of
+    // two squares: Sigma_2d^-1 = U U^T with U upper triangular gives
+    // q = (a1 dx)^2 + (b1 dx + b2 dy)^2, a1 = sqrt(k / Sa), b1 = -Sb sqrt(k /
+    // (Sa det)), b2 = Sa sqrt(k / (Sa det)), k = log2(e) / 2.  Evaluated this
+    // way q has no cancellation (the expanded conic form loses precision along
+    // the long axis of an elongated footprint, in proportion to its condition
+    // number); det is the Cauchy-Binet sum of squares.
+    const float kq = 0.5f * kLog2e;
+    const float a1 = sqrtf(kq / h.Sa);
+    const float rs = sqrtf(kq / (h.Sa * h.det));
+    A.rec_geom[slot] = make_float4(h.uv[0], h.uv[1], a1, -h.Sb * rs);
+    A.rec_color[slot] = make_float4(h.Sa * rs, log2f(h.a), h.rgb[0], h.rgb[1]);
     A.rec_blue[slot] = h.rgb[2];
     // alpha = a 2^power2 >= 1/255 needs -power2 <= log2(255 a); the margin
     // keeps the per-tile test of the instance emission conservative under

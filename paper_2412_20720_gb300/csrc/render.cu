@@ -3,7 +3,7 @@
 //
 // Forward: one CTA per (view, 16x16 tile).  A thread owns a vertical strip of
 // kPPT pixels of one column, so the per-entry work that does not depend on the
-// row (shared-memory loads, dx, A' dx^2, B' dx) is done once for kPPT pixels.
+// row (shared-memory loads, dx, (a1 dx)^2, b1 dx) is done once for kPPT pixels.
 // The tile's depth-sorted list is staged through shared memory in batches of
 // 256 records; the CTA stops loading once every pixel has reached the
 // transmittance cutoff (__syncthreads_count).  alpha = min(0.99, a 2^-q),
@@ -31,7 +31,7 @@ namespace {
 struct RenderArgs {
   const uint2 *ranges;
   const uint32_t *inst_val;
-  const float4 *rec_geom, *rec_color;  // rec_color: (C', log2 a, r, g)
+  const float4 *rec_geom, *rec_color;  // rec_geom: (u, v, a1, b1); rec_color: (b2, log2 a, r, g)
   const float *rec_blue;
   const float4 *rec_aux;  // auxiliary mode only
   uint32_t vis_cap;
@@ -98,9 +98,10 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
 
 // kMode 0: image (and the per-pixel state of the backward pass); 3: image
 // only -- no last-contributor index is tracked (the plane is written as 0);
-// 1 (kStats): also counts the pixel-entry alpha evaluations
-// and the composited entries (diagnostic variant used to state the
-// algorithmic work); 2 (kAux): also blends the per-slot depth and flow with
+// 1 (kStats): also counts the pixel-entry alpha evaluations, the composited
+// entries and the evaluations up to each pixel's last composited entry (the
+// ones the backward pass repeats) -- a diagnostic variant used to state the
+// algorithmic work; 2 (kAux): also blends the per-slot depth and flow with
 // the colour weights and writes depth, opacity 1 - T and flow planes.
 // A pixel that has stopped is marked by a negative T (its final transmittance
 // negated; a live pixel always has T >= 1e-4) and by the row centre +inf,
@@ -137,10 +138,12 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
   float T[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
   float X0[kAux ? PPT : 1], X1[kAux ? PPT : 1], X2[kAux ? PPT : 1];  // depth, flow_u, flow_v sums
   uint32_t last[PPT];
+  uint32_t pend[kStats ? PPT : 1];  // evaluations since the pixel's last composited entry
   int nlive = 0;  // pixels of this thread still compositing
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     const bool in = px < V.width && py0 + k < V.height;
+    if (kStats) pend[k] = 0u;
     T[k] = in ? 1.0f : -1.0f;
     C0[k] = C1[k] = C2[k] = 0.f;
     if (kAux) X0[k] = X1[k] = X2[k] = 0.f;
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
     pyc[k] = in ? (float)(py0 + k) + 0.5f : stopped_row();
     nlive += in;
   }
-  uint32_t n_eval = 0u, n_comp = 0u;
+  uint32_t n_eval = 0u, n_comp = 0u, n_evb = 0u;
   for (uint32_t base = range.x; base < range.y; base += kBatch) {
     if (__syncthreads_count(nlive > 0) == 0) break;
     stage_batch<NT, kBatch>(A.inst_val, A.rec_geom, A.rec_color, A.rec_blue, A.vis_cap, base, range.y, s_geom, s_col,
@@ -175,7 +178,10 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         const AlphaEval e = pixel_alpha<decltype(clamp_tag)::value>(ct, geom.y, col.x, pyc[k]);
-        if (kStats) n_eval += T[k] > 0.0f;
+        if (kStats) {
+          n_eval += T[k] > 0.0f;
+          pend[k] += T[k] > 0.0f;
+        }
         if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
           const float Tn = __fsub_rn(T[k], w);
@@ -195,7 +201,11 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
             }
             T[k] = Tn;
             if (kTrack) last[k] = pos0 + (uint32_t)j;
-            if (kStats) ++n_comp;
+            if (kStats) {
+              ++n_comp;
+              n_evb += pend[k];
+              pend[k] = 0u;
+            }
           }
         }
       }
@@ -218,15 +228,17 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
     }
   }
   if (kStats) {
-    unsigned long long ev = n_eval, co = n_comp;
+    unsigned long long ev = n_eval, co = n_comp, eb = n_evb;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       ev += __shfl_xor_sync(0xffffffffu, ev, o);
       co += __shfl_xor_sync(0xffffffffu, co, o);
+      eb += __shfl_xor_sync(0xffffffffu, eb, o);
     }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&stats[0], ev);
       atomicAdd(&stats[1], co);
+      atomicAdd(&stats[2], eb);
     }
   }
   const int64_t HW = (int64_t)V.width * V.height;
@@ -403,7 +415,10 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
       }
       if (!__any_sync(0xffffffffu, contrib)) return;
       const float dx = ct.dx;
-      const float An = 2.0f * kLn2 * geom.z, Bn = kLn2 * geom.w, Cn = 2.0f * kLn2 * col.x;
+      // the natural-log conic (A, B, C) of the record's factors: A' = a1^2 +
+      // b1^2, B' = 2 b1 b2, C' = b2^2 in base 2
+      const float An = 2.0f * kLn2 * __fmaf_rn(geom.z, geom.z, geom.w * geom.w);
+      const float Bn = 2.0f * kLn2 * (geom.w * col.x), Cn = 2.0f * kLn2 * (col.x * col.x);
       // g = (du, dv, dA', dB', dC', da, dr, dg), plus db.
       float g[8] = {-(An * dx * S0 + Bn * S1), -(Cn * S1 + Bn * dx * S0), -0.5f * dx * dx * S0, -dx * S1,
                     -0.5f * S2, S0 * ex2_approx(-col.y), gr, gg};

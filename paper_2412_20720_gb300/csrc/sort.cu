@@ -241,22 +241,32 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
   }
 }
 
-// Does the ellipse {d : A d_x^2 + B d_x d_y + C d_y^2 <= tau} around (u, v)
-// meet the box [x0, x1] x [y0, y1] of a tile's pixel centres?  Exact minimum
-// of the positive definite form over the box: 0 if the centre is inside, else
-// the least of the four edge minima (edge x = X: d_y = clamp(-B X / (2 C))).
-// Every operation is an explicitly rounded FP32 operation in a fixed order,
-// so the decision is reproducible bit for bit.  Entries of tiles it rejects
-// are skipped at every pixel of the tile (alpha < 1/255), so dropping them
-// leaves the image unchanged.
-// kx = -B / (2 C) and ky = -B / (2 A), the edge minimisers per unit offset,
-// depend on the Gaussian only and are computed once per slot (edge_slopes).
-__device__ __forceinline__ float2 edge_slopes(float A, float B, float C) {
-  return make_float2(__fdiv_rn(-B, __fmul_rn(2.0f, C)), __fdiv_rn(-B, __fmul_rn(2.0f, A)));
+// Does the ellipse {d : q(d) <= tau} around (u, v) meet the box [x0, x1] x
+// [y0, y1] of a tile's pixel centres?  q(d) = (a1 d_x)^2 + (b1 d_x + b2 d_y)^2
+// is the record's exponent as a sum of two squares.  Exact minimum of q over
+// the box: 0 if the centre is inside, else the least of the four edge minima.
+// On an edge d_x = X, q is least at d_y = kx X (kx = -b1 / b2), where it is
+// (a1 X)^2; on an edge d_y = Y at d_x = ky Y (ky = -b1 b2 / (a1^2 + b1^2)); a
+// minimiser outside the edge is clamped to it.  q is evaluated at the
+// (clamped) point as the sum of two squares, so nothing cancels.  Every
+// operation is an explicitly rounded FP32 operation in a fixed order, so the
+// decision is reproducible bit for bit.  Entries of tiles it rejects are
+// skipped at every pixel of the tile (alpha < 1/255), so dropping them leaves
+// the image unchanged.  kx and ky depend on the Gaussian only and are
+// computed once per slot (edge_slopes).
+__device__ __forceinline__ float2 edge_slopes(float a1, float b1, float b2) {
+  return make_float2(__fdiv_rn(-b1, b2),
+                     __fdiv_rn(__fmul_rn(-b1, b2), __fmaf_rn(a1, a1, __fmul_rn(b1, b1))));
 }
 
-__device__ __forceinline__ bool ellipse_meets_box(float u, float v, float A, float B, float C, float kx, float ky,
-                                                  float tau, float x0, float x1, float y0, float y1) {
+__device__ __forceinline__ float sum_sq(float a1, float b1, float b2, float x, float y) {
+  const float ax = __fmul_rn(a1, x);
+  const float w = __fmaf_rn(b2, y, __fmul_rn(b1, x));
+  return __fmaf_rn(w, w, __fmul_rn(ax, ax));
+}
+
+__device__ __forceinline__ bool ellipse_meets_box(float u, float v, float a1, float b1, float b2, float kx,
+                                                  float ky, float tau, float x0, float x1, float y0, float y1) {
   const float lx = __fsub_rn(x0, u), hx = __fsub_rn(x1, u);
   const float ly = __fsub_rn(y0, v), hy = __fsub_rn(y1, v);
   if (lx <= 0.0f && hx >= 0.0f && ly <= 0.0f && hy >= 0.0f) return tau >= 0.0f;
@@ -265,14 +275,10 @@ __device__ __forceinline__ bool ellipse_meets_box(float u, float v, float A, flo
   for (int k = 0; k < 2; ++k) {
     const float X = k ? hx : lx;
     const float Yv = fminf(fmaxf(__fmul_rn(kx, X), ly), hy);
-    const float qx = __fadd_rn(__fadd_rn(__fmul_rn(A, __fmul_rn(X, X)), __fmul_rn(B, __fmul_rn(X, Yv))),
-                               __fmul_rn(C, __fmul_rn(Yv, Yv)));
-    m = fminf(m, qx);
+    m = fminf(m, sum_sq(a1, b1, b2, X, Yv));
     const float Y = k ? hy : ly;
     const float Xv = fminf(fmaxf(__fmul_rn(ky, Y), lx), hx);
-    const float qy = __fadd_rn(__fadd_rn(__fmul_rn(A, __fmul_rn(Xv, Xv)), __fmul_rn(B, __fmul_rn(Xv, Y))),
-                               __fmul_rn(C, __fmul_rn(Y, Y)));
-    m = fminf(m, qy);
+    m = fminf(m, sum_sq(a1, b1, b2, Xv, Y));
   }
   return m <= tau;
 }
@@ -299,14 +305,15 @@ struct EmitArgs {
   int64_t total_tiles;
 };
 
-// Emission record of depth-sorted position j holding slot s: (u, v, A', B'),
-// (C', kx, ky, tau), (slot, view, packed rect lo, packed rect hi); returns
+// Emission record of depth-sorted position j holding slot s: (u, v, a1, b1),
+// (b2, kx, ky, tau), (slot, view, packed rect lo, packed rect hi); returns
 // the number of (slot, tile) pairs to enumerate for it.  Only tiles whose
-// pixel-centre box meets the 1/255 ellipse are kept, so the pairs are
-// enumerated over the rect cut to the ellipse's bounding box: half-extents
-// sqrt(tau C'/det), sqrt(tau A'/det) with det = A'C' - B'^2/4, widened by
-// 0.1% + 0.05 px against rounding (a box outside them is far outside the
-// ellipse, which the exact test of the emission rejects as well).  With tile
+// pixel-centre box meets the 1/255 ellipse q <= tau are kept, so the pairs
+// are enumerated over the rect cut to the ellipse's bounding box: with q =
+// (a1 dx)^2 + (b1 dx + b2 dy)^2 the half-extents are sqrt(tau) / a1 and
+// sqrt(tau (a1^2 + b1^2)) / (a1 b2), widened by 0.1% + 0.05 px against
+// rounding (a box outside them is far outside the ellipse, which the exact
+// test of the emission rejects as well).  With tile
 // edge T, tile tx's centre box [T tx + 0.5, T tx + T - 0.5] can meet
 // [u - rx, u + rx] only for ceil((u - rx - T + 0.5) / T) <= tx <= floor((u + rx - 0.5) / T).
 template <int MAXV>
@@ -322,13 +329,14 @@ __device__ __forceinline__ uint32_t pair_record(const EmitArgs &A, const RasterV
     cc = A.color[s].x;
     tau = A.tau[s];
     int x0 = mm.z & 0xffff, y0 = (uint32_t)mm.z >> 16, x1 = mm.w & 0xffff, y1 = (uint32_t)mm.w >> 16;
-    const float det = g.z * cc - 0.25f * g.w * g.w;
     if (tau < 0.0f) {
       x1 = x0;
-    } else if (det > 0.0f) {
+    } else if (g.z > 0.0f && cc > 0.0f) {
       const RasterView &V = rv.v[MAXV == 1 ? 0 : min(max(mm.y, 0), rv.nviews - 1)];
       const float T = (float)V.tile, iT = 1.0f / T;
-      const float rx = sqrtf(tau * cc / det) * 1.001f + 0.05f, ry = sqrtf(tau * g.z / det) * 1.001f + 0.05f;
+      const float st = sqrtf(tau);
+      const float rx = st / g.z * 1.001f + 0.05f;
+      const float ry = st * sqrtf(g.z * g.z + g.w * g.w) / (g.z * cc) * 1.001f + 0.05f;
       const float lx = ceilf((g.x - rx - (T - 0.5f)) * iT), hx = floorf((g.x + rx - 0.5f) * iT);
       const float ly = ceilf((g.y - ry - (T - 0.5f)) * iT), hy = floorf((g.y + ry - 0.5f) * iT);
       if (lx > (float)x0) x0 = (int)fminf(lx, (float)x1);
@@ -455,7 +463,7 @@ struct PairWalk {
   int lo;  // position within the chunk
   int x0, y0, x1, tx, ty;
   uint32_t slot, view;
-  float u, v, A, B, C, kx, ky, tau;
+  float u, v, a1, b1, b2, kx, ky, tau;
 };
 
 __device__ __forceinline__ void walk_load(const EmitArgs &A, const EmitChunkSmem &S, int lo, PairWalk &w) {
@@ -464,9 +472,9 @@ __device__ __forceinline__ void walk_load(const EmitArgs &A, const EmitChunkSmem
   w.lo = lo;
   w.u = __int_as_float(r0.x);
   w.v = __int_as_float(r0.y);
-  w.A = __int_as_float(r0.z);
-  w.B = __int_as_float(r0.w);
-  w.C = __int_as_float(r1.x);
+  w.a1 = __int_as_float(r0.z);
+  w.b1 = __int_as_float(r0.w);
+  w.b2 = __int_as_float(r1.x);
   w.kx = __int_as_float(r1.y);
   w.ky = __int_as_float(r1.z);
   w.tau = __int_as_float(r1.w);
@@ -517,7 +525,7 @@ __device__ __forceinline__ bool walk_keep(const RasterViews<MAXV> &rv, const Pai
   const float bx0 = (float)(w.tx * T) + 0.5f, by0 = (float)(w.ty * T) + 0.5f;
   const float bx1 = (float)min(w.tx * T + T - 1, V.width - 1) + 0.5f;
   const float by1 = (float)min(w.ty * T + T - 1, V.height - 1) + 0.5f;
-  return ellipse_meets_box(w.u, w.v, w.A, w.B, w.C, w.kx, w.ky, w.tau, bx0, bx1, by0, by1);
+  return ellipse_meets_box(w.u, w.v, w.a1, w.b1, w.b2, w.kx, w.ky, w.tau, bx0, bx1, by0, by1);
 }
 
 template <int MAXV>
@@ -864,4 +872,22 @@ extern "C" int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, ui
                                                                 &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1], nullptr, 0);
   }
   return cudaGetLastError() == cudaSuccess ? FGS4D_OK : FGS4D_ERR_CUDA;
+}
+
+extern "C" int fgs4d_sort_depth_static_status(void *stream) {
+  using namespace fgs4d;
+  StaticSortScratch *s = nullptr;
+  const int rc = static_scratch(&s);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // The status bits of the last call: the radix passes OR a timed-out
+  // look-back or an out-of-range position into ctl[1]; the next call's init
+  // kernel clears the word, so it is read here, after the stream drains.
+  uint32_t status = 0;
+  if (cudaMemcpyAsync(&status, &s->ctl[1], sizeof status, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FGS4D_ERR_CUDA;
+  if (status & kStatusTimeout) return FGS4D_ERR_TIMEOUT;
+  if (status & kStatusInternal) return FGS4D_ERR_INTERNAL;
+  return FGS4D_OK;
 }

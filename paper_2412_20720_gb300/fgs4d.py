@@ -30,11 +30,12 @@ TILE = 16  # default tile edge; 8 is the other supported size
 
 EXPORTED = ("fgs4d_workspace_size", "fgs4d_workspace_layout", "fgs4d_preprocess", "fgs4d_bin_sort",
             "fgs4d_bin_sort_kernels", "fgs4d_render_fwd", "fgs4d_render_image", "fgs4d_render_aux",
-            "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians",
+            "fgs4d_render_stats", "fgs4d_render_bwd", "fgs4d_render_bwd_composite",
+            "fgs4d_render_bwd_preprocess", "fgs4d_render_aux_bwd", "fgs4d_split_gaussians",
             "fgs4d_mask_loss", "fgs4d_adam_tick", "fgs4d_adam_update", "fgs4d_adam_update_set",
             "fgs4d_render_features",
             "fgs4d_render_features_bwd", "fgs4d_l1_loss", "fgs4d_l1_loss_part", "fgs4d_sort_depth_static",
-            "fgs4d_wait_selftest", "fgs4d_get_status", "fgs4d_status_string")
+            "fgs4d_sort_depth_static_status", "fgs4d_wait_selftest", "fgs4d_get_status", "fgs4d_status_string")
 STATIC_SORT_MAX = 1 << 20
 ADAM_MAX_TENSORS = 16
 
@@ -123,6 +124,9 @@ def load():
                                      vp]
     lib.fgs4d_render_aux_bwd.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t, vp, vp,
                                          P(GaussiansGrad), vp]
+    lib.fgs4d_render_bwd_composite.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, vp]
+    lib.fgs4d_render_bwd_preprocess.argtypes = [P(Gaussians), P(View), i32, P(Settings), vp, C.c_size_t,
+                                                P(GaussiansGrad), vp]
     lib.fgs4d_split_gaussians.argtypes = [P(Gaussians), vp, i64, i32, vp, C.c_float, P(Settings), P(GaussiansOut), vp]
     lib.fgs4d_mask_loss.argtypes = [vp, i64, vp, vp, vp]
     lib.fgs4d_render_features.argtypes = [i64, P(View), i32, P(Settings), vp, C.c_size_t, vp, i32, vp, vp, vp]
@@ -134,6 +138,7 @@ def load():
     lib.fgs4d_l1_loss.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.fgs4d_l1_loss_part.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     lib.fgs4d_sort_depth_static.argtypes = [vp, i64, vp, vp]
+    lib.fgs4d_sort_depth_static_status.argtypes = [vp]
     lib.fgs4d_wait_selftest.argtypes = [vp, C.c_size_t, vp]
     lib.fgs4d_get_status.argtypes = [vp, C.c_size_t, vp, P(C.c_int64)]
     lib.fgs4d_status_string.argtypes = [C.c_int]
@@ -265,6 +270,18 @@ def render_bwd(gaussians: Gaussians, views, nviews: int, settings: Settings, ws:
                                    C.byref(grads), stream), "fgs4d_render_bwd")
 
 
+def render_bwd_composite(n: int, views, nviews: int, settings: Settings, ws: int, ws_bytes: int, dL_drgb: int,
+                         stream: int):
+    _check(load().fgs4d_render_bwd_composite(int(n), views, int(nviews), C.byref(settings), ws, ws_bytes, dL_drgb,
+                                             stream), "fgs4d_render_bwd_composite")
+
+
+def render_bwd_preprocess(gaussians: Gaussians, views, nviews: int, settings: Settings, ws: int, ws_bytes: int,
+                          grads: GaussiansGrad, stream: int):
+    _check(load().fgs4d_render_bwd_preprocess(C.byref(gaussians), views, int(nviews), C.byref(settings), ws, ws_bytes,
+                                              C.byref(grads), stream), "fgs4d_render_bwd_preprocess")
+
+
 def render_aux_bwd(gaussians: Gaussians, views, nviews: int, settings: Settings, ws: int, ws_bytes: int,
                    dL_drgb: int, dL_daux: int, grads: GaussiansGrad, stream: int):
     _check(load().fgs4d_render_aux_bwd(C.byref(gaussians), views, int(nviews), C.byref(settings), ws, ws_bytes,
@@ -334,6 +351,13 @@ def sort_depth_static(depth_keys: int, n: int, sorted_slots: int, stream: int):
     """Depth sort with the library's own device scratch (no allocation);
     see fgs4d_sort_depth_static in include/fgs4d.h for who needs it."""
     _check(load().fgs4d_sort_depth_static(depth_keys, int(n), sorted_slots, stream), "fgs4d_sort_depth_static")
+
+
+def sort_depth_static_status(stream: int) -> int:
+    """Synchronises the stream and returns the device-side outcome of the last
+    sort_depth_static call on the current device (OK, ERR_TIMEOUT or
+    ERR_INTERNAL)."""
+    return int(load().fgs4d_sort_depth_static_status(stream))
 
 
 def get_status(ws: int, ws_bytes: int, stream: int):

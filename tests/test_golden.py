@@ -80,3 +80,10 @@ def test_oracle_tiny_render_matches_the_stored_values():
     np.testing.assert_allclose(margin[g["py"], g["px"]], g["margin"], rtol=0, atol=1e-12)
     np.testing.assert_allclose(img.reshape(3, -1).sum(axis=1), g["sum_rgb"], rtol=1e-12)
     np.testing.assert_allclose(T.sum(), g["sum_T"], rtol=1e-12)
+    pix = g["py"] * view["width"] + g["px"]
+    plain = np.concatenate([img.reshape(3, -1)[:, pix], T.reshape(1, -1)[:, pix]]).T
+    alts = make_golden.alternatives(params, view, cfg, pix, plain)
+    assert sum(a.shape[0] for a in g["alternatives"]) > 0  # some sampled pixels sit on a threshold
+    for got, want in zip(alts, g["alternatives"]):
+        assert got.shape == want.shape
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)

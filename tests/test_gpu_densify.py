@@ -9,7 +9,8 @@ import oracle
 from paper_2412_20720_gb300 import synthetic as sy
 from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, split_gaussians
 
-from helpers import PIXEL_MARGIN, compare_group, keep_clear_of_boundaries, oracle_settings, subset, to_device
+from helpers import (compare_group, loss_gradient_at_settled_pixels, oracle_flags, oracle_proj, oracle_settings,
+                     to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -20,15 +21,15 @@ def test_densify_stats_match_oracle_over_views():
     views = [sy.tiny_view(96, 72, t=0.45), sy.tiny_view(80, 64, t=0.55)]
     cfg = RenderConfig(sh_degree=2, t_order=1, inst_capacity=1 << 18)
     params = sc.as_dict()
-    params = subset(params, keep_clear_of_boundaries(params, views, cfg))
     n = params["mean"].shape[0]
     st = oracle_settings(cfg)
     rng = np.random.default_rng(10)
-    dimgs, expect = [], np.zeros((n, 4))
+    dimgs, expect, maybe = [], np.zeros((n, 4)), np.zeros(n)
     for v in views:
+        prr = oracle_proj(params, v, cfg)
+        maybe += (prr["uncertain"] & 1) > 0
         pr = oracle.preprocess(params, v, st)
-        img, T, nc, mg = oracle.render(pr, v, st)
-        d = rng.standard_normal(img.shape) * (mg >= PIXEL_MARGIN)
+        d = loss_gradient_at_settled_pixels(rng, oracle_flags(prr, v, cfg), (3, int(v["height"]), int(v["width"])))
         dimgs.append(d)
         expect += oracle.densify_stats(params, pr, v, st, d)
     r = Renderer(n, views, cfg)
@@ -40,7 +41,11 @@ def test_densify_stats_match_oracle_over_views():
     r.backward(p, flat, grads, densify_stats=stats)
     r.check()
     got = stats.cpu().numpy().astype(np.float64)
-    np.testing.assert_array_equal(got[:, 2], expect[:, 2])
+    # view counts: equal where every view's decision is certain; where some
+    # are uncertain, within that many views of the FP64 count
+    cert = maybe == 0
+    np.testing.assert_array_equal(got[cert, 2], expect[cert, 2])
+    assert np.all(np.abs(got[~cert, 2] - expect[~cert, 2]) <= maybe[~cert])
     assert expect[:, 2].max() == 2 and (expect[:, 2] == 1).any()
     compare_group("|dL/dmu_2d|", got[:, 0], expect[:, 0], 1e-3, 1e-4)
     compare_group("|dL/dmu_t|", got[:, 1], expect[:, 1], 1e-3, 1e-4)

@@ -1,34 +1,29 @@
 """The CUDA path (through the C ABI) against the stored oracle render of the
-tiny configuration (tests/golden/tiny_2000_128x96.txt): sampled pixels clear
-of every alpha threshold within the image tolerance, without running the
-oracle."""
+tiny configuration (tests/golden/tiny_2000_128x96.txt): every sampled pixel
+within the image tolerance of the stored result or of one of its stored
+admissible alternatives, without running the oracle."""
 import os
 import sys
 
 import numpy as np
 import pytest
 
-from helpers import PIXEL_MARGIN, GpuRun
+from helpers import IMAGE_ATOL, GpuRun
 
 sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
 import make_golden  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-IMAGE_ATOL = 2e-4
-
 
 def test_tiny_render_matches_the_stored_oracle_values():
     g = make_golden.read()
     params, view, cfg = make_golden.tiny_scene_inputs()
-    # The fixture kept every Gaussian of the seeded scene (none sits at a
-    # threshold), so the full scene is the fixture's input.
     assert params["mean"].shape[0] == g["kept"]
     run = GpuRun(params, [view], cfg)
-    ok = g["margin"] >= PIXEL_MARGIN
-    assert ok.mean() >= 0.95
-    py, px = g["py"][ok], g["px"][ok]
-    rgb = run.images[0][:, py, px].T
-    assert np.abs(rgb - g["rgb"][ok]).max() <= IMAGE_ATOL
-    T = run.T.reshape(view["height"], view["width"])[py, px]
-    assert np.abs(T - g["T"][ok]).max() <= IMAGE_ATOL
+    py, px = g["py"], g["px"]
+    got = np.concatenate([run.images[0][:, py, px], run.T.reshape(view["height"], view["width"])[py, px][None]]).T
+    plain = np.concatenate([g["rgb"], g["T"][:, None]], axis=1)
+    for q in range(py.size):
+        cands = np.concatenate([plain[q:q + 1], g["alternatives"][q]])
+        assert np.abs(cands - got[q]).max(axis=1).min() <= IMAGE_ATOL, (py[q], px[q], got[q], cands)

@@ -8,7 +8,8 @@ import oracle
 from paper_2412_20720_gb300 import synthetic as sy
 from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, mask_loss
 
-from helpers import PIXEL_MARGIN, compare_group, keep_clear_of_boundaries, oracle_settings, subset, to_device
+from helpers import (RELAX, check_pixels, compare_group, loss_gradient_at_settled_pixels, oracle_flags,
+                     oracle_settings, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -21,9 +22,7 @@ def masked_case(seed=13, n=2000, L=2, NT=1):
     params["mask_logit"] = np.random.default_rng(seed).normal(0.0, 1.5, n).astype(np.float32)
     view = sy.tiny_view(112, 88, t=0.5)
     cfg = RenderConfig(sh_degree=L, t_order=NT, inst_capacity=1 << 18, mask_threshold=EPS)
-    with_thr = dict(params, mask_threshold=float(np.float32(EPS)))
-    keep = keep_clear_of_boundaries(with_thr, [view], cfg)
-    return subset(params, keep), view, cfg
+    return params, view, cfg
 
 
 def oracle_params(params):
@@ -38,7 +37,8 @@ def run_gpu(params, view, cfg, dimg=None):
     p["mask_logit"] = torch.from_numpy(params["mask_logit"]).cuda()
     img = r.forward(p)
     counts = r.check()
-    out = {"img": r.split(img)[0].cpu().numpy(), "visible": counts[0]}
+    out = {"img": r.split(img)[0].cpu().numpy(), "visible": counts[0],
+           "T": r.workspace_view(r.layout.pix_T, torch.float32, r.total_pixels).cpu().numpy()}
     if dimg is not None:
         grads = {k: torch.zeros_like(v) for k, v in p.items()}
         r.backward(p, torch.from_numpy(dimg.reshape(-1).astype(np.float32)).cuda(), grads)
@@ -50,22 +50,22 @@ def run_gpu(params, view, cfg, dimg=None):
 def test_masked_render_matches_oracle():
     params, view, cfg = masked_case()
     st = oracle_settings(cfg)
-    pr = oracle.preprocess(oracle_params(params), view, st)
-    img, T, nc, mg = oracle.render(pr, view, st)
-    ok = mg >= PIXEL_MARGIN
+    pr = oracle.preprocess(oracle_params(params), view, st, relax=RELAX)
     g = run_gpu(params, view, cfg)
-    assert g["visible"] == int((pr["status"] == 0).sum())
+    unc = (pr["uncertain"] & 1) > 0
+    certain = int(((pr["status"] == 0) & ~unc).sum())
+    assert certain <= g["visible"] <= certain + int(unc.sum())
     assert (pr["status"] == 7).sum() > 100
-    assert np.abs(g["img"] - img)[:, ok].max() <= 2e-4
+    check_pixels(pr, view, cfg, np.arange(view["width"] * view["height"]), g["img"].reshape(3, -1).T, g["T"])
 
 
 def test_mask_gradient_matches_oracle():
     params, view, cfg = masked_case(seed=14)
     st = oracle_settings(cfg)
     op = oracle_params(params)
+    flags = oracle_flags(oracle.preprocess(op, view, st, relax=RELAX), view, cfg)
     pr = oracle.preprocess(op, view, st)
-    img, T, nc, mg = oracle.render(pr, view, st)
-    dimg = np.random.default_rng(15).standard_normal(img.shape) * (mg >= PIXEL_MARGIN)
+    dimg = loss_gradient_at_settled_pixels(np.random.default_rng(15), flags, (3,) + flags.shape)
     g_orc = oracle.render_backward(op, pr, view, st, dimg)
     g = run_gpu(params, view, cfg, dimg)["grads"]
     assert np.abs(g_orc["mask_logit"]).max() > 0

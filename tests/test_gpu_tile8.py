@@ -10,9 +10,8 @@ from paper_2412_20720_gb300 import fgs4d
 from paper_2412_20720_gb300 import synthetic as sy
 from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, autotune
 
-from helpers import GpuRun, canonical_ranges, compare_group, oracle_settings, to_device
-from test_gpu_parity import (_grad_case, _oracle_sorted, _synthetic_records, _write_records, check_gradients,
-                             check_image, check_records, tiny_case)
+from helpers import GpuRun, canonical_ranges, check_image, check_records, oracle_settings, to_device
+from test_gpu_parity import KEEP_ALL, _grad_case, _synthetic_records, _write_records, check_gradients, tiny_case
 
 pytestmark = pytest.mark.gpu
 
@@ -41,13 +40,13 @@ def test_bin_sort_bit_exact_at_tile_8(n, W, H):
     import torch
     rng = np.random.default_rng(n + 8)
     gw, gh = (W + 7) // 8, (H + 7) // 8
-    rec = _synthetic_records(rng, n, W, H, 8, tile=8)
+    rec = _synthetic_records(rng, n, W, H, 8, tile=8, tau=KEEP_ALL)
     cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=60 * n + 16, tile=8)
     r = Renderer(n, [sy.tiny_view(W, H)], cfg)
     _write_records(r, rec, 0)
     fgs4d.bin_sort(n, r.views, r.nviews, r.settings, r.ws.data_ptr(), r.ws_bytes, r.stream())
     counts = r.check()
-    keys, vals, ranges = _oracle_sorted(rec, W, H, tile=8)
+    keys, vals, ranges = oracle.sort_instances(rec["rect"], rec["depth"], gw, gh)
     m = keys.shape[0]
     assert counts[1] == m
     tiles = r.workspace_view(r.layout.inst_tile, torch.int32, m).cpu().numpy()
@@ -73,10 +72,9 @@ def test_autotune_over_both_tile_sizes():
                               for b in (256, 128)}
     assert r.settings.tile == res["tile"] and r.settings.pixels_per_thread == res["pixels_per_thread"]
     assert r.settings.shared_batch == res["shared_batch"]
-    img = r.split(r.forward(dev))[0].cpu().numpy()
-    r.check()
     # The chosen tile edge renders the oracle's image at that edge.
-    ost = oracle_settings(RenderConfig(**{**cfg.__dict__, "tile": res["tile"]}))
-    ref, T, nc, mg = oracle.render(oracle.preprocess(params, view, ost), view, ost)
-    ok = mg >= 1e-3
-    assert np.abs(img - ref)[:, ok].max() <= 2e-4
+    run = GpuRun(params, [view], RenderConfig(**{**cfg.__dict__, "tile": res["tile"],
+                                                 "pixels_per_thread": res["pixels_per_thread"],
+                                                 "shared_batch": res["shared_batch"]}))
+    np.testing.assert_array_equal(run.images[0], r.split(r.forward(dev))[0].cpu().numpy())
+    check_image(run, params, view, run.renderer.config)

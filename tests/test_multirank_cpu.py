@@ -1,8 +1,8 @@
-"""The N > 1 path of bench.py on CPU: two gloo ranks (no GPU).  Every rank
-renders its own sweep (weak scaling, no collective on the data path); the
-only exchange is the max-over-ranks of the timings, and the whole-job rate is
-the units all ranks processed over the slowest rank's time.  The reference
-arm prints from rank 0 only."""
+"""The N > 1 path of bench.py on CPU: two gloo ranks (no GPU).  The ranks
+shard the views of one sweep (rank r renders views k = r mod N; weak scaling,
+no collective on the data path); the only exchange is the max-over-ranks of
+the timings, and the whole-job rate is the units all ranks processed over the
+slowest rank's time.  The reference arm prints from rank 0 only."""
 import os
 import socket
 
@@ -25,7 +25,10 @@ def _worker(rank, world, port, q):
         import bench
         ms = [10.0, 12.5][rank]
         mx = bench.max_over_ranks(ms, world, torch.device("cpu"))
-        q.put((rank, mx, bench.job_rate(300, world, mx)))
+        mine = bench.shard_views(300, rank, world)
+        shards = [None] * world
+        dist.all_gather_object(shards, mine)
+        q.put((rank, mx, bench.job_rate(len(mine), world, mx), shards))
     finally:
         dist.destroy_process_group()
 
@@ -43,9 +46,25 @@ def test_two_gloo_ranks_aggregate_like_the_bench():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert [o[0] for o in out] == [0, 1]
-    for _, mx, rate in out:
+    for _, mx, rate, shards in out:
         assert mx == 12.5  # the slower rank's time
         assert rate == pytest.approx(2 * 300 / 0.0125)
+        # every view of the 600-view sweep is rendered by exactly one rank
+        assert [len(s) for s in shards] == [300, 300]
+        assert sorted(shards[0] + shards[1]) == list(range(600))
+
+
+def test_sharded_sweep_views_are_distinct():
+    import bench
+    from paper_2412_20720_gb300 import synthetic as sy
+    world = 4
+    ts = set()
+    for r in range(world):
+        for k in bench.shard_views(5, r, world):
+            v = sy.orbit_view(k, 5 * world, 64, 48)
+            ts.add((float(v["t"]), tuple(float(x) for x in v["campos"])))
+    assert len(ts) == 5 * world
+    assert bench.shard_views(300, 0, 1) == list(range(300))  # N = 1: the plain sweep
 
 
 def test_single_rank_needs_no_process_group():

@@ -442,82 +442,6 @@ def test_sort_instances_against_lexsort():
     np.testing.assert_array_equal(ranges[nz, 0], np.concatenate([[0], np.cumsum(counts)[:-1]])[nz])
 
 
-# ------------------------------------------------------- tile culling pins
-
-def _random_ellipse(rng):
-    """Random positive definite q = A dx^2 + B dx dy + C dy^2 (FP32 values)."""
-    ang = rng.uniform(0, math.pi)
-    s1, s2 = np.exp(rng.uniform(math.log(0.5), math.log(40.0), 2))
-    c, s = math.cos(ang), math.sin(ang)
-    Rm = np.array([[c, -s], [s, c]])
-    Q = Rm @ np.diag([1 / s1 ** 2, 1 / s2 ** 2]) @ Rm.T * 0.5 * math.log2(math.e)
-    return np.float32(Q[0, 0]), np.float32(2 * Q[0, 1]), np.float32(Q[1, 1])
-
-
-def test_ellipse_tile_test_is_safe_and_tight():
-    """Safety: a tile is never dropped while one of its pixel centres lies
-    inside the ellipse q <= tau (brute force over all 256 centres, FP64).
-    Tightness: the test equals the exact minimum of q over the centre box,
-    estimated on a dense grid, away from the threshold."""
-    rng = np.random.default_rng(41)
-    kept = dropped = 0
-    for _ in range(1500):
-        A, B, C = _random_ellipse(rng)
-        u, v = np.float32(rng.uniform(-40, 80)), np.float32(rng.uniform(-40, 80))
-        tau = np.float32(rng.uniform(0.0, 8.0))
-        tx, ty = int(rng.integers(0, 3)), int(rng.integers(0, 3))
-        x0, x1, y0, y1 = tx * 16 + 0.5, tx * 16 + 15.5, ty * 16 + 0.5, ty * 16 + 15.5
-        keep = oracle.ellipse_meets_box(u, v, A, B, C, tau, x0, x1, y0, y1)
-        px, py = np.meshgrid(np.arange(16) + x0, np.arange(16) + y0)
-        dx, dy = px - float(u), py - float(v)
-        q = float(A) * dx * dx + float(B) * dx * dy + float(C) * dy * dy
-        if q.min() <= float(tau) * (1 - 1e-6):
-            assert keep
-        gx, gy = np.meshgrid(np.linspace(x0, x1, 241), np.linspace(y0, y1, 241))
-        gx, gy = gx - float(u), gy - float(v)
-        qmin = (float(A) * gx * gx + float(B) * gx * gy + float(C) * gy * gy).min()
-        if qmin > float(tau) + 1e-3 * (1 + float(tau)):
-            assert not keep
-        if qmin < float(tau) - 1e-3 * (1 + float(tau)):
-            assert keep
-        kept += keep
-        dropped += not keep
-    assert kept > 200 and dropped > 200
-
-
-def test_culled_sort_keeps_exactly_the_meeting_tiles():
-    rng = np.random.default_rng(42)
-    W, H = 150, 110
-    gw, gh = (W + 15) // 16, (H + 15) // 16
-    n = 300
-    rect = np.zeros((n, 4), dtype=np.int32)
-    rect[:, 0] = rng.integers(0, gw, n)
-    rect[:, 1] = rng.integers(0, gh, n)
-    rect[:, 2] = np.minimum(gw, rect[:, 0] + rng.integers(1, 6, n))
-    rect[:, 3] = np.minimum(gh, rect[:, 1] + rng.integers(1, 6, n))
-    uv = np.stack([rng.uniform(0, W, n), rng.uniform(0, H, n)], 1).astype(np.float32)
-    conic2 = np.array([_random_ellipse(rng) for _ in range(n)], dtype=np.float32)
-    tau = rng.uniform(0, 8, n).astype(np.float32)
-    depth = rng.uniform(1, 5, n).astype(np.float32)
-    keys, vals, ranges = oracle.sort_instances(rect, depth, gw, gh, uv=uv, conic2=conic2, tau=tau, width=W,
-                                               height=H)
-    expect = set()
-    for i in range(n):
-        for ty in range(rect[i, 1], rect[i, 3]):
-            for tx in range(rect[i, 0], rect[i, 2]):
-                x1 = min(tx * 16 + 15, W - 1) + 0.5
-                y1 = min(ty * 16 + 15, H - 1) + 0.5
-                if oracle.ellipse_meets_box(uv[i, 0], uv[i, 1], *conic2[i], tau[i], tx * 16 + 0.5, x1, ty * 16 + 0.5,
-                                            y1):
-                    expect.add((ty * gw + tx, i))
-    got = set(zip((keys >> np.uint64(32)).astype(np.int64).tolist(), vals.tolist()))
-    assert got == expect
-    full, _, _ = oracle.sort_instances(rect, depth, gw, gh)
-    assert 0 < len(got) < full.shape[0]
-    t = (keys >> np.uint64(32)).astype(np.int64)
-    assert np.all(np.diff(t) >= 0)
-
-
 # ------------------------------------------------ auxiliary channel pins
 
 def test_flow_vanishes_without_space_time_coupling():

@@ -25,6 +25,10 @@ for L, NT, n, (w, h) in ((3, 2, 64, (32, 32)), (1, 1, 300, (45, 29)), (0, 0, 40,
     img, T, nc, mg = oracle.render(pr, view, st)
     pix = np.array([[0, 0], [w - 1, h - 1], [w // 2, h // 2]], dtype=np.int32)
     oracle.render_pixels(pr, view, st, pix)
+    prr = oracle.preprocess(p, view, st, relax=1e-3)
+    oracle.render_pixels_admissible(prr, view, st, np.arange(w * h),
+                                    oracle.Tolerance(eps_conic=1e-3, eps_uv=1e-5, eps_uv_abs=1e-3, eps_a=1e-4,
+                                                     eps_alpha=1e-5, depth_ulps=4), extra=np.ones((n, 3)))
     dimg = np.random.default_rng(0).standard_normal(img.shape)
     oracle.render_backward(p, pr, view, st, dimg)
     aux = oracle.aux_records(p, pr, view, st, 0.05)

@@ -40,20 +40,46 @@ def _bin_sort_order(keys_np):
 
 
 def test_static_depth_sort_matches_bin_sort_on_consecutive_calls():
+    """Sizes up to the scratch's limit (FGS4D_STATIC_SORT_MAX keys: the
+    largest grid and look-back chain the array was sized for), each sorted
+    twice in a row, each call's device status read back."""
     import torch
     rng = np.random.default_rng(20)
     stream = torch.cuda.current_stream().cuda_stream
-    for n in (70_001, 2047):  # a second, smaller sort over the same scratch
+    # a large sort, a smaller one over the same scratch, then the limit
+    for n in (70_001, 2047, fgs4d.STATIC_SORT_MAX):
         keys = _depth_keys(rng, n)
         expect = _bin_sort_order(keys)
         keys_dev = torch.from_numpy(keys.view(np.int32)).cuda()
         for _ in range(2):
             out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
             fgs4d.sort_depth_static(keys_dev.data_ptr(), n, out.data_ptr(), stream)
-            torch.cuda.synchronize()
+            assert fgs4d.sort_depth_static_status(stream) == fgs4d.OK
             assert torch.equal(out, expect)
         # The permutation is the stable order of the keys.
         np.testing.assert_array_equal(out.cpu().numpy(), np.argsort(keys, kind="stable"))
+
+
+def test_static_depth_sort_allocates_no_device_memory():
+    """After a first call (which looks up the scratch's address), further
+    calls leave the device memory in use unchanged."""
+    import torch
+    rng = np.random.default_rng(21)
+    stream = torch.cuda.current_stream().cuda_stream
+    n = 300_001
+    keys_dev = torch.from_numpy(_depth_keys(rng, n).view(np.int32)).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    fgs4d.sort_depth_static(keys_dev.data_ptr(), n, out.data_ptr(), stream)
+    assert fgs4d.sort_depth_static_status(stream) == fgs4d.OK
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    for _ in range(3):
+        fgs4d.sort_depth_static(keys_dev.data_ptr(), n, out.data_ptr(), stream)
+        assert fgs4d.sort_depth_static_status(stream) == fgs4d.OK
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    assert after[:2] == before[:2]
+    assert after[2] >= before[2]  # free device memory did not shrink
 
 
 def test_static_depth_sort_rejects_sizes_beyond_its_scratch():

@@ -401,7 +401,7 @@ def run_ours(args, rank, world, local):
     launches_per_frame = 1 + fgs4d.bin_sort_kernels(scene.n, vv[0][0], vv[0][1], s) + 1
 
     # Capacity and work counts over the whole sweep (outside the timed region).
-    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    stats = torch.zeros(3, dtype=torch.int64, device=dev)  # fgs4d_render_stats adds three counters
     vis, inst, evals, comps = [], [], [], []
     for k in range(nviews):
         v, n1 = vv[k]
@@ -414,7 +414,7 @@ def run_ours(args, rank, world, local):
             raise RuntimeError("view %d: %s (counts %s)" % (k, fgs4d.status_string(code), counts))
         vis.append(counts[0])
         inst.append(counts[1])
-        e, c = stats.tolist()
+        e, c, _ = stats.tolist()
         evals.append(e)
         comps.append(c)
 

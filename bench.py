@@ -64,11 +64,14 @@ FLOPS_PER_BWD_COMP = 25
 ISSUE_PER_SM_CLK = 4
 # One ncu capture of the image-mode compositor (render_fwd_kernel, mode 3) on
 # this workload: DRAM bytes (read + write) and warp instructions per launch,
-# averaged over the captured launches.  Valid only for the compositor source
-# it was taken from (sha256 prefix of csrc/render.cu); any other source
-# reports null.
-NCU_RENDER_FWD = {"render_cu_sha256": None, "shape": None, "dram_bytes": None, "warp_insts": None,
-                  "launches": None, "capture": None}
+# averaged over the captured launches (the first three of the timed sweep,
+# views 0-2).  Valid only for the compositor sources it was taken from
+# (sha256 prefix of csrc/render.cu + csrc/fgs4d_internal.cuh) and block
+# shape; any other build reports null.
+NCU_RENDER_FWD = {"render_cu_sha256": "c814b4c9e375cc8f", "shape": "16/4/128", "dram_bytes": 5.02e6, "warp_insts": 128.73e6,
+                  "views": [0, 1, 2], "capture": "ncu --set full --clock-control none --nvtx --nvtx-include timed/ "
+                                                 "-k regex:render_fwd_kernel -c 3 on python bench.py --steps 1 "
+                                                 "--warmup 1 --shape 16/4/128 (no other legs)"}
 
 
 def parse():
@@ -83,6 +86,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurements")
+    p.add_argument("--batched", choices=("all", "sphere", "urban"), default="all",
+                   help="which batched workloads to run (default both)")
+    p.add_argument("--urban-views", type=int, default=12,
+                   help="views of the urban rig used (default all 12; fewer for profiling a small case)")
+    p.add_argument("--urban-group", type=int, default=6, help="urban views per call (default 6)")
     p.add_argument("--inflight", type=int, default=8, help="headline frames in flight (one stream and workspace each)")
     p.add_argument("--stage-blocks", type=int, default=1,
                    help="resident blocks per SM of the latency-bound stages (0 = full-GPU grids)")
@@ -340,9 +348,14 @@ def sy_orbit_view(k: int):
 
 
 def render_cu_sha256() -> str:
+    """sha256 prefix of the compositor's sources (render.cu and the shared
+    alpha evaluation in fgs4d_internal.cuh)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2412_20720_gb300", "csrc", "render.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("render.cu", "fgs4d_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2412_20720_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ----------------------------------------------------------------- ours
@@ -438,8 +451,10 @@ def run_ours(args, rank, world, local):
     barrier()
     torch.cuda.synchronize()
     start.record(stream)
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler restrict itself to the timed sweep
     for step in range(K):
         sweep(comp_evs[step])
+    torch.cuda.nvtx.range_pop()
     end.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -498,13 +513,15 @@ def run_ours(args, rank, world, local):
     shape = "%d/%d/%d" % (tuned["tile"], tuned["pixels_per_thread"], tuned["shared_batch"])
     ncu_ok = NCU_RENDER_FWD["render_cu_sha256"] == render_cu_sha256() and NCU_RENDER_FWD["shape"] == shape
     issue = None
-    if ncu_ok and NCU_RENDER_FWD["warp_insts"]:
-        # the issue-slot ceiling: the launch's warp instructions at one per
-        # scheduler per clock on every SM
-        floor_ms = NCU_RENDER_FWD["warp_insts"] / (nsm * ISSUE_PER_SM_CLK * sm_max * 1e6) * 1e3
-        issue = {"warp_insts_per_launch": NCU_RENDER_FWD["warp_insts"], "issue_limited_ms": floor_ms,
-                 "frac": floor_ms / comp_ms,
-                 "basis": "ncu warp instructions of this build / (SMs x 4 schedulers x max SM clock)"}
+    if ncu_ok and NCU_RENDER_FWD["warp_insts"] and len(evals) >= 3:
+        # The issue-slot ceiling: the captured views' warp instructions per
+        # alpha evaluation, times this sweep's mean evaluations, at one warp
+        # instruction per scheduler per clock on every SM.
+        per_eval = NCU_RENDER_FWD["warp_insts"] / float(np.mean([evals[v] for v in NCU_RENDER_FWD["views"]]))
+        floor_ms = per_eval * np.mean(evals) / (nsm * ISSUE_PER_SM_CLK * sm_max * 1e6) * 1e3
+        issue = {"warp_insts_per_alpha_eval": per_eval, "issue_limited_ms": floor_ms, "frac": floor_ms / comp_ms,
+                 "basis": "ncu warp instructions per alpha evaluation of this build x the sweep's mean evaluations "
+                          "/ (SMs x 4 schedulers x max SM clock)"}
 
     # ---------------------------------------------------------- e2e
     e2e = None
@@ -558,10 +575,15 @@ def run_ours(args, rank, world, local):
     # ---------------------------------------------------------- batched views
     batched = None
     if not args.no_batched:
-        batched = [run_batched(dev, sy.sphere_scene(), sy.sphere_views(64), "sphere-1M-64views-mixed-res", 2, 8,
-                               tiles=(16, 8), hbm=hbm),
-                   run_batched(dev, sy.urban_scene(), sy.urban_views(), "urban-3M-6cams-x-2t-1920x1080", 2, 6,
-                               plain=False, hbm=hbm)]
+        batched = []
+        if args.batched in ("all", "sphere"):
+            batched.append(run_batched(dev, sy.sphere_scene(), sy.sphere_views(64), "sphere-1M-64views-mixed-res", 2, 8,
+                                       tiles=(16, 8), hbm=hbm))
+        if args.batched in ("all", "urban"):
+            uv = sy.urban_views()[:args.urban_views]
+            label = "urban-3M-6cams-x-2t-1920x1080" if len(uv) == 12 and args.urban_group == 6 else \
+                "urban-3M-%dviews-1920x1080-%d-per-call" % (len(uv), args.urban_group)
+            batched.append(run_batched(dev, sy.urban_scene(), uv, label, 2, args.urban_group, plain=False, hbm=hbm))
 
     # ---------------------------------------------------------- C0
     c0 = None if args.no_c0 else run_tiny(dev)
@@ -797,7 +819,9 @@ def run_train(args, dev, scene, params, world, barrier, views, tgt_scene, target
     codes = [r.status()[0]] + [g.status()[0] for g in vp.groups]
 
     # Stages of the 4-view call alone, and the compositors' work counts.
+    torch.cuda.nvtx.range_push("train-stages")
     stages = fwd_bwd_stage_ms(r, pr, None, grads, loss=lambda img: l1_loss(img, target)[1])
+    torch.cuda.nvtx.range_pop()
     ev, co, evb = compositor_counts(r, pr)
     flops_fwd = FLOPS_PER_EVAL * ev + FLOPS_PER_COMP * co
     flops_bwd = FLOPS_PER_EVAL * evb + FLOPS_PER_BWD_COMP * co
@@ -917,9 +941,11 @@ def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,),
     # Per-stage times: each group's call alone on the GPU, events between the
     # stages, summed over the groups of a step.
     stages = {}
+    torch.cuda.nvtx.range_push("batched-stages")
     for r, dL in zip(rs, dLs):
         for k, v in fwd_bwd_stage_ms(r, params, dL, grads, reps=2).items():
             stages[k] = stages.get(k, 0.0) + v
+    torch.cuda.nvtx.range_pop()
     tiles_tot = sum(int(r.layout.total_tiles) for r in rs)
     bs_bytes = bin_sort_bytes(vis_tot, inst_tot, tiles_tot // len(rs)) if rs else 0.0
     bs_gbs = bs_bytes / (stages["bin_sort"] * 1e-3) / 1e9

@@ -19,8 +19,8 @@ import oracle
 from paper_2412_20720_gb300 import synthetic as sy
 from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, l1_loss
 
-from helpers import (check_pixels, compare_group, loss_gradient_at_settled_pixels, oracle_flags, oracle_proj,
-                     oracle_settings, to_device)
+from helpers import (ORDER_FLOOR, ORDER_RTOL, check_pixels, compare_group, loss_gradient_at_settled_pixels,
+                     oracle_flags, oracle_proj, oracle_settings, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -96,7 +96,7 @@ def test_training_step_graph_replays_equal_the_plain_step():
         np.testing.assert_array_equal(_pixel_T(r), T0)
         assert abs(float(loss_g.item()) - plain[1]) <= 1e-6 * plain[1]
         for k in PARAM_KEYS:
-            compare_group(k, grads[k].cpu().numpy().astype(np.float64), plain[2][k], 1e-5, 1e-6)
+            compare_group(k, grads[k].cpu().numpy().astype(np.float64), plain[2][k], ORDER_RTOL, ORDER_FLOOR)
     # the replayed images against the oracle, the loss against its definition
     _check_images_against_oracle(r, params, views, cfg, img_g, T0)
     ref = np.abs(img_g.cpu().numpy().astype(np.float64) - target).mean()
@@ -154,7 +154,7 @@ def test_mixed_resolution_view_group_graph_matches_plain_calls_and_oracle():
         np.testing.assert_array_equal(_pixel_T(r), T0)
         for k in PARAM_KEYS:
             got = grads[k].cpu().numpy().astype(np.float64)
-            compare_group(k, got, plain_g[k], 1e-5, 1e-6)
+            compare_group(k, got, plain_g[k], ORDER_RTOL, ORDER_FLOOR)
             compare_group(k, got, g_orc[k], 1e-3, 1e-4)
     _check_images_against_oracle(r, params, views, cfg, img_g, T0)
     assert len(set(r.sizes)) == 4

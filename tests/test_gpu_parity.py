@@ -610,7 +610,7 @@ def test_backward_in_two_stages_equals_one_call():
     fgs4d_render_bwd does (up to the order of the atomic sums)."""
     import torch
     from paper_2412_20720_gb300.render import Renderer
-    from helpers import to_device
+    from helpers import ORDER_FLOOR, ORDER_RTOL, to_device
     params, view, cfg = tiny_case(131, 77, 3, 2, (0.1, 0.2, 0.3))
     p = to_device(params)
     r = Renderer(params["mean"].shape[0], [view], cfg)
@@ -627,9 +627,9 @@ def test_backward_in_two_stages_equals_one_call():
                                 r._grads(two, None), st)
     r.check()
     slot_two = r.workspace_view(r.layout.slot_grad, torch.float32, 12 * nv).cpu().numpy()
-    compare_group("slot gradients", slot_two, slot_one, 1e-5, 1e-6)
+    compare_group("slot gradients", slot_two, slot_one, ORDER_RTOL, ORDER_FLOOR)
     for k in PARAM_KEYS:
-        compare_group(k, two[k].cpu().numpy(), one[k].cpu().numpy(), 1e-5, 1e-6)
+        compare_group(k, two[k].cpu().numpy(), one[k].cpu().numpy(), ORDER_RTOL, ORDER_FLOOR)
 
 
 def test_render_stats_counts_the_composited_entries():

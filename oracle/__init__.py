@@ -194,11 +194,25 @@ def _view_c(view) -> _View:
 
 
 class _ParamsHold:
-    def __init__(self, params):
+    def __init__(self, params, settings=None):
         # FP32 inputs are upcast exactly; FP64 inputs (finite differences) pass through.
         self.arrs = {k: np.ascontiguousarray(params[k], dtype=np.float64)
                      for k in ("mean", "log_scale", "q_l", "q_r", "opacity_logit", "sh")}
         n = self.arrs["mean"].shape[0]
+        # The C side reads n rows of each array and (L+1)^2 (N_t+1) SH rows
+        # per Gaussian: refuse anything shorter instead of reading past it.
+        want = {"mean": (n, 4), "log_scale": (n, 4), "q_l": (n, 4), "q_r": (n, 4), "opacity_logit": (n,)}
+        for k, shp in want.items():
+            if self.arrs[k].shape != shp:
+                raise ValueError("oracle parameter %s has shape %s, expected %s" % (k, self.arrs[k].shape, shp))
+        sh = self.arrs["sh"]
+        if sh.ndim != 3 or sh.shape[0] != n or sh.shape[2] != 3:
+            raise ValueError("oracle parameter sh has shape %s, expected (%d, K, 3)" % (sh.shape, n))
+        if settings is not None:
+            K = (settings.sh_degree + 1) ** 2 * (settings.t_order + 1)
+            if sh.shape[1] != K:
+                raise ValueError("oracle parameter sh has %d rows per Gaussian; SH degree %d and temporal order %d "
+                                 "take %d" % (sh.shape[1], settings.sh_degree, settings.t_order, K))
         mask = params.get("mask_logit")
         if mask is not None:  # optional Compact-4DGS significance mask
             self.arrs["mask_logit"] = np.ascontiguousarray(mask, dtype=np.float64)
@@ -214,7 +228,7 @@ def preprocess(params, view, settings: Settings, relax: float = 0.0):
     are marked ("uncertain", "rect_lo", "rect_hi"; orc_preprocess_relaxed);
     the FP64 decisions and values are the same either way."""
     lib = _load()
-    ph = _ParamsHold(params)
+    ph = _ParamsHold(params, settings)
     n = ph.n
     out = {}
     for name, dt, w in _PROJ_FIELDS:
@@ -319,7 +333,7 @@ def aux_records(params, proj, view, settings: Settings, flow_dt: float, relax: f
     relax > 0 and a projection from preprocess(..., relax), also filled for
     the Gaussians it marks as possibly present)."""
     lib = _load()
-    ph = _ParamsHold(params)
+    ph = _ParamsHold(params, settings)
     aux = np.zeros((ph.n, 3))
     pc, keep = _proj_c(proj)
     lib.orc_aux(C.byref(ph.c), C.byref(_view_c(view)), C.byref(settings._c()), float(flow_dt), float(relax),
@@ -406,7 +420,7 @@ def render_backward(params, proj, view, settings: Settings, dimg: np.ndarray):
     """Exact reverse-mode gradient (FP64) of <dimg, image> w.r.t. the
     parameters; also returns the per-Gaussian 2D gradients."""
     lib = _load()
-    ph = _ParamsHold(params)
+    ph = _ParamsHold(params, settings)
     K = ph.arrs["sh"].shape[1]
     g, gc = _alloc_grads(ph.n, K)
     dimg = np.ascontiguousarray(dimg, dtype=np.float64)
@@ -423,7 +437,7 @@ def render_aux_backward(params, proj, view, settings: Settings, dimg: np.ndarray
     aux = (depth, opacity, flow_u, flow_v) of render_aux; the flow planes of
     daux must be zero (flow is not differentiated)."""
     lib = _load()
-    ph = _ParamsHold(params)
+    ph = _ParamsHold(params, settings)
     K = ph.arrs["sh"].shape[1]
     g, gc = _alloc_grads(ph.n, K)
     dimg = np.ascontiguousarray(dimg, dtype=np.float64)
@@ -475,7 +489,7 @@ def densify_stats(params, proj, view, settings: Settings, dimg: np.ndarray) -> n
 def preprocess_backward(params, view, settings: Settings, g_uv, g_conic, g_a, g_rgb):
     """Adjoint of the per-Gaussian chain alone, from given 2D gradients."""
     lib = _load()
-    ph = _ParamsHold(params)
+    ph = _ParamsHold(params, settings)
     K = ph.arrs["sh"].shape[1]
     g, gc = _alloc_grads(ph.n, K)
     ins = [np.ascontiguousarray(a, dtype=np.float64) for a in (g_uv, g_conic, g_a, g_rgb)]

@@ -295,11 +295,12 @@ def test_walk_budget_is_flagged():
 
 def _on_axis(view, z, sigma, t_mean=0.5, t_scale=0.3, logit=0.0):
     """One isotropic Gaussian on the optical axis at camera depth z (the
-    tiny view's camera sits at world (0, 0, -3) looking along +z)."""
+    tiny view's camera sits at world (0, 0, -3) looking along +z); SH rows
+    for degree 1 x temporal order 1 (the default settings here)."""
     return {"mean": np.array([[0.0, 0.0, z - 3.0, t_mean]]),
             "log_scale": np.array([[math.log(sigma)] * 3 + [math.log(t_scale)]]),
             "q_l": np.array([[1.0, 0, 0, 0]]), "q_r": np.array([[1.0, 0, 0, 0]]),
-            "opacity_logit": np.array([logit]), "sh": np.zeros((1, 4, 3))}
+            "opacity_logit": np.array([logit]), "sh": np.zeros((1, 8, 3))}
 
 
 def test_temporal_cull_on_the_threshold_is_uncertain():

@@ -122,6 +122,8 @@ int compute_layout(const fgs4d_settings *s, int64_t n, const fgs4d_view *views, 
   const int k = s->stage_blocks_per_sm;
   L.pre_grid = k ? std::min(L.pre_blocks, 152 * k) : L.pre_blocks;
   L.sort_grid = 152 * (k ? k : 4);
+  L.tile_sort_sub = s->inst_capacity >= kWideTileSortMinCap ? 3 : 1;
+  L.tile_sort_grid = 152 * (k ? std::min(k, 3) : 3);
   L.emit_grid = std::max(1, std::min(L.chunk_cap, 152 * (k ? 2 * k : 8)));
   L.depth_blocks = (int32_t)((L.vis_cap + kDepthSortTile - 1) / kDepthSortTile);
   L.tile_blocks = (int32_t)((L.inst_cap + kInstSortTile - 1) / kInstSortTile);

@@ -21,6 +21,9 @@ constexpr int kDepthSortItems = 4;  // keys per thread per radix block of the de
 constexpr int kDepthSortTile = kSortThreads * kDepthSortItems;
 constexpr int kInstSortItems = 8;   // keys per thread per radix block of the instance (tile-id) sort
 constexpr int kInstSortTile = kSortThreads * kInstSortItems;
+// Instance capacity from which the instance sort takes three sub-tiles per
+// ticket (a third of the look-backs, fewer resident blocks).
+constexpr int64_t kWideTileSortMinCap = int64_t(1) << 26;
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;
@@ -121,6 +124,8 @@ struct Layout {
   int32_t emit_grid;      // persistent emission blocks
   int32_t pre_grid;       // persistent preprocess blocks
   int32_t sort_grid;      // persistent radix-pass blocks (at most; one radix tile each at least)
+  int32_t tile_sort_sub;  // sub-tiles of kInstSortTile keys per ticket of the instance sort (1 or 3)
+  int32_t tile_sort_grid; // persistent instance-sort blocks with 3 sub-tiles per ticket
   int32_t depth_blocks, tile_blocks;
   int32_t depth_passes, tile_passes;
   int32_t tile_bits;
@@ -144,12 +149,12 @@ __device__ __forceinline__ void grid_dependency_sync() {
 }
 
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
-                              Args... args) {
+inline cudaError_t launch_pdl_smem(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                                   cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -157,6 +162,21 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st,
+                              Args... args) {
+  return launch_pdl_smem(kernel, grid, block, 0, st, args...);
+}
+
+// Lets `kernel` take `bytes` of dynamic shared memory (above the 48 KB
+// default); set on the current device (a per-function attribute, not a
+// stream operation, so it may run while a stream is being captured).
+template <typename... KArgs>
+inline cudaError_t allow_dynamic_smem(void (*kernel)(KArgs...), size_t bytes) {
+  return cudaFuncSetAttribute(reinterpret_cast<const void *>(kernel), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes);
 }
 
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }

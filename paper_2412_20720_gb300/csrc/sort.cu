@@ -13,7 +13,7 @@
 // ceil(tile_bits / 8) times.
 //
 // Each radix pass is one kernel: blocks take tickets in launch order, rank
-// their 2048 keys stably with warp match, publish per-digit counts and find
+// their keys stably with warp ballots, publish per-digit counts and find
 // their per-digit global offsets by decoupled look-back over the earlier
 // tickets (bounded waits), then scatter through shared memory.
 #include <algorithm>
@@ -122,122 +122,197 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint32_t
   }
 }
 
-// One stable 8-bit LSD pass over radix tiles of kSortThreads x kItems keys.
-// Small sorts (the depth sort of the visible slots) take short tiles, so
-// that more SMs share a pass; the instance sort takes long ones.
+// 16-byte asynchronous copy global -> shared; bytes past src_bytes are
+// zero-filled and not read.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Waits until at most n (0..2) of this thread's copy groups are pending.
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  if (n <= 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  else if (n == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  else asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+}
+
+// Shared memory of one radix block: the ticket's keys and values (input,
+// then the block-local order), per-warp digit counts (two sets, alternating
+// between sub-tiles), per-sub-tile digit starts and the digits' global
+// starts.
+template <int kItems, int kSub>
+struct RadixSmem {
+  uint32_t keys[kSortThreads * kItems * kSub];
+  uint32_t vals[kSortThreads * kItems * kSub];
+  uint32_t wcount[kSub > 1 ? 2 : 1][kSortThreads / 32][kRadixBins];
+  uint32_t bstart[kSub][kRadixBins];  // first block-local position of each digit in sub-tile s
+  uint32_t sbase[kSub][kRadixBins];   // keys of each digit in the sub-tiles before s
+  uint32_t gstart[kRadixBins];        // global position of the ticket's first key of each digit
+  uint32_t scan[12];
+  uint32_t ticket;
+};
+template <int kItems, int kSub>
+constexpr size_t radix_smem_bytes() {
+  return sizeof(RadixSmem<kItems, kSub>);
+}
+
+// One stable 8-bit LSD pass.  A block takes tickets in launch order; a
+// ticket is kSub consecutive sub-tiles of kSortThreads x kItems keys.  Each
+// warp copies the keys (and values) it ranks into shared memory with
+// cp.async, one copy group per sub-tile, so later sub-tiles arrive while the
+// first is ranked.  Ranking is stable within a warp's segment (item-major,
+// lane-minor): the lanes holding the same digit are found by nine ballots
+// (eight digit bits and the padding bit), and the lowest of them adds the
+// group's size to the warp's count of that digit.  Each sub-tile is then
+// placed in block-local digit order in its own part of the buffer.  One
+// decoupled look-back per ticket gives the ticket's global start of each
+// digit, and the scatter writes each sub-tile's digit runs.  Small sorts
+// (the depth sort) take short sub-tiles, so that more SMs share a pass;
+// very large instance sorts take three sub-tiles per ticket, which divides
+// the look-backs per key by three.
 //
 // With `ranges` (the last pass of the tile sort, keys = global tile ids
 // below total_tiles) the pass also records each tile's [start, end) in the
-// sorted list.  A radix tile's staged keys are ordered by the full key (the
+// sorted list.  A sub-tile's staged keys are ordered by the full key (the
 // pass input is ordered by the lower digits and the staging is stable), so
-// the equal keys of a radix tile form one run; its first and last output
+// the equal keys of a sub-tile form one run; its first and last output
 // positions go to atomicMin on start and atomicMax on end, which the
 // emission initialised to (0xffffffff, 0).  A tile with no instance keeps
 // start > end, which every reader takes as empty.
-template <bool kValsAreIndex, int kItems>
+template <bool kValsAreIndex, int kItems, int kSub>
 __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
     uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ count_ptr, int64_t cap, int32_t shift,
     const uint32_t *__restrict__ hist, uint32_t *state, uint32_t *ticket, uint32_t *status, uint2 *ranges,
     int64_t total_tiles) {
+  static_assert(kSub >= 1 && kSub <= 3, "copy groups are waited for by count (at most 2 pending)");
+  static_assert(kItems % 4 == 0, "whole 16-byte copies per warp segment");
   grid_dependency_sync();
-  __shared__ uint32_t s_ticket;
-  __shared__ uint32_t s_wcount[kSortThreads / 32][kRadixBins];
-  __shared__ uint32_t s_bstart[kRadixBins];
-  __shared__ uint32_t s_gstart[kRadixBins];
-  __shared__ uint32_t s_scan[9];
-  constexpr int kTileKeys = kSortThreads * kItems;
-  __shared__ uint32_t s_keys[kTileKeys];
-  __shared__ uint32_t s_vals[kTileKeys];
-
-  const int64_t count = min64((int64_t)*count_ptr, cap);
-  // Persistent: tiles are taken by ticket, so a tile's look-back only waits
-  // on tiles that running blocks already hold.
-  while (true) {
-  if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
-  for (int d = threadIdx.x; d < (kSortThreads / 32) * kRadixBins; d += kSortThreads) (&s_wcount[0][0])[d] = 0u;
-  __syncthreads();
-  const int64_t b = s_ticket;
-  const int64_t tile0 = b * kTileKeys;
-  if (tile0 >= count) return;
-
+  constexpr int kSubKeys = kSortThreads * kItems;
+  constexpr int kTileKeys = kSubKeys * kSub;
+  constexpr int kWarps = kSortThreads / 32;
+  constexpr int kSegKeys = 32 * kItems;  // keys of one warp in a sub-tile
+  extern __shared__ __align__(16) unsigned char radix_smem[];
+  RadixSmem<kItems, kSub> &S = *reinterpret_cast<RadixSmem<kItems, kSub> *>(radix_smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  uint32_t key[kItems], val[kItems], rank[kItems];
-  int dig[kItems];
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    const int64_t idx = tile0 + warp * (32 * kItems) + k * 32 + lane;
-    if (idx < count) {
-      key[k] = keys_in[idx];
-      val[k] = kValsAreIndex ? (uint32_t)idx : vals_in[idx];
-      dig[k] = (key[k] >> shift) & (kRadixBins - 1);
-    } else {
-      key[k] = 0u;
-      val[k] = 0u;
-      dig[k] = kRadixBins;  // padding: ranked nowhere
-    }
-  }
-  // Stable rank within the warp's contiguous segment (item-major, lane-minor).
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    const int d = dig[k];
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t before = 0u;
-    if (d < kRadixBins) before = s_wcount[warp][d];
-    __syncwarp();
-    if (d < kRadixBins && lane == __ffs(peers) - 1) s_wcount[warp][d] = before + __popc(peers);
-    __syncwarp();
-    rank[k] = before + __popc(peers & lt_mask);
-  }
-  __syncthreads();
-  // Per digit: exclusive prefix over warps; block count.
-  const int d = threadIdx.x;
-  uint32_t cnt = 0u;
-#pragma unroll
-  for (int w = 0; w < kSortThreads / 32; ++w) {
-    const uint32_t c = s_wcount[w][d];
-    s_wcount[w][d] = cnt;
-    cnt += c;
-  }
+  const int64_t count = min64((int64_t)*count_ptr, cap);
+  for (int i = threadIdx.x; i < (int)(sizeof S.wcount / sizeof(uint32_t)); i += kSortThreads) (&S.wcount[0][0][0])[i] = 0u;
   uint32_t total;
-  s_bstart[d] = block_exclusive_scan(cnt, s_scan, &total);
-  const uint32_t gpre = block_exclusive_scan(hist[d], s_scan, &total);
-  const uint32_t prefix = radix_lookback(state, b, d, cnt, status);
-  s_gstart[d] = gpre + prefix;
-  __syncthreads();
-  // Block-local order through shared memory, then coalesced runs per digit.
+  // Keys of the digits below each digit over the whole input: the same for
+  // every ticket.
+  const uint32_t gpre = block_exclusive_scan(hist[threadIdx.x], S.scan, &total);
+  // Persistent: tickets are taken in order, so a ticket's look-back only
+  // waits on tickets that running blocks already hold.
+  while (true) {
+    if (threadIdx.x == 0) S.ticket = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t b = S.ticket;
+    const int64_t tile0 = b * kTileKeys;
+    if (tile0 >= count) return;
 #pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    if (dig[k] < kRadixBins) {
-      const uint32_t pos = s_bstart[dig[k]] + s_wcount[warp][dig[k]] + rank[k];
-      s_keys[pos] = key[k];
-      s_vals[pos] = val[k];
-    }
-  }
-  __syncthreads();
-  const int32_t nvalid = (int32_t)min64(kTileKeys, count - tile0);
-  for (int p = threadIdx.x; p < nvalid; p += kSortThreads) {
-    const uint32_t kk = s_keys[p];
-    const int dd = (kk >> shift) & (kRadixBins - 1);
-    const uint32_t gpos = s_gstart[dd] + ((uint32_t)p - s_bstart[dd]);
-    if ((int64_t)gpos < count) {
-      keys_out[gpos] = kk;
-      vals_out[gpos] = s_vals[p];
-      if (ranges) {
-        if ((int64_t)kk < total_tiles) {
-          uint32_t *r = reinterpret_cast<uint32_t *>(&ranges[kk]);
-          if (p == 0 || s_keys[p - 1] != kk) atomicMin(&r[0], gpos);
-          if (p == nvalid - 1 || s_keys[p + 1] != kk) atomicMax(&r[1], gpos + 1u);
-        } else {
-          atomicOr(status, kStatusInternal);
+    for (int s = 0; s < kSub; ++s) {
+      const int seg = s * kSubKeys + warp * kSegKeys;
+      for (int c = lane; c < kSegKeys / 4; c += 32) {
+        const int64_t i0 = tile0 + seg + 4 * c;
+        if (i0 < count) {
+          const int bytes = (int)min64(16, (count - i0) * 4);
+          cp_async16(&S.keys[seg + 4 * c], keys_in + i0, bytes);
+          if (!kValsAreIndex) cp_async16(&S.vals[seg + 4 * c], vals_in + i0, bytes);
         }
       }
-    } else {
-      atomicOr(status, kStatusInternal);
+      cp_async_commit();
     }
-  }
-  __syncthreads();  // shared memory is reused by the next tile
+    const int d = threadIdx.x;  // the digit this thread scans and looks back for
+    uint32_t tot = 0u;          // keys of digit d in the sub-tiles so far
+#pragma unroll
+    for (int s = 0; s < kSub; ++s) {
+      uint32_t(&wc)[kWarps][kRadixBins] = S.wcount[kSub > 1 ? (s & 1) : 0];
+      cp_async_wait_pending(kSub - 1 - s);
+      __syncwarp();  // the warp's copies of sub-tile s are visible to all its lanes
+      const int seg = s * kSubKeys + warp * kSegKeys;
+      uint32_t key[kItems], val[kItems], rank[kItems];
+      int dig[kItems];
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        const int li = seg + k * 32 + lane;
+        if (tile0 + li < count) {
+          key[k] = S.keys[li];
+          val[k] = kValsAreIndex ? (uint32_t)(tile0 + li) : S.vals[li];
+          dig[k] = (key[k] >> shift) & (kRadixBins - 1);
+        } else {
+          key[k] = 0u;
+          val[k] = 0u;
+          dig[k] = kRadixBins;  // padding: ranked nowhere
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        const int dk = dig[k];
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int bit = 0; bit < 9; ++bit) {
+          const uint32_t set = (uint32_t)((dk >> bit) & 1);
+          peers &= ~(__ballot_sync(0xffffffffu, set) ^ (0u - set));
+        }
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0u;
+        if (lane == leader && dk < kRadixBins) base = atomicAdd(&wc[warp][dk], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        __syncwarp();  // item k's counts land before item k + 1's
+        rank[k] = base + __popc(peers & lt_mask);
+      }
+      __syncthreads();
+      // Per digit: exclusive prefix over warps; sub-tile count and start.
+      uint32_t cnt = 0u;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = wc[w][d];
+        wc[w][d] = cnt;
+        cnt += c;
+      }
+      S.sbase[s][d] = tot;
+      tot += cnt;
+      S.bstart[s][d] = block_exclusive_scan(cnt, S.scan, &total);
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        if (dig[k] < kRadixBins) {
+          const uint32_t pos = s * kSubKeys + S.bstart[s][dig[k]] + wc[warp][dig[k]] + rank[k];
+          S.keys[pos] = key[k];
+          S.vals[pos] = val[k];
+        }
+      }
+      __syncwarp();
+      for (int i = lane; i < kRadixBins; i += 32) wc[warp][i] = 0u;  // the warp's row, for sub-tile s + 2
+    }
+    S.gstart[d] = gpre + radix_lookback(state, b, d, tot, status);
+    __syncthreads();
+    // Coalesced runs per digit and sub-tile.
+    const int32_t nvalid = (int32_t)min64(kTileKeys, count - tile0);
+    for (int p = threadIdx.x; p < nvalid; p += kSortThreads) {
+      const int s = p / kSubKeys, q = p - s * kSubKeys;
+      const uint32_t kk = S.keys[p];
+      const int dd = (kk >> shift) & (kRadixBins - 1);
+      const uint32_t gpos = S.gstart[dd] + S.sbase[s][dd] + ((uint32_t)q - S.bstart[s][dd]);
+      if ((int64_t)gpos < count) {
+        keys_out[gpos] = kk;
+        vals_out[gpos] = S.vals[p];
+        if (ranges) {
+          if ((int64_t)kk < total_tiles) {
+            const int qend = min(kSubKeys, nvalid - s * kSubKeys);
+            uint32_t *r = reinterpret_cast<uint32_t *>(&ranges[kk]);
+            if (q == 0 || S.keys[p - 1] != kk) atomicMin(&r[0], gpos);
+            if (q == qend - 1 || S.keys[p + 1] != kk) atomicMax(&r[1], gpos + 1u);
+          } else {
+            atomicOr(status, kStatusInternal);
+          }
+        }
+      } else {
+        atomicOr(status, kStatusInternal);
+      }
+    }
+    __syncthreads();  // shared memory is reused by the next ticket
   }
 }
 
@@ -690,6 +765,7 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
     if (L.depth_blocks > 0) {
       const int hb = std::min(L.depth_blocks, L.sort_grid);
       const int pb = std::min(L.depth_blocks, L.sort_grid);
+      constexpr size_t smem = radix_smem_bytes<kDepthSortItems, 1>();
       e = launch_pdl(radix_hist_kernel<kDepthSortItems>, (unsigned)hb, kSortThreads, st, dkey,
                      (const uint32_t *)(ctr + kCtrVisible), (int64_t)L.vis_cap, (int32_t)L.depth_passes, hist_d,
                      dstate, (int32_t)L.depth_blocks, (uint2 *)nullptr, (int64_t)0);
@@ -699,8 +775,9 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
         uint32_t *state = dstate + (size_t)p * L.depth_blocks * kRadixBins;
         const uint32_t *kin = p == 0 ? dkey : dk[in];
         const uint32_t *vin = p == 0 ? nullptr : dv[in];
-        e = launch_pdl(p == 0 ? radix_pass_kernel<true, kDepthSortItems> : radix_pass_kernel<false, kDepthSortItems>,
-                       (unsigned)pb, kSortThreads, st, kin, vin, dk[out], dv[out],
+        e = launch_pdl_smem(p == 0 ? radix_pass_kernel<true, kDepthSortItems, 1>
+                                   : radix_pass_kernel<false, kDepthSortItems, 1>,
+                            (unsigned)pb, kSortThreads, smem, st, kin, vin, dk[out], dv[out],
                        (const uint32_t *)(ctr + kCtrVisible), (int64_t)L.vis_cap, (int32_t)(kRadixBits * p),
                        (const uint32_t *)(hist_d + p * kRadixBins), state, ctr + kCtrTicketDepth + p, status,
                        (uint2 *)nullptr, (int64_t)0);
@@ -715,15 +792,26 @@ cudaError_t bin_sort_typed(const Layout &L, const fgs4d_view *views, int32_t nvi
   }
   // 3. Stable sort of the instances by global tile id (digit histograms
   // taken by the emission); the last pass also records the tile ranges.
-  const int pbt = std::min(L.tile_blocks, L.sort_grid);
+  // Very large instance lists take three sub-tiles per ticket (at most 3
+  // blocks of 73 KB per SM), the others one.
+  const bool wide = L.tile_sort_sub == 3;
+  const int tickets = (L.tile_blocks + L.tile_sort_sub - 1) / L.tile_sort_sub;
+  const int pbt = std::min(tickets, wide ? L.tile_sort_grid : L.sort_grid);
+  constexpr size_t smem1 = radix_smem_bytes<kInstSortItems, 1>(), smem3 = radix_smem_bytes<kInstSortItems, 3>();
+  if (wide) {
+    e = allow_dynamic_smem(radix_pass_kernel<false, kInstSortItems, 3>, smem3);
+    if (e != cudaSuccess) return e;
+  }
   for (int p = 0; p < L.tile_passes; ++p) {
     const int in = p & 1, out = in ^ 1;
     const bool last = p == L.tile_passes - 1;
     uint32_t *state = tstate + (size_t)p * L.tile_blocks * kRadixBins;
-    e = launch_pdl(radix_pass_kernel<false, kInstSortItems>, (unsigned)pbt, kSortThreads, st, (const uint32_t *)ik[in],
-                   (const uint32_t *)iv[in], ik[out], iv[out], (const uint32_t *)(ctr + kCtrInstances),
-                   (int64_t)L.inst_cap, (int32_t)(kRadixBits * p), (const uint32_t *)(hist_t + p * kRadixBins), state,
-                   ctr + kCtrTicketTile + p, status, last ? ranges : (uint2 *)nullptr, (int64_t)L.total_tiles);
+    e = launch_pdl_smem(wide ? radix_pass_kernel<false, kInstSortItems, 3> : radix_pass_kernel<false, kInstSortItems, 1>,
+                        (unsigned)pbt, kSortThreads, wide ? smem3 : smem1, st, (const uint32_t *)ik[in],
+                        (const uint32_t *)iv[in], ik[out], iv[out], (const uint32_t *)(ctr + kCtrInstances),
+                        (int64_t)L.inst_cap, (int32_t)(kRadixBits * p), (const uint32_t *)(hist_t + p * kRadixBins),
+                        state, ctr + kCtrTicketTile + p, status, last ? ranges : (uint2 *)nullptr,
+                        (int64_t)L.total_tiles);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -854,6 +942,7 @@ extern "C" int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, ui
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int blocks = (int)((n + kSortTile - 1) / kSortTile);
+  constexpr size_t smem = radix_smem_bytes<kSortItems, 1>();
   static_sort_init_kernel<<<1, 256, 0, st>>>(s, (uint32_t)n);
   radix_hist_kernel<kSortItems><<<blocks, kSortThreads, 0, st>>>(depth_keys, &s->ctl[0], FGS4D_STATIC_SORT_MAX,
                                                           kMaxPasses, &s->hist[0][0], &s->state[0][0][0],
@@ -863,11 +952,11 @@ extern "C" int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, ui
     const uint32_t *kin = p == 0 ? depth_keys : s->keys[in];
     uint32_t *vout = p == kMaxPasses - 1 ? sorted_slots : s->vals[out];
     if (p == 0)
-      radix_pass_kernel<true, kSortItems><<<blocks, kSortThreads, 0, st>>>(kin, nullptr, s->keys[out], vout, &s->ctl[0],
+      radix_pass_kernel<true, kSortItems, 1><<<blocks, kSortThreads, smem, st>>>(kin, nullptr, s->keys[out], vout, &s->ctl[0],
                                                                FGS4D_STATIC_SORT_MAX, kRadixBits * p, s->hist[p],
                                                                &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1], nullptr, 0);
     else
-      radix_pass_kernel<false, kSortItems><<<blocks, kSortThreads, 0, st>>>(kin, s->vals[in], s->keys[out], vout, &s->ctl[0],
+      radix_pass_kernel<false, kSortItems, 1><<<blocks, kSortThreads, smem, st>>>(kin, s->vals[in], s->keys[out], vout, &s->ctl[0],
                                                                 FGS4D_STATIC_SORT_MAX, kRadixBits * p, s->hist[p],
                                                                 &s->state[p][0][0], &s->ctl[8 + p], &s->ctl[1], nullptr, 0);
   }

@@ -269,10 +269,14 @@ def _read_instances(r, m, ntiles):
 
 
 # Visible capacities equal to the slot count and well above it (the pair scan
-# and depth sort size their grids and look-back rows by the capacity).
-@pytest.mark.parametrize("n,W,H,vis_cap", [(1, 16, 16, 0), (2047, 144, 112, 0), (70_001, 1352, 1014, 0),
-                                           (70_001, 1352, 1014, 400_000), (150_001, 1352, 1014, 0)])
-def test_bin_sort_bit_exact_on_synthetic_records(n, W, H, vis_cap):
+# and depth sort size their grids and look-back rows by the capacity); an
+# instance capacity of 2^26 takes the instance sort with three sub-tiles per
+# ticket.
+@pytest.mark.parametrize("n,W,H,vis_cap,inst_cap", [(1, 16, 16, 0, 0), (2047, 144, 112, 0, 0),
+                                                    (70_001, 1352, 1014, 0, 0), (70_001, 1352, 1014, 400_000, 0),
+                                                    (150_001, 1352, 1014, 0, 0), (2047, 144, 112, 0, 1 << 26),
+                                                    (150_001, 1352, 1014, 0, 1 << 26)])
+def test_bin_sort_bit_exact_on_synthetic_records(n, W, H, vis_cap, inst_cap):
     """With ellipses that meet every tile, the sorted instance list and tile
     ranges equal the oracle's bit for bit: one instance per tile of each
     rect, ordered by (tile, FP32 depth, slot), on records written straight
@@ -282,7 +286,7 @@ def test_bin_sort_bit_exact_on_synthetic_records(n, W, H, vis_cap):
     rng = np.random.default_rng(n)
     gw, gh = (W + 15) // 16, (H + 15) // 16
     rec = _synthetic_records(rng, n, W, H, 6, tau=KEEP_ALL)
-    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=40 * n + 16, vis_capacity=vis_cap)
+    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=inst_cap or 40 * n + 16, vis_capacity=vis_cap)
     r = Renderer(n, [sy.tiny_view(W, H)], cfg)
     _write_records(r, rec, 0)
     fgs4d.bin_sort(n, r.views, r.nviews, r.settings, r.ws.data_ptr(), r.ws_bytes, r.stream())

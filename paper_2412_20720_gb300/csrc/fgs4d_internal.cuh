@@ -183,25 +183,10 @@ __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return
 __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
-  uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Relaxed (non-ordering) accesses for look-back words whose flag and value
-// share one word: a reader needs only that word, so no fence is implied.
+// share one word: a reader needs only that word, and no block reads data
+// that another block of the same launch published beside it, so no
+// acquire / release ordering is needed.
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
   uint32_t v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -209,6 +194,14 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
 }
 __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint64_t *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // Decoupled look-back over uint64 block states (flag in bits 62-63: 1 =
@@ -219,15 +212,15 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
 __device__ __forceinline__ uint64_t lookback_u64(uint64_t *state, int32_t bid, uint64_t agg, uint32_t *status) {
   constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kMask = (1ull << 62) - 1;
   if (bid == 0) {
-    st_release(&state[0], kInc | agg);
+    st_relaxed(&state[0], kInc | agg);
     return 0;
   }
-  st_release(&state[bid], kAgg | agg);
+  st_relaxed(&state[bid], kAgg | agg);
   uint64_t prefix = 0;
   int32_t j = bid - 1;
   uint32_t polls = 0;
   while (j >= 0) {
-    const uint64_t s = ld_acquire(&state[j]);
+    const uint64_t s = ld_relaxed(&state[j]);
     const uint64_t f = s & ~kMask;
     if (f == 0) {
       if (++polls > kSpinLimit) {
@@ -241,7 +234,7 @@ __device__ __forceinline__ uint64_t lookback_u64(uint64_t *state, int32_t bid, u
     if (f == kInc) break;
     --j;
   }
-  st_release(&state[bid], kInc | (prefix + agg));
+  st_relaxed(&state[bid], kInc | (prefix + agg));
   return prefix;
 }
 
@@ -254,16 +247,16 @@ __device__ __forceinline__ uint64_t lookback_u64_warp(uint64_t *state, int32_t b
   constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kMask = (1ull << 62) - 1;
   const int lane = threadIdx.x & 31;
   if (bid == 0) {
-    if (lane == 0) st_release(&state[0], kInc | agg);
+    if (lane == 0) st_relaxed(&state[0], kInc | agg);
     return 0;
   }
-  if (lane == 0) st_release(&state[bid], kAgg | agg);
+  if (lane == 0) st_relaxed(&state[bid], kAgg | agg);
   uint64_t prefix = 0;
   int32_t window = bid - 1;
   uint32_t polls = 0;
   while (true) {
     const int32_t j = window - lane;
-    const uint64_t s = j >= 0 ? ld_acquire(&state[j]) : kInc;  // before block 0: inclusive 0
+    const uint64_t s = j >= 0 ? ld_relaxed(&state[j]) : kInc;  // before block 0: inclusive 0
     const uint64_t f = s & ~kMask;
     const uint32_t not_ready = __ballot_sync(0xffffffffu, f == 0);
     const uint32_t inc = __ballot_sync(0xffffffffu, f == kInc);
@@ -284,7 +277,7 @@ __device__ __forceinline__ uint64_t lookback_u64_warp(uint64_t *state, int32_t b
     if (first < 32) break;  // reached an inclusive prefix
     window -= 32;
   }
-  if (lane == 0) st_release(&state[bid], kInc | (prefix + agg));
+  if (lane == 0) st_relaxed(&state[bid], kInc | (prefix + agg));
   return prefix;
 }
 

@@ -118,13 +118,15 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_kernel(F
   const uint2 range = tile_range(A.ranges, gt);
   const float pxc = (float)px + 0.5f;
   if (threadIdx.x < D) s_gate[threadIdx.x] = A.gate ? A.gate[threadIdx.x] : 1.0f;
-  float T[kFeatPPT], pyc[kFeatPPT], F[kFeatPPT][D];
+  static_assert(kFeatPPT <= 4, "a strip inside one row group");
+  const float gyc = row_group_centre(py0);
+  float T[kFeatPPT], off[kFeatPPT], F[kFeatPPT][D];
   bool live = false;
 #pragma unroll
   for (int k = 0; k < kFeatPPT; ++k) {
     const bool in = px < V.width && py0 + k < V.height;
     T[k] = in ? 1.0f : -1.0f;
-    pyc[k] = in ? (float)(py0 + k) + 0.5f : stopped_row();
+    off[k] = in ? row_offset(py0 + k) : stopped_offset();
 #pragma unroll
     for (int c = 0; c < D; ++c) F[k][c] = 0.f;
     live = live || in;
@@ -139,16 +141,17 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_kernel(F
       const float4 geom = s_geom[j];
       const float2 ca = s_ca[j];
       const ColumnTerms ct = column_terms(geom, pxc, ca.y);
+      const float w4 = group_w(ct, geom.y, ca.x, gyc);
       const bool clamp = entry_clamps(ca.y);
 #pragma unroll
       for (int k = 0; k < kFeatPPT; ++k) {
-        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, pyc[k], clamp);
-        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
+        const AlphaEval e = pixel_alpha(ct, w4, ca.x, off[k], clamp);
+        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row offset +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
           const float Tn = __fsub_rn(T[k], w);
           if (Tn < kTMin) {
             T[k] = -T[k];
-            pyc[k] = stopped_row();
+            off[k] = stopped_offset();
           } else {
 #pragma unroll
             for (int c = 0; c < D; ++c) F[k][c] = __fmaf_rn(s_fhat[j * (D + 1) + c], w, F[k][c]);
@@ -216,13 +219,14 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
   }
   const int64_t HW = (int64_t)V.width * V.height;
   const float *dF = A.dL_dF + V.pix_base * D;
-  float T[kFeatPPT], pyc[kFeatPPT], G[kFeatPPT][D];
+  const float gyc = row_group_centre(py0);
+  float T[kFeatPPT], off[kFeatPPT], G[kFeatPPT][D];
   bool live = false;
 #pragma unroll
   for (int k = 0; k < kFeatPPT; ++k) {
     const bool in = px < V.width && py0 + k < V.height;
     T[k] = in ? 1.0f : -1.0f;
-    pyc[k] = in ? (float)(py0 + k) + 0.5f : stopped_row();
+    off[k] = in ? row_offset(py0 + k) : stopped_offset();
     const int64_t p = (int64_t)(py0 + k) * V.width + px;
 #pragma unroll
     for (int c = 0; c < D; ++c) G[k][c] = in ? dF[c * HW + p] : 0.f;
@@ -239,6 +243,7 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
       const float4 geom = s_geom[j];
       const float2 ca = s_ca[j];
       const ColumnTerms ct = column_terms(geom, pxc, ca.y);
+      const float w4 = group_w(ct, geom.y, ca.x, gyc);
       const bool clamp = entry_clamps(ca.y);
       float v[32];
 #pragma unroll
@@ -246,13 +251,13 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
       bool contrib = false;
 #pragma unroll
       for (int k = 0; k < kFeatPPT; ++k) {
-        const AlphaEval e = pixel_alpha(ct, geom.y, ca.x, pyc[k], clamp);
-        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
+        const AlphaEval e = pixel_alpha(ct, w4, ca.x, off[k], clamp);
+        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row offset +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
           const float Tn = __fsub_rn(T[k], w);
           if (Tn < kTMin) {
             T[k] = -T[k];
-            pyc[k] = stopped_row();
+            off[k] = stopped_offset();
           } else {
             contrib = true;
 #pragma unroll

@@ -345,8 +345,20 @@ __device__ __forceinline__ ColumnTerms column_terms(float4 geom, float pxc, floa
   return c;
 }
 
+// Pixel rows are taken in groups of four (rows 4m .. 4m + 3).  At row y the
+// second factor w = b2 (v - (y + 0.5)) + b1 dx is evaluated as
+// fma(b2, -(y mod 4), w4) from the group's w4 = fma(b2, v - (4m + 0.5), b1 dx):
+// one FFMA per pixel once w4 is formed per entry, and the same rounding for
+// a pixel whatever the block's strip shape, so every compositor (forward,
+// backward, features) takes the same alpha bit for bit.
+__device__ __forceinline__ float row_group_centre(int32_t y) { return (float)(y & ~3) + 0.5f; }
+__device__ __forceinline__ float row_offset(int32_t y) { return -(float)(y & 3); }
+__device__ __forceinline__ float group_w(const ColumnTerms &c, float v, float b2, float gyc) {
+  return __fmaf_rn(b2, __fsub_rn(v, gyc), c.bdx);
+}
+
 struct AlphaEval {
-  float dy, aG, alpha;  // aG = a 2^-q before the 0.99 clamp
+  float aG, alpha;  // aG = a 2^-q before the 0.99 clamp
 };
 
 // min(x, y) that returns NaN when either operand is NaN (fminf returns the
@@ -358,9 +370,10 @@ __device__ __forceinline__ float min_nan(float x, float y) {
 }
 
 // A pixel that has stopped (or lies outside the image) is given the row
-// centre +inf: dy = -inf makes q = +inf (or NaN when b2 = 0), so alpha is 0
-// (or NaN) and fails the 1/255 test without a separate per-pixel flag test.
-__device__ __forceinline__ float stopped_row() { return __int_as_float(0x7f800000); }
+// offset +inf: w = +inf (or NaN when b2 = 0) makes q = +inf (or NaN), so
+// alpha is 0 (or NaN) and fails the 1/255 test without a separate per-pixel
+// flag test.
+__device__ __forceinline__ float stopped_offset() { return __int_as_float(0x7f800000); }
 
 // alpha = min(0.99, a 2^-q).  The clamp can only act for a > 0.98: with
 // q >= 0 (a positive definite form, up to rounding) a 2^-q stays below 0.99
@@ -370,19 +383,19 @@ __device__ __forceinline__ float stopped_row() { return __int_as_float(0x7f80000
 constexpr float kLog2NoClamp = -0.0291463f;  // log2(0.98)
 __device__ __forceinline__ bool entry_clamps(float la) { return la > kLog2NoClamp; }
 
-// b2: color.x of the record; alpha = a 2^-q with q the sum of two squares.
+// w4: group_w of the pixel's row group; off: row_offset of its row (or
+// stopped_offset); b2: color.x of the record.
 template <bool kClamp>
-__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float b2, float pyc) {
+__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float w4, float b2, float off) {
   AlphaEval e;
-  e.dy = __fsub_rn(v, pyc);
-  const float w = __fmaf_rn(b2, e.dy, c.bdx);
+  const float w = __fmaf_rn(b2, off, w4);
   e.aG = ex2_approx(-__fmaf_rn(w, w, c.adx2));
   e.alpha = kClamp ? min_nan(0.99f, e.aG) : e.aG;
   return e;
 }
 
-__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float v, float b2, float pyc, bool clamp) {
-  return clamp ? pixel_alpha<true>(c, v, b2, pyc) : pixel_alpha<false>(c, v, b2, pyc);
+__device__ __forceinline__ AlphaEval pixel_alpha(const ColumnTerms &c, float w4, float b2, float off, bool clamp) {
+  return clamp ? pixel_alpha<true>(c, w4, b2, off) : pixel_alpha<false>(c, w4, b2, off);
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;

@@ -104,7 +104,7 @@ __device__ __forceinline__ void stage_batch(const uint32_t *inst_val, const floa
 // algorithmic work; 2 (kAux): also blends the per-slot depth and flow with
 // the colour weights and writes depth, opacity 1 - T and flow planes.
 // A pixel that has stopped is marked by a negative T (its final transmittance
-// negated; a live pixel always has T >= 1e-4) and by the row centre +inf,
+// negated; a live pixel always has T >= 1e-4) and by the row offset +inf,
 // which makes every later alpha fail the 1/255 test, so the inner loop tests
 // no flag.  The update stays a branch: whole warps skip it for entries that
 // miss all their pixels.
@@ -135,7 +135,13 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
   const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * PPT;
   const uint2 range = tile_range(A.ranges, gt);
   const float pxc = (float)px + 0.5f;
-  float T[PPT], C0[PPT], C1[PPT], C2[PPT], pyc[PPT];
+  // Row groups of the strip (one for strips of up to 4 rows, which never
+  // straddle a group; PPT / 4 otherwise) and each pixel's row offset.
+  constexpr int kGroups = (PPT + 3) / 4;
+  float gyc[kGroups];
+#pragma unroll
+  for (int g = 0; g < kGroups; ++g) gyc[g] = row_group_centre(py0 + 4 * g);
+  float T[PPT], C0[PPT], C1[PPT], C2[PPT], off[PPT];
   float X0[kAux ? PPT : 1], X1[kAux ? PPT : 1], X2[kAux ? PPT : 1];  // depth, flow_u, flow_v sums
   uint32_t last[PPT];
   uint32_t pend[kStats ? PPT : 1];  // evaluations since the pixel's last composited entry
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
     C0[k] = C1[k] = C2[k] = 0.f;
     if (kAux) X0[k] = X1[k] = X2[k] = 0.f;
     last[k] = 0u;
-    pyc[k] = in ? (float)(py0 + k) + 0.5f : stopped_row();
+    off[k] = in ? row_offset(py0 + k) : stopped_offset();
     nlive += in;
   }
   uint32_t n_eval = 0u, n_comp = 0u, n_evb = 0u;
@@ -175,19 +181,22 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
       const float4 col = s_col[j];
       const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc, col.y);
+      float w4[kGroups];
+#pragma unroll
+      for (int g = 0; g < kGroups; ++g) w4[g] = group_w(ct, geom.y, col.x, gyc[g]);
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        const AlphaEval e = pixel_alpha<decltype(clamp_tag)::value>(ct, geom.y, col.x, pyc[k]);
+        const AlphaEval e = pixel_alpha<decltype(clamp_tag)::value>(ct, w4[k >> 2], col.x, off[k]);
         if (kStats) {
           n_eval += T[k] > 0.0f;
           pend[k] += T[k] > 0.0f;
         }
-        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row +inf)
+        if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row offset +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
           const float Tn = __fsub_rn(T[k], w);
           if (Tn < kTMin) {
             T[k] = -T[k];
-            pyc[k] = stopped_row();
+            off[k] = stopped_offset();
             --nlive;
           } else {
             C0[k] = __fmaf_rn(col.z, w, C0[k]);
@@ -218,7 +227,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
     } else {
       // No entry of the batch can clamp: two entries per iteration, the
       // liveness test once per pair (a pixel that stopped at the first
-      // takes no alpha from the second: its row is +inf).
+      // takes no alpha from the second: its row offset is +inf).
       int j = 0;
       for (; j + 1 < nb && nlive > 0; j += 2) {
         entry(j, std::false_type());
@@ -324,14 +333,18 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
   // Dr[k] = sum over channels of dL/dX * (X composited behind the current
   // entry), X = R, G, B (and depth, opacity): the "behind" terms of
   // dL/dalpha enter only through this sum, which grows by w * (dL/dX . x_i).
-  float T[kPPT], dC0[kPPT], dC1[kPPT], dC2[kPPT], Dr[kPPT], pyc[kPPT];
+  constexpr int kGroups = (kPPT + 3) / 4;  // row groups of the strip (see group_w)
+  float gyc[kGroups];
+#pragma unroll
+  for (int g = 0; g < kGroups; ++g) gyc[g] = row_group_centre(py0 + 4 * g);
+  float T[kPPT], dC0[kPPT], dC1[kPPT], dC2[kPPT], Dr[kPPT], off[kPPT];
   float dD[kAux ? kPPT : 1], dO[kAux ? kPPT : 1];
   uint32_t last[kPPT];
   uint32_t my_max = 0u;
   const float *g = A.dL_drgb + V.pix_base * 3;
 #pragma unroll
   for (int k = 0; k < kPPT; ++k) {
-    pyc[k] = (float)(py0 + k) + 0.5f;
+    off[k] = row_offset(py0 + k);
     T[k] = 1.0f;
     dC0[k] = dC1[k] = dC2[k] = 0.f;
     last[k] = 0u;
@@ -378,6 +391,13 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
       const float4 col = s_col[j];
       const float blue = s_blue[j];
       const ColumnTerms ct = column_terms(geom, pxc, col.y);
+      // group_w, keeping v - (group row centre) for the pixels' dy
+      float dy4[kGroups], w4[kGroups];
+#pragma unroll
+      for (int g = 0; g < kGroups; ++g) {
+        dy4[g] = __fsub_rn(geom.y, gyc[g]);
+        w4[g] = __fmaf_rn(col.x, dy4[g], ct.bdx);
+      }
       // The conic and centre gradients of the strip share dx: accumulate the
       // moments S0 = sum gp, S1 = sum gp dy, S2 = sum gp dy^2 of
       // gp = dL/d(natural-log power) and form the five sums once per entry.
@@ -389,7 +409,7 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
         if (pos >= last[k]) continue;
-        const AlphaEval e = pixel_alpha<kClamp>(ct, geom.y, col.x, pyc[k]);
+        const AlphaEval e = pixel_alpha<kClamp>(ct, w4[k >> 2], col.x, off[k]);
         if (!(e.alpha >= kAlphaMin)) continue;  // the forward's skip decision, NaN included
         contrib = true;
         const float io = rcp_approx(__fsub_rn(1.0f, e.alpha));
@@ -407,10 +427,11 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
         Dr[k] += w * Dc;
         if (!(kClamp && e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
           const float gp = g_alpha * e.alpha;  // d alpha / d (natural-log power)
-          const float gpy = gp * e.dy;
+          const float dy = dy4[k >> 2] + off[k];  // v - pixel row centre
+          const float gpy = gp * dy;
           S0 += gp;
           S1 += gpy;
-          S2 += gpy * e.dy;
+          S2 += gpy * dy;
         }
       }
       if (!__any_sync(0xffffffffu, contrib)) return;

@@ -337,6 +337,9 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
   float gyc[kGroups];
 #pragma unroll
   for (int g = 0; g < kGroups; ++g) gyc[g] = row_group_centre(py0 + 4 * g);
+  // Row offsets of the strip's pixels within their groups: -(k mod 4) when
+  // the strip starts a group (4 and 8 rows), else -((py0 + k) mod 4).
+  const float base_off = row_offset(py0);
   float T[kPPT], dC0[kPPT], dC1[kPPT], dC2[kPPT], Dr[kPPT], off[kPPT];
   float dD[kAux ? kPPT : 1], dO[kAux ? kPPT : 1];
   uint32_t last[kPPT];
@@ -403,13 +406,20 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
       // gp = dL/d(natural-log power) and form the five sums once per entry.
       // A pixel that is not skipped has alpha = a 2^-q (below the clamp), so
       // gp = g_alpha a 2^-q is also the opacity term: dL/da = S0 / a.
-      float S0 = 0.f, S1 = 0.f, S2 = 0.f, gr = 0.f, gg = 0.f, gb = 0.f, gz = 0.f;
+      // Per row group: P0 = sum gp, P1 = sum o gp, P2 = sum o^2 gp with the
+      // pixel's dy = dyb - o, o = k mod 4 (a constant of the unrolled loop),
+      // so that S1 = dyb P0 - P1 and S2 = dyb^2 P0 - 2 dyb P1 + P2 follow
+      // once per entry.
+      float P0[kGroups], P1[kGroups], P2[kGroups];
+#pragma unroll
+      for (int g = 0; g < kGroups; ++g) P0[g] = P1[g] = P2[g] = 0.f;
+      float gr = 0.f, gg = 0.f, gb = 0.f, gz = 0.f;
       const float zj = kAux ? s_aux[j].x : 0.f;
       bool contrib = false;
 #pragma unroll
       for (int k = 0; k < kPPT; ++k) {
         if (pos >= last[k]) continue;
-        const AlphaEval e = pixel_alpha<kClamp>(ct, w4[k >> 2], col.x, off[k]);
+        const AlphaEval e = pixel_alpha<kClamp>(ct, w4[k >> 2], col.x, kPPT >= 4 ? -(float)(k & 3) : off[k]);
         if (!(e.alpha >= kAlphaMin)) continue;  // the forward's skip decision, NaN included
         contrib = true;
         const float io = rcp_approx(__fsub_rn(1.0f, e.alpha));
@@ -427,14 +437,24 @@ __global__ void __launch_bounds__(TILE *TILE / kPPT) render_bwd_kernel(RenderBwd
         Dr[k] += w * Dc;
         if (!(kClamp && e.aG > 0.99f)) {  // min(0.99, .) is locally constant when clamped
           const float gp = g_alpha * e.alpha;  // d alpha / d (natural-log power)
-          const float dy = dy4[k >> 2] + off[k];  // v - pixel row centre
-          const float gpy = gp * dy;
-          S0 += gp;
-          S1 += gpy;
-          S2 += gpy * dy;
+          const float o = (float)(k & 3);
+          P0[k >> 2] += gp;
+          if (k & 3) {
+            P1[k >> 2] = __fmaf_rn(o, gp, P1[k >> 2]);
+            P2[k >> 2] = __fmaf_rn(o * o, gp, P2[k >> 2]);
+          }
         }
       }
       if (!__any_sync(0xffffffffu, contrib)) return;
+      // the strip's moments S0 = sum gp, S1 = sum gp dy, S2 = sum gp dy^2
+      float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+#pragma unroll
+      for (int g = 0; g < kGroups; ++g) {
+        const float dyb = dy4[g] + base_off;  // dy of the group's first row in the strip
+        S0 += P0[g];
+        S1 += dyb * P0[g] - P1[g];
+        S2 += dyb * (dyb * P0[g] - 2.0f * P1[g]) + P2[g];
+      }
       const float dx = ct.dx;
       // the natural-log conic (A, B, C) of the record's factors: A' = a1^2 +
       // b1^2, B' = 2 b1 b2, C' = b2^2 in base 2

@@ -66,7 +66,7 @@ def to_device(params: dict):
     return {k: torch.from_numpy(np.ascontiguousarray(params[k], dtype=np.float32)).cuda() for k in PARAM_KEYS}
 
 
-class GpuRun:
+class CudaRender:
     """One forward through the C ABI, with the documented workspace regions
     read back."""
 
@@ -113,7 +113,7 @@ class GpuRun:
         return {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}, slot
 
 
-def records_from_gpu(run: GpuRun):
+def records_from_gpu(run: CudaRender):
     """Decode the GPU's per-slot records into oracle units.  The record
     holds the base-2 exponent's factors (a1, b1, b2): q2 = (a1 dx)^2 + (b1 dx
     + b2 dy)^2 = (1/2) log2(e) d^T Q d; "factor" is (u11, u12, u22) of the

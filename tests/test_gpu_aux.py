@@ -82,7 +82,7 @@ def test_depth_and_opacity_gradients_match_oracle(L, NT):
     per-parameter gradients against the oracle's adjoint (pinned by central
     differences on the CPU)."""
     import torch
-    from helpers import compare_group, records_from_gpu, GpuRun
+    from helpers import compare_group, records_from_gpu, CudaRender
     from paper_2412_20720_gb300.render import PARAM_KEYS
     params, views, cfg = case(96, 80, L, NT, seed=6)
     view = views[0]
@@ -97,7 +97,7 @@ def test_depth_and_opacity_gradients_match_oracle(L, NT):
     daux[:2] = loss_gradient_at_settled_pixels(rng, flags, (2,) + flags.shape)
     g_orc = oracle.render_aux_backward(params, pr, view, st, dimg, daux)
 
-    run = GpuRun(params, views, cfg)  # records for the slot order
+    run = CudaRender(params, views, cfg)  # records for the slot order
     r = run.renderer
     r.forward_aux(run.params, 0.05)
     grads = {k: torch.zeros_like(v) for k, v in run.params.items()}

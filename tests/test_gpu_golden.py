@@ -8,7 +8,7 @@ import sys
 import numpy as np
 import pytest
 
-from helpers import IMAGE_ATOL, GpuRun
+from helpers import IMAGE_ATOL, CudaRender
 
 sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
 import make_golden  # noqa: E402
@@ -20,7 +20,7 @@ def test_tiny_render_matches_the_stored_oracle_values():
     g = make_golden.read()
     params, view, cfg = make_golden.tiny_scene_inputs()
     assert params["mean"].shape[0] == g["kept"]
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     py, px = g["py"], g["px"]
     got = np.concatenate([run.images[0][:, py, px], run.T.reshape(view["height"], view["width"])[py, px][None]]).T
     plain = np.concatenate([g["rgb"], g["T"][:, None]], axis=1)

@@ -16,7 +16,7 @@ from paper_2412_20720_gb300 import fgs4d
 from paper_2412_20720_gb300 import synthetic as sy
 from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig
 
-from helpers import (GpuRun, canonical_ranges, check_image, check_pixels, check_records, compare_group,
+from helpers import (CudaRender, canonical_ranges, check_image, check_pixels, check_records, compare_group,
                      loss_gradient_at_settled_pixels, oracle_proj, oracle_settings, pixel_tolerance, records_from_gpu,
                      subset)
 
@@ -34,7 +34,7 @@ def tiny_case(width=128, height=96, L=1, NT=1, bg=(0.0, 0.0, 0.0), seed=0, n=200
 
 def test_preprocess_records_match_oracle():
     params, view, cfg = tiny_case()
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     check_records(run, params, view, cfg)
 
 
@@ -44,7 +44,7 @@ def test_preprocess_records_match_oracle():
                                          (17, 33, 0, 4, (0.0, 0.3, 0.0))])
 def test_image_matches_oracle(w, h, L, NT, bg):
     params, view, cfg = tiny_case(w, h, L, NT, bg)
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     check_records(run, params, view, cfg)
     check_image(run, params, view, cfg)
 
@@ -67,7 +67,7 @@ def test_opaque_gaussians_reach_the_clamp():
     params, view, cfg = _opaque_case()
     pr = oracle.preprocess(params, view, oracle_settings(cfg))
     assert (pr["a_eff"][pr["status"] == 0] > 0.99).sum() >= 20
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     check_image(run, params, view, cfg)
     check_gradients(*_grad_case(params, view, cfg))
 
@@ -81,7 +81,7 @@ def test_full_size_orbit_view_sampled():
     view = sy.orbit_view(37)
     cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 23)
     params = sc.as_dict()
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     rng = np.random.default_rng(7)
     nv = run.counts[0]
     assert nv > 50_000
@@ -104,9 +104,9 @@ def test_batched_views_equal_single_views():
              sy.look_at((-2.0, 0.3, 2.0), (0, 0, 0), (0, -1, 0), 64, 64, 0.55)]
     cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 19, bg=(0.1, 0.0, 0.2))
     params = sc.as_dict()
-    batch = GpuRun(params, views, cfg)
+    batch = CudaRender(params, views, cfg)
     for k, v in enumerate(views):
-        single = GpuRun(params, [v], cfg)
+        single = CudaRender(params, [v], cfg)
         np.testing.assert_array_equal(batch.images[k], single.images[0])
         check_records(batch, params, v, cfg, k)
         check_image(batch, params, v, cfg, k)
@@ -140,7 +140,7 @@ def test_single_pixel_and_one_pixel_wide_views(tile):
              _crop(sy.tiny_view(128, 96, t=0.3), 0, 0, 128, 96)]
     cfg = RenderConfig(sh_degree=2, t_order=1, inst_capacity=1 << 18, bg=(0.3, 0.2, 0.1), tile=tile)
     params = sc.as_dict()
-    run = GpuRun(params, views, cfg)
+    run = CudaRender(params, views, cfg)
     _check_views_against_oracle(run, params, views, cfg)
 
 
@@ -158,10 +158,10 @@ def test_maximum_view_count_in_one_call():
                                 (0, -1, 0), w, h, k / (fgs4d.MAX_VIEWS - 1), hfov_deg=15.0))
     cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=1 << 20, bg=(0.0, 0.1, 0.0))
     params = sc.as_dict()
-    run = GpuRun(params, views, cfg)
+    run = CudaRender(params, views, cfg)
     _check_views_against_oracle(run, params, views, cfg)
     for k in (0, fgs4d.MAX_VIEWS - 1):
-        np.testing.assert_array_equal(run.images[k], GpuRun(params, [views[k]], cfg).images[0])
+        np.testing.assert_array_equal(run.images[k], CudaRender(params, [views[k]], cfg).images[0])
 
 
 def test_block_shapes_render_identically():
@@ -174,7 +174,7 @@ def test_block_shapes_render_identically():
     runs = []
     for p, b in ((2, 256), (4, 256), (8, 256), (4, 128), (2, 128)):  # shapes and shared batch sizes
         c = RenderConfig(**{**cfg.__dict__, "pixels_per_thread": p, "shared_batch": b})
-        run = GpuRun(params, [view], c)
+        run = CudaRender(params, [view], c)
         runs.append((run, run.backward([dimg])[0]))
     for run, g in runs[1:]:
         np.testing.assert_array_equal(run.images[0], runs[0][0].images[0])
@@ -464,7 +464,7 @@ def test_instance_list_is_the_rect_membership_minus_skipped_pairs():
     """The instance list of a rendered scene against the tile rasterizer's
     rect membership, with no reference to the kernel's own cull test."""
     params, view, cfg = tiny_case(131, 77, 1, 1)
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     assert check_instance_list(run, params, view, cfg) > 100
 
 
@@ -473,7 +473,7 @@ def test_instance_list_at_tile_8_and_several_views():
     views = [sy.tiny_view(96, 80, t=0.4), sy.look_at((1.5, -0.5, -2.5), (0, 0, 0), (0, -1, 0), 100, 70, 0.6)]
     cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=1 << 19, tile=8)
     params = sc.as_dict()
-    run = GpuRun(params, views, cfg)
+    run = CudaRender(params, views, cfg)
     for k, v in enumerate(views):
         assert check_instance_list(run, params, v, cfg, k) > 100
 
@@ -485,7 +485,7 @@ def test_instance_list_full_size_sampled_tiles():
     view = sy.orbit_view(120)
     cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 23)
     params = sc.as_dict()
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     rng = np.random.default_rng(17)
     tiles = rng.choice(85 * 64, 150, replace=False)
     assert check_instance_list(run, params, view, cfg, 0, tiles_to_check=tiles) > 1000
@@ -497,7 +497,7 @@ def test_empty_scene_renders_background():
     view = sy.tiny_view(50, 30)
     cfg = RenderConfig(sh_degree=1, t_order=1, bg=(0.25, 0.5, 0.75), inst_capacity=1024)
     empty = {k: v[:0] for k, v in sy.tiny_scene().as_dict().items()}
-    run = GpuRun(empty, [view], cfg)
+    run = CudaRender(empty, [view], cfg)
     assert run.counts[:2] == [0, 0]
     for ch, b in enumerate(cfg.bg):
         assert np.all(run.images[0][ch] == np.float32(b))
@@ -509,14 +509,14 @@ def test_all_temporally_culled_renders_background():
     sc["mean"][:, 3] = 50.0  # far from t = 0.5 for every temporal scale
     view = sy.tiny_view(64, 48)
     cfg = RenderConfig(sh_degree=1, t_order=1, bg=(0.3, 0.3, 0.3), inst_capacity=1024)
-    run = GpuRun(sc, [view], cfg)
+    run = CudaRender(sc, [view], cfg)
     assert run.counts[0] == 0
     assert np.all(run.images[0] == np.float32(0.3))
 
 
 def test_non_finite_parameters_are_culled_not_propagated():
     params, view, cfg = tiny_case(n=1500)
-    clean = GpuRun(params, [view], cfg)
+    clean = CudaRender(params, [view], cfg)
     bad = {k: v.copy() for k, v in params.items()}
     n = bad["mean"].shape[0]
     rng = np.random.default_rng(3)
@@ -531,15 +531,15 @@ def test_non_finite_parameters_are_culled_not_propagated():
     bad["q_l"][idx[0]] = 0.0  # zero quaternion: invalid
     keep = np.ones(n, bool)
     keep[idx] = False
-    poisoned = GpuRun(bad, [view], cfg)
-    removed = GpuRun(subset(params, keep), [view], cfg)
+    poisoned = CudaRender(bad, [view], cfg)
+    removed = CudaRender(subset(params, keep), [view], cfg)
     assert np.isfinite(poisoned.images[0]).all()
     np.testing.assert_array_equal(poisoned.images[0], removed.images[0])
 
 
 def test_instance_capacity_overflow_is_reported_and_recoverable():
     params, view, cfg = tiny_case()
-    full = GpuRun(params, [view], cfg)
+    full = CudaRender(params, [view], cfg)
     need = full.counts[1]
     small = RenderConfig(sh_degree=1, t_order=1, inst_capacity=max(1, need // 3))
     from paper_2412_20720_gb300.render import Renderer
@@ -549,7 +549,7 @@ def test_instance_capacity_overflow_is_reported_and_recoverable():
     code, counts = r.status()
     assert code == fgs4d.ERR_CAPACITY
     assert counts[1] == need // 3 and counts[3] == need
-    again = GpuRun(params, [view], RenderConfig(sh_degree=1, t_order=1, inst_capacity=counts[3]))
+    again = CudaRender(params, [view], RenderConfig(sh_degree=1, t_order=1, inst_capacity=counts[3]))
     np.testing.assert_array_equal(again.images[0], full.images[0])
 
 
@@ -570,7 +570,7 @@ def test_visible_capacity_overflow_is_reported():
 def _grad_case(params, view, cfg, seed=5):
     """GPU and oracle gradients of a loss whose image gradient is random at
     every pixel where each decision is settled (zero elsewhere)."""
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     ost = oracle_settings(cfg)
     _, flags = check_image(run, params, view, cfg)
     pr = oracle.preprocess(params, view, ost)
@@ -645,7 +645,7 @@ def test_render_stats_counts_the_composited_entries():
     from paper_2412_20720_gb300.render import Renderer
     from helpers import to_device
     params, view, cfg = tiny_case(128, 96, 1, 1)
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     _, flags = check_image(run, params, view, cfg)
     pr = oracle_proj(params, view, cfg)
     Tg, lastg = run.pixel_planes(0)

@@ -10,7 +10,7 @@ from paper_2412_20720_gb300 import fgs4d
 from paper_2412_20720_gb300 import synthetic as sy
 from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer, autotune
 
-from helpers import GpuRun, canonical_ranges, check_image, check_records, oracle_settings, to_device
+from helpers import CudaRender, canonical_ranges, check_image, check_records, oracle_settings, to_device
 from test_gpu_parity import KEEP_ALL, _grad_case, _synthetic_records, _write_records, check_gradients, tiny_case
 
 pytestmark = pytest.mark.gpu
@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("w,h,L,NT,bg", [(128, 96, 1, 1, (0.0, 0.0, 0.0)), (131, 77, 3, 2, (0.2, 0.5, 0.7))])
 def test_image_matches_oracle_at_tile_8(w, h, L, NT, bg):
     params, view, cfg = tiny_case(w, h, L, NT, bg, tile=8)
-    run = GpuRun(params, [view], cfg)
+    run = CudaRender(params, [view], cfg)
     check_records(run, params, view, cfg)
     check_image(run, params, view, cfg)
 
@@ -27,7 +27,7 @@ def test_image_matches_oracle_at_tile_8(w, h, L, NT, bg):
 def test_tile_8_block_shapes_render_identically():
     """Block shape and shared batch size change the work split only."""
     params, view, cfg = tiny_case(131, 77, 2, 1, (0.1, 0.1, 0.1), tile=8)
-    runs = [GpuRun(params, [view], RenderConfig(**{**cfg.__dict__, "pixels_per_thread": p, "shared_batch": b}))
+    runs = [CudaRender(params, [view], RenderConfig(**{**cfg.__dict__, "pixels_per_thread": p, "shared_batch": b}))
             for p, b in ((1, 256), (2, 256), (2, 128))]
     for run in runs[1:]:
         np.testing.assert_array_equal(run.images[0], runs[0].images[0])
@@ -73,7 +73,7 @@ def test_autotune_over_both_tile_sizes():
     assert r.settings.tile == res["tile"] and r.settings.pixels_per_thread == res["pixels_per_thread"]
     assert r.settings.shared_batch == res["shared_batch"]
     # The chosen tile edge renders the oracle's image at that edge.
-    run = GpuRun(params, [view], RenderConfig(**{**cfg.__dict__, "tile": res["tile"],
+    run = CudaRender(params, [view], RenderConfig(**{**cfg.__dict__, "tile": res["tile"],
                                                  "pixels_per_thread": res["pixels_per_thread"],
                                                  "shared_batch": res["shared_batch"]}))
     np.testing.assert_array_equal(run.images[0], r.split(r.forward(dev))[0].cpu().numpy())

@@ -20,6 +20,9 @@ beside it.  Per-stage times and the rooflines of the forward and backward
 compositors come from an untimed pass with one step alone.  "batched": the
 1M-Gaussian 64-view mixed-resolution workload and the 3M-Gaussian urban rig,
 with per-stage times.  "c0": the 2k-Gaussian 128x96 configuration.
+"extensions": the rows built beyond the render path (auxiliary channels,
+densification statistics and the 4D split, the Compact-4DGS mask, scale-gated
+features), each timed on the headline scene with its roofline.
 
 Timing: W untimed warm-up steps, then K steps between a barrier +
 synchronize on both sides, CUDA events on the launching stream, max over
@@ -98,6 +101,8 @@ def parse():
                                                  "instead of the autotune (for profiling a fixed kernel)")
     p.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     p.add_argument("--no-c0", action="store_true", help="skip the 2k-Gaussian configuration")
+    p.add_argument("--no-ext", action="store_true",
+                   help="skip the rows beyond the render path (aux channels, densification, mask, features)")
     return p.parse_args()
 
 
@@ -585,6 +590,13 @@ def run_ours(args, rank, world, local):
                 "urban-3M-%dviews-1920x1080-%d-per-call" % (len(uv), args.urban_group)
             batched.append(run_batched(dev, sy.urban_scene(), uv, label, 2, args.urban_group, plain=False, hbm=hbm))
 
+    # ---------------------------------------------------------- rows beyond the render path
+    ext = None
+    if not args.no_ext and rank == 0:
+        ext = run_extensions(dev, scene.n, params, [sy.orbit_view(k, nviews, W_IMG, H_IMG)
+                                                    for k in range(0, nviews, max(1, nviews // 8))][:8],
+                             fp32_peak, hbm)
+
     # ---------------------------------------------------------- C0
     c0 = None if args.no_c0 else run_tiny(dev)
 
@@ -639,6 +651,7 @@ def run_ours(args, rank, world, local):
             "train": train,
             "batched": batched,
             "c0": c0,
+            "extensions": ext,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -1066,6 +1079,175 @@ def run_batched(dev, scene, views, label, steps, group, plain=True, tiles=(16,),
         del per_res, singles
     del rs
     torch.cuda.empty_cache()
+    return out
+
+
+def run_extensions(dev, scene_n: int, params: dict, views, fp32_peak: float, hbm: float, reps: int = 3):
+    """The rows built beyond the render path, each on the headline scene (one
+    1352x1014 view per call, ``views`` of the sweep), timed with CUDA events
+    around the launches after the view's preprocess and bin_sort (mean of
+    ``reps`` after a warm-up, averaged over the views):
+
+    - auxiliary channels (depth, opacity, flow): fgs4d_render_aux and
+      fgs4d_render_aux_bwd against fgs4d_render_fwd / fgs4d_render_bwd;
+    - densification statistics: fgs4d_render_bwd with and without them, and
+      the 4D split of every Gaussian into 2 children;
+    - the Compact-4DGS mask: preprocess with and without the mask, and the
+      mask loss over 32M logits;
+    - scale-gated features, D = 8 / 16 / 32: the feature compositor and its
+      adjoint.
+
+    Compositor rooflines count FP32 flops (FMA = 2) per alpha evaluation and
+    per composited (pixel, entry) as the headline does, with the extra
+    channels' multiply-adds; the split and the mask loss count their bytes."""
+    import numpy as np
+    import torch
+
+    from paper_2412_20720_gb300 import fgs4d
+    from paper_2412_20720_gb300.render import PARAM_KEYS, RenderConfig, Renderer
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+    cfg = RenderConfig(sh_degree=3, t_order=2, inst_capacity=1 << 24)
+    r = Renderer(scene_n, views[:1], cfg, device=dev)
+    vv = [fgs4d.make_views([v]) for v in views]
+    ws, wsb = r.ws.data_ptr(), r.ws_bytes
+    g = r.gaussians(params)
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    mask_logit = (torch.randn(scene_n, generator=gen) + 2.0).to(dev)
+    gm = r.gaussians({**params, "mask_logit": mask_logit})
+    grads = {k: torch.zeros_like(params[k]) for k in PARAM_KEYS}
+    gg = r._grads(grads, None)
+    dens = torch.zeros(scene_n, 4, dtype=torch.float32, device=dev)
+    ggd = r._grads(grads, dens)
+    npx = r.total_pixels
+    rgb = torch.empty(3 * npx, dtype=torch.float32, device=dev)
+    aux = torch.empty(4 * npx, dtype=torch.float32, device=dev)
+    dL = torch.randn(3 * npx, generator=gen).to(dev) * 1e-3
+    dA = torch.cat([torch.randn(2 * npx, generator=gen), torch.zeros(2 * npx)]).to(dev) * 1e-3
+    feats = {D: torch.randn(scene_n, D, generator=gen).to(dev) for D in (8, 16, 32)}
+    gates = {D: torch.rand(D, generator=gen).to(dev) for D in (8, 16, 32)}
+    fout = {D: torch.empty(D * npx, dtype=torch.float32, device=dev) for D in (8, 16, 32)}
+    fdl = {D: (torch.randn(D * npx, generator=gen) * 1e-3).to(dev) for D in (8, 16, 32)}
+    fgrad = {D: torch.zeros(scene_n, D, dtype=torch.float32, device=dev) for D in (8, 16, 32)}
+    ggate = {D: torch.zeros(D, dtype=torch.float32, device=dev) for D in (8, 16, 32)}
+
+    def t_ms(fn):
+        fn()
+        acc = 0.0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            acc += a.elapsed_time(b)
+        return acc / reps
+
+    names = ["fwd", "bwd", "aux", "aux_bwd", "bwd_densify", "pre", "pre_mask"] + \
+        ["feat%d" % D for D in (8, 16, 32)] + ["feat%d_bwd" % D for D in (8, 16, 32)]
+    ms = {k: [] for k in names}
+    work = {"evals": [], "comps": [], "evals_bwd": []}
+    for v, n1 in vv:
+        def prep(gx=g):
+            fgs4d.preprocess(gx, v, n1, r.settings, ws, wsb, st)
+        def sort():
+            fgs4d.bin_sort(r.n, v, n1, r.settings, ws, wsb, st)
+        stats = torch.zeros(3, dtype=torch.int64, device=dev)
+        prep()
+        sort()
+        fgs4d.render_stats(r.n, v, n1, r.settings, ws, wsb, rgb.data_ptr(), stats.data_ptr(), st)
+        ev, co, evb = (int(x) for x in stats.tolist())
+        work["evals"].append(ev)
+        work["comps"].append(co)
+        work["evals_bwd"].append(evb)
+        ms["pre"].append(t_ms(prep))
+        ms["pre_mask"].append(t_ms(lambda: prep(gm)))
+        prep()
+        sort()
+        ms["aux"].append(t_ms(lambda: fgs4d.render_aux(g, v, n1, r.settings, ws, wsb, 0.01, rgb.data_ptr(), None,
+                                                       aux.data_ptr(), st)))
+        ms["aux_bwd"].append(t_ms(lambda: fgs4d.render_aux_bwd(g, v, n1, r.settings, ws, wsb, dL.data_ptr(),
+                                                               dA.data_ptr(), gg, st)))
+        ms["fwd"].append(t_ms(lambda: fgs4d.render_fwd(r.n, v, n1, r.settings, ws, wsb, rgb.data_ptr(), None, st)))
+        ms["bwd"].append(t_ms(lambda: fgs4d.render_bwd(g, v, n1, r.settings, ws, wsb, dL.data_ptr(), gg, st)))
+        ms["bwd_densify"].append(t_ms(lambda: fgs4d.render_bwd(g, v, n1, r.settings, ws, wsb, dL.data_ptr(), ggd,
+                                                               st)))
+        for D in (8, 16, 32):
+            ms["feat%d" % D].append(t_ms(lambda: fgs4d.render_features(
+                r.n, v, n1, r.settings, ws, wsb, feats[D].data_ptr(), D, gates[D].data_ptr(), fout[D].data_ptr(),
+                st)))
+            ms["feat%d_bwd" % D].append(t_ms(lambda: fgs4d.render_features_bwd(
+                r.n, v, n1, r.settings, ws, wsb, feats[D].data_ptr(), D, gates[D].data_ptr(), fdl[D].data_ptr(),
+                fgrad[D].data_ptr(), ggate[D].data_ptr(), st)))
+    code, _ = r.status()
+    m = {k: float(np.mean(x)) for k, x in ms.items()}
+    ev, co, evb = (float(np.mean(work[k])) for k in ("evals", "comps", "evals_bwd"))
+
+    def alu(flops, t):
+        return {"bound": "alu", "achieved": flops / t / 1e9, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": flops / t / 1e9 / fp32_peak, "flops_per_launch": flops, "launch_ms": t}
+
+    # Split: every Gaussian into 2 children (0.59 GB moved); mask loss over
+    # 32M logits (384 MB: larger than L2, as at the paper's largest scenes
+    # with several times their Gaussians between prunings).
+    nsplit, kids = scene_n, 2
+    idx = torch.randperm(scene_n, generator=gen)[:nsplit].to(torch.int32).to(dev)
+    eps = torch.randn(nsplit, kids, 4, generator=gen).to(dev)
+    src = fgs4d.make_gaussians({k: params[k].data_ptr() for k in PARAM_KEYS}, scene_n)
+    outs = {k: torch.empty((nsplit * kids,) + tuple(params[k].shape[1:]), dtype=torch.float32, device=dev)
+            for k in PARAM_KEYS}
+    dst = fgs4d.GaussiansOut(*(outs[k].data_ptr() for k in PARAM_KEYS), nsplit * kids)
+    split_ms = t_ms(lambda: fgs4d.split_gaussians(src, idx.data_ptr(), nsplit, kids, eps.data_ptr(), 1.6,
+                                                  r.settings, dst, st))
+    row = sum(int(np.prod(params[k].shape[1:])) * 4 for k in PARAM_KEYS)  # bytes of one Gaussian's parameters
+    split_bytes = nsplit * (4 + row) + nsplit * kids * (16 + row)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    n_mask = 32 << 20
+    big_logit = torch.randn(n_mask, generator=gen).to(dev)
+    mgrad = torch.zeros(n_mask, dtype=torch.float32, device=dev)
+    mloss_ms = t_ms(lambda: fgs4d.mask_loss(big_logit.data_ptr(), n_mask, loss.data_ptr(), mgrad.data_ptr(), st))
+    mloss_bytes = 12.0 * n_mask
+
+    def hbm_line(b, t):
+        return {"bound": "hbm", "achieved": b / t / 1e6, "peak": hbm, "unit": "GB/s", "frac": b / t / 1e6 / hbm,
+                "bytes_per_launch": b, "launch_ms": t}
+
+    aux_extra = 6  # depth and the two flow channels: three multiply-adds per composited entry
+    out = {
+        "workload": "%s, %d views of the sweep, one view per call" % (WORKLOAD, len(views)),
+        "status": fgs4d.status_string(code),
+        "basis": "CUDA events around each launch after the view's preprocess and bin_sort, mean of %d runs after a "
+                 "warm-up, averaged over the views" % reps,
+        "work_per_view": {"alpha_evals": ev, "composited": co, "alpha_evals_bwd": evb},
+        "aux_channels": {
+            "render_aux_ms": m["aux"], "render_fwd_ms": m["fwd"], "render_aux_bwd_ms": m["aux_bwd"],
+            "render_bwd_ms": m["bwd"],
+            "roofline": alu(FLOPS_PER_EVAL * ev + (FLOPS_PER_COMP + aux_extra) * co, m["aux"]),
+            "roofline_bwd": alu(FLOPS_PER_EVAL * evb + (FLOPS_PER_BWD_COMP + 6) * co, m["aux_bwd"]),
+            "flops_basis": "forward: %d per evaluation, %d per composited entry (colour + depth + flow); backward: "
+                           "%d per evaluation up to the last composited entry, %d per composited entry"
+                           % (FLOPS_PER_EVAL, FLOPS_PER_COMP + aux_extra, FLOPS_PER_EVAL, FLOPS_PER_BWD_COMP + 6)},
+        "densify": {
+            "render_bwd_ms": m["bwd"], "render_bwd_with_stats_ms": m["bwd_densify"],
+            "overhead": m["bwd_densify"] / m["bwd"] - 1.0,
+            "split": {"parents": nsplit, "children_per_parent": kids, "ms": split_ms,
+                      "roofline": hbm_line(split_bytes, split_ms),
+                      "bytes_basis": "index and parameter row of each parent read, one 4D draw read and one "
+                                     "parameter row written per child (%d B a row)" % row}},
+        "mask": {
+            "preprocess_ms": m["pre"], "preprocess_with_mask_ms": m["pre_mask"],
+            "overhead": m["pre_mask"] / m["pre"] - 1.0,
+            "mask_loss": {"gaussians": n_mask, "ms": mloss_ms, "roofline": hbm_line(mloss_bytes, mloss_ms),
+                          "bytes_basis": "mask logit read, gradient read and written (12 B per Gaussian)"}},
+        "features": {},
+    }
+    for D in (8, 16, 32):
+        out["features"]["D%d" % D] = {
+            "render_features_ms": m["feat%d" % D], "render_features_bwd_ms": m["feat%d_bwd" % D],
+            "roofline": alu(FLOPS_PER_EVAL * ev + (4 + 2 * D) * co, m["feat%d" % D]),
+            "roofline_bwd": alu(FLOPS_PER_EVAL * ev + (4 + 2 * D) * co, m["feat%d_bwd" % D]),
+            "flops_basis": "%d per evaluation, 4 + 2 D per composited entry (T alpha, T - T alpha, D multiply-adds; "
+                           "the adjoint: D multiply-adds into the per-entry sums)" % FLOPS_PER_EVAL}
     return out
 
 

@@ -857,48 +857,71 @@ struct SplitArgs {
   float *o_logit, *o_sh;
 };
 
+// One thread per child for the draw; the children's SH rows (the bulk of
+// the bytes) are then copied by whole warps, consecutive lanes on
+// consecutive floats of a row.
 __global__ void __launch_bounds__(128) split_kernel(SplitArgs A) {
   grid_dependency_sync();
-  const int64_t child = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (child >= A.m * A.k_children) return;
-  const int64_t j = child / A.k_children;
-  const int32_t i = A.idx[j];
-  float *osh = A.o_sh + child * A.k3;
-  if (i < 0 || (int64_t)i >= A.n) {
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    A.o_mean[child] = A.o_log_scale[child] = A.o_q_l[child] = A.o_q_r[child] = z;
-    A.o_logit[child] = 0.f;
-    for (int k = 0; k < A.k3; ++k) osh[k] = 0.f;
-    return;
-  }
-  const float4 m = A.mean[i], ls = A.log_scale[i], a4 = A.q_l[i], b4 = A.q_r[i];
-  const float il = rsqrtf(a4.x * a4.x + a4.y * a4.y + a4.z * a4.z + a4.w * a4.w);
-  const float ir = rsqrtf(b4.x * b4.x + b4.y * b4.y + b4.z * b4.z + b4.w * b4.w);
-  const float a = a4.x * il, b = a4.y * il, c = a4.z * il, d = a4.w * il;
-  const float p = b4.x * ir, q = b4.y * ir, r = b4.z * ir, s = b4.w * ir;
-  const float Lm[4][4] = {{a, -b, -c, -d}, {b, a, -d, c}, {c, d, a, -b}, {d, -c, b, a}};
-  const float Rm[4][4] = {{p, -q, -r, -s}, {q, p, s, -r}, {r, -s, p, q}, {s, r, -q, p}};
-  const float4 e = A.eps[child];
-  const float se[4] = {expf(ls.x) * e.x, expf(ls.y) * e.y, expf(ls.z) * e.z, expf(ls.w) * e.w};
-  float off[4];
+  __shared__ int32_t s_src[128];  // parent of each child of the block, -1: none
+  const int64_t total = A.m * A.k_children;
+  const int64_t c0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t child = c0 + threadIdx.x;
+  int32_t src = -1;
+  if (child < total) {
+    const int64_t j = child / A.k_children;
+    const int32_t i = A.idx[j];
+    if (i < 0 || (int64_t)i >= A.n) {
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      A.o_mean[child] = A.o_log_scale[child] = A.o_q_l[child] = A.o_q_r[child] = z;
+      A.o_logit[child] = 0.f;
+    } else {
+      src = i;
+      const float4 m = A.mean[i], ls = A.log_scale[i], a4 = A.q_l[i], b4 = A.q_r[i];
+      const float il = rsqrtf(a4.x * a4.x + a4.y * a4.y + a4.z * a4.z + a4.w * a4.w);
+      const float ir = rsqrtf(b4.x * b4.x + b4.y * b4.y + b4.z * b4.z + b4.w * b4.w);
+      const float a = a4.x * il, b = a4.y * il, c = a4.z * il, d = a4.w * il;
+      const float p = b4.x * ir, q = b4.y * ir, r = b4.z * ir, s = b4.w * ir;
+      const float Lm[4][4] = {{a, -b, -c, -d}, {b, a, -d, c}, {c, d, a, -b}, {d, -c, b, a}};
+      const float Rm[4][4] = {{p, -q, -r, -s}, {q, p, s, -r}, {r, -s, p, q}, {s, r, -q, p}};
+      const float4 e = A.eps[child];
+      const float se[4] = {expf(ls.x) * e.x, expf(ls.y) * e.y, expf(ls.z) * e.z, expf(ls.w) * e.w};
+      float off[4];
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    float acc = 0.f;
+      for (int x = 0; x < 4; ++x) {
+        float acc = 0.f;
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const float Rxy = Lm[x][0] * Rm[0][y] + Lm[x][1] * Rm[1][y] + Lm[x][2] * Rm[2][y] + Lm[x][3] * Rm[3][y];
-      acc += Rxy * se[y];
+        for (int y = 0; y < 4; ++y) {
+          const float Rxy = Lm[x][0] * Rm[0][y] + Lm[x][1] * Rm[1][y] + Lm[x][2] * Rm[2][y] + Lm[x][3] * Rm[3][y];
+          acc += Rxy * se[y];
+        }
+        off[x] = acc;
+      }
+      A.o_mean[child] = make_float4(m.x + off[0], m.y + off[1], m.z + off[2], m.w + off[3]);
+      A.o_log_scale[child] =
+          make_float4(ls.x - A.log_shrink, ls.y - A.log_shrink, ls.z - A.log_shrink, ls.w - A.log_shrink);
+      A.o_q_l[child] = a4;
+      A.o_q_r[child] = b4;
+      A.o_logit[child] = A.logit[i];
     }
-    off[x] = acc;
   }
-  A.o_mean[child] = make_float4(m.x + off[0], m.y + off[1], m.z + off[2], m.w + off[3]);
-  A.o_log_scale[child] =
-      make_float4(ls.x - A.log_shrink, ls.y - A.log_shrink, ls.z - A.log_shrink, ls.w - A.log_shrink);
-  A.o_q_l[child] = a4;
-  A.o_q_r[child] = b4;
-  A.o_logit[child] = A.logit[i];
-  const float *src = A.sh + (int64_t)i * A.k3;
-  for (int k = 0; k < A.k3; ++k) osh[k] = src[k];
+  s_src[threadIdx.x] = src;
+  __syncthreads();
+  const int nchild = (int)min64((int64_t)blockDim.x, total - c0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  // float4 copies when rows of both arrays start on 16-byte boundaries
+  const bool vec = (A.k3 & 3) == 0 && ((reinterpret_cast<uintptr_t>(A.sh) | reinterpret_cast<uintptr_t>(A.o_sh)) & 15) == 0;
+  const int width = vec ? A.k3 >> 2 : A.k3;
+  for (int c = warp; c < nchild; c += nwarps) {
+    const int32_t i = s_src[c];
+    const int64_t orow = (c0 + c) * A.k3, irow = (int64_t)(i >= 0 ? i : 0) * A.k3;
+    for (int k = lane; k < width; k += 32) {
+      if (vec)
+        reinterpret_cast<float4 *>(A.o_sh + orow)[k] =
+            i >= 0 ? reinterpret_cast<const float4 *>(A.sh + irow)[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      else
+        A.o_sh[orow + k] = i >= 0 ? A.sh[irow + k] : 0.f;
+    }
+  }
 }
 
 }  // namespace

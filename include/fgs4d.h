@@ -433,8 +433,9 @@ int fgs4d_wait_selftest(void *scratch, size_t scratch_bytes, void *stream);
  * synchronise the device and fail under a fixed memory budget).  The paper
  * has no counterpart; this is a packaging of the depth-sort step of
  * fgs4d_bin_sort.
- * Input: depth_keys, device uint32 [n] (FP32 bit patterns of positive depths;
- * any uint32 keys sort correctly).  Output: sorted_slots, device uint32 [n],
+ * Input: depth_keys, device uint32 [n] at any 4-byte aligned address (FP32 bit
+ * patterns of positive depths; any uint32 keys sort correctly).  Output:
+ * sorted_slots, device uint32 [n],
  * the indices 0..n-1 in (key, index) order -- the same permutation
  * fgs4d_bin_sort writes to its sorted_slots region for the same keys.
  * Scratch: one library-owned device array of about 18 MB (FGS4D_STATIC_SORT_MAX

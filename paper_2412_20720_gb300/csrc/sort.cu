@@ -160,7 +160,8 @@ constexpr size_t radix_smem_bytes() {
 // ticket is kSub consecutive sub-tiles of kSortThreads x kItems keys.  Each
 // warp copies the keys (and values) it ranks into shared memory with
 // cp.async, one copy group per sub-tile, so later sub-tiles arrive while the
-// first is ranked.  Ranking is stable within a warp's segment (item-major,
+// first is ranked (16-byte copies: keys_in and vals_in start on 16-byte
+// boundaries, as the workspace's arrays do).  Ranking is stable within a warp's segment (item-major,
 // lane-minor): the lanes holding the same digit are found by nine ballots
 // (eight digit bits and the padding bit), and the lowest of them adds the
 // group's size to the warp's count of that digit.  Each sub-tile is then
@@ -947,9 +948,18 @@ extern "C" int fgs4d_sort_depth_static(const uint32_t *depth_keys, int64_t n, ui
   radix_hist_kernel<kSortItems><<<blocks, kSortThreads, 0, st>>>(depth_keys, &s->ctl[0], FGS4D_STATIC_SORT_MAX,
                                                           kMaxPasses, &s->hist[0][0], &s->state[0][0][0],
                                                           kStaticSortBlocks, nullptr, 0);
+  // The passes stage keys with 16-byte copies: keys that do not start on a
+  // 16-byte boundary are first copied into the buffer pass 0 does not write.
+  const uint32_t *keys0 = depth_keys;
+  if (reinterpret_cast<uintptr_t>(depth_keys) & 15u) {
+    if (cudaMemcpyAsync(s->keys[1], depth_keys, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return FGS4D_ERR_CUDA;
+    keys0 = s->keys[1];
+  }
   for (int p = 0; p < kMaxPasses; ++p) {
     const int out = p & 1, in = out ^ 1;
-    const uint32_t *kin = p == 0 ? depth_keys : s->keys[in];
+    const uint32_t *kin = p == 0 ? keys0 : s->keys[in];
     uint32_t *vout = p == kMaxPasses - 1 ? sorted_slots : s->vals[out];
     if (p == 0)
       radix_pass_kernel<true, kSortItems, 1><<<blocks, kSortThreads, smem, st>>>(kin, nullptr, s->keys[out], vout, &s->ctl[0],

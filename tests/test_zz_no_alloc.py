@@ -60,6 +60,24 @@ def test_static_depth_sort_matches_bin_sort_on_consecutive_calls():
         np.testing.assert_array_equal(out.cpu().numpy(), np.argsort(keys, kind="stable"))
 
 
+def test_static_depth_sort_takes_keys_at_any_4_byte_boundary():
+    """Keys that start 4, 8 and 12 bytes past a 16-byte boundary (a slice of a
+    larger array) sort like aligned ones."""
+    import torch
+    rng = np.random.default_rng(22)
+    stream = torch.cuda.current_stream().cuda_stream
+    n = 100_003
+    keys = _depth_keys(rng, n + 3)
+    base = torch.from_numpy(keys.view(np.int32)).cuda()
+    assert base.data_ptr() % 16 == 0
+    for off in (1, 2, 3):
+        sub = keys[off:off + n]
+        out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        fgs4d.sort_depth_static(base.data_ptr() + 4 * off, n, out.data_ptr(), stream)
+        assert fgs4d.sort_depth_static_status(stream) == fgs4d.OK
+        np.testing.assert_array_equal(out.cpu().numpy(), np.argsort(sub, kind="stable"))
+
+
 def test_static_depth_sort_allocates_no_device_memory():
     """After a first call (which looks up the scratch's address), further
     calls leave the device memory in use unchanged."""

@@ -32,6 +32,18 @@ template <int TILE>
 __host__ __device__ constexpr int feat_threads() {
   return TILE * TILE / kFeatPPT;
 }
+// The adjoint reduces D sums per (warp, entry): with D <= 16 it takes 4-pixel
+// strips at 16x16 (64 threads), half the warps per tile and so half the
+// reductions.  Alpha does not depend on the strip shape (row groups), so it
+// still equals the forward's bit for bit.
+template <int TILE, int D>
+__host__ __device__ constexpr int feat_bwd_ppt() {
+  return (TILE == 16 && D <= 16) ? 4 : kFeatPPT;
+}
+template <int TILE, int D>
+__host__ __device__ constexpr int feat_bwd_threads() {
+  return TILE * TILE / feat_bwd_ppt<TILE, D>();
+}
 
 struct FeatArgs {
   const uint2 *ranges;
@@ -193,9 +205,11 @@ __device__ __forceinline__ float warp_transpose_sum(float (&a)[32], int lane) {
 }
 
 template <int MAXV, int TILE, int D>
-__global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kernel(FeatArgs A, RasterViews<MAXV> rv) {
+__global__ void __launch_bounds__(feat_bwd_threads<TILE, D>())
+    render_features_bwd_kernel(FeatArgs A, RasterViews<MAXV> rv) {
   grid_dependency_sync();
-  constexpr int kFeatBatch = feat_threads<TILE>();
+  constexpr int kPPT = feat_bwd_ppt<TILE, D>();
+  constexpr int kFeatBatch = feat_bwd_threads<TILE, D>();
   __shared__ float4 s_geom[kFeatBatch];
   __shared__ float2 s_ca[kFeatBatch];
   __shared__ int32_t s_gi[kFeatBatch];
@@ -209,7 +223,7 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
   const int32_t lt = gt - V.tile_base;
   const int32_t tx = lt % V.gw, ty = lt / V.gw;
   const int32_t px = tx * TILE + (threadIdx.x & (TILE - 1));
-  const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * kFeatPPT;
+  const int32_t py0 = ty * TILE + (threadIdx.x / TILE) * kPPT;
   const uint2 range = tile_range(A.ranges, gt);
   const float pxc = (float)px + 0.5f;
   const int lane = threadIdx.x & 31;
@@ -220,10 +234,10 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
   const int64_t HW = (int64_t)V.width * V.height;
   const float *dF = A.dL_dF + V.pix_base * D;
   const float gyc = row_group_centre(py0);
-  float T[kFeatPPT], off[kFeatPPT], G[kFeatPPT][D];
+  float T[kPPT], off[kPPT], G[kPPT][D];
   bool live = false;
 #pragma unroll
-  for (int k = 0; k < kFeatPPT; ++k) {
+  for (int k = 0; k < kPPT; ++k) {
     const bool in = px < V.width && py0 + k < V.height;
     T[k] = in ? 1.0f : -1.0f;
     off[k] = in ? row_offset(py0 + k) : stopped_offset();
@@ -250,7 +264,7 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
       for (int c = 0; c < 32; ++c) v[c] = 0.f;
       bool contrib = false;
 #pragma unroll
-      for (int k = 0; k < kFeatPPT; ++k) {
+      for (int k = 0; k < kPPT; ++k) {
         const AlphaEval e = pixel_alpha(ct, w4, ca.x, off[k], clamp);
         if (e.alpha >= kAlphaMin) {  // false for stopped pixels (row offset +inf)
           const float w = __fmul_rn(e.alpha, T[k]);
@@ -268,7 +282,7 @@ __global__ void __launch_bounds__(feat_threads<TILE>()) render_features_bwd_kern
       }
       live = false;
 #pragma unroll
-      for (int k = 0; k < kFeatPPT; ++k) live = live || T[k] > 0.0f;
+      for (int k = 0; k < kPPT; ++k) live = live || T[k] > 0.0f;
       if (!__any_sync(0xffffffffu, contrib)) continue;
       const int32_t gi = s_gi[j];
       const float vc = warp_transpose_sum<D>(v, lane);  // lane c: component c of the warp's sum
@@ -290,7 +304,9 @@ template <int MAXV, int TILE, int D>
 cudaError_t launch_feat_tile(const FeatArgs &A, const RasterViews<MAXV> &rv, unsigned grid, bool backward,
                              cudaStream_t st) {
   constexpr unsigned NT = feat_threads<TILE>();
-  if (backward) return launch_pdl(render_features_bwd_kernel<MAXV, TILE, D>, grid, NT, st, A, rv);
+  if (backward)
+    return launch_pdl(render_features_bwd_kernel<MAXV, TILE, D>, grid, (unsigned)feat_bwd_threads<TILE, D>(), st, A,
+                      rv);
   return launch_pdl(render_features_kernel<MAXV, TILE, D>, grid, NT, st, A, rv);
 }
 

@@ -29,11 +29,11 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = kFlagAgg - 1u;
 
-// Decoupled look-back of digit d for radix tile b: publishes the tile's count
-// of the digit, sums the counts of the tiles before it back to the nearest
-// inclusive prefix (reading a window of kWin predecessor tiles per round trip:
-// their words are independent loads), publishes the tile's inclusive prefix
-// and returns the exclusive one.  Flag and value share one word, so relaxed
+// Decoupled look-back of digit d for ticket b (one or more radix sub-tiles):
+// publishes the ticket's count of the digit, sums the counts of the tickets
+// before it back to the nearest inclusive prefix (reading a window of kWin
+// predecessors per round trip: their words are independent loads), publishes
+// the ticket's inclusive prefix and returns the exclusive one.  Flag and value share one word, so relaxed
 // accesses suffice.  A predecessor that never posts makes the wait give up
 // after kSpinLimit polls: the timeout bit is set and the partial prefix
 // returned (the caller's bounds checks keep every store in range).

@@ -578,8 +578,9 @@ def run_ours(args, rank, world, local):
             train["cpu_baseline"] = cpu_train
 
     # ---------------------------------------------------------- batched views
+    # (rank 0 only: the other ranks' lines are not printed, and no collective follows)
     batched = None
-    if not args.no_batched:
+    if not args.no_batched and rank == 0:
         batched = []
         if args.batched in ("all", "sphere"):
             batched.append(run_batched(dev, sy.sphere_scene(), sy.sphere_views(64), "sphere-1M-64views-mixed-res", 2, 8,
@@ -598,7 +599,7 @@ def run_ours(args, rank, world, local):
                              fp32_peak, hbm)
 
     # ---------------------------------------------------------- C0
-    c0 = None if args.no_c0 else run_tiny(dev)
+    c0 = None if args.no_c0 or rank != 0 else run_tiny(dev)
 
     if rank == 0:
         line = {

@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
       const float4 geom = s_geom[j];
       const float4 col = s_col[j];
       const float blue = s_blue[j];
+      const float4 xa = kAux ? s_aux[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // depth and flow of the entry
       const ColumnTerms ct = column_terms(geom, pxc, col.y);
       float w4[kGroups];
 #pragma unroll
@@ -203,10 +204,9 @@ __global__ void __launch_bounds__(TILE *TILE / PPT, (fwd_min_blocks<TILE, PPT, k
             C1[k] = __fmaf_rn(col.w, w, C1[k]);
             C2[k] = __fmaf_rn(blue, w, C2[k]);
             if (kAux) {
-              const float4 x = s_aux[j];
-              X0[k] = __fmaf_rn(x.x, w, X0[k]);
-              X1[k] = __fmaf_rn(x.y, w, X1[k]);
-              X2[k] = __fmaf_rn(x.z, w, X2[k]);
+              X0[k] = __fmaf_rn(xa.x, w, X0[k]);
+              X1[k] = __fmaf_rn(xa.y, w, X1[k]);
+              X2[k] = __fmaf_rn(xa.z, w, X2[k]);
             }
             T[k] = Tn;
             if (kTrack) last[k] = pos0 + (uint32_t)j;

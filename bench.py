@@ -71,7 +71,7 @@ ISSUE_PER_SM_CLK = 4
 # views 0-2).  Valid only for the compositor sources it was taken from
 # (sha256 prefix of csrc/render.cu + csrc/fgs4d_internal.cuh) and block
 # shape; any other build reports null.
-NCU_RENDER_FWD = {"render_cu_sha256": "853160f27f8a77c9", "shape": "16/4/128", "dram_bytes": 5.02e6, "warp_insts": 125.43e6,
+NCU_RENDER_FWD = {"render_cu_sha256": "eb51d3ae1b99e20c", "shape": "16/4/128", "dram_bytes": 5.02e6, "warp_insts": 125.43e6,
                   "views": [0, 1, 2], "capture": "ncu --set full --clock-control none --nvtx --nvtx-include timed/ "
                                                  "-k regex:render_fwd_kernel -c 3 on python bench.py --steps 1 "
                                                  "--warmup 1 --shape 16/4/128 (no other legs)"}

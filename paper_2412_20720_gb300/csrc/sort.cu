@@ -629,7 +629,8 @@ __device__ __forceinline__ void set_instance_total(const EmitArgs &A, uint64_t a
 
 // Thread t of chunk c decides pairs c kEmitChunk + 8 t + [0, 8) and keeps
 // the tile ids and slots of the kept ones in registers; a block scan and the
-// look-back over the chunks give their output positions.  Persistent: chunks
+// look-back over the chunks give their output positions (the pairs are staged
+// in shared memory meanwhile and written with coalesced stores).  Persistent: chunks
 // are taken by ticket, so a chunk's look-back only waits on chunks that
 // running blocks hold.  Also clears the tile sort's look-back rows of the
 // radix tiles covering chunk c's pairs (there are no more instances than
@@ -684,28 +685,46 @@ __global__ void __launch_bounds__(kEmitBlock) emit_kernel(EmitArgs A, RasterView
     }
     uint32_t total;
     const uint32_t local = block_exclusive_scan(__popc(m), s_scan, &total);
+    // The kept pairs go to shared memory in pair order, and the tile-id
+    // histograms are taken, while warp 0 looks back (it stages its own
+    // afterwards); the chunk is then written with coalesced stores.  The
+    // walk is over (the scan's barriers), so the chunk's records and pair
+    // prefix hold the staged tile ids and slots.
+    static_assert(sizeof S.rec >= kEmitChunk * sizeof(uint32_t) && sizeof S.pref >= kEmitChunk * sizeof(uint32_t),
+                  "staging fits");
+    uint32_t *s_stage_key = reinterpret_cast<uint32_t *>(S.rec), *s_stage_val = S.pref;
+    auto stage = [&]() {
+      uint32_t q = local;
+#pragma unroll
+      for (int k = 0; k < kPairsPerThread; ++k) {
+        if (m & (1u << k)) {
+          s_stage_key[q] = kt[k];
+          s_stage_val[q] = ks[k];
+          ++q;
+          for (int p = 0; p < A.tile_passes; ++p)
+            atomicAdd(&s_hist[p][(kt[k] >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
+        }
+      }
+    };
+    if (threadIdx.x >= 32) stage();
     if (threadIdx.x < 32) {
       const uint64_t prefix = lookback_u64_warp(A.lb_chunk, (int32_t)c, total, &A.counters[kCtrStatus]);
       if (threadIdx.x == 0) {
         s_prefix = prefix;
         if (c == nchunks - 1u) set_instance_total(A, prefix + total);
       }
+      stage();
     }
     __syncthreads();
-    uint64_t pos = s_prefix + local;
-#pragma unroll
-    for (int k = 0; k < kPairsPerThread; ++k) {
-      if (m & (1u << k)) {
-        if (pos < (uint64_t)A.inst_cap) {
-          A.inst_key[pos] = kt[k];
-          A.inst_val[pos] = ks[k];
-        }
-        ++pos;
-        for (int p = 0; p < A.tile_passes; ++p)
-          atomicAdd(&s_hist[p][(kt[k] >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
+    const uint64_t base = s_prefix;
+    for (uint32_t t = threadIdx.x; t < total; t += kEmitBlock) {
+      const uint64_t pos = base + t;
+      if (pos < (uint64_t)A.inst_cap) {
+        A.inst_key[pos] = s_stage_key[t];
+        A.inst_val[pos] = s_stage_val[t];
       }
     }
-    __syncthreads();  // S, s_ticket and s_prefix are reused by the next chunk
+    __syncthreads();  // S, the staged pairs, s_ticket and s_prefix are reused by the next chunk
   }
   for (int p = 0; p < A.tile_passes; ++p) {
     const uint32_t h = s_hist[p][threadIdx.x];

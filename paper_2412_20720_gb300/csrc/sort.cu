@@ -161,8 +161,9 @@ constexpr size_t radix_smem_bytes() {
 // warp copies the keys (and values) it ranks into shared memory with
 // cp.async, one copy group per sub-tile, so later sub-tiles arrive while the
 // first is ranked (16-byte copies: keys_in and vals_in start on 16-byte
-// boundaries, as the workspace's arrays do).  Ranking is stable within a warp's segment (item-major,
-// lane-minor): the lanes holding the same digit are found by nine ballots
+// boundaries, as the workspace's arrays do).  Ranking is stable within a
+// warp's segment (item-major, lane-minor): the lanes holding the same digit
+// are found by nine ballots
 // (eight digit bits and the padding bit), and the lowest of them adds the
 // group's size to the warp's count of that digit.  Each sub-tile is then
 // placed in block-local digit order in its own part of the buffer.  One

@@ -271,12 +271,13 @@ def _read_instances(r, m, ntiles):
 # Visible capacities equal to the slot count and well above it (the pair scan
 # and depth sort size their grids and look-back rows by the capacity); an
 # instance capacity of 2^26 takes the instance sort with three sub-tiles per
-# ticket.
-@pytest.mark.parametrize("n,W,H,vis_cap,inst_cap", [(1, 16, 16, 0, 0), (2047, 144, 112, 0, 0),
-                                                    (70_001, 1352, 1014, 0, 0), (70_001, 1352, 1014, 400_000, 0),
-                                                    (150_001, 1352, 1014, 0, 0), (2047, 144, 112, 0, 1 << 26),
-                                                    (150_001, 1352, 1014, 0, 1 << 26)])
-def test_bin_sort_bit_exact_on_synthetic_records(n, W, H, vis_cap, inst_cap):
+# ticket; stage_blocks_per_sm > 0 takes the lean (one or two blocks per SM)
+# persistent grids.
+@pytest.mark.parametrize("n,W,H,vis_cap,inst_cap,stage_blocks", [
+    (1, 16, 16, 0, 0, 0), (2047, 144, 112, 0, 0, 0), (70_001, 1352, 1014, 0, 0, 0),
+    (70_001, 1352, 1014, 400_000, 0, 0), (150_001, 1352, 1014, 0, 0, 0), (2047, 144, 112, 0, 1 << 26, 0),
+    (150_001, 1352, 1014, 0, 1 << 26, 0), (150_001, 1352, 1014, 0, 1 << 26, 1), (70_001, 1352, 1014, 0, 0, 2)])
+def test_bin_sort_bit_exact_on_synthetic_records(n, W, H, vis_cap, inst_cap, stage_blocks):
     """With ellipses that meet every tile, the sorted instance list and tile
     ranges equal the oracle's bit for bit: one instance per tile of each
     rect, ordered by (tile, FP32 depth, slot), on records written straight
@@ -286,7 +287,8 @@ def test_bin_sort_bit_exact_on_synthetic_records(n, W, H, vis_cap, inst_cap):
     rng = np.random.default_rng(n)
     gw, gh = (W + 15) // 16, (H + 15) // 16
     rec = _synthetic_records(rng, n, W, H, 6, tau=KEEP_ALL)
-    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=inst_cap or 40 * n + 16, vis_capacity=vis_cap)
+    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=inst_cap or 40 * n + 16, vis_capacity=vis_cap,
+                       stage_blocks_per_sm=stage_blocks)
     r = Renderer(n, [sy.tiny_view(W, H)], cfg)
     _write_records(r, rec, 0)
     fgs4d.bin_sort(n, r.views, r.nviews, r.settings, r.ws.data_ptr(), r.ws_bytes, r.stream())
@@ -468,10 +470,11 @@ def test_instance_list_is_the_rect_membership_minus_skipped_pairs():
     assert check_instance_list(run, params, view, cfg) > 100
 
 
-def test_instance_list_at_tile_8_and_several_views():
+@pytest.mark.parametrize("inst_cap", [1 << 19, 1 << 26])  # 2^26: three sub-tiles per tile-sort ticket
+def test_instance_list_at_tile_8_and_several_views(inst_cap):
     sc = sy.make_scene(3000, 14, (-1, -1, -1), (1, 1, 1), sh_degree=1, t_order=1)
     views = [sy.tiny_view(96, 80, t=0.4), sy.look_at((1.5, -0.5, -2.5), (0, 0, 0), (0, -1, 0), 100, 70, 0.6)]
-    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=1 << 19, tile=8)
+    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=inst_cap, tile=8)
     params = sc.as_dict()
     run = CudaRender(params, views, cfg)
     for k, v in enumerate(views):

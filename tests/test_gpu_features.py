@@ -13,10 +13,10 @@ from helpers import (check_pixels, compare_group, loss_gradient_at_settled_pixel
 pytestmark = pytest.mark.gpu
 
 
-def feat_case(D, ts=(0.5,), seed=17, n=1500):
+def feat_case(D, ts=(0.5,), seed=17, n=1500, tile=16):
     sc = sy.make_scene(n, seed, (-1, -1, -1), (1, 1, 1), sh_degree=1, t_order=1)
     views = [sy.tiny_view(96, 72, t=t) for t in ts]
-    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=1 << 18)
+    cfg = RenderConfig(sh_degree=1, t_order=1, inst_capacity=1 << 18, tile=tile)
     params = sc.as_dict()
     rng = np.random.default_rng(seed)
     feats = rng.standard_normal((params["mean"].shape[0], D)).astype(np.float32)
@@ -50,10 +50,12 @@ def test_feature_map_matches_oracle(D, ts):
         assert np.abs(got[k].reshape(D, -1).T - chosen[:, 5:]).max() <= 2e-4
 
 
-def test_feature_backward_matches_oracle():
+# The adjoint takes 4-pixel strips for D <= 16 on 16-pixel tiles, 2-pixel
+# strips otherwise.
+@pytest.mark.parametrize("D,tile", [(32, 16), (16, 16), (8, 16), (8, 8)])
+def test_feature_backward_matches_oracle(D, tile):
     import torch
-    D = 32
-    params, views, cfg, feats, gate = feat_case(D, seed=18)
+    params, views, cfg, feats, gate = feat_case(D, seed=18, tile=tile)
     view = views[0]
     st = oracle_settings(cfg)
     flags = oracle_flags(oracle_proj(params, view, cfg), view, cfg)

@@ -52,17 +52,28 @@ def test_densify_stats_match_oracle_over_views():
     assert np.all(got[:, 3] == 0)
 
 
-def test_split_children_match_oracle():
+# SH rows of 144, 54 and 3 floats: copied as float4 when the row length is a
+# multiple of 4, as floats otherwise.  One parent index is out of range: its
+# children are written as zeros.
+@pytest.mark.parametrize("L,NT", [(3, 2), (2, 1), (0, 0)])
+def test_split_children_match_oracle(L, NT):
     import torch
-    sc = sy.make_scene(500, 11, (-1, -1, -1), (1, 1, 1), sh_degree=3, t_order=2)
+    sc = sy.make_scene(500, 11, (-1, -1, -1), (1, 1, 1), sh_degree=L, t_order=NT)
     params = sc.as_dict()
     rng = np.random.default_rng(12)
     idx = rng.choice(500, 77, replace=False).astype(np.int32)
     eps = rng.standard_normal((77, 3, 4)).astype(np.float32)
-    cfg = RenderConfig(sh_degree=3, t_order=2)
-    out = split_gaussians(to_device(params), torch.from_numpy(idx).cuda(), torch.from_numpy(eps).cuda(), 1.6, cfg)
+    bad = 5
+    idx_gpu = idx.copy()
+    idx_gpu[bad] = 500  # out of range
+    cfg = RenderConfig(sh_degree=L, t_order=NT)
+    out = split_gaussians(to_device(params), torch.from_numpy(idx_gpu).cuda(), torch.from_numpy(eps).cuda(), 1.6,
+                          cfg)
     torch.cuda.synchronize()
     ref = oracle.split_sample(params, idx, eps, 1.6)
+    for k in PARAM_KEYS:
+        ref[k] = np.array(ref[k], copy=True)
+        ref[k][3 * bad:3 * bad + 3] = 0.0
     for k in PARAM_KEYS:
         got = out[k].cpu().numpy().astype(np.float64)
         assert got.shape == ref[k].shape, k
